@@ -1,0 +1,374 @@
+"""Benchmark: Monte Carlo edge-weighted PPR on one GB300 (or N, sharded by source).
+
+One step = one pass of the whole hot path over the workload: build the walk
+layout from the device-resident CSR (node records, weight prefixes), run R
+walks from every source with the persistent walker, and aggregate the
+endpoints into sparse count rows and top-k.  The metric is walk steps per
+second (draws consumed); walks per second and the roofline of the walker
+kernel are reported beside it.
+
+Default workload: R-MAT scale 20 (1,048,576 nodes, 16.8M edges plus the
+dangling repair), Zipf(1.5) weights in [1, 1000], ~5 % dangling nodes,
+alpha = 0.2, R = 100, top-32 per source, Philox seed 1.
+
+--impl reference times the CPU oracle (single-threaded C) on a bounded sample
+of the same workload and prints the same line with "impl": "reference".
+"""
+from __future__ import annotations
+
+import argparse
+import hashlib
+import json
+import os
+import statistics
+import subprocess
+import sys
+import time
+
+import numpy as np
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+WORKLOADS = {
+    "rmat20": dict(alpha=0.2, R=100, seed=1, topk=32, segments=False,
+                   desc="R-MAT scale 20, 16.8M edges (a=.57 b=.19 c=.19), Zipf(1.5) w in [1,1000], 5% dangling"),
+    "er1k": dict(alpha=0.15, R=1000, seed=1, topk=32, segments=False,
+                 desc="Erdos-Renyi n=1000 m=10000, w U[1,10]"),
+}
+L2_FLUSH_BYTES = 512 << 20
+
+
+def env_rank():
+    return int(os.environ.get("RANK", 0)), int(os.environ.get("WORLD_SIZE", 1)), int(os.environ.get("LOCAL_RANK", 0))
+
+
+def shard(n_src: int, rank: int, world: int):
+    """Contiguous source range of a rank: sources are independent, so ranks
+    share nothing but the graph (replicated)."""
+    per = (n_src + world - 1) // world
+    a = min(n_src, rank * per)
+    return a, min(n_src, a + per)
+
+
+class Clocks:
+    """nvidia-smi sampling of SM clocks and throttle reasons during the timed region."""
+
+    FIELDS = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+              "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+              "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, device: int, path: str | None):
+        self.path = path or os.path.join(ROOT, "gpurun_out", f"clocks_{os.getpid()}.csv")
+        self.device = device
+        self.proc = None
+
+    def start(self):
+        try:
+            os.makedirs(os.path.dirname(self.path), exist_ok=True)
+            self.f = open(self.path, "w")
+            self.proc = subprocess.Popen(["nvidia-smi", f"--id={self.device}", f"--query-gpu={self.FIELDS}",
+                                          "--format=csv,noheader,nounits", "-lms", "200"], stdout=self.f,
+                                         stderr=subprocess.DEVNULL)
+        except (OSError, FileNotFoundError):
+            self.proc = None
+
+    def stop(self):
+        if not self.proc:
+            return None
+        self.proc.terminate()
+        try:
+            self.proc.wait(timeout=5)
+        except subprocess.TimeoutExpired:
+            self.proc.kill()
+        self.f.close()
+        sm, smax, reasons = [], 0.0, set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        for line in open(self.path):
+            parts = [p.strip() for p in line.split(",")]
+            if len(parts) < 9:
+                continue
+            try:
+                sm.append(float(parts[1]))
+                smax = max(smax, float(parts[2]))
+            except ValueError:
+                continue
+            for nm, v in zip(names, parts[5:9]):
+                if v.lower() == "active":
+                    reasons.add(nm)
+        if not sm:
+            return None
+        return {"sm_mhz": statistics.median(sm), "sm_max_mhz": smax, "reasons": sorted(reasons), "samples": len(sm)}
+
+
+def measured_peaks():
+    p = os.path.join(ROOT, "MEASURED_PEAKS.json")
+    if os.path.exists(p):
+        d = json.load(open(p))
+        return float(d["hbm_gbs"]), "measured"
+    return 6800.0, "fallback"
+
+
+def kernel_source_hash():
+    h = hashlib.sha256()
+    for f in ("walk.cu", "ppr_internal.cuh"):
+        h.update(open(os.path.join(ROOT, "paper_1903_11749_gb300", "csrc", f), "rb").read())
+    return h.hexdigest()[:16]
+
+
+def recorded_traffic(workload: str):
+    """DRAM bytes per walker launch from the committed ncu summary, if it was
+    taken on the current kernel source; else None."""
+    p = os.path.join(ROOT, "profiles", "walker_traffic.json")
+    if not os.path.exists(p):
+        return None
+    d = json.load(open(p))
+    e = d.get(workload)
+    if not e or e.get("kernel_hash") != kernel_source_hash():
+        return None
+    return e.get("dram_bytes_per_launch")
+
+
+def cpu_baseline(g, wl, budget_s: float = 15.0):
+    """The oracle as it stands (single-threaded C + numpy counting) on an evenly
+    strided sample of sources; returns steps/s and a description."""
+    sys.path.insert(0, os.path.join(ROOT, "oracle"))
+    import oracle as O
+    O.build()
+    og = O.prepare(g.n, g.row_ptr, g.col, g.w)
+    # calibrate on a small sample, then size the sample to the budget
+    t0 = time.perf_counter()
+    ends, steps = O.walks(og, wl["alpha"], wl["R"], wl["seed"], 0, 200)
+    dt = max(time.perf_counter() - t0, 1e-3)
+    n_src = int(max(200, min(g.n, 200 * budget_s / dt)))
+    stride = max(1, g.n // n_src)
+    total_steps, total_walks, t_all = 0, 0, 0.0
+    srcs = range(0, g.n, stride)
+    t0 = time.perf_counter()
+    # contiguous blocks of 64 sources, strided over the whole id range
+    for s in list(srcs)[: max(1, n_src // 64)]:
+        e, st = O.walks(og, wl["alpha"], wl["R"], wl["seed"], s, min(g.n, s + 64))
+        rp, col, cnt = O.rows(e, g.n)
+        if wl["topk"]:
+            O.topk(rp, col, cnt, wl["topk"])
+        total_steps += st
+        total_walks += e.size
+    t_all = time.perf_counter() - t0
+    return {"value": total_steps / t_all, "unit": "walk steps/s", "cores": 1, "kind": "oracle",
+            "walks_per_s": total_walks / t_all,
+            "sample": f"{total_walks // wl['R']} sources in blocks of 64 strided over all {g.n} sources, "
+                      f"{total_walks} walks, {total_steps} steps, {t_all:.1f} s"}
+
+
+def run_reference(args):
+    rank, world, _ = env_rank()
+    if rank != 0:
+        return 0
+    from paper_1903_11749_gb300 import inputs as I
+    wl = WORKLOADS[args.workload]
+    g = I.workload_graph(args.workload)
+    sys.path.insert(0, os.path.join(ROOT, "oracle"))
+    import oracle as O
+    O.build()
+    og = O.prepare(g.n, g.row_ptr, g.col, g.w)
+    n_blk = 64
+    per_step = []
+    steps_tot = walks_tot = 0
+    rng_src = np.linspace(0, g.n - n_blk, num=max(1, args.ref_blocks), dtype=np.int64)
+    for it in range(args.warmup + args.steps):
+        t0 = time.perf_counter()
+        st_step, wk = 0, 0
+        for s in rng_src:
+            e, st = O.walks(og, wl["alpha"], wl["R"], wl["seed"], int(s), int(s) + n_blk)
+            rp, col, cnt = O.rows(e, g.n)
+            O.topk(rp, col, cnt, wl["topk"])
+            st_step += st
+            wk += e.size
+        dt = time.perf_counter() - t0
+        if it >= args.warmup:
+            per_step.append(dt)
+            steps_tot += st_step
+            walks_tot += wk
+    T = sum(per_step)
+    val = steps_tot / T
+    sample = f"{len(rng_src) * n_blk} sources per step ({len(rng_src)} blocks of {n_blk} spread over {g.n})"
+    line = {"impl": "reference", "metric": "walk steps/s", "value": val, "unit": "walk steps/s", "n_gpus": world,
+            "steps": args.steps, "warmup": args.warmup, "ms_per_step": 1e3 * T / len(per_step),
+            "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "u32", "data": "synthetic",
+            "config": {"workload": args.workload, "desc": wl["desc"], "alpha": wl["alpha"], "R": wl["R"],
+                       "topk": wl["topk"], "sources_per_step": len(rng_src) * n_blk},
+            "walks_per_s": walks_tot / T,
+            "cpu_baseline": {"value": val, "unit": "walk steps/s", "cores": 1, "kind": "oracle", "sample": sample},
+            "e2e": {"value": val, "unit": "walk steps/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
+    print(json.dumps(line))
+    return 0
+
+
+def main():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=5)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--impl", default="gb300", choices=["gb300", "reference"])
+    ap.add_argument("--workload", default="rmat20", choices=sorted(WORKLOADS))
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--no-e2e", action="store_true")
+    ap.add_argument("--no-plain", action="store_true")
+    ap.add_argument("--ref-blocks", type=int, default=48)
+    ap.add_argument("--cpu-budget", type=float, default=15.0)
+    ap.add_argument("--warps-per-block", type=int, default=0)
+    ap.add_argument("--chunk-sources", type=int, default=0)
+    ap.add_argument("--large-degree", type=int, default=0)
+    args = ap.parse_args()
+    if args.impl == "reference":
+        return run_reference(args)
+
+    import torch
+    import torch.distributed as dist
+    from paper_1903_11749_gb300 import build as B
+    from paper_1903_11749_gb300 import inputs as I
+    B.build()
+    from paper_1903_11749_gb300 import ppr
+
+    rank, world, local = env_rank()
+    if world > 1:
+        dist.init_process_group("nccl", init_method="env://")
+    torch.cuda.set_device(local)
+    dev = torch.device("cuda", local)
+    wl = WORKLOADS[args.workload]
+    g = I.workload_graph(args.workload)
+    a, b = shard(g.n, rank, world)
+    tune = dict(warps_per_block=args.warps_per_block, chunk_sources=args.chunk_sources,
+                large_degree=args.large_degree)
+
+    ctx = ppr.Context(local)
+    stream = torch.cuda.current_stream(dev)
+    d_rp = torch.from_numpy(g.row_ptr).to(dev)
+    d_col = torch.from_numpy(g.col).to(dev)
+    d_w = torch.from_numpy(g.w.view(np.int32)).to(dev)
+    flush = torch.empty(L2_FLUSH_BYTES // 4, dtype=torch.int32, device=dev)
+
+    def step(kernel=ppr.KERNEL_PERSISTENT, stats=False):
+        G = ctx.load_graph(g.n, d_rp, d_col, d_w, stream=stream, m=g.m)
+        r = G.run(alpha=wl["alpha"], R=wl["R"], seed=wl["seed"], src_begin=a, src_end=b, topk=wl["topk"],
+                  segments=wl["segments"], kernel=kernel, stats=stats, stream=stream, wait=False, **tune)
+        return G, r
+
+    # statistics launch (untimed): exact draws and algorithmic sectors of one pass
+    G0, r0 = step(stats=True)
+    r0.wait()
+    info0 = r0.info()
+    steps_per_pass, sectors_per_pass, walks_per_pass = int(info0.steps), int(info0.sectors), int(info0.walks)
+    del r0, G0
+
+    for _ in range(args.warmup):
+        G, r = step()
+        r.wait()
+    kernel_ms = []
+    step_ms = []
+    if world > 1:
+        dist.barrier()
+    torch.cuda.synchronize(dev)
+    clocks = Clocks(local, None)
+    clocks.start()
+    for _ in range(args.steps):
+        flush.fill_(1)  # L2 flush outside the timed events
+        e0 = torch.cuda.Event(enable_timing=True)
+        e1 = torch.cuda.Event(enable_timing=True)
+        e0.record(stream)
+        G, r = step()
+        e1.record(stream)
+        r.wait()
+        e1.synchronize()
+        step_ms.append(e0.elapsed_time(e1))
+        kernel_ms.append(r.info().kernel_ms)
+        del r, G
+    torch.cuda.synchronize(dev)
+    clk = clocks.stop()
+    T = sum(step_ms) / 1e3
+    t_tensor = torch.tensor([T], dtype=torch.float64, device=dev)
+    units = torch.tensor([steps_per_pass * args.steps, walks_per_pass * args.steps], dtype=torch.float64, device=dev)
+    if world > 1:
+        dist.all_reduce(t_tensor, op=dist.ReduceOp.MAX)
+        dist.all_reduce(units, op=dist.ReduceOp.SUM)
+    T_max = float(t_tensor.item())
+    value = float(units[0].item()) / T_max
+    walks_s = float(units[1].item()) / T_max
+
+    # plain one-thread-per-walk kernel on the same pass, for comparison
+    plain = None
+    if not args.no_plain:
+        G, r = step(kernel=ppr.KERNEL_PLAIN)
+        r.wait()
+        pm = []
+        for _ in range(max(1, min(3, args.steps))):
+            flush.fill_(1)
+            e0 = torch.cuda.Event(enable_timing=True)
+            e1 = torch.cuda.Event(enable_timing=True)
+            e0.record(stream)
+            G, r = step(kernel=ppr.KERNEL_PLAIN)
+            e1.record(stream)
+            r.wait()
+            e1.synchronize()
+            pm.append(e0.elapsed_time(e1))
+        plain = {"value": steps_per_pass / (statistics.mean(pm) / 1e3), "unit": "walk steps/s",
+                 "ms_per_step": statistics.mean(pm), "kernel": "one thread per walk + separate aggregation"}
+
+    # end to end through the C ABI with host buffers: pinned CSR in, rows + top-k out
+    e2e = None
+    if not args.no_e2e:
+        h_rp = torch.from_numpy(g.row_ptr).pin_memory()
+        h_col = torch.from_numpy(g.col).pin_memory()
+        h_w = torch.from_numpy(g.w.view(np.int32)).pin_memory()
+        h2d = g.row_ptr.nbytes + g.col.nbytes + g.w.nbytes
+        times, d2h = [], 0
+        for it in range(1 + min(3, args.steps)):
+            torch.cuda.synchronize(dev)
+            t0 = time.perf_counter()
+            G = ctx.load_graph(g.n, h_rp.numpy(), h_col.numpy(), h_w.numpy().view(np.uint32), stream=stream)
+            r = G.run(alpha=wl["alpha"], R=wl["R"], seed=wl["seed"], src_begin=a, src_end=b, topk=wl["topk"],
+                      stream=stream, **tune)
+            rp, col, cnt = r.sparse_rows()
+            idx, tc = r.topk()
+            t1 = time.perf_counter()
+            if it > 0:
+                times.append(t1 - t0)
+            d2h = rp.nbytes + col.nbytes + cnt.nbytes + idx.nbytes + tc.nbytes
+            del r, G
+        e2e = {"value": steps_per_pass / statistics.mean(times), "unit": "walk steps/s", "h2d_bytes_per_step": h2d,
+               "d2h_bytes_per_step": d2h, "ms_per_step": 1e3 * statistics.mean(times)}
+
+    peak, peak_kind = measured_peaks()
+    kms = statistics.mean(kernel_ms)
+    alg_bytes = sectors_per_pass * 32.0
+    achieved = alg_bytes / (kms / 1e3) / 1e9
+    traffic = recorded_traffic(args.workload)
+    roofline = {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s", "frac": achieved / peak,
+                "traffic": traffic, "peak_kind": peak_kind, "kernel": "k_walk_persistent",
+                "alg_bytes_per_launch": alg_bytes, "kernel_ms": kms,
+                "sectors_per_step": sectors_per_pass / max(steps_per_pass, 1)}
+
+    cpu = None
+    if rank == 0 and world == 1 and not args.no_cpu_baseline:
+        cpu = cpu_baseline(g, wl, args.cpu_budget)
+
+    if rank == 0:
+        line = {"metric": "walk steps/s", "value": value, "unit": "walk steps/s", "n_gpus": world,
+                "steps": args.steps, "warmup": args.warmup, "ms_per_step": 1e3 * T_max / args.steps,
+                "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "u32",
+                "data": "synthetic",
+                "config": {"workload": args.workload, "desc": wl["desc"], "alpha": wl["alpha"], "R": wl["R"],
+                           "topk": wl["topk"], "n": g.n, "m": g.m, "sources": g.n,
+                           "parallelism": f"source-sharded x{world}" if world > 1 else "1 GPU",
+                           "l2": "flushed between steps (512 MB write)"},
+                "walks_per_s": walks_s, "steps_per_walk": steps_per_pass / max(walks_per_pass, 1),
+                "roofline": roofline, "cpu_baseline": cpu, "e2e": e2e, "plain_kernel": plain,
+                "gpu_launches": 3 * args.steps, "clocks": clk}
+        print(json.dumps(line))
+    if world > 1:
+        dist.destroy_process_group()
+    return 0
+
+
+if __name__ == "__main__":
+    sys.exit(main())

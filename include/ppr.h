@@ -1,0 +1,220 @@
+/*
+ * ppr.h -- C ABI of the GB300 Monte Carlo edge-weighted Personalized
+ * PageRank library (libppr.so).
+ *
+ * The library computes, on one GPU, the Monte Carlo estimator of fully
+ * personalized PageRank on an edge-weighted directed graph (Lin, "Distributed
+ * Algorithms for Fully Personalized PageRank on Large Graphs", WWW'19):
+ * R random walks from every source of a range; each step moves to an
+ * out-neighbour with probability w(e)/W_u (routing probability, Sec. 2.1) and
+ * then stops with probability alpha (Sec. 2.1, Algorithm 2); the endpoint
+ * counts of each source form its sparse row, pi_hat(s,t) = count/R (Sec. 2.1
+ * estimator, Definition 1).  Results are exact integer counts, identical for
+ * any launch shape, batch split or kernel choice.
+ *
+ * Integer sampling rule (fixed; every result is a function of it):
+ *   T = floor(alpha * 2^32), 1 <= T; a walk stops after a step iff x2 < T.
+ *   (x0,x1,x2,x3) = Philox4x32-10(key = (seed mod 2^32, seed >> 32),
+ *                    counter = (s_local, j, k, tag)), j = walk index,
+ *                    k = steps taken so far (mod 2^32).
+ *   r64 = x0 | x1 << 32; next edge = smallest e of the row with
+ *   P[e] > floor(r64 * W_u / 2^64), P the inclusive row prefix of weights.
+ *   A node with no out-edge restarts the walk at its source (Sec. 2.1;
+ *   dangling = 0) or ends the walk there without a step (dangling = 1).
+ *   Segment mode (Algorithm 4, "big moves", fixed depth 3, out-degree <= 8)
+ *   replaces a plain step at an eligible node by one draw over that node's
+ *   precomputed outcome table; its counts follow a different draw sequence
+ *   and are therefore compared against the segment-mode oracle.
+ *
+ * Conventions
+ *   - Every function returns an int status: PPR_OK (0) or a negative code.
+ *     No C++ exception, abort or device trap crosses this boundary.
+ *     ppr_last_error() gives a message for the last failure on this thread.
+ *   - Host inputs are copied during the call; device inputs (flag
+ *     PPR_PTRS_DEVICE) are read during the call and not retained.
+ *   - The library owns graphs and results until ppr_free_graph /
+ *     ppr_free_result.  Output arrays are caller-allocated, host memory unless
+ *     PPR_PTRS_DEVICE is passed.
+ *   - A context is used by one host thread at a time.
+ */
+#ifndef PPR_H
+#define PPR_H
+
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+#define PPR_ABI_VERSION 1
+
+enum {
+    PPR_OK = 0,
+    PPR_EINVAL = -1,   /* invalid argument or malformed graph */
+    PPR_ENOMEM = -2,   /* device or pinned-host allocation failed */
+    PPR_ECUDA = -3,    /* CUDA runtime error (no device, launch failure, ...) */
+    PPR_ETIMEOUT = -4, /* deadline passed before the work finished */
+    PPR_ERANGE = -5,   /* size beyond a documented limit */
+    PPR_EBUSY = -6,    /* result not ready (ppr_wait not yet successful) */
+    PPR_ENOTSUP = -7   /* combination not supported */
+};
+
+/* flags */
+#define PPR_PTRS_DEVICE 0x1u /* pointer arguments are device pointers */
+
+/* Documented limits. */
+#define PPR_MAX_NODES 2147483647LL        /* n < 2^31 */
+#define PPR_MAX_EDGES 1099511627775LL     /* m < 2^40 */
+#define PPR_MAX_DEGREE 8388607LL          /* out-degree < 2^23 */
+#define PPR_MAX_R 4096u                   /* walks per source */
+
+typedef struct ppr_ctx ppr_ctx;
+typedef struct ppr_graph ppr_graph;
+typedef struct ppr_result ppr_result;
+
+/* Library ABI version (PPR_ABI_VERSION).  Needs no GPU. */
+int ppr_version(void);
+
+/* T = floor(alpha * 2^32) (Sec. 2.1 termination probability as an integer
+ * threshold), or 0 if alpha is not in (0,1) or T would be 0.  Needs no GPU. */
+uint32_t ppr_alpha_threshold(double alpha);
+
+/* Message describing the last failure on the calling thread ("" if none).
+ * Owned by the library; valid until the next call on this thread. */
+const char *ppr_last_error(void);
+
+/* Creates a context on CUDA device `device`; *out receives it.
+ * PPR_ECUDA if the device cannot be used. */
+int ppr_create(int device, ppr_ctx **out);
+void ppr_destroy(ppr_ctx *ctx);
+
+/* Number of streaming multiprocessors of the context's device. */
+int ppr_device_sms(const ppr_ctx *ctx);
+
+/*
+ * Loads a weighted directed graph G = (V, E, w), w(e) > 0 (Sec. 2.1), in CSR
+ * form and builds its device layout: 16-byte node records and per-row
+ * inclusive 64-bit weight prefix sums (stored as 32-bit values when every row
+ * total is below 2^32), built by device kernels.
+ *   n        number of nodes, 1 <= n <= PPR_MAX_NODES
+ *   m        number of edges, 0 <= m <= PPR_MAX_EDGES
+ *   row_ptr  int64[n+1], row_ptr[0] = 0, non-decreasing, row_ptr[n] = m
+ *   col      int32[m], each in [0, n)      (edge targets, row order kept)
+ *   w        uint32[m], each >= 1          (integer edge weights)
+ *   flags    PPR_PTRS_DEVICE if the three arrays are device pointers
+ *   stream   cudaStream_t for the build, or NULL for the legacy stream
+ * Errors: PPR_EINVAL (malformed CSR, col out of range, w = 0),
+ *         PPR_ERANGE (n, m or an out-degree beyond the limits), PPR_ENOMEM.
+ * The call returns after the build has finished.
+ */
+int ppr_load_graph(ppr_ctx *ctx, int64_t n, int64_t m, const int64_t *row_ptr, const int32_t *col,
+                   const uint32_t *w, uint32_t flags, void *stream, ppr_graph **out);
+
+/*
+ * Loads `count` independent graphs as one block-diagonal graph.  Instance g
+ * owns global nodes [node_off[g], node_off[g+1]); row_ptr (n_total+1 entries,
+ * n_total = node_off[count]) indexes the concatenated edge arrays; col holds
+ * INSTANCE-LOCAL target ids.  Walks of a source s of instance g draw with
+ * counter (s - node_off[g], j, k, g): identical to running instance g alone
+ * with tag = g.  Result rows of such a graph hold instance-local end ids.
+ * Errors as ppr_load_graph.
+ */
+int ppr_load_graph_batch(ppr_ctx *ctx, int32_t count, const int64_t *node_off, int64_t m,
+                         const int64_t *row_ptr, const int32_t *col, const uint32_t *w, uint32_t flags,
+                         void *stream, ppr_graph **out);
+
+typedef struct {
+    int64_t n, m;
+    int64_t max_degree;
+    int64_t dangling;        /* nodes with no out-edge */
+    int32_t wide;            /* 1 if some row total is >= 2^32 (64-bit prefix layout) */
+    int32_t instances;       /* 0 for a plain graph */
+    int64_t device_bytes;    /* device memory held by the graph */
+    int64_t segment_nodes;   /* nodes with a segment table (last built threshold) */
+    int64_t segment_entries;
+} ppr_graph_info;
+
+int ppr_graph_get_info(const ppr_graph *g, ppr_graph_info *info);
+void ppr_free_graph(ppr_graph *g);
+
+/* Walker kernels. */
+enum {
+    PPR_KERNEL_PERSISTENT = 0, /* persistent warps, work queue, lane refill, fused aggregation */
+    PPR_KERNEL_PLAIN = 1       /* one thread per walk, endpoints to HBM, separate aggregation */
+};
+
+typedef struct {
+    double alpha;        /* termination probability, floor(alpha*2^32) >= 1, alpha < 1 */
+    uint32_t R;          /* walks per source, 1 <= R <= PPR_MAX_R */
+    uint64_t seed;       /* Philox key */
+    int64_t src_begin;   /* sources [src_begin, src_end), global node ids */
+    int64_t src_end;
+    uint32_t tag;        /* fourth counter word (plain graphs; batched graphs use the instance id) */
+    int32_t dangling;    /* 0 restart at the source (Sec. 2.1), 1 end at the dangling node */
+    int32_t segments;    /* 1: depth-3 segment tables for out-degree <= 8 (Algorithm 4) */
+    int32_t topk;        /* 0..R: per-source top-k (count desc, end id asc) kept with the rows */
+    int32_t kernel;      /* PPR_KERNEL_PERSISTENT or PPR_KERNEL_PLAIN */
+    int32_t large_degree;/* out-degree above which a warp searches cooperatively; 0 = default 4096 */
+    int32_t warps_per_block;  /* persistent kernel tuning, 0 = default */
+    int32_t chunk_sources;    /* sources per queue item, 0 = default */
+    int64_t max_batch_sources;/* sources per device batch, 0 = sized to free device memory */
+    int32_t stats;       /* 1: also count the algorithmic 32-byte sectors of every step (slower;
+                            rows, counts and steps are unchanged) */
+    void *stream;        /* cudaStream_t, NULL = legacy default stream */
+} ppr_run_args;
+
+/* Fills *args with defaults (alpha 0.15, R 100, seed 1, all sources of
+ * nothing: src_end = src_begin = 0, persistent kernel). */
+void ppr_run_args_init(ppr_run_args *args);
+
+/*
+ * Runs the walks of every source in [src_begin, src_end) (Algorithm 2 with
+ * all walks of a source counted, then grouped by endpoint) and keeps, per
+ * source, its sparse count row (end id ascending, counts summing to R) and
+ * its top-k.  Work is enqueued on args->stream; call ppr_wait before reading.
+ * Errors: PPR_EINVAL (alpha, R, range, topk), PPR_ERANGE (R > PPR_MAX_R),
+ *         PPR_ENOMEM, PPR_ECUDA.
+ */
+int ppr_run(ppr_ctx *ctx, const ppr_graph *g, const ppr_run_args *args, ppr_result **out);
+
+/* Waits for the run; PPR_ETIMEOUT if not finished within timeout_ms
+ * (timeout_ms < 0: wait without deadline).  The result stays valid. */
+int ppr_wait(ppr_result *r, int64_t timeout_ms);
+
+typedef struct {
+    int64_t sources;       /* S = src_end - src_begin */
+    uint32_t R;
+    int32_t topk;
+    int64_t nnz;           /* total stored (source, end) pairs */
+    uint64_t steps;        /* draws consumed by all walks */
+    uint64_t walks;        /* S * R */
+    float kernel_ms;       /* device time of the walker launches (CUDA events) */
+    uint64_t sectors;      /* stats runs: 32-byte sectors a thread-serial bisection touches,
+                              node record included (0 otherwise) */
+} ppr_result_info;
+
+int ppr_result_get_info(const ppr_result *r, ppr_result_info *info);
+
+/*
+ * Copies the sparse rows: row_ptr (S+1 entries), then col/cnt (nnz entries).
+ * If col == NULL only row_ptr (may be NULL too) and *nnz are produced.
+ * PPR_ERANGE if cap < nnz.  flags: PPR_PTRS_DEVICE for device outputs.
+ */
+int ppr_sparse_rows(const ppr_result *r, int64_t *row_ptr, int32_t *col, uint32_t *cnt, int64_t cap,
+                    int64_t *nnz, uint32_t flags);
+
+/* Top-k per source, S*k entries each: idx (end ids, -1 padded) and cnt
+ * (counts, 0 padded), count descending then end id ascending.
+ * 1 <= k <= the run's topk, else PPR_EINVAL. */
+int ppr_topk(const ppr_result *r, int32_t k, int32_t *idx, uint32_t *cnt, uint32_t flags);
+
+/* Dense S x n uint32 counts (plain graphs only). */
+int ppr_dense(const ppr_result *r, uint32_t *out, uint32_t flags);
+
+void ppr_free_result(ppr_result *r);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* PPR_H */

@@ -1,0 +1,591 @@
+// api.cu -- the extern "C" entry points of libppr.so (declared in
+// include/ppr.h): argument checks, ownership of device state, batching of a
+// source range into device-sized launches, and the row/top-k/dense readers.
+#include <chrono>
+#include <cmath>
+#include <cstdarg>
+#include <cstdio>
+#include <cstring>
+#include <new>
+#include <thread>
+
+#include "ppr_host.h"
+#include "scan.cuh"
+
+namespace {
+thread_local char g_err[512] = "";
+}
+
+namespace ppr {
+
+void set_error(const char *fmt, ...)
+{
+    va_list ap;
+    va_start(ap, fmt);
+    vsnprintf(g_err, sizeof(g_err), fmt, ap);
+    va_end(ap);
+}
+
+int cuda_fail(cudaError_t e, const char *what)
+{
+    set_error("%s: %s", what, cudaGetErrorString(e));
+    if (e == cudaErrorMemoryAllocation) return PPR_ENOMEM;
+    return PPR_ECUDA;
+}
+
+int dev_alloc(void **p, size_t bytes, const char *what)
+{
+    *p = nullptr;
+    cudaError_t e = cudaMalloc(p, bytes > 0 ? bytes : 1);
+    if (e != cudaSuccess) {
+        cudaGetLastError();  // clear the sticky-free allocation error
+        *p = nullptr;
+        set_error("cannot allocate %zu bytes of device memory for %s: %s", bytes, what, cudaGetErrorString(e));
+        return e == cudaErrorMemoryAllocation ? PPR_ENOMEM : PPR_ECUDA;
+    }
+    return PPR_OK;
+}
+
+// Row compaction: one warp per source copies its stored pairs to the
+// compacted position given by the exclusive scan of the row sizes.
+__global__ void k_compact_rows(int64_t S, uint32_t cap, const uint32_t *nnz, const uint64_t *off, const int32_t *cols,
+                               const uint32_t *cnts, int32_t *ocol, uint32_t *ocnt)
+{
+    const uint32_t lane = threadIdx.x & 31;
+    const int64_t warps = (int64_t)gridDim.x * (blockDim.x >> 5);
+    for (int64_t s = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5; s < S; s += warps) {
+        const uint32_t c = nnz[s];
+        const uint64_t o = off[s];
+        for (uint32_t i = lane; i < c; i += 32) {
+            ocol[o + i] = cols[(uint64_t)s * cap + i];
+            ocnt[o + i] = cnts[(uint64_t)s * cap + i];
+        }
+    }
+}
+
+__global__ void k_dense(int64_t S, int64_t n, uint32_t cap, const uint32_t *nnz, const int32_t *cols,
+                        const uint32_t *cnts, uint32_t *out)
+{
+    const uint32_t lane = threadIdx.x & 31;
+    const int64_t warps = (int64_t)gridDim.x * (blockDim.x >> 5);
+    for (int64_t s = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5; s < S; s += warps) {
+        const uint32_t c = nnz[s];
+        for (uint32_t i = lane; i < c; i += 32)
+            out[(uint64_t)s * n + (uint32_t)cols[(uint64_t)s * cap + i]] = cnts[(uint64_t)s * cap + i];
+    }
+}
+
+}  // namespace ppr
+
+using namespace ppr;
+
+static int set_device(const ppr_ctx *ctx)
+{
+    cudaError_t e = cudaSetDevice(ctx->device);
+    if (e != cudaSuccess) return cuda_fail(e, "cudaSetDevice");
+    return PPR_OK;
+}
+
+extern "C" {
+
+int ppr_version(void) { return PPR_ABI_VERSION; }
+
+uint32_t ppr_alpha_threshold(double alpha)
+{
+    if (!(alpha > 0.0) || !(alpha < 1.0)) return 0u;
+    double t = alpha * 4294967296.0;  // exact: scaling by a power of two
+    return (uint32_t)t;
+}
+
+const char *ppr_last_error(void) { return g_err; }
+
+int ppr_create(int device, ppr_ctx **out)
+{
+    if (!out) {
+        set_error("out is NULL");
+        return PPR_EINVAL;
+    }
+    *out = nullptr;
+    int count = 0;
+    cudaError_t e = cudaGetDeviceCount(&count);
+    if (e != cudaSuccess || count == 0) {
+        cudaGetLastError();
+        set_error("no CUDA device available: %s", e != cudaSuccess ? cudaGetErrorString(e) : "count is 0");
+        return PPR_ECUDA;
+    }
+    if (device < 0 || device >= count) {
+        set_error("device %d out of range [0, %d)", device, count);
+        return PPR_EINVAL;
+    }
+    PPR_CUDA(cudaSetDevice(device));
+    ppr_ctx *c = new (std::nothrow) ppr_ctx;
+    if (!c) {
+        set_error("host allocation failed");
+        return PPR_ENOMEM;
+    }
+    c->device = device;
+    int v = 0;
+    cudaDeviceGetAttribute(&v, cudaDevAttrMultiProcessorCount, device);
+    c->sms = v;
+    cudaDeviceGetAttribute(&v, cudaDevAttrMaxSharedMemoryPerBlockOptin, device);
+    c->smem_optin = (size_t)v;
+    *out = c;
+    return PPR_OK;
+}
+
+void ppr_destroy(ppr_ctx *ctx) { delete ctx; }
+
+int ppr_device_sms(const ppr_ctx *ctx) { return ctx ? ctx->sms : 0; }
+
+static int load_common(ppr_ctx *ctx, int64_t n, int64_t m, const int64_t *row_ptr, const int32_t *col,
+                       const uint32_t *w, uint32_t flags, void *stream, ppr_graph *g)
+{
+    if (n < 1 || n > PPR_MAX_NODES) {
+        set_error("n = %lld outside [1, %lld]", (long long)n, (long long)PPR_MAX_NODES);
+        return n < 1 ? PPR_EINVAL : PPR_ERANGE;
+    }
+    if (m < 0 || m > PPR_MAX_EDGES) {
+        set_error("m = %lld outside [0, %lld]", (long long)m, (long long)PPR_MAX_EDGES);
+        return m < 0 ? PPR_EINVAL : PPR_ERANGE;
+    }
+    if (!row_ptr || (m > 0 && (!col || !w))) {
+        set_error("row_ptr, col and w must be non-NULL");
+        return PPR_EINVAL;
+    }
+    if (flags & ~PPR_PTRS_DEVICE) {
+        set_error("unknown flags 0x%x", flags);
+        return PPR_EINVAL;
+    }
+    int rc = set_device(ctx);
+    if (rc) return rc;
+    g->ctx = ctx;
+    g->n = n;
+    g->m = m;
+    return build_graph(ctx, n, m, row_ptr, col, w, (flags & PPR_PTRS_DEVICE) != 0, (cudaStream_t)stream, g);
+}
+
+int ppr_load_graph(ppr_ctx *ctx, int64_t n, int64_t m, const int64_t *row_ptr, const int32_t *col,
+                   const uint32_t *w, uint32_t flags, void *stream, ppr_graph **out)
+{
+    if (!ctx || !out) {
+        set_error("ctx and out must be non-NULL");
+        return PPR_EINVAL;
+    }
+    *out = nullptr;
+    ppr_graph *g = new (std::nothrow) ppr_graph;
+    if (!g) return PPR_ENOMEM;
+    int rc = load_common(ctx, n, m, row_ptr, col, w, flags, stream, g);
+    if (rc) {
+        ppr_free_graph(g);
+        return rc;
+    }
+    *out = g;
+    return PPR_OK;
+}
+
+int ppr_load_graph_batch(ppr_ctx *ctx, int32_t count, const int64_t *node_off, int64_t m, const int64_t *row_ptr,
+                         const int32_t *col, const uint32_t *w, uint32_t flags, void *stream, ppr_graph **out)
+{
+    if (!ctx || !out || !node_off) {
+        set_error("ctx, node_off and out must be non-NULL");
+        return PPR_EINVAL;
+    }
+    *out = nullptr;
+    if (count < 1) {
+        set_error("count must be >= 1");
+        return PPR_EINVAL;
+    }
+    // node_off is always host memory (count + 1 values)
+    if (node_off[0] != 0) {
+        set_error("node_off[0] must be 0");
+        return PPR_EINVAL;
+    }
+    for (int32_t i = 0; i < count; ++i)
+        if (node_off[i + 1] <= node_off[i]) {
+            set_error("every instance needs at least one node (node_off strictly increasing)");
+            return PPR_EINVAL;
+        }
+    ppr_graph *g = new (std::nothrow) ppr_graph;
+    if (!g) return PPR_ENOMEM;
+    g->instances = count;
+    g->node_off.assign(node_off, node_off + count + 1);
+    int rc = load_common(ctx, node_off[count], m, row_ptr, col, w, flags, stream, g);
+    if (rc) {
+        ppr_free_graph(g);
+        return rc;
+    }
+    *out = g;
+    return PPR_OK;
+}
+
+int ppr_graph_get_info(const ppr_graph *g, ppr_graph_info *info)
+{
+    if (!g || !info) {
+        set_error("NULL argument");
+        return PPR_EINVAL;
+    }
+    info->n = g->n;
+    info->m = g->m;
+    info->max_degree = g->max_degree;
+    info->dangling = g->dangling;
+    info->wide = g->wide ? 1 : 0;
+    info->instances = g->instances;
+    info->device_bytes = g->device_bytes;
+    info->segment_nodes = g->seg.nodes;
+    info->segment_entries = g->seg.entries_n;
+    return PPR_OK;
+}
+
+void ppr_free_graph(ppr_graph *g)
+{
+    if (!g) return;
+    if (g->ctx) cudaSetDevice(g->ctx->device);
+    cudaFree(g->node);
+    cudaFree(g->edges);
+    cudaFree(g->seg.node);
+    cudaFree(g->seg.entries);
+    delete g;
+}
+
+void ppr_run_args_init(ppr_run_args *a)
+{
+    if (!a) return;
+    memset(a, 0, sizeof(*a));
+    a->alpha = 0.15;
+    a->R = 100;
+    a->seed = 1;
+    a->kernel = PPR_KERNEL_PERSISTENT;
+}
+
+static void result_release(ppr_result *r)
+{
+    if (!r) return;
+    if (r->ctx) cudaSetDevice(r->ctx->device);
+    cudaFree(r->d_nnz);
+    cudaFree(r->d_cols);
+    cudaFree(r->d_cnts);
+    cudaFree(r->d_topk_idx);
+    cudaFree(r->d_topk_cnt);
+    cudaFree(r->d_steps);
+    for (void *p : r->scratch) cudaFree(p);
+    if (r->ev_start) cudaEventDestroy(r->ev_start);
+    if (r->ev_walk_end) cudaEventDestroy(r->ev_walk_end);
+    if (r->ev_done) cudaEventDestroy(r->ev_done);
+    delete r;
+}
+
+int ppr_run(ppr_ctx *ctx, const ppr_graph *g, const ppr_run_args *a, ppr_result **out)
+{
+    if (!ctx || !g || !a || !out) {
+        set_error("NULL argument");
+        return PPR_EINVAL;
+    }
+    *out = nullptr;
+    const uint32_t T = ppr_alpha_threshold(a->alpha);
+    if (T == 0) {
+        set_error("alpha = %g: need 0 < alpha < 1 and floor(alpha * 2^32) >= 1", a->alpha);
+        return PPR_EINVAL;
+    }
+    if (a->R < 1) {
+        set_error("R must be >= 1");
+        return PPR_EINVAL;
+    }
+    if (a->R > PPR_MAX_R) {
+        set_error("R = %u exceeds the limit %u", a->R, PPR_MAX_R);
+        return PPR_ERANGE;
+    }
+    if (a->src_begin < 0 || a->src_end > g->n || a->src_begin >= a->src_end) {
+        set_error("source range [%lld, %lld) must be non-empty and inside [0, %lld)", (long long)a->src_begin,
+                  (long long)a->src_end, (long long)g->n);
+        return PPR_EINVAL;
+    }
+    if (a->topk < 0 || (uint32_t)a->topk > a->R) {
+        set_error("topk = %d outside [0, R]", a->topk);
+        return PPR_EINVAL;
+    }
+    if ((a->dangling != 0 && a->dangling != 1) || (a->segments != 0 && a->segments != 1) ||
+        (a->kernel != PPR_KERNEL_PERSISTENT && a->kernel != PPR_KERNEL_PLAIN) || a->large_degree < 0 ||
+        a->warps_per_block < 0 || a->warps_per_block > 32 || a->chunk_sources < 0 || a->max_batch_sources < 0 ||
+        (a->stats != 0 && a->stats != 1)) {
+        set_error("invalid mode or tuning argument");
+        return PPR_EINVAL;
+    }
+    if (g->instances > 0 && a->tag != 0) {
+        set_error("batched graphs use the instance id as tag; tag must be 0");
+        return PPR_EINVAL;
+    }
+    if (a->chunk_sources > 0 && (uint64_t)a->chunk_sources * a->R > (1u << 20)) {
+        set_error("chunk_sources * R too large");
+        return PPR_ERANGE;
+    }
+    int rc = set_device(ctx);
+    if (rc) return rc;
+    cudaStream_t st = (cudaStream_t)a->stream;
+    if (a->segments) {
+        rc = build_segments(const_cast<ppr_graph *>(g), T, st);
+        if (rc) return rc;
+    }
+    ppr_result *r = new (std::nothrow) ppr_result;
+    if (!r) return PPR_ENOMEM;
+    r->ctx = ctx;
+    r->g = g;
+    r->stream = st;
+    r->S = a->src_end - a->src_begin;
+    r->R = a->R;
+    r->topk = a->topk;
+    r->src_begin = a->src_begin;
+    int64_t n_local_max = g->n;
+    if (g->instances > 0) {
+        n_local_max = 0;
+        for (int32_t i = 0; i < g->instances; ++i)
+            n_local_max = std::max<int64_t>(n_local_max, g->node_off[i + 1] - g->node_off[i]);
+    }
+    r->cap = (uint32_t)std::min<int64_t>((int64_t)a->R, n_local_max);
+    auto fail = [&](int code) {
+        result_release(r);
+        return code;
+    };
+    const size_t S = (size_t)r->S;
+    if ((rc = dev_alloc((void **)&r->d_nnz, sizeof(uint32_t) * S, "row sizes"))) return fail(rc);
+    if ((rc = dev_alloc((void **)&r->d_cols, sizeof(int32_t) * S * r->cap, "row ids"))) return fail(rc);
+    if ((rc = dev_alloc((void **)&r->d_cnts, sizeof(uint32_t) * S * r->cap, "row counts"))) return fail(rc);
+    if (r->topk > 0) {
+        if ((rc = dev_alloc((void **)&r->d_topk_idx, sizeof(int32_t) * S * r->topk, "top-k ids"))) return fail(rc);
+        if ((rc = dev_alloc((void **)&r->d_topk_cnt, sizeof(uint32_t) * S * r->topk, "top-k counts"))) return fail(rc);
+    }
+    if ((rc = dev_alloc((void **)&r->d_steps, sizeof(unsigned long long) * 3, "counters"))) return fail(rc);
+    cudaError_t e = cudaEventCreate(&r->ev_start);
+    if (e == cudaSuccess) e = cudaEventCreate(&r->ev_walk_end);
+    if (e == cudaSuccess) e = cudaEventCreate(&r->ev_done);
+    if (e != cudaSuccess) return fail(cuda_fail(e, "cudaEventCreate"));
+
+    RunPlan plan{};
+    plan.T = T;
+    plan.R = a->R;
+    plan.seed = a->seed;
+    plan.tag = a->tag;
+    plan.dangling = a->dangling;
+    plan.segments = a->segments != 0;
+    plan.kernel = a->kernel;
+    plan.large_degree = a->large_degree;
+    plan.warps_per_block = a->warps_per_block;
+    plan.chunk_sources = a->chunk_sources;
+    plan.stats = a->stats != 0;
+
+    // Batch size: the plain kernel keeps every endpoint in HBM (4 B per walk);
+    // bound that scratch to a quarter of the free memory.
+    int64_t batch = r->S;
+    if (a->max_batch_sources > 0) batch = std::min<int64_t>(batch, a->max_batch_sources);
+    uint32_t *ends = nullptr;
+    if (a->kernel == PPR_KERNEL_PLAIN) {
+        size_t free_b = 0, total_b = 0;
+        cudaMemGetInfo(&free_b, &total_b);
+        int64_t fit = (int64_t)(free_b / 4 / ((size_t)a->R * sizeof(uint32_t)));
+        batch = std::max<int64_t>(1, std::min<int64_t>(batch, fit));
+        if ((rc = dev_alloc((void **)&ends, sizeof(uint32_t) * (size_t)batch * a->R, "endpoint buffer")))
+            return fail(rc);
+        r->scratch.push_back(ends);
+    }
+    if ((e = cudaMemsetAsync(r->d_steps, 0, sizeof(unsigned long long) * 3, st)) != cudaSuccess)
+        return fail(cuda_fail(e, "memset"));
+    if ((e = cudaEventRecord(r->ev_start, st)) != cudaSuccess) return fail(cuda_fail(e, "cudaEventRecord"));
+    for (int64_t b = a->src_begin; b < a->src_end; b += batch) {
+        int64_t be = std::min<int64_t>(a->src_end, b + batch);
+        rc = launch_walks(ctx, g, plan, r, b, be, b - a->src_begin, ends, r->d_steps + 1, st);
+        if (rc) {
+            cudaStreamSynchronize(st);
+            return fail(rc);
+        }
+    }
+    if ((e = cudaEventRecord(r->ev_walk_end, st)) != cudaSuccess) return fail(cuda_fail(e, "cudaEventRecord"));
+    if ((e = cudaEventRecord(r->ev_done, st)) != cudaSuccess) return fail(cuda_fail(e, "cudaEventRecord"));
+    *out = r;
+    return PPR_OK;
+}
+
+int ppr_wait(ppr_result *r, int64_t timeout_ms)
+{
+    if (!r) {
+        set_error("NULL result");
+        return PPR_EINVAL;
+    }
+    int rc = set_device(r->ctx);
+    if (rc) return rc;
+    if (r->waited) return PPR_OK;
+    auto t0 = std::chrono::steady_clock::now();
+    for (;;) {
+        cudaError_t e = cudaEventQuery(r->ev_done);
+        if (e == cudaSuccess) break;
+        if (e != cudaErrorNotReady) return cuda_fail(e, "run");
+        if (timeout_ms >= 0) {
+            auto ms = std::chrono::duration_cast<std::chrono::milliseconds>(std::chrono::steady_clock::now() - t0).count();
+            if (ms >= timeout_ms) {
+                set_error("run not finished after %lld ms", (long long)timeout_ms);
+                return PPR_ETIMEOUT;
+            }
+        }
+        std::this_thread::sleep_for(std::chrono::microseconds(50));
+    }
+    unsigned long long cnt[3] = {0, 0, 0};
+    PPR_CUDA(cudaMemcpy(cnt, r->d_steps, sizeof(cnt), cudaMemcpyDeviceToHost));
+    r->steps = cnt[0];
+    r->sectors = cnt[2];
+    float ms = 0.f;
+    PPR_CUDA(cudaEventElapsedTime(&ms, r->ev_start, r->ev_walk_end));
+    r->kernel_ms = ms;
+    r->waited = true;
+    return PPR_OK;
+}
+
+static int need_done(const ppr_result *r)
+{
+    if (!r) {
+        set_error("NULL result");
+        return PPR_EINVAL;
+    }
+    if (!r->waited) {
+        set_error("result not ready: call ppr_wait first");
+        return PPR_EBUSY;
+    }
+    return set_device(r->ctx);
+}
+
+int ppr_result_get_info(const ppr_result *r, ppr_result_info *info)
+{
+    if (!r || !info) {
+        set_error("NULL argument");
+        return PPR_EINVAL;
+    }
+    info->sources = r->S;
+    info->R = r->R;
+    info->topk = r->topk;
+    info->nnz = r->nnz_total;
+    info->steps = r->steps;
+    info->walks = (uint64_t)r->S * r->R;
+    info->kernel_ms = r->kernel_ms;
+    info->sectors = r->sectors;
+    return PPR_OK;
+}
+
+int ppr_sparse_rows(const ppr_result *rc_, int64_t *row_ptr, int32_t *col, uint32_t *cnt, int64_t cap, int64_t *nnz,
+                    uint32_t flags)
+{
+    int rc = need_done(rc_);
+    if (rc) return rc;
+    ppr_result *r = const_cast<ppr_result *>(rc_);
+    const bool dev_out = (flags & PPR_PTRS_DEVICE) != 0;
+    cudaStream_t st = r->stream;
+    const int64_t S = r->S;
+    int64_t tiles = (S + kScanTile - 1) / kScanTile;
+    uint64_t *d_off = nullptr, *d_tmp = nullptr;
+    if ((rc = dev_alloc((void **)&d_off, sizeof(uint64_t) * (S + 1), "row offsets"))) return rc;
+    if ((rc = dev_alloc((void **)&d_tmp, sizeof(uint64_t) * (tiles + 2), "scan scratch"))) return cudaFree(d_off), rc;
+    int32_t *d_col = nullptr;
+    uint32_t *d_cnt = nullptr;
+    auto done = [&](int code) {
+        cudaFree(d_off);
+        cudaFree(d_tmp);
+        if (!dev_out) {
+            cudaFree(d_col);
+            cudaFree(d_cnt);
+        }
+        return code;
+    };
+    exclusive_scan_u32(r->d_nnz, S, d_off, d_tmp, st);
+    uint64_t total = 0;
+    cudaError_t e = cudaMemcpyAsync(&total, d_off + S, sizeof(uint64_t), cudaMemcpyDeviceToHost, st);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(st);
+    if (e != cudaSuccess) return done(cuda_fail(e, "row scan"));
+    r->nnz_total = (int64_t)total;
+    if (nnz) *nnz = (int64_t)total;
+    if (row_ptr) {
+        e = cudaMemcpyAsync(row_ptr, d_off, sizeof(int64_t) * (S + 1),
+                            dev_out ? cudaMemcpyDeviceToDevice : cudaMemcpyDeviceToHost, st);
+        if (e != cudaSuccess) return done(cuda_fail(e, "row_ptr copy"));
+    }
+    if (col || cnt) {
+        if (!col || !cnt) {
+            set_error("col and cnt must both be given");
+            return done(PPR_EINVAL);
+        }
+        if (cap < (int64_t)total) {
+            set_error("capacity %lld < nnz %llu", (long long)cap, (unsigned long long)total);
+            return done(PPR_ERANGE);
+        }
+        if (dev_out) {
+            d_col = col;
+            d_cnt = cnt;
+        } else {
+            if ((rc = dev_alloc((void **)&d_col, sizeof(int32_t) * (total + 1), "compacted ids"))) return done(rc);
+            if ((rc = dev_alloc((void **)&d_cnt, sizeof(uint32_t) * (total + 1), "compacted counts"))) return done(rc);
+        }
+        int blocks = (int)std::min<int64_t>((S + 7) / 8, (int64_t)r->ctx->sms * 32);
+        if (blocks < 1) blocks = 1;
+        k_compact_rows<<<blocks, 256, 0, st>>>(S, r->cap, r->d_nnz, d_off, r->d_cols, r->d_cnts, d_col, d_cnt);
+        e = cudaGetLastError();
+        if (e == cudaSuccess && !dev_out && total > 0) {
+            e = cudaMemcpyAsync(col, d_col, sizeof(int32_t) * total, cudaMemcpyDeviceToHost, st);
+            if (e == cudaSuccess) e = cudaMemcpyAsync(cnt, d_cnt, sizeof(uint32_t) * total, cudaMemcpyDeviceToHost, st);
+        }
+        if (e != cudaSuccess) return done(cuda_fail(e, "row compaction"));
+    }
+    e = cudaStreamSynchronize(st);
+    if (e != cudaSuccess) return done(cuda_fail(e, "sparse rows"));
+    return done(PPR_OK);
+}
+
+int ppr_topk(const ppr_result *r, int32_t k, int32_t *idx, uint32_t *cnt, uint32_t flags)
+{
+    int rc = need_done(r);
+    if (rc) return rc;
+    if (k < 1 || k > r->topk) {
+        set_error("k = %d outside [1, %d] (the run's topk)", k, r->topk);
+        return PPR_EINVAL;
+    }
+    if (!idx || !cnt) {
+        set_error("idx and cnt must be non-NULL");
+        return PPR_EINVAL;
+    }
+    cudaMemcpyKind kind = (flags & PPR_PTRS_DEVICE) ? cudaMemcpyDeviceToDevice : cudaMemcpyDeviceToHost;
+    PPR_CUDA(cudaMemcpy2DAsync(idx, sizeof(int32_t) * k, r->d_topk_idx, sizeof(int32_t) * r->topk, sizeof(int32_t) * k,
+                               (size_t)r->S, kind, r->stream));
+    PPR_CUDA(cudaMemcpy2DAsync(cnt, sizeof(uint32_t) * k, r->d_topk_cnt, sizeof(uint32_t) * r->topk,
+                               sizeof(uint32_t) * k, (size_t)r->S, kind, r->stream));
+    PPR_CUDA(cudaStreamSynchronize(r->stream));
+    return PPR_OK;
+}
+
+int ppr_dense(const ppr_result *r, uint32_t *out, uint32_t flags)
+{
+    int rc = need_done(r);
+    if (rc) return rc;
+    if (!out) {
+        set_error("out is NULL");
+        return PPR_EINVAL;
+    }
+    if (r->g->instances > 0) {
+        set_error("dense output is defined for plain graphs only");
+        return PPR_ENOTSUP;
+    }
+    const int64_t n = r->g->n;
+    const size_t bytes = sizeof(uint32_t) * (size_t)r->S * (size_t)n;
+    const bool dev_out = (flags & PPR_PTRS_DEVICE) != 0;
+    uint32_t *d = out;
+    if (!dev_out && (rc = dev_alloc((void **)&d, bytes, "dense counts"))) return rc;
+    cudaError_t e = cudaMemsetAsync(d, 0, bytes, r->stream);
+    int blocks = (int)std::min<int64_t>((r->S + 7) / 8, (int64_t)r->ctx->sms * 32);
+    if (blocks < 1) blocks = 1;
+    if (e == cudaSuccess) {
+        k_dense<<<blocks, 256, 0, r->stream>>>(r->S, n, r->cap, r->d_nnz, r->d_cols, r->d_cnts, d);
+        e = cudaGetLastError();
+    }
+    if (e == cudaSuccess && !dev_out) e = cudaMemcpyAsync(out, d, bytes, cudaMemcpyDeviceToHost, r->stream);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(r->stream);
+    if (!dev_out) cudaFree(d);
+    if (e != cudaSuccess) return cuda_fail(e, "dense");
+    return PPR_OK;
+}
+
+void ppr_free_result(ppr_result *r) { result_release(r); }
+
+}  // extern "C"

@@ -1,0 +1,510 @@
+// graph.cu -- device construction of the walk layout (node records, per-row
+// inclusive weight prefixes) and of the depth-3 segment tables.
+//
+// Sec. 2.1 defines the routing probability r(s,t) = w(<s,t>) / sum_v w(<s,v>).
+// The step rule realises it exactly over integers with the row's inclusive
+// prefix P and total W_u: the next edge is the first e with P[e] > x for x
+// uniform on [0, W_u).  Algorithm 4 ("big moves") precomputes, for small
+// nodes, the distribution over short walk outcomes; here it is built with a
+// fixed depth of 3 in 2^62 fixed point, one warp per node.
+#include <cstdio>
+
+#include "ppr_host.h"
+#include "scan.cuh"
+
+namespace ppr {
+
+enum : uint32_t { kBadRowPtr = 1u, kBadCol = 2u, kBadWeight = 4u };
+
+struct BuildStats {
+    unsigned long long max_total;
+    unsigned long long max_degree;
+    unsigned long long dangling;
+    unsigned int status;
+};
+
+// Instance of global node u in a block-diagonal graph (node_off has count+1
+// entries); returns 0 for a plain graph.
+__device__ __forceinline__ int32_t instance_of(const int64_t *node_off, int32_t count, int64_t u)
+{
+    int32_t lo = 0, hi = count;  // find last g with node_off[g] <= u
+    while (hi - lo > 1) {
+        int32_t mid = (lo + hi) >> 1;
+        if (node_off[mid] <= u) lo = mid;
+        else hi = mid;
+    }
+    return lo;
+}
+
+// Pass 1: one warp per row.  Validates the CSR, sums the row weights.
+__global__ void k_rows_pass1(int64_t n, int64_t m, const int64_t *row_ptr, const int32_t *col,
+                             const uint32_t *w, const int64_t *node_off, int32_t count, uint64_t *W,
+                             BuildStats *st)
+{
+    const int lane = threadIdx.x & 31;
+    const int64_t warps = (int64_t)gridDim.x * (blockDim.x >> 5);
+    for (int64_t u = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5; u < n; u += warps) {
+        int64_t a = row_ptr[u], b = row_ptr[u + 1];
+        bool bad = a < 0 || b < a || b > m || (u == 0 && a != 0) || (u == n - 1 && b != m);
+        if (bad) {
+            if (lane == 0) atomicOr(&st->status, kBadRowPtr);
+            if (lane == 0) W[u] = 0;
+            continue;
+        }
+        int64_t lo_id = 0, hi_id = n;
+        if (count > 0) {
+            int32_t g = instance_of(node_off, count, u);
+            lo_id = 0;
+            hi_id = node_off[g + 1] - node_off[g];
+        }
+        uint64_t sum = 0;
+        uint32_t flags = 0;
+        for (int64_t e = a + lane; e < b; e += 32) {
+            uint32_t we = w[e];
+            int64_t c = col[e];
+            if (we == 0) flags |= kBadWeight;
+            if (c < lo_id || c >= hi_id) flags |= kBadCol;
+            sum += we;
+        }
+#pragma unroll
+        for (int o = 16; o > 0; o >>= 1) {
+            sum += __shfl_xor_sync(0xffffffffu, sum, o);
+            flags |= __shfl_xor_sync(0xffffffffu, flags, o);
+        }
+        if (lane == 0) {
+            W[u] = sum;
+            if (flags) atomicOr(&st->status, flags);
+            atomicMax(&st->max_total, (unsigned long long)sum);
+            atomicMax(&st->max_degree, (unsigned long long)(b - a));
+            if (b == a) atomicAdd(&st->dangling, 1ull);
+        }
+    }
+}
+
+// Pass 2: one warp per row.  Inclusive prefix of the row's weights (warp scan
+// over 32-edge chunks with a carry) into the edge records; the node record.
+template <bool WIDE>
+__global__ void k_rows_pass2(int64_t n, const int64_t *row_ptr, const int32_t *col, const uint32_t *w,
+                             const int64_t *node_off, int32_t count, const uint64_t *W, NodeRec *node,
+                             void *edges_v)
+{
+    const int lane = threadIdx.x & 31;
+    const int64_t warps = (int64_t)gridDim.x * (blockDim.x >> 5);
+    for (int64_t u = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5; u < n; u += warps) {
+        int64_t a = row_ptr[u], b = row_ptr[u + 1];
+        int64_t base_id = 0;
+        if (count > 0) base_id = node_off[instance_of(node_off, count, u)];
+        uint64_t carry = 0;
+        for (int64_t e0 = a; e0 < b; e0 += 32) {
+            int64_t e = e0 + lane;
+            uint64_t v = e < b ? (uint64_t)w[e] : 0ull;
+#pragma unroll
+            for (int o = 1; o < 32; o <<= 1) {
+                uint64_t y = __shfl_up_sync(0xffffffffu, v, o);
+                if (lane >= o) v += y;
+            }
+            uint64_t P = carry + v;
+            if (e < b) {
+                int32_t c = (int32_t)(col[e] + base_id);
+                if (WIDE) {
+                    EdgeW r;
+                    r.P = P;
+                    r.col = c;
+                    r.pad = 0;
+                    reinterpret_cast<EdgeW *>(edges_v)[e] = r;
+                } else {
+                    EdgeN r;
+                    r.P = (uint32_t)P;
+                    r.col = c;
+                    reinterpret_cast<EdgeN *>(edges_v)[e] = r;
+                }
+            }
+            carry += __shfl_sync(0xffffffffu, v, 31);
+        }
+        if (lane == 0) {
+            NodeRec r;
+            r.word0 = pack_word0((uint64_t)a, (uint32_t)(b - a), false);
+            r.total = W[u];
+            node[u] = r;
+        }
+    }
+}
+
+int build_graph(ppr_ctx *ctx, int64_t n, int64_t m, const int64_t *row_ptr, const int32_t *col,
+                const uint32_t *w, bool device_ptrs, cudaStream_t st, ppr_graph *g)
+{
+    const int64_t *d_rp = row_ptr;
+    const int32_t *d_col = col;
+    const uint32_t *d_w = w;
+    std::vector<void *> tmp;
+    auto cleanup = [&]() {
+        for (void *p : tmp) cudaFree(p);
+        tmp.clear();
+    };
+    int rc;
+    if (!device_ptrs) {
+        void *p;
+        if ((rc = dev_alloc(&p, sizeof(int64_t) * (n + 1), "row_ptr copy"))) return cleanup(), rc;
+        tmp.push_back(p);
+        d_rp = (const int64_t *)p;
+        if (m > 0) {
+            if ((rc = dev_alloc(&p, sizeof(int32_t) * m, "col copy"))) return cleanup(), rc;
+            tmp.push_back(p);
+            d_col = (const int32_t *)p;
+            if ((rc = dev_alloc(&p, sizeof(uint32_t) * m, "w copy"))) return cleanup(), rc;
+            tmp.push_back(p);
+            d_w = (const uint32_t *)p;
+        }
+        cudaError_t e = cudaMemcpyAsync((void *)d_rp, row_ptr, sizeof(int64_t) * (n + 1), cudaMemcpyHostToDevice, st);
+        if (e == cudaSuccess && m > 0)
+            e = cudaMemcpyAsync((void *)d_col, col, sizeof(int32_t) * m, cudaMemcpyHostToDevice, st);
+        if (e == cudaSuccess && m > 0)
+            e = cudaMemcpyAsync((void *)d_w, w, sizeof(uint32_t) * m, cudaMemcpyHostToDevice, st);
+        if (e != cudaSuccess) return cleanup(), cuda_fail(e, "graph upload");
+    }
+    int64_t *d_off = nullptr;
+    if (g->instances > 0) {
+        void *p;
+        if ((rc = dev_alloc(&p, sizeof(int64_t) * (g->instances + 1), "node_off"))) return cleanup(), rc;
+        tmp.push_back(p);
+        d_off = (int64_t *)p;
+        cudaError_t e = cudaMemcpyAsync(d_off, g->node_off.data(), sizeof(int64_t) * (g->instances + 1),
+                                        cudaMemcpyHostToDevice, st);
+        if (e != cudaSuccess) return cleanup(), cuda_fail(e, "node_off upload");
+    }
+    void *p;
+    if ((rc = dev_alloc(&p, sizeof(uint64_t) * n, "row totals"))) return cleanup(), rc;
+    tmp.push_back(p);
+    uint64_t *d_W = (uint64_t *)p;
+    if ((rc = dev_alloc(&p, sizeof(BuildStats), "build stats"))) return cleanup(), rc;
+    tmp.push_back(p);
+    BuildStats *d_st = (BuildStats *)p;
+    cudaError_t e = cudaMemsetAsync(d_st, 0, sizeof(BuildStats), st);
+    if (e != cudaSuccess) return cleanup(), cuda_fail(e, "memset");
+
+    const int threads = 256;
+    int64_t want_blocks = (n + 7) / 8;
+    int blocks = (int)std::min<int64_t>(want_blocks, (int64_t)ctx->sms * 64);
+    if (blocks < 1) blocks = 1;
+    k_rows_pass1<<<blocks, threads, 0, st>>>(n, m, d_rp, d_col, d_w, d_off, g->instances, d_W, d_st);
+    BuildStats hs;
+    e = cudaMemcpyAsync(&hs, d_st, sizeof(BuildStats), cudaMemcpyDeviceToHost, st);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(st);
+    if (e != cudaSuccess) return cleanup(), cuda_fail(e, "graph validation");
+    if (hs.status & kBadRowPtr) {
+        set_error("row_ptr must start at 0, be non-decreasing and end at m");
+        return cleanup(), PPR_EINVAL;
+    }
+    if (hs.status & kBadCol) {
+        set_error("an edge target is outside [0, n) (of its instance)");
+        return cleanup(), PPR_EINVAL;
+    }
+    if (hs.status & kBadWeight) {
+        set_error("edge weights must be >= 1 (w(e) > 0, Sec. 2.1)");
+        return cleanup(), PPR_EINVAL;
+    }
+    if ((int64_t)hs.max_degree > PPR_MAX_DEGREE) {
+        set_error("out-degree %llu exceeds the limit %lld", hs.max_degree, (long long)PPR_MAX_DEGREE);
+        return cleanup(), PPR_ERANGE;
+    }
+    g->wide = hs.max_total >= (1ull << 32);
+    g->max_degree = (int64_t)hs.max_degree;
+    g->dangling = (int64_t)hs.dangling;
+    size_t edge_bytes = (size_t)m * (g->wide ? sizeof(EdgeW) : sizeof(EdgeN));
+    if ((rc = dev_alloc((void **)&g->node, sizeof(NodeRec) * n, "node records"))) return cleanup(), rc;
+    if ((rc = dev_alloc(&g->edges, edge_bytes > 0 ? edge_bytes : 16, "edge records"))) return cleanup(), rc;
+    g->device_bytes = (int64_t)(sizeof(NodeRec) * n + edge_bytes);
+    if (g->wide)
+        k_rows_pass2<true><<<blocks, threads, 0, st>>>(n, d_rp, d_col, d_w, d_off, g->instances, d_W, g->node, g->edges);
+    else
+        k_rows_pass2<false><<<blocks, threads, 0, st>>>(n, d_rp, d_col, d_w, d_off, g->instances, d_W, g->node, g->edges);
+    e = cudaGetLastError();
+    if (e == cudaSuccess) e = cudaStreamSynchronize(st);
+    cleanup();
+    if (e != cudaSuccess) return cuda_fail(e, "graph build");
+    return PPR_OK;
+}
+
+// ------------------------------------------------------------ segments ----
+
+constexpr int kSegMaxDeg = 8;
+constexpr int kSegMaxOut = 64;
+constexpr int kSegMaxContrib = 2048;  // >= 2 * (8 + 64 + 512)
+
+__device__ __forceinline__ uint64_t mul_shift32(uint64_t q, uint32_t f)
+{
+    // floor(q * f / 2^32), q < 2^63
+    uint64_t lo = q * (uint64_t)f;
+    uint64_t hi = __umul64hi(q, (uint64_t)f);
+    return (hi << 32) | (lo >> 32);
+}
+
+__device__ __forceinline__ uint64_t mul_div(uint64_t q, uint64_t num, uint64_t den)
+{
+    unsigned __int128 p = (unsigned __int128)q * num;
+    return (uint64_t)(p / den);
+}
+
+template <class E>
+struct RowView {
+    const NodeRec *node;
+    E edges;
+    __device__ __forceinline__ uint32_t deg(uint32_t u) const { return (uint32_t)(node[u].word0 >> 40) & kCountMask; }
+    __device__ __forceinline__ uint64_t begin(uint32_t u) const { return node[u].word0 & kBeginMask; }
+    __device__ __forceinline__ uint64_t total(uint32_t u) const { return node[u].total; }
+    // weight and target of the i-th edge of u
+    __device__ __forceinline__ void edge(uint32_t u, uint32_t i, uint64_t &wt, uint32_t &tgt) const
+    {
+        uint64_t b = begin(u);
+        auto r = edges.load(b + i);
+        uint64_t prev = i > 0 ? E::key(edges.load(b + i - 1)) : 0ull;
+        wt = E::key(r) - prev;
+        tgt = E::target(r);
+    }
+};
+
+struct SegScratch {
+    uint64_t key[kSegMaxContrib];
+    uint64_t val[kSegMaxContrib];
+    unsigned int count;
+    unsigned int flags;
+};
+
+// Builds v's outcome list in shared memory (sorted by key, reduced, zero
+// weights dropped).  Returns the number of outcomes, 0 if v is not eligible.
+// All lanes call it; the result is the same on every lane.
+template <class E>
+__device__ uint32_t seg_build_node(const RowView<E> &G, uint32_t v, uint32_t T, SegScratch *sc)
+{
+    const uint32_t lane = threadIdx.x & 31;
+    const uint32_t d1 = G.deg(v);
+    if (d1 < 1 || d1 > kSegMaxDeg) return 0;
+    // eligibility: depth-1 and depth-2 nodes have out-degree <= 8
+    bool ok = true;
+    for (uint32_t p = lane; p < d1 * kSegMaxDeg; p += 32) {
+        uint32_t i1 = p / kSegMaxDeg, i2 = p % kSegMaxDeg;
+        uint64_t wt;
+        uint32_t a;
+        G.edge(v, i1, wt, a);
+        uint32_t da = G.deg(a);
+        if (da > kSegMaxDeg) ok = false;
+        else if (i2 < da) {
+            uint32_t b;
+            G.edge(a, i2, wt, b);
+            if (G.deg(b) > kSegMaxDeg) ok = false;
+        }
+    }
+    if (!__all_sync(0xffffffffu, ok)) return 0;
+    if (lane == 0) sc->count = 0;
+    __syncwarp();
+    const uint32_t cont = (uint32_t)(0x100000000ull - T);  // 2^32 - T, T >= 1
+    const uint64_t Wv = G.total(v);
+    auto push = [&](uint32_t node, uint32_t active, uint32_t len, uint64_t q) {
+        unsigned int i = atomicAdd(&sc->count, 1u);
+        sc->key[i] = ((uint64_t)active << 63) | ((uint64_t)node << 8) | len;
+        sc->val[i] = q;
+    };
+    // all paths of length 1, 2, 3: enumerate (i1, i2, i3) with the shorter
+    // paths emitted by the combinations whose trailing indices are 0
+    for (uint32_t p = lane; p < d1 * kSegMaxDeg * kSegMaxDeg; p += 32) {
+        uint32_t i1 = p / (kSegMaxDeg * kSegMaxDeg), i2 = (p / kSegMaxDeg) % kSegMaxDeg, i3 = p % kSegMaxDeg;
+        uint64_t w1;
+        uint32_t a;
+        G.edge(v, i1, w1, a);
+        uint64_t q1 = mul_div(1ull << 62, w1, Wv);
+        uint32_t da = G.deg(a);
+        if (i2 == 0 && i3 == 0) {
+            push(a, 0, 0, mul_shift32(q1, T));
+            if (da == 0) push(a, 1, 1, mul_shift32(q1, cont));
+        }
+        if (da == 0 || i2 >= da) continue;
+        uint64_t w2;
+        uint32_t b;
+        G.edge(a, i2, w2, b);
+        uint64_t q2 = mul_div(mul_shift32(q1, cont), w2, G.total(a));
+        uint32_t db = G.deg(b);
+        if (i3 == 0) {
+            push(b, 0, 0, mul_shift32(q2, T));
+            if (db == 0) push(b, 1, 2, mul_shift32(q2, cont));
+        }
+        if (db == 0 || i3 >= db) continue;
+        uint64_t w3;
+        uint32_t c;
+        G.edge(b, i3, w3, c);
+        uint64_t q3 = mul_div(mul_shift32(q2, cont), w3, G.total(b));
+        push(c, 0, 0, mul_shift32(q3, T));
+        push(c, 1, 3, mul_shift32(q3, cont));
+    }
+    __syncwarp();
+    const uint32_t cnt = sc->count;
+    const uint32_t P2 = next_pow2(cnt);
+    for (uint32_t i = cnt + lane; i < P2; i += 32) {
+        sc->key[i] = ~0ull;
+        sc->val[i] = 0;
+    }
+    __syncwarp();
+    // bitonic sort of (key, val) pairs by key
+    for (uint32_t k = 2; k <= P2; k <<= 1) {
+        for (uint32_t j = k >> 1; j > 0; j >>= 1) {
+            for (uint32_t i = lane; i < P2; i += 32) {
+                uint32_t l = i ^ j;
+                if (l > i) {
+                    uint64_t x = sc->key[i], y = sc->key[l];
+                    bool up = (i & k) == 0;
+                    if ((x > y) == up) {
+                        sc->key[i] = y;
+                        sc->key[l] = x;
+                        uint64_t t = sc->val[i];
+                        sc->val[i] = sc->val[l];
+                        sc->val[l] = t;
+                    }
+                }
+            }
+            __syncwarp();
+        }
+    }
+    // reduce equal keys (integer sums: order free) -- lane 0, at most 2048 entries
+    if (lane == 0) {
+        uint32_t outn = 0;
+        uint32_t i = 0;
+        while (i < cnt) {
+            uint64_t k = sc->key[i], s = 0;
+            while (i < cnt && sc->key[i] == k) s += sc->val[i++];
+            if (s > 0) {
+                sc->key[outn] = k;
+                sc->val[outn] = s;
+                ++outn;
+            }
+        }
+        sc->flags = outn;
+    }
+    __syncwarp();
+    uint32_t outn = sc->flags;
+    __syncwarp();
+    return outn <= (uint32_t)kSegMaxOut ? outn : 0u;
+}
+
+template <class E>
+__global__ void k_seg_count(RowView<E> G, int64_t n, uint32_t T, uint32_t *counts)
+{
+    extern __shared__ __align__(16) unsigned char smem_raw[];
+    SegScratch *sc = reinterpret_cast<SegScratch *>(smem_raw) + (threadIdx.x >> 5);
+    const int64_t warps = (int64_t)gridDim.x * (blockDim.x >> 5);
+    for (int64_t v = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5; v < n; v += warps) {
+        uint32_t c = seg_build_node(G, (uint32_t)v, T, sc);
+        if ((threadIdx.x & 31) == 0) counts[v] = c;
+    }
+}
+
+template <class E>
+__global__ void k_seg_write(RowView<E> G, int64_t n, uint32_t T, const uint64_t *offs, SegEntry *ent,
+                            NodeRec *seg_node)
+{
+    extern __shared__ __align__(16) unsigned char smem_raw[];
+    SegScratch *sc = reinterpret_cast<SegScratch *>(smem_raw) + (threadIdx.x >> 5);
+    const uint32_t lane = threadIdx.x & 31;
+    const int64_t warps = (int64_t)gridDim.x * (blockDim.x >> 5);
+    for (int64_t v = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5; v < n; v += warps) {
+        uint64_t o = offs[v];
+        uint32_t c = (uint32_t)(offs[v + 1] - o);
+        if (c == 0) {
+            if (lane == 0) seg_node[v] = G.node[v];
+            continue;
+        }
+        uint32_t c2 = seg_build_node(G, (uint32_t)v, T, sc);
+        (void)c2;  // identical to the counting pass
+        if (lane == 0) {
+            uint64_t acc = 0;
+            for (uint32_t i = 0; i < c; ++i) {
+                uint64_t k = sc->key[i];
+                acc += sc->val[i];
+                SegEntry s;
+                s.cum = acc;
+                s.node = (uint32_t)((k >> 8) & 0x7fffffffull);
+                s.mark_len = ((uint32_t)(k >> 63) << 8) | (uint32_t)(k & 0xff);
+                ent[o + i] = s;
+            }
+            NodeRec r;
+            r.word0 = pack_word0(o, c, true);
+            r.total = acc;
+            seg_node[v] = r;
+        }
+        __syncwarp();
+    }
+}
+
+int build_segments(ppr_graph *g, uint32_t T, cudaStream_t st)
+{
+    if (g->seg.T == T && g->seg.node) return PPR_OK;
+    if (g->seg.node) cudaFree(g->seg.node);
+    if (g->seg.entries) cudaFree(g->seg.entries);
+    g->seg = SegCache{};
+    const int64_t n = g->n;
+    uint32_t *d_cnt = nullptr;
+    uint64_t *d_off = nullptr, *d_tmp = nullptr;
+    int rc;
+    int64_t tiles = (n + kScanTile - 1) / kScanTile;
+    if ((rc = dev_alloc((void **)&d_cnt, sizeof(uint32_t) * n, "segment counts"))) return rc;
+    if ((rc = dev_alloc((void **)&d_off, sizeof(uint64_t) * (n + 1), "segment offsets"))) return cudaFree(d_cnt), rc;
+    if ((rc = dev_alloc((void **)&d_tmp, sizeof(uint64_t) * (tiles + 2), "scan scratch")))
+        return cudaFree(d_cnt), cudaFree(d_off), rc;
+    auto fail = [&](int code) {
+        cudaFree(d_cnt);
+        cudaFree(d_off);
+        cudaFree(d_tmp);
+        return code;
+    };
+    const int wpb = 2;
+    const size_t smem = sizeof(SegScratch) * wpb;
+    int blocks = (int)std::min<int64_t>((n + wpb - 1) / wpb, (int64_t)g->ctx->sms * 32);
+    if (blocks < 1) blocks = 1;
+    cudaError_t e;
+    if (g->wide) {
+        RowView<WideEdges> G{g->node, WideEdges{(const EdgeW *)g->edges}};
+        cudaFuncSetAttribute(k_seg_count<WideEdges>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+        k_seg_count<WideEdges><<<blocks, wpb * 32, smem, st>>>(G, n, T, d_cnt);
+    } else {
+        RowView<NarrowEdges> G{g->node, NarrowEdges{(const EdgeN *)g->edges}};
+        cudaFuncSetAttribute(k_seg_count<NarrowEdges>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+        k_seg_count<NarrowEdges><<<blocks, wpb * 32, smem, st>>>(G, n, T, d_cnt);
+    }
+    exclusive_scan_u32(d_cnt, n, d_off, d_tmp, st);
+    uint64_t total = 0;
+    e = cudaMemcpyAsync(&total, d_off + n, sizeof(uint64_t), cudaMemcpyDeviceToHost, st);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(st);
+    if (e != cudaSuccess) return fail(cuda_fail(e, "segment count"));
+    if ((rc = dev_alloc((void **)&g->seg.node, sizeof(NodeRec) * n, "segment node records"))) return fail(rc);
+    if ((rc = dev_alloc((void **)&g->seg.entries, sizeof(SegEntry) * (total > 0 ? total : 1), "segment tables"))) {
+        cudaFree(g->seg.node);
+        g->seg.node = nullptr;
+        return fail(rc);
+    }
+    if (g->wide) {
+        RowView<WideEdges> G{g->node, WideEdges{(const EdgeW *)g->edges}};
+        cudaFuncSetAttribute(k_seg_write<WideEdges>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+        k_seg_write<WideEdges><<<blocks, wpb * 32, smem, st>>>(G, n, T, d_off, g->seg.entries, g->seg.node);
+    } else {
+        RowView<NarrowEdges> G{g->node, NarrowEdges{(const EdgeN *)g->edges}};
+        cudaFuncSetAttribute(k_seg_write<NarrowEdges>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+        k_seg_write<NarrowEdges><<<blocks, wpb * 32, smem, st>>>(G, n, T, d_off, g->seg.entries, g->seg.node);
+    }
+    e = cudaGetLastError();
+    if (e == cudaSuccess) e = cudaStreamSynchronize(st);
+    if (e != cudaSuccess) return fail(cuda_fail(e, "segment build"));
+    g->seg.T = T;
+    g->seg.entries_n = (int64_t)total;
+    {
+        // number of nodes with a table, for the info query
+        std::vector<uint32_t> hc((size_t)n);
+        e = cudaMemcpy(hc.data(), d_cnt, sizeof(uint32_t) * n, cudaMemcpyDeviceToHost);
+        if (e != cudaSuccess) return fail(cuda_fail(e, "segment count copy"));
+        int64_t nz = 0;
+        for (uint32_t c : hc) nz += c > 0;
+        g->seg.nodes = nz;
+    }
+    g->device_bytes += (int64_t)(sizeof(NodeRec) * n + sizeof(SegEntry) * total);
+    fail(PPR_OK);
+    return PPR_OK;
+}
+
+}  // namespace ppr

@@ -1,0 +1,105 @@
+// ppr_host.h -- host-side objects behind the C ABI (not part of the ABI).
+#pragma once
+
+#include <cstdint>
+#include <string>
+#include <vector>
+
+#include <cuda_runtime.h>
+
+#include "../../include/ppr.h"
+#include "ppr_internal.cuh"
+
+namespace ppr {
+
+void set_error(const char *fmt, ...);
+int cuda_fail(cudaError_t e, const char *what);
+
+#define PPR_CUDA(call)                                                 \
+    do {                                                               \
+        cudaError_t e_ = (call);                                       \
+        if (e_ != cudaSuccess) return ::ppr::cuda_fail(e_, #call);     \
+    } while (0)
+
+// Device allocation that reports PPR_ENOMEM.
+int dev_alloc(void **p, size_t bytes, const char *what);
+
+struct SegCache {
+    uint32_t T = 0;               // threshold the tables were built for (0 = none)
+    NodeRec *node = nullptr;      // node records with eligible nodes switched to their tables
+    SegEntry *entries = nullptr;  // all tables
+    int64_t nodes = 0, entries_n = 0;
+};
+
+}  // namespace ppr
+
+struct ppr_ctx {
+    int device = 0;
+    int sms = 0;
+    size_t smem_optin = 0;
+};
+
+struct ppr_graph {
+    ppr_ctx *ctx = nullptr;
+    int64_t n = 0, m = 0;
+    int64_t max_degree = 0, dangling = 0;
+    bool wide = false;
+    ppr::NodeRec *node = nullptr;
+    void *edges = nullptr;  // EdgeN[m] or EdgeW[m]
+    // block-diagonal instances
+    int32_t instances = 0;
+    std::vector<int64_t> node_off;  // host copy, count+1
+    ppr::SegCache seg;
+    int64_t device_bytes = 0;
+};
+
+struct ppr_result {
+    ppr_ctx *ctx = nullptr;
+    const ppr_graph *g = nullptr;
+    cudaStream_t stream = nullptr;
+    int64_t S = 0;
+    uint32_t R = 0;
+    int32_t topk = 0;
+    uint32_t cap = 0;
+    int64_t src_begin = 0;
+    uint32_t *d_nnz = nullptr;
+    int32_t *d_cols = nullptr;
+    uint32_t *d_cnts = nullptr;
+    int32_t *d_topk_idx = nullptr;
+    uint32_t *d_topk_cnt = nullptr;
+    unsigned long long *d_steps = nullptr;  // [0] steps, [1] work-queue head, [2] sectors
+    cudaEvent_t ev_start = nullptr, ev_walk_end = nullptr, ev_done = nullptr;
+    bool waited = false;
+    uint64_t steps = 0, sectors = 0;
+    float kernel_ms = 0.f;
+    int64_t nnz_total = -1;
+    std::vector<void *> scratch;  // freed with the result
+};
+
+namespace ppr {
+
+// graph.cu
+int build_graph(ppr_ctx *ctx, int64_t n, int64_t m, const int64_t *row_ptr, const int32_t *col,
+                const uint32_t *w, bool device_ptrs, cudaStream_t st, ppr_graph *g);
+int build_segments(ppr_graph *g, uint32_t T, cudaStream_t st);
+
+// walk.cu
+struct RunPlan {
+    uint32_t T, R;
+    uint64_t seed;
+    uint32_t tag;
+    int32_t dangling;
+    bool segments;
+    int32_t kernel;
+    int32_t large_degree;
+    int32_t warps_per_block;
+    int32_t chunk_sources;
+    bool stats;
+};
+// Enqueues the walks of sources [s_begin, s_end) writing output rows from
+// out_row0.  ends: S * R endpoint scratch for the plain kernel (else unused);
+// queue: one device counter for the persistent kernel's work queue.
+int launch_walks(ppr_ctx *ctx, const ppr_graph *g, const RunPlan &p, ppr_result *r, int64_t s_begin,
+                 int64_t s_end, int64_t out_row0, uint32_t *ends, unsigned long long *queue, cudaStream_t st);
+
+}  // namespace ppr

@@ -1,0 +1,318 @@
+// ppr_internal.cuh -- device-side building blocks of libppr.so (sm_103a).
+//
+// Graph layout in HBM
+//   NodeRec (16 B, one aligned half-sector per node)
+//     word0 = begin (bits 0..39) | count (bits 40..62) | segment flag (bit 63)
+//     word1 = W_u, the row's total weight (Sec. 2.1 routing denominator), or
+//             Q_v, the total fixed-point mass of a segment table (Algorithm 4)
+//   plain rows:  begin/count index the edge-record array
+//   segment rows: begin/count index the segment-entry array
+//   EdgeN (8 B): {uint32 P, int32 col}  -- narrow layout, every W_u < 2^32
+//   EdgeW (16 B): {uint64 P, int32 col, pad} -- wide layout
+//   SegEntry (16 B): {uint64 cum, uint32 node, uint32 mark_len}
+//   P / cum are inclusive prefix sums within the row / table.
+#pragma once
+
+#include <cstdint>
+#include <cuda_runtime.h>
+
+namespace ppr {
+
+constexpr uint64_t kBeginMask = (1ull << 40) - 1;
+constexpr uint32_t kCountMask = (1u << 23) - 1;
+constexpr uint64_t kSegFlag = 1ull << 63;
+
+struct __align__(16) NodeRec {
+    uint64_t word0;
+    uint64_t total;
+};
+
+struct __align__(8) EdgeN {
+    uint32_t P;
+    int32_t col;
+};
+
+struct __align__(16) EdgeW {
+    uint64_t P;
+    int32_t col;
+    uint32_t pad;
+};
+
+struct __align__(16) SegEntry {
+    uint64_t cum;
+    uint32_t node;
+    uint32_t mark_len;  // (active << 8) | len
+};
+
+__host__ __device__ inline uint64_t pack_word0(uint64_t begin, uint32_t count, bool seg)
+{
+    return (begin & kBeginMask) | ((uint64_t)(count & kCountMask) << 40) | (seg ? kSegFlag : 0ull);
+}
+
+// ---------------------------------------------------------------- Philox ----
+// Philox4x32-10 (Salmon, Moraes, Dror, Shaw, SC'11): ten rounds; each round
+// takes the 32x32->64 products of counter words 0 and 2 with two fixed
+// multipliers, and the new words are (hi1 ^ c1 ^ k0, lo1, hi0 ^ c3 ^ k1, lo0);
+// the key advances by the golden-ratio and sqrt(3) Weyl increments between
+// rounds.
+__device__ __forceinline__ uint4 philox4x32_10(uint4 c, uint32_t k0, uint32_t k1)
+{
+#pragma unroll
+    for (int r = 0; r < 10; ++r) {
+        if (r > 0) {
+            k0 += 0x9E3779B9u;
+            k1 += 0xBB67AE85u;
+        }
+        const uint32_t m0 = 0xD2511F53u, m1 = 0xCD9E8D57u;
+        uint32_t lo0 = m0 * c.x, hi0 = __umulhi(m0, c.x);
+        uint32_t lo1 = m1 * c.z, hi1 = __umulhi(m1, c.z);
+        c = make_uint4(hi1 ^ c.y ^ k0, lo1, hi0 ^ c.w ^ k1, lo0);
+    }
+    return c;
+}
+
+// floor(r * W / 2^64) for a 32-bit W, exactly, with two 32x32 products.
+__device__ __forceinline__ uint64_t mulhi64_by32(uint32_t r_lo, uint32_t r_hi, uint32_t W)
+{
+    uint64_t a = (uint64_t)r_lo * W;
+    uint64_t b = (uint64_t)r_hi * W + (a >> 32);
+    return b >> 32;
+}
+
+__device__ __forceinline__ uint64_t mulhi64(uint64_t r, uint64_t W) { return __umul64hi(r, W); }
+
+// ---------------------------------------------------------------- loads ----
+__device__ __forceinline__ NodeRec load_node(const NodeRec *node, uint32_t u)
+{
+    uint4 v = __ldg(reinterpret_cast<const uint4 *>(node) + u);
+    NodeRec r;
+    r.word0 = (uint64_t)v.x | ((uint64_t)v.y << 32);
+    r.total = (uint64_t)v.z | ((uint64_t)v.w << 32);
+    return r;
+}
+
+struct NarrowEdges {
+    using Key = uint32_t;
+    const EdgeN *e;
+    __device__ __forceinline__ uint2 load(uint64_t i) const
+    {
+        return __ldg(reinterpret_cast<const uint2 *>(e) + i);
+    }
+    __device__ __forceinline__ static uint64_t key(uint2 v) { return v.x; }
+    __device__ __forceinline__ static uint32_t target(uint2 v) { return v.y; }
+    using Rec = uint2;
+};
+
+struct WideEdges {
+    const EdgeW *e;
+    __device__ __forceinline__ uint4 load(uint64_t i) const
+    {
+        return __ldg(reinterpret_cast<const uint4 *>(e) + i);
+    }
+    __device__ __forceinline__ static uint64_t key(uint4 v) { return (uint64_t)v.x | ((uint64_t)v.y << 32); }
+    __device__ __forceinline__ static uint32_t target(uint4 v) { return v.z; }
+    using Rec = uint4;
+};
+
+// Segment entries have the same 16-byte shape as wide edges: key = cum,
+// target = node, and the fourth word carries mark_len.
+struct SegTable {
+    const SegEntry *e;
+    __device__ __forceinline__ uint4 load(uint64_t i) const
+    {
+        return __ldg(reinterpret_cast<const uint4 *>(e) + i);
+    }
+    __device__ __forceinline__ static uint64_t key(uint4 v) { return (uint64_t)v.x | ((uint64_t)v.y << 32); }
+    __device__ __forceinline__ static uint32_t target(uint4 v) { return v.z; }
+    using Rec = uint4;
+};
+
+// Smallest index e in [lo, lo+n) with key(e) > x, given key(lo+n-1) > x.
+// Thread-serial bisection; returns the record at e.
+template <class E>
+__device__ __forceinline__ typename E::Rec search_serial(const E &edges, uint64_t lo, uint32_t n, uint64_t x)
+{
+    while (n > 1) {
+        uint32_t half = n >> 1;
+        typename E::Rec v = edges.load(lo + half - 1);
+        if (E::key(v) <= x) {
+            lo += half;
+            n -= half;
+        } else {
+            n = half;
+        }
+    }
+    return edges.load(lo);
+}
+
+// The same bisection, also counting the distinct 32-byte sectors its probes
+// touch (consecutive probes in one sector count once).  Used by the
+// statistics launch that measures the algorithmic bytes of a run.
+template <class E>
+__device__ __forceinline__ typename E::Rec search_serial_tally(const E &edges, uint64_t lo, uint32_t n, uint64_t x,
+                                                              uint32_t &sectors)
+{
+    const uint64_t base = reinterpret_cast<uint64_t>(edges.e);
+    constexpr uint64_t rec = sizeof(typename E::Rec);
+    uint64_t last = ~0ull;
+    while (n > 1) {
+        uint32_t half = n >> 1;
+        uint64_t sec = (base + (lo + half - 1) * rec) >> 5;
+        if (sec != last) ++sectors, last = sec;
+        typename E::Rec v = edges.load(lo + half - 1);
+        if (E::key(v) <= x) {
+            lo += half;
+            n -= half;
+        } else {
+            n = half;
+        }
+    }
+    uint64_t sec = (base + lo * rec) >> 5;
+    if (sec != last) ++sectors;
+    return edges.load(lo);
+}
+
+// Same result, computed by the whole warp for one lane's search (all 32 lanes
+// must call it with the same arguments).  Each round splits the range into 32
+// parts, every lane reads the last key of one part and a ballot locates the
+// part holding the answer: ceil(log32 n) + 1 rounds instead of log2 n
+// dependent loads.
+template <class E>
+__device__ __forceinline__ typename E::Rec search_warp(const E &edges, uint64_t lo, uint32_t n, uint64_t x)
+{
+    const uint32_t lane = threadIdx.x & 31;
+    while (n > 32) {
+        uint32_t end_i = (uint32_t)(((uint64_t)(lane + 1) * n) >> 5);  // part i = [i*n/32, (i+1)*n/32)
+        uint32_t beg_i = (uint32_t)(((uint64_t)lane * n) >> 5);
+        bool above = true;
+        if (end_i > beg_i) above = E::key(edges.load(lo + end_i - 1)) > x;
+        uint32_t mask = __ballot_sync(0xffffffffu, above);
+        uint32_t f = __ffs(mask) - 1;  // mask != 0: the last part ends at n-1 whose key > x
+        uint32_t nb = (uint32_t)(((uint64_t)f * n) >> 5);
+        uint32_t ne = (uint32_t)(((uint64_t)(f + 1) * n) >> 5);
+        lo += nb;
+        n = ne - nb;
+    }
+    typename E::Rec v{};
+    bool above = false;
+    if (lane < n) {
+        v = edges.load(lo + lane);
+        above = E::key(v) > x;
+    }
+    uint32_t mask = __ballot_sync(0xffffffffu, above);
+    uint32_t f = __ffs(mask) - 1;
+    typename E::Rec r;
+    if constexpr (sizeof(typename E::Rec) == 8) {
+        r.x = __shfl_sync(0xffffffffu, v.x, f);
+        r.y = __shfl_sync(0xffffffffu, v.y, f);
+    } else {
+        r.x = __shfl_sync(0xffffffffu, v.x, f);
+        r.y = __shfl_sync(0xffffffffu, v.y, f);
+        r.z = __shfl_sync(0xffffffffu, v.z, f);
+        r.w = __shfl_sync(0xffffffffu, v.w, f);
+    }
+    return r;
+}
+
+// ----------------------------------------------------------- aggregation ----
+// Per-source aggregation of R endpoints (Algorithm 2's final grouping of the
+// terminated walks by (head, tail)), done by one warp in shared memory:
+// bitonic sort of the endpoints, run-length counting, row write-out, then a
+// second bitonic sort of (count desc, end asc) keys for the top-k.
+
+__device__ __forceinline__ uint32_t next_pow2(uint32_t v)
+{
+    uint32_t p = 1;
+    while (p < v) p <<= 1;
+    return p;
+}
+
+template <class T>
+__device__ __forceinline__ void warp_bitonic_sort(T *a, uint32_t n_pow2)
+{
+    const uint32_t lane = threadIdx.x & 31;
+    for (uint32_t k = 2; k <= n_pow2; k <<= 1) {
+        for (uint32_t j = k >> 1; j > 0; j >>= 1) {
+            for (uint32_t i = lane; i < n_pow2; i += 32) {
+                uint32_t l = i ^ j;
+                if (l > i) {
+                    T x = a[i], y = a[l];
+                    bool up = (i & k) == 0;
+                    if ((x > y) == up) {
+                        a[i] = y;
+                        a[l] = x;
+                    }
+                }
+            }
+            __syncwarp();
+        }
+    }
+}
+
+struct AggOut {
+    uint32_t *nnz;       // [S]
+    int32_t *cols;       // [S * cap]
+    uint32_t *cnts;      // [S * cap]
+    int32_t *topk_idx;   // [S * topk]
+    uint32_t *topk_cnt;  // [S * topk]
+    uint32_t cap;
+    int32_t topk;
+};
+
+// ends: the R endpoints of one source (shared memory).  sortbuf: next_pow2(R)
+// uint32 and keys: next_pow2(R) uint64 of per-warp shared scratch.  Writes
+// row `out_row` of the outputs.  All 32 lanes call it.
+__device__ inline void aggregate_source(const uint32_t *ends, uint32_t R, uint32_t *sortbuf, uint64_t *keys,
+                                        const AggOut &o, uint64_t out_row)
+{
+    const uint32_t lane = threadIdx.x & 31;
+    const uint32_t P2 = next_pow2(R);
+    for (uint32_t i = lane; i < P2; i += 32) sortbuf[i] = i < R ? ends[i] : 0xffffffffu;
+    __syncwarp();
+    warp_bitonic_sort(sortbuf, P2);
+    // One run per distinct endpoint.  A run is found at its last element;
+    // its first element comes from a lower-bound search of the sorted buffer.
+    const uint64_t rbase = out_row * o.cap;
+    uint32_t nrun = 0;
+    for (uint32_t base = 0; base < R; base += 32) {
+        uint32_t i = base + lane;
+        uint32_t v = i < R ? sortbuf[i] : 0u;
+        bool tail = i < R && (i == R - 1 || sortbuf[i + 1] != v);
+        uint32_t m = __ballot_sync(0xffffffffu, tail);
+        if (tail) {
+            uint32_t r = nrun + __popc(m & ((1u << lane) - 1));
+            uint32_t lo = 0, hi = i;
+            while (lo < hi) {
+                uint32_t mid = (lo + hi) >> 1;
+                if (sortbuf[mid] < v) lo = mid + 1;
+                else hi = mid;
+            }
+            uint32_t c = i - lo + 1;
+            o.cols[rbase + r] = (int32_t)v;
+            o.cnts[rbase + r] = c;
+            if (o.topk > 0) keys[r] = ((uint64_t)(~c) << 32) | v;
+        }
+        nrun += __popc(m);
+    }
+    if (lane == 0) o.nnz[out_row] = nrun;
+    if (o.topk > 0) {
+        uint32_t K2 = next_pow2(nrun);
+        for (uint32_t i = nrun + lane; i < K2; i += 32) keys[i] = ~0ull;
+        __syncwarp();
+        warp_bitonic_sort(keys, K2);
+        const uint64_t tb = out_row * (uint64_t)o.topk;
+        for (uint32_t i = lane; i < (uint32_t)o.topk; i += 32) {
+            if (i < nrun) {
+                uint64_t k = keys[i];
+                o.topk_idx[tb + i] = (int32_t)(uint32_t)k;
+                o.topk_cnt[tb + i] = ~(uint32_t)(k >> 32);
+            } else {
+                o.topk_idx[tb + i] = -1;
+                o.topk_cnt[tb + i] = 0;
+            }
+        }
+    }
+    __syncwarp();
+}
+
+}  // namespace ppr

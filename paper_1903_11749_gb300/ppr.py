@@ -1,0 +1,276 @@
+"""Python binding of libppr.so: argument marshalling only.
+
+Every computation runs in the CUDA library behind include/ppr.h; this module
+passes pointers and sizes through ctypes and turns status codes into
+exceptions.  Host arrays are numpy arrays; device arrays are torch CUDA
+tensors (their data pointers are passed with PPR_PTRS_DEVICE).  There is no
+fallback: if the library is missing or cannot load, every call raises.
+"""
+from __future__ import annotations
+
+import ctypes as C
+import os
+
+import numpy as np
+
+_HERE = os.path.dirname(os.path.abspath(__file__))
+LIB_PATH = os.path.join(_HERE, "libppr.so")
+
+PPR_OK, PPR_EINVAL, PPR_ENOMEM, PPR_ECUDA, PPR_ETIMEOUT, PPR_ERANGE, PPR_EBUSY, PPR_ENOTSUP = 0, -1, -2, -3, -4, -5, -6, -7
+PPR_PTRS_DEVICE = 1
+KERNEL_PERSISTENT, KERNEL_PLAIN = 0, 1
+_NAMES = {-1: "EINVAL", -2: "ENOMEM", -3: "ECUDA", -4: "ETIMEOUT", -5: "ERANGE", -6: "EBUSY", -7: "ENOTSUP"}
+
+
+class PPRError(RuntimeError):
+    def __init__(self, code: int, msg: str):
+        super().__init__(f"{_NAMES.get(code, code)}: {msg}")
+        self.code = code
+
+
+class GraphInfo(C.Structure):
+    _fields_ = [("n", C.c_int64), ("m", C.c_int64), ("max_degree", C.c_int64), ("dangling", C.c_int64),
+                ("wide", C.c_int32), ("instances", C.c_int32), ("device_bytes", C.c_int64),
+                ("segment_nodes", C.c_int64), ("segment_entries", C.c_int64)]
+
+
+class RunArgs(C.Structure):
+    _fields_ = [("alpha", C.c_double), ("R", C.c_uint32), ("seed", C.c_uint64), ("src_begin", C.c_int64),
+                ("src_end", C.c_int64), ("tag", C.c_uint32), ("dangling", C.c_int32), ("segments", C.c_int32),
+                ("topk", C.c_int32), ("kernel", C.c_int32), ("large_degree", C.c_int32),
+                ("warps_per_block", C.c_int32), ("chunk_sources", C.c_int32), ("max_batch_sources", C.c_int64),
+                ("stats", C.c_int32), ("stream", C.c_void_p)]
+
+
+class ResultInfo(C.Structure):
+    _fields_ = [("sources", C.c_int64), ("R", C.c_uint32), ("topk", C.c_int32), ("nnz", C.c_int64),
+                ("steps", C.c_uint64), ("walks", C.c_uint64), ("kernel_ms", C.c_float), ("sectors", C.c_uint64)]
+
+
+# Every symbol include/ppr.h declares, with its ctypes signature.
+_SIGS = {
+    "ppr_version": (C.c_int, []),
+    "ppr_alpha_threshold": (C.c_uint32, [C.c_double]),
+    "ppr_last_error": (C.c_char_p, []),
+    "ppr_create": (C.c_int, [C.c_int, C.POINTER(C.c_void_p)]),
+    "ppr_destroy": (None, [C.c_void_p]),
+    "ppr_device_sms": (C.c_int, [C.c_void_p]),
+    "ppr_load_graph": (C.c_int, [C.c_void_p, C.c_int64, C.c_int64, C.c_void_p, C.c_void_p, C.c_void_p, C.c_uint32,
+                                 C.c_void_p, C.POINTER(C.c_void_p)]),
+    "ppr_load_graph_batch": (C.c_int, [C.c_void_p, C.c_int32, C.c_void_p, C.c_int64, C.c_void_p, C.c_void_p,
+                                       C.c_void_p, C.c_uint32, C.c_void_p, C.POINTER(C.c_void_p)]),
+    "ppr_graph_get_info": (C.c_int, [C.c_void_p, C.POINTER(GraphInfo)]),
+    "ppr_free_graph": (None, [C.c_void_p]),
+    "ppr_run_args_init": (None, [C.POINTER(RunArgs)]),
+    "ppr_run": (C.c_int, [C.c_void_p, C.c_void_p, C.POINTER(RunArgs), C.POINTER(C.c_void_p)]),
+    "ppr_wait": (C.c_int, [C.c_void_p, C.c_int64]),
+    "ppr_result_get_info": (C.c_int, [C.c_void_p, C.POINTER(ResultInfo)]),
+    "ppr_sparse_rows": (C.c_int, [C.c_void_p, C.c_void_p, C.c_void_p, C.c_void_p, C.c_int64,
+                                  C.POINTER(C.c_int64), C.c_uint32]),
+    "ppr_topk": (C.c_int, [C.c_void_p, C.c_int32, C.c_void_p, C.c_void_p, C.c_uint32]),
+    "ppr_dense": (C.c_int, [C.c_void_p, C.c_void_p, C.c_uint32]),
+    "ppr_free_result": (None, [C.c_void_p]),
+}
+
+_lib = None
+
+
+def lib():
+    """The loaded CUDA library; raises if it has not been built."""
+    global _lib
+    if _lib is None:
+        if not os.path.exists(LIB_PATH):
+            raise ImportError(f"{LIB_PATH} is missing: build it with paper_1903_11749_gb300.build.build()")
+        L = C.CDLL(LIB_PATH)
+        for name, (res, args) in _SIGS.items():
+            fn = getattr(L, name)
+            fn.restype = res
+            fn.argtypes = args
+        _lib = L
+    return _lib
+
+
+def _check(rc: int):
+    if rc != PPR_OK:
+        raise PPRError(rc, lib().ppr_last_error().decode(errors="replace"))
+
+
+def alpha_threshold(alpha: float) -> int:
+    return int(lib().ppr_alpha_threshold(alpha))
+
+
+def _ptr(a):
+    """(pointer, is_device) of a numpy array or a torch tensor."""
+    if isinstance(a, np.ndarray):
+        assert a.flags.c_contiguous
+        return a.ctypes.data, False
+    if hasattr(a, "data_ptr"):
+        assert a.is_contiguous()
+        return a.data_ptr(), a.is_cuda
+    raise TypeError(type(a))
+
+
+def _stream_ptr(stream):
+    if stream is None:
+        return None
+    return getattr(stream, "cuda_stream", stream)
+
+
+class Context:
+    def __init__(self, device: int = 0):
+        h = C.c_void_p()
+        _check(lib().ppr_create(device, C.byref(h)))
+        self.h = h
+        self.device = device
+
+    @property
+    def sms(self) -> int:
+        return lib().ppr_device_sms(self.h)
+
+    def close(self):
+        if self.h:
+            lib().ppr_destroy(self.h)
+            self.h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def load_graph(self, n, row_ptr, col, w, stream=None, m=None) -> "Graph":
+        rp, dev = _ptr(row_ptr)
+        cp, dev2 = _ptr(col)
+        wp, dev3 = _ptr(w)
+        if not (dev == dev2 == dev3):
+            raise ValueError("row_ptr, col and w must all be host arrays or all device tensors")
+        if m is None:
+            m = int(row_ptr[-1]) if not dev else int(row_ptr[-1].item())
+        h = C.c_void_p()
+        _check(lib().ppr_load_graph(self.h, n, m, rp, cp, wp, PPR_PTRS_DEVICE if dev else 0, _stream_ptr(stream),
+                                    C.byref(h)))
+        return Graph(self, h)
+
+    def load_graph_batch(self, node_off, row_ptr, col, w, stream=None) -> "Graph":
+        node_off = np.ascontiguousarray(node_off, dtype=np.int64)
+        rp, dev = _ptr(row_ptr)
+        cp, _ = _ptr(col)
+        wp, _ = _ptr(w)
+        m = int(row_ptr[-1]) if not dev else int(row_ptr[-1].item())
+        h = C.c_void_p()
+        _check(lib().ppr_load_graph_batch(self.h, len(node_off) - 1, node_off.ctypes.data, m, rp, cp, wp,
+                                          PPR_PTRS_DEVICE if dev else 0, _stream_ptr(stream), C.byref(h)))
+        return Graph(self, h)
+
+
+class Graph:
+    def __init__(self, ctx: Context, h):
+        self.ctx = ctx
+        self.h = h
+
+    def info(self) -> GraphInfo:
+        gi = GraphInfo()
+        _check(lib().ppr_graph_get_info(self.h, C.byref(gi)))
+        return gi
+
+    def free(self):
+        if self.h:
+            lib().ppr_free_graph(self.h)
+            self.h = None
+
+    def __del__(self):
+        try:
+            self.free()
+        except Exception:
+            pass
+
+    def run(self, alpha=0.15, R=100, seed=1, src_begin=0, src_end=None, tag=0, dangling=0, segments=False,
+            topk=0, kernel=KERNEL_PERSISTENT, large_degree=0, warps_per_block=0, chunk_sources=0,
+            max_batch_sources=0, stats=False, stream=None, wait=True) -> "Result":
+        a = RunArgs()
+        lib().ppr_run_args_init(C.byref(a))
+        a.alpha, a.R, a.seed = alpha, R, seed
+        a.src_begin = src_begin
+        a.src_end = self.info().n if src_end is None else src_end
+        a.tag, a.dangling, a.segments, a.topk, a.kernel = tag, dangling, int(bool(segments)), topk, kernel
+        a.large_degree, a.warps_per_block, a.chunk_sources = large_degree, warps_per_block, chunk_sources
+        a.max_batch_sources = max_batch_sources
+        a.stats = int(bool(stats))
+        a.stream = _stream_ptr(stream)
+        h = C.c_void_p()
+        _check(lib().ppr_run(self.ctx.h, self.h, C.byref(a), C.byref(h)))
+        r = Result(self, h, a.src_end - a.src_begin, topk)
+        if wait:
+            r.wait()
+        return r
+
+
+class Result:
+    def __init__(self, graph: Graph, h, S: int, topk: int):
+        self.graph = graph
+        self.h = h
+        self.S = S
+        self.topk_k = topk
+
+    def wait(self, timeout_ms: int = -1):
+        _check(lib().ppr_wait(self.h, timeout_ms))
+        return self
+
+    def info(self) -> ResultInfo:
+        ri = ResultInfo()
+        _check(lib().ppr_result_get_info(self.h, C.byref(ri)))
+        return ri
+
+    def nnz(self) -> int:
+        n = C.c_int64()
+        _check(lib().ppr_sparse_rows(self.h, None, None, None, 0, C.byref(n), 0))
+        return n.value
+
+    def sparse_rows(self):
+        """(row_ptr int64[S+1], col int32[nnz], cnt uint32[nnz]) as numpy arrays."""
+        row_ptr = np.zeros(self.S + 1, dtype=np.int64)
+        n = C.c_int64()
+        _check(lib().ppr_sparse_rows(self.h, row_ptr.ctypes.data, None, None, 0, C.byref(n), 0))
+        col = np.zeros(max(n.value, 1), dtype=np.int32)
+        cnt = np.zeros(max(n.value, 1), dtype=np.uint32)
+        _check(lib().ppr_sparse_rows(self.h, row_ptr.ctypes.data, col.ctypes.data, cnt.ctypes.data, len(col),
+                                     C.byref(n), 0))
+        return row_ptr, col[: n.value], cnt[: n.value]
+
+    def sparse_rows_into(self, row_ptr, col, cnt) -> int:
+        """Fills caller buffers (numpy host arrays or torch device tensors)."""
+        rp, dev = _ptr(row_ptr)
+        cp, _ = _ptr(col)
+        kp, _ = _ptr(cnt)
+        n = C.c_int64()
+        _check(lib().ppr_sparse_rows(self.h, rp, cp, kp, int(col.shape[0]), C.byref(n), PPR_PTRS_DEVICE if dev else 0))
+        return n.value
+
+    def topk(self, k: int | None = None):
+        k = self.topk_k if k is None else k
+        idx = np.zeros((self.S, k), dtype=np.int32)
+        cnt = np.zeros((self.S, k), dtype=np.uint32)
+        _check(lib().ppr_topk(self.h, k, idx.ctypes.data, cnt.ctypes.data, 0))
+        return idx, cnt
+
+    def topk_into(self, k: int, idx, cnt):
+        ip, dev = _ptr(idx)
+        cp, _ = _ptr(cnt)
+        _check(lib().ppr_topk(self.h, k, ip, cp, PPR_PTRS_DEVICE if dev else 0))
+
+    def dense(self):
+        n = self.graph.info().n
+        out = np.zeros((self.S, n), dtype=np.uint32)
+        _check(lib().ppr_dense(self.h, out.ctypes.data, 0))
+        return out
+
+    def free(self):
+        if self.h:
+            lib().ppr_free_result(self.h)
+            self.h = None
+
+    def __del__(self):
+        try:
+            self.free()
+        except Exception:
+            pass

@@ -1,0 +1,264 @@
+"""GPU path (through the C ABI) against the CPU oracle, element by element.
+
+Counts are integers: every comparison is bit-exact.  Cases span several
+chunks and warps with ragged tails (R not a multiple of 32, source counts not
+a multiple of the chunk), dangling nodes in both modes, self-loops and
+parallel edges, rows long enough for the cooperative search, both kernels,
+tags and seeds, sub-ranges of sources, batch splits and the error paths.
+"""
+import numpy as np
+import pytest
+
+from paper_1903_11749_gb300 import inputs as I
+
+pytestmark = pytest.mark.gpu
+
+
+@pytest.fixture(scope="module")
+def ppr():
+    from paper_1903_11749_gb300 import build as B
+    B.build()
+    from paper_1903_11749_gb300 import ppr as P
+    return P
+
+
+@pytest.fixture(scope="module")
+def ctx(ppr):
+    return ppr.Context(0)
+
+
+def oracle_rows(oracle, g, alpha, R, seed, s_begin=0, s_end=None, tag=0, dangling=0, segments=False, topk=0,
+                og=None):
+    og = og or oracle.prepare(g.n, g.row_ptr, g.col, g.w)
+    ends, steps = oracle.walks(og, alpha, R, seed, s_begin, s_end, tag, dangling, segments)
+    rp, col, cnt = oracle.rows(ends, g.n)
+    out = {"rows": (rp, col, cnt), "steps": steps, "ends": ends}
+    if topk:
+        out["topk"] = oracle.topk(rp, col, cnt, topk)
+    return out
+
+
+def assert_same(res, ref, topk=0):
+    rp, col, cnt = res.sparse_rows()
+    orp, ocol, ocnt = ref["rows"]
+    assert np.array_equal(rp, orp)
+    assert np.array_equal(col, ocol)
+    assert np.array_equal(cnt, ocnt)
+    if topk:
+        idx, tc = res.topk(topk)
+        oidx, otc = ref["topk"]
+        assert np.array_equal(idx, oidx)
+        assert np.array_equal(tc, otc)
+    assert res.info().steps == ref["steps"]
+
+
+def test_er1k_dense_matches_oracle(ppr, ctx, oracle):
+    """The 1000-node ER workload (alpha 0.15, R 1000, seed 1), all n*n counts."""
+    g = I.er_graph(1000, 10_000, 1, 10, seed=12345)
+    G = ctx.load_graph(g.n, g.row_ptr, g.col, g.w)
+    ref = oracle_rows(oracle, g, 0.15, 1000, 1, topk=32)
+    for kernel in (ppr.KERNEL_PERSISTENT, ppr.KERNEL_PLAIN):
+        res = G.run(alpha=0.15, R=1000, seed=1, topk=32, kernel=kernel)
+        assert_same(res, ref, topk=32)
+        D = res.dense()
+        assert np.array_equal(D, oracle.dense(ref["ends"], g.n))
+        assert (D.sum(axis=1) == 1000).all()
+
+
+@pytest.mark.parametrize("R", [1, 7, 31, 33, 100, 257])
+@pytest.mark.parametrize("kernel", [0, 1])
+def test_small_graphs_ragged(ppr, ctx, oracle, R, kernel):
+    g = I.random_small_graph(97, 400, seed=R, wmax=9, dangling=5)
+    G = ctx.load_graph(g.n, g.row_ptr, g.col, g.w)
+    for dangling in (0, 1):
+        ref = oracle_rows(oracle, g, 0.3, R, seed=5 + R, dangling=dangling, topk=min(R, 5))
+        res = G.run(alpha=0.3, R=R, seed=5 + R, dangling=dangling, topk=min(R, 5), kernel=kernel)
+        assert_same(res, ref, topk=min(R, 5))
+
+
+def test_self_loops_parallel_edges_and_skew(ppr, ctx, oracle):
+    g = I.from_edges(6, [(0, 1, 1000), (0, 2, 1), (0, 1, 3), (1, 1, 2), (1, 3, 5), (2, 0, 1), (2, 4, 7), (3, 0, 1),
+                         (3, 5, 1), (4, 2, 2)])
+    G = ctx.load_graph(g.n, g.row_ptr, g.col, g.w)
+    for kernel in (0, 1):
+        ref = oracle_rows(oracle, g, 0.15, 4000, seed=9, topk=6)
+        assert_same(G.run(alpha=0.15, R=4000, seed=9, topk=6, kernel=kernel), ref, topk=6)
+
+
+def test_tags_seeds_and_subranges(ppr, ctx, oracle):
+    g = I.er_graph(500, 4000, 1, 10, seed=3)
+    G = ctx.load_graph(g.n, g.row_ptr, g.col, g.w)
+    og = oracle.prepare(g.n, g.row_ptr, g.col, g.w)
+    for seed, tag, a, b in [(1, 0, 0, 500), (2**40 + 17, 3, 17, 389), (123456789, 0xFFFFFFFF, 499, 500)]:
+        ref = oracle_rows(oracle, g, 0.2, 45, seed, a, b, tag, topk=10, og=og)
+        for kernel in (0, 1):
+            res = G.run(alpha=0.2, R=45, seed=seed, src_begin=a, src_end=b, tag=tag, topk=10, kernel=kernel)
+            assert_same(res, ref, topk=10)
+
+
+def test_batches_and_chunking_do_not_change_results(ppr, ctx, oracle):
+    g = I.er_graph(700, 6000, 1, 10, seed=4)
+    G = ctx.load_graph(g.n, g.row_ptr, g.col, g.w)
+    ref = oracle_rows(oracle, g, 0.15, 60, 7, topk=4)
+    for kw in (dict(kernel=1, max_batch_sources=33), dict(chunk_sources=1), dict(chunk_sources=13, warps_per_block=2),
+               dict(chunk_sources=64, warps_per_block=1), dict(max_batch_sources=250)):
+        assert_same(G.run(alpha=0.15, R=60, seed=7, topk=4, **kw), ref, topk=4)
+
+
+def _hub_graph(deg_hub=20000, n=30000, seed=11):
+    rng = np.random.Generator(np.random.PCG64(seed))
+    edges = [(0, int(t), int(w)) for t, w in zip(rng.integers(1, n, deg_hub), rng.integers(1, 1000, deg_hub))]
+    # mid-size rows (5000 edges) and small rows pointing back at the hub
+    for h in (1, 2):
+        edges += [(h, int(t), int(w)) for t, w in zip(rng.integers(0, n, 5000), rng.integers(1, 50, 5000))]
+    for u in range(3, n):
+        edges.append((u, 0, int(rng.integers(1, 10))))
+        edges.append((u, int(rng.integers(0, n)), int(rng.integers(1, 10))))
+    return I.from_edges(n, edges)
+
+
+def test_large_rows_cooperative_search(ppr, ctx, oracle):
+    """Rows above the cooperative threshold (default 4096, and 1 to force every
+    row through it) give the same edge as the bisection."""
+    g = _hub_graph()
+    G = ctx.load_graph(g.n, g.row_ptr, g.col, g.w)
+    ref = oracle_rows(oracle, g, 0.15, 50, 3, 0, 2000, topk=8)
+    for large in (0, 1, 32, 100000):
+        assert_same(G.run(alpha=0.15, R=50, seed=3, src_end=2000, topk=8, large_degree=large), ref, topk=8)
+
+
+def test_segment_mode_matches_segment_oracle(ppr, ctx, oracle):
+    g = I.random_small_graph(400, 1100, seed=21, wmax=30, dangling=20)
+    G = ctx.load_graph(g.n, g.row_ptr, g.col, g.w)
+    og = oracle.prepare(g.n, g.row_ptr, g.col, g.w)
+    for alpha, dangling in ((0.15, 0), (0.5, 1)):
+        ref = oracle_rows(oracle, g, alpha, 77, 2, dangling=dangling, segments=True, topk=5, og=og)
+        assert (np.diff(og.seg_off) > 0).sum() > 50
+        for kernel in (0, 1):
+            res = G.run(alpha=alpha, R=77, seed=2, dangling=dangling, segments=True, topk=5, kernel=kernel)
+            assert_same(res, ref, topk=5)
+        info = G.info()
+        assert info.segment_nodes == int((np.diff(og.seg_off) > 0).sum())
+        assert info.segment_entries == int(og.seg_off[-1])
+
+
+def test_batched_instances_equal_each_instance_alone(ppr, ctx, oracle):
+    inst = I.chung_lu_instances(count=12, nmin=20, nmax=400, seed=5)
+    G = ctx.load_graph_batch(inst.node_off, inst.row_ptr, inst.col, inst.w)
+    res = G.run(alpha=0.15, R=40, seed=1, topk=4)
+    rp, col, cnt = res.sparse_rows()
+    idx, tc = res.topk()
+    for gi in range(inst.count):
+        sub = inst.instance(gi)
+        ref = oracle_rows(oracle, sub, 0.15, 40, 1, tag=gi, topk=4)
+        a, b = int(inst.node_off[gi]), int(inst.node_off[gi + 1])
+        orp, ocol, ocnt = ref["rows"]
+        assert np.array_equal(rp[a: b + 1] - rp[a], orp)
+        assert np.array_equal(col[rp[a]: rp[b]], ocol)
+        assert np.array_equal(cnt[rp[a]: rp[b]], ocnt)
+        assert np.array_equal(idx[a:b], ref["topk"][0])
+        assert np.array_equal(tc[a:b], ref["topk"][1])
+
+
+def test_device_inputs_and_outputs(ppr, ctx, oracle):
+    import torch
+    g = I.er_graph(400, 3000, 1, 10, seed=8)
+    dev = torch.device("cuda:0")
+    G = ctx.load_graph(g.n, torch.from_numpy(g.row_ptr).to(dev), torch.from_numpy(g.col).to(dev),
+                       torch.from_numpy(g.w.view(np.int32)).to(dev))
+    res = G.run(alpha=0.15, R=32, seed=4, topk=3)
+    ref = oracle_rows(oracle, g, 0.15, 32, 4, topk=3)
+    nnz = res.nnz()
+    rp = torch.zeros(g.n + 1, dtype=torch.int64, device=dev)
+    col = torch.zeros(nnz, dtype=torch.int32, device=dev)
+    cnt = torch.zeros(nnz, dtype=torch.int32, device=dev)
+    assert res.sparse_rows_into(rp, col, cnt) == nnz
+    orp, ocol, ocnt = ref["rows"]
+    assert np.array_equal(rp.cpu().numpy(), orp)
+    assert np.array_equal(col.cpu().numpy(), ocol)
+    assert np.array_equal(cnt.cpu().numpy().view(np.uint32), ocnt)
+    idx = torch.zeros((g.n, 2), dtype=torch.int32, device=dev)
+    tc = torch.zeros((g.n, 2), dtype=torch.int32, device=dev)
+    res.topk_into(2, idx, tc)
+    assert np.array_equal(idx.cpu().numpy(), ref["topk"][0][:, :2])
+
+
+def test_dangling_sources_and_single_node(ppr, ctx, oracle):
+    g = I.from_edges(4, [(0, 1, 1), (1, 2, 1), (2, 0, 1)])
+    G = ctx.load_graph(g.n, g.row_ptr, g.col, g.w)
+    for mode in (0, 1):
+        res = G.run(alpha=0.15, R=100, seed=1, src_begin=3, src_end=4, dangling=mode, topk=2)
+        rp, col, cnt = res.sparse_rows()
+        assert col.tolist() == [3] and cnt.tolist() == [100]
+    g1 = I.from_edges(1, [])
+    G1 = ctx.load_graph(1, g1.row_ptr, np.zeros(0, np.int32), np.zeros(0, np.uint32))
+    for mode in (0, 1):
+        rp, col, cnt = G1.run(alpha=0.5, R=10, seed=1, dangling=mode).sparse_rows()
+        assert col.tolist() == [0] and cnt.tolist() == [10]
+
+
+def test_wide_rows(ppr, ctx, oracle):
+    """Row totals above 2^32 switch to the 64-bit prefix layout."""
+    big = 2**32 - 5
+    g = I.from_edges(5, [(0, 1, big), (0, 2, big), (0, 3, 7), (1, 0, 1), (2, 4, big), (2, 0, 3), (3, 0, 1),
+                         (4, 4, 1), (4, 0, big)])
+    G = ctx.load_graph(g.n, g.row_ptr, g.col, g.w)
+    assert G.info().wide == 1
+    ref = oracle_rows(oracle, g, 0.25, 500, 3, topk=3)
+    for kernel in (0, 1):
+        assert_same(G.run(alpha=0.25, R=500, seed=3, topk=3, kernel=kernel), ref, topk=3)
+
+
+def test_invalid_inputs_are_rejected(ppr, ctx):
+    E = ppr.PPRError
+    g = I.er_graph(50, 200, seed=1)
+    bad_w = g.w.copy()
+    bad_w[7] = 0
+    with pytest.raises(E) as ei:
+        ctx.load_graph(g.n, g.row_ptr, g.col, bad_w)
+    assert ei.value.code == ppr.PPR_EINVAL
+    bad_c = g.col.copy()
+    bad_c[3] = 50
+    with pytest.raises(E):
+        ctx.load_graph(g.n, g.row_ptr, bad_c, g.w)
+    bad_rp = g.row_ptr.copy()
+    bad_rp[10], bad_rp[11] = bad_rp[11], bad_rp[10] - 1
+    with pytest.raises(E):
+        ctx.load_graph(g.n, bad_rp, g.col, g.w)
+    G = ctx.load_graph(g.n, g.row_ptr, g.col, g.w)
+    for kw, code in ((dict(alpha=0.0), ppr.PPR_EINVAL), (dict(alpha=1.0), ppr.PPR_EINVAL),
+                     (dict(alpha=2.0**-40), ppr.PPR_EINVAL), (dict(R=0), ppr.PPR_EINVAL),
+                     (dict(R=5000), ppr.PPR_ERANGE), (dict(src_begin=10, src_end=10), ppr.PPR_EINVAL),
+                     (dict(src_end=51), ppr.PPR_EINVAL), (dict(topk=101), ppr.PPR_EINVAL),
+                     (dict(dangling=2), ppr.PPR_EINVAL)):
+        with pytest.raises(E) as ei:
+            G.run(**kw)
+        assert ei.value.code == code, kw
+    res = G.run(R=10, topk=3)
+    with pytest.raises(E):
+        res.topk(4)
+
+
+@pytest.mark.slow
+def test_rmat20_full_size_sampled(ppr, ctx, oracle):
+    """The R-MAT scale-20 workload (alpha 0.2, R 100, top-32), every source on
+    the GPU in the benchmark's launch configuration; 400 sampled sources
+    recomputed by the oracle and compared exactly; every row sums to R."""
+    g = I.workload_graph("rmat20")
+    G = ctx.load_graph(g.n, g.row_ptr, g.col, g.w)
+    res = G.run(alpha=0.2, R=100, seed=1, topk=32)
+    rp, col, cnt = res.sparse_rows()
+    idx, tc = res.topk()
+    rowsum = np.add.reduceat(cnt.astype(np.int64), rp[:-1]) if len(cnt) else np.zeros(0)
+    assert (np.diff(rp) >= 1).all() and (rowsum == 100).all()
+    og = oracle.prepare(g.n, g.row_ptr, g.col, g.w)
+    rng = np.random.Generator(np.random.PCG64(0))
+    sample = np.unique(np.concatenate([rng.integers(0, g.n, 380), np.argsort(-g.degrees())[:10],
+                                       np.flatnonzero(g.degrees() == 0)[:10]]))
+    for s in sample:
+        ref = oracle_rows(oracle, g, 0.2, 100, 1, int(s), int(s) + 1, topk=32, og=og)
+        orp, ocol, ocnt = ref["rows"]
+        assert np.array_equal(col[rp[s]: rp[s + 1]], ocol)
+        assert np.array_equal(cnt[rp[s]: rp[s + 1]], ocnt)
+        assert np.array_equal(idx[s], ref["topk"][0][0])
+        assert np.array_equal(tc[s], ref["topk"][1][0])
