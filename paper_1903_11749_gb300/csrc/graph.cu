@@ -124,7 +124,8 @@ __global__ void k_rows_pass2(int64_t n, const int64_t *row_ptr, const int32_t *c
         if (lane == 0) {
             NodeRec r;
             r.word0 = pack_word0((uint64_t)a, (uint32_t)(b - a), false);
-            r.total = W[u];
+            // a single out-edge needs no draw-to-edge search: keep its target inline
+            r.total = (b - a == 1) ? (uint64_t)(uint32_t)(col[a] + base_id) : W[u];
             node[u] = r;
         }
     }
@@ -251,7 +252,13 @@ struct RowView {
     E edges;
     __device__ __forceinline__ uint32_t deg(uint32_t u) const { return (uint32_t)(node[u].word0 >> 40) & kCountMask; }
     __device__ __forceinline__ uint64_t begin(uint32_t u) const { return node[u].word0 & kBeginMask; }
-    __device__ __forceinline__ uint64_t total(uint32_t u) const { return node[u].total; }
+    // row total = last inclusive prefix (the node record holds the target of a
+    // single-edge row instead of its total)
+    __device__ __forceinline__ uint64_t total(uint32_t u) const
+    {
+        uint32_t d = deg(u);
+        return d ? E::key(edges.load(begin(u) + d - 1)) : 0ull;
+    }
     // weight and target of the i-th edge of u
     __device__ __forceinline__ void edge(uint32_t u, uint32_t i, uint64_t &wt, uint32_t &tgt) const
     {
@@ -408,7 +415,7 @@ __global__ void k_seg_write(RowView<E> G, int64_t n, uint32_t T, const uint64_t 
         uint64_t o = offs[v];
         uint32_t c = (uint32_t)(offs[v + 1] - o);
         if (c == 0) {
-            if (lane == 0) seg_node[v] = G.node[v];
+            if (lane == 0) seg_node[v] = G.node[v];  // not eligible: plain record
             continue;
         }
         uint32_t c2 = seg_build_node(G, (uint32_t)v, T, sc);

@@ -4,6 +4,7 @@
 //   NodeRec (16 B, one aligned half-sector per node)
 //     word0 = begin (bits 0..39) | count (bits 40..62) | segment flag (bit 63)
 //     word1 = W_u, the row's total weight (Sec. 2.1 routing denominator), or
+//             the target id when the row has exactly one edge (no search), or
 //             Q_v, the total fixed-point mass of a segment table (Algorithm 4)
 //   plain rows:  begin/count index the edge-record array
 //   segment rows: begin/count index the segment-entry array

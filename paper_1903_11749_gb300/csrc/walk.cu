@@ -72,7 +72,7 @@ __device__ __forceinline__ bool walk_step(const KParams &p, const E &edges, bool
     const bool segf = SEG && (w0 >> 63);
     const uint64_t r64 = (uint64_t)x.x | ((uint64_t)x.y << 32);
     uint64_t xr = 0;
-    if (act && cnt > 0) {
+    if (act && (cnt > 1 || segf)) {
         if (segf || total >= (1ull << 32)) xr = mulhi64(r64, total);
         else xr = mulhi64_by32(x.x, x.y, (uint32_t)total);
     }
@@ -112,6 +112,8 @@ __device__ __forceinline__ bool walk_step(const KParams &p, const E &edges, bool
             return true;
         }
         next = src;
+    } else if (cnt == 1) {
+        next = (uint32_t)total;  // single out-edge: target kept in the node record
     } else if (!big) {
         next = E::target(STATS ? search_serial_tally(edges, beg, cnt, xr, tl.sectors) : search_serial(edges, beg, cnt, xr));
     }
@@ -187,15 +189,56 @@ __global__ void __launch_bounds__(128) k_aggregate(KParams p)
 }
 
 // ------------------------------------------------------- persistent (K5) ----
+// Every lane runs its own walk as a small state machine that issues at most
+// one 16-byte load per loop iteration:
+//   NODE   load the node record of the tail u (the step's Philox draw is
+//          computed while the load is in flight);
+//   SEARCH one bisection probe of the row prefix (or of the segment table);
+//   FINAL  load the chosen record when the last probe did not bring it.
+// Lanes in different phases share each load instruction, so a lane deep in a
+// long bisection does not hold back the others (a lockstep step would wait
+// for the longest search of the warp every step).  Rows longer than
+// p.large are searched by the whole warp (search_warp) at the start of an
+// iteration.  Lanes that finish a walk are refilled from the warp's current
+// chunk; a chunk's R-endpoint blocks are aggregated in shared memory as soon
+// as its last walk ends, while the next chunk's walks are already running.
 struct SlotState {
     uint32_t base, nsrc, total, issued, done, ctr_base, tag, live;
 };
 
+enum : uint32_t { kIdle = 0, kNode = 1, kSearch = 2, kFinal = 3, kCoop = 4, kResolved = 5 };
+
+template <class E>
+__device__ __forceinline__ const uint4 *block_of(const void *base, uint64_t idx)
+{
+    // 16-byte aligned block holding record idx
+    return reinterpret_cast<const uint4 *>(base) + ((idx * sizeof(typename E::Rec)) >> 4);
+}
+
+template <class E>
+__device__ __forceinline__ void rec_in_block(uint4 v, uint64_t idx, uint64_t &key, uint32_t &tgt, uint32_t &aux)
+{
+    if constexpr (sizeof(typename E::Rec) == 8) {
+        const bool hi = (idx & 1) != 0;
+        key = hi ? v.z : v.x;
+        tgt = hi ? v.w : v.y;
+        aux = 0;
+    } else {
+        key = (uint64_t)v.x | ((uint64_t)v.y << 32);
+        tgt = v.z;
+        aux = v.w;
+    }
+}
+
+#ifndef PPR_WALK_MINB
+#define PPR_WALK_MINB 1  // minimum resident 256-thread blocks per SM requested from ptxas
+#endif
+
 template <class E, bool SEG, bool STATS>
-__global__ void __launch_bounds__(256) k_walk_persistent(KParams p)
+__global__ void __launch_bounds__(256, PPR_WALK_MINB) k_walk_persistent(KParams p)
 {
     extern __shared__ __align__(16) unsigned char smem_raw[];
-    const uint32_t lane = threadIdx.x & 31, wid = threadIdx.x >> 5, nw = blockDim.x >> 5;
+    const uint32_t lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
     // per-warp shared memory: keys[P2] u64 | sortbuf[P2] u32 | slot ends [2][slot_cap] u32 | SlotState[2]
     const size_t per_warp = (size_t)p.P2 * 12 + (size_t)p.slot_cap * 8 + sizeof(SlotState) * 2;
     const size_t per_warp_al = (per_warp + 15) & ~(size_t)15;
@@ -204,20 +247,23 @@ __global__ void __launch_bounds__(256) k_walk_persistent(KParams p)
     uint32_t *sortbuf = reinterpret_cast<uint32_t *>(mine + (size_t)p.P2 * 8);
     uint32_t *slot_ends = sortbuf + p.P2;
     SlotState *ss = reinterpret_cast<SlotState *>(slot_ends + 2 * (size_t)p.slot_cap);
-    (void)nw;
     const E edges = make_edges<E>(p.edges);
 
     if (lane < 2) ss[lane].live = 0;
     __syncwarp();
     int cur = -1;
     bool queue_empty = false;
-    bool active = false;
-    uint32_t slot = 0, widx = 0, src = 0, sctr = 0, j = 0, k = 0, u = 0, tag = 0;
+    uint32_t phase = kIdle;
+    uint32_t slot = 0, widx = 0, src = 0, j = 0, k = 0, u = 0;
+    uint32_t n = 0, x2 = 0;
+    uint64_t lo = 0, x = 0;
+    bool segw = false;
     Tally tl;
+    uint64_t last_sec = ~0ull;  // statistics only
 
     for (;;) {
         // ---- refill idle lanes from the issuing slot, opening chunks as needed
-        uint32_t idle = __ballot_sync(0xffffffffu, !active);
+        uint32_t idle = __ballot_sync(0xffffffffu, phase == kIdle);
         while (idle) {
             if (cur < 0 || ss[cur].issued == ss[cur].total) {
                 if (queue_empty) break;
@@ -254,61 +300,210 @@ __global__ void __launch_bounds__(256) k_walk_persistent(KParams p)
                 __syncwarp();
                 cur = fresh;
             }
-            const SlotState s = ss[cur];
-            const uint32_t avail = s.total - s.issued;
-            const uint32_t nidle = __popc(idle);
-            const uint32_t take = min(avail, nidle);
+            const uint32_t issued = ss[cur].issued, total = ss[cur].total, base = ss[cur].base;
+            const uint32_t take = min(total - issued, (uint32_t)__popc(idle));
             const uint32_t rank = __popc(idle & ((1u << lane) - 1));
             if (((idle >> lane) & 1) && rank < take) {
-                widx = s.issued + rank;
+                widx = issued + rank;
                 slot = (uint32_t)cur;
                 const uint32_t i = widx / p.R;
                 j = widx - i * p.R;
-                src = s.base + i;
-                sctr = src - s.ctr_base;
-                tag = s.tag;
+                src = base + i;
                 k = 0;
                 u = src;
-                active = true;
+                phase = kNode;
             }
             __syncwarp();
-            if (lane == 0) ss[cur].issued = s.issued + take;
+            if (lane == 0) ss[cur].issued = issued + take;
             __syncwarp();
-            idle = __ballot_sync(0xffffffffu, !active);
+            idle = __ballot_sync(0xffffffffu, phase == kIdle);
         }
-        const uint32_t act_mask = __ballot_sync(0xffffffffu, active);
-        if (act_mask == 0 && queue_empty && !ss[0].live && !ss[1].live) break;
+        const uint32_t act_mask = __ballot_sync(0xffffffffu, phase != kIdle);
+        if (act_mask == 0) {
+            if (queue_empty && !ss[0].live && !ss[1].live) break;
+        }
 
-        // ---- one step of every active walk
-        uint32_t end = 0;
-        bool fin = false;
-        if (act_mask) fin = walk_step<E, SEG, true, STATS>(p, edges, active, src, sctr, j, tag, k, u, end, tl);
+        // ---- rows above the cooperative threshold: searched by the whole warp
+        if (!STATS) {
+            uint32_t cm = __ballot_sync(0xffffffffu, phase == kCoop);
+            while (cm) {
+                const uint32_t L = __ffs(cm) - 1;
+                cm &= cm - 1;
+                const uint64_t l0 = __shfl_sync(0xffffffffu, lo, L);
+                const uint32_t n0 = __shfl_sync(0xffffffffu, n, L);
+                const uint64_t xx = __shfl_sync(0xffffffffu, x, L);
+                auto rec = search_warp(edges, l0, n0, xx);
+                if (lane == L) {
+                    u = E::target(rec);  // the chosen edge's target; the step completes below
+                    phase = kResolved;
+                }
+            }
+        }
+
+        // ---- one load per active lane
+        uint64_t aidx = 0;
+        if (phase == kNode) {
+            aidx = u;
+        } else if (phase == kSearch) {
+            aidx = lo + (n >> 1) - 1;
+        } else if (phase == kFinal) {
+            aidx = lo;
+        }
+        const bool loads = phase == kNode || phase == kSearch || phase == kFinal;
+        uint4 v = make_uint4(0, 0, 0, 0);
+        if (loads) {
+            const uint4 *addr;
+            if (phase == kNode) addr = reinterpret_cast<const uint4 *>(p.node) + aidx;
+            else if (SEG && segw) addr = reinterpret_cast<const uint4 *>(p.seg) + aidx;
+            else addr = block_of<E>(p.edges, aidx);
+            v = __ldg(addr);
+        }
+
+        // Philox of the step a lane starts, overlapping the node-record load
+        uint4 rnd = make_uint4(0, 0, 0, 0);
+        if (phase == kNode) rnd = philox4x32_10(make_uint4(src - ss[slot].ctr_base, j, k, ss[slot].tag), p.k0, p.k1);
+
+        bool step_done = false, fin = false;
+        uint32_t next = 0, end = 0;
+        if (phase == kNode) {
+            const uint64_t w0 = (uint64_t)v.x | ((uint64_t)v.y << 32);
+            const uint64_t total = (uint64_t)v.z | ((uint64_t)v.w << 32);
+            const uint32_t cnt = (uint32_t)(w0 >> 40) & kCountMask;
+            const bool segf = SEG && (w0 >> 63);
+            x2 = rnd.z;
+            if (STATS) {
+                ++tl.sectors;
+                last_sec = ~0ull;
+            }
+            if (cnt == 0) {
+                if (p.dangling == 1) {
+                    fin = true;
+                    end = u;
+                } else {
+                    next = src;
+                    step_done = true;
+                }
+            } else if (cnt == 1 && !segf) {
+                next = (uint32_t)total;
+                step_done = true;
+            } else {
+                const uint64_t r64 = (uint64_t)rnd.x | ((uint64_t)rnd.y << 32);
+                x = (segf || total >= (1ull << 32)) ? mulhi64(r64, total) : mulhi64_by32(rnd.x, rnd.y, (uint32_t)total);
+                lo = w0 & kBeginMask;
+                n = cnt;
+                segw = segf;
+                phase = (!STATS && !segf && cnt > p.large) ? kCoop : (n > 1 ? kSearch : kFinal);
+            }
+        } else if (phase == kSearch) {
+            uint64_t key;
+            uint32_t tgt, aux;
+            if (SEG && segw) rec_in_block<SegTable>(v, aidx, key, tgt, aux);
+            else rec_in_block<E>(v, aidx, key, tgt, aux);
+            if (STATS) {
+                const uint64_t sec = (SEG && segw) ? ((reinterpret_cast<uint64_t>(p.seg) + aidx * 16) >> 5)
+                                                   : ((reinterpret_cast<uint64_t>(p.edges) + aidx * sizeof(typename E::Rec)) >> 5);
+                if (sec != last_sec) ++tl.sectors, last_sec = sec;
+            }
+            const uint32_t half = n >> 1;
+            if (key <= x) {
+                lo += half;
+                n -= half;
+            } else {
+                n = half;
+            }
+            if (n == 1) {
+                // the answer is lo; the 16-byte block just loaded may already hold it
+                const bool in_block = (SEG && segw) ? (lo == aidx)
+                                                    : (sizeof(typename E::Rec) == 8 ? ((lo >> 1) == (aidx >> 1)) : (lo == aidx));
+                if (in_block) {  // (same sector as the probe: no new sector for the statistics)
+                    uint64_t k2;
+                    if (SEG && segw) rec_in_block<SegTable>(v, lo, k2, tgt, aux);
+                    else rec_in_block<E>(v, lo, k2, tgt, aux);
+                    if (SEG && segw) {
+                        if ((aux >> 8) == 0) {
+                            fin = true;
+                            end = tgt;
+                            ++tl.steps;
+                        } else {
+                            u = tgt;
+                            k += aux & 0xffu;
+                            ++tl.steps;
+                            phase = kNode;
+                        }
+                    } else {
+                        next = tgt;
+                        step_done = true;
+                    }
+                } else {
+                    phase = kFinal;
+                }
+            }
+        } else if (phase == kFinal) {
+            uint64_t key;
+            uint32_t tgt, aux;
+            if (SEG && segw) rec_in_block<SegTable>(v, aidx, key, tgt, aux);
+            else rec_in_block<E>(v, aidx, key, tgt, aux);
+            if (STATS) {
+                const uint64_t sec = (SEG && segw) ? ((reinterpret_cast<uint64_t>(p.seg) + aidx * 16) >> 5)
+                                                   : ((reinterpret_cast<uint64_t>(p.edges) + aidx * sizeof(typename E::Rec)) >> 5);
+                if (sec != last_sec) ++tl.sectors, last_sec = sec;
+            }
+            if (SEG && segw) {
+                ++tl.steps;
+                if ((aux >> 8) == 0) {
+                    fin = true;
+                    end = tgt;
+                } else {
+                    u = tgt;
+                    k += aux & 0xffu;
+                    phase = kNode;
+                }
+            } else {
+                next = tgt;
+                step_done = true;
+            }
+        } else if (phase == kResolved) {
+            next = u;  // chosen by the cooperative search
+            step_done = true;
+        }
+        if (step_done) {
+            ++tl.steps;
+            ++k;
+            u = next;
+            if (x2 < p.T) {
+                fin = true;
+                end = u;
+            } else {
+                phase = kNode;
+            }
+        }
         if (fin) {
             slot_ends[(size_t)slot * p.slot_cap + widx] = end - ss[slot].ctr_base;
-            active = false;
+            phase = kIdle;
         }
         const uint32_t f0 = __ballot_sync(0xffffffffu, fin && slot == 0);
         const uint32_t f1 = __ballot_sync(0xffffffffu, fin && slot == 1);
-        __syncwarp();
-        if (lane == 0) {
-            ss[0].done += __popc(f0);
-            ss[1].done += __popc(f1);
-        }
-        __syncwarp();
-
-        // ---- aggregate finished chunks in shared memory
+        if ((f0 | f1) != 0) {
+            __syncwarp();
+            if (lane == 0) {
+                ss[0].done += __popc(f0);
+                ss[1].done += __popc(f1);
+            }
+            __syncwarp();
+            // ---- aggregate finished chunks in shared memory
 #pragma unroll
-        for (int sI = 0; sI < 2; ++sI) {
-            const SlotState s = ss[sI];
-            if (s.live && s.done == s.total && s.issued == s.total) {
-                for (uint32_t i = 0; i < s.nsrc; ++i) {
-                    const uint64_t row = (uint64_t)p.out_row0 + (uint64_t)((int64_t)(s.base + i) - p.s_begin);
-                    aggregate_source(slot_ends + (size_t)sI * p.slot_cap + (size_t)i * p.R, p.R, sortbuf, keys,
-                                     p.out, row);
+            for (int sI = 0; sI < 2; ++sI) {
+                const SlotState s = ss[sI];
+                if (s.live && s.done == s.total && s.issued == s.total) {
+                    for (uint32_t i = 0; i < s.nsrc; ++i) {
+                        const uint64_t row = (uint64_t)p.out_row0 + (uint64_t)((int64_t)(s.base + i) - p.s_begin);
+                        aggregate_source(slot_ends + (size_t)sI * p.slot_cap + (size_t)i * p.R, p.R, sortbuf, keys,
+                                         p.out, row);
+                    }
+                    __syncwarp();
+                    if (lane == 0) ss[sI].live = 0;
+                    __syncwarp();
                 }
-                __syncwarp();
-                if (lane == 0) ss[sI].live = 0;
-                __syncwarp();
             }
         }
     }
