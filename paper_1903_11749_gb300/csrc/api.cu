@@ -372,12 +372,14 @@ int ppr_run(ppr_ctx *ctx, const ppr_graph *g, const ppr_run_args *a, ppr_result 
     plan.chunk_sources = a->chunk_sources;
     plan.stats = a->stats != 0;
 
-    // Batch size: the plain kernel keeps every endpoint in HBM (4 B per walk);
-    // bound that scratch to a quarter of the free memory.
+    // Batch size (the paper's per-pipeline walk budget, gamma <= alpha*M/(n*c),
+    // Sec. 4.3, becomes a source batch sized to device memory): every walk of
+    // a batch keeps its 4-byte endpoint in HBM until the batch is aggregated;
+    // that scratch is bounded to a quarter of the free memory.
     int64_t batch = r->S;
     if (a->max_batch_sources > 0) batch = std::min<int64_t>(batch, a->max_batch_sources);
     uint32_t *ends = nullptr;
-    if (a->kernel == PPR_KERNEL_PLAIN) {
+    {
         size_t free_b = 0, total_b = 0;
         cudaMemGetInfo(&free_b, &total_b);
         int64_t fit = (int64_t)(free_b / 4 / ((size_t)a->R * sizeof(uint32_t)));

@@ -36,10 +36,9 @@ struct KParams {
     const int4 *chunks;       // batched graphs: {base, nsrc, instance, 0}; else null
     const int64_t *inst_off;  // batched graphs: node_off
     AggOut out;
-    uint32_t *ends;           // plain kernel: S * R endpoints
+    uint32_t *ends;           // S * R endpoints (instance-local ids)
     unsigned long long *queue;
     unsigned long long *steps;    // [0] draws consumed, [2] algorithmic sectors (statistics launch)
-    uint32_t slot_cap;        // walks per chunk slot (CS * R)
     uint32_t P2;              // next_pow2(R)
 };
 
@@ -189,46 +188,20 @@ __global__ void __launch_bounds__(128) k_aggregate(KParams p)
 }
 
 // ------------------------------------------------------- persistent (K5) ----
-// Every lane runs its own walk as a small state machine that issues at most
-// one 16-byte load per loop iteration:
-//   NODE   load the node record of the tail u (the step's Philox draw is
-//          computed while the load is in flight);
-//   SEARCH one bisection probe of the row prefix (or of the segment table);
-//   FINAL  load the chosen record when the last probe did not bring it.
-// Lanes in different phases share each load instruction, so a lane deep in a
-// long bisection does not hold back the others (a lockstep step would wait
-// for the longest search of the warp every step).  Rows longer than
-// p.large are searched by the whole warp (search_warp) at the start of an
-// iteration.  Lanes that finish a walk are refilled from the warp's current
-// chunk; a chunk's R-endpoint blocks are aggregated in shared memory as soon
-// as its last walk ends, while the next chunk's walks are already running.
-struct SlotState {
-    uint32_t base, nsrc, total, issued, done, ctr_base, tag, live;
+// Persistent warps.  Each warp pulls chunks of sources from a global queue
+// (one atomic per chunk) and keeps all 32 lanes busy: a lane whose walk ends
+// takes the next walk of the chunk at once, so a warp never waits for the
+// longest of 32 geometric walk lengths (the paper's pipelines keep the
+// cluster busy the same way: new walks start while old ones finish).  Steps
+// run in lockstep; a row longer than p.large is searched by the whole warp
+// (search_warp) instead of by one lane's bisection, which shortens the
+// dependent-load chain the warp waits on.  Endpoints go to the per-walk
+// buffer and k_aggregate reduces them per source.  No shared memory is used
+// for walking, leaving the whole L1 to cache node records and probes.
+struct WarpQueue {
+    uint32_t base, nsrc, ctr_base, tag;  // current chunk
+    uint32_t issued, total;
 };
-
-enum : uint32_t { kIdle = 0, kNode = 1, kSearch = 2, kFinal = 3, kCoop = 4, kResolved = 5 };
-
-template <class E>
-__device__ __forceinline__ const uint4 *block_of(const void *base, uint64_t idx)
-{
-    // 16-byte aligned block holding record idx
-    return reinterpret_cast<const uint4 *>(base) + ((idx * sizeof(typename E::Rec)) >> 4);
-}
-
-template <class E>
-__device__ __forceinline__ void rec_in_block(uint4 v, uint64_t idx, uint64_t &key, uint32_t &tgt, uint32_t &aux)
-{
-    if constexpr (sizeof(typename E::Rec) == 8) {
-        const bool hi = (idx & 1) != 0;
-        key = hi ? v.z : v.x;
-        tgt = hi ? v.w : v.y;
-        aux = 0;
-    } else {
-        key = (uint64_t)v.x | ((uint64_t)v.y << 32);
-        tgt = v.z;
-        aux = v.w;
-    }
-}
 
 #ifndef PPR_WALK_MINB
 #define PPR_WALK_MINB 1  // minimum resident 256-thread blocks per SM requested from ptxas
@@ -237,38 +210,25 @@ __device__ __forceinline__ void rec_in_block(uint4 v, uint64_t idx, uint64_t &ke
 template <class E, bool SEG, bool STATS>
 __global__ void __launch_bounds__(256, PPR_WALK_MINB) k_walk_persistent(KParams p)
 {
-    extern __shared__ __align__(16) unsigned char smem_raw[];
+    __shared__ WarpQueue wq_all[8];
     const uint32_t lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
-    // per-warp shared memory: keys[P2] u64 | sortbuf[P2] u32 | slot ends [2][slot_cap] u32 | SlotState[2]
-    const size_t per_warp = (size_t)p.P2 * 12 + (size_t)p.slot_cap * 8 + sizeof(SlotState) * 2;
-    const size_t per_warp_al = (per_warp + 15) & ~(size_t)15;
-    unsigned char *mine = smem_raw + per_warp_al * wid;
-    uint64_t *keys = reinterpret_cast<uint64_t *>(mine);
-    uint32_t *sortbuf = reinterpret_cast<uint32_t *>(mine + (size_t)p.P2 * 8);
-    uint32_t *slot_ends = sortbuf + p.P2;
-    SlotState *ss = reinterpret_cast<SlotState *>(slot_ends + 2 * (size_t)p.slot_cap);
+    WarpQueue &wq = wq_all[wid];
     const E edges = make_edges<E>(p.edges);
-
-    if (lane < 2) ss[lane].live = 0;
+    if (lane == 0) {
+        wq.issued = 0;
+        wq.total = 0;
+    }
     __syncwarp();
-    int cur = -1;
     bool queue_empty = false;
-    uint32_t phase = kIdle;
-    uint32_t slot = 0, widx = 0, src = 0, j = 0, k = 0, u = 0;
-    uint32_t n = 0, x2 = 0;
-    uint64_t lo = 0, x = 0;
-    bool segw = false;
+    bool active = false;
+    uint32_t src = 0, sctr = 0, j = 0, k = 0, u = 0, tag = 0, ctr_base = 0;
+    uint64_t slot = 0;  // endpoint index (output row * R + j)
     Tally tl;
-    uint64_t last_sec = ~0ull;  // statistics only
 
     for (;;) {
-        // ---- refill idle lanes from the issuing slot, opening chunks as needed
-        uint32_t idle = __ballot_sync(0xffffffffu, phase == kIdle);
-        while (idle) {
-            if (cur < 0 || ss[cur].issued == ss[cur].total) {
-                if (queue_empty) break;
-                const int fresh = cur < 0 ? 0 : (cur ^ 1);
-                if (ss[fresh].live) break;  // older chunk still has walks in flight
+        uint32_t idle = __ballot_sync(0xffffffffu, !active);
+        while (idle && !queue_empty) {
+            if (wq.issued == wq.total) {
                 unsigned long long c = 0;
                 if (lane == 0) c = atomicAdd(p.queue, 1ull);
                 c = __shfl_sync(0xffffffffu, c, 0);
@@ -277,234 +237,51 @@ __global__ void __launch_bounds__(256, PPR_WALK_MINB) k_walk_persistent(KParams 
                     break;
                 }
                 if (lane == 0) {
-                    SlotState s;
                     if (p.chunks) {
                         int4 d = p.chunks[c];
-                        s.base = (uint32_t)d.x;
-                        s.nsrc = (uint32_t)d.y;
-                        s.ctr_base = (uint32_t)p.inst_off[d.z];
-                        s.tag = (uint32_t)d.z;
+                        wq.base = (uint32_t)d.x;
+                        wq.nsrc = (uint32_t)d.y;
+                        wq.ctr_base = (uint32_t)p.inst_off[d.z];
+                        wq.tag = (uint32_t)d.z;
                     } else {
                         int64_t b = p.s_begin + (int64_t)c * p.CS;
-                        s.base = (uint32_t)b;
-                        s.nsrc = (uint32_t)std::min<int64_t>((int64_t)p.CS, p.s_end - b);
-                        s.ctr_base = 0;
-                        s.tag = p.tag;
+                        wq.base = (uint32_t)b;
+                        wq.nsrc = (uint32_t)std::min<int64_t>((int64_t)p.CS, p.s_end - b);
+                        wq.ctr_base = 0;
+                        wq.tag = p.tag;
                     }
-                    s.total = s.nsrc * p.R;
-                    s.issued = 0;
-                    s.done = 0;
-                    s.live = 1;
-                    ss[fresh] = s;
+                    wq.issued = 0;
+                    wq.total = wq.nsrc * p.R;
                 }
                 __syncwarp();
-                cur = fresh;
             }
-            const uint32_t issued = ss[cur].issued, total = ss[cur].total, base = ss[cur].base;
-            const uint32_t take = min(total - issued, (uint32_t)__popc(idle));
+            const uint32_t issued = wq.issued;
+            const uint32_t take = min(wq.total - issued, (uint32_t)__popc(idle));
             const uint32_t rank = __popc(idle & ((1u << lane) - 1));
             if (((idle >> lane) & 1) && rank < take) {
-                widx = issued + rank;
-                slot = (uint32_t)cur;
-                const uint32_t i = widx / p.R;
-                j = widx - i * p.R;
-                src = base + i;
+                const uint32_t w = issued + rank;
+                const uint32_t i = w / p.R;
+                j = w - i * p.R;
+                src = wq.base + i;
+                ctr_base = wq.ctr_base;
+                sctr = src - ctr_base;
+                tag = wq.tag;
+                slot = ((uint64_t)((int64_t)src - p.s_begin)) * p.R + j;
                 k = 0;
                 u = src;
-                phase = kNode;
+                active = true;
             }
             __syncwarp();
-            if (lane == 0) ss[cur].issued = issued + take;
+            if (lane == 0) wq.issued = issued + take;
             __syncwarp();
-            idle = __ballot_sync(0xffffffffu, phase == kIdle);
+            idle = __ballot_sync(0xffffffffu, !active);
         }
-        const uint32_t act_mask = __ballot_sync(0xffffffffu, phase != kIdle);
-        if (act_mask == 0) {
-            if (queue_empty && !ss[0].live && !ss[1].live) break;
-        }
+        if (__ballot_sync(0xffffffffu, active) == 0) break;  // queue drained and every walk done
 
-        // ---- rows above the cooperative threshold: searched by the whole warp
-        if (!STATS) {
-            uint32_t cm = __ballot_sync(0xffffffffu, phase == kCoop);
-            while (cm) {
-                const uint32_t L = __ffs(cm) - 1;
-                cm &= cm - 1;
-                const uint64_t l0 = __shfl_sync(0xffffffffu, lo, L);
-                const uint32_t n0 = __shfl_sync(0xffffffffu, n, L);
-                const uint64_t xx = __shfl_sync(0xffffffffu, x, L);
-                auto rec = search_warp(edges, l0, n0, xx);
-                if (lane == L) {
-                    u = E::target(rec);  // the chosen edge's target; the step completes below
-                    phase = kResolved;
-                }
-            }
-        }
-
-        // ---- one load per active lane
-        uint64_t aidx = 0;
-        if (phase == kNode) {
-            aidx = u;
-        } else if (phase == kSearch) {
-            aidx = lo + (n >> 1) - 1;
-        } else if (phase == kFinal) {
-            aidx = lo;
-        }
-        const bool loads = phase == kNode || phase == kSearch || phase == kFinal;
-        uint4 v = make_uint4(0, 0, 0, 0);
-        if (loads) {
-            const uint4 *addr;
-            if (phase == kNode) addr = reinterpret_cast<const uint4 *>(p.node) + aidx;
-            else if (SEG && segw) addr = reinterpret_cast<const uint4 *>(p.seg) + aidx;
-            else addr = block_of<E>(p.edges, aidx);
-            v = __ldg(addr);
-        }
-
-        // Philox of the step a lane starts, overlapping the node-record load
-        uint4 rnd = make_uint4(0, 0, 0, 0);
-        if (phase == kNode) rnd = philox4x32_10(make_uint4(src - ss[slot].ctr_base, j, k, ss[slot].tag), p.k0, p.k1);
-
-        bool step_done = false, fin = false;
-        uint32_t next = 0, end = 0;
-        if (phase == kNode) {
-            const uint64_t w0 = (uint64_t)v.x | ((uint64_t)v.y << 32);
-            const uint64_t total = (uint64_t)v.z | ((uint64_t)v.w << 32);
-            const uint32_t cnt = (uint32_t)(w0 >> 40) & kCountMask;
-            const bool segf = SEG && (w0 >> 63);
-            x2 = rnd.z;
-            if (STATS) {
-                ++tl.sectors;
-                last_sec = ~0ull;
-            }
-            if (cnt == 0) {
-                if (p.dangling == 1) {
-                    fin = true;
-                    end = u;
-                } else {
-                    next = src;
-                    step_done = true;
-                }
-            } else if (cnt == 1 && !segf) {
-                next = (uint32_t)total;
-                step_done = true;
-            } else {
-                const uint64_t r64 = (uint64_t)rnd.x | ((uint64_t)rnd.y << 32);
-                x = (segf || total >= (1ull << 32)) ? mulhi64(r64, total) : mulhi64_by32(rnd.x, rnd.y, (uint32_t)total);
-                lo = w0 & kBeginMask;
-                n = cnt;
-                segw = segf;
-                phase = (!STATS && !segf && cnt > p.large) ? kCoop : (n > 1 ? kSearch : kFinal);
-            }
-        } else if (phase == kSearch) {
-            uint64_t key;
-            uint32_t tgt, aux;
-            if (SEG && segw) rec_in_block<SegTable>(v, aidx, key, tgt, aux);
-            else rec_in_block<E>(v, aidx, key, tgt, aux);
-            if (STATS) {
-                const uint64_t sec = (SEG && segw) ? ((reinterpret_cast<uint64_t>(p.seg) + aidx * 16) >> 5)
-                                                   : ((reinterpret_cast<uint64_t>(p.edges) + aidx * sizeof(typename E::Rec)) >> 5);
-                if (sec != last_sec) ++tl.sectors, last_sec = sec;
-            }
-            const uint32_t half = n >> 1;
-            if (key <= x) {
-                lo += half;
-                n -= half;
-            } else {
-                n = half;
-            }
-            if (n == 1) {
-                // the answer is lo; the 16-byte block just loaded may already hold it
-                const bool in_block = (SEG && segw) ? (lo == aidx)
-                                                    : (sizeof(typename E::Rec) == 8 ? ((lo >> 1) == (aidx >> 1)) : (lo == aidx));
-                if (in_block) {  // (same sector as the probe: no new sector for the statistics)
-                    uint64_t k2;
-                    if (SEG && segw) rec_in_block<SegTable>(v, lo, k2, tgt, aux);
-                    else rec_in_block<E>(v, lo, k2, tgt, aux);
-                    if (SEG && segw) {
-                        if ((aux >> 8) == 0) {
-                            fin = true;
-                            end = tgt;
-                            ++tl.steps;
-                        } else {
-                            u = tgt;
-                            k += aux & 0xffu;
-                            ++tl.steps;
-                            phase = kNode;
-                        }
-                    } else {
-                        next = tgt;
-                        step_done = true;
-                    }
-                } else {
-                    phase = kFinal;
-                }
-            }
-        } else if (phase == kFinal) {
-            uint64_t key;
-            uint32_t tgt, aux;
-            if (SEG && segw) rec_in_block<SegTable>(v, aidx, key, tgt, aux);
-            else rec_in_block<E>(v, aidx, key, tgt, aux);
-            if (STATS) {
-                const uint64_t sec = (SEG && segw) ? ((reinterpret_cast<uint64_t>(p.seg) + aidx * 16) >> 5)
-                                                   : ((reinterpret_cast<uint64_t>(p.edges) + aidx * sizeof(typename E::Rec)) >> 5);
-                if (sec != last_sec) ++tl.sectors, last_sec = sec;
-            }
-            if (SEG && segw) {
-                ++tl.steps;
-                if ((aux >> 8) == 0) {
-                    fin = true;
-                    end = tgt;
-                } else {
-                    u = tgt;
-                    k += aux & 0xffu;
-                    phase = kNode;
-                }
-            } else {
-                next = tgt;
-                step_done = true;
-            }
-        } else if (phase == kResolved) {
-            next = u;  // chosen by the cooperative search
-            step_done = true;
-        }
-        if (step_done) {
-            ++tl.steps;
-            ++k;
-            u = next;
-            if (x2 < p.T) {
-                fin = true;
-                end = u;
-            } else {
-                phase = kNode;
-            }
-        }
-        if (fin) {
-            slot_ends[(size_t)slot * p.slot_cap + widx] = end - ss[slot].ctr_base;
-            phase = kIdle;
-        }
-        const uint32_t f0 = __ballot_sync(0xffffffffu, fin && slot == 0);
-        const uint32_t f1 = __ballot_sync(0xffffffffu, fin && slot == 1);
-        if ((f0 | f1) != 0) {
-            __syncwarp();
-            if (lane == 0) {
-                ss[0].done += __popc(f0);
-                ss[1].done += __popc(f1);
-            }
-            __syncwarp();
-            // ---- aggregate finished chunks in shared memory
-#pragma unroll
-            for (int sI = 0; sI < 2; ++sI) {
-                const SlotState s = ss[sI];
-                if (s.live && s.done == s.total && s.issued == s.total) {
-                    for (uint32_t i = 0; i < s.nsrc; ++i) {
-                        const uint64_t row = (uint64_t)p.out_row0 + (uint64_t)((int64_t)(s.base + i) - p.s_begin);
-                        aggregate_source(slot_ends + (size_t)sI * p.slot_cap + (size_t)i * p.R, p.R, sortbuf, keys,
-                                         p.out, row);
-                    }
-                    __syncwarp();
-                    if (lane == 0) ss[sI].live = 0;
-                    __syncwarp();
-                }
-            }
+        uint32_t end = 0;
+        if (walk_step<E, SEG, true, STATS>(p, edges, active, src, sctr, j, tag, k, u, end, tl)) {
+            p.ends[slot] = end - ctr_base;
+            active = false;
         }
     }
     warp_add_tally<STATS>(p.steps, tl);
@@ -512,44 +289,38 @@ __global__ void __launch_bounds__(256, PPR_WALK_MINB) k_walk_persistent(KParams 
 
 // ------------------------------------------------------------- launcher ----
 
-template <class E, bool SEG, bool STATS>
-static int launch_typed(ppr_ctx *ctx, const KParams &kp0, const RunPlan &plan, int64_t S, cudaStream_t st)
+static int launch_aggregate(ppr_ctx *ctx, const KParams &kp, int64_t S, cudaStream_t st)
 {
-    KParams kp = kp0;
+    const int aw = 4;
+    size_t smem = (size_t)aw * kp.P2 * 12;
+    if (smem > 48 * 1024) PPR_CUDA(cudaFuncSetAttribute(k_aggregate, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
+    int ablocks = (int)std::min<int64_t>((S + aw - 1) / aw, (int64_t)ctx->sms * 16);
+    if (ablocks < 1) ablocks = 1;
+    k_aggregate<<<ablocks, aw * 32, smem, st>>>(kp);
+    PPR_CUDA(cudaGetLastError());
+    return PPR_OK;
+}
+
+template <class E, bool SEG, bool STATS>
+static int launch_typed(ppr_ctx *ctx, const KParams &kp, const RunPlan &plan, int64_t S, cudaStream_t st)
+{
     if (plan.kernel == PPR_KERNEL_PLAIN) {
         uint64_t total = (uint64_t)S * kp.R;
         int blocks = (int)std::min<uint64_t>((total + 255) / 256, (uint64_t)ctx->sms * 64);
         if (blocks < 1) blocks = 1;
         k_walk_plain<E, SEG, STATS><<<blocks, 256, 0, st>>>(kp);
         PPR_CUDA(cudaGetLastError());
-        const int aw = 4;
-        size_t smem = (size_t)aw * kp.P2 * 12;
-        if (smem > 48 * 1024) PPR_CUDA(cudaFuncSetAttribute(k_aggregate, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
-        int ablocks = (int)std::min<int64_t>((S + aw - 1) / aw, (int64_t)ctx->sms * 16);
-        if (ablocks < 1) ablocks = 1;
-        k_aggregate<<<ablocks, aw * 32, smem, st>>>(kp);
-        PPR_CUDA(cudaGetLastError());
-        return PPR_OK;
+        return launch_aggregate(ctx, kp, S, st);
     }
-    int wpb = plan.warps_per_block > 0 ? plan.warps_per_block : 8;
-    const size_t per_warp = (size_t)kp.P2 * 12 + (size_t)kp.slot_cap * 8 + sizeof(SlotState) * 2;
-    const size_t per_warp_al = (per_warp + 15) & ~(size_t)15;
-    while (wpb > 1 && per_warp_al * wpb > ctx->smem_optin) wpb >>= 1;
-    size_t smem = per_warp_al * wpb;
-    if (smem > ctx->smem_optin) {
-        set_error("persistent walker needs %zu bytes of shared memory per warp", per_warp_al);
-        return PPR_ERANGE;
-    }
-    PPR_CUDA(cudaFuncSetAttribute(k_walk_persistent<E, SEG, STATS>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
     int per_sm = 0;
-    PPR_CUDA(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_walk_persistent<E, SEG, STATS>, wpb * 32, smem));
+    PPR_CUDA(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_walk_persistent<E, SEG, STATS>, 256, 0));
     if (per_sm < 1) per_sm = 1;
     int64_t blocks = (int64_t)ctx->sms * per_sm;
-    int64_t needed = ((int64_t)kp.nchunks + wpb - 1) / wpb;
+    int64_t needed = ((int64_t)kp.nchunks + 7) / 8;
     if (blocks > needed) blocks = std::max<int64_t>(needed, 1);
-    k_walk_persistent<E, SEG, STATS><<<(unsigned)blocks, wpb * 32, smem, st>>>(kp);
+    k_walk_persistent<E, SEG, STATS><<<(unsigned)blocks, 256, 0, st>>>(kp);
     PPR_CUDA(cudaGetLastError());
-    return PPR_OK;
+    return launch_aggregate(ctx, kp, S, st);
 }
 
 int launch_walks(ppr_ctx *ctx, const ppr_graph *g, const RunPlan &plan, ppr_result *r, int64_t s_begin,
@@ -593,9 +364,8 @@ int launch_walks(ppr_ctx *ctx, const ppr_graph *g, const RunPlan &plan, ppr_resu
             return PPR_ENOTSUP;
         }
     } else {
-        uint32_t CS = plan.chunk_sources > 0 ? (uint32_t)plan.chunk_sources : std::max(1u, 512u / plan.R);
+        uint32_t CS = plan.chunk_sources > 0 ? (uint32_t)plan.chunk_sources : std::max(1u, 1024u / plan.R);
         kp.CS = CS;
-        kp.slot_cap = CS * plan.R;
         if (g->instances > 0) {
             // chunks never cross an instance boundary
             const auto &off = g->node_off;
