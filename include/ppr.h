@@ -154,7 +154,8 @@ typedef struct {
     int32_t segments;    /* 1: depth-3 segment tables for out-degree <= 8 (Algorithm 4) */
     int32_t topk;        /* 0..R: per-source top-k (count desc, end id asc) kept with the rows */
     int32_t kernel;      /* PPR_KERNEL_PERSISTENT or PPR_KERNEL_PLAIN */
-    int32_t large_degree;/* out-degree above which a warp searches cooperatively; 0 = default 4096 */
+    int32_t large_degree;/* out-degree above which the whole warp searches a lane's row
+                            cooperatively (persistent kernel); 0 = never (default) */
     int32_t warps_per_block;  /* persistent kernel tuning, 0 = default */
     int32_t chunk_sources;    /* sources per queue item, 0 = default */
     int64_t max_batch_sources;/* sources per device batch, 0 = sized to free device memory */

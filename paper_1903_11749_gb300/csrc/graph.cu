@@ -131,6 +131,90 @@ __global__ void k_rows_pass2(int64_t n, const int64_t *row_ptr, const int32_t *c
     }
 }
 
+// Record slots of each blocked row (narrow layout).
+__global__ void k_row_records(int64_t n, const int64_t *row_ptr, uint32_t *sizes)
+{
+    for (int64_t u = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; u < n; u += (int64_t)gridDim.x * blockDim.x)
+        sizes[u] = blocked_row_records((uint32_t)(row_ptr[u + 1] - row_ptr[u]));
+}
+
+// Pass 2, narrow layout: one warp per row writes the edge records of a
+// blocked row (inclusive prefix by warp scan), the padding, and the summary
+// levels; then the node record.
+__global__ void k_rows_pass2_blocked(int64_t n, const int64_t *row_ptr, const int32_t *col, const uint32_t *w,
+                                     const int64_t *node_off, int32_t count, const uint64_t *W, const uint64_t *region,
+                                     NodeRec *node, EdgeN *E)
+{
+    const int lane = threadIdx.x & 31;
+    const int64_t warps = (int64_t)gridDim.x * (blockDim.x >> 5);
+    uint32_t *K = reinterpret_cast<uint32_t *>(E);
+    for (int64_t u = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5; u < n; u += warps) {
+        const int64_t a = row_ptr[u];
+        const uint32_t d = (uint32_t)(row_ptr[u + 1] - a);
+        int64_t base_id = 0;
+        if (count > 0) base_id = node_off[instance_of(node_off, count, u)];
+        const uint64_t reg = region[u];
+        if (d >= 2) {
+            const uint32_t L = tree_levels(d);
+            const uint32_t S = summary_sectors(d);
+            const uint64_t eb = reg + 4ull * S;
+            // key slot (uint32 index) of level l, key i: sectors of higher levels first
+            auto level_key = [&](uint32_t l, uint32_t i) -> uint64_t {
+                uint32_t off = 0;
+                for (uint32_t m = L; m > l; --m) off += level_sectors(d, m);
+                return (reg + 4ull * off) * 2 + i;
+            };
+            uint64_t carry = 0;
+            for (uint32_t e0 = 0; e0 < d; e0 += 32) {
+                const uint32_t i = e0 + lane;
+                uint64_t v = i < d ? (uint64_t)w[a + i] : 0ull;
+#pragma unroll
+                for (int o = 1; o < 32; o <<= 1) {
+                    uint64_t y = __shfl_up_sync(0xffffffffu, v, o);
+                    if (lane >= o) v += y;
+                }
+                const uint64_t P = carry + v;
+                if (i < d) {
+                    EdgeN r;
+                    r.P = (uint32_t)P;
+                    r.col = (int32_t)(col[a + i] + base_id);
+                    E[eb + i] = r;
+                    if (L > 0 && ((i & 7) == 7 || i == d - 1)) K[level_key(1, i >> 3)] = (uint32_t)P;
+                }
+                carry += __shfl_sync(0xffffffffu, v, 31);
+            }
+            // padding records up to the sector boundary
+            for (uint32_t i = d + lane; i < 4 * ceil_shift(d, 2); i += 32) {
+                EdgeN r;
+                r.P = 0xffffffffu;
+                r.col = 0;
+                E[eb + i] = r;
+            }
+            if (L > 0) {
+                const uint32_t n1 = ceil_shift(d, 3);
+                for (uint32_t i = n1 + lane; i < 8 * level_sectors(d, 1); i += 32) K[level_key(1, i)] = 0xffffffffu;
+                __syncwarp();
+                for (uint32_t l = 2; l <= L; ++l) {
+                    const uint32_t nl = ceil_shift(d, 3 * l), np = ceil_shift(d, 3 * (l - 1));
+                    for (uint32_t i = lane; i < 8 * level_sectors(d, l); i += 32) {
+                        uint32_t kv = 0xffffffffu;
+                        if (i < nl) kv = K[level_key(l - 1, min(8 * i + 8, np) - 1)];
+                        K[level_key(l, i)] = kv;
+                    }
+                    __syncwarp();
+                }
+            }
+        }
+        if (lane == 0) {
+            NodeRec r;
+            r.word0 = pack_word0(reg, d, false);
+            // a single out-edge needs no draw-to-edge search: keep its target inline
+            r.total = (d == 1) ? (uint64_t)(uint32_t)(col[a] + base_id) : W[u];
+            node[u] = r;
+        }
+    }
+}
+
 int build_graph(ppr_ctx *ctx, int64_t n, int64_t m, const int64_t *row_ptr, const int32_t *col,
                 const uint32_t *w, bool device_ptrs, cudaStream_t st, ppr_graph *g)
 {
@@ -211,14 +295,40 @@ int build_graph(ppr_ctx *ctx, int64_t n, int64_t m, const int64_t *row_ptr, cons
     g->wide = hs.max_total >= (1ull << 32);
     g->max_degree = (int64_t)hs.max_degree;
     g->dangling = (int64_t)hs.dangling;
-    size_t edge_bytes = (size_t)m * (g->wide ? sizeof(EdgeW) : sizeof(EdgeN));
     if ((rc = dev_alloc((void **)&g->node, sizeof(NodeRec) * n, "node records"))) return cleanup(), rc;
-    if ((rc = dev_alloc(&g->edges, edge_bytes > 0 ? edge_bytes : 16, "edge records"))) return cleanup(), rc;
-    g->device_bytes = (int64_t)(sizeof(NodeRec) * n + edge_bytes);
-    if (g->wide)
+    if (g->wide) {
+        size_t edge_bytes = (size_t)m * sizeof(EdgeW);
+        if ((rc = dev_alloc(&g->edges, edge_bytes > 0 ? edge_bytes : 16, "edge records"))) return cleanup(), rc;
+        g->device_bytes = (int64_t)(sizeof(NodeRec) * n + edge_bytes);
         k_rows_pass2<true><<<blocks, threads, 0, st>>>(n, d_rp, d_col, d_w, d_off, g->instances, d_W, g->node, g->edges);
-    else
-        k_rows_pass2<false><<<blocks, threads, 0, st>>>(n, d_rp, d_col, d_w, d_off, g->instances, d_W, g->node, g->edges);
+    } else {
+        // blocked rows: record slots per row, their offsets, then the rows
+        uint32_t *d_sizes;
+        uint64_t *d_region, *d_scan;
+        int64_t tiles = (n + kScanTile - 1) / kScanTile;
+        if ((rc = dev_alloc((void **)&d_sizes, sizeof(uint32_t) * n, "row sizes"))) return cleanup(), rc;
+        tmp.push_back(d_sizes);
+        if ((rc = dev_alloc((void **)&d_region, sizeof(uint64_t) * (n + 1), "row regions"))) return cleanup(), rc;
+        tmp.push_back(d_region);
+        if ((rc = dev_alloc((void **)&d_scan, sizeof(uint64_t) * (tiles + 2), "scan scratch"))) return cleanup(), rc;
+        tmp.push_back(d_scan);
+        int sblocks = (int)std::min<int64_t>((n + 255) / 256, (int64_t)ctx->sms * 16);
+        k_row_records<<<sblocks, 256, 0, st>>>(n, d_rp, d_sizes);
+        exclusive_scan_u32(d_sizes, n, d_region, d_scan, st);
+        uint64_t slots = 0;
+        e = cudaMemcpyAsync(&slots, d_region + n, sizeof(uint64_t), cudaMemcpyDeviceToHost, st);
+        if (e == cudaSuccess) e = cudaStreamSynchronize(st);
+        if (e != cudaSuccess) return cleanup(), cuda_fail(e, "row layout");
+        if (slots > kBeginMask) {
+            set_error("edge layout needs %llu record slots, beyond 2^40", (unsigned long long)slots);
+            return cleanup(), PPR_ERANGE;
+        }
+        size_t edge_bytes = (size_t)(slots > 0 ? slots : 2) * sizeof(EdgeN);
+        if ((rc = dev_alloc(&g->edges, edge_bytes, "edge records"))) return cleanup(), rc;
+        g->device_bytes = (int64_t)(sizeof(NodeRec) * n + edge_bytes);
+        k_rows_pass2_blocked<<<blocks, threads, 0, st>>>(n, d_rp, d_col, d_w, d_off, g->instances, d_W, d_region,
+                                                          g->node, (EdgeN *)g->edges);
+    }
     e = cudaGetLastError();
     if (e == cudaSuccess) e = cudaStreamSynchronize(st);
     cleanup();
@@ -257,12 +367,19 @@ struct RowView {
     __device__ __forceinline__ uint64_t total(uint32_t u) const
     {
         uint32_t d = deg(u);
-        return d ? E::key(edges.load(begin(u) + d - 1)) : 0ull;
+        if (d == 1) return 1;  // with wt = 1 above: the single edge has ratio 1
+        return d ? E::key(edges.load(E::edge_base(begin(u), d) + d - 1)) : 0ull;
     }
     // weight and target of the i-th edge of u
     __device__ __forceinline__ void edge(uint32_t u, uint32_t i, uint64_t &wt, uint32_t &tgt) const
     {
-        uint64_t b = begin(u);
+        const uint32_t d = deg(u);
+        if (d == 1) {  // target kept in the node record; weight ratio is 1
+            wt = 1;
+            tgt = (uint32_t)node[u].total;
+            return;
+        }
+        uint64_t b = E::edge_base(begin(u), d);
         auto r = edges.load(b + i);
         uint64_t prev = i > 0 ? E::key(edges.load(b + i - 1)) : 0ull;
         wt = E::key(r) - prev;

@@ -9,7 +9,20 @@
 //   plain rows:  begin/count index the edge-record array
 //   segment rows: begin/count index the segment-entry array
 //   EdgeN (8 B): {uint32 P, int32 col}  -- narrow layout, every W_u < 2^32
-//   EdgeW (16 B): {uint64 P, int32 col, pad} -- wide layout
+//   EdgeW (16 B): {uint64 P, int32 col, pad} -- wide layout (flat rows)
+//
+// Narrow rows are stored as static search trees ("blocked" rows): a row with
+// d >= 2 edges starts on a 32-byte sector; its region holds the summary
+// levels (top level first), then the edge records in blocks of 8 (the area
+// rounded up to whole sectors, padding keys 0xFFFFFFFF).  Level 1 keeps the
+// last prefix of every 8-record block, level l+1 the last key of every
+// 8-key sector of level l, up to a top level of at most 8 keys (one sector).
+// A search reads one sector per level and one 8-record block: the same edge
+// as bisection of the flat prefix (the first P > x is unique), found with
+// ceil(log8 d) + 1 dependent loads instead of ceil(log2 d) + 1.  The alias
+// tree of the paper (Algorithm 3) splits large neighbour sets the same way so
+// that a selection touches one small set per level; Lemma 1 is the analogous
+// exactness argument.
 //   SegEntry (16 B): {uint64 cum, uint32 node, uint32 mark_len}
 //   P / cum are inclusive prefix sums within the row / table.
 #pragma once
@@ -48,6 +61,35 @@ struct __align__(16) SegEntry {
 __host__ __device__ inline uint64_t pack_word0(uint64_t begin, uint32_t count, bool seg)
 {
     return (begin & kBeginMask) | ((uint64_t)(count & kCountMask) << 40) | (seg ? kSegFlag : 0ull);
+}
+
+// ceil(d / 2^s)
+__host__ __device__ __forceinline__ uint32_t ceil_shift(uint32_t d, uint32_t s) { return (d + (1u << s) - 1) >> s; }
+
+// Number of summary levels above a blocked row of d edges (0 for d <= 8).
+__host__ __device__ __forceinline__ uint32_t tree_levels(uint32_t d)
+{
+    uint32_t L = 0;
+    while (d > (1u << (3 * (L + 1)))) ++L;
+    return L;
+}
+
+// Sectors of level l (1 <= l <= L): ceil(keys_l / 8) = ceil(d / 8^(l+1)).
+__host__ __device__ __forceinline__ uint32_t level_sectors(uint32_t d, uint32_t l) { return ceil_shift(d, 3 * (l + 1)); }
+
+__host__ __device__ __forceinline__ uint32_t summary_sectors(uint32_t d)
+{
+    uint32_t L = tree_levels(d), S = 0;
+    for (uint32_t l = 1; l <= L; ++l) S += level_sectors(d, l);
+    return S;
+}
+
+// 8-byte record slots a blocked row occupies (a one-edge row keeps its target
+// in the node record and needs none).
+__host__ __device__ __forceinline__ uint32_t blocked_row_records(uint32_t d)
+{
+    if (d <= 1) return 0;
+    return 4 * summary_sectors(d) + 4 * ceil_shift(d, 2);
 }
 
 // ---------------------------------------------------------------- Philox ----
@@ -95,6 +137,11 @@ __device__ __forceinline__ NodeRec load_node(const NodeRec *node, uint32_t u)
 struct NarrowEdges {
     using Key = uint32_t;
     const EdgeN *e;
+    // record index of edge 0 of a row whose region starts at `begin`
+    __host__ __device__ __forceinline__ static uint64_t edge_base(uint64_t begin, uint32_t d)
+    {
+        return begin + 4ull * summary_sectors(d);
+    }
     __device__ __forceinline__ uint2 load(uint64_t i) const
     {
         return __ldg(reinterpret_cast<const uint2 *>(e) + i);
@@ -106,6 +153,7 @@ struct NarrowEdges {
 
 struct WideEdges {
     const EdgeW *e;
+    __host__ __device__ __forceinline__ static uint64_t edge_base(uint64_t begin, uint32_t) { return begin; }
     __device__ __forceinline__ uint4 load(uint64_t i) const
     {
         return __ldg(reinterpret_cast<const uint4 *>(e) + i);
@@ -171,6 +219,56 @@ __device__ __forceinline__ typename E::Rec search_serial_tally(const E &edges, u
     uint64_t sec = (base + lo * rec) >> 5;
     if (sec != last) ++sectors;
     return edges.load(lo);
+}
+
+__device__ __forceinline__ uint32_t count_le(uint4 k, uint32_t x)
+{
+    return (uint32_t)(k.x <= x) + (uint32_t)(k.y <= x) + (uint32_t)(k.z <= x) + (uint32_t)(k.w <= x);
+}
+
+// Search of a blocked narrow row (layout above): returns the target of the
+// first edge with P > x.  TALLY counts the 32-byte sectors read.
+template <bool TALLY>
+__device__ __forceinline__ uint32_t search_blocked(const EdgeN *E, uint64_t begin, uint32_t d, uint32_t x,
+                                                   uint32_t &sectors)
+{
+    const uint32_t L = tree_levels(d);
+    uint32_t S = 0;
+    for (uint32_t l = 1; l <= L; ++l) S += level_sectors(d, l);
+    const uint4 *base = reinterpret_cast<const uint4 *>(E + begin);  // sector-aligned
+    uint32_t b = 0, off = 0;
+    for (uint32_t l = L; l >= 1; --l) {
+        const uint4 *p = base + 2ull * (off + b);
+        const uint4 k0 = __ldg(p), k1 = __ldg(p + 1);
+        const uint32_t c = count_le(k0, x) + count_le(k1, x);
+        off += level_sectors(d, l);
+        b = b * 8 + c;
+        if (TALLY) ++sectors;
+    }
+    const uint32_t len = min(8u, d - 8 * b);
+    const uint4 *q = base + 2ull * (S + 2 * b);  // 8-record block b
+    const uint4 r0 = __ldg(q), r1 = __ldg(q + 1);
+    uint4 r2 = make_uint4(0xffffffffu, 0, 0xffffffffu, 0), r3 = r2;
+    if (len > 4) {
+        r2 = __ldg(q + 2);
+        r3 = __ldg(q + 3);
+    }
+    if (TALLY) sectors += len > 4 ? 2 : 1;
+    // records are (P, col) pairs: keys in .x/.z, targets in .y/.w
+    const uint32_t c = (uint32_t)(r0.x <= x) + (uint32_t)(r0.z <= x) + (uint32_t)(r1.x <= x) + (uint32_t)(r1.z <= x) +
+                       (uint32_t)(r2.x <= x) + (uint32_t)(r2.z <= x) + (uint32_t)(r3.x <= x) + (uint32_t)(r3.z <= x);
+    uint32_t t;
+    switch (c) {
+    case 0: t = r0.y; break;
+    case 1: t = r0.w; break;
+    case 2: t = r1.y; break;
+    case 3: t = r1.w; break;
+    case 4: t = r2.y; break;
+    case 5: t = r2.w; break;
+    case 6: t = r3.y; break;
+    default: t = r3.w; break;
+    }
+    return t;
 }
 
 // Same result, computed by the whole warp for one lane's search (all 32 lanes

@@ -84,8 +84,8 @@ __device__ __forceinline__ bool walk_step(const KParams &p, const E &edges, bool
         while (bigmask) {
             const uint32_t L = __ffs(bigmask) - 1;
             bigmask &= bigmask - 1;
-            const uint64_t lo = __shfl_sync(0xffffffffu, beg, L);
             const uint32_t n = __shfl_sync(0xffffffffu, cnt, L);
+            const uint64_t lo = E::edge_base(__shfl_sync(0xffffffffu, beg, L), n);
             const uint64_t xx = __shfl_sync(0xffffffffu, xr, L);
             auto rec = search_warp(edges, lo, n, xx);
             if (lane == L) next = E::target(rec);
@@ -114,7 +114,11 @@ __device__ __forceinline__ bool walk_step(const KParams &p, const E &edges, bool
     } else if (cnt == 1) {
         next = (uint32_t)total;  // single out-edge: target kept in the node record
     } else if (!big) {
-        next = E::target(STATS ? search_serial_tally(edges, beg, cnt, xr, tl.sectors) : search_serial(edges, beg, cnt, xr));
+        if constexpr (sizeof(typename E::Rec) == 8) {
+            next = search_blocked<STATS>(edges.e, beg, cnt, (uint32_t)xr, tl.sectors);
+        } else {
+            next = E::target(STATS ? search_serial_tally(edges, beg, cnt, xr, tl.sectors) : search_serial(edges, beg, cnt, xr));
+        }
     }
     ++tl.steps;
     ++k;
@@ -155,8 +159,12 @@ __device__ __forceinline__ void warp_add_tally(unsigned long long *dst, const Ta
 }
 
 // ------------------------------------------------------------ plain (K4) ----
+#ifndef PPR_WALK_MINB
+#define PPR_WALK_MINB 8  // resident 256-thread blocks per SM asked of ptxas (8: 32 registers, 64 warps)
+#endif
+
 template <class E, bool SEG, bool STATS>
-__global__ void __launch_bounds__(256) k_walk_plain(KParams p)
+__global__ void __launch_bounds__(256, PPR_WALK_MINB) k_walk_plain(KParams p)
 {
     const E edges = make_edges<E>(p.edges);
     const uint64_t S = (uint64_t)(p.s_end - p.s_begin);
@@ -202,10 +210,6 @@ struct WarpQueue {
     uint32_t base, nsrc, ctr_base, tag;  // current chunk
     uint32_t issued, total;
 };
-
-#ifndef PPR_WALK_MINB
-#define PPR_WALK_MINB 1  // minimum resident 256-thread blocks per SM requested from ptxas
-#endif
 
 template <class E, bool SEG, bool STATS>
 __global__ void __launch_bounds__(256, PPR_WALK_MINB) k_walk_persistent(KParams p)
@@ -338,7 +342,7 @@ int launch_walks(ppr_ctx *ctx, const ppr_graph *g, const RunPlan &plan, ppr_resu
     kp.k1 = (uint32_t)(plan.seed >> 32);
     kp.tag = plan.tag;
     kp.dangling = plan.dangling;
-    kp.large = plan.large_degree > 0 ? (uint32_t)plan.large_degree : 4096u;
+    kp.large = plan.large_degree > 0 ? (uint32_t)plan.large_degree : 0xffffffffu;  // 0: off
     kp.s_begin = s_begin;
     kp.s_end = s_end;
     kp.out_row0 = out_row0;
