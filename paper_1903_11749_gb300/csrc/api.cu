@@ -33,10 +33,13 @@ int cuda_fail(cudaError_t e, const char *what)
     return PPR_ECUDA;
 }
 
-int dev_alloc(void **p, size_t bytes, const char *what)
+// Device memory comes from the device's default stream-ordered pool, which
+// the context sets to keep freed memory reserved: repeated runs reuse it
+// without cudaMalloc/cudaFree round trips to the driver.
+int dev_alloc(void **p, size_t bytes, const char *what, cudaStream_t st)
 {
     *p = nullptr;
-    cudaError_t e = cudaMalloc(p, bytes > 0 ? bytes : 1);
+    cudaError_t e = cudaMallocAsync(p, bytes > 0 ? bytes : 1, st);
     if (e != cudaSuccess) {
         cudaGetLastError();  // clear the sticky-free allocation error
         *p = nullptr;
@@ -44,6 +47,11 @@ int dev_alloc(void **p, size_t bytes, const char *what)
         return e == cudaErrorMemoryAllocation ? PPR_ENOMEM : PPR_ECUDA;
     }
     return PPR_OK;
+}
+
+void dev_free(void *p, cudaStream_t st)
+{
+    if (p) cudaFreeAsync(p, st);
 }
 
 // Row compaction: one warp per source copies its stored pairs to the
@@ -129,6 +137,11 @@ int ppr_create(int device, ppr_ctx **out)
     c->sms = v;
     cudaDeviceGetAttribute(&v, cudaDevAttrMaxSharedMemoryPerBlockOptin, device);
     c->smem_optin = (size_t)v;
+    cudaMemPool_t pool;
+    if (cudaDeviceGetDefaultMemPool(&pool, device) == cudaSuccess) {
+        uint64_t keep = ~0ull;  // keep freed blocks reserved for reuse
+        cudaMemPoolSetAttribute(pool, cudaMemPoolAttrReleaseThreshold, &keep);
+    }
     *out = c;
     return PPR_OK;
 }
@@ -161,6 +174,7 @@ static int load_common(ppr_ctx *ctx, int64_t n, int64_t m, const int64_t *row_pt
     g->ctx = ctx;
     g->n = n;
     g->m = m;
+    g->stream = (cudaStream_t)stream;
     return build_graph(ctx, n, m, row_ptr, col, w, (flags & PPR_PTRS_DEVICE) != 0, (cudaStream_t)stream, g);
 }
 
@@ -240,10 +254,10 @@ void ppr_free_graph(ppr_graph *g)
 {
     if (!g) return;
     if (g->ctx) cudaSetDevice(g->ctx->device);
-    cudaFree(g->node);
-    cudaFree(g->edges);
-    cudaFree(g->seg.node);
-    cudaFree(g->seg.entries);
+    dev_free(g->node, g->stream);
+    dev_free(g->edges, g->stream);
+    dev_free(g->seg.node, g->stream);
+    dev_free(g->seg.entries, g->stream);
     delete g;
 }
 
@@ -261,13 +275,13 @@ static void result_release(ppr_result *r)
 {
     if (!r) return;
     if (r->ctx) cudaSetDevice(r->ctx->device);
-    cudaFree(r->d_nnz);
-    cudaFree(r->d_cols);
-    cudaFree(r->d_cnts);
-    cudaFree(r->d_topk_idx);
-    cudaFree(r->d_topk_cnt);
-    cudaFree(r->d_steps);
-    for (void *p : r->scratch) cudaFree(p);
+    dev_free(r->d_nnz, r->stream);
+    dev_free(r->d_cols, r->stream);
+    dev_free(r->d_cnts, r->stream);
+    dev_free(r->d_topk_idx, r->stream);
+    dev_free(r->d_topk_cnt, r->stream);
+    dev_free(r->d_steps, r->stream);
+    for (void *p : r->scratch) dev_free(p, r->stream);
     if (r->ev_start) cudaEventDestroy(r->ev_start);
     if (r->ev_walk_end) cudaEventDestroy(r->ev_walk_end);
     if (r->ev_done) cudaEventDestroy(r->ev_done);
@@ -346,14 +360,14 @@ int ppr_run(ppr_ctx *ctx, const ppr_graph *g, const ppr_run_args *a, ppr_result 
         return code;
     };
     const size_t S = (size_t)r->S;
-    if ((rc = dev_alloc((void **)&r->d_nnz, sizeof(uint32_t) * S, "row sizes"))) return fail(rc);
-    if ((rc = dev_alloc((void **)&r->d_cols, sizeof(int32_t) * S * r->cap, "row ids"))) return fail(rc);
-    if ((rc = dev_alloc((void **)&r->d_cnts, sizeof(uint32_t) * S * r->cap, "row counts"))) return fail(rc);
+    if ((rc = dev_alloc((void **)&r->d_nnz, sizeof(uint32_t) * S, "row sizes", st))) return fail(rc);
+    if ((rc = dev_alloc((void **)&r->d_cols, sizeof(int32_t) * S * r->cap, "row ids", st))) return fail(rc);
+    if ((rc = dev_alloc((void **)&r->d_cnts, sizeof(uint32_t) * S * r->cap, "row counts", st))) return fail(rc);
     if (r->topk > 0) {
-        if ((rc = dev_alloc((void **)&r->d_topk_idx, sizeof(int32_t) * S * r->topk, "top-k ids"))) return fail(rc);
-        if ((rc = dev_alloc((void **)&r->d_topk_cnt, sizeof(uint32_t) * S * r->topk, "top-k counts"))) return fail(rc);
+        if ((rc = dev_alloc((void **)&r->d_topk_idx, sizeof(int32_t) * S * r->topk, "top-k ids", st))) return fail(rc);
+        if ((rc = dev_alloc((void **)&r->d_topk_cnt, sizeof(uint32_t) * S * r->topk, "top-k counts", st))) return fail(rc);
     }
-    if ((rc = dev_alloc((void **)&r->d_steps, sizeof(unsigned long long) * 3, "counters"))) return fail(rc);
+    if ((rc = dev_alloc((void **)&r->d_steps, sizeof(unsigned long long) * 3, "counters", st))) return fail(rc);
     cudaError_t e = cudaEventCreate(&r->ev_start);
     if (e == cudaSuccess) e = cudaEventCreate(&r->ev_walk_end);
     if (e == cudaSuccess) e = cudaEventCreate(&r->ev_done);
@@ -384,7 +398,7 @@ int ppr_run(ppr_ctx *ctx, const ppr_graph *g, const ppr_run_args *a, ppr_result 
         cudaMemGetInfo(&free_b, &total_b);
         int64_t fit = (int64_t)(free_b / 4 / ((size_t)a->R * sizeof(uint32_t)));
         batch = std::max<int64_t>(1, std::min<int64_t>(batch, fit));
-        if ((rc = dev_alloc((void **)&ends, sizeof(uint32_t) * (size_t)batch * a->R, "endpoint buffer")))
+        if ((rc = dev_alloc((void **)&ends, sizeof(uint32_t) * (size_t)batch * a->R, "endpoint buffer", st)))
             return fail(rc);
         r->scratch.push_back(ends);
     }
@@ -480,16 +494,17 @@ int ppr_sparse_rows(const ppr_result *rc_, int64_t *row_ptr, int32_t *col, uint3
     const int64_t S = r->S;
     int64_t tiles = (S + kScanTile - 1) / kScanTile;
     uint64_t *d_off = nullptr, *d_tmp = nullptr;
-    if ((rc = dev_alloc((void **)&d_off, sizeof(uint64_t) * (S + 1), "row offsets"))) return rc;
-    if ((rc = dev_alloc((void **)&d_tmp, sizeof(uint64_t) * (tiles + 2), "scan scratch"))) return cudaFree(d_off), rc;
+    if ((rc = dev_alloc((void **)&d_off, sizeof(uint64_t) * (S + 1), "row offsets", st))) return rc;
+    if ((rc = dev_alloc((void **)&d_tmp, sizeof(uint64_t) * (tiles + 2), "scan scratch", st)))
+        return dev_free(d_off, st), rc;
     int32_t *d_col = nullptr;
     uint32_t *d_cnt = nullptr;
     auto done = [&](int code) {
-        cudaFree(d_off);
-        cudaFree(d_tmp);
+        dev_free(d_off, st);
+        dev_free(d_tmp, st);
         if (!dev_out) {
-            cudaFree(d_col);
-            cudaFree(d_cnt);
+            dev_free(d_col, st);
+            dev_free(d_cnt, st);
         }
         return code;
     };
@@ -518,8 +533,8 @@ int ppr_sparse_rows(const ppr_result *rc_, int64_t *row_ptr, int32_t *col, uint3
             d_col = col;
             d_cnt = cnt;
         } else {
-            if ((rc = dev_alloc((void **)&d_col, sizeof(int32_t) * (total + 1), "compacted ids"))) return done(rc);
-            if ((rc = dev_alloc((void **)&d_cnt, sizeof(uint32_t) * (total + 1), "compacted counts"))) return done(rc);
+            if ((rc = dev_alloc((void **)&d_col, sizeof(int32_t) * (total + 1), "compacted ids", st))) return done(rc);
+            if ((rc = dev_alloc((void **)&d_cnt, sizeof(uint32_t) * (total + 1), "compacted counts", st))) return done(rc);
         }
         int blocks = (int)std::min<int64_t>((S + 7) / 8, (int64_t)r->ctx->sms * 32);
         if (blocks < 1) blocks = 1;
@@ -573,7 +588,7 @@ int ppr_dense(const ppr_result *r, uint32_t *out, uint32_t flags)
     const size_t bytes = sizeof(uint32_t) * (size_t)r->S * (size_t)n;
     const bool dev_out = (flags & PPR_PTRS_DEVICE) != 0;
     uint32_t *d = out;
-    if (!dev_out && (rc = dev_alloc((void **)&d, bytes, "dense counts"))) return rc;
+    if (!dev_out && (rc = dev_alloc((void **)&d, bytes, "dense counts", r->stream))) return rc;
     cudaError_t e = cudaMemsetAsync(d, 0, bytes, r->stream);
     int blocks = (int)std::min<int64_t>((r->S + 7) / 8, (int64_t)r->ctx->sms * 32);
     if (blocks < 1) blocks = 1;
@@ -583,7 +598,7 @@ int ppr_dense(const ppr_result *r, uint32_t *out, uint32_t flags)
     }
     if (e == cudaSuccess && !dev_out) e = cudaMemcpyAsync(out, d, bytes, cudaMemcpyDeviceToHost, r->stream);
     if (e == cudaSuccess) e = cudaStreamSynchronize(r->stream);
-    if (!dev_out) cudaFree(d);
+    if (!dev_out) dev_free(d, r->stream);
     if (e != cudaSuccess) return cuda_fail(e, "dense");
     return PPR_OK;
 }

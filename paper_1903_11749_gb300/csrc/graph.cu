@@ -223,20 +223,20 @@ int build_graph(ppr_ctx *ctx, int64_t n, int64_t m, const int64_t *row_ptr, cons
     const uint32_t *d_w = w;
     std::vector<void *> tmp;
     auto cleanup = [&]() {
-        for (void *p : tmp) cudaFree(p);
+        for (void *p : tmp) dev_free(p, st);
         tmp.clear();
     };
     int rc;
     if (!device_ptrs) {
         void *p;
-        if ((rc = dev_alloc(&p, sizeof(int64_t) * (n + 1), "row_ptr copy"))) return cleanup(), rc;
+        if ((rc = dev_alloc(&p, sizeof(int64_t) * (n + 1), "row_ptr copy", st))) return cleanup(), rc;
         tmp.push_back(p);
         d_rp = (const int64_t *)p;
         if (m > 0) {
-            if ((rc = dev_alloc(&p, sizeof(int32_t) * m, "col copy"))) return cleanup(), rc;
+            if ((rc = dev_alloc(&p, sizeof(int32_t) * m, "col copy", st))) return cleanup(), rc;
             tmp.push_back(p);
             d_col = (const int32_t *)p;
-            if ((rc = dev_alloc(&p, sizeof(uint32_t) * m, "w copy"))) return cleanup(), rc;
+            if ((rc = dev_alloc(&p, sizeof(uint32_t) * m, "w copy", st))) return cleanup(), rc;
             tmp.push_back(p);
             d_w = (const uint32_t *)p;
         }
@@ -250,7 +250,7 @@ int build_graph(ppr_ctx *ctx, int64_t n, int64_t m, const int64_t *row_ptr, cons
     int64_t *d_off = nullptr;
     if (g->instances > 0) {
         void *p;
-        if ((rc = dev_alloc(&p, sizeof(int64_t) * (g->instances + 1), "node_off"))) return cleanup(), rc;
+        if ((rc = dev_alloc(&p, sizeof(int64_t) * (g->instances + 1), "node_off", st))) return cleanup(), rc;
         tmp.push_back(p);
         d_off = (int64_t *)p;
         cudaError_t e = cudaMemcpyAsync(d_off, g->node_off.data(), sizeof(int64_t) * (g->instances + 1),
@@ -258,10 +258,10 @@ int build_graph(ppr_ctx *ctx, int64_t n, int64_t m, const int64_t *row_ptr, cons
         if (e != cudaSuccess) return cleanup(), cuda_fail(e, "node_off upload");
     }
     void *p;
-    if ((rc = dev_alloc(&p, sizeof(uint64_t) * n, "row totals"))) return cleanup(), rc;
+    if ((rc = dev_alloc(&p, sizeof(uint64_t) * n, "row totals", st))) return cleanup(), rc;
     tmp.push_back(p);
     uint64_t *d_W = (uint64_t *)p;
-    if ((rc = dev_alloc(&p, sizeof(BuildStats), "build stats"))) return cleanup(), rc;
+    if ((rc = dev_alloc(&p, sizeof(BuildStats), "build stats", st))) return cleanup(), rc;
     tmp.push_back(p);
     BuildStats *d_st = (BuildStats *)p;
     cudaError_t e = cudaMemsetAsync(d_st, 0, sizeof(BuildStats), st);
@@ -295,10 +295,10 @@ int build_graph(ppr_ctx *ctx, int64_t n, int64_t m, const int64_t *row_ptr, cons
     g->wide = hs.max_total >= (1ull << 32);
     g->max_degree = (int64_t)hs.max_degree;
     g->dangling = (int64_t)hs.dangling;
-    if ((rc = dev_alloc((void **)&g->node, sizeof(NodeRec) * n, "node records"))) return cleanup(), rc;
+    if ((rc = dev_alloc((void **)&g->node, sizeof(NodeRec) * n, "node records", st))) return cleanup(), rc;
     if (g->wide) {
         size_t edge_bytes = (size_t)m * sizeof(EdgeW);
-        if ((rc = dev_alloc(&g->edges, edge_bytes > 0 ? edge_bytes : 16, "edge records"))) return cleanup(), rc;
+        if ((rc = dev_alloc(&g->edges, edge_bytes > 0 ? edge_bytes : 16, "edge records", st))) return cleanup(), rc;
         g->device_bytes = (int64_t)(sizeof(NodeRec) * n + edge_bytes);
         k_rows_pass2<true><<<blocks, threads, 0, st>>>(n, d_rp, d_col, d_w, d_off, g->instances, d_W, g->node, g->edges);
     } else {
@@ -306,11 +306,11 @@ int build_graph(ppr_ctx *ctx, int64_t n, int64_t m, const int64_t *row_ptr, cons
         uint32_t *d_sizes;
         uint64_t *d_region, *d_scan;
         int64_t tiles = (n + kScanTile - 1) / kScanTile;
-        if ((rc = dev_alloc((void **)&d_sizes, sizeof(uint32_t) * n, "row sizes"))) return cleanup(), rc;
+        if ((rc = dev_alloc((void **)&d_sizes, sizeof(uint32_t) * n, "row sizes", st))) return cleanup(), rc;
         tmp.push_back(d_sizes);
-        if ((rc = dev_alloc((void **)&d_region, sizeof(uint64_t) * (n + 1), "row regions"))) return cleanup(), rc;
+        if ((rc = dev_alloc((void **)&d_region, sizeof(uint64_t) * (n + 1), "row regions", st))) return cleanup(), rc;
         tmp.push_back(d_region);
-        if ((rc = dev_alloc((void **)&d_scan, sizeof(uint64_t) * (tiles + 2), "scan scratch"))) return cleanup(), rc;
+        if ((rc = dev_alloc((void **)&d_scan, sizeof(uint64_t) * (tiles + 2), "scan scratch", st))) return cleanup(), rc;
         tmp.push_back(d_scan);
         int sblocks = (int)std::min<int64_t>((n + 255) / 256, (int64_t)ctx->sms * 16);
         k_row_records<<<sblocks, 256, 0, st>>>(n, d_rp, d_sizes);
@@ -324,7 +324,7 @@ int build_graph(ppr_ctx *ctx, int64_t n, int64_t m, const int64_t *row_ptr, cons
             return cleanup(), PPR_ERANGE;
         }
         size_t edge_bytes = (size_t)(slots > 0 ? slots : 2) * sizeof(EdgeN);
-        if ((rc = dev_alloc(&g->edges, edge_bytes, "edge records"))) return cleanup(), rc;
+        if ((rc = dev_alloc(&g->edges, edge_bytes, "edge records", st))) return cleanup(), rc;
         g->device_bytes = (int64_t)(sizeof(NodeRec) * n + edge_bytes);
         k_rows_pass2_blocked<<<blocks, threads, 0, st>>>(n, d_rp, d_col, d_w, d_off, g->instances, d_W, d_region,
                                                           g->node, (EdgeN *)g->edges);
@@ -560,22 +560,22 @@ __global__ void k_seg_write(RowView<E> G, int64_t n, uint32_t T, const uint64_t 
 int build_segments(ppr_graph *g, uint32_t T, cudaStream_t st)
 {
     if (g->seg.T == T && g->seg.node) return PPR_OK;
-    if (g->seg.node) cudaFree(g->seg.node);
-    if (g->seg.entries) cudaFree(g->seg.entries);
+    dev_free(g->seg.node, st);
+    dev_free(g->seg.entries, st);
     g->seg = SegCache{};
     const int64_t n = g->n;
     uint32_t *d_cnt = nullptr;
     uint64_t *d_off = nullptr, *d_tmp = nullptr;
     int rc;
     int64_t tiles = (n + kScanTile - 1) / kScanTile;
-    if ((rc = dev_alloc((void **)&d_cnt, sizeof(uint32_t) * n, "segment counts"))) return rc;
-    if ((rc = dev_alloc((void **)&d_off, sizeof(uint64_t) * (n + 1), "segment offsets"))) return cudaFree(d_cnt), rc;
-    if ((rc = dev_alloc((void **)&d_tmp, sizeof(uint64_t) * (tiles + 2), "scan scratch")))
-        return cudaFree(d_cnt), cudaFree(d_off), rc;
+    if ((rc = dev_alloc((void **)&d_cnt, sizeof(uint32_t) * n, "segment counts", st))) return rc;
+    if ((rc = dev_alloc((void **)&d_off, sizeof(uint64_t) * (n + 1), "segment offsets", st))) return dev_free(d_cnt, st), rc;
+    if ((rc = dev_alloc((void **)&d_tmp, sizeof(uint64_t) * (tiles + 2), "scan scratch", st)))
+        return dev_free(d_cnt, st), dev_free(d_off, st), rc;
     auto fail = [&](int code) {
-        cudaFree(d_cnt);
-        cudaFree(d_off);
-        cudaFree(d_tmp);
+        dev_free(d_cnt, st);
+        dev_free(d_off, st);
+        dev_free(d_tmp, st);
         return code;
     };
     const int wpb = 2;
@@ -597,9 +597,9 @@ int build_segments(ppr_graph *g, uint32_t T, cudaStream_t st)
     e = cudaMemcpyAsync(&total, d_off + n, sizeof(uint64_t), cudaMemcpyDeviceToHost, st);
     if (e == cudaSuccess) e = cudaStreamSynchronize(st);
     if (e != cudaSuccess) return fail(cuda_fail(e, "segment count"));
-    if ((rc = dev_alloc((void **)&g->seg.node, sizeof(NodeRec) * n, "segment node records"))) return fail(rc);
-    if ((rc = dev_alloc((void **)&g->seg.entries, sizeof(SegEntry) * (total > 0 ? total : 1), "segment tables"))) {
-        cudaFree(g->seg.node);
+    if ((rc = dev_alloc((void **)&g->seg.node, sizeof(NodeRec) * n, "segment node records", st))) return fail(rc);
+    if ((rc = dev_alloc((void **)&g->seg.entries, sizeof(SegEntry) * (total > 0 ? total : 1), "segment tables", st))) {
+        dev_free(g->seg.node, st);
         g->seg.node = nullptr;
         return fail(rc);
     }

@@ -21,8 +21,9 @@ int cuda_fail(cudaError_t e, const char *what);
         if (e_ != cudaSuccess) return ::ppr::cuda_fail(e_, #call);     \
     } while (0)
 
-// Device allocation that reports PPR_ENOMEM.
-int dev_alloc(void **p, size_t bytes, const char *what);
+// Stream-ordered device allocation (reports PPR_ENOMEM) and release.
+int dev_alloc(void **p, size_t bytes, const char *what, cudaStream_t st);
+void dev_free(void *p, cudaStream_t st);
 
 struct SegCache {
     uint32_t T = 0;               // threshold the tables were built for (0 = none)
@@ -41,6 +42,7 @@ struct ppr_ctx {
 
 struct ppr_graph {
     ppr_ctx *ctx = nullptr;
+    cudaStream_t stream = nullptr;  // stream the graph was built on
     int64_t n = 0, m = 0;
     int64_t max_degree = 0, dangling = 0;
     bool wide = false;

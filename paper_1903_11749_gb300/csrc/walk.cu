@@ -380,12 +380,12 @@ int launch_walks(ppr_ctx *ctx, const ppr_graph *g, const RunPlan &plan, ppr_resu
             }
             kp.nchunks = (uint32_t)chunks.size();
             void *d = nullptr;
-            if ((rc = dev_alloc(&d, sizeof(int4) * std::max<size_t>(chunks.size(), 1), "chunk table"))) return rc;
+            if ((rc = dev_alloc(&d, sizeof(int4) * std::max<size_t>(chunks.size(), 1), "chunk table", st))) return rc;
             r->scratch.push_back(d);
             PPR_CUDA(cudaMemcpyAsync(d, chunks.data(), sizeof(int4) * chunks.size(), cudaMemcpyHostToDevice, st));
             kp.chunks = (const int4 *)d;
             void *o = nullptr;
-            if ((rc = dev_alloc(&o, sizeof(int64_t) * (g->instances + 1), "instance offsets"))) return rc;
+            if ((rc = dev_alloc(&o, sizeof(int64_t) * (g->instances + 1), "instance offsets", st))) return rc;
             r->scratch.push_back(o);
             PPR_CUDA(cudaMemcpyAsync(o, off.data(), sizeof(int64_t) * (g->instances + 1), cudaMemcpyHostToDevice, st));
             kp.inst_off = (const int64_t *)o;
