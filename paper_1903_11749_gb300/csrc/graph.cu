@@ -208,8 +208,9 @@ __global__ void k_rows_pass2_blocked(int64_t n, const int64_t *row_ptr, const in
         if (lane == 0) {
             NodeRec r;
             r.word0 = pack_word0(reg, d, false);
-            // a single out-edge needs no draw-to-edge search: keep its target inline
-            r.total = (d == 1) ? (uint64_t)(uint32_t)(col[a] + base_id) : W[u];
+            // a single out-edge needs no draw-to-edge search: keep its target inline;
+            // otherwise W_u (< 2^32 here) with the row's summary shape above it
+            r.total = (d == 1) ? (uint64_t)(uint32_t)(col[a] + base_id) : pack_blocked_total(W[u], d);
             node[u] = r;
         }
     }

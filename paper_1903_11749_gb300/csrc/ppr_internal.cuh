@@ -5,7 +5,9 @@
 //     word0 = begin (bits 0..39) | count (bits 40..62) | segment flag (bit 63)
 //     word1 = W_u, the row's total weight (Sec. 2.1 routing denominator), or
 //             the target id when the row has exactly one edge (no search), or
-//             Q_v, the total fixed-point mass of a segment table (Algorithm 4)
+//             Q_v, the total fixed-point mass of a segment table (Algorithm 4);
+//             narrow blocked rows keep W_u in bits 0..31 and their summary
+//             size S (bits 32..55) and level count L (bits 56..59) above it
 //   plain rows:  begin/count index the edge-record array
 //   segment rows: begin/count index the segment-entry array
 //   EdgeN (8 B): {uint32 P, int32 col}  -- narrow layout, every W_u < 2^32
@@ -221,52 +223,61 @@ __device__ __forceinline__ typename E::Rec search_serial_tally(const E &edges, u
     return edges.load(lo);
 }
 
-__device__ __forceinline__ uint32_t count_le(uint4 k, uint32_t x)
+// One 32-byte sector in a single 256-bit load (sm_100+ vector width).
+struct Sector {
+    uint32_t v[8];
+};
+__device__ __forceinline__ Sector ld_sector(const void *p)
 {
-    return (uint32_t)(k.x <= x) + (uint32_t)(k.y <= x) + (uint32_t)(k.z <= x) + (uint32_t)(k.w <= x);
+    Sector s;
+    asm("ld.global.nc.v8.u32 {%0,%1,%2,%3,%4,%5,%6,%7}, [%8];"
+                 : "=r"(s.v[0]), "=r"(s.v[1]), "=r"(s.v[2]), "=r"(s.v[3]), "=r"(s.v[4]), "=r"(s.v[5]), "=r"(s.v[6]),
+                   "=r"(s.v[7])
+                 : "l"(p));
+    return s;
 }
 
-// Search of a blocked narrow row (layout above): returns the target of the
-// first edge with P > x.  TALLY counts the 32-byte sectors read.
-template <bool TALLY>
-__device__ __forceinline__ uint32_t search_blocked(const EdgeN *E, uint64_t begin, uint32_t d, uint32_t x,
-                                                   uint32_t &sectors)
+__host__ __device__ __forceinline__ uint64_t pack_blocked_total(uint64_t W, uint32_t d)
 {
-    const uint32_t L = tree_levels(d);
-    uint32_t S = 0;
-    for (uint32_t l = 1; l <= L; ++l) S += level_sectors(d, l);
-    const uint4 *base = reinterpret_cast<const uint4 *>(E + begin);  // sector-aligned
+    return W | ((uint64_t)summary_sectors(d) << 32) | ((uint64_t)tree_levels(d) << 56);
+}
+
+// Search of a blocked narrow row (layout above) whose region starts at record
+// `begin`, with S summary sectors over L levels: the target of the first edge
+// with P > x.  TALLY counts the 32-byte sectors read.
+template <bool TALLY>
+__device__ __forceinline__ uint32_t search_blocked(const EdgeN *E, uint64_t begin, uint32_t d, uint32_t S, uint32_t L,
+                                                   uint32_t x, uint32_t &sectors)
+{
+    const unsigned char *base = reinterpret_cast<const unsigned char *>(E + begin);  // sector-aligned
     uint32_t b = 0, off = 0;
     for (uint32_t l = L; l >= 1; --l) {
-        const uint4 *p = base + 2ull * (off + b);
-        const uint4 k0 = __ldg(p), k1 = __ldg(p + 1);
-        const uint32_t c = count_le(k0, x) + count_le(k1, x);
+        const Sector k = ld_sector(base + 32ull * (off + b));
+        uint32_t c = 0;
+#pragma unroll
+        for (int i = 0; i < 8; ++i) c += (uint32_t)(k.v[i] <= x);
         off += level_sectors(d, l);
         b = b * 8 + c;
         if (TALLY) ++sectors;
     }
     const uint32_t len = min(8u, d - 8 * b);
-    const uint4 *q = base + 2ull * (S + 2 * b);  // 8-record block b
-    const uint4 r0 = __ldg(q), r1 = __ldg(q + 1);
-    uint4 r2 = make_uint4(0xffffffffu, 0, 0xffffffffu, 0), r3 = r2;
-    if (len > 4) {
-        r2 = __ldg(q + 2);
-        r3 = __ldg(q + 3);
+    const unsigned char *q = base + 32ull * (S + 2 * b);  // 8-record block b: (P, col) pairs
+    const Sector r0 = ld_sector(q);
+    Sector r1;
+    if (len > 4) r1 = ld_sector(q + 32);
+    else {
+#pragma unroll
+        for (int i = 0; i < 8; ++i) r1.v[i] = 0xffffffffu;
     }
     if (TALLY) sectors += len > 4 ? 2 : 1;
-    // records are (P, col) pairs: keys in .x/.z, targets in .y/.w
-    const uint32_t c = (uint32_t)(r0.x <= x) + (uint32_t)(r0.z <= x) + (uint32_t)(r1.x <= x) + (uint32_t)(r1.z <= x) +
-                       (uint32_t)(r2.x <= x) + (uint32_t)(r2.z <= x) + (uint32_t)(r3.x <= x) + (uint32_t)(r3.z <= x);
-    uint32_t t;
-    switch (c) {
-    case 0: t = r0.y; break;
-    case 1: t = r0.w; break;
-    case 2: t = r1.y; break;
-    case 3: t = r1.w; break;
-    case 4: t = r2.y; break;
-    case 5: t = r2.w; break;
-    case 6: t = r3.y; break;
-    default: t = r3.w; break;
+    uint32_t c = 0;
+#pragma unroll
+    for (int i = 0; i < 4; ++i) c += (uint32_t)(r0.v[2 * i] <= x) + (uint32_t)(r1.v[2 * i] <= x);
+    uint32_t t = r1.v[7];
+#pragma unroll
+    for (int i = 6; i >= 0; --i) {
+        const uint32_t cand = i < 4 ? r0.v[2 * i + 1] : r1.v[2 * (i - 4) + 1];
+        if (c == (uint32_t)i) t = cand;
     }
     return t;
 }

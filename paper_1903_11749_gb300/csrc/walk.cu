@@ -72,7 +72,8 @@ __device__ __forceinline__ bool walk_step(const KParams &p, const E &edges, bool
     const uint64_t r64 = (uint64_t)x.x | ((uint64_t)x.y << 32);
     uint64_t xr = 0;
     if (act && (cnt > 1 || segf)) {
-        if (segf || total >= (1ull << 32)) xr = mulhi64(r64, total);
+        // narrow rows hold the summary shape above bit 32 (W < 2^32 there)
+        if (segf || sizeof(typename E::Rec) != 8) xr = mulhi64(r64, total);
         else xr = mulhi64_by32(x.x, x.y, (uint32_t)total);
     }
     uint32_t next = 0;
@@ -115,7 +116,8 @@ __device__ __forceinline__ bool walk_step(const KParams &p, const E &edges, bool
         next = (uint32_t)total;  // single out-edge: target kept in the node record
     } else if (!big) {
         if constexpr (sizeof(typename E::Rec) == 8) {
-            next = search_blocked<STATS>(edges.e, beg, cnt, (uint32_t)xr, tl.sectors);
+            next = search_blocked<STATS>(edges.e, beg, cnt, (uint32_t)(total >> 32) & 0xffffffu, (uint32_t)(total >> 56),
+                                         (uint32_t)xr, tl.sectors);
         } else {
             next = E::target(STATS ? search_serial_tally(edges, beg, cnt, xr, tl.sectors) : search_serial(edges, beg, cnt, xr));
         }
@@ -160,7 +162,7 @@ __device__ __forceinline__ void warp_add_tally(unsigned long long *dst, const Ta
 
 // ------------------------------------------------------------ plain (K4) ----
 #ifndef PPR_WALK_MINB
-#define PPR_WALK_MINB 8  // resident 256-thread blocks per SM asked of ptxas (8: 32 registers, 64 warps)
+#define PPR_WALK_MINB 6  // resident 256-thread blocks per SM asked of ptxas (6: 40 registers, no spills)
 #endif
 
 template <class E, bool SEG, bool STATS>
