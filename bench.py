@@ -271,6 +271,7 @@ def main():
     torch.cuda.synchronize(dev)
     clocks = Clocks(local, None)
     clocks.start()
+    launches0 = ppr.kernel_launches()
     for _ in range(args.steps):
         flush.fill_(1)  # L2 flush outside the timed events
         e0 = torch.cuda.Event(enable_timing=True)
@@ -284,6 +285,7 @@ def main():
         kernel_ms.append(r.info().kernel_ms)
         del r, G
     torch.cuda.synchronize(dev)
+    launches = ppr.kernel_launches() - launches0
     clk = clocks.stop()
     T = sum(step_ms) / 1e3
     t_tensor = torch.tensor([T], dtype=torch.float64, device=dev)
@@ -363,7 +365,7 @@ def main():
                            "l2": "flushed between steps (512 MB write)"},
                 "walks_per_s": walks_s, "steps_per_walk": steps_per_pass / max(walks_per_pass, 1),
                 "roofline": roofline, "cpu_baseline": cpu, "e2e": e2e, "plain_kernel": plain,
-                "gpu_launches": 3 * args.steps, "clocks": clk}
+                "gpu_launches": launches, "clocks": clk}
         print(json.dumps(line))
     if world > 1:
         dist.destroy_process_group()

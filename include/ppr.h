@@ -83,6 +83,10 @@ uint32_t ppr_alpha_threshold(double alpha);
  * Owned by the library; valid until the next call on this thread. */
 const char *ppr_last_error(void);
 
+/* Number of CUDA kernels this library has launched in the process so far
+ * (all contexts).  Needs no GPU. */
+int64_t ppr_kernel_launches(void);
+
 /* Creates a context on CUDA device `device`; *out receives it.
  * PPR_ECUDA if the device cannot be used. */
 int ppr_create(int device, ppr_ctx **out);

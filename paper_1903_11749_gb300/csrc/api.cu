@@ -12,8 +12,11 @@
 #include "ppr_host.h"
 #include "scan.cuh"
 
+#include <atomic>
+
 namespace {
 thread_local char g_err[512] = "";
+std::atomic<long long> g_launches{0};
 }
 
 namespace ppr {
@@ -25,6 +28,8 @@ void set_error(const char *fmt, ...)
     vsnprintf(g_err, sizeof(g_err), fmt, ap);
     va_end(ap);
 }
+
+void note_launch() { g_launches.fetch_add(1, std::memory_order_relaxed); }
 
 int cuda_fail(cudaError_t e, const char *what)
 {
@@ -106,6 +111,8 @@ uint32_t ppr_alpha_threshold(double alpha)
 }
 
 const char *ppr_last_error(void) { return g_err; }
+
+int64_t ppr_kernel_launches(void) { return (int64_t)g_launches.load(); }
 
 int ppr_create(int device, ppr_ctx **out)
 {
@@ -539,6 +546,7 @@ int ppr_sparse_rows(const ppr_result *rc_, int64_t *row_ptr, int32_t *col, uint3
         int blocks = (int)std::min<int64_t>((S + 7) / 8, (int64_t)r->ctx->sms * 32);
         if (blocks < 1) blocks = 1;
         k_compact_rows<<<blocks, 256, 0, st>>>(S, r->cap, r->d_nnz, d_off, r->d_cols, r->d_cnts, d_col, d_cnt);
+        note_launch();
         e = cudaGetLastError();
         if (e == cudaSuccess && !dev_out && total > 0) {
             e = cudaMemcpyAsync(col, d_col, sizeof(int32_t) * total, cudaMemcpyDeviceToHost, st);
@@ -594,6 +602,7 @@ int ppr_dense(const ppr_result *r, uint32_t *out, uint32_t flags)
     if (blocks < 1) blocks = 1;
     if (e == cudaSuccess) {
         k_dense<<<blocks, 256, 0, r->stream>>>(r->S, n, r->cap, r->d_nnz, r->d_cols, r->d_cnts, d);
+        note_launch();
         e = cudaGetLastError();
     }
     if (e == cudaSuccess && !dev_out) e = cudaMemcpyAsync(out, d, bytes, cudaMemcpyDeviceToHost, r->stream);

@@ -273,6 +273,7 @@ int build_graph(ppr_ctx *ctx, int64_t n, int64_t m, const int64_t *row_ptr, cons
     int blocks = (int)std::min<int64_t>(want_blocks, (int64_t)ctx->sms * 64);
     if (blocks < 1) blocks = 1;
     k_rows_pass1<<<blocks, threads, 0, st>>>(n, m, d_rp, d_col, d_w, d_off, g->instances, d_W, d_st);
+    note_launch();
     BuildStats hs;
     e = cudaMemcpyAsync(&hs, d_st, sizeof(BuildStats), cudaMemcpyDeviceToHost, st);
     if (e == cudaSuccess) e = cudaStreamSynchronize(st);
@@ -302,6 +303,7 @@ int build_graph(ppr_ctx *ctx, int64_t n, int64_t m, const int64_t *row_ptr, cons
         if ((rc = dev_alloc(&g->edges, edge_bytes > 0 ? edge_bytes : 16, "edge records", st))) return cleanup(), rc;
         g->device_bytes = (int64_t)(sizeof(NodeRec) * n + edge_bytes);
         k_rows_pass2<true><<<blocks, threads, 0, st>>>(n, d_rp, d_col, d_w, d_off, g->instances, d_W, g->node, g->edges);
+        note_launch();
     } else {
         // blocked rows: record slots per row, their offsets, then the rows
         uint32_t *d_sizes;
@@ -315,6 +317,7 @@ int build_graph(ppr_ctx *ctx, int64_t n, int64_t m, const int64_t *row_ptr, cons
         tmp.push_back(d_scan);
         int sblocks = (int)std::min<int64_t>((n + 255) / 256, (int64_t)ctx->sms * 16);
         k_row_records<<<sblocks, 256, 0, st>>>(n, d_rp, d_sizes);
+        note_launch();
         exclusive_scan_u32(d_sizes, n, d_region, d_scan, st);
         uint64_t slots = 0;
         e = cudaMemcpyAsync(&slots, d_region + n, sizeof(uint64_t), cudaMemcpyDeviceToHost, st);
@@ -329,6 +332,7 @@ int build_graph(ppr_ctx *ctx, int64_t n, int64_t m, const int64_t *row_ptr, cons
         g->device_bytes = (int64_t)(sizeof(NodeRec) * n + edge_bytes);
         k_rows_pass2_blocked<<<blocks, threads, 0, st>>>(n, d_rp, d_col, d_w, d_off, g->instances, d_W, d_region,
                                                           g->node, (EdgeN *)g->edges);
+                                                          note_launch();
     }
     e = cudaGetLastError();
     if (e == cudaSuccess) e = cudaStreamSynchronize(st);
@@ -588,10 +592,12 @@ int build_segments(ppr_graph *g, uint32_t T, cudaStream_t st)
         RowView<WideEdges> G{g->node, WideEdges{(const EdgeW *)g->edges}};
         cudaFuncSetAttribute(k_seg_count<WideEdges>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
         k_seg_count<WideEdges><<<blocks, wpb * 32, smem, st>>>(G, n, T, d_cnt);
+        note_launch();
     } else {
         RowView<NarrowEdges> G{g->node, NarrowEdges{(const EdgeN *)g->edges}};
         cudaFuncSetAttribute(k_seg_count<NarrowEdges>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
         k_seg_count<NarrowEdges><<<blocks, wpb * 32, smem, st>>>(G, n, T, d_cnt);
+        note_launch();
     }
     exclusive_scan_u32(d_cnt, n, d_off, d_tmp, st);
     uint64_t total = 0;
@@ -608,10 +614,12 @@ int build_segments(ppr_graph *g, uint32_t T, cudaStream_t st)
         RowView<WideEdges> G{g->node, WideEdges{(const EdgeW *)g->edges}};
         cudaFuncSetAttribute(k_seg_write<WideEdges>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
         k_seg_write<WideEdges><<<blocks, wpb * 32, smem, st>>>(G, n, T, d_off, g->seg.entries, g->seg.node);
+        note_launch();
     } else {
         RowView<NarrowEdges> G{g->node, NarrowEdges{(const EdgeN *)g->edges}};
         cudaFuncSetAttribute(k_seg_write<NarrowEdges>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
         k_seg_write<NarrowEdges><<<blocks, wpb * 32, smem, st>>>(G, n, T, d_off, g->seg.entries, g->seg.node);
+        note_launch();
     }
     e = cudaGetLastError();
     if (e == cudaSuccess) e = cudaStreamSynchronize(st);

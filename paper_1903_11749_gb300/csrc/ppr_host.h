@@ -13,6 +13,7 @@
 namespace ppr {
 
 void set_error(const char *fmt, ...);
+void note_launch();  // counts every kernel launch of the library (ppr_kernel_launches)
 int cuda_fail(cudaError_t e, const char *what);
 
 #define PPR_CUDA(call)                                                 \

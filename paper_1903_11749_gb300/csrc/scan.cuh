@@ -8,6 +8,8 @@
 
 namespace ppr {
 
+void note_launch();
+
 constexpr int kScanThreads = 512;
 constexpr int kScanItems = 8;
 constexpr int kScanTile = kScanThreads * kScanItems;
@@ -102,8 +104,11 @@ inline void exclusive_scan_u32(const uint32_t *in, int64_t n, uint64_t *out, uin
         return;
     }
     k_scan_tile_sums<<<(unsigned)tiles, kScanThreads, 0, st>>>(in, n, tmp);
+    note_launch();
     k_scan_tile_offsets<<<1, 1024, 0, st>>>(tmp, tiles, tmp + tiles);
+    note_launch();
     k_scan_apply<<<(unsigned)tiles, kScanThreads, 0, st>>>(in, n, tmp, out);
+    note_launch();
 }
 
 }  // namespace ppr

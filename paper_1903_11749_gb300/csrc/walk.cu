@@ -40,6 +40,8 @@ struct KParams {
     unsigned long long *queue;
     unsigned long long *steps;    // [0] draws consumed, [2] algorithmic sectors (statistics launch)
     uint32_t P2;              // next_pow2(R)
+    uint64_t r_magic;         // ceil(2^40 / R): walk index -> source index by multiply-shift
+    int32_t fuse;             // persistent kernel aggregates finished chunks itself
 };
 
 // One step of one walk.  Returns true when the walk has ended (end is set).
@@ -200,41 +202,52 @@ __global__ void __launch_bounds__(128) k_aggregate(KParams p)
 // ------------------------------------------------------- persistent (K5) ----
 // Persistent warps.  Each warp pulls chunks of sources from a global queue
 // (one atomic per chunk) and keeps all 32 lanes busy: a lane whose walk ends
-// takes the next walk of the chunk at once, so a warp never waits for the
-// longest of 32 geometric walk lengths (the paper's pipelines keep the
+// takes the next walk of the newest chunk at once, so a warp never waits for
+// the longest of 32 geometric walk lengths (the paper's pipelines keep the
 // cluster busy the same way: new walks start while old ones finish).  Steps
-// run in lockstep; a row longer than p.large is searched by the whole warp
-// (search_warp) instead of by one lane's bisection, which shortens the
-// dependent-load chain the warp waits on.  Endpoints go to the per-walk
-// buffer and k_aggregate reduces them per source.  No shared memory is used
-// for walking, leaving the whole L1 to cache node records and probes.
-struct WarpQueue {
-    uint32_t base, nsrc, ctr_base, tag;  // current chunk
-    uint32_t issued, total;
+// run in lockstep; a row longer than p.large can be searched by the whole
+// warp (search_warp).  Endpoints go to the per-walk buffer; a warp tracks up
+// to kRing chunks in flight and, when the last walk of a chunk ends (and
+// p.fuse is set), reduces that chunk's sources itself in a small shared
+// sort buffer (aggregate_source) while the other warps keep walking.
+struct ChunkSlot {
+    uint32_t base, nsrc, ctr_base, tag, total, issued, done, live;
 };
+constexpr int kRing = 4;
+
+__device__ __forceinline__ uint32_t div_by_R(uint32_t w, uint64_t magic)
+{
+    return (uint32_t)(((uint64_t)w * magic) >> 40);  // exact for w < 2^20, R <= 4096
+}
 
 template <class E, bool SEG, bool STATS>
 __global__ void __launch_bounds__(256, PPR_WALK_MINB) k_walk_persistent(KParams p)
 {
-    __shared__ WarpQueue wq_all[8];
+    extern __shared__ __align__(16) unsigned char smem_raw[];
     const uint32_t lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
-    WarpQueue &wq = wq_all[wid];
+    const size_t per_warp = sizeof(ChunkSlot) * kRing + (p.fuse ? (size_t)p.P2 * 12 : 0);
+    unsigned char *mine = smem_raw + per_warp * wid;
+    ChunkSlot *ring = reinterpret_cast<ChunkSlot *>(mine);
+    uint64_t *keys = reinterpret_cast<uint64_t *>(mine + sizeof(ChunkSlot) * kRing);
+    uint32_t *sortbuf = reinterpret_cast<uint32_t *>(keys + p.P2);
     const E edges = make_edges<E>(p.edges);
-    if (lane == 0) {
-        wq.issued = 0;
-        wq.total = 0;
-    }
+    if (lane < kRing) ring[lane].live = 0;
     __syncwarp();
+    int cur = -1;
     bool queue_empty = false;
     bool active = false;
+    uint32_t rs = 0;  // ring slot of the lane's walk
     uint32_t src = 0, sctr = 0, j = 0, k = 0, u = 0, tag = 0, ctr_base = 0;
-    uint64_t slot = 0;  // endpoint index (output row * R + j)
+    uint64_t slot = 0;  // endpoint index: (src - s_begin) * R + j
     Tally tl;
 
     for (;;) {
+        // ---- refill idle lanes from the newest chunk, opening chunks as needed
         uint32_t idle = __ballot_sync(0xffffffffu, !active);
         while (idle && !queue_empty) {
-            if (wq.issued == wq.total) {
+            if (cur < 0 || ring[cur].issued == ring[cur].total) {
+                const int nxt = cur < 0 ? 0 : (cur + 1) % kRing;
+                if (ring[nxt].live) break;  // every ring slot still has walks in flight
                 unsigned long long c = 0;
                 if (lane == 0) c = atomicAdd(p.queue, 1ull);
                 c = __shfl_sync(0xffffffffu, c, 0);
@@ -243,52 +256,102 @@ __global__ void __launch_bounds__(256, PPR_WALK_MINB) k_walk_persistent(KParams 
                     break;
                 }
                 if (lane == 0) {
+                    ChunkSlot cs;
                     if (p.chunks) {
                         int4 d = p.chunks[c];
-                        wq.base = (uint32_t)d.x;
-                        wq.nsrc = (uint32_t)d.y;
-                        wq.ctr_base = (uint32_t)p.inst_off[d.z];
-                        wq.tag = (uint32_t)d.z;
+                        cs.base = (uint32_t)d.x;
+                        cs.nsrc = (uint32_t)d.y;
+                        cs.ctr_base = (uint32_t)p.inst_off[d.z];
+                        cs.tag = (uint32_t)d.z;
                     } else {
                         int64_t b = p.s_begin + (int64_t)c * p.CS;
-                        wq.base = (uint32_t)b;
-                        wq.nsrc = (uint32_t)std::min<int64_t>((int64_t)p.CS, p.s_end - b);
-                        wq.ctr_base = 0;
-                        wq.tag = p.tag;
+                        cs.base = (uint32_t)b;
+                        cs.nsrc = (uint32_t)std::min<int64_t>((int64_t)p.CS, p.s_end - b);
+                        cs.ctr_base = 0;
+                        cs.tag = p.tag;
                     }
-                    wq.issued = 0;
-                    wq.total = wq.nsrc * p.R;
+                    cs.total = cs.nsrc * p.R;
+                    cs.issued = 0;
+                    cs.done = 0;
+                    cs.live = 1;
+                    ring[nxt] = cs;
                 }
                 __syncwarp();
+                cur = nxt;
             }
-            const uint32_t issued = wq.issued;
-            const uint32_t take = min(wq.total - issued, (uint32_t)__popc(idle));
+            const uint32_t issued = ring[cur].issued;
+            const uint32_t take = min(ring[cur].total - issued, (uint32_t)__popc(idle));
             const uint32_t rank = __popc(idle & ((1u << lane) - 1));
             if (((idle >> lane) & 1) && rank < take) {
                 const uint32_t w = issued + rank;
-                const uint32_t i = w / p.R;
+                const uint32_t i = div_by_R(w, p.r_magic);
                 j = w - i * p.R;
-                src = wq.base + i;
-                ctr_base = wq.ctr_base;
+                src = ring[cur].base + i;
+                ctr_base = ring[cur].ctr_base;
                 sctr = src - ctr_base;
-                tag = wq.tag;
+                tag = ring[cur].tag;
+                rs = (uint32_t)cur;
                 slot = ((uint64_t)((int64_t)src - p.s_begin)) * p.R + j;
                 k = 0;
                 u = src;
                 active = true;
             }
             __syncwarp();
-            if (lane == 0) wq.issued = issued + take;
+            if (lane == 0) ring[cur].issued = issued + take;
             __syncwarp();
             idle = __ballot_sync(0xffffffffu, !active);
         }
-        if (__ballot_sync(0xffffffffu, active) == 0) break;  // queue drained and every walk done
+        const bool any_active = __any_sync(0xffffffffu, active);
 
-        uint32_t end = 0;
-        if (walk_step<E, SEG, true, STATS>(p, edges, active, src, sctr, j, tag, k, u, end, tl)) {
-            p.ends[slot] = end - ctr_base;
-            active = false;
+        // ---- one step of every active walk
+        bool fin = false;
+        if (any_active) {
+            uint32_t end = 0;
+            fin = walk_step<E, SEG, true, STATS>(p, edges, active, src, sctr, j, tag, k, u, end, tl);
+            if (fin) {
+                p.ends[slot] = end - ctr_base;
+                active = false;
+            }
         }
+        if (p.fuse && (__any_sync(0xffffffffu, fin) || !any_active)) {
+            // per-slot completion counts, then reduce every chunk whose walks are all done
+            uint32_t add[kRing];
+#pragma unroll
+            for (int r = 0; r < kRing; ++r) add[r] = __popc(__ballot_sync(0xffffffffu, fin && rs == (uint32_t)r));
+            __syncwarp();
+            if (lane == 0) {
+#pragma unroll
+                for (int r = 0; r < kRing; ++r) ring[r].done += add[r];
+            }
+            __syncwarp();
+#pragma unroll 1
+            for (int r = 0; r < kRing; ++r) {
+                const ChunkSlot cs = ring[r];
+                if (cs.live && cs.done == cs.total && cs.issued == cs.total) {
+                    for (uint32_t i = 0; i < cs.nsrc; ++i) {
+                        const uint64_t row = (uint64_t)((int64_t)(cs.base + i) - p.s_begin);
+                        aggregate_source(p.ends + row * p.R, p.R, sortbuf, keys, p.out, (uint64_t)p.out_row0 + row);
+                    }
+                    __syncwarp();
+                    if (lane == 0) ring[r].live = 0;
+                    __syncwarp();
+                }
+            }
+        }
+        if (!any_active && queue_empty) {
+            bool live = false;
+#pragma unroll
+            for (int r = 0; r < kRing; ++r) live |= ring[r].live && p.fuse;
+            if (!live) break;
+        }
+        if (!p.fuse && lane == 0) {
+            // without the fused reduction a slot only feeds lanes: it is free
+            // again as soon as all its walks are issued
+#pragma unroll
+            for (int r = 0; r < kRing; ++r)
+                if (ring[r].live && ring[r].issued == ring[r].total) ring[r].live = 0;
+        }
+        __syncwarp();
     }
     warp_add_tally<STATS>(p.steps, tl);
 }
@@ -303,6 +366,7 @@ static int launch_aggregate(ppr_ctx *ctx, const KParams &kp, int64_t S, cudaStre
     int ablocks = (int)std::min<int64_t>((S + aw - 1) / aw, (int64_t)ctx->sms * 16);
     if (ablocks < 1) ablocks = 1;
     k_aggregate<<<ablocks, aw * 32, smem, st>>>(kp);
+    note_launch();
     PPR_CUDA(cudaGetLastError());
     return PPR_OK;
 }
@@ -315,18 +379,22 @@ static int launch_typed(ppr_ctx *ctx, const KParams &kp, const RunPlan &plan, in
         int blocks = (int)std::min<uint64_t>((total + 255) / 256, (uint64_t)ctx->sms * 64);
         if (blocks < 1) blocks = 1;
         k_walk_plain<E, SEG, STATS><<<blocks, 256, 0, st>>>(kp);
+        note_launch();
         PPR_CUDA(cudaGetLastError());
         return launch_aggregate(ctx, kp, S, st);
     }
+    const size_t smem = 8 * (sizeof(ChunkSlot) * kRing + (kp.fuse ? (size_t)kp.P2 * 12 : 0));
+    PPR_CUDA(cudaFuncSetAttribute(k_walk_persistent<E, SEG, STATS>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
     int per_sm = 0;
-    PPR_CUDA(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_walk_persistent<E, SEG, STATS>, 256, 0));
+    PPR_CUDA(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_walk_persistent<E, SEG, STATS>, 256, smem));
     if (per_sm < 1) per_sm = 1;
     int64_t blocks = (int64_t)ctx->sms * per_sm;
     int64_t needed = ((int64_t)kp.nchunks + 7) / 8;
     if (blocks > needed) blocks = std::max<int64_t>(needed, 1);
-    k_walk_persistent<E, SEG, STATS><<<(unsigned)blocks, 256, 0, st>>>(kp);
+    k_walk_persistent<E, SEG, STATS><<<(unsigned)blocks, 256, smem, st>>>(kp);
+    note_launch();
     PPR_CUDA(cudaGetLastError());
-    return launch_aggregate(ctx, kp, S, st);
+    return kp.fuse ? PPR_OK : launch_aggregate(ctx, kp, S, st);
 }
 
 int launch_walks(ppr_ctx *ctx, const ppr_graph *g, const RunPlan &plan, ppr_result *r, int64_t s_begin,
@@ -361,6 +429,9 @@ int launch_walks(ppr_ctx *ctx, const ppr_graph *g, const RunPlan &plan, ppr_resu
     uint32_t P2 = 1;
     while (P2 < plan.R) P2 <<= 1;
     kp.P2 = P2;
+    kp.r_magic = ((1ull << 40) + plan.R - 1) / plan.R;
+    // fused reduction needs next_pow2(R) * 12 bytes of shared memory per warp
+    kp.fuse = (plan.kernel == PPR_KERNEL_PERSISTENT && P2 <= 256) ? 1 : 0;
     int rc;
 
     std::vector<int4> chunks;
@@ -370,7 +441,7 @@ int launch_walks(ppr_ctx *ctx, const ppr_graph *g, const RunPlan &plan, ppr_resu
             return PPR_ENOTSUP;
         }
     } else {
-        uint32_t CS = plan.chunk_sources > 0 ? (uint32_t)plan.chunk_sources : std::max(1u, 1024u / plan.R);
+        uint32_t CS = plan.chunk_sources > 0 ? (uint32_t)plan.chunk_sources : std::max(1u, 400u / plan.R);
         kp.CS = CS;
         if (g->instances > 0) {
             // chunks never cross an instance boundary

@@ -52,6 +52,7 @@ _SIGS = {
     "ppr_version": (C.c_int, []),
     "ppr_alpha_threshold": (C.c_uint32, [C.c_double]),
     "ppr_last_error": (C.c_char_p, []),
+    "ppr_kernel_launches": (C.c_int64, []),
     "ppr_create": (C.c_int, [C.c_int, C.POINTER(C.c_void_p)]),
     "ppr_destroy": (None, [C.c_void_p]),
     "ppr_device_sms": (C.c_int, [C.c_void_p]),
@@ -93,6 +94,10 @@ def lib():
 def _check(rc: int):
     if rc != PPR_OK:
         raise PPRError(rc, lib().ppr_last_error().decode(errors="replace"))
+
+
+def kernel_launches() -> int:
+    return int(lib().ppr_kernel_launches())
 
 
 def alpha_threshold(alpha: float) -> int:
