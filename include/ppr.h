@@ -165,6 +165,8 @@ typedef struct {
     int64_t max_batch_sources;/* sources per device batch, 0 = sized to free device memory */
     int32_t stats;       /* 1: also count the algorithmic 32-byte sectors of every step (slower;
                             rows, counts and steps are unchanged) */
+    int32_t fused_aggregation; /* 1: persistent warps reduce their finished chunks themselves
+                                  (R <= 256); 0: a separate reduction kernel (default) */
     void *stream;        /* cudaStream_t, NULL = legacy default stream */
 } ppr_run_args;
 

@@ -36,6 +36,7 @@ __device__ __forceinline__ int32_t instance_of(const int64_t *node_off, int32_t 
     return lo;
 }
 
+// Wide layout (some row total >= 2^32), two passes.
 // Pass 1: one warp per row.  Validates the CSR, sums the row weights.
 __global__ void k_rows_pass1(int64_t n, int64_t m, const int64_t *row_ptr, const int32_t *col,
                              const uint32_t *w, const int64_t *node_off, int32_t count, uint64_t *W,
@@ -131,89 +132,392 @@ __global__ void k_rows_pass2(int64_t n, const int64_t *row_ptr, const int32_t *c
     }
 }
 
-// Record slots of each blocked row (narrow layout).
-__global__ void k_row_records(int64_t n, const int64_t *row_ptr, uint32_t *sizes)
+// ----------------------------------------------------- single-pass build ----
+// The narrow (32-bit prefix) layout is built in one validating pass over the
+// input: k_layout checks row_ptr and sizes every blocked row; after the scan
+// of those sizes, k_build_small builds every row of at most 32 edges with one
+// thread, and queues longer rows for k_build_mid (one warp per row) and
+// k_build_big (one block per row).  A row total >= 2^32 sets kWide and the
+// graph is rebuilt in the wide layout.
+enum : uint32_t { kWide = 8u, kBigDegree = 16u };
+constexpr uint32_t kSmallRow = 32, kMidRow = 8192;
+
+struct LayoutStats {
+    unsigned long long max_degree;
+    unsigned long long dangling;
+    unsigned int status;
+    unsigned int n_mid, n_big;
+};
+
+__device__ __forceinline__ void block_stats(LayoutStats *st, uint32_t deg_max, uint32_t dang, uint32_t flags)
 {
-    for (int64_t u = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; u < n; u += (int64_t)gridDim.x * blockDim.x)
-        sizes[u] = blocked_row_records((uint32_t)(row_ptr[u + 1] - row_ptr[u]));
+    __shared__ uint32_t s_max, s_dang, s_flags;
+    if (threadIdx.x == 0) {
+        s_max = 0;
+        s_dang = 0;
+        s_flags = 0;
+    }
+    __syncthreads();
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) {
+        deg_max = max(deg_max, __shfl_xor_sync(0xffffffffu, deg_max, o));
+        dang += __shfl_xor_sync(0xffffffffu, dang, o);
+        flags |= __shfl_xor_sync(0xffffffffu, flags, o);
+    }
+    if ((threadIdx.x & 31) == 0) {
+        atomicMax(&s_max, deg_max);
+        atomicAdd(&s_dang, dang);
+        atomicOr(&s_flags, flags);
+    }
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        if (s_max) atomicMax(&st->max_degree, (unsigned long long)s_max);
+        if (s_dang) atomicAdd(&st->dangling, (unsigned long long)s_dang);
+        if (s_flags) atomicOr(&st->status, s_flags);
+    }
 }
 
-// Pass 2, narrow layout: one warp per row writes the edge records of a
-// blocked row (inclusive prefix by warp scan), the padding, and the summary
-// levels; then the node record.
-__global__ void k_rows_pass2_blocked(int64_t n, const int64_t *row_ptr, const int32_t *col, const uint32_t *w,
-                                     const int64_t *node_off, int32_t count, const uint64_t *W, const uint64_t *region,
-                                     NodeRec *node, EdgeN *E)
+__global__ void __launch_bounds__(256) k_layout(int64_t n, int64_t m, const int64_t *row_ptr, uint32_t *sizes,
+                                                LayoutStats *st)
 {
-    const int lane = threadIdx.x & 31;
-    const int64_t warps = (int64_t)gridDim.x * (blockDim.x >> 5);
-    uint32_t *K = reinterpret_cast<uint32_t *>(E);
-    for (int64_t u = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5; u < n; u += warps) {
-        const int64_t a = row_ptr[u];
-        const uint32_t d = (uint32_t)(row_ptr[u + 1] - a);
-        int64_t base_id = 0;
-        if (count > 0) base_id = node_off[instance_of(node_off, count, u)];
-        const uint64_t reg = region[u];
-        if (d >= 2) {
-            const uint32_t L = tree_levels(d);
-            const uint32_t S = summary_sectors(d);
-            const uint64_t eb = reg + 4ull * S;
-            // key slot (uint32 index) of level l, key i: sectors of higher levels first
-            auto level_key = [&](uint32_t l, uint32_t i) -> uint64_t {
-                uint32_t off = 0;
-                for (uint32_t m = L; m > l; --m) off += level_sectors(d, m);
-                return (reg + 4ull * off) * 2 + i;
-            };
-            uint64_t carry = 0;
-            for (uint32_t e0 = 0; e0 < d; e0 += 32) {
-                const uint32_t i = e0 + lane;
-                uint64_t v = i < d ? (uint64_t)w[a + i] : 0ull;
-#pragma unroll
-                for (int o = 1; o < 32; o <<= 1) {
-                    uint64_t y = __shfl_up_sync(0xffffffffu, v, o);
-                    if (lane >= o) v += y;
-                }
-                const uint64_t P = carry + v;
-                if (i < d) {
-                    EdgeN r;
-                    r.P = (uint32_t)P;
-                    r.col = (int32_t)(col[a + i] + base_id);
-                    E[eb + i] = r;
-                    if (L > 0 && ((i & 7) == 7 || i == d - 1)) K[level_key(1, i >> 3)] = (uint32_t)P;
-                }
-                carry += __shfl_sync(0xffffffffu, v, 31);
+    uint32_t dmax = 0, dang = 0, flags = 0;
+    for (int64_t u = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; u < n; u += (int64_t)gridDim.x * blockDim.x) {
+        const int64_t a = row_ptr[u], b = row_ptr[u + 1];
+        const bool bad = a < 0 || b < a || b > m || (u == 0 && a != 0) || (u == n - 1 && b != m);
+        uint32_t sz = 0;
+        if (bad) {
+            flags |= kBadRowPtr;
+        } else if (b - a > PPR_MAX_DEGREE) {
+            flags |= kBigDegree;
+        } else {
+            const uint32_t d = (uint32_t)(b - a);
+            dmax = max(dmax, d);
+            dang += d == 0;
+            sz = blocked_row_records(d);
+        }
+        sizes[u] = sz;
+    }
+    block_stats(st, dmax, dang, flags);
+}
+
+struct BuildArgs {
+    int64_t n;
+    const int64_t *row_ptr;
+    const int32_t *col;
+    const uint32_t *w;
+    const int64_t *node_off;
+    int32_t count;
+    const uint64_t *region;
+    NodeRec *node;
+    EdgeN *E;
+    LayoutStats *st;
+    uint32_t *list;  // mid rows from the front, big rows from the back
+};
+
+// u32 slot of key i of level l of a blocked row (region reg, degree d, L levels)
+__device__ __forceinline__ uint64_t key_slot(uint64_t reg, uint32_t d, uint32_t L, uint32_t l, uint32_t i)
+{
+    uint32_t off = 0;
+    for (uint32_t q = L; q > l; --q) off += level_sectors(d, q);
+    return (reg + 4ull * off) * 2 + i;
+}
+
+__device__ __forceinline__ void write_node(const BuildArgs &A, int64_t u, uint64_t reg, uint32_t d, uint64_t W,
+                                           uint32_t first_target)
+{
+    NodeRec r;
+    r.word0 = pack_word0(reg, d, false);
+    r.total = d == 1 ? (uint64_t)first_target : (d == 0 ? 0ull : pack_blocked_total(W, d));
+    A.node[u] = r;
+}
+
+__device__ __forceinline__ int64_t instance_base(const BuildArgs &A, int64_t u, int64_t &hi_id)
+{
+    if (A.count == 0) {
+        hi_id = A.n;
+        return 0;
+    }
+    const int32_t g = instance_of(A.node_off, A.count, u);
+    hi_id = A.node_off[g + 1] - A.node_off[g];
+    return A.node_off[g];
+}
+
+// summary levels 2..L from level 1 (already written), padding included;
+// the calling group (warp or block) strides over keys with `rank`/`size`
+__device__ void write_upper_levels(uint32_t *K, uint64_t reg, uint32_t d, uint32_t L, uint32_t rank, uint32_t size,
+                                   bool block)
+{
+    for (uint32_t l = 2; l <= L; ++l) {
+        const uint32_t nl = ceil_shift(d, 3 * l), np = ceil_shift(d, 3 * (l - 1));
+        for (uint32_t i = rank; i < 8 * level_sectors(d, l); i += size) {
+            uint32_t kv = 0xffffffffu;
+            if (i < nl) kv = K[key_slot(reg, d, L, l - 1, min(8 * i + 8, np) - 1)];
+            K[key_slot(reg, d, L, l, i)] = kv;
+        }
+        if (block) __syncthreads();
+        else __syncwarp();
+    }
+}
+
+__global__ void __launch_bounds__(256) k_build_small(BuildArgs A)
+{
+    uint32_t *K = reinterpret_cast<uint32_t *>(A.E);
+    uint32_t flags = 0;
+    for (int64_t u = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; u < A.n; u += (int64_t)gridDim.x * blockDim.x) {
+        const int64_t a = A.row_ptr[u];
+        const uint32_t d = (uint32_t)(A.row_ptr[u + 1] - a);
+        if (d > kSmallRow) {
+            if (d <= kMidRow) A.list[atomicAdd(&A.st->n_mid, 1u)] = (uint32_t)u;
+            else A.list[A.n - 1 - atomicAdd(&A.st->n_big, 1u)] = (uint32_t)u;
+            continue;
+        }
+        int64_t hi_id;
+        const int64_t base_id = instance_base(A, u, hi_id);
+        const uint64_t reg = A.region[u];
+        const uint32_t L = tree_levels(d);  // 0 or 1 here
+        const uint64_t eb = reg + 4ull * summary_sectors(d);
+        uint64_t P = 0;
+        uint32_t first = 0;
+        for (uint32_t i = 0; i < d; ++i) {
+            const uint32_t wi = A.w[a + i];
+            const int64_t c = A.col[a + i];
+            if (wi == 0) flags |= kBadWeight;
+            if (c < 0 || c >= hi_id) flags |= kBadCol;
+            P += wi;
+            if (i == 0) first = (uint32_t)(c + base_id);
+            if (d >= 2) {
+                EdgeN r;
+                r.P = (uint32_t)P;
+                r.col = (int32_t)(c + base_id);
+                A.E[eb + i] = r;
+                if (L > 0 && ((i & 7) == 7 || i == d - 1)) K[key_slot(reg, d, L, 1, i >> 3)] = (uint32_t)P;
             }
-            // padding records up to the sector boundary
-            for (uint32_t i = d + lane; i < 4 * ceil_shift(d, 2); i += 32) {
+        }
+        if (P >= (1ull << 32)) flags |= kWide;
+        if (d >= 2) {
+            for (uint32_t i = d; i < 4 * ceil_shift(d, 2); ++i) {
                 EdgeN r;
                 r.P = 0xffffffffu;
                 r.col = 0;
-                E[eb + i] = r;
+                A.E[eb + i] = r;
             }
-            if (L > 0) {
-                const uint32_t n1 = ceil_shift(d, 3);
-                for (uint32_t i = n1 + lane; i < 8 * level_sectors(d, 1); i += 32) K[level_key(1, i)] = 0xffffffffu;
-                __syncwarp();
-                for (uint32_t l = 2; l <= L; ++l) {
-                    const uint32_t nl = ceil_shift(d, 3 * l), np = ceil_shift(d, 3 * (l - 1));
-                    for (uint32_t i = lane; i < 8 * level_sectors(d, l); i += 32) {
-                        uint32_t kv = 0xffffffffu;
-                        if (i < nl) kv = K[level_key(l - 1, min(8 * i + 8, np) - 1)];
-                        K[level_key(l, i)] = kv;
-                    }
-                    __syncwarp();
-                }
-            }
+            if (L > 0)
+                for (uint32_t i = ceil_shift(d, 3); i < 8 * level_sectors(d, 1); ++i) K[key_slot(reg, d, L, 1, i)] = 0xffffffffu;
         }
-        if (lane == 0) {
-            NodeRec r;
-            r.word0 = pack_word0(reg, d, false);
-            // a single out-edge needs no draw-to-edge search: keep its target inline;
-            // otherwise W_u (< 2^32 here) with the row's summary shape above it
-            r.total = (d == 1) ? (uint64_t)(uint32_t)(col[a] + base_id) : pack_blocked_total(W[u], d);
-            node[u] = r;
-        }
+        write_node(A, u, reg, d, P, first);
     }
+    block_stats(A.st, 0, 0, flags);
+}
+
+__global__ void __launch_bounds__(256) k_build_mid(BuildArgs A)
+{
+    uint32_t *K = reinterpret_cast<uint32_t *>(A.E);
+    const uint32_t lane = threadIdx.x & 31;
+    const int64_t warps = (int64_t)gridDim.x * (blockDim.x >> 5);
+    uint32_t flags = 0;
+    const uint32_t nmid = A.st->n_mid;
+    for (int64_t t = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5; t < nmid; t += warps) {
+        const int64_t u = A.list[t];
+        const int64_t a = A.row_ptr[u];
+        const uint32_t d = (uint32_t)(A.row_ptr[u + 1] - a);
+        int64_t hi_id;
+        const int64_t base_id = instance_base(A, u, hi_id);
+        const uint64_t reg = A.region[u];
+        const uint32_t L = tree_levels(d);
+        const uint64_t eb = reg + 4ull * summary_sectors(d);
+        uint64_t carry = 0;
+        for (uint32_t e0 = 0; e0 < d; e0 += 32) {
+            const uint32_t i = e0 + lane;
+            uint64_t v = 0;
+            int64_t c = 0;
+            if (i < d) {
+                v = A.w[a + i];
+                c = A.col[a + i];
+                if (v == 0) flags |= kBadWeight;
+                if (c < 0 || c >= hi_id) flags |= kBadCol;
+            }
+#pragma unroll
+            for (int o = 1; o < 32; o <<= 1) {
+                const uint64_t y = __shfl_up_sync(0xffffffffu, v, o);
+                if (lane >= o) v += y;
+            }
+            const uint64_t P = carry + v;
+            if (i < d) {
+                EdgeN r;
+                r.P = (uint32_t)P;
+                r.col = (int32_t)(c + base_id);
+                A.E[eb + i] = r;
+                if ((i & 7) == 7 || i == d - 1) K[key_slot(reg, d, L, 1, i >> 3)] = (uint32_t)P;
+            }
+            carry += __shfl_sync(0xffffffffu, v, 31);
+        }
+        if (carry >= (1ull << 32)) flags |= kWide;
+        for (uint32_t i = d + lane; i < 4 * ceil_shift(d, 2); i += 32) {
+            EdgeN r;
+            r.P = 0xffffffffu;
+            r.col = 0;
+            A.E[eb + i] = r;
+        }
+        for (uint32_t i = ceil_shift(d, 3) + lane; i < 8 * level_sectors(d, 1); i += 32)
+            K[key_slot(reg, d, L, 1, i)] = 0xffffffffu;
+        __syncwarp();
+        write_upper_levels(K, reg, d, L, lane, 32, false);
+        if (lane == 0) write_node(A, u, reg, d, carry, 0);
+    }
+    block_stats(A.st, 0, 0, flags);
+}
+
+__global__ void __launch_bounds__(512) k_build_big(BuildArgs A)
+{
+    __shared__ uint64_t s_warp[16];
+    uint32_t *K = reinterpret_cast<uint32_t *>(A.E);
+    const uint32_t tid = threadIdx.x, lane = tid & 31, wid = tid >> 5, nw = blockDim.x >> 5;
+    uint32_t flags = 0;
+    const uint32_t nbig = A.st->n_big;
+    for (uint32_t t = blockIdx.x; t < nbig; t += gridDim.x) {
+        const int64_t u = A.list[A.n - 1 - t];
+        const int64_t a = A.row_ptr[u];
+        const uint32_t d = (uint32_t)(A.row_ptr[u + 1] - a);
+        int64_t hi_id;
+        const int64_t base_id = instance_base(A, u, hi_id);
+        const uint64_t reg = A.region[u];
+        const uint32_t L = tree_levels(d);
+        const uint64_t eb = reg + 4ull * summary_sectors(d);
+        uint64_t carry = 0;
+        for (uint32_t e0 = 0; e0 < d; e0 += blockDim.x) {
+            const uint32_t i = e0 + tid;
+            uint64_t v = 0;
+            int64_t c = 0;
+            if (i < d) {
+                v = A.w[a + i];
+                c = A.col[a + i];
+                if (v == 0) flags |= kBadWeight;
+                if (c < 0 || c >= hi_id) flags |= kBadCol;
+            }
+#pragma unroll
+            for (int o = 1; o < 32; o <<= 1) {
+                const uint64_t y = __shfl_up_sync(0xffffffffu, v, o);
+                if (lane >= o) v += y;
+            }
+            if (lane == 31) s_warp[wid] = v;
+            __syncthreads();
+            uint64_t before = 0, chunk = 0;
+            for (uint32_t q = 0; q < nw; ++q) {
+                if (q < wid) before += s_warp[q];
+                chunk += s_warp[q];
+            }
+            const uint64_t P = carry + before + v;
+            if (i < d) {
+                EdgeN r;
+                r.P = (uint32_t)P;
+                r.col = (int32_t)(c + base_id);
+                A.E[eb + i] = r;
+                if ((i & 7) == 7 || i == d - 1) K[key_slot(reg, d, L, 1, i >> 3)] = (uint32_t)P;
+            }
+            carry += chunk;
+            __syncthreads();
+        }
+        if (carry >= (1ull << 32)) flags |= kWide;
+        for (uint32_t i = d + tid; i < 4 * ceil_shift(d, 2); i += blockDim.x) {
+            EdgeN r;
+            r.P = 0xffffffffu;
+            r.col = 0;
+            A.E[eb + i] = r;
+        }
+        for (uint32_t i = ceil_shift(d, 3) + tid; i < 8 * level_sectors(d, 1); i += blockDim.x)
+            K[key_slot(reg, d, L, 1, i)] = 0xffffffffu;
+        __syncthreads();
+        write_upper_levels(K, reg, d, L, tid, blockDim.x, true);
+        if (tid == 0) write_node(A, u, reg, d, carry, 0);
+        __syncthreads();
+    }
+    // one status word per block
+    __shared__ uint32_t s_flags;
+    if (tid == 0) s_flags = 0;
+    __syncthreads();
+    if (flags) atomicOr(&s_flags, flags);
+    __syncthreads();
+    if (tid == 0 && s_flags) atomicOr(&A.st->status, s_flags);
+}
+
+// Narrow layout in one pass.  Returns PPR_OK, an error, or 1 when a row total
+// reaches 2^32 (the caller then builds the wide layout).
+static int build_narrow(ppr_ctx *ctx, int64_t n, int64_t m, const int64_t *d_rp, const int32_t *d_col,
+                        const uint32_t *d_w, const int64_t *d_off, cudaStream_t st, ppr_graph *g,
+                        std::vector<void *> &tmp)
+{
+    int rc;
+    uint32_t *d_sizes;
+    uint64_t *d_region, *d_scan;
+    LayoutStats *d_ls;
+    uint32_t *d_list;
+    const int64_t tiles = (n + kScanTile - 1) / kScanTile;
+    if ((rc = dev_alloc((void **)&d_sizes, sizeof(uint32_t) * n, "row sizes", st))) return rc;
+    tmp.push_back(d_sizes);
+    if ((rc = dev_alloc((void **)&d_region, sizeof(uint64_t) * (n + 1), "row regions", st))) return rc;
+    tmp.push_back(d_region);
+    if ((rc = dev_alloc((void **)&d_scan, sizeof(uint64_t) * (tiles + 2), "scan scratch", st))) return rc;
+    tmp.push_back(d_scan);
+    if ((rc = dev_alloc((void **)&d_ls, sizeof(LayoutStats), "layout stats", st))) return rc;
+    tmp.push_back(d_ls);
+    if ((rc = dev_alloc((void **)&d_list, sizeof(uint32_t) * n, "long-row list", st))) return rc;
+    tmp.push_back(d_list);
+    cudaError_t e = cudaMemsetAsync(d_ls, 0, sizeof(LayoutStats), st);
+    if (e != cudaSuccess) return cuda_fail(e, "memset");
+    const int tblocks = (int)std::max<int64_t>(1, std::min<int64_t>((n + 255) / 256, (int64_t)ctx->sms * 16));
+    k_layout<<<tblocks, 256, 0, st>>>(n, m, d_rp, d_sizes, d_ls);
+    note_launch();
+    exclusive_scan_u32(d_sizes, n, d_region, d_scan, st);
+    LayoutStats hs;
+    uint64_t slots = 0;
+    e = cudaMemcpyAsync(&hs, d_ls, sizeof(hs), cudaMemcpyDeviceToHost, st);
+    if (e == cudaSuccess) e = cudaMemcpyAsync(&slots, d_region + n, sizeof(uint64_t), cudaMemcpyDeviceToHost, st);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(st);
+    if (e != cudaSuccess) return cuda_fail(e, "graph layout");
+    if (hs.status & kBadRowPtr) {
+        set_error("row_ptr must start at 0, be non-decreasing and end at m");
+        return PPR_EINVAL;
+    }
+    if (hs.status & kBigDegree) {
+        set_error("an out-degree exceeds the limit %lld", (long long)PPR_MAX_DEGREE);
+        return PPR_ERANGE;
+    }
+    if (slots > kBeginMask) {
+        set_error("edge layout needs %llu record slots, beyond 2^40", (unsigned long long)slots);
+        return PPR_ERANGE;
+    }
+    g->max_degree = (int64_t)hs.max_degree;
+    g->dangling = (int64_t)hs.dangling;
+    if ((rc = dev_alloc((void **)&g->node, sizeof(NodeRec) * n, "node records", st))) return rc;
+    const size_t edge_bytes = (size_t)(slots > 0 ? slots : 2) * sizeof(EdgeN);
+    if ((rc = dev_alloc(&g->edges, edge_bytes, "edge records", st))) return rc;
+    g->device_bytes = (int64_t)(sizeof(NodeRec) * n + edge_bytes);
+    BuildArgs A{n, d_rp, d_col, d_w, d_off, g->instances, d_region, g->node, (EdgeN *)g->edges, d_ls, d_list};
+    k_build_small<<<tblocks, 256, 0, st>>>(A);
+    note_launch();
+    k_build_mid<<<ctx->sms * 8, 256, 0, st>>>(A);
+    note_launch();
+    k_build_big<<<ctx->sms, 512, 0, st>>>(A);
+    note_launch();
+    e = cudaMemcpyAsync(&hs, d_ls, sizeof(hs), cudaMemcpyDeviceToHost, st);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(st);
+    if (e != cudaSuccess) return cuda_fail(e, "graph build");
+    if (hs.status & kBadCol) {
+        set_error("an edge target is outside [0, n) (of its instance)");
+        return PPR_EINVAL;
+    }
+    if (hs.status & kBadWeight) {
+        set_error("edge weights must be >= 1 (w(e) > 0, Sec. 2.1)");
+        return PPR_EINVAL;
+    }
+    if (hs.status & kWide) {
+        dev_free(g->node, st);
+        dev_free(g->edges, st);
+        g->node = nullptr;
+        g->edges = nullptr;
+        return 1;
+    }
+    return PPR_OK;
 }
 
 int build_graph(ppr_ctx *ctx, int64_t n, int64_t m, const int64_t *row_ptr, const int32_t *col,
@@ -258,6 +562,12 @@ int build_graph(ppr_ctx *ctx, int64_t n, int64_t m, const int64_t *row_ptr, cons
                                         cudaMemcpyHostToDevice, st);
         if (e != cudaSuccess) return cleanup(), cuda_fail(e, "node_off upload");
     }
+    rc = build_narrow(ctx, n, m, d_rp, d_col, d_w, d_off, st, g, tmp);
+    if (rc != 1) {
+        cleanup();
+        return rc;
+    }
+    // some row total reaches 2^32: 64-bit prefixes in flat rows
     void *p;
     if ((rc = dev_alloc(&p, sizeof(uint64_t) * n, "row totals", st))) return cleanup(), rc;
     tmp.push_back(p);
@@ -294,45 +604,16 @@ int build_graph(ppr_ctx *ctx, int64_t n, int64_t m, const int64_t *row_ptr, cons
         set_error("out-degree %llu exceeds the limit %lld", hs.max_degree, (long long)PPR_MAX_DEGREE);
         return cleanup(), PPR_ERANGE;
     }
-    g->wide = hs.max_total >= (1ull << 32);
+    g->wide = true;
     g->max_degree = (int64_t)hs.max_degree;
     g->dangling = (int64_t)hs.dangling;
     if ((rc = dev_alloc((void **)&g->node, sizeof(NodeRec) * n, "node records", st))) return cleanup(), rc;
-    if (g->wide) {
+    {
         size_t edge_bytes = (size_t)m * sizeof(EdgeW);
         if ((rc = dev_alloc(&g->edges, edge_bytes > 0 ? edge_bytes : 16, "edge records", st))) return cleanup(), rc;
         g->device_bytes = (int64_t)(sizeof(NodeRec) * n + edge_bytes);
         k_rows_pass2<true><<<blocks, threads, 0, st>>>(n, d_rp, d_col, d_w, d_off, g->instances, d_W, g->node, g->edges);
         note_launch();
-    } else {
-        // blocked rows: record slots per row, their offsets, then the rows
-        uint32_t *d_sizes;
-        uint64_t *d_region, *d_scan;
-        int64_t tiles = (n + kScanTile - 1) / kScanTile;
-        if ((rc = dev_alloc((void **)&d_sizes, sizeof(uint32_t) * n, "row sizes", st))) return cleanup(), rc;
-        tmp.push_back(d_sizes);
-        if ((rc = dev_alloc((void **)&d_region, sizeof(uint64_t) * (n + 1), "row regions", st))) return cleanup(), rc;
-        tmp.push_back(d_region);
-        if ((rc = dev_alloc((void **)&d_scan, sizeof(uint64_t) * (tiles + 2), "scan scratch", st))) return cleanup(), rc;
-        tmp.push_back(d_scan);
-        int sblocks = (int)std::min<int64_t>((n + 255) / 256, (int64_t)ctx->sms * 16);
-        k_row_records<<<sblocks, 256, 0, st>>>(n, d_rp, d_sizes);
-        note_launch();
-        exclusive_scan_u32(d_sizes, n, d_region, d_scan, st);
-        uint64_t slots = 0;
-        e = cudaMemcpyAsync(&slots, d_region + n, sizeof(uint64_t), cudaMemcpyDeviceToHost, st);
-        if (e == cudaSuccess) e = cudaStreamSynchronize(st);
-        if (e != cudaSuccess) return cleanup(), cuda_fail(e, "row layout");
-        if (slots > kBeginMask) {
-            set_error("edge layout needs %llu record slots, beyond 2^40", (unsigned long long)slots);
-            return cleanup(), PPR_ERANGE;
-        }
-        size_t edge_bytes = (size_t)(slots > 0 ? slots : 2) * sizeof(EdgeN);
-        if ((rc = dev_alloc(&g->edges, edge_bytes, "edge records", st))) return cleanup(), rc;
-        g->device_bytes = (int64_t)(sizeof(NodeRec) * n + edge_bytes);
-        k_rows_pass2_blocked<<<blocks, threads, 0, st>>>(n, d_rp, d_col, d_w, d_off, g->instances, d_W, d_region,
-                                                          g->node, (EdgeN *)g->edges);
-                                                          note_launch();
     }
     e = cudaGetLastError();
     if (e == cudaSuccess) e = cudaStreamSynchronize(st);

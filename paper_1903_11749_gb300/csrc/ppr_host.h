@@ -98,6 +98,7 @@ struct RunPlan {
     int32_t warps_per_block;
     int32_t chunk_sources;
     bool stats;
+    bool fused_aggregation;
 };
 // Enqueues the walks of sources [s_begin, s_end) writing output rows from
 // out_row0.  ends: S * R endpoint scratch for the plain kernel (else unused);

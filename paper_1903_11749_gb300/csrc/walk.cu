@@ -431,7 +431,7 @@ int launch_walks(ppr_ctx *ctx, const ppr_graph *g, const RunPlan &plan, ppr_resu
     kp.P2 = P2;
     kp.r_magic = ((1ull << 40) + plan.R - 1) / plan.R;
     // fused reduction needs next_pow2(R) * 12 bytes of shared memory per warp
-    kp.fuse = (plan.kernel == PPR_KERNEL_PERSISTENT && P2 <= 256) ? 1 : 0;
+    kp.fuse = (plan.kernel == PPR_KERNEL_PERSISTENT && plan.fused_aggregation && P2 <= 256) ? 1 : 0;
     int rc;
 
     std::vector<int4> chunks;
