@@ -265,6 +265,7 @@ def main():
         G, r = step()
         r.wait()
     kernel_ms = []
+    run_ms = []
     step_ms = []
     if world > 1:
         dist.barrier()
@@ -283,6 +284,7 @@ def main():
         e1.synchronize()
         step_ms.append(e0.elapsed_time(e1))
         kernel_ms.append(r.info().kernel_ms)
+        run_ms.append(r.info().run_ms)
         del r, G
     torch.cuda.synchronize(dev)
     launches = ppr.kernel_launches() - launches0
@@ -347,7 +349,7 @@ def main():
     traffic = recorded_traffic(args.workload)
     roofline = {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s", "frac": achieved / peak,
                 "traffic": traffic, "peak_kind": peak_kind, "kernel": "k_walk_persistent",
-                "alg_bytes_per_launch": alg_bytes, "kernel_ms": kms,
+                "alg_bytes_per_launch": alg_bytes, "kernel_ms": kms, "walk_and_reduce_ms": statistics.mean(run_ms),
                 "sectors_per_step": sectors_per_pass / max(steps_per_pass, 1)}
 
     cpu = None

@@ -195,9 +195,10 @@ typedef struct {
     int64_t nnz;           /* total stored (source, end) pairs */
     uint64_t steps;        /* draws consumed by all walks */
     uint64_t walks;        /* S * R */
-    float kernel_ms;       /* device time of the walker launches (CUDA events) */
-    uint64_t sectors;      /* stats runs: 32-byte sectors a thread-serial bisection touches,
-                              node record included (0 otherwise) */
+    float kernel_ms;       /* device time of the walker launches alone (CUDA events) */
+    uint64_t sectors;      /* stats runs: 32-byte sectors the row searches read, node records
+                              included (0 otherwise) */
+    float run_ms;          /* device time of the whole run: walkers and reductions */
 } ppr_result_info;
 
 int ppr_result_get_info(const ppr_result *r, ppr_result_info *info);

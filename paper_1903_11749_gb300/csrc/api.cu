@@ -292,6 +292,7 @@ static void result_release(ppr_result *r)
     if (r->ev_start) cudaEventDestroy(r->ev_start);
     if (r->ev_walk_end) cudaEventDestroy(r->ev_walk_end);
     if (r->ev_done) cudaEventDestroy(r->ev_done);
+    for (cudaEvent_t ev : r->walk_events) cudaEventDestroy(ev);
     delete r;
 }
 
@@ -456,7 +457,13 @@ int ppr_wait(ppr_result *r, int64_t timeout_ms)
     r->sectors = cnt[2];
     float ms = 0.f;
     PPR_CUDA(cudaEventElapsedTime(&ms, r->ev_start, r->ev_walk_end));
-    r->kernel_ms = ms;
+    r->run_ms = ms;
+    float kms = 0.f;
+    for (size_t i = 0; i + 1 < r->walk_events.size(); i += 2) {
+        PPR_CUDA(cudaEventElapsedTime(&ms, r->walk_events[i], r->walk_events[i + 1]));
+        kms += ms;
+    }
+    r->kernel_ms = kms;
     r->waited = true;
     return PPR_OK;
 }
@@ -487,6 +494,7 @@ int ppr_result_get_info(const ppr_result *r, ppr_result_info *info)
     info->steps = r->steps;
     info->walks = (uint64_t)r->S * r->R;
     info->kernel_ms = r->kernel_ms;
+    info->run_ms = r->run_ms;
     info->sectors = r->sectors;
     return PPR_OK;
 }

@@ -72,9 +72,11 @@ struct ppr_result {
     uint32_t *d_topk_cnt = nullptr;
     unsigned long long *d_steps = nullptr;  // [0] steps, [1] work-queue head, [2] sectors
     cudaEvent_t ev_start = nullptr, ev_walk_end = nullptr, ev_done = nullptr;
+    std::vector<cudaEvent_t> walk_events;  // (before, after) each walker launch
     bool waited = false;
     uint64_t steps = 0, sectors = 0;
-    float kernel_ms = 0.f;
+    float kernel_ms = 0.f;  // walker launches only
+    float run_ms = 0.f;     // walkers, reductions and everything between
     int64_t nnz_total = -1;
     std::vector<void *> scratch;  // freed with the result
 };

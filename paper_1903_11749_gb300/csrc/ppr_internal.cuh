@@ -425,4 +425,115 @@ __device__ inline void aggregate_source(const uint32_t *ends, uint32_t R, uint32
     __syncwarp();
 }
 
+// Register-resident variant for next_pow2(R) = 32 * E <= 1024: the sorted
+// block lives in registers in striped order (element i = e * 32 + lane), a
+// bitonic network runs on shuffles (partner distance < 32) and in-register
+// exchanges (distance >= 32).  Runs are found from neighbour values; the
+// top-k sorts 32-bit keys (R - count) << 12 | run, whose order is count
+// descending then end id ascending because runs are numbered in id order.
+template <int E>
+__device__ __forceinline__ void warp_sort_reg(uint32_t (&v)[E])
+{
+    const uint32_t lane = threadIdx.x & 31;
+    constexpr int N = 32 * E;
+#pragma unroll
+    for (int k = 2; k <= N; k <<= 1) {
+#pragma unroll
+        for (int j = k >> 1; j > 0; j >>= 1) {
+            if (j >= 32) {
+#pragma unroll
+                for (int e = 0; e < E; ++e) {
+                    const int f = e ^ (j >> 5);
+                    if (f > e) {
+                        const bool up = (((uint32_t)e * 32 + lane) & (uint32_t)k) == 0;
+                        const uint32_t a = v[e], b = v[f];
+                        const bool sw = (a > b) == up;
+                        v[e] = sw ? b : a;
+                        v[f] = sw ? a : b;
+                    }
+                }
+            } else {
+#pragma unroll
+                for (int e = 0; e < E; ++e) {
+                    const uint32_t o = __shfl_xor_sync(0xffffffffu, v[e], j);
+                    const bool up = (((uint32_t)e * 32 + lane) & (uint32_t)k) == 0;
+                    const bool lower = (lane & (uint32_t)j) == 0;
+                    v[e] = (lower == up) ? min(v[e], o) : max(v[e], o);
+                }
+            }
+        }
+    }
+}
+
+// scratch: 3 * R uint32 of per-warp shared memory
+template <int E>
+__device__ inline void aggregate_source_reg(const uint32_t *ends, uint32_t R, uint32_t *scratch, const AggOut &o,
+                                            uint64_t out_row)
+{
+    const uint32_t lane = threadIdx.x & 31;
+    uint32_t *start_pos = scratch, *run_id = scratch + R, *kbuf = scratch + 2 * R;
+    uint32_t v[E];
+#pragma unroll
+    for (int e = 0; e < E; ++e) {
+        const uint32_t i = (uint32_t)e * 32 + lane;
+        v[e] = i < R ? ends[i] : 0xffffffffu;
+    }
+    warp_sort_reg<E>(v);
+    const uint64_t rbase = out_row * o.cap;
+    uint32_t nrun = 0;
+#pragma unroll
+    for (int e = 0; e < E; ++e) {
+        const uint32_t i = (uint32_t)e * 32 + lane;
+        const uint32_t pu = __shfl_up_sync(0xffffffffu, v[e], 1);
+        const uint32_t pe = __shfl_sync(0xffffffffu, v[e > 0 ? e - 1 : 0], 31);
+        const uint32_t nd = __shfl_down_sync(0xffffffffu, v[e], 1);
+        const uint32_t ne = __shfl_sync(0xffffffffu, v[e + 1 < E ? e + 1 : e], 0);
+        const uint32_t prev = lane == 0 ? pe : pu;
+        const uint32_t next = lane == 31 ? ne : nd;
+        const bool valid = i < R;
+        const bool head = valid && (i == 0 || prev != v[e]);
+        const bool tail = valid && (i == R - 1 || next != v[e]);
+        const uint32_t hb = __ballot_sync(0xffffffffu, head);
+        const uint32_t run = nrun + __popc(hb & ((2u << lane) - 1)) - 1;  // run of element i
+        if (head) {
+            start_pos[run] = i;
+            run_id[run] = v[e];
+        }
+        __syncwarp();
+        if (tail) {
+            const uint32_t c = i - start_pos[run] + 1;
+            o.cols[rbase + run] = (int32_t)v[e];
+            o.cnts[rbase + run] = c;
+            kbuf[run] = ((R - c) << 12) | run;
+        }
+        nrun += __popc(hb);
+    }
+    if (lane == 0) o.nnz[out_row] = nrun;
+    if (o.topk > 0) {
+        __syncwarp();
+        uint32_t kv[E];
+#pragma unroll
+        for (int e = 0; e < E; ++e) {
+            const uint32_t i = (uint32_t)e * 32 + lane;
+            kv[e] = i < nrun ? kbuf[i] : 0xffffffffu;
+        }
+        warp_sort_reg<E>(kv);
+        const uint64_t tb = out_row * (uint64_t)o.topk;
+#pragma unroll
+        for (int e = 0; e < E; ++e) {
+            const uint32_t i = (uint32_t)e * 32 + lane;
+            if (i < (uint32_t)o.topk) {
+                if (i < nrun) {
+                    o.topk_idx[tb + i] = (int32_t)run_id[kv[e] & 0xfffu];
+                    o.topk_cnt[tb + i] = R - (kv[e] >> 12);
+                } else {
+                    o.topk_idx[tb + i] = -1;
+                    o.topk_cnt[tb + i] = 0;
+                }
+            }
+        }
+    }
+    __syncwarp();
+}
+
 }  // namespace ppr

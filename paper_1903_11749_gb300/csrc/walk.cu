@@ -187,16 +187,25 @@ __global__ void __launch_bounds__(256, PPR_WALK_MINB) k_walk_plain(KParams p)
     warp_add_tally<STATS>(p.steps, tl);
 }
 
+// E > 0: register-resident reduction for next_pow2(R) = 32 * E; E = 0:
+// shared-memory reduction (any R).
+template <int E>
 __global__ void __launch_bounds__(128) k_aggregate(KParams p)
 {
     extern __shared__ __align__(16) unsigned char smem_raw[];
     const uint32_t wid = threadIdx.x >> 5, nw = blockDim.x >> 5;
-    uint64_t *keys = reinterpret_cast<uint64_t *>(smem_raw) + (size_t)wid * p.P2;
-    uint32_t *sortbuf = reinterpret_cast<uint32_t *>(reinterpret_cast<uint64_t *>(smem_raw) + (size_t)nw * p.P2) +
-                        (size_t)wid * p.P2;
+    unsigned char *scratch = smem_raw + (size_t)wid * p.P2 * 12;
     const uint64_t S = (uint64_t)(p.s_end - p.s_begin);
-    for (uint64_t i = (uint64_t)blockIdx.x * nw + wid; i < S; i += (uint64_t)gridDim.x * nw)
-        aggregate_source(p.ends + i * p.R, p.R, sortbuf, keys, p.out, (uint64_t)p.out_row0 + i);
+    for (uint64_t i = (uint64_t)blockIdx.x * nw + wid; i < S; i += (uint64_t)gridDim.x * nw) {
+        if constexpr (E > 0) {
+            aggregate_source_reg<E>(p.ends + i * p.R, p.R, reinterpret_cast<uint32_t *>(scratch), p.out,
+                                    (uint64_t)p.out_row0 + i);
+        } else {
+            uint64_t *keys = reinterpret_cast<uint64_t *>(scratch);
+            aggregate_source(p.ends + i * p.R, p.R, reinterpret_cast<uint32_t *>(keys + p.P2), keys, p.out,
+                             (uint64_t)p.out_row0 + i);
+        }
+    }
 }
 
 // ------------------------------------------------------- persistent (K5) ----
@@ -228,8 +237,7 @@ __global__ void __launch_bounds__(256, PPR_WALK_MINB) k_walk_persistent(KParams 
     const size_t per_warp = sizeof(ChunkSlot) * kRing + (p.fuse ? (size_t)p.P2 * 12 : 0);
     unsigned char *mine = smem_raw + per_warp * wid;
     ChunkSlot *ring = reinterpret_cast<ChunkSlot *>(mine);
-    uint64_t *keys = reinterpret_cast<uint64_t *>(mine + sizeof(ChunkSlot) * kRing);
-    uint32_t *sortbuf = reinterpret_cast<uint32_t *>(keys + p.P2);
+    unsigned char *scratch = mine + sizeof(ChunkSlot) * kRing;
     const E edges = make_edges<E>(p.edges);
     if (lane < kRing) ring[lane].live = 0;
     __syncwarp();
@@ -330,7 +338,9 @@ __global__ void __launch_bounds__(256, PPR_WALK_MINB) k_walk_persistent(KParams 
                 if (cs.live && cs.done == cs.total && cs.issued == cs.total) {
                     for (uint32_t i = 0; i < cs.nsrc; ++i) {
                         const uint64_t row = (uint64_t)((int64_t)(cs.base + i) - p.s_begin);
-                        aggregate_source(p.ends + row * p.R, p.R, sortbuf, keys, p.out, (uint64_t)p.out_row0 + row);
+                        uint64_t *keys = reinterpret_cast<uint64_t *>(scratch);
+                        aggregate_source(p.ends + row * p.R, p.R, reinterpret_cast<uint32_t *>(keys + p.P2), keys, p.out,
+                                         (uint64_t)p.out_row0 + row);
                     }
                     __syncwarp();
                     if (lane == 0) ring[r].live = 0;
@@ -358,29 +368,58 @@ __global__ void __launch_bounds__(256, PPR_WALK_MINB) k_walk_persistent(KParams 
 
 // ------------------------------------------------------------- launcher ----
 
-static int launch_aggregate(ppr_ctx *ctx, const KParams &kp, int64_t S, cudaStream_t st)
+template <int E>
+static int launch_aggregate_e(ppr_ctx *ctx, const KParams &kp, int64_t S, cudaStream_t st)
 {
     const int aw = 4;
     size_t smem = (size_t)aw * kp.P2 * 12;
-    if (smem > 48 * 1024) PPR_CUDA(cudaFuncSetAttribute(k_aggregate, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
+    if (smem > 48 * 1024)
+        PPR_CUDA(cudaFuncSetAttribute(k_aggregate<E>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
     int ablocks = (int)std::min<int64_t>((S + aw - 1) / aw, (int64_t)ctx->sms * 16);
     if (ablocks < 1) ablocks = 1;
-    k_aggregate<<<ablocks, aw * 32, smem, st>>>(kp);
+    k_aggregate<E><<<ablocks, aw * 32, smem, st>>>(kp);
     note_launch();
     PPR_CUDA(cudaGetLastError());
     return PPR_OK;
 }
 
-template <class E, bool SEG, bool STATS>
-static int launch_typed(ppr_ctx *ctx, const KParams &kp, const RunPlan &plan, int64_t S, cudaStream_t st)
+static int launch_aggregate(ppr_ctx *ctx, const KParams &kp, int64_t S, cudaStream_t st)
 {
+    switch (kp.P2) {
+    case 1: case 2: case 4: case 8: case 16: case 32: return launch_aggregate_e<1>(ctx, kp, S, st);
+    case 64: return launch_aggregate_e<2>(ctx, kp, S, st);
+    case 128: return launch_aggregate_e<4>(ctx, kp, S, st);
+    case 256: return launch_aggregate_e<8>(ctx, kp, S, st);
+    case 512: return launch_aggregate_e<16>(ctx, kp, S, st);
+    case 1024: return launch_aggregate_e<32>(ctx, kp, S, st);
+    default: return launch_aggregate_e<0>(ctx, kp, S, st);
+    }
+}
+
+// Events around a walker launch, for the walker-only device time.
+static int walker_event(ppr_result *r, cudaStream_t st)
+{
+    cudaEvent_t ev;
+    PPR_CUDA(cudaEventCreate(&ev));
+    r->walk_events.push_back(ev);
+    PPR_CUDA(cudaEventRecord(ev, st));
+    return PPR_OK;
+}
+
+template <class E, bool SEG, bool STATS>
+static int launch_typed(ppr_ctx *ctx, const KParams &kp, const RunPlan &plan, int64_t S, cudaStream_t st,
+                        ppr_result *r)
+{
+    int rc;
     if (plan.kernel == PPR_KERNEL_PLAIN) {
         uint64_t total = (uint64_t)S * kp.R;
         int blocks = (int)std::min<uint64_t>((total + 255) / 256, (uint64_t)ctx->sms * 64);
         if (blocks < 1) blocks = 1;
+        if ((rc = walker_event(r, st))) return rc;
         k_walk_plain<E, SEG, STATS><<<blocks, 256, 0, st>>>(kp);
         note_launch();
         PPR_CUDA(cudaGetLastError());
+        if ((rc = walker_event(r, st))) return rc;
         return launch_aggregate(ctx, kp, S, st);
     }
     const size_t smem = 8 * (sizeof(ChunkSlot) * kRing + (kp.fuse ? (size_t)kp.P2 * 12 : 0));
@@ -391,9 +430,11 @@ static int launch_typed(ppr_ctx *ctx, const KParams &kp, const RunPlan &plan, in
     int64_t blocks = (int64_t)ctx->sms * per_sm;
     int64_t needed = ((int64_t)kp.nchunks + 7) / 8;
     if (blocks > needed) blocks = std::max<int64_t>(needed, 1);
+    if ((rc = walker_event(r, st))) return rc;
     k_walk_persistent<E, SEG, STATS><<<(unsigned)blocks, 256, smem, st>>>(kp);
     note_launch();
     PPR_CUDA(cudaGetLastError());
+    if ((rc = walker_event(r, st))) return rc;
     return kp.fuse ? PPR_OK : launch_aggregate(ctx, kp, S, st);
 }
 
@@ -469,16 +510,16 @@ int launch_walks(ppr_ctx *ctx, const ppr_graph *g, const RunPlan &plan, ppr_resu
     }
     if (plan.stats) {
         if (g->wide)
-            return plan.segments ? launch_typed<WideEdges, true, true>(ctx, kp, plan, S, st)
-                                 : launch_typed<WideEdges, false, true>(ctx, kp, plan, S, st);
-        return plan.segments ? launch_typed<NarrowEdges, true, true>(ctx, kp, plan, S, st)
-                             : launch_typed<NarrowEdges, false, true>(ctx, kp, plan, S, st);
+            return plan.segments ? launch_typed<WideEdges, true, true>(ctx, kp, plan, S, st, r)
+                                 : launch_typed<WideEdges, false, true>(ctx, kp, plan, S, st, r);
+        return plan.segments ? launch_typed<NarrowEdges, true, true>(ctx, kp, plan, S, st, r)
+                             : launch_typed<NarrowEdges, false, true>(ctx, kp, plan, S, st, r);
     }
     if (g->wide)
-        return plan.segments ? launch_typed<WideEdges, true, false>(ctx, kp, plan, S, st)
-                             : launch_typed<WideEdges, false, false>(ctx, kp, plan, S, st);
-    return plan.segments ? launch_typed<NarrowEdges, true, false>(ctx, kp, plan, S, st)
-                         : launch_typed<NarrowEdges, false, false>(ctx, kp, plan, S, st);
+        return plan.segments ? launch_typed<WideEdges, true, false>(ctx, kp, plan, S, st, r)
+                             : launch_typed<WideEdges, false, false>(ctx, kp, plan, S, st, r);
+    return plan.segments ? launch_typed<NarrowEdges, true, false>(ctx, kp, plan, S, st, r)
+                         : launch_typed<NarrowEdges, false, false>(ctx, kp, plan, S, st, r);
 }
 
 }  // namespace ppr

@@ -44,7 +44,8 @@ class RunArgs(C.Structure):
 
 class ResultInfo(C.Structure):
     _fields_ = [("sources", C.c_int64), ("R", C.c_uint32), ("topk", C.c_int32), ("nnz", C.c_int64),
-                ("steps", C.c_uint64), ("walks", C.c_uint64), ("kernel_ms", C.c_float), ("sectors", C.c_uint64)]
+                ("steps", C.c_uint64), ("walks", C.c_uint64), ("kernel_ms", C.c_float), ("sectors", C.c_uint64),
+                ("run_ms", C.c_float)]
 
 
 # Every symbol include/ppr.h declares, with its ctypes signature.
