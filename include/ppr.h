@@ -143,7 +143,7 @@ void ppr_free_graph(ppr_graph *g);
 
 /* Walker kernels. */
 enum {
-    PPR_KERNEL_PERSISTENT = 0, /* persistent warps, work queue, lane refill, fused aggregation */
+    PPR_KERNEL_PERSISTENT = 0, /* persistent warps, work queue, lane refill; per-source reduction kernel */
     PPR_KERNEL_PLAIN = 1       /* one thread per walk, endpoints to HBM, separate aggregation */
 };
 
@@ -165,8 +165,6 @@ typedef struct {
     int64_t max_batch_sources;/* sources per device batch, 0 = sized to free device memory */
     int32_t stats;       /* 1: also count the algorithmic 32-byte sectors of every step (slower;
                             rows, counts and steps are unchanged) */
-    int32_t fused_aggregation; /* 1: persistent warps reduce their finished chunks themselves
-                                  (R <= 256); 0: a separate reduction kernel (default) */
     void *stream;        /* cudaStream_t, NULL = legacy default stream */
 } ppr_run_args;
 

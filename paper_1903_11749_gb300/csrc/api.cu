@@ -328,7 +328,7 @@ int ppr_run(ppr_ctx *ctx, const ppr_graph *g, const ppr_run_args *a, ppr_result 
     if ((a->dangling != 0 && a->dangling != 1) || (a->segments != 0 && a->segments != 1) ||
         (a->kernel != PPR_KERNEL_PERSISTENT && a->kernel != PPR_KERNEL_PLAIN) || a->large_degree < 0 ||
         a->warps_per_block < 0 || a->warps_per_block > 32 || a->chunk_sources < 0 || a->max_batch_sources < 0 ||
-        (a->stats != 0 && a->stats != 1) || (a->fused_aggregation != 0 && a->fused_aggregation != 1)) {
+        (a->stats != 0 && a->stats != 1)) {
         set_error("invalid mode or tuning argument");
         return PPR_EINVAL;
     }
@@ -393,7 +393,6 @@ int ppr_run(ppr_ctx *ctx, const ppr_graph *g, const ppr_run_args *a, ppr_result 
     plan.warps_per_block = a->warps_per_block;
     plan.chunk_sources = a->chunk_sources;
     plan.stats = a->stats != 0;
-    plan.fused_aggregation = a->fused_aggregation != 0;
 
     // Batch size (the paper's per-pipeline walk budget, gamma <= alpha*M/(n*c),
     // Sec. 4.3, becomes a source batch sized to device memory): every walk of
@@ -416,7 +415,7 @@ int ppr_run(ppr_ctx *ctx, const ppr_graph *g, const ppr_run_args *a, ppr_result 
     if ((e = cudaEventRecord(r->ev_start, st)) != cudaSuccess) return fail(cuda_fail(e, "cudaEventRecord"));
     for (int64_t b = a->src_begin; b < a->src_end; b += batch) {
         int64_t be = std::min<int64_t>(a->src_end, b + batch);
-        rc = launch_walks(ctx, g, plan, r, b, be, b - a->src_begin, ends, r->d_steps + 1, st);
+        rc = launch_walks(ctx, g, plan, r, b, be, b - a->src_begin, ends, r->d_steps + 1, st, true);
         if (rc) {
             cudaStreamSynchronize(st);
             return fail(rc);

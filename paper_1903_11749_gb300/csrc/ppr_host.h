@@ -100,12 +100,13 @@ struct RunPlan {
     int32_t warps_per_block;
     int32_t chunk_sources;
     bool stats;
-    bool fused_aggregation;
 };
 // Enqueues the walks of sources [s_begin, s_end) writing output rows from
 // out_row0.  ends: S * R endpoint scratch for the plain kernel (else unused);
 // queue: one device counter for the persistent kernel's work queue.
+// timed: record CUDA events around every walker launch into r.
 int launch_walks(ppr_ctx *ctx, const ppr_graph *g, const RunPlan &p, ppr_result *r, int64_t s_begin,
-                 int64_t s_end, int64_t out_row0, uint32_t *ends, unsigned long long *queue, cudaStream_t st);
+                 int64_t s_end, int64_t out_row0, uint32_t *ends, unsigned long long *queue, cudaStream_t st,
+                 bool timed);
 
 }  // namespace ppr

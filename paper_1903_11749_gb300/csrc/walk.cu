@@ -41,7 +41,6 @@ struct KParams {
     unsigned long long *steps;    // [0] draws consumed, [2] algorithmic sectors (statistics launch)
     uint32_t P2;              // next_pow2(R)
     uint64_t r_magic;         // ceil(2^40 / R): walk index -> source index by multiply-shift
-    int32_t fuse;             // persistent kernel aggregates finished chunks itself
 };
 
 // One step of one walk.  Returns true when the walk has ended (end is set).
@@ -211,18 +210,17 @@ __global__ void __launch_bounds__(128) k_aggregate(KParams p)
 // ------------------------------------------------------- persistent (K5) ----
 // Persistent warps.  Each warp pulls chunks of sources from a global queue
 // (one atomic per chunk) and keeps all 32 lanes busy: a lane whose walk ends
-// takes the next walk of the newest chunk at once, so a warp never waits for
+// takes the next walk of the warp's chunk at once, so a warp never waits for
 // the longest of 32 geometric walk lengths (the paper's pipelines keep the
 // cluster busy the same way: new walks start while old ones finish).  Steps
 // run in lockstep; a row longer than p.large can be searched by the whole
-// warp (search_warp).  Endpoints go to the per-walk buffer; a warp tracks up
-// to kRing chunks in flight and, when the last walk of a chunk ends (and
-// p.fuse is set), reduces that chunk's sources itself in a small shared
-// sort buffer (aggregate_source) while the other warps keep walking.
-struct ChunkSlot {
-    uint32_t base, nsrc, ctr_base, tag, total, issued, done, live;
+// warp (search_warp).  Endpoints go to the per-walk buffer, reduced per
+// source by k_aggregate.  The walker uses no shared memory beyond the queue
+// state, so L1 keeps its full size.
+struct WarpQueue {
+    uint32_t base, ctr_base, tag;  // current chunk
+    uint32_t issued, total;
 };
-constexpr int kRing = 4;
 
 __device__ __forceinline__ uint32_t div_by_R(uint32_t w, uint64_t magic)
 {
@@ -232,30 +230,25 @@ __device__ __forceinline__ uint32_t div_by_R(uint32_t w, uint64_t magic)
 template <class E, bool SEG, bool STATS>
 __global__ void __launch_bounds__(256, PPR_WALK_MINB) k_walk_persistent(KParams p)
 {
-    extern __shared__ __align__(16) unsigned char smem_raw[];
+    __shared__ WarpQueue wq_all[8];
     const uint32_t lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
-    const size_t per_warp = sizeof(ChunkSlot) * kRing + (p.fuse ? (size_t)p.P2 * 12 : 0);
-    unsigned char *mine = smem_raw + per_warp * wid;
-    ChunkSlot *ring = reinterpret_cast<ChunkSlot *>(mine);
-    unsigned char *scratch = mine + sizeof(ChunkSlot) * kRing;
+    WarpQueue &wq = wq_all[wid];
     const E edges = make_edges<E>(p.edges);
-    if (lane < kRing) ring[lane].live = 0;
+    if (lane == 0) {
+        wq.issued = 0;
+        wq.total = 0;
+    }
     __syncwarp();
-    int cur = -1;
     bool queue_empty = false;
     bool active = false;
-    uint32_t rs = 0;  // ring slot of the lane's walk
     uint32_t src = 0, sctr = 0, j = 0, k = 0, u = 0, tag = 0, ctr_base = 0;
     uint64_t slot = 0;  // endpoint index: (src - s_begin) * R + j
     Tally tl;
 
     for (;;) {
-        // ---- refill idle lanes from the newest chunk, opening chunks as needed
         uint32_t idle = __ballot_sync(0xffffffffu, !active);
         while (idle && !queue_empty) {
-            if (cur < 0 || ring[cur].issued == ring[cur].total) {
-                const int nxt = cur < 0 ? 0 : (cur + 1) % kRing;
-                if (ring[nxt].live) break;  // every ring slot still has walks in flight
+            if (wq.issued == wq.total) {
                 unsigned long long c = 0;
                 if (lane == 0) c = atomicAdd(p.queue, 1ull);
                 c = __shfl_sync(0xffffffffu, c, 0);
@@ -264,104 +257,53 @@ __global__ void __launch_bounds__(256, PPR_WALK_MINB) k_walk_persistent(KParams 
                     break;
                 }
                 if (lane == 0) {
-                    ChunkSlot cs;
+                    uint32_t nsrc;
                     if (p.chunks) {
-                        int4 d = p.chunks[c];
-                        cs.base = (uint32_t)d.x;
-                        cs.nsrc = (uint32_t)d.y;
-                        cs.ctr_base = (uint32_t)p.inst_off[d.z];
-                        cs.tag = (uint32_t)d.z;
+                        const int4 d = p.chunks[c];
+                        wq.base = (uint32_t)d.x;
+                        nsrc = (uint32_t)d.y;
+                        wq.ctr_base = (uint32_t)p.inst_off[d.z];
+                        wq.tag = (uint32_t)d.z;
                     } else {
-                        int64_t b = p.s_begin + (int64_t)c * p.CS;
-                        cs.base = (uint32_t)b;
-                        cs.nsrc = (uint32_t)std::min<int64_t>((int64_t)p.CS, p.s_end - b);
-                        cs.ctr_base = 0;
-                        cs.tag = p.tag;
+                        const int64_t b = p.s_begin + (int64_t)c * p.CS;
+                        wq.base = (uint32_t)b;
+                        nsrc = (uint32_t)std::min<int64_t>((int64_t)p.CS, p.s_end - b);
+                        wq.ctr_base = 0;
+                        wq.tag = p.tag;
                     }
-                    cs.total = cs.nsrc * p.R;
-                    cs.issued = 0;
-                    cs.done = 0;
-                    cs.live = 1;
-                    ring[nxt] = cs;
+                    wq.issued = 0;
+                    wq.total = nsrc * p.R;
                 }
                 __syncwarp();
-                cur = nxt;
             }
-            const uint32_t issued = ring[cur].issued;
-            const uint32_t take = min(ring[cur].total - issued, (uint32_t)__popc(idle));
+            const uint32_t issued = wq.issued;
+            const uint32_t take = min(wq.total - issued, (uint32_t)__popc(idle));
             const uint32_t rank = __popc(idle & ((1u << lane) - 1));
             if (((idle >> lane) & 1) && rank < take) {
                 const uint32_t w = issued + rank;
                 const uint32_t i = div_by_R(w, p.r_magic);
                 j = w - i * p.R;
-                src = ring[cur].base + i;
-                ctr_base = ring[cur].ctr_base;
+                src = wq.base + i;
+                ctr_base = wq.ctr_base;
                 sctr = src - ctr_base;
-                tag = ring[cur].tag;
-                rs = (uint32_t)cur;
+                tag = wq.tag;
                 slot = ((uint64_t)((int64_t)src - p.s_begin)) * p.R + j;
                 k = 0;
                 u = src;
                 active = true;
             }
             __syncwarp();
-            if (lane == 0) ring[cur].issued = issued + take;
+            if (lane == 0) wq.issued = issued + take;
             __syncwarp();
             idle = __ballot_sync(0xffffffffu, !active);
         }
-        const bool any_active = __any_sync(0xffffffffu, active);
+        if (__ballot_sync(0xffffffffu, active) == 0) break;  // queue drained and every walk done
 
-        // ---- one step of every active walk
-        bool fin = false;
-        if (any_active) {
-            uint32_t end = 0;
-            fin = walk_step<E, SEG, true, STATS>(p, edges, active, src, sctr, j, tag, k, u, end, tl);
-            if (fin) {
-                p.ends[slot] = end - ctr_base;
-                active = false;
-            }
+        uint32_t end = 0;
+        if (walk_step<E, SEG, true, STATS>(p, edges, active, src, sctr, j, tag, k, u, end, tl)) {
+            p.ends[slot] = end - ctr_base;
+            active = false;
         }
-        if (p.fuse && (__any_sync(0xffffffffu, fin) || !any_active)) {
-            // per-slot completion counts, then reduce every chunk whose walks are all done
-            uint32_t add[kRing];
-#pragma unroll
-            for (int r = 0; r < kRing; ++r) add[r] = __popc(__ballot_sync(0xffffffffu, fin && rs == (uint32_t)r));
-            __syncwarp();
-            if (lane == 0) {
-#pragma unroll
-                for (int r = 0; r < kRing; ++r) ring[r].done += add[r];
-            }
-            __syncwarp();
-#pragma unroll 1
-            for (int r = 0; r < kRing; ++r) {
-                const ChunkSlot cs = ring[r];
-                if (cs.live && cs.done == cs.total && cs.issued == cs.total) {
-                    for (uint32_t i = 0; i < cs.nsrc; ++i) {
-                        const uint64_t row = (uint64_t)((int64_t)(cs.base + i) - p.s_begin);
-                        uint64_t *keys = reinterpret_cast<uint64_t *>(scratch);
-                        aggregate_source(p.ends + row * p.R, p.R, reinterpret_cast<uint32_t *>(keys + p.P2), keys, p.out,
-                                         (uint64_t)p.out_row0 + row);
-                    }
-                    __syncwarp();
-                    if (lane == 0) ring[r].live = 0;
-                    __syncwarp();
-                }
-            }
-        }
-        if (!any_active && queue_empty) {
-            bool live = false;
-#pragma unroll
-            for (int r = 0; r < kRing; ++r) live |= ring[r].live && p.fuse;
-            if (!live) break;
-        }
-        if (!p.fuse && lane == 0) {
-            // without the fused reduction a slot only feeds lanes: it is free
-            // again as soon as all its walks are issued
-#pragma unroll
-            for (int r = 0; r < kRing; ++r)
-                if (ring[r].live && ring[r].issued == ring[r].total) ring[r].live = 0;
-        }
-        __syncwarp();
     }
     warp_add_tally<STATS>(p.steps, tl);
 }
@@ -399,6 +341,7 @@ static int launch_aggregate(ppr_ctx *ctx, const KParams &kp, int64_t S, cudaStre
 // Events around a walker launch, for the walker-only device time.
 static int walker_event(ppr_result *r, cudaStream_t st)
 {
+    if (!r) return PPR_OK;  // allocation-free runs record no events
     cudaEvent_t ev;
     PPR_CUDA(cudaEventCreate(&ev));
     r->walk_events.push_back(ev);
@@ -422,25 +365,25 @@ static int launch_typed(ppr_ctx *ctx, const KParams &kp, const RunPlan &plan, in
         if ((rc = walker_event(r, st))) return rc;
         return launch_aggregate(ctx, kp, S, st);
     }
-    const size_t smem = 8 * (sizeof(ChunkSlot) * kRing + (kp.fuse ? (size_t)kp.P2 * 12 : 0));
-    PPR_CUDA(cudaFuncSetAttribute(k_walk_persistent<E, SEG, STATS>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
     int per_sm = 0;
-    PPR_CUDA(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_walk_persistent<E, SEG, STATS>, 256, smem));
+    PPR_CUDA(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_walk_persistent<E, SEG, STATS>, 256, 0));
     if (per_sm < 1) per_sm = 1;
     int64_t blocks = (int64_t)ctx->sms * per_sm;
     int64_t needed = ((int64_t)kp.nchunks + 7) / 8;
     if (blocks > needed) blocks = std::max<int64_t>(needed, 1);
     if ((rc = walker_event(r, st))) return rc;
-    k_walk_persistent<E, SEG, STATS><<<(unsigned)blocks, 256, smem, st>>>(kp);
+    k_walk_persistent<E, SEG, STATS><<<(unsigned)blocks, 256, 0, st>>>(kp);
     note_launch();
     PPR_CUDA(cudaGetLastError());
     if ((rc = walker_event(r, st))) return rc;
-    return kp.fuse ? PPR_OK : launch_aggregate(ctx, kp, S, st);
+    return launch_aggregate(ctx, kp, S, st);
 }
 
 int launch_walks(ppr_ctx *ctx, const ppr_graph *g, const RunPlan &plan, ppr_result *r, int64_t s_begin,
-                 int64_t s_end, int64_t out_row0, uint32_t *ends, unsigned long long *queue, cudaStream_t st)
+                 int64_t s_end, int64_t out_row0, uint32_t *ends, unsigned long long *queue, cudaStream_t st,
+                 bool timed)
 {
+    ppr_result *ev_owner = timed ? r : nullptr;
     const int64_t S = s_end - s_begin;
     if (S <= 0) return PPR_OK;
     KParams kp{};
@@ -471,8 +414,6 @@ int launch_walks(ppr_ctx *ctx, const ppr_graph *g, const RunPlan &plan, ppr_resu
     while (P2 < plan.R) P2 <<= 1;
     kp.P2 = P2;
     kp.r_magic = ((1ull << 40) + plan.R - 1) / plan.R;
-    // fused reduction needs next_pow2(R) * 12 bytes of shared memory per warp
-    kp.fuse = (plan.kernel == PPR_KERNEL_PERSISTENT && plan.fused_aggregation && P2 <= 256) ? 1 : 0;
     int rc;
 
     std::vector<int4> chunks;
@@ -510,16 +451,16 @@ int launch_walks(ppr_ctx *ctx, const ppr_graph *g, const RunPlan &plan, ppr_resu
     }
     if (plan.stats) {
         if (g->wide)
-            return plan.segments ? launch_typed<WideEdges, true, true>(ctx, kp, plan, S, st, r)
-                                 : launch_typed<WideEdges, false, true>(ctx, kp, plan, S, st, r);
-        return plan.segments ? launch_typed<NarrowEdges, true, true>(ctx, kp, plan, S, st, r)
-                             : launch_typed<NarrowEdges, false, true>(ctx, kp, plan, S, st, r);
+            return plan.segments ? launch_typed<WideEdges, true, true>(ctx, kp, plan, S, st, ev_owner)
+                                 : launch_typed<WideEdges, false, true>(ctx, kp, plan, S, st, ev_owner);
+        return plan.segments ? launch_typed<NarrowEdges, true, true>(ctx, kp, plan, S, st, ev_owner)
+                             : launch_typed<NarrowEdges, false, true>(ctx, kp, plan, S, st, ev_owner);
     }
     if (g->wide)
-        return plan.segments ? launch_typed<WideEdges, true, false>(ctx, kp, plan, S, st, r)
-                             : launch_typed<WideEdges, false, false>(ctx, kp, plan, S, st, r);
-    return plan.segments ? launch_typed<NarrowEdges, true, false>(ctx, kp, plan, S, st, r)
-                         : launch_typed<NarrowEdges, false, false>(ctx, kp, plan, S, st, r);
+        return plan.segments ? launch_typed<WideEdges, true, false>(ctx, kp, plan, S, st, ev_owner)
+                             : launch_typed<WideEdges, false, false>(ctx, kp, plan, S, st, ev_owner);
+    return plan.segments ? launch_typed<NarrowEdges, true, false>(ctx, kp, plan, S, st, ev_owner)
+                         : launch_typed<NarrowEdges, false, false>(ctx, kp, plan, S, st, ev_owner);
 }
 
 }  // namespace ppr

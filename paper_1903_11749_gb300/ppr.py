@@ -39,7 +39,7 @@ class RunArgs(C.Structure):
                 ("src_end", C.c_int64), ("tag", C.c_uint32), ("dangling", C.c_int32), ("segments", C.c_int32),
                 ("topk", C.c_int32), ("kernel", C.c_int32), ("large_degree", C.c_int32),
                 ("warps_per_block", C.c_int32), ("chunk_sources", C.c_int32), ("max_batch_sources", C.c_int64),
-                ("stats", C.c_int32), ("fused_aggregation", C.c_int32), ("stream", C.c_void_p)]
+                ("stats", C.c_int32), ("stream", C.c_void_p)]
 
 
 class ResultInfo(C.Structure):
@@ -192,7 +192,7 @@ class Graph:
 
     def run(self, alpha=0.15, R=100, seed=1, src_begin=0, src_end=None, tag=0, dangling=0, segments=False,
             topk=0, kernel=KERNEL_PERSISTENT, large_degree=0, warps_per_block=0, chunk_sources=0,
-            max_batch_sources=0, stats=False, fused_aggregation=False, stream=None, wait=True) -> "Result":
+            max_batch_sources=0, stats=False, stream=None, wait=True) -> "Result":
         a = RunArgs()
         lib().ppr_run_args_init(C.byref(a))
         a.alpha, a.R, a.seed = alpha, R, seed
@@ -202,7 +202,6 @@ class Graph:
         a.large_degree, a.warps_per_block, a.chunk_sources = large_degree, warps_per_block, chunk_sources
         a.max_batch_sources = max_batch_sources
         a.stats = int(bool(stats))
-        a.fused_aggregation = int(bool(fused_aggregation))
         a.stream = _stream_ptr(stream)
         h = C.c_void_p()
         _check(lib().ppr_run(self.ctx.h, self.h, C.byref(a), C.byref(h)))

@@ -102,7 +102,7 @@ def test_batches_and_chunking_do_not_change_results(ppr, ctx, oracle):
     ref = oracle_rows(oracle, g, 0.15, 60, 7, topk=4)
     for kw in (dict(kernel=1, max_batch_sources=33), dict(chunk_sources=1), dict(chunk_sources=13, warps_per_block=2),
                dict(chunk_sources=64, warps_per_block=1), dict(max_batch_sources=250),
-               dict(fused_aggregation=True), dict(fused_aggregation=True, chunk_sources=3, max_batch_sources=101)):
+               dict(chunk_sources=3, max_batch_sources=101)):
         assert_same(G.run(alpha=0.15, R=60, seed=7, topk=4, **kw), ref, topk=4)
 
 
