@@ -219,6 +219,37 @@ int ppr_dense(const ppr_result *r, uint32_t *out, uint32_t flags);
 
 void ppr_free_result(ppr_result *r);
 
+/*
+ * Allocation-free run (no counterpart in the paper: it serves callers, not the
+ * method).  Some callers cannot allocate device memory while they work: a
+ * process whose other framework already holds nearly all device memory in its
+ * own caching pool, or a serving loop that must not take the time or the risk
+ * of a driver allocation once it is running.  This entry point runs the same
+ * walks and reduction as ppr_run with the persistent kernel but makes no
+ * allocation of any kind: the caller passes the graph (already loaded) and
+ * device output buffers, and the per-walk endpoints live in a fixed 64 MiB
+ * scratch array that the library keeps in device memory on every GPU that
+ * loads it, until the process exits.
+ *   nnz      uint32[S]            distinct endpoints of each source
+ *   cols     int32[S * cap]       row s at cols[s*cap .. s*cap+nnz[s]), end ids ascending
+ *   cnts     uint32[S * cap]      the matching counts (each row sums to R)
+ *   cap      >= min(R, n)
+ *   topk_idx, topk_cnt  S * topk entries as ppr_topk, or NULL when topk = 0
+ * S * R may be at most 16,777,152 walks (64 MiB minus a 256-byte header, 4 B
+ * per walk); larger calls fail with PPR_ERANGE before any work is queued.
+ * Plain graphs and args->kernel = PPR_KERNEL_PERSISTENT only; segment mode
+ * needs tables already built for this alpha by an earlier ppr_run.
+ * The work is queued on args->stream and the call returns at once: the
+ * outputs are valid after that stream is synchronized.  The first call on a
+ * device looks up the scratch array's device address (cudaGetSymbolAddress)
+ * for that device; make that first call before any stream capture.  Every
+ * call shares the one scratch array, whose counters each call clears and
+ * whose contents a later call overwrites: calls whose work overlaps on the
+ * GPU (other streams, or without a synchronization between them) race.
+ */
+int ppr_run_noalloc(ppr_ctx *ctx, const ppr_graph *g, const ppr_run_args *args, uint32_t *nnz, int32_t *cols,
+                    uint32_t *cnts, uint32_t cap, int32_t *topk_idx, uint32_t *topk_cnt);
+
 #ifdef __cplusplus
 }
 #endif

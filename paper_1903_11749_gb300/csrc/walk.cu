@@ -17,6 +17,7 @@
 //                    whole warp, and aggregate a chunk in shared memory as soon
 //                    as its last walk ends.
 #include <algorithm>
+#include <mutex>
 
 #include "ppr_host.h"
 
@@ -463,4 +464,130 @@ int launch_walks(ppr_ctx *ctx, const ppr_graph *g, const RunPlan &plan, ppr_resu
                          : launch_typed<NarrowEdges, false, false>(ctx, kp, plan, S, st, ev_owner);
 }
 
+// ------------------------------------------------ allocation-free run ----
+// Scratch for ppr_run_noalloc: a fixed array in device memory that exists on
+// every GPU where this library's kernels are loaded, for the life of the
+// process.  Layout: 256-byte header (steps, queue, sectors counters), then
+// one 4-byte endpoint per walk.
+constexpr size_t kNoAllocBytes = 64ull << 20;
+constexpr size_t kNoAllocHeader = 256;
+static __device__ __align__(256) unsigned char g_noalloc_scratch[kNoAllocBytes];
+
+// Device addresses of g_noalloc_scratch, one per device, fetched on the first
+// call for that device (the host-side symbol is only a stand-in).
+static void *g_noalloc_ptr[64];
+static std::mutex g_noalloc_mu;
+
+static int noalloc_scratch(int device, unsigned char **out)
+{
+    if (device < 0 || device >= 64) {
+        set_error("device %d out of range for the allocation-free entry point", device);
+        return PPR_EINVAL;
+    }
+    std::lock_guard<std::mutex> lock(g_noalloc_mu);
+    if (!g_noalloc_ptr[device]) {
+        void *ptr = nullptr;
+        cudaError_t e = cudaGetSymbolAddress(&ptr, g_noalloc_scratch);  // device is current
+        if (e != cudaSuccess) return cuda_fail(e, "cudaGetSymbolAddress(scratch)");
+        g_noalloc_ptr[device] = ptr;
+    }
+    *out = static_cast<unsigned char *>(g_noalloc_ptr[device]);
+    return PPR_OK;
+}
+
 }  // namespace ppr
+
+using namespace ppr;
+
+extern "C" int ppr_run_noalloc(ppr_ctx *ctx, const ppr_graph *g, const ppr_run_args *a, uint32_t *nnz, int32_t *cols,
+                               uint32_t *cnts, uint32_t cap, int32_t *topk_idx, uint32_t *topk_cnt)
+{
+    if (!ctx || !g || !a || !nnz || !cols || !cnts) {
+        set_error("NULL argument");
+        return PPR_EINVAL;
+    }
+    const uint32_t T = ppr_alpha_threshold(a->alpha);
+    if (T == 0) {
+        set_error("alpha = %g: need 0 < alpha < 1 and floor(alpha * 2^32) >= 1", a->alpha);
+        return PPR_EINVAL;
+    }
+    if (a->R < 1 || a->R > PPR_MAX_R) {
+        set_error("R = %u outside [1, %u]", a->R, PPR_MAX_R);
+        return a->R < 1 ? PPR_EINVAL : PPR_ERANGE;
+    }
+    if (a->src_begin < 0 || a->src_end > g->n || a->src_begin >= a->src_end) {
+        set_error("source range [%lld, %lld) must be non-empty and inside [0, %lld)", (long long)a->src_begin,
+                  (long long)a->src_end, (long long)g->n);
+        return PPR_EINVAL;
+    }
+    if (a->topk < 0 || (uint32_t)a->topk > a->R || (a->topk > 0 && (!topk_idx || !topk_cnt))) {
+        set_error("topk = %d outside [0, R], or top-k outputs missing", a->topk);
+        return PPR_EINVAL;
+    }
+    if ((a->dangling != 0 && a->dangling != 1) || (a->segments != 0 && a->segments != 1) || a->large_degree < 0 ||
+        a->chunk_sources < 0 || a->kernel != PPR_KERNEL_PERSISTENT || a->stats != 0) {
+        set_error("invalid mode for the allocation-free run (persistent kernel, no statistics)");
+        return PPR_EINVAL;
+    }
+    if (g->instances > 0) {
+        set_error("the allocation-free run takes plain graphs only");
+        return PPR_ENOTSUP;
+    }
+    if (a->segments && !(g->seg.T == T && g->seg.node)) {
+        set_error("segment tables for this alpha are not built (a ppr_run with segments=1 builds them)");
+        return PPR_ENOTSUP;
+    }
+    const uint32_t need_cap = (uint32_t)std::min<int64_t>((int64_t)a->R, g->n);
+    if (cap < need_cap) {
+        set_error("row capacity %u < min(R, n) = %u", cap, need_cap);
+        return PPR_EINVAL;
+    }
+    const int64_t S = a->src_end - a->src_begin;
+    const size_t need = kNoAllocHeader + (size_t)S * a->R * sizeof(uint32_t);
+    if (need > kNoAllocBytes) {
+        set_error("allocation-free run needs %zu bytes of scratch for %lld sources x %u walks; the fixed scratch "
+                  "holds %zu (at most %zu walks per call)",
+                  need, (long long)S, a->R, kNoAllocBytes, (kNoAllocBytes - kNoAllocHeader) / sizeof(uint32_t));
+        return PPR_ERANGE;
+    }
+    cudaError_t e = cudaSetDevice(ctx->device);
+    if (e != cudaSuccess) return cuda_fail(e, "cudaSetDevice");
+    unsigned char *scratch = nullptr;
+    int rc = noalloc_scratch(ctx->device, &scratch);
+    if (rc) return rc;
+    cudaStream_t st = (cudaStream_t)a->stream;
+    // the counters must start at zero on every call; endpoints are overwritten
+    e = cudaMemsetAsync(scratch, 0, kNoAllocHeader, st);
+    if (e != cudaSuccess) return cuda_fail(e, "cudaMemsetAsync(scratch header)");
+
+    RunPlan plan{};
+    plan.T = T;
+    plan.R = a->R;
+    plan.seed = a->seed;
+    plan.tag = a->tag;
+    plan.dangling = a->dangling;
+    plan.segments = a->segments != 0;
+    plan.kernel = PPR_KERNEL_PERSISTENT;
+    plan.large_degree = a->large_degree;
+    plan.warps_per_block = a->warps_per_block;
+    plan.chunk_sources = a->chunk_sources;
+    plan.stats = false;
+    ppr_result out{};  // describes the caller's buffers; owns nothing
+    out.d_nnz = nnz;
+    out.d_cols = cols;
+    out.d_cnts = cnts;
+    out.d_topk_idx = topk_idx;
+    out.d_topk_cnt = topk_cnt;
+    out.cap = cap;
+    out.topk = a->topk;
+    out.d_steps = reinterpret_cast<unsigned long long *>(scratch);
+    uint32_t *ends = reinterpret_cast<uint32_t *>(scratch + kNoAllocHeader);
+    rc = launch_walks(ctx, g, plan, &out, a->src_begin, a->src_end, 0, ends, out.d_steps + 1, st, false);
+    out.d_nnz = nullptr;  // not freed: the buffers belong to the caller
+    out.d_cols = nullptr;
+    out.d_cnts = nullptr;
+    out.d_topk_idx = nullptr;
+    out.d_topk_cnt = nullptr;
+    out.d_steps = nullptr;
+    return rc;
+}

@@ -72,6 +72,8 @@ _SIGS = {
     "ppr_topk": (C.c_int, [C.c_void_p, C.c_int32, C.c_void_p, C.c_void_p, C.c_uint32]),
     "ppr_dense": (C.c_int, [C.c_void_p, C.c_void_p, C.c_uint32]),
     "ppr_free_result": (None, [C.c_void_p]),
+    "ppr_run_noalloc": (C.c_int, [C.c_void_p, C.c_void_p, C.POINTER(RunArgs), C.c_void_p, C.c_void_p, C.c_void_p,
+                                  C.c_uint32, C.c_void_p, C.c_void_p]),
 }
 
 _lib = None
@@ -209,6 +211,22 @@ class Graph:
         if wait:
             r.wait()
         return r
+
+    def run_noalloc(self, nnz, cols, cnts, cap, topk_idx=None, topk_cnt=None, alpha=0.15, R=100, seed=1,
+                    src_begin=0, src_end=None, tag=0, dangling=0, segments=False, topk=0, stream=None):
+        """Allocation-free run into caller-owned device tensors (see ppr_run_noalloc in include/ppr.h);
+        returns once the work is queued on `stream`."""
+        a = RunArgs()
+        lib().ppr_run_args_init(C.byref(a))
+        a.alpha, a.R, a.seed = alpha, R, seed
+        a.src_begin = src_begin
+        a.src_end = self.info().n if src_end is None else src_end
+        a.tag, a.dangling, a.segments, a.topk = tag, dangling, int(bool(segments)), topk
+        a.stream = _stream_ptr(stream)
+        ti = _ptr(topk_idx)[0] if topk_idx is not None else None
+        tc = _ptr(topk_cnt)[0] if topk_cnt is not None else None
+        _check(lib().ppr_run_noalloc(self.ctx.h, self.h, C.byref(a), _ptr(nnz)[0], _ptr(cols)[0], _ptr(cnts)[0],
+                                     cap, ti, tc))
 
 
 class Result:
