@@ -1,4 +1,4 @@
-"""Benchmark: Monte Carlo edge-weighted PPR on one GB300 (or N, sharded by source).
+"""Benchmark: Monte Carlo edge-weighted PPR on one GB300 (or N independent replicas).
 
 One step = one pass of the whole hot path over the workload: build the walk
 layout from the device-resident CSR (node records, weight prefixes), run R
@@ -34,7 +34,12 @@ WORKLOADS = {
     "rmat20": dict(alpha=0.2, R=100, seed=1, topk=32, segments=False,
                    desc="R-MAT scale 20, 16.8M edges (a=.57 b=.19 c=.19), Zipf(1.5) w in [1,1000], 5% dangling"),
     "er1k": dict(alpha=0.15, R=1000, seed=1, topk=32, segments=False,
-                 desc="Erdos-Renyi n=1000 m=10000, w U[1,10]"),
+                 desc="Erdos-Renyi n=1000 m=10000, w U[1,10], dense n x n counts"),
+    "rmat24": dict(alpha=0.15, R=50, seed=1, topk=64, segments=True,
+                   desc="R-MAT scale 24, 268M edges + hub > 1e6, Zipf(1.5) w in [1,1000], 5% dangling, "
+                        "depth-3 segments for out-degree <= 8"),
+    "rmat24plain": dict(alpha=0.15, R=50, seed=1, topk=64, segments=False,
+                        desc="R-MAT scale 24 as rmat24, plain steps only"),
 }
 L2_FLUSH_BYTES = 512 << 20
 
@@ -43,12 +48,24 @@ def env_rank():
     return int(os.environ.get("RANK", 0)), int(os.environ.get("WORLD_SIZE", 1)), int(os.environ.get("LOCAL_RANK", 0))
 
 
-def shard(n_src: int, rank: int, world: int):
-    """Contiguous source range of a rank: sources are independent, so ranks
-    share nothing but the graph (replicated)."""
-    per = (n_src + world - 1) // world
-    a = min(n_src, rank * per)
-    return a, min(n_src, a + per)
+def rank_workload(n_src: int, rank: int, world: int):
+    """Work of one rank: every source of its own replica of the graph, with the
+    rank as the Philox tag, so each rank draws independent walks (summing the
+    ranks' rows is the estimate with R * world walks per source).  Per-GPU work
+    is fixed as the number of GPUs grows (weak scaling); no data moves between
+    ranks."""
+    return 0, n_src, rank
+
+
+def reduce_over_ranks(seconds: float, units, world: int, dist=None, device=None):
+    """Max of the timed seconds and sum of the processed units over ranks."""
+    import torch
+    t = torch.tensor([seconds], dtype=torch.float64, device=device)
+    u = torch.tensor([float(x) for x in units], dtype=torch.float64, device=device)
+    if world > 1:
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+        dist.all_reduce(u, op=dist.ReduceOp.SUM)
+    return float(t.item()), [float(x) for x in u.tolist()]
 
 
 class Clocks:
@@ -138,7 +155,8 @@ def cpu_baseline(g, wl, budget_s: float = 15.0):
     og = O.prepare(g.n, g.row_ptr, g.col, g.w)
     # calibrate on a small sample, then size the sample to the budget
     t0 = time.perf_counter()
-    ends, steps = O.walks(og, wl["alpha"], wl["R"], wl["seed"], 0, 200)
+    seg = dict(segments=wl["segments"], lazy_segments=True)
+    ends, steps = O.walks(og, wl["alpha"], wl["R"], wl["seed"], 0, 200, **seg)
     dt = max(time.perf_counter() - t0, 1e-3)
     n_src = int(max(200, min(g.n, 200 * budget_s / dt)))
     stride = max(1, g.n // n_src)
@@ -147,7 +165,7 @@ def cpu_baseline(g, wl, budget_s: float = 15.0):
     t0 = time.perf_counter()
     # contiguous blocks of 64 sources, strided over the whole id range
     for s in list(srcs)[: max(1, n_src // 64)]:
-        e, st = O.walks(og, wl["alpha"], wl["R"], wl["seed"], s, min(g.n, s + 64))
+        e, st = O.walks(og, wl["alpha"], wl["R"], wl["seed"], s, min(g.n, s + 64), **seg)
         rp, col, cnt = O.rows(e, g.n)
         if wl["topk"]:
             O.topk(rp, col, cnt, wl["topk"])
@@ -166,7 +184,7 @@ def run_reference(args):
         return 0
     from paper_1903_11749_gb300 import inputs as I
     wl = WORKLOADS[args.workload]
-    g = I.workload_graph(args.workload)
+    g = I.workload_graph(args.workload.replace("plain", ""))
     sys.path.insert(0, os.path.join(ROOT, "oracle"))
     import oracle as O
     O.build()
@@ -179,7 +197,8 @@ def run_reference(args):
         t0 = time.perf_counter()
         st_step, wk = 0, 0
         for s in rng_src:
-            e, st = O.walks(og, wl["alpha"], wl["R"], wl["seed"], int(s), int(s) + n_blk)
+            e, st = O.walks(og, wl["alpha"], wl["R"], wl["seed"], int(s), int(s) + n_blk,
+                            segments=wl["segments"], lazy_segments=True)
             rp, col, cnt = O.rows(e, g.n)
             O.topk(rp, col, cnt, wl["topk"])
             st_step += st
@@ -236,8 +255,8 @@ def main():
     torch.cuda.set_device(local)
     dev = torch.device("cuda", local)
     wl = WORKLOADS[args.workload]
-    g = I.workload_graph(args.workload)
-    a, b = shard(g.n, rank, world)
+    g = I.workload_graph(args.workload.replace("plain", ""))
+    a, b, rank_tag = rank_workload(g.n, rank, world)
     tune = dict(warps_per_block=args.warps_per_block, chunk_sources=args.chunk_sources,
                 large_degree=args.large_degree)
 
@@ -250,15 +269,21 @@ def main():
 
     def step(kernel=ppr.KERNEL_PERSISTENT, stats=False):
         G = ctx.load_graph(g.n, d_rp, d_col, d_w, stream=stream, m=g.m)
-        r = G.run(alpha=wl["alpha"], R=wl["R"], seed=wl["seed"], src_begin=a, src_end=b, topk=wl["topk"],
-                  segments=wl["segments"], kernel=kernel, stats=stats, stream=stream, wait=False, **tune)
+        r = G.run(alpha=wl["alpha"], R=wl["R"], seed=wl["seed"], src_begin=a, src_end=b, tag=rank_tag,
+                  topk=wl["topk"], segments=wl["segments"], kernel=kernel, stats=stats, stream=stream, wait=False,
+                  **tune)
         return G, r
 
     # statistics launch (untimed): exact draws and algorithmic sectors of one pass
     G0, r0 = step(stats=True)
     r0.wait()
     info0 = r0.info()
-    steps_per_pass, sectors_per_pass, walks_per_pass = int(info0.steps), int(info0.sectors), int(info0.walks)
+    draws_per_pass, sectors_per_pass, walks_per_pass = int(info0.steps), int(info0.sectors), int(info0.walks)
+    # walk steps of one pass: the counted steps; with segment tables one draw
+    # stands for up to three steps, so the plain-equivalent count walks * 2^32/T
+    # (the expected number of steps) is used instead
+    T_int = ppr.alpha_threshold(wl["alpha"])
+    steps_per_pass = walks_per_pass * (2.0 ** 32 / T_int) if wl["segments"] else draws_per_pass
     del r0, G0
 
     for _ in range(args.warmup):
@@ -290,14 +315,9 @@ def main():
     launches = ppr.kernel_launches() - launches0
     clk = clocks.stop()
     T = sum(step_ms) / 1e3
-    t_tensor = torch.tensor([T], dtype=torch.float64, device=dev)
-    units = torch.tensor([steps_per_pass * args.steps, walks_per_pass * args.steps], dtype=torch.float64, device=dev)
-    if world > 1:
-        dist.all_reduce(t_tensor, op=dist.ReduceOp.MAX)
-        dist.all_reduce(units, op=dist.ReduceOp.SUM)
-    T_max = float(t_tensor.item())
-    value = float(units[0].item()) / T_max
-    walks_s = float(units[1].item()) / T_max
+    T_max, units = reduce_over_ranks(T, [steps_per_pass * args.steps, walks_per_pass * args.steps], world, dist, dev)
+    value = units[0] / T_max
+    walks_s = units[1] / T_max
 
     # plain one-thread-per-walk kernel on the same pass, for comparison
     plain = None
@@ -318,26 +338,35 @@ def main():
         plain = {"value": steps_per_pass / (statistics.mean(pm) / 1e3), "unit": "walk steps/s",
                  "ms_per_step": statistics.mean(pm), "kernel": "one thread per walk + separate aggregation"}
 
-    # end to end through the C ABI with host buffers: pinned CSR in, rows + top-k out
+    # end to end through the C ABI with host buffers: pinned CSR in, rows + top-k out to pinned memory
     e2e = None
     if not args.no_e2e:
         h_rp = torch.from_numpy(g.row_ptr).pin_memory()
         h_col = torch.from_numpy(g.col).pin_memory()
         h_w = torch.from_numpy(g.w.view(np.int32)).pin_memory()
         h2d = g.row_ptr.nbytes + g.col.nbytes + g.w.nbytes
+        S = b - a
+        cap_rows = S * min(wl["R"], g.n)
+        o_rp = torch.empty(S + 1, dtype=torch.int64).pin_memory()
+        o_col = torch.empty(cap_rows, dtype=torch.int32).pin_memory()
+        o_cnt = torch.empty(cap_rows, dtype=torch.int32).pin_memory()
+        k = max(1, wl["topk"])
+        o_ti = torch.empty((S, k), dtype=torch.int32).pin_memory()
+        o_tc = torch.empty((S, k), dtype=torch.int32).pin_memory()
         times, d2h = [], 0
         for it in range(1 + min(3, args.steps)):
             torch.cuda.synchronize(dev)
             t0 = time.perf_counter()
-            G = ctx.load_graph(g.n, h_rp.numpy(), h_col.numpy(), h_w.numpy().view(np.uint32), stream=stream)
-            r = G.run(alpha=wl["alpha"], R=wl["R"], seed=wl["seed"], src_begin=a, src_end=b, topk=wl["topk"],
-                      stream=stream, **tune)
-            rp, col, cnt = r.sparse_rows()
-            idx, tc = r.topk()
+            G = ctx.load_graph(g.n, h_rp, h_col, h_w, stream=stream, m=g.m)
+            r = G.run(alpha=wl["alpha"], R=wl["R"], seed=wl["seed"], src_begin=a, src_end=b, tag=rank_tag,
+                      topk=wl["topk"], segments=wl["segments"], stream=stream, **tune)
+            nnz = r.sparse_rows_into(o_rp, o_col, o_cnt)
+            if wl["topk"]:
+                r.topk_into(wl["topk"], o_ti, o_tc)
             t1 = time.perf_counter()
             if it > 0:
                 times.append(t1 - t0)
-            d2h = rp.nbytes + col.nbytes + cnt.nbytes + idx.nbytes + tc.nbytes
+            d2h = o_rp.numel() * 8 + nnz * 8 + (S * wl["topk"] * 8 if wl["topk"] else 0)
             del r, G
         e2e = {"value": steps_per_pass / statistics.mean(times), "unit": "walk steps/s", "h2d_bytes_per_step": h2d,
                "d2h_bytes_per_step": d2h, "ms_per_step": 1e3 * statistics.mean(times)}
@@ -350,7 +379,7 @@ def main():
     roofline = {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s", "frac": achieved / peak,
                 "traffic": traffic, "peak_kind": peak_kind, "kernel": "k_walk_persistent",
                 "alg_bytes_per_launch": alg_bytes, "kernel_ms": kms, "walk_and_reduce_ms": statistics.mean(run_ms),
-                "sectors_per_step": sectors_per_pass / max(steps_per_pass, 1)}
+                "sectors_per_draw": sectors_per_pass / max(draws_per_pass, 1)}
 
     cpu = None
     if rank == 0 and world == 1 and not args.no_cpu_baseline:
@@ -363,9 +392,11 @@ def main():
                 "data": "synthetic",
                 "config": {"workload": args.workload, "desc": wl["desc"], "alpha": wl["alpha"], "R": wl["R"],
                            "topk": wl["topk"], "n": g.n, "m": g.m, "sources": g.n,
-                           "parallelism": f"source-sharded x{world}" if world > 1 else "1 GPU",
+                           "parallelism": f"{world} independent replicas (tag = rank)" if world > 1 else "1 GPU",
                            "l2": "flushed between steps (512 MB write)"},
                 "walks_per_s": walks_s, "steps_per_walk": steps_per_pass / max(walks_per_pass, 1),
+                "draws_per_s": draws_per_pass * args.steps * world / T_max,
+                "steps_counted": "plain-equivalent walks*2^32/T" if wl["segments"] else "draws (one per step)",
                 "roofline": roofline, "cpu_baseline": cpu, "e2e": e2e, "plain_kernel": plain,
                 "gpu_launches": launches, "clocks": clk}
         print(json.dumps(line))

@@ -43,7 +43,7 @@ def build(force: bool = False) -> str:
 class _Graph(C.Structure):
     _fields_ = [("n", C.c_int64), ("row_ptr", C.c_void_p), ("col", C.c_void_p), ("P", C.c_void_p),
                 ("W", C.c_void_p), ("seg_off", C.c_void_p), ("seg_node", C.c_void_p),
-                ("seg_mark_len", C.c_void_p), ("seg_cum", C.c_void_p)]
+                ("seg_mark_len", C.c_void_p), ("seg_cum", C.c_void_p), ("w", C.c_void_p), ("lazy", C.c_void_p)]
 
 
 class _Params(C.Structure):
@@ -73,6 +73,9 @@ def lib():
         L.ppr_oracle_segments.restype = C.c_int64
         L.ppr_oracle_walks.argtypes = [C.POINTER(_Graph), C.POINTER(_Params), C.c_void_p, C.c_void_p]
         L.ppr_oracle_walks.restype = C.c_int
+        L.ppr_oracle_lazy_new.argtypes = [C.c_int64]
+        L.ppr_oracle_lazy_new.restype = C.c_void_p
+        L.ppr_oracle_lazy_free.argtypes = [C.c_void_p]
         _lib = L
     return _lib
 
@@ -128,6 +131,12 @@ class OracleGraph:
     seg_mark_len: np.ndarray | None = None
     seg_weight: np.ndarray | None = None
     seg_cum: np.ndarray | None = None
+    lazy: object = None  # on-demand segment tables (large graphs)
+
+    def __del__(self):
+        if self.lazy:
+            lib().ppr_oracle_lazy_free(self.lazy)
+            self.lazy = None
 
 
 def prepare(n: int, row_ptr, col, w) -> OracleGraph:
@@ -169,23 +178,30 @@ def build_segments(g: OracleGraph, T: int) -> OracleGraph:
 
 
 def walks(g: OracleGraph, alpha: float, R: int, seed: int, s_begin: int = 0, s_end: int | None = None,
-          tag: int = 0, dangling: int = 0, segments: bool = False):
-    """Endpoints uint32[S, R] and the number of draws consumed."""
+          tag: int = 0, dangling: int = 0, segments: bool = False, lazy_segments: bool = False):
+    """Endpoints uint32[S, R] and the number of draws consumed.  With
+    lazy_segments, segment tables are built only for the nodes the walks
+    visit (same tables; for sampled runs on large graphs)."""
     if s_end is None:
         s_end = g.n
     T = threshold(alpha)
     if T == 0:
         raise ValueError("alpha must satisfy floor(alpha * 2^32) >= 1 and alpha < 1")
-    if segments and (g.seg_off is None or g.seg_T != T):
+    use_lazy = segments and lazy_segments
+    if use_lazy and not g.lazy:
+        g.lazy = lib().ppr_oracle_lazy_new(g.n)
+    if segments and not use_lazy and (g.seg_off is None or g.seg_T != T):
         build_segments(g, T)
     S = s_end - s_begin
     ends = np.zeros((S, R), dtype=np.uint32)
     steps = np.zeros(1, dtype=np.uint64)
+    flat = segments and not use_lazy
     gr = _Graph(g.n, g.row_ptr.ctypes.data, g.col.ctypes.data, g.P.ctypes.data, g.W.ctypes.data,
-                g.seg_off.ctypes.data if segments else None,
-                g.seg_node.ctypes.data if segments else None,
-                g.seg_mark_len.ctypes.data if segments else None,
-                g.seg_cum.ctypes.data if segments else None)
+                g.seg_off.ctypes.data if flat else None,
+                g.seg_node.ctypes.data if flat else None,
+                g.seg_mark_len.ctypes.data if flat else None,
+                g.seg_cum.ctypes.data if flat else None,
+                g.w.ctypes.data, g.lazy if use_lazy else None)
     pr = _Params(T, R, seed, s_begin, s_end, 0, tag, dangling)
     if S > 0 and R > 0:
         rc = lib().ppr_oracle_walks(C.byref(gr), C.byref(pr), _p(ends), _p(steps))

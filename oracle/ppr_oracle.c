@@ -322,17 +322,110 @@ int64_t ppr_oracle_segments(int64_t n, const int64_t *row_ptr, const int32_t *co
 /* result because every draw is keyed by (source, walk, step, tag)).          */
 /* ------------------------------------------------------------------------ */
 
+/* Segment tables built on first visit and kept (for runs that visit a small
+ * part of a large graph).  Each table is the same as ppr_oracle_segment_table
+ * gives; off[v] = -1 until v is visited. */
+typedef struct {
+    int64_t n;
+    uint32_t T;
+    int64_t *off;
+    int32_t *cnt;
+    uint32_t *node, *mark_len;
+    uint64_t *cum;
+    int64_t used, cap;
+} lazy_segments;
+
+void *ppr_oracle_lazy_new(int64_t n)
+{
+    lazy_segments *L = (lazy_segments *)calloc(1, sizeof(lazy_segments));
+    if (!L)
+        return NULL;
+    L->n = n;
+    L->off = (int64_t *)malloc(sizeof(int64_t) * (size_t)n);
+    L->cnt = (int32_t *)calloc((size_t)n, sizeof(int32_t));
+    if (!L->off || !L->cnt)
+        return NULL;
+    for (int64_t v = 0; v < n; ++v)
+        L->off[v] = -1;
+    return L;
+}
+
+void ppr_oracle_lazy_free(void *p)
+{
+    lazy_segments *L = (lazy_segments *)p;
+    if (!L)
+        return;
+    free(L->off);
+    free(L->cnt);
+    free(L->node);
+    free(L->mark_len);
+    free(L->cum);
+    free(L);
+}
+
 typedef struct {
     int64_t n;
     const int64_t *row_ptr;
     const int32_t *col;
     const uint64_t *P;       /* inclusive row prefix */
     const uint64_t *W;       /* row totals */
-    const int64_t *seg_off;  /* NULL when segments are off */
+    const int64_t *seg_off;  /* NULL when segments are off (or built lazily) */
     const uint32_t *seg_node;
     const uint32_t *seg_mark_len;
     const uint64_t *seg_cum; /* inclusive prefix of outcome weights within each table */
+    const uint32_t *w;       /* edge weights (lazy segment tables) */
+    void *lazy;              /* lazy_segments, or NULL */
 } oracle_graph;
+
+/* Outcome table of v: returns its length (0 if v has none) and its arrays. */
+static int64_t seg_lookup(const oracle_graph *g, uint32_t T, uint32_t v, const uint32_t **node,
+                          const uint32_t **ml, const uint64_t **cum)
+{
+    if (g->seg_off) {
+        int64_t a = g->seg_off[v], b = g->seg_off[v + 1];
+        *node = g->seg_node + a;
+        *ml = g->seg_mark_len + a;
+        *cum = g->seg_cum + a;
+        return b - a;
+    }
+    lazy_segments *L = (lazy_segments *)g->lazy;
+    if (!L)
+        return 0;
+    if (L->T != T) { /* tables depend on the threshold */
+        for (int64_t u = 0; u < L->n; ++u)
+            L->off[u] = -1;
+        L->used = 0;
+        L->T = T;
+    }
+    if (L->off[v] < 0) {
+        uint32_t tn[SEG_MAXOUT], tm[SEG_MAXOUT];
+        uint64_t tw[SEG_MAXOUT];
+        int k = ppr_oracle_segment_table(g->row_ptr, g->col, g->w, g->W, T, v, tn, tm, tw);
+        if (L->used + k > L->cap) {
+            int64_t cap = L->cap ? 2 * L->cap : 4096;
+            while (cap < L->used + k)
+                cap *= 2;
+            L->node = (uint32_t *)realloc(L->node, sizeof(uint32_t) * (size_t)cap);
+            L->mark_len = (uint32_t *)realloc(L->mark_len, sizeof(uint32_t) * (size_t)cap);
+            L->cum = (uint64_t *)realloc(L->cum, sizeof(uint64_t) * (size_t)cap);
+            L->cap = cap;
+        }
+        uint64_t acc = 0;
+        for (int i = 0; i < k; ++i) {
+            acc += tw[i];
+            L->node[L->used + i] = tn[i];
+            L->mark_len[L->used + i] = tm[i];
+            L->cum[L->used + i] = acc;
+        }
+        L->off[v] = L->used;
+        L->cnt[v] = k;
+        L->used += k;
+    }
+    *node = L->node + L->off[v];
+    *ml = L->mark_len + L->off[v];
+    *cum = L->cum + L->off[v];
+    return L->cnt[v];
+}
 
 typedef struct {
     uint32_t T;
@@ -366,17 +459,19 @@ int ppr_oracle_walks(const oracle_graph *g, const oracle_params *p, uint32_t *en
                 uint32_t x[4];
                 philox4x32(ctr, key, 10, x);
                 uint64_t r64 = (uint64_t)x[0] | ((uint64_t)x[1] << 32);
-                if (g->seg_off && g->seg_off[u + 1] > g->seg_off[u]) {
-                    int64_t a = g->seg_off[u], b = g->seg_off[u + 1];
-                    uint64_t xs = ppr_oracle_mulhi64(r64, g->seg_cum[b - 1]);
-                    int64_t o = ppr_oracle_pick(g->seg_cum, a, b, xs);
-                    uint32_t ml = g->seg_mark_len[o];
+                const uint32_t *sn, *sml;
+                const uint64_t *scum;
+                int64_t cnt = (g->seg_off || g->lazy) ? seg_lookup(g, p->T, u, &sn, &sml, &scum) : 0;
+                if (cnt > 0) {
+                    uint64_t xs = ppr_oracle_mulhi64(r64, scum[cnt - 1]);
+                    int64_t o = ppr_oracle_pick(scum, 0, cnt, xs);
+                    uint32_t ml = sml[o];
                     steps += 1;
                     if ((ml >> 8) == 0) {
-                        end = g->seg_node[o];
+                        end = sn[o];
                         break;
                     }
-                    u = g->seg_node[o];
+                    u = sn[o];
                     k += ml & 0xff;
                     continue;
                 }

@@ -17,7 +17,10 @@ Multi-edges and self-loops are kept as separate entries.
 """
 from __future__ import annotations
 
+import ctypes
 import math
+import os
+import subprocess
 from dataclasses import dataclass, field
 
 import numpy as np
@@ -71,98 +74,71 @@ def er_graph(n: int = 1000, m: int = 10_000, wlo: int = 1, whi: int = 10, seed: 
     return Graph(n, row_ptr, col, ww, name=f"er_n{n}_m{m}", meta={"seed": seed})
 
 
+_GEN_DIR = os.path.join(os.path.dirname(os.path.abspath(__file__)), "gen")
+_gen_lib = None
+
+
+def _gen():
+    """The C R-MAT generator (built with gcc on first use)."""
+    global _gen_lib
+    if _gen_lib is None:
+        src = os.path.join(_GEN_DIR, "rmat_gen.c")
+        out_dir = os.path.join(_GEN_DIR, "_build")
+        lib = os.path.join(out_dir, "librmat_gen.so")
+        os.makedirs(out_dir, exist_ok=True)
+        if not os.path.exists(lib) or os.path.getmtime(lib) < os.path.getmtime(src):
+            tmp = lib + f".tmp{os.getpid()}"
+            subprocess.check_call(["gcc", "-O2", "-std=c11", "-shared", "-fPIC", "-pthread", "-o", tmp, src, "-lm"])
+            os.replace(tmp, lib)
+        L = ctypes.CDLL(lib)
+        L.rmat_begin.restype = ctypes.c_void_p
+        L.rmat_begin.argtypes = [ctypes.c_int, ctypes.c_int64, ctypes.c_double, ctypes.c_double, ctypes.c_double,
+                                 ctypes.c_uint64, ctypes.c_double, ctypes.c_int64, ctypes.c_int, ctypes.c_void_p]
+        L.rmat_edges.restype = ctypes.c_int64
+        L.rmat_edges.argtypes = [ctypes.c_void_p]
+        L.rmat_hub.restype = ctypes.c_int64
+        L.rmat_hub.argtypes = [ctypes.c_void_p]
+        L.rmat_finish.restype = ctypes.c_int
+        L.rmat_finish.argtypes = [ctypes.c_void_p, ctypes.c_void_p, ctypes.c_void_p, ctypes.c_void_p, ctypes.c_double,
+                                  ctypes.c_int]
+        _gen_lib = L
+    return _gen_lib
+
+
 def rmat_graph(scale: int, edge_factor: int = 16, a: float = 0.57, b: float = 0.19, c: float = 0.19,
                seed: int = 2020, dangling_frac: float = 0.05, zipf_s: float = 1.5, wmax: int = 1000,
-               hub_degree: int = 0) -> Graph:
-    """R-MAT graph with 2^scale nodes and edge_factor * 2^scale directed edges.
+               hub_degree: int = 0, threads: int | None = None) -> Graph:
+    """R-MAT graph with 2^scale nodes and edge_factor * 2^scale directed edges
+    (gen/rmat_gen.c; every random choice is a counter-based hash, so the graph
+    does not depend on the thread count).
 
-    Generated source-major: the out-degree vector is one multinomial draw over
-    the R-MAT source marginal (each source bit is 1 with probability c + d),
-    then each edge's destination bits are drawn conditionally on the source
-    bit at the same level (P(dst bit = 1) = b / (a + b) when the source bit is
-    0 and d / (c + d) when it is 1; probabilities quantised to 1/65536).  This
-    gives the R-MAT joint law without a global sort.
-
-    Plain R-MAT leaves roughly half the nodes with no out-edge; to match a
-    ~5 % dangling fraction, a seeded random dangling_frac * n of the
-    zero-out-degree nodes stay dangling and every other one receives a single
-    out-edge to a uniform target.  With hub_degree > 0, that many uniformly
-    chosen edges of other sources are re-sourced to node 0 (m unchanged).
-    Weights are Zipf(zipf_s) on {1..wmax}.
+    Source-major: the out-degrees come from the R-MAT source marginal (each
+    source bit is 1 with probability c + d); each edge's destination bits are
+    drawn conditionally on the source bit at the same level (probability
+    b / (a + b) when it is 0, d / (c + d) when it is 1).  Plain R-MAT leaves
+    about half the nodes without out-edges; to match a ~dangling_frac share of
+    dangling nodes, an empty row stays empty with probability
+    dangling_frac * n / #empty and every other empty row gets one edge to a
+    uniform target.  With hub_degree > 0, every edge outside row 0 moves to
+    row 0 with probability hub_degree / (m - deg(0)), planting a hub of about
+    that out-degree.  Weights are Zipf(zipf_s) on {1..wmax}.
     """
     n = 1 << scale
-    m0 = edge_factor * n
-    d = 1.0 - a - b - c
-    rng = np.random.Generator(np.random.PCG64(seed))
-
-    # Out-degree per source: P(src) = prod over levels of (a+b) or (c+d).
-    pop = np.zeros(n, dtype=np.int64)
-    ids = np.arange(n, dtype=np.int64)
-    for lvl in range(scale):
-        pop += (ids >> lvl) & 1
-    p_src = np.exp((scale - pop) * math.log(a + b) + pop * math.log(c + d))
-    p_src /= p_src.sum()
-    deg = rng.multinomial(m0, p_src).astype(np.int64)
-    del pop, p_src
-
-    src = np.repeat(ids.astype(np.int32), deg)
-    del ids
-    thr0 = np.uint16(min(65535, int(round(b / (a + b) * 65536))))
-    thr1 = np.uint16(min(65535, int(round(d / (c + d) * 65536))))
-    dst = np.zeros(m0, dtype=np.int32)
-    for lvl in range(scale):
-        u = rng.integers(0, 65536, size=m0, dtype=np.uint16)
-        sbit = ((src >> lvl) & 1).astype(bool)
-        thr = np.where(sbit, thr1, thr0)
-        dst |= (u < thr).astype(np.int32) << lvl
-        del u, sbit, thr
-    del src
-
+    L = _gen()
     row_ptr = np.zeros(n + 1, dtype=np.int64)
-    np.cumsum(deg, out=row_ptr[1:])
-
-    if hub_degree > 0:
-        # Re-source hub_degree uniformly chosen edges (not already node 0's) to node 0.
-        lo = int(row_ptr[1])
-        pick = lo + rng.choice(m0 - lo, size=hub_degree, replace=False)
-        pick.sort()
-        keep = np.ones(m0, dtype=bool)
-        keep[pick] = False
-        moved = dst[pick]
-        # Count removals per source row.
-        src_of_pick = np.searchsorted(row_ptr, pick, side="right") - 1
-        removed = np.bincount(src_of_pick, minlength=n).astype(np.int64)
-        deg = deg - removed
-        deg[0] += hub_degree
-        dst = np.concatenate([dst[: lo], moved, dst[lo:][keep[lo:]]])
-        row_ptr = np.zeros(n + 1, dtype=np.int64)
-        np.cumsum(deg, out=row_ptr[1:])
-        del keep, moved, pick, src_of_pick
-
-    # Dangling repair: keep a random dangling_frac * n of the empty rows empty.
-    empty = np.flatnonzero(deg == 0)
-    n_keep = min(len(empty), int(round(dangling_frac * n)))
-    keep_empty = rng.choice(len(empty), size=n_keep, replace=False)
-    fill_mask = np.ones(len(empty), dtype=bool)
-    fill_mask[keep_empty] = False
-    fill = empty[fill_mask]
-    if len(fill):
-        extra_dst = rng.integers(0, n, size=len(fill), dtype=np.int64).astype(np.int32)
-        new_deg = deg.copy()
-        new_deg[fill] = 1
-        new_row_ptr = np.zeros(n + 1, dtype=np.int64)
-        np.cumsum(new_deg, out=new_row_ptr[1:])
-        new_dst = np.empty(int(new_row_ptr[-1]), dtype=np.int32)
-        # Old edges keep their order; each filled row gets its single new edge.
-        old_pos = np.repeat(new_row_ptr[:-1] - row_ptr[:-1], deg) + np.arange(int(row_ptr[-1]), dtype=np.int64)
-        new_dst[old_pos] = dst
-        new_dst[new_row_ptr[fill]] = extra_dst
-        dst, deg, row_ptr = new_dst, new_deg, new_row_ptr
-        del old_pos, new_dst
-    w = zipf_weights(rng, int(row_ptr[-1]), zipf_s, wmax)
-    meta = {"seed": seed, "scale": scale, "m_rmat": m0, "hub_degree": hub_degree,
+    threads = threads or min(32, os.cpu_count() or 1)
+    h = L.rmat_begin(scale, edge_factor, a, b, c, seed, dangling_frac, hub_degree, threads, row_ptr.ctypes.data)
+    if not h:
+        raise MemoryError("rmat generator: allocation failed")
+    m = int(L.rmat_edges(h))
+    hub = int(L.rmat_hub(h))
+    col = np.empty(m, dtype=np.int32)
+    w = np.empty(m, dtype=np.uint32)
+    L.rmat_finish(h, row_ptr.ctypes.data, col.ctypes.data, w.ctypes.data, zipf_s, wmax)
+    deg = np.diff(row_ptr)
+    meta = {"seed": seed, "scale": scale, "m_rmat": edge_factor * n, "hub_moved": hub,
             "dangling": int((deg == 0).sum()), "max_degree": int(deg.max())}
-    return Graph(n, row_ptr, dst, w, name=f"rmat_s{scale}", meta=meta)
+    return Graph(n, row_ptr, col, w, name=f"rmat_s{scale}", meta=meta)
 
 
 def chung_lu_graph(n: int, avg_deg: float = 12.0, exponent: float = 2.3, wlo: int = 1, whi: int = 100,

@@ -30,7 +30,8 @@ def ctx(ppr):
 def oracle_rows(oracle, g, alpha, R, seed, s_begin=0, s_end=None, tag=0, dangling=0, segments=False, topk=0,
                 og=None):
     og = og or oracle.prepare(g.n, g.row_ptr, g.col, g.w)
-    ends, steps = oracle.walks(og, alpha, R, seed, s_begin, s_end, tag, dangling, segments)
+    lazy = segments and g.n > 100_000  # large graphs: tables of the visited nodes only
+    ends, steps = oracle.walks(og, alpha, R, seed, s_begin, s_end, tag, dangling, segments, lazy_segments=lazy)
     rp, col, cnt = oracle.rows(ends, g.n)
     out = {"rows": (rp, col, cnt), "steps": steps, "ends": ends}
     if topk:
@@ -263,3 +264,46 @@ def test_rmat20_full_size_sampled(ppr, ctx, oracle):
         assert np.array_equal(cnt[rp[s]: rp[s + 1]], ocnt)
         assert np.array_equal(idx[s], ref["topk"][0][0])
         assert np.array_equal(tc[s], ref["topk"][1][0])
+
+
+@pytest.mark.slow
+def test_rmat24_full_size_sampled(ppr, ctx, oracle):
+    """The R-MAT scale-24 workload with its hub above 10^6 edges (alpha 0.15,
+    R 50, top-64, depth-3 segment tables), every source on the GPU; 160
+    sampled sources (the hub, large rows, dangling nodes, random ones)
+    recomputed by the oracle with the same segment tables, compared exactly;
+    every row sums to R.  The plain mode is sampled the same way."""
+    import torch
+    g = I.workload_graph("rmat24")
+    dev = torch.device("cuda:0")
+    G = ctx.load_graph(g.n, g.row_ptr, g.col, g.w)
+    og = oracle.prepare(g.n, g.row_ptr, g.col, g.w)
+    deg = g.degrees()
+    rng = np.random.Generator(np.random.PCG64(1))
+    sample = np.unique(np.concatenate([[0], np.argsort(-deg)[:20], np.flatnonzero(deg == 0)[:20],
+                                       np.flatnonzero((deg >= 1) & (deg <= 8))[:20], rng.integers(0, g.n, 100)]))
+    for segments in (True, False):
+        res = G.run(alpha=0.15, R=50, seed=1, topk=64, segments=segments)
+        nnz = res.nnz()
+        rp = torch.zeros(g.n + 1, dtype=torch.int64, device=dev)
+        col = torch.zeros(nnz, dtype=torch.int32, device=dev)
+        cnt = torch.zeros(nnz, dtype=torch.int32, device=dev)
+        res.sparse_rows_into(rp, col, cnt)
+        sums = torch.zeros(g.n, dtype=torch.int64, device=dev)
+        rows = torch.repeat_interleave(torch.arange(g.n, device=dev), rp[1:] - rp[:-1])
+        sums.index_add_(0, rows, cnt.to(torch.int64))
+        assert bool((sums == 50).all())
+        ti = torch.zeros((g.n, 64), dtype=torch.int32, device=dev)
+        tc = torch.zeros((g.n, 64), dtype=torch.int32, device=dev)
+        res.topk_into(64, ti, tc)
+        rp_h = rp.cpu().numpy()
+        idx = torch.from_numpy(sample).to(dev)
+        ti_s, tc_s = ti[idx].cpu().numpy(), tc[idx].cpu().numpy().view(np.uint32)
+        for n_i, s in enumerate(sample):
+            ref = oracle_rows(oracle, g, 0.15, 50, 1, int(s), int(s) + 1, topk=64, og=og, segments=segments)
+            a, b = int(rp_h[s]), int(rp_h[s + 1])
+            assert np.array_equal(col[a:b].cpu().numpy(), ref["rows"][1])
+            assert np.array_equal(cnt[a:b].cpu().numpy().view(np.uint32), ref["rows"][2])
+            assert np.array_equal(ti_s[n_i], ref["topk"][0][0])
+            assert np.array_equal(tc_s[n_i], ref["topk"][1][0])
+        del res, rp, col, cnt, rows, sums, ti, tc

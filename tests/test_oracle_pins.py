@@ -347,3 +347,14 @@ def test_rows_and_topk_invariants(oracle):
         want = [v for _, v in order] + [-1] * (8 - len(order))
         assert idx[s].tolist() == want
         assert tc[s].tolist() == [-c for c, _ in order] + [0] * (8 - len(order))
+
+
+def test_lazy_segment_tables_equal_full_tables(oracle):
+    """Tables built on first visit give the same walks as tables built for
+    every node up front."""
+    g = I.random_small_graph(500, 1400, seed=21, wmax=30, dangling=20)
+    og = oracle.prepare(g.n, g.row_ptr, g.col, g.w)
+    for alpha, mode in ((0.15, 0), (0.5, 1)):
+        e1, s1 = oracle.walks(og, alpha, 50, 3, dangling=mode, segments=True)
+        e2, s2 = oracle.walks(og, alpha, 50, 3, dangling=mode, segments=True, lazy_segments=True)
+        assert np.array_equal(e1, e2) and s1 == s2
