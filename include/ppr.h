@@ -156,7 +156,8 @@ typedef struct {
     uint32_t tag;        /* fourth counter word (plain graphs; batched graphs use the instance id) */
     int32_t dangling;    /* 0 restart at the source (Sec. 2.1), 1 end at the dangling node */
     int32_t segments;    /* 1: depth-3 segment tables for out-degree <= 8 (Algorithm 4) */
-    int32_t topk;        /* 0..R: per-source top-k (count desc, end id asc) kept with the rows */
+    int32_t topk;        /* 0..PPR_MAX_R: per-source top-k (count desc, end id asc) kept with the
+                            rows; entries past the row's distinct endpoints are (-1, 0) */
     int32_t kernel;      /* PPR_KERNEL_PERSISTENT or PPR_KERNEL_PLAIN */
     int32_t large_degree;/* out-degree above which the whole warp searches a lane's row
                             cooperatively (persistent kernel); 0 = never (default) */

@@ -321,8 +321,8 @@ int ppr_run(ppr_ctx *ctx, const ppr_graph *g, const ppr_run_args *a, ppr_result 
                   (long long)a->src_end, (long long)g->n);
         return PPR_EINVAL;
     }
-    if (a->topk < 0 || (uint32_t)a->topk > a->R) {
-        set_error("topk = %d outside [0, R]", a->topk);
+    if (a->topk < 0 || (uint32_t)a->topk > PPR_MAX_R) {
+        set_error("topk = %d outside [0, %u]", a->topk, PPR_MAX_R);
         return PPR_EINVAL;
     }
     if ((a->dangling != 0 && a->dangling != 1) || (a->segments != 0 && a->segments != 1) ||

@@ -532,6 +532,11 @@ __device__ inline void aggregate_source_reg(const uint32_t *ends, uint32_t R, ui
                 }
             }
         }
+        // k may exceed the sorted block (k > next_pow2(R) >= nnz): pad the rest
+        for (uint32_t i = 32u * E + lane; i < (uint32_t)o.topk; i += 32) {
+            o.topk_idx[tb + i] = -1;
+            o.topk_cnt[tb + i] = 0;
+        }
     }
     __syncwarp();
 }

@@ -520,8 +520,8 @@ extern "C" int ppr_run_noalloc(ppr_ctx *ctx, const ppr_graph *g, const ppr_run_a
                   (long long)a->src_end, (long long)g->n);
         return PPR_EINVAL;
     }
-    if (a->topk < 0 || (uint32_t)a->topk > a->R || (a->topk > 0 && (!topk_idx || !topk_cnt))) {
-        set_error("topk = %d outside [0, R], or top-k outputs missing", a->topk);
+    if (a->topk < 0 || (uint32_t)a->topk > PPR_MAX_R || (a->topk > 0 && (!topk_idx || !topk_cnt))) {
+        set_error("topk = %d outside [0, %u], or top-k outputs missing", a->topk, PPR_MAX_R);
         return PPR_EINVAL;
     }
     if ((a->dangling != 0 && a->dangling != 1) || (a->segments != 0 && a->segments != 1) || a->large_degree < 0 ||

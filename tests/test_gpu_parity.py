@@ -77,6 +77,16 @@ def test_small_graphs_ragged(ppr, ctx, oracle, R, kernel):
         assert_same(res, ref, topk=min(R, 5))
 
 
+def test_topk_larger_than_R(ppr, ctx, oracle):
+    """k above R (and above next_pow2(R)) returns the whole row by count, padded."""
+    g = I.er_graph(300, 2000, seed=6)
+    G = ctx.load_graph(g.n, g.row_ptr, g.col, g.w)
+    for R, k in ((50, 64), (20, 100), (7, 33)):
+        ref = oracle_rows(oracle, g, 0.15, R, 2, topk=k)
+        for kernel in (0, 1):
+            assert_same(G.run(alpha=0.15, R=R, seed=2, topk=k, kernel=kernel), ref, topk=k)
+
+
 def test_self_loops_parallel_edges_and_skew(ppr, ctx, oracle):
     g = I.from_edges(6, [(0, 1, 1000), (0, 2, 1), (0, 1, 3), (1, 1, 2), (1, 3, 5), (2, 0, 1), (2, 4, 7), (3, 0, 1),
                          (3, 5, 1), (4, 2, 2)])
@@ -231,7 +241,7 @@ def test_invalid_inputs_are_rejected(ppr, ctx):
     for kw, code in ((dict(alpha=0.0), ppr.PPR_EINVAL), (dict(alpha=1.0), ppr.PPR_EINVAL),
                      (dict(alpha=2.0**-40), ppr.PPR_EINVAL), (dict(R=0), ppr.PPR_EINVAL),
                      (dict(R=5000), ppr.PPR_ERANGE), (dict(src_begin=10, src_end=10), ppr.PPR_EINVAL),
-                     (dict(src_end=51), ppr.PPR_EINVAL), (dict(topk=101), ppr.PPR_EINVAL),
+                     (dict(src_end=51), ppr.PPR_EINVAL), (dict(topk=4097), ppr.PPR_EINVAL),
                      (dict(dangling=2), ppr.PPR_EINVAL)):
         with pytest.raises(E) as ei:
             G.run(**kw)
