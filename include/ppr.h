@@ -183,6 +183,31 @@ void ppr_run_args_init(ppr_run_args *args);
  */
 int ppr_run(ppr_ctx *ctx, const ppr_graph *g, const ppr_run_args *args, ppr_result **out);
 
+/*
+ * As ppr_run, for an explicit list of `count` source node ids (host memory,
+ * copied; each in [0, n); repeats allowed).  Row i of the result belongs to
+ * sources[i]; walks of that source use its node id in the counter, so a row
+ * equals the row ppr_run gives for the same node.  args->src_begin/src_end are
+ * ignored.  Plain graphs only (PPR_ENOTSUP for batched graphs).
+ */
+int ppr_run_list(ppr_ctx *ctx, const ppr_graph *g, const ppr_run_args *args, const int32_t *sources, int64_t count,
+                 ppr_result **out);
+
+/* Bytes of device workspace ppr_run_into needs for these arguments. */
+int ppr_workspace_size(const ppr_graph *g, const ppr_run_args *args, size_t *bytes);
+
+/*
+ * ppr_run into caller-owned device memory: the workspace (>= ppr_workspace_size
+ * bytes, 256-byte aligned) holds the per-walk endpoints and counters, and the
+ * rows and top-k go to the caller's buffers (layout as ppr_run_noalloc below).
+ * Persistent kernel only; segment tables must already exist for this alpha.
+ * The call only enqueues work on args->stream: no allocation, no host copy and
+ * no synchronization, so it may be recorded into a CUDA graph.  Two calls that
+ * share a workspace and overlap on the GPU race.
+ */
+int ppr_run_into(ppr_ctx *ctx, const ppr_graph *g, const ppr_run_args *args, void *workspace, size_t bytes,
+                 uint32_t *nnz, int32_t *cols, uint32_t *cnts, uint32_t cap, int32_t *topk_idx, uint32_t *topk_cnt);
+
 /* Waits for the run; PPR_ETIMEOUT if not finished within timeout_ms
  * (timeout_ms < 0: wait without deadline).  The result stays valid. */
 int ppr_wait(ppr_result *r, int64_t timeout_ms);

@@ -265,6 +265,7 @@ void ppr_free_graph(ppr_graph *g)
     dev_free(g->edges, g->stream);
     dev_free(g->seg.node, g->stream);
     dev_free(g->seg.entries, g->stream);
+    dev_free(g->d_node_off, g->stream);
     delete g;
 }
 
@@ -296,13 +297,10 @@ static void result_release(ppr_result *r)
     delete r;
 }
 
-int ppr_run(ppr_ctx *ctx, const ppr_graph *g, const ppr_run_args *a, ppr_result **out)
+// Checks shared by every run entry point; count = number of sources (from the
+// range, or of an explicit list).  Fills *plan.
+static int check_run(const ppr_graph *g, const ppr_run_args *a, int64_t count, bool list, RunPlan *plan)
 {
-    if (!ctx || !g || !a || !out) {
-        set_error("NULL argument");
-        return PPR_EINVAL;
-    }
-    *out = nullptr;
     const uint32_t T = ppr_alpha_threshold(a->alpha);
     if (T == 0) {
         set_error("alpha = %g: need 0 < alpha < 1 and floor(alpha * 2^32) >= 1", a->alpha);
@@ -316,9 +314,13 @@ int ppr_run(ppr_ctx *ctx, const ppr_graph *g, const ppr_run_args *a, ppr_result 
         set_error("R = %u exceeds the limit %u", a->R, PPR_MAX_R);
         return PPR_ERANGE;
     }
-    if (a->src_begin < 0 || a->src_end > g->n || a->src_begin >= a->src_end) {
+    if (!list && (a->src_begin < 0 || a->src_end > g->n || a->src_begin >= a->src_end)) {
         set_error("source range [%lld, %lld) must be non-empty and inside [0, %lld)", (long long)a->src_begin,
                   (long long)a->src_end, (long long)g->n);
+        return PPR_EINVAL;
+    }
+    if (list && count < 1) {
+        set_error("the source list is empty");
         return PPR_EINVAL;
     }
     if (a->topk < 0 || (uint32_t)a->topk > PPR_MAX_R) {
@@ -336,15 +338,59 @@ int ppr_run(ppr_ctx *ctx, const ppr_graph *g, const ppr_run_args *a, ppr_result 
         set_error("batched graphs use the instance id as tag; tag must be 0");
         return PPR_EINVAL;
     }
+    if (g->instances > 0 && list) {
+        set_error("source lists are supported on plain graphs");
+        return PPR_ENOTSUP;
+    }
     if (a->chunk_sources > 0 && (uint64_t)a->chunk_sources * a->R > (1u << 20)) {
         set_error("chunk_sources * R too large");
         return PPR_ERANGE;
     }
-    int rc = set_device(ctx);
+    *plan = RunPlan{};
+    plan->T = T;
+    plan->R = a->R;
+    plan->seed = a->seed;
+    plan->tag = a->tag;
+    plan->dangling = a->dangling;
+    plan->segments = a->segments != 0;
+    plan->kernel = a->kernel;
+    plan->large_degree = a->large_degree;
+    plan->warps_per_block = a->warps_per_block;
+    plan->chunk_sources = a->chunk_sources;
+    plan->stats = a->stats != 0;
+    return PPR_OK;
+}
+
+static uint32_t row_capacity(const ppr_graph *g, uint32_t R)
+{
+    int64_t n_local_max = g->n;
+    if (g->instances > 0) {
+        n_local_max = 0;
+        for (int32_t i = 0; i < g->instances; ++i)
+            n_local_max = std::max<int64_t>(n_local_max, g->node_off[i + 1] - g->node_off[i]);
+    }
+    return (uint32_t)std::min<int64_t>((int64_t)R, n_local_max);
+}
+
+// ppr_run / ppr_run_list: result-owned outputs, batches sized to memory.
+static int run_common(ppr_ctx *ctx, const ppr_graph *g, const ppr_run_args *a, const int32_t *list, int64_t count,
+                      ppr_result **out)
+{
+    RunPlan plan;
+    int rc = check_run(g, a, count, list != nullptr, &plan);
+    if (rc) return rc;
+    if (list) {
+        for (int64_t i = 0; i < count; ++i)
+            if (list[i] < 0 || list[i] >= g->n) {
+                set_error("source %lld of the list (%d) is outside [0, %lld)", (long long)i, list[i], (long long)g->n);
+                return PPR_EINVAL;
+            }
+    }
+    rc = set_device(ctx);
     if (rc) return rc;
     cudaStream_t st = (cudaStream_t)a->stream;
     if (a->segments) {
-        rc = build_segments(const_cast<ppr_graph *>(g), T, st);
+        rc = build_segments(const_cast<ppr_graph *>(g), plan.T, st);
         if (rc) return rc;
     }
     ppr_result *r = new (std::nothrow) ppr_result;
@@ -352,17 +398,11 @@ int ppr_run(ppr_ctx *ctx, const ppr_graph *g, const ppr_run_args *a, ppr_result 
     r->ctx = ctx;
     r->g = g;
     r->stream = st;
-    r->S = a->src_end - a->src_begin;
+    r->S = list ? count : a->src_end - a->src_begin;
     r->R = a->R;
     r->topk = a->topk;
-    r->src_begin = a->src_begin;
-    int64_t n_local_max = g->n;
-    if (g->instances > 0) {
-        n_local_max = 0;
-        for (int32_t i = 0; i < g->instances; ++i)
-            n_local_max = std::max<int64_t>(n_local_max, g->node_off[i + 1] - g->node_off[i]);
-    }
-    r->cap = (uint32_t)std::min<int64_t>((int64_t)a->R, n_local_max);
+    r->src_begin = list ? 0 : a->src_begin;
+    r->cap = row_capacity(g, a->R);
     auto fail = [&](int code) {
         result_release(r);
         return code;
@@ -375,24 +415,18 @@ int ppr_run(ppr_ctx *ctx, const ppr_graph *g, const ppr_run_args *a, ppr_result 
         if ((rc = dev_alloc((void **)&r->d_topk_idx, sizeof(int32_t) * S * r->topk, "top-k ids", st))) return fail(rc);
         if ((rc = dev_alloc((void **)&r->d_topk_cnt, sizeof(uint32_t) * S * r->topk, "top-k counts", st))) return fail(rc);
     }
-    if ((rc = dev_alloc((void **)&r->d_steps, sizeof(unsigned long long) * 3, "counters", st))) return fail(rc);
+    if ((rc = dev_alloc((void **)&r->d_steps, sizeof(unsigned long long) * 4, "counters", st))) return fail(rc);
+    uint32_t *d_list = nullptr;
+    if (list) {
+        if ((rc = dev_alloc((void **)&d_list, sizeof(uint32_t) * S, "source list", st))) return fail(rc);
+        r->scratch.push_back(d_list);
+        cudaError_t e = cudaMemcpyAsync(d_list, list, sizeof(uint32_t) * S, cudaMemcpyHostToDevice, st);
+        if (e != cudaSuccess) return fail(cuda_fail(e, "source list upload"));
+    }
     cudaError_t e = cudaEventCreate(&r->ev_start);
     if (e == cudaSuccess) e = cudaEventCreate(&r->ev_walk_end);
     if (e == cudaSuccess) e = cudaEventCreate(&r->ev_done);
     if (e != cudaSuccess) return fail(cuda_fail(e, "cudaEventCreate"));
-
-    RunPlan plan{};
-    plan.T = T;
-    plan.R = a->R;
-    plan.seed = a->seed;
-    plan.tag = a->tag;
-    plan.dangling = a->dangling;
-    plan.segments = a->segments != 0;
-    plan.kernel = a->kernel;
-    plan.large_degree = a->large_degree;
-    plan.warps_per_block = a->warps_per_block;
-    plan.chunk_sources = a->chunk_sources;
-    plan.stats = a->stats != 0;
 
     // Batch size (the paper's per-pipeline walk budget, gamma <= alpha*M/(n*c),
     // Sec. 4.3, becomes a source batch sized to device memory): every walk of
@@ -400,22 +434,22 @@ int ppr_run(ppr_ctx *ctx, const ppr_graph *g, const ppr_run_args *a, ppr_result 
     // that scratch is bounded to a quarter of the free memory.
     int64_t batch = r->S;
     if (a->max_batch_sources > 0) batch = std::min<int64_t>(batch, a->max_batch_sources);
-    uint32_t *ends = nullptr;
     {
         size_t free_b = 0, total_b = 0;
         cudaMemGetInfo(&free_b, &total_b);
         int64_t fit = (int64_t)(free_b / 4 / ((size_t)a->R * sizeof(uint32_t)));
         batch = std::max<int64_t>(1, std::min<int64_t>(batch, fit));
-        if ((rc = dev_alloc((void **)&ends, sizeof(uint32_t) * (size_t)batch * a->R, "endpoint buffer", st)))
-            return fail(rc);
-        r->scratch.push_back(ends);
     }
-    if ((e = cudaMemsetAsync(r->d_steps, 0, sizeof(unsigned long long) * 3, st)) != cudaSuccess)
+    unsigned char *ws = nullptr;
+    if ((rc = dev_alloc((void **)&ws, launch_workspace_bytes(g, plan, batch), "walk workspace", st))) return fail(rc);
+    r->scratch.push_back(ws);
+    if ((e = cudaMemsetAsync(r->d_steps, 0, sizeof(unsigned long long) * 4, st)) != cudaSuccess)
         return fail(cuda_fail(e, "memset"));
     if ((e = cudaEventRecord(r->ev_start, st)) != cudaSuccess) return fail(cuda_fail(e, "cudaEventRecord"));
-    for (int64_t b = a->src_begin; b < a->src_end; b += batch) {
-        int64_t be = std::min<int64_t>(a->src_end, b + batch);
-        rc = launch_walks(ctx, g, plan, r, b, be, b - a->src_begin, ends, r->d_steps + 1, st, true);
+    const Outputs o{r->d_nnz, r->d_cols, r->d_cnts, r->cap, r->d_topk_idx, r->d_topk_cnt, r->topk, r->d_steps};
+    for (int64_t b = 0; b < r->S; b += batch) {
+        const int64_t nb = std::min<int64_t>(r->S - b, batch);
+        rc = launch_walks(ctx, g, plan, o, r->src_begin + b, nb, d_list ? d_list + b : nullptr, b, ws, st, r);
         if (rc) {
             cudaStreamSynchronize(st);
             return fail(rc);
@@ -425,6 +459,81 @@ int ppr_run(ppr_ctx *ctx, const ppr_graph *g, const ppr_run_args *a, ppr_result 
     if ((e = cudaEventRecord(r->ev_done, st)) != cudaSuccess) return fail(cuda_fail(e, "cudaEventRecord"));
     *out = r;
     return PPR_OK;
+}
+
+int ppr_run(ppr_ctx *ctx, const ppr_graph *g, const ppr_run_args *a, ppr_result **out)
+{
+    if (!ctx || !g || !a || !out) {
+        set_error("NULL argument");
+        return PPR_EINVAL;
+    }
+    *out = nullptr;
+    return run_common(ctx, g, a, nullptr, 0, out);
+}
+
+int ppr_run_list(ppr_ctx *ctx, const ppr_graph *g, const ppr_run_args *a, const int32_t *sources, int64_t count,
+                 ppr_result **out)
+{
+    if (!ctx || !g || !a || !out || !sources) {
+        set_error("NULL argument");
+        return PPR_EINVAL;
+    }
+    *out = nullptr;
+    return run_common(ctx, g, a, sources, count, out);
+}
+
+int ppr_workspace_size(const ppr_graph *g, const ppr_run_args *a, size_t *bytes)
+{
+    if (!g || !a || !bytes) {
+        set_error("NULL argument");
+        return PPR_EINVAL;
+    }
+    RunPlan plan;
+    int rc = check_run(g, a, 0, false, &plan);
+    if (rc) return rc;
+    *bytes = 256 + launch_workspace_bytes(g, plan, a->src_end - a->src_begin);
+    return PPR_OK;
+}
+
+int ppr_run_into(ppr_ctx *ctx, const ppr_graph *g, const ppr_run_args *a, void *workspace, size_t bytes,
+                 uint32_t *nnz, int32_t *cols, uint32_t *cnts, uint32_t cap, int32_t *topk_idx, uint32_t *topk_cnt)
+{
+    if (!ctx || !g || !a || !workspace || !nnz || !cols || !cnts) {
+        set_error("NULL argument");
+        return PPR_EINVAL;
+    }
+    RunPlan plan;
+    int rc = check_run(g, a, 0, false, &plan);
+    if (rc) return rc;
+    if (a->kernel != PPR_KERNEL_PERSISTENT || a->stats) {
+        set_error("ppr_run_into runs the persistent kernel without statistics");
+        return PPR_EINVAL;
+    }
+    if (a->topk > 0 && (!topk_idx || !topk_cnt)) {
+        set_error("top-k outputs missing");
+        return PPR_EINVAL;
+    }
+    if (a->segments && !(g->seg.T == plan.T && g->seg.node)) {
+        set_error("segment tables for this alpha are not built (a ppr_run with segments=1 builds them)");
+        return PPR_ENOTSUP;
+    }
+    if (cap < row_capacity(g, a->R)) {
+        set_error("row capacity %u < min(R, n) = %u", cap, row_capacity(g, a->R));
+        return PPR_EINVAL;
+    }
+    const int64_t S = a->src_end - a->src_begin;
+    const size_t need = 256 + launch_workspace_bytes(g, plan, S);
+    if (bytes < need || (reinterpret_cast<uintptr_t>(workspace) & 255)) {
+        set_error("workspace of %zu bytes at %p: need %zu bytes, 256-byte aligned", bytes, workspace, need);
+        return PPR_EINVAL;
+    }
+    if ((rc = set_device(ctx))) return rc;
+    cudaStream_t st = (cudaStream_t)a->stream;
+    unsigned char *w = static_cast<unsigned char *>(workspace);
+    cudaError_t e = cudaMemsetAsync(w, 0, 256, st);  // counters start at zero
+    if (e != cudaSuccess) return cuda_fail(e, "cudaMemsetAsync(workspace counters)");
+    const Outputs o{nnz, cols, cnts, cap, topk_idx, topk_cnt, a->topk, reinterpret_cast<unsigned long long *>(w)};
+    return launch_walks(ctx, g, plan, o, a->src_begin, S, nullptr, 0, w + 256, st, nullptr);
 }
 
 int ppr_wait(ppr_result *r, int64_t timeout_ms)

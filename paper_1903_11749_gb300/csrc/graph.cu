@@ -553,11 +553,10 @@ int build_graph(ppr_ctx *ctx, int64_t n, int64_t m, const int64_t *row_ptr, cons
         if (e != cudaSuccess) return cleanup(), cuda_fail(e, "graph upload");
     }
     int64_t *d_off = nullptr;
-    if (g->instances > 0) {
-        void *p;
-        if ((rc = dev_alloc(&p, sizeof(int64_t) * (g->instances + 1), "node_off", st))) return cleanup(), rc;
-        tmp.push_back(p);
-        d_off = (int64_t *)p;
+    if (g->instances > 0) {  // kept with the graph: the walker reads instance offsets
+        if ((rc = dev_alloc((void **)&g->d_node_off, sizeof(int64_t) * (g->instances + 1), "node_off", st)))
+            return cleanup(), rc;
+        d_off = g->d_node_off;
         cudaError_t e = cudaMemcpyAsync(d_off, g->node_off.data(), sizeof(int64_t) * (g->instances + 1),
                                         cudaMemcpyHostToDevice, st);
         if (e != cudaSuccess) return cleanup(), cuda_fail(e, "node_off upload");

@@ -52,6 +52,7 @@ struct ppr_graph {
     // block-diagonal instances
     int32_t instances = 0;
     std::vector<int64_t> node_off;  // host copy, count+1
+    int64_t *d_node_off = nullptr;  // device copy
     ppr::SegCache seg;
     int64_t device_bytes = 0;
 };
@@ -70,7 +71,7 @@ struct ppr_result {
     uint32_t *d_cnts = nullptr;
     int32_t *d_topk_idx = nullptr;
     uint32_t *d_topk_cnt = nullptr;
-    unsigned long long *d_steps = nullptr;  // [0] steps, [1] work-queue head, [2] sectors
+    unsigned long long *d_steps = nullptr;  // counters: [0] steps, [1] work queue, [2] sectors, [3] chunks
     cudaEvent_t ev_start = nullptr, ev_walk_end = nullptr, ev_done = nullptr;
     std::vector<cudaEvent_t> walk_events;  // (before, after) each walker launch
     bool waited = false;
@@ -104,9 +105,26 @@ struct RunPlan {
 // Enqueues the walks of sources [s_begin, s_end) writing output rows from
 // out_row0.  ends: S * R endpoint scratch for the plain kernel (else unused);
 // queue: one device counter for the persistent kernel's work queue.
-// timed: record CUDA events around every walker launch into r.
-int launch_walks(ppr_ctx *ctx, const ppr_graph *g, const RunPlan &p, ppr_result *r, int64_t s_begin,
-                 int64_t s_end, int64_t out_row0, uint32_t *ends, unsigned long long *queue, cudaStream_t st,
-                 bool timed);
+// Where a launch writes: rows (nnz / cols / cnts at row * cap), top-k, and
+// the counters block: [0] steps, [1] work queue, [2] sectors, [3] chunk count.
+struct Outputs {
+    uint32_t *nnz;
+    int32_t *cols;
+    uint32_t *cnts;
+    uint32_t cap;
+    int32_t *topk_idx;
+    uint32_t *topk_cnt;
+    int32_t topk;
+    unsigned long long *counters;
+};
+
+// Device workspace one launch of S sources needs (endpoints, chunk table).
+size_t launch_workspace_bytes(const ppr_graph *g, const RunPlan &p, int64_t S);
+
+// Enqueues walks and reduction for S sources: node s_begin + i, or
+// src_list[i] (device) when given; rows go to out_row0 + i.  ws holds
+// launch_workspace_bytes.  ev_owner: record walker-time events into it.
+int launch_walks(ppr_ctx *ctx, const ppr_graph *g, const RunPlan &p, const Outputs &o, int64_t s_begin, int64_t S,
+                 const uint32_t *src_list, int64_t out_row0, unsigned char *ws, cudaStream_t st, ppr_result *ev_owner);
 
 }  // namespace ppr

@@ -20,6 +20,7 @@
 #include <mutex>
 
 #include "ppr_host.h"
+#include "scan.cuh"
 
 namespace ppr {
 
@@ -34,7 +35,9 @@ struct KParams {
     int64_t out_row0;         // output row of s_begin
     uint32_t CS;              // sources per chunk
     uint32_t nchunks;
-    const int4 *chunks;       // batched graphs: {base, nsrc, instance, 0}; else null
+    const unsigned long long *nchunks_dev;  // batched graphs: chunk count written on the device
+    const int4 *chunks;       // batched graphs: {position, nsrc, instance, 0}; else null
+    const uint32_t *src_list; // explicit sources (position -> node id); null: s_begin + position
     const int64_t *inst_off;  // batched graphs: node_off
     AggOut out;
     uint32_t *ends;           // S * R endpoints (instance-local ids)
@@ -178,7 +181,7 @@ __global__ void __launch_bounds__(256, PPR_WALK_MINB) k_walk_plain(KParams p)
          t += (uint64_t)gridDim.x * blockDim.x) {
         const uint64_t i = t / p.R;
         const uint32_t j = (uint32_t)(t - i * p.R);
-        const uint32_t src = (uint32_t)(p.s_begin + (int64_t)i);
+        const uint32_t src = p.src_list ? p.src_list[i] : (uint32_t)(p.s_begin + (int64_t)i);
         uint32_t k = 0, u = src, end = 0;
         while (!walk_step<E, SEG, false, STATS>(p, edges, true, src, src, j, p.tag, k, u, end, tl)) {
         }
@@ -219,7 +222,7 @@ __global__ void __launch_bounds__(128) k_aggregate(KParams p)
 // source by k_aggregate.  The walker uses no shared memory beyond the queue
 // state, so L1 keeps its full size.
 struct WarpQueue {
-    uint32_t base, ctr_base, tag;  // current chunk
+    uint32_t base, ctr_base, tag;  // current chunk: first position, counter base, tag
     uint32_t issued, total;
 };
 
@@ -253,7 +256,8 @@ __global__ void __launch_bounds__(256, PPR_WALK_MINB) k_walk_persistent(KParams 
                 unsigned long long c = 0;
                 if (lane == 0) c = atomicAdd(p.queue, 1ull);
                 c = __shfl_sync(0xffffffffu, c, 0);
-                if (c >= p.nchunks) {
+                const unsigned long long nch = p.nchunks_dev ? *p.nchunks_dev : p.nchunks;
+                if (c >= nch) {
                     queue_empty = true;
                     break;
                 }
@@ -266,9 +270,9 @@ __global__ void __launch_bounds__(256, PPR_WALK_MINB) k_walk_persistent(KParams 
                         wq.ctr_base = (uint32_t)p.inst_off[d.z];
                         wq.tag = (uint32_t)d.z;
                     } else {
-                        const int64_t b = p.s_begin + (int64_t)c * p.CS;
+                        const int64_t b = (int64_t)c * p.CS;
                         wq.base = (uint32_t)b;
-                        nsrc = (uint32_t)std::min<int64_t>((int64_t)p.CS, p.s_end - b);
+                        nsrc = (uint32_t)std::min<int64_t>((int64_t)p.CS, (p.s_end - p.s_begin) - b);
                         wq.ctr_base = 0;
                         wq.tag = p.tag;
                     }
@@ -284,11 +288,12 @@ __global__ void __launch_bounds__(256, PPR_WALK_MINB) k_walk_persistent(KParams 
                 const uint32_t w = issued + rank;
                 const uint32_t i = div_by_R(w, p.r_magic);
                 j = w - i * p.R;
-                src = wq.base + i;
+                const uint32_t pos = wq.base + i;
+                src = p.src_list ? p.src_list[pos] : (uint32_t)(p.s_begin + pos);
                 ctr_base = wq.ctr_base;
                 sctr = src - ctr_base;
                 tag = wq.tag;
-                slot = ((uint64_t)((int64_t)src - p.s_begin)) * p.R + j;
+                slot = (uint64_t)pos * p.R + j;
                 k = 0;
                 u = src;
                 active = true;
@@ -380,12 +385,55 @@ static int launch_typed(ppr_ctx *ctx, const KParams &kp, const RunPlan &plan, in
     return launch_aggregate(ctx, kp, S, st);
 }
 
-int launch_walks(ppr_ctx *ctx, const ppr_graph *g, const RunPlan &plan, ppr_result *r, int64_t s_begin,
-                 int64_t s_end, int64_t out_row0, uint32_t *ends, unsigned long long *queue, cudaStream_t st,
-                 bool timed)
+// Chunk table of a batched graph, built on the device: chunks of at most CS
+// sources that never cross an instance boundary, with positions relative to
+// s_begin; the count goes to *nchunks.
+__global__ void k_chunk_count(int32_t count, const int64_t *node_off, int64_t s_begin, int64_t s_end, uint32_t CS,
+                              uint32_t *cnt)
 {
-    ppr_result *ev_owner = timed ? r : nullptr;
-    const int64_t S = s_end - s_begin;
+    for (int32_t gi = blockIdx.x * blockDim.x + threadIdx.x; gi < count; gi += gridDim.x * blockDim.x) {
+        const int64_t a = max(node_off[gi], s_begin), b = min(node_off[gi + 1], s_end);
+        cnt[gi] = b > a ? (uint32_t)((b - a + CS - 1) / CS) : 0u;
+    }
+}
+
+__global__ void k_chunk_fill(int32_t count, const int64_t *node_off, int64_t s_begin, int64_t s_end, uint32_t CS,
+                             const uint64_t *offs, int4 *chunks, unsigned long long *nchunks)
+{
+    for (int32_t gi = blockIdx.x * blockDim.x + threadIdx.x; gi < count; gi += gridDim.x * blockDim.x) {
+        const int64_t a = max(node_off[gi], s_begin), b = min(node_off[gi + 1], s_end);
+        uint64_t o = offs[gi];
+        for (int64_t s = a; s < b; s += CS, ++o)
+            chunks[o] = make_int4((int)(s - s_begin), (int)min((int64_t)CS, b - s), gi, 0);
+        if (gi == count - 1) *nchunks = offs[count];
+    }
+}
+
+static uint32_t chunk_sources(const RunPlan &plan)
+{
+    return plan.chunk_sources > 0 ? (uint32_t)plan.chunk_sources : std::max(1u, 400u / plan.R);
+}
+
+static size_t align256(size_t x) { return (x + 255) & ~(size_t)255; }
+
+size_t launch_workspace_bytes(const ppr_graph *g, const RunPlan &plan, int64_t S)
+{
+    size_t b = align256((size_t)S * plan.R * sizeof(uint32_t));  // endpoints
+    if (g->instances > 0 && plan.kernel == PPR_KERNEL_PERSISTENT) {
+        const uint32_t CS = chunk_sources(plan);
+        const int64_t cnt = g->instances;
+        const int64_t tiles = (cnt + kScanTile - 1) / kScanTile;
+        b += align256(sizeof(int4) * (size_t)((S + CS - 1) / CS + cnt + 1));  // chunk table
+        b += align256(sizeof(uint32_t) * (size_t)cnt);                      // per-instance chunk counts
+        b += align256(sizeof(uint64_t) * (size_t)(cnt + 1));                // their offsets
+        b += align256(sizeof(uint64_t) * (size_t)(tiles + 2));              // scan scratch
+    }
+    return b;
+}
+
+int launch_walks(ppr_ctx *ctx, const ppr_graph *g, const RunPlan &plan, const Outputs &o, int64_t s_begin, int64_t S,
+                 const uint32_t *src_list, int64_t out_row0, unsigned char *ws, cudaStream_t st, ppr_result *ev_owner)
+{
     if (S <= 0) return PPR_OK;
     KParams kp{};
     kp.node = plan.segments ? g->seg.node : g->node;
@@ -399,56 +447,58 @@ int launch_walks(ppr_ctx *ctx, const ppr_graph *g, const RunPlan &plan, ppr_resu
     kp.dangling = plan.dangling;
     kp.large = plan.large_degree > 0 ? (uint32_t)plan.large_degree : 0xffffffffu;  // 0: off
     kp.s_begin = s_begin;
-    kp.s_end = s_end;
+    kp.s_end = s_begin + S;
+    kp.src_list = src_list;
     kp.out_row0 = out_row0;
-    kp.out.nnz = r->d_nnz;
-    kp.out.cols = r->d_cols;
-    kp.out.cnts = r->d_cnts;
-    kp.out.topk_idx = r->d_topk_idx;
-    kp.out.topk_cnt = r->d_topk_cnt;
-    kp.out.cap = r->cap;
-    kp.out.topk = r->topk;
-    kp.steps = r->d_steps;
-    kp.queue = queue;
-    kp.ends = ends;
+    kp.out.nnz = o.nnz;
+    kp.out.cols = o.cols;
+    kp.out.cnts = o.cnts;
+    kp.out.topk_idx = o.topk_idx;
+    kp.out.topk_cnt = o.topk_cnt;
+    kp.out.cap = o.cap;
+    kp.out.topk = o.topk;
+    kp.steps = o.counters;
+    kp.queue = o.counters + 1;
     uint32_t P2 = 1;
     while (P2 < plan.R) P2 <<= 1;
     kp.P2 = P2;
     kp.r_magic = ((1ull << 40) + plan.R - 1) / plan.R;
-    int rc;
+    kp.ends = reinterpret_cast<uint32_t *>(ws);
+    size_t off = align256((size_t)S * plan.R * sizeof(uint32_t));
 
-    std::vector<int4> chunks;
     if (plan.kernel == PPR_KERNEL_PLAIN) {
         if (g->instances > 0) {
             set_error("the plain kernel runs plain graphs only");
             return PPR_ENOTSUP;
         }
     } else {
-        uint32_t CS = plan.chunk_sources > 0 ? (uint32_t)plan.chunk_sources : std::max(1u, 400u / plan.R);
+        const uint32_t CS = chunk_sources(plan);
         kp.CS = CS;
         if (g->instances > 0) {
-            // chunks never cross an instance boundary
-            const auto &off = g->node_off;
-            for (int32_t gi = 0; gi < g->instances; ++gi) {
-                int64_t a = std::max(off[gi], s_begin), b = std::min(off[gi + 1], s_end);
-                for (int64_t s = a; s < b; s += CS)
-                    chunks.push_back(make_int4((int)s, (int)std::min<int64_t>(CS, b - s), gi, 0));
-            }
-            kp.nchunks = (uint32_t)chunks.size();
-            void *d = nullptr;
-            if ((rc = dev_alloc(&d, sizeof(int4) * std::max<size_t>(chunks.size(), 1), "chunk table", st))) return rc;
-            r->scratch.push_back(d);
-            PPR_CUDA(cudaMemcpyAsync(d, chunks.data(), sizeof(int4) * chunks.size(), cudaMemcpyHostToDevice, st));
-            kp.chunks = (const int4 *)d;
-            void *o = nullptr;
-            if ((rc = dev_alloc(&o, sizeof(int64_t) * (g->instances + 1), "instance offsets", st))) return rc;
-            r->scratch.push_back(o);
-            PPR_CUDA(cudaMemcpyAsync(o, off.data(), sizeof(int64_t) * (g->instances + 1), cudaMemcpyHostToDevice, st));
-            kp.inst_off = (const int64_t *)o;
+            const int64_t cnt = g->instances;
+            int4 *chunks = reinterpret_cast<int4 *>(ws + off);
+            off += align256(sizeof(int4) * (size_t)((S + CS - 1) / CS + cnt + 1));
+            uint32_t *ccount = reinterpret_cast<uint32_t *>(ws + off);
+            off += align256(sizeof(uint32_t) * (size_t)cnt);
+            uint64_t *coffs = reinterpret_cast<uint64_t *>(ws + off);
+            off += align256(sizeof(uint64_t) * (size_t)(cnt + 1));
+            uint64_t *ctmp = reinterpret_cast<uint64_t *>(ws + off);
+            const int cb = (int)std::min<int64_t>((cnt + 255) / 256, 1024);
+            k_chunk_count<<<cb, 256, 0, st>>>((int32_t)cnt, g->d_node_off, s_begin, s_begin + S, CS, ccount);
+            note_launch();
+            exclusive_scan_u32(ccount, cnt, coffs, ctmp, st);
+            k_chunk_fill<<<cb, 256, 0, st>>>((int32_t)cnt, g->d_node_off, s_begin, s_begin + S, CS, coffs, chunks,
+                                             o.counters + 3);
+            note_launch();
+            PPR_CUDA(cudaGetLastError());
+            kp.chunks = chunks;
+            kp.inst_off = g->d_node_off;
+            kp.nchunks_dev = o.counters + 3;
+            kp.nchunks = (uint32_t)((S + CS - 1) / CS + cnt);  // upper bound, for the grid size
         } else {
             kp.nchunks = (uint32_t)((S + CS - 1) / CS);
         }
-        PPR_CUDA(cudaMemsetAsync(queue, 0, sizeof(unsigned long long), st));
+        PPR_CUDA(cudaMemsetAsync(kp.queue, 0, sizeof(unsigned long long), st));
     }
     if (plan.stats) {
         if (g->wide)
@@ -572,22 +622,7 @@ extern "C" int ppr_run_noalloc(ppr_ctx *ctx, const ppr_graph *g, const ppr_run_a
     plan.warps_per_block = a->warps_per_block;
     plan.chunk_sources = a->chunk_sources;
     plan.stats = false;
-    ppr_result out{};  // describes the caller's buffers; owns nothing
-    out.d_nnz = nnz;
-    out.d_cols = cols;
-    out.d_cnts = cnts;
-    out.d_topk_idx = topk_idx;
-    out.d_topk_cnt = topk_cnt;
-    out.cap = cap;
-    out.topk = a->topk;
-    out.d_steps = reinterpret_cast<unsigned long long *>(scratch);
-    uint32_t *ends = reinterpret_cast<uint32_t *>(scratch + kNoAllocHeader);
-    rc = launch_walks(ctx, g, plan, &out, a->src_begin, a->src_end, 0, ends, out.d_steps + 1, st, false);
-    out.d_nnz = nullptr;  // not freed: the buffers belong to the caller
-    out.d_cols = nullptr;
-    out.d_cnts = nullptr;
-    out.d_topk_idx = nullptr;
-    out.d_topk_cnt = nullptr;
-    out.d_steps = nullptr;
-    return rc;
+    Outputs out{nnz, cols, cnts, cap, topk_idx, topk_cnt, a->topk, reinterpret_cast<unsigned long long *>(scratch)};
+    return launch_walks(ctx, g, plan, out, a->src_begin, a->src_end - a->src_begin, nullptr, 0,
+                        scratch + kNoAllocHeader, st, nullptr);
 }

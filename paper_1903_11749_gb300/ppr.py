@@ -74,6 +74,11 @@ _SIGS = {
     "ppr_free_result": (None, [C.c_void_p]),
     "ppr_run_noalloc": (C.c_int, [C.c_void_p, C.c_void_p, C.POINTER(RunArgs), C.c_void_p, C.c_void_p, C.c_void_p,
                                   C.c_uint32, C.c_void_p, C.c_void_p]),
+    "ppr_run_list": (C.c_int, [C.c_void_p, C.c_void_p, C.POINTER(RunArgs), C.c_void_p, C.c_int64,
+                               C.POINTER(C.c_void_p)]),
+    "ppr_workspace_size": (C.c_int, [C.c_void_p, C.POINTER(RunArgs), C.POINTER(C.c_size_t)]),
+    "ppr_run_into": (C.c_int, [C.c_void_p, C.c_void_p, C.POINTER(RunArgs), C.c_void_p, C.c_size_t, C.c_void_p,
+                               C.c_void_p, C.c_void_p, C.c_uint32, C.c_void_p, C.c_void_p]),
 }
 
 _lib = None
@@ -191,6 +196,47 @@ class Graph:
             self.free()
         except Exception:
             pass
+
+    def _args(self, alpha=0.15, R=100, seed=1, src_begin=0, src_end=None, tag=0, dangling=0, segments=False,
+              topk=0, kernel=KERNEL_PERSISTENT, large_degree=0, warps_per_block=0, chunk_sources=0,
+              max_batch_sources=0, stats=False, stream=None):
+        a = RunArgs()
+        lib().ppr_run_args_init(C.byref(a))
+        a.alpha, a.R, a.seed = alpha, R, seed
+        a.src_begin = src_begin
+        a.src_end = self.info().n if src_end is None else src_end
+        a.tag, a.dangling, a.segments, a.topk, a.kernel = tag, dangling, int(bool(segments)), topk, kernel
+        a.large_degree, a.warps_per_block, a.chunk_sources = large_degree, warps_per_block, chunk_sources
+        a.max_batch_sources = max_batch_sources
+        a.stats = int(bool(stats))
+        a.stream = _stream_ptr(stream)
+        return a
+
+    def run_list(self, sources, wait=True, **kw) -> "Result":
+        """Walks from an explicit list of source ids; row i belongs to sources[i]."""
+        src = np.ascontiguousarray(sources, dtype=np.int32)
+        a = self._args(**kw)
+        h = C.c_void_p()
+        _check(lib().ppr_run_list(self.ctx.h, self.h, C.byref(a), src.ctypes.data, len(src), C.byref(h)))
+        r = Result(self, h, len(src), kw.get("topk", 0))
+        if wait:
+            r.wait()
+        return r
+
+    def workspace_size(self, **kw) -> int:
+        a = self._args(**kw)
+        n = C.c_size_t()
+        _check(lib().ppr_workspace_size(self.h, C.byref(a), C.byref(n)))
+        return n.value
+
+    def run_into(self, workspace, nnz, cols, cnts, cap, topk_idx=None, topk_cnt=None, **kw):
+        """Enqueues a run into caller-owned device tensors (no allocation; capturable)."""
+        a = self._args(**kw)
+        ti = _ptr(topk_idx)[0] if topk_idx is not None else None
+        tc = _ptr(topk_cnt)[0] if topk_cnt is not None else None
+        nbytes = workspace.numel() * workspace.element_size()
+        _check(lib().ppr_run_into(self.ctx.h, self.h, C.byref(a), _ptr(workspace)[0], nbytes, _ptr(nnz)[0],
+                                  _ptr(cols)[0], _ptr(cnts)[0], cap, ti, tc))
 
     def run(self, alpha=0.15, R=100, seed=1, src_begin=0, src_end=None, tag=0, dangling=0, segments=False,
             topk=0, kernel=KERNEL_PERSISTENT, large_degree=0, warps_per_block=0, chunk_sources=0,

@@ -221,6 +221,84 @@ def test_wide_rows(ppr, ctx, oracle):
         assert_same(G.run(alpha=0.25, R=500, seed=3, topk=3, kernel=kernel), ref, topk=3)
 
 
+def test_source_lists_equal_range_rows(ppr, ctx, oracle):
+    """A run over an explicit list (repeats, any order) gives each listed
+    source the same row and top-k as the range run."""
+    g = I.random_small_graph(800, 6000, seed=41, wmax=20, dangling=10)
+    G = ctx.load_graph(g.n, g.row_ptr, g.col, g.w)
+    ref = G.run(alpha=0.2, R=50, seed=3, topk=6)
+    rp, col, cnt = ref.sparse_rows()
+    idx, tc = ref.topk()
+    rng = np.random.Generator(np.random.PCG64(4))
+    lst = np.concatenate([rng.integers(0, g.n, 333), [5, 5, 5, g.n - 1, 0]]).astype(np.int32)
+    for kernel in (0, 1):
+        res = G.run_list(lst, alpha=0.2, R=50, seed=3, topk=6, kernel=kernel, max_batch_sources=97)
+        lrp, lcol, lcnt = res.sparse_rows()
+        lidx, ltc = res.topk()
+        for i, s_ in enumerate(lst):
+            assert np.array_equal(lcol[lrp[i]:lrp[i + 1]], col[rp[s_]:rp[s_ + 1]])
+            assert np.array_equal(lcnt[lrp[i]:lrp[i + 1]], cnt[rp[s_]:rp[s_ + 1]])
+            assert np.array_equal(lidx[i], idx[s_]) and np.array_equal(ltc[i], tc[s_])
+    with pytest.raises(ppr.PPRError):
+        G.run_list(np.array([0, g.n], dtype=np.int32))
+
+
+def _rows_from_fixed(nnz, cols, cnts, cap):
+    nnz = nnz.cpu().numpy().astype(np.int64)
+    S = len(nnz)
+    cols = cols.cpu().numpy().reshape(S, cap)
+    cnts = cnts.cpu().numpy().view(np.uint32).reshape(S, cap)
+    rp = np.zeros(S + 1, dtype=np.int64)
+    np.cumsum(nnz, out=rp[1:])
+    return rp, np.concatenate([cols[s, :nnz[s]] for s in range(S)]), np.concatenate([cnts[s, :nnz[s]] for s in range(S)])
+
+
+@pytest.mark.parametrize("batched", [False, True])
+def test_run_into_and_cuda_graph_replay(ppr, ctx, oracle, batched):
+    """ppr_run_into (caller workspace, no allocation) gives ppr_run's rows,
+    also when recorded into a CUDA graph and replayed twice."""
+    import torch
+    dev = torch.device("cuda:0")
+    if batched:
+        inst = I.chung_lu_instances(count=9, nmin=30, nmax=500, seed=8)
+        G = ctx.load_graph_batch(inst.node_off, inst.row_ptr, inst.col, inst.w)
+        n, cap = int(inst.node_off[-1]), min(64, int(np.diff(inst.node_off).max()))
+    else:
+        g = I.random_small_graph(1200, 9000, seed=43, wmax=20, dangling=10)
+        G = ctx.load_graph(g.n, g.row_ptr, g.col, g.w)
+        n, cap = g.n, 64
+    kw = dict(alpha=0.15, R=64, seed=9, topk=5, chunk_sources=3)
+    ref = G.run(**kw)
+    rp0, col0, cnt0 = ref.sparse_rows()
+    ti0, tc0 = ref.topk()
+    ws = torch.zeros(G.workspace_size(**kw), dtype=torch.uint8, device=dev)
+    nnz = torch.zeros(n, dtype=torch.int32, device=dev)
+    cols = torch.zeros(n * cap, dtype=torch.int32, device=dev)
+    cnts = torch.zeros(n * cap, dtype=torch.int32, device=dev)
+    ti = torch.zeros((n, 5), dtype=torch.int32, device=dev)
+    tc = torch.zeros((n, 5), dtype=torch.int32, device=dev)
+    s = torch.cuda.Stream(dev)
+    with torch.cuda.stream(s):
+        G.run_into(ws, nnz, cols, cnts, cap, ti, tc, stream=s, **kw)
+    s.synchronize()
+    got = _rows_from_fixed(nnz, cols, cnts, cap)
+    for a_, b_ in zip(got, (rp0, col0, cnt0)):
+        assert np.array_equal(a_, b_)
+    assert np.array_equal(ti.cpu().numpy(), ti0)
+    graph = torch.cuda.CUDAGraph()
+    with torch.cuda.graph(graph, stream=s, capture_error_mode="thread_local"):
+        G.run_into(ws, nnz, cols, cnts, cap, ti, tc, stream=s, **kw)
+    for _ in range(2):
+        nnz.zero_()
+        cols.zero_()
+        graph.replay()
+        torch.cuda.synchronize()
+        got = _rows_from_fixed(nnz, cols, cnts, cap)
+        for a_, b_ in zip(got, (rp0, col0, cnt0)):
+            assert np.array_equal(a_, b_)
+        assert np.array_equal(tc.cpu().numpy().view(np.uint32), tc0)
+
+
 def test_invalid_inputs_are_rejected(ppr, ctx):
     E = ppr.PPRError
     g = I.er_graph(50, 200, seed=1)
