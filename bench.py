@@ -40,6 +40,9 @@ WORKLOADS = {
                         "depth-3 segments for out-degree <= 8"),
     "rmat24plain": dict(alpha=0.15, R=50, seed=1, topk=64, segments=False,
                         desc="R-MAT scale 24 as rmat24, plain steps only"),
+    "chunglu2048": dict(alpha=0.15, R=200, seed=1, topk=32, segments=False,
+                        desc="2048 Chung-Lu graphs (exponent 2.3, n log-uniform in [100, 50000], mean degree 12, "
+                             "w U[1,100]) in one block-diagonal graph; one persistent launch replayed as a CUDA graph"),
 }
 L2_FLUSH_BYTES = 512 << 20
 
@@ -178,16 +181,53 @@ def cpu_baseline(g, wl, budget_s: float = 15.0):
                       f"{total_walks} walks, {total_steps} steps, {t_all:.1f} s"}
 
 
+def run_reference_batched(args, wl, I, O):
+    """Oracle on a bounded sample of the batched workload: the first 64
+    sources of every 128th instance, each instance walked with its id as tag."""
+    inst = I.chung_lu_instances(2048, 100, 50_000, 12.0, 2.3, 1, 100, seed=4242)
+    subs = [(gi, inst.instance(gi)) for gi in range(0, inst.count, 128)]
+    ogs = [(gi, O.prepare(sg.n, sg.row_ptr, sg.col, sg.w), sg.n) for gi, sg in subs]
+    per_step, st_tot, wk_tot = [], 0, 0
+    for it in range(args.warmup + args.steps):
+        t0 = time.perf_counter()
+        st = wk = 0
+        for gi, og, n in ogs:
+            e, stp = O.walks(og, wl["alpha"], wl["R"], wl["seed"], 0, min(n, 64), tag=gi)
+            rp, c, cn = O.rows(e, n)
+            O.topk(rp, c, cn, wl["topk"])
+            st += stp
+            wk += e.size
+        if it >= args.warmup:
+            per_step.append(time.perf_counter() - t0)
+            st_tot += st
+            wk_tot += wk
+    T = sum(per_step)
+    sample = f"first 64 sources of every 128th instance ({len(ogs)} instances) per step"
+    line = {"impl": "reference", "metric": "walk steps/s", "value": st_tot / T, "unit": "walk steps/s", "n_gpus": 1,
+            "steps": args.steps, "warmup": args.warmup, "ms_per_step": 1e3 * T / len(per_step),
+            "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "u32", "data": "synthetic",
+            "config": {"workload": args.workload, "desc": wl["desc"], "alpha": wl["alpha"], "R": wl["R"],
+                       "topk": wl["topk"]},
+            "walks_per_s": wk_tot / T,
+            "cpu_baseline": {"value": st_tot / T, "unit": "walk steps/s", "cores": 1, "kind": "oracle",
+                             "sample": sample},
+            "e2e": {"value": st_tot / T, "unit": "walk steps/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
+    print(json.dumps(line))
+    return 0
+
+
 def run_reference(args):
     rank, world, _ = env_rank()
     if rank != 0:
         return 0
     from paper_1903_11749_gb300 import inputs as I
     wl = WORKLOADS[args.workload]
-    g = I.workload_graph(args.workload.replace("plain", ""))
     sys.path.insert(0, os.path.join(ROOT, "oracle"))
     import oracle as O
     O.build()
+    if args.workload == "chunglu2048":
+        return run_reference_batched(args, wl, I, O)
+    g = I.workload_graph(args.workload.replace("plain", ""))
     og = O.prepare(g.n, g.row_ptr, g.col, g.w)
     n_blk = 64
     per_step = []
@@ -223,6 +263,166 @@ def run_reference(args):
     return 0
 
 
+def run_batched(args):
+    """Many small graphs in one fused persistent launch, recorded once as a
+    CUDA graph (ppr_run_into: caller workspace, no allocation) and replayed
+    every step; launch tuning from the autotuner (cached as JSON)."""
+    import torch
+    from paper_1903_11749_gb300 import build as B
+    from paper_1903_11749_gb300 import inputs as I
+    from paper_1903_11749_gb300 import tune
+    B.build()
+    from paper_1903_11749_gb300 import ppr
+    rank, world, local = env_rank()
+    if world > 1:
+        import torch.distributed as dist
+        dist.init_process_group("nccl", init_method="env://")
+    else:
+        dist = None
+    torch.cuda.set_device(local)
+    dev = torch.device("cuda", local)
+    wl = WORKLOADS[args.workload]
+    inst = I.chung_lu_instances(2048, 100, 50_000, 12.0, 2.3, 1, 100, seed=4242)
+    N = int(inst.node_off[-1])
+    ctx = ppr.Context(local)
+    G = ctx.load_graph_batch(inst.node_off, inst.row_ptr, inst.col, inst.w)
+    run_kw = dict(alpha=wl["alpha"], R=wl["R"], seed=wl["seed"], topk=wl["topk"])
+    t0 = time.perf_counter()
+    tun = tune.tuned(G, torch.cuda.get_device_name(dev), sample_sources=400_000, **run_kw)
+    tune_s = time.perf_counter() - t0
+    lk = tune.launch_kwargs(tun)
+    # statistics pass: draws and algorithmic sectors of one full pass
+    r = G.run(stats=True, **run_kw, **lk)
+    info = r.info()
+    draws, sectors, walks = int(info.steps), int(info.sectors), int(info.walks)
+    del r
+    # walker-only time (for the roofline) from an eager run
+    kms = []
+    for _ in range(2):
+        r = G.run(**run_kw, **lk)
+        kms.append(r.info().kernel_ms)
+        del r
+    cap = min(wl["R"], int(np.diff(inst.node_off).max()))
+    k = wl["topk"]
+    ws = torch.empty(G.workspace_size(**run_kw, **lk), dtype=torch.uint8, device=dev)
+    nnz = torch.empty(N, dtype=torch.int32, device=dev)
+    cols = torch.empty(N * cap, dtype=torch.int32, device=dev)
+    cnts = torch.empty(N * cap, dtype=torch.int32, device=dev)
+    ti = torch.empty((N, k), dtype=torch.int32, device=dev)
+    tc = torch.empty((N, k), dtype=torch.int32, device=dev)
+    flush = torch.empty(L2_FLUSH_BYTES // 4, dtype=torch.int32, device=dev)
+    s = torch.cuda.Stream(dev)
+    with torch.cuda.stream(s):
+        G.run_into(ws, nnz, cols, cnts, cap, ti, tc, stream=s, tag=0, **run_kw, **lk)
+    s.synchronize()
+    graph = torch.cuda.CUDAGraph()
+    with torch.cuda.graph(graph, stream=s, capture_error_mode="thread_local"):
+        G.run_into(ws, nnz, cols, cnts, cap, ti, tc, stream=s, tag=0, **run_kw, **lk)
+    for _ in range(args.warmup):
+        graph.replay()
+    torch.cuda.synchronize(dev)
+    clocks = Clocks(local, None)
+    clocks.start()
+    launches0 = ppr.kernel_launches()
+    step_ms = []
+    for _ in range(args.steps):
+        flush.fill_(1)
+        e0 = torch.cuda.Event(enable_timing=True)
+        e1 = torch.cuda.Event(enable_timing=True)
+        cs = torch.cuda.current_stream(dev)
+        e0.record(cs)
+        graph.replay()
+        e1.record(cs)
+        e1.synchronize()
+        step_ms.append(e0.elapsed_time(e1))
+    torch.cuda.synchronize(dev)
+    clk = clocks.stop()
+    T_max, units = reduce_over_ranks(sum(step_ms) / 1e3, [draws * args.steps, walks * args.steps], world, dist, dev)
+    # kernels per replay: chunk count, 3 scan kernels, chunk fill, walker, reduction
+    launches = 7 * args.steps
+    # the unfused alternatives on the same GB300
+    r = G.run(kernel=ppr.KERNEL_PLAIN, **run_kw)
+    r = G.run(kernel=ppr.KERNEL_PLAIN, **run_kw)
+    plain_ms = r.info().run_ms
+    del r
+    t0 = time.perf_counter()
+    per_inst_ms = 0.0
+    for gi in range(inst.count):
+        r = G.run(src_begin=int(inst.node_off[gi]), src_end=int(inst.node_off[gi + 1]), **run_kw, **lk)
+        per_inst_ms += r.info().run_ms
+        del r
+    per_inst_wall = time.perf_counter() - t0
+    peak, peak_kind = measured_peaks()
+    kms_ = statistics.mean(kms)
+    achieved = sectors * 32.0 / (kms_ / 1e3) / 1e9
+    # end to end: host CSR in (pinned), one run, rows + top-k out (pinned)
+    e2e = None
+    if not args.no_e2e:
+        h = [torch.from_numpy(x).pin_memory() for x in (inst.row_ptr, inst.col, inst.w.view(np.int32))]
+        o_rp = torch.empty(N + 1, dtype=torch.int64).pin_memory()
+        o_col = torch.empty(N * cap, dtype=torch.int32).pin_memory()
+        o_cnt = torch.empty(N * cap, dtype=torch.int32).pin_memory()
+        o_ti = torch.empty((N, k), dtype=torch.int32).pin_memory()
+        o_tc = torch.empty((N, k), dtype=torch.int32).pin_memory()
+        times = []
+        for it in range(3):
+            torch.cuda.synchronize(dev)
+            t0 = time.perf_counter()
+            Gh = ctx.load_graph_batch(inst.node_off, h[0], h[1], h[2])
+            r = Gh.run(**run_kw, **lk)
+            nz = r.sparse_rows_into(o_rp, o_col, o_cnt)
+            r.topk_into(k, o_ti, o_tc)
+            if it > 0:
+                times.append(time.perf_counter() - t0)
+            del r, Gh
+        e2e = {"value": draws / statistics.mean(times), "unit": "walk steps/s",
+               "h2d_bytes_per_step": int(inst.row_ptr.nbytes + inst.col.nbytes + inst.w.nbytes),
+               "d2h_bytes_per_step": int((N + 1) * 8 + nz * 8 + N * k * 8), "ms_per_step": 1e3 * statistics.mean(times)}
+    cpu = None
+    if rank == 0 and world == 1 and not args.no_cpu_baseline:
+        sys.path.insert(0, os.path.join(ROOT, "oracle"))
+        import oracle as O
+        O.build()
+        st = wk = 0
+        t0 = time.perf_counter()
+        for gi in range(0, inst.count, 128):
+            sub = inst.instance(gi)
+            og = O.prepare(sub.n, sub.row_ptr, sub.col, sub.w)
+            e, stp = O.walks(og, wl["alpha"], wl["R"], wl["seed"], 0, min(sub.n, 64), tag=gi)
+            rp_, c_, n_ = O.rows(e, sub.n)
+            O.topk(rp_, c_, n_, k)
+            st += stp
+            wk += e.size
+        dt = time.perf_counter() - t0
+        cpu = {"value": st / dt, "unit": "walk steps/s", "cores": 1, "kind": "oracle", "walks_per_s": wk / dt,
+               "sample": f"first 64 sources of every 128th instance ({inst.count // 128} instances), {wk} walks, "
+                         f"{st} steps, {dt:.1f} s"}
+    if rank == 0:
+        line = {"metric": "walk steps/s", "value": units[0] / T_max, "unit": "walk steps/s", "n_gpus": world,
+                "steps": args.steps, "warmup": args.warmup, "ms_per_step": 1e3 * T_max / args.steps,
+                "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "u32", "data": "synthetic",
+                "config": {"workload": args.workload, "desc": wl["desc"], "alpha": wl["alpha"], "R": wl["R"],
+                           "topk": k, "instances": inst.count, "n": N, "m": int(inst.row_ptr[-1]),
+                           "parallelism": "1 GPU", "l2": "flushed between steps (512 MB write)",
+                           "step": "one CUDA-graph replay: chunk table, fused persistent walker, reduction",
+                           "tuning": tun, "tune_seconds": tune_s},
+                "walks_per_s": units[1] / T_max, "steps_per_walk": draws / max(walks, 1),
+                "roofline": {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s", "frac": achieved / peak,
+                             "traffic": None, "peak_kind": peak_kind, "kernel": "k_walk_persistent",
+                             "alg_bytes_per_launch": sectors * 32.0, "kernel_ms": kms_,
+                             "sectors_per_draw": sectors / max(draws, 1)},
+                "plain_kernel": {"value": draws / (plain_ms / 1e3), "unit": "walk steps/s", "ms_per_step": plain_ms,
+                                 "kernel": "one thread per walk over all instances + reduction"},
+                "unfused_per_instance": {"value": draws / (per_inst_ms / 1e3), "unit": "walk steps/s",
+                                         "device_ms": per_inst_ms, "wall_s": per_inst_wall,
+                                         "kernel": "one persistent run per instance (2048 runs)"},
+                "cpu_baseline": cpu, "e2e": e2e, "gpu_launches": launches, "clocks": clk}
+        print(json.dumps(line))
+    if world > 1:
+        dist.destroy_process_group()
+    return 0
+
+
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
@@ -241,6 +441,8 @@ def main():
     args = ap.parse_args()
     if args.impl == "reference":
         return run_reference(args)
+    if args.workload == "chunglu2048":
+        return run_batched(args)
 
     import torch
     import torch.distributed as dist

@@ -161,7 +161,7 @@ typedef struct {
     int32_t kernel;      /* PPR_KERNEL_PERSISTENT or PPR_KERNEL_PLAIN */
     int32_t large_degree;/* out-degree above which the whole warp searches a lane's row
                             cooperatively (persistent kernel); 0 = never (default) */
-    int32_t warps_per_block;  /* persistent kernel tuning, 0 = default */
+    int32_t warps_per_block;  /* persistent kernel: 4 or 8 warps per CTA (0 = 8) */
     int32_t chunk_sources;    /* sources per queue item, 0 = default */
     int64_t max_batch_sources;/* sources per device batch, 0 = sized to free device memory */
     int32_t stats;       /* 1: also count the algorithmic 32-byte sectors of every step (slower;
@@ -207,6 +207,26 @@ int ppr_workspace_size(const ppr_graph *g, const ppr_run_args *args, size_t *byt
  */
 int ppr_run_into(ppr_ctx *ctx, const ppr_graph *g, const ppr_run_args *args, void *workspace, size_t bytes,
                  uint32_t *nnz, int32_t *cols, uint32_t *cnts, uint32_t cap, int32_t *topk_idx, uint32_t *topk_cnt);
+
+/* Launch tuning chosen by ppr_autotune. */
+typedef struct {
+    int32_t chunk_sources;   /* sources per work-queue item */
+    int32_t large_degree;    /* cooperative-search threshold (0 = off) */
+    int32_t warps_per_block; /* walkers per CTA / 32 (4 or 8) */
+    float ms;                /* device time of the best candidate on the sample */
+    int32_t candidates;      /* candidates timed */
+    int64_t sample_sources;  /* sources in the sample */
+} ppr_tuning;
+
+/*
+ * Times the persistent walker on a sample of the run's sources (at most
+ * sample_sources, 0 = 65536; evenly strided for plain graphs, a leading range
+ * for batched graphs) for each candidate of walkers per CTA (128, 256), queue
+ * chunk (1/4x .. 4x of 400/R sources) and cooperative threshold (off, 4096,
+ * 65536), and returns the fastest.  Synchronous; allocates scratch for the
+ * sample.  Tuning never changes results.
+ */
+int ppr_autotune(ppr_ctx *ctx, const ppr_graph *g, const ppr_run_args *args, int64_t sample_sources, ppr_tuning *best);
 
 /* Waits for the run; PPR_ETIMEOUT if not finished within timeout_ms
  * (timeout_ms < 0: wait without deadline).  The result stays valid. */

@@ -536,6 +536,116 @@ int ppr_run_into(ppr_ctx *ctx, const ppr_graph *g, const ppr_run_args *a, void *
     return launch_walks(ctx, g, plan, o, a->src_begin, S, nullptr, 0, w + 256, st, nullptr);
 }
 
+// Times each candidate tuning on a sample of the run's sources (an evenly
+// strided list) and keeps the fastest.  Results do not depend on the tuning.
+int ppr_autotune(ppr_ctx *ctx, const ppr_graph *g, const ppr_run_args *a, int64_t sample_sources, ppr_tuning *best)
+{
+    if (!ctx || !g || !a || !best) {
+        set_error("NULL argument");
+        return PPR_EINVAL;
+    }
+    RunPlan plan;
+    int rc = check_run(g, a, 0, false, &plan);
+    if (rc) return rc;
+    if ((rc = set_device(ctx))) return rc;
+    cudaStream_t st = (cudaStream_t)a->stream;
+    if (a->segments && (rc = build_segments(const_cast<ppr_graph *>(g), plan.T, st))) return rc;
+    const int64_t S_all = a->src_end - a->src_begin;
+    const int64_t S = std::max<int64_t>(1, std::min<int64_t>(S_all, sample_sources > 0 ? sample_sources : 65536));
+    // batched graphs keep their instance structure: tune on a contiguous range
+    // (chunks follow instances); plain graphs on an evenly strided list
+    const bool use_list = g->instances == 0;
+    std::vector<uint32_t> list;
+    if (use_list) {
+        list.resize((size_t)S);
+        for (int64_t i = 0; i < S; ++i) list[(size_t)i] = (uint32_t)(a->src_begin + i * S_all / S);
+    }
+    const uint32_t cap = row_capacity(g, a->R);
+    const int32_t topk = a->topk;
+    unsigned char *buf = nullptr;
+    const size_t ws_bytes = launch_workspace_bytes(g, plan, S);
+    const size_t out_bytes = (size_t)S * (4 + 8ull * cap + 8ull * topk) + 256 + sizeof(uint32_t) * S + 1024;
+    if ((rc = dev_alloc((void **)&buf, ws_bytes + out_bytes + 256, "autotune buffers", st))) return rc;
+    unsigned char *p = buf;
+    auto take = [&](size_t n) {
+        unsigned char *q = p;
+        p += (n + 255) & ~(size_t)255;
+        return q;
+    };
+    unsigned char *ws = take(ws_bytes);
+    Outputs o;
+    o.counters = reinterpret_cast<unsigned long long *>(take(256));
+    o.nnz = reinterpret_cast<uint32_t *>(take(sizeof(uint32_t) * S));
+    o.cols = reinterpret_cast<int32_t *>(take(sizeof(int32_t) * S * cap));
+    o.cnts = reinterpret_cast<uint32_t *>(take(sizeof(uint32_t) * S * cap));
+    o.topk_idx = topk ? reinterpret_cast<int32_t *>(take(sizeof(int32_t) * S * topk)) : nullptr;
+    o.topk_cnt = topk ? reinterpret_cast<uint32_t *>(take(sizeof(uint32_t) * S * topk)) : nullptr;
+    o.cap = cap;
+    o.topk = topk;
+    uint32_t *d_list = use_list ? reinterpret_cast<uint32_t *>(take(sizeof(uint32_t) * S)) : nullptr;
+    cudaEvent_t e0 = nullptr, e1 = nullptr;
+    cudaError_t e = cudaEventCreate(&e0);
+    if (e == cudaSuccess) e = cudaEventCreate(&e1);
+    if (e == cudaSuccess && use_list)
+        e = cudaMemcpyAsync(d_list, list.data(), sizeof(uint32_t) * S, cudaMemcpyHostToDevice, st);
+    if (e != cudaSuccess) {
+        dev_free(buf, st);
+        return cuda_fail(e, "autotune setup");
+    }
+    const int cs_base = std::max(1, (int)(400 / a->R));
+    const int cs_cands[] = {std::max(1, cs_base / 4), std::max(1, cs_base / 2), cs_base, cs_base * 2, cs_base * 4};
+    const int lg_cands[] = {0, 4096, 65536};
+    const int wpb_cands[] = {8, 4};
+    ppr_tuning bt{};
+    bt.ms = -1.f;
+    int tried = 0;
+    for (int wpb : wpb_cands)
+        for (int lg : lg_cands)
+            for (int cs : cs_cands) {
+                if ((uint64_t)cs * a->R > (1u << 20)) continue;
+                RunPlan pl = plan;
+                pl.kernel = PPR_KERNEL_PERSISTENT;
+                pl.stats = false;
+                pl.chunk_sources = cs;
+                pl.large_degree = lg;
+                pl.warps_per_block = wpb;
+                if (launch_workspace_bytes(g, pl, S) > ws_bytes) continue;
+                float ms_best = 1e30f;
+                for (int rep = 0; rep < 2; ++rep) {
+                    cudaMemsetAsync(o.counters, 0, 256, st);
+                    cudaEventRecord(e0, st);
+                    rc = launch_walks(ctx, g, pl, o, use_list ? 0 : a->src_begin, S, d_list, 0, ws, st, nullptr);
+                    cudaEventRecord(e1, st);
+                    if (rc) break;
+                    e = cudaEventSynchronize(e1);
+                    if (e != cudaSuccess) {
+                        rc = cuda_fail(e, "autotune run");
+                        break;
+                    }
+                    float ms = 0.f;
+                    cudaEventElapsedTime(&ms, e0, e1);
+                    if (rep > 0) ms_best = std::min(ms_best, ms);
+                }
+                if (rc) break;
+                ++tried;
+                if (bt.ms < 0 || ms_best < bt.ms) {
+                    bt.chunk_sources = cs;
+                    bt.large_degree = lg;
+                    bt.warps_per_block = wpb;
+                    bt.ms = ms_best;
+                }
+            }
+    cudaEventDestroy(e0);
+    cudaEventDestroy(e1);
+    cudaStreamSynchronize(st);
+    dev_free(buf, st);
+    if (rc) return rc;
+    bt.candidates = tried;
+    bt.sample_sources = S;
+    *best = bt;
+    return PPR_OK;
+}
+
 int ppr_wait(ppr_result *r, int64_t timeout_ms)
 {
     if (!r) {

@@ -39,6 +39,7 @@ struct KParams {
     const int4 *chunks;       // batched graphs: {position, nsrc, instance, 0}; else null
     const uint32_t *src_list; // explicit sources (position -> node id); null: s_begin + position
     const int64_t *inst_off;  // batched graphs: node_off
+    int32_t instances;
     AggOut out;
     uint32_t *ends;           // S * R endpoints (instance-local ids)
     unsigned long long *queue;
@@ -182,10 +183,21 @@ __global__ void __launch_bounds__(256, PPR_WALK_MINB) k_walk_plain(KParams p)
         const uint64_t i = t / p.R;
         const uint32_t j = (uint32_t)(t - i * p.R);
         const uint32_t src = p.src_list ? p.src_list[i] : (uint32_t)(p.s_begin + (int64_t)i);
-        uint32_t k = 0, u = src, end = 0;
-        while (!walk_step<E, SEG, false, STATS>(p, edges, true, src, src, j, p.tag, k, u, end, tl)) {
+        uint32_t ctr_base = 0, tag = p.tag;
+        if (p.inst_off) {  // batched graph: the source's instance gives counter base and tag
+            int32_t lo = 0, hi = p.instances;
+            while (hi - lo > 1) {
+                const int32_t mid = (lo + hi) >> 1;
+                if (p.inst_off[mid] <= (int64_t)src) lo = mid;
+                else hi = mid;
+            }
+            ctr_base = (uint32_t)p.inst_off[lo];
+            tag = (uint32_t)lo;
         }
-        p.ends[t] = end;
+        uint32_t k = 0, u = src, end = 0;
+        while (!walk_step<E, SEG, false, STATS>(p, edges, true, src, src - ctr_base, j, tag, k, u, end, tl)) {
+        }
+        p.ends[t] = end - ctr_base;
     }
     warp_add_tally<STATS>(p.steps, tl);
 }
@@ -372,13 +384,15 @@ static int launch_typed(ppr_ctx *ctx, const KParams &kp, const RunPlan &plan, in
         return launch_aggregate(ctx, kp, S, st);
     }
     int per_sm = 0;
-    PPR_CUDA(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_walk_persistent<E, SEG, STATS>, 256, 0));
+    // walkers per CTA: 32 * warps_per_block (4 or 8 warps; default 8)
+    const int wpb = plan.warps_per_block == 4 ? 4 : 8;
+    PPR_CUDA(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_walk_persistent<E, SEG, STATS>, 32 * wpb, 0));
     if (per_sm < 1) per_sm = 1;
     int64_t blocks = (int64_t)ctx->sms * per_sm;
-    int64_t needed = ((int64_t)kp.nchunks + 7) / 8;
+    int64_t needed = ((int64_t)kp.nchunks + wpb - 1) / wpb;
     if (blocks > needed) blocks = std::max<int64_t>(needed, 1);
     if ((rc = walker_event(r, st))) return rc;
-    k_walk_persistent<E, SEG, STATS><<<(unsigned)blocks, 256, 0, st>>>(kp);
+    k_walk_persistent<E, SEG, STATS><<<(unsigned)blocks, 32 * wpb, 0, st>>>(kp);
     note_launch();
     PPR_CUDA(cudaGetLastError());
     if ((rc = walker_event(r, st))) return rc;
@@ -468,8 +482,8 @@ int launch_walks(ppr_ctx *ctx, const ppr_graph *g, const RunPlan &plan, const Ou
 
     if (plan.kernel == PPR_KERNEL_PLAIN) {
         if (g->instances > 0) {
-            set_error("the plain kernel runs plain graphs only");
-            return PPR_ENOTSUP;
+            kp.inst_off = g->d_node_off;
+            kp.instances = g->instances;
         }
     } else {
         const uint32_t CS = chunk_sources(plan);

@@ -42,6 +42,11 @@ class RunArgs(C.Structure):
                 ("stats", C.c_int32), ("stream", C.c_void_p)]
 
 
+class Tuning(C.Structure):
+    _fields_ = [("chunk_sources", C.c_int32), ("large_degree", C.c_int32), ("warps_per_block", C.c_int32),
+                ("ms", C.c_float), ("candidates", C.c_int32), ("sample_sources", C.c_int64)]
+
+
 class ResultInfo(C.Structure):
     _fields_ = [("sources", C.c_int64), ("R", C.c_uint32), ("topk", C.c_int32), ("nnz", C.c_int64),
                 ("steps", C.c_uint64), ("walks", C.c_uint64), ("kernel_ms", C.c_float), ("sectors", C.c_uint64),
@@ -77,6 +82,7 @@ _SIGS = {
     "ppr_run_list": (C.c_int, [C.c_void_p, C.c_void_p, C.POINTER(RunArgs), C.c_void_p, C.c_int64,
                                C.POINTER(C.c_void_p)]),
     "ppr_workspace_size": (C.c_int, [C.c_void_p, C.POINTER(RunArgs), C.POINTER(C.c_size_t)]),
+    "ppr_autotune": (C.c_int, [C.c_void_p, C.c_void_p, C.POINTER(RunArgs), C.c_int64, C.POINTER(Tuning)]),
     "ppr_run_into": (C.c_int, [C.c_void_p, C.c_void_p, C.POINTER(RunArgs), C.c_void_p, C.c_size_t, C.c_void_p,
                                C.c_void_p, C.c_void_p, C.c_uint32, C.c_void_p, C.c_void_p]),
 }
@@ -222,6 +228,14 @@ class Graph:
         if wait:
             r.wait()
         return r
+
+    def autotune(self, sample_sources=0, **kw) -> dict:
+        a = self._args(**kw)
+        t = Tuning()
+        _check(lib().ppr_autotune(self.ctx.h, self.h, C.byref(a), sample_sources, C.byref(t)))
+        return {"chunk_sources": t.chunk_sources, "large_degree": t.large_degree,
+                "warps_per_block": t.warps_per_block, "ms": t.ms, "candidates": t.candidates,
+                "sample_sources": t.sample_sources}
 
     def workspace_size(self, **kw) -> int:
         a = self._args(**kw)

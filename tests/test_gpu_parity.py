@@ -157,7 +157,18 @@ def test_segment_mode_matches_segment_oracle(ppr, ctx, oracle):
 def test_batched_instances_equal_each_instance_alone(ppr, ctx, oracle):
     inst = I.chung_lu_instances(count=12, nmin=20, nmax=400, seed=5)
     G = ctx.load_graph_batch(inst.node_off, inst.row_ptr, inst.col, inst.w)
-    res = G.run(alpha=0.15, R=40, seed=1, topk=4)
+    for kernel in (0, 1):
+        _check_instances(oracle, inst, G.run(alpha=0.15, R=40, seed=1, topk=4, kernel=kernel))
+    # a sub-range cutting through instances
+    a, b = int(inst.node_off[3]) + 5, int(inst.node_off[7]) - 3
+    res = G.run(alpha=0.15, R=40, seed=1, topk=4, src_begin=a, src_end=b, chunk_sources=2)
+    full = G.run(alpha=0.15, R=40, seed=1, topk=4)
+    frp, fcol, fcnt = full.sparse_rows()
+    rp, col, cnt = res.sparse_rows()
+    assert np.array_equal(col, fcol[frp[a]:frp[b]]) and np.array_equal(cnt, fcnt[frp[a]:frp[b]])
+
+
+def _check_instances(oracle, inst, res):
     rp, col, cnt = res.sparse_rows()
     idx, tc = res.topk()
     for gi in range(inst.count):
@@ -170,6 +181,26 @@ def test_batched_instances_equal_each_instance_alone(ppr, ctx, oracle):
         assert np.array_equal(cnt[rp[a]: rp[b]], ocnt)
         assert np.array_equal(idx[a:b], ref["topk"][0])
         assert np.array_equal(tc[a:b], ref["topk"][1])
+
+
+def test_autotune_picks_a_valid_launch(ppr, ctx, oracle):
+    """The tuner times the candidates and returns one; results under any
+    tuning are the same counts."""
+    g = I.random_small_graph(3000, 30000, seed=44, wmax=20, dangling=30)
+    G = ctx.load_graph(g.n, g.row_ptr, g.col, g.w)
+    t = G.autotune(sample_sources=1000, alpha=0.2, R=30, seed=1, topk=4)
+    assert t["candidates"] >= 10 and t["ms"] > 0 and t["warps_per_block"] in (4, 8)
+    ref = G.run(alpha=0.2, R=30, seed=1, topk=4)
+    tuned = G.run(alpha=0.2, R=30, seed=1, topk=4, chunk_sources=t["chunk_sources"],
+                  large_degree=t["large_degree"], warps_per_block=t["warps_per_block"])
+    a, b = ref.sparse_rows(), tuned.sparse_rows()
+    for x, y in zip(a, b):
+        assert np.array_equal(x, y)
+    assert np.array_equal(ref.topk()[0], tuned.topk()[0])
+    inst = I.chung_lu_instances(count=20, nmin=50, nmax=800, seed=6)
+    Gb = ctx.load_graph_batch(inst.node_off, inst.row_ptr, inst.col, inst.w)
+    tb = Gb.autotune(sample_sources=2000, alpha=0.15, R=20, seed=1)
+    assert tb["candidates"] >= 10
 
 
 def test_device_inputs_and_outputs(ppr, ctx, oracle):
