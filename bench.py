@@ -40,6 +40,9 @@ WORKLOADS = {
                         "depth-3 segments for out-degree <= 8"),
     "rmat24plain": dict(alpha=0.15, R=50, seed=1, topk=64, segments=False,
                         desc="R-MAT scale 24 as rmat24, plain steps only"),
+    "serve": dict(alpha=0.15, R=100, seed=1, topk=32, segments=False,
+                  desc="queries on the R-MAT scale-24 graph resident on the device: |S| log-uniform in [1, 1e5] "
+                       "distinct uniform sources, Poisson arrivals at rho x measured capacity"),
     "chunglu2048": dict(alpha=0.15, R=200, seed=1, topk=32, segments=False,
                         desc="2048 Chung-Lu graphs (exponent 2.3, n log-uniform in [100, 50000], mean degree 12, "
                              "w U[1,100]) in one block-diagonal graph; one persistent launch replayed as a CUDA graph"),
@@ -423,6 +426,98 @@ def run_batched(args):
     return 0
 
 
+def run_serving(args):
+    """Continuous-batching service on the scale-24 graph: first the capacity
+    (queries submitted back to back), then a Poisson stream at rho x that rate;
+    latency = completion - submission (steady clock, inside the library)."""
+    import threading
+    import torch
+    from paper_1903_11749_gb300 import build as B
+    from paper_1903_11749_gb300 import inputs as I
+    B.build()
+    from paper_1903_11749_gb300 import ppr
+    rank, world, local = env_rank()
+    if rank != 0:
+        return 0
+    torch.cuda.set_device(local)
+    wl = WORKLOADS["serve"]
+    g = I.workload_graph("rmat24")
+    ctx = ppr.Context(local)
+    G = ctx.load_graph(g.n, g.row_ptr, g.col, g.w)
+    rng = np.random.Generator(np.random.PCG64(777))
+    smax = 100_000
+    n_warm, n_meas = args.serve_warmup, args.serve_queries
+
+    def make_queries(k):
+        sizes = np.floor(np.exp(rng.uniform(0.0, np.log(smax), k))).astype(np.int64)
+        return [rng.choice(g.n, size=int(s), replace=False).astype(np.int32) for s in sizes]
+
+    kw = dict(alpha=wl["alpha"], R=wl["R"], seed=wl["seed"], topk=wl["topk"])
+    ctx.serve_start(G, streams=args.serve_streams, max_sources=smax, max_topk=wl["topk"])
+
+    def run_stream(queries, rate):
+        """Submit at Poisson times (rate queries/s; 0 = back to back), poll all."""
+        ids = [None] * len(queries)
+        gaps = rng.exponential(1.0 / rate, len(queries)) if rate > 0 else np.zeros(len(queries))
+        t_start = time.perf_counter()
+
+        def submitter():
+            t_next = t_start
+            for i, q in enumerate(queries):
+                t_next += gaps[i]
+                d = t_next - time.perf_counter()
+                if d > 0:
+                    time.sleep(d)
+                ids[i] = ctx.submit(q, **kw)
+
+        th = threading.Thread(target=submitter)
+        th.start()
+        stats = []
+        for i, q in enumerate(queries):
+            while ids[i] is None:
+                time.sleep(0.0002)
+            stats.append(ctx.poll(ids[i], len(q), kw["topk"], timeout_ms=600000)[2])
+        th.join()
+        return stats
+
+    warm = make_queries(n_warm)
+    st = run_stream(warm, 0)  # back to back: the service capacity
+    t0 = min(x["submit_ns"] for x in st)
+    t1 = max(x["done_ns"] for x in st)
+    cap_walks = sum(x["walks"] for x in st) / ((t1 - t0) / 1e9)
+    mean_walks = np.mean([len(q) for q in warm]) * wl["R"]
+    results = {}
+    clocks = Clocks(local, None)
+    clocks.start()
+    for rho in args.serve_rho:
+        qs = make_queries(n_meas)
+        rate = rho * cap_walks / (((smax - 1) / np.log(smax)) * wl["R"])
+        st = run_stream(qs, rate)
+        lat = np.array([(x["done_ns"] - x["submit_ns"]) / 1e6 for x in st])
+        t0 = min(x["submit_ns"] for x in st)
+        t1 = max(x["done_ns"] for x in st)
+        walks = sum(x["walks"] for x in st)
+        results[str(rho)] = {"queries": len(qs), "rate_qps": rate, "p50_ms": float(np.percentile(lat, 50)),
+                             "p99_ms": float(np.percentile(lat, 99)), "mean_ms": float(lat.mean()),
+                             "walks_per_s": walks / ((t1 - t0) / 1e9), "seconds": (t1 - t0) / 1e9}
+    clk = clocks.stop()
+    ctx.serve_stop()
+    T = ppr.alpha_threshold(wl["alpha"])
+    main_r = results[str(args.serve_rho[0])]
+    line = {"metric": "walk steps/s", "value": main_r["walks_per_s"] * (2.0 ** 32 / T), "unit": "walk steps/s",
+            "n_gpus": 1, "steps": n_meas, "warmup": n_warm, "ms_per_step": main_r["mean_ms"],
+            "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "u32", "data": "synthetic",
+            "config": {"workload": "serve", "desc": wl["desc"], "alpha": wl["alpha"], "R": wl["R"], "topk": wl["topk"],
+                       "n": g.n, "m": g.m, "streams": args.serve_streams,
+                       "steps_counted": "expected steps walks*2^32/T of the delivered walks",
+                       "step": "one query (ms_per_step = mean latency)"},
+            "p50_ms": main_r["p50_ms"], "p99_ms": main_r["p99_ms"], "walks_per_s": main_r["walks_per_s"],
+            "capacity_walks_per_s": cap_walks, "mean_walks_per_query": mean_walks, "by_rho": results,
+            "clocks": clk, "gpu_launches": None}
+    print(json.dumps(line))
+    return 0
+
+
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
@@ -438,11 +533,19 @@ def main():
     ap.add_argument("--warps-per-block", type=int, default=0)
     ap.add_argument("--chunk-sources", type=int, default=0)
     ap.add_argument("--large-degree", type=int, default=0)
+    ap.add_argument("--serve-queries", type=int, default=2000)
+    ap.add_argument("--serve-warmup", type=int, default=200)
+    ap.add_argument("--serve-streams", type=int, default=4)
+    ap.add_argument("--serve-rho", type=float, nargs="+", default=[0.5, 0.8])
+    ap.add_argument("--sample-every", type=int, default=0,
+                    help="profiling case: walk only every k-th source (an explicit source list)")
     args = ap.parse_args()
     if args.impl == "reference":
         return run_reference(args)
     if args.workload == "chunglu2048":
         return run_batched(args)
+    if args.workload == "serve":
+        return run_serving(args)
 
     import torch
     import torch.distributed as dist
@@ -469,11 +572,16 @@ def main():
     d_w = torch.from_numpy(g.w.view(np.int32)).to(dev)
     flush = torch.empty(L2_FLUSH_BYTES // 4, dtype=torch.int32, device=dev)
 
+    sample = np.arange(a, b, args.sample_every, dtype=np.int32) if args.sample_every > 0 else None
+
     def step(kernel=ppr.KERNEL_PERSISTENT, stats=False):
         G = ctx.load_graph(g.n, d_rp, d_col, d_w, stream=stream, m=g.m)
-        r = G.run(alpha=wl["alpha"], R=wl["R"], seed=wl["seed"], src_begin=a, src_end=b, tag=rank_tag,
-                  topk=wl["topk"], segments=wl["segments"], kernel=kernel, stats=stats, stream=stream, wait=False,
-                  **tune)
+        kw = dict(alpha=wl["alpha"], R=wl["R"], seed=wl["seed"], tag=rank_tag, topk=wl["topk"],
+                  segments=wl["segments"], kernel=kernel, stats=stats, stream=stream, wait=False, **tune)
+        if sample is not None:
+            r = G.run_list(sample, **kw)
+        else:
+            r = G.run(src_begin=a, src_end=b, **kw)
         return G, r
 
     # statistics launch (untimed): exact draws and algorithmic sectors of one pass

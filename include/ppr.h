@@ -296,6 +296,55 @@ void ppr_free_result(ppr_result *r);
 int ppr_run_noalloc(ppr_ctx *ctx, const ppr_graph *g, const ppr_run_args *args, uint32_t *nnz, int32_t *cols,
                     uint32_t *cnts, uint32_t cap, int32_t *topk_idx, uint32_t *topk_cnt);
 
+/* ---------------------------------------------------------------- serving
+ * Multi-source queries with continuous batching: a scheduler thread admits
+ * queries in arrival order as soon as one of `streams` device slots is free
+ * and the query's device memory fits the budget left by the queries in
+ * flight; queries run concurrently on their own streams.  Each query returns
+ * the top-k of every one of its sources (same counts as ppr_run_list with
+ * the same alpha, R and seed; tag 0, dangling mode 0, plain steps).
+ */
+typedef struct {
+    int32_t streams;        /* concurrent queries on the device (default 4) */
+    int64_t max_sources;    /* sources per query (default 100000) */
+    int32_t max_topk;       /* largest k a query may ask for (0 = 64) */
+    int64_t memory_budget;  /* device bytes for queries in flight (0 = a quarter of free memory) */
+    int64_t max_pending;    /* queries waiting for admission before ppr_submit returns PPR_EBUSY (0 = no limit) */
+    int32_t chunk_sources, large_degree, warps_per_block; /* walker tuning (0 = defaults) */
+} ppr_serve_cfg;
+
+typedef struct {
+    int64_t submit_ns, admit_ns, done_ns; /* steady-clock times of submission, admission, completion */
+    uint64_t walks;
+    int64_t sources;
+} ppr_query_stats;
+
+void ppr_serve_cfg_init(ppr_serve_cfg *cfg);
+
+/* Starts serving graph g (plain graphs) on the context; one server per context. */
+int ppr_serve_start(ppr_ctx *ctx, const ppr_graph *g, const ppr_serve_cfg *cfg);
+
+/* Stops serving: queries not yet admitted are cancelled (their poll fails with
+ * PPR_EINVAL); running queries finish first.  ppr_destroy stops it too. */
+int ppr_serve_stop(ppr_ctx *ctx);
+
+/*
+ * Queues a query for `ns` source ids (host memory, copied; each in [0, n)).
+ * Thread-safe.  *qid identifies it for ppr_poll.  Errors: PPR_EINVAL (bad
+ * arguments, serving not started), PPR_ERANGE (larger than the memory budget),
+ * PPR_EBUSY (max_pending reached, or stopping).
+ */
+int ppr_submit(ppr_ctx *ctx, const int32_t *srcs, int64_t ns, double alpha, uint32_t R, uint64_t seed, int32_t topk,
+               uint64_t *qid);
+
+/*
+ * Waits up to timeout_ms (< 0: no deadline) for query qid.  On success writes
+ * its top-k (ns * topk ids and counts, row i for srcs[i], as ppr_topk) into
+ * idx / cnt (host memory, either may be NULL), fills *stats if non-NULL, and
+ * forgets the query.  PPR_ETIMEOUT leaves it pending.  Thread-safe.
+ */
+int ppr_poll(ppr_ctx *ctx, uint64_t qid, int32_t *idx, uint32_t *cnt, int64_t timeout_ms, ppr_query_stats *stats);
+
 #ifdef __cplusplus
 }
 #endif

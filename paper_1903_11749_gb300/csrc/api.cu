@@ -153,7 +153,12 @@ int ppr_create(int device, ppr_ctx **out)
     return PPR_OK;
 }
 
-void ppr_destroy(ppr_ctx *ctx) { delete ctx; }
+void ppr_destroy(ppr_ctx *ctx)
+{
+    if (!ctx) return;
+    if (ctx->server) ppr_serve_stop(ctx);
+    delete ctx;
+}
 
 int ppr_device_sms(const ppr_ctx *ctx) { return ctx ? ctx->sms : 0; }
 

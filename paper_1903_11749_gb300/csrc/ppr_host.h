@@ -35,10 +35,15 @@ struct SegCache {
 
 }  // namespace ppr
 
+namespace ppr {
+struct Server;
+}
+
 struct ppr_ctx {
     int device = 0;
     int sms = 0;
     size_t smem_optin = 0;
+    ppr::Server *server = nullptr;  // serving state (ppr_serve_start)
 };
 
 struct ppr_graph {

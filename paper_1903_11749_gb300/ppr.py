@@ -47,6 +47,17 @@ class Tuning(C.Structure):
                 ("ms", C.c_float), ("candidates", C.c_int32), ("sample_sources", C.c_int64)]
 
 
+class ServeCfg(C.Structure):
+    _fields_ = [("streams", C.c_int32), ("max_sources", C.c_int64), ("max_topk", C.c_int32),
+                ("memory_budget", C.c_int64), ("max_pending", C.c_int64), ("chunk_sources", C.c_int32),
+                ("large_degree", C.c_int32), ("warps_per_block", C.c_int32)]
+
+
+class QueryStats(C.Structure):
+    _fields_ = [("submit_ns", C.c_int64), ("admit_ns", C.c_int64), ("done_ns", C.c_int64), ("walks", C.c_uint64),
+                ("sources", C.c_int64)]
+
+
 class ResultInfo(C.Structure):
     _fields_ = [("sources", C.c_int64), ("R", C.c_uint32), ("topk", C.c_int32), ("nnz", C.c_int64),
                 ("steps", C.c_uint64), ("walks", C.c_uint64), ("kernel_ms", C.c_float), ("sectors", C.c_uint64),
@@ -83,6 +94,12 @@ _SIGS = {
                                C.POINTER(C.c_void_p)]),
     "ppr_workspace_size": (C.c_int, [C.c_void_p, C.POINTER(RunArgs), C.POINTER(C.c_size_t)]),
     "ppr_autotune": (C.c_int, [C.c_void_p, C.c_void_p, C.POINTER(RunArgs), C.c_int64, C.POINTER(Tuning)]),
+    "ppr_serve_cfg_init": (None, [C.POINTER(ServeCfg)]),
+    "ppr_serve_start": (C.c_int, [C.c_void_p, C.c_void_p, C.POINTER(ServeCfg)]),
+    "ppr_serve_stop": (C.c_int, [C.c_void_p]),
+    "ppr_submit": (C.c_int, [C.c_void_p, C.c_void_p, C.c_int64, C.c_double, C.c_uint32, C.c_uint64, C.c_int32,
+                             C.POINTER(C.c_uint64)]),
+    "ppr_poll": (C.c_int, [C.c_void_p, C.c_uint64, C.c_void_p, C.c_void_p, C.c_int64, C.POINTER(QueryStats)]),
     "ppr_run_into": (C.c_int, [C.c_void_p, C.c_void_p, C.POINTER(RunArgs), C.c_void_p, C.c_size_t, C.c_void_p,
                                C.c_void_p, C.c_void_p, C.c_uint32, C.c_void_p, C.c_void_p]),
 }
@@ -156,6 +173,34 @@ class Context:
             self.close()
         except Exception:
             pass
+
+    # ---- serving
+    def serve_start(self, graph: "Graph", **cfg):
+        c = ServeCfg()
+        lib().ppr_serve_cfg_init(C.byref(c))
+        for k_, v in cfg.items():
+            setattr(c, k_, v)
+        _check(lib().ppr_serve_start(self.h, graph.h, C.byref(c)))
+        self._serving = graph
+
+    def serve_stop(self):
+        _check(lib().ppr_serve_stop(self.h))
+        self._serving = None
+
+    def submit(self, sources, alpha=0.15, R=100, seed=1, topk=32) -> int:
+        src = np.ascontiguousarray(sources, dtype=np.int32)
+        q = C.c_uint64()
+        _check(lib().ppr_submit(self.h, src.ctypes.data, len(src), alpha, R, seed, topk, C.byref(q)))
+        return q.value
+
+    def poll(self, qid: int, ns: int, topk: int, timeout_ms: int = -1):
+        """(idx int32[ns, topk], cnt uint32[ns, topk], stats dict) of a finished query."""
+        idx = np.zeros((ns, topk), dtype=np.int32)
+        cnt = np.zeros((ns, topk), dtype=np.uint32)
+        st = QueryStats()
+        _check(lib().ppr_poll(self.h, qid, idx.ctypes.data, cnt.ctypes.data, timeout_ms, C.byref(st)))
+        return idx, cnt, {"submit_ns": st.submit_ns, "admit_ns": st.admit_ns, "done_ns": st.done_ns,
+                          "walks": st.walks, "sources": st.sources}
 
     def load_graph(self, n, row_ptr, col, w, stream=None, m=None) -> "Graph":
         rp, dev = _ptr(row_ptr)

@@ -1,0 +1,102 @@
+"""Serving: multi-source queries admitted by continuous batching.
+
+Each query's top-k must be the same when it runs alone, when it runs in a
+mix of overlapping queries (tolerance 0: the counts are integers), and as a
+ppr_run_list of the same sources."""
+import threading
+
+import numpy as np
+import pytest
+
+from paper_1903_11749_gb300 import inputs as I
+
+pytestmark = pytest.mark.gpu
+
+
+@pytest.fixture(scope="module")
+def env():
+    from paper_1903_11749_gb300 import build as B
+    B.build()
+    from paper_1903_11749_gb300 import ppr
+    g = I.random_small_graph(6000, 60000, seed=51, wmax=50, dangling=60)
+    return ppr, g
+
+
+def _queries(n, count, seed, smax=3000):
+    rng = np.random.Generator(np.random.PCG64(seed))
+    sizes = np.floor(np.exp(rng.uniform(0, np.log(smax), count))).astype(int)
+    return [rng.choice(n, size=int(s), replace=False).astype(np.int32) for s in sizes]
+
+
+def test_alone_equals_mix_equals_run_list(env):
+    ppr, g = env
+    ctx = ppr.Context(0)
+    G = ctx.load_graph(g.n, g.row_ptr, g.col, g.w)
+    qs = _queries(g.n, 24, seed=1)
+    kw = dict(alpha=0.15, R=60, seed=7, topk=8)
+    ctx.serve_start(G, streams=3)
+    alone = []
+    for src in qs:
+        qid = ctx.submit(src, **kw)
+        alone.append(ctx.poll(qid, len(src), kw["topk"], timeout_ms=60000)[:2])
+    # the mix: two submitting threads, then poll everything
+    ids = [None] * len(qs)
+
+    def submitter(part):
+        for i in part:
+            ids[i] = ctx.submit(qs[i], **kw)
+
+    th = [threading.Thread(target=submitter, args=(range(k, len(qs), 2),)) for k in range(2)]
+    for t in th:
+        t.start()
+    for t in th:
+        t.join()
+    stats = []
+    for i, src in enumerate(qs):
+        idx, cnt, st = ctx.poll(ids[i], len(src), kw["topk"], timeout_ms=60000)
+        assert np.array_equal(idx, alone[i][0]) and np.array_equal(cnt, alone[i][1])
+        stats.append(st)
+    assert all(st["done_ns"] >= st["admit_ns"] >= st["submit_ns"] for st in stats)
+    # several queries were in flight at once
+    spans = sorted((st["admit_ns"], st["done_ns"]) for st in stats)
+    assert any(spans[i + 1][0] < spans[i][1] for i in range(len(spans) - 1))
+    ctx.serve_stop()
+    for i, src in enumerate(qs[:6]):
+        ref = G.run_list(src, alpha=kw["alpha"], R=kw["R"], seed=kw["seed"], topk=kw["topk"])
+        ridx, rcnt = ref.topk()
+        assert np.array_equal(ridx, alone[i][0]) and np.array_equal(rcnt, alone[i][1])
+
+
+def test_memory_admission_and_errors(env):
+    ppr, g = env
+    ctx = ppr.Context(0)
+    G = ctx.load_graph(g.n, g.row_ptr, g.col, g.w)
+    with pytest.raises(ppr.PPRError):
+        ctx.submit(np.arange(5, dtype=np.int32))  # not started
+    # a budget that fits one large query at a time: queries wait for memory
+    ctx.serve_start(G, streams=4, memory_budget=2 << 20, max_sources=4000)
+    qs = _queries(g.n, 10, seed=2, smax=3000)
+    kw = dict(alpha=0.2, R=40, seed=3, topk=5)
+    ids = [ctx.submit(s, **kw) for s in qs]
+    res = [ctx.poll(q, len(s), 5, timeout_ms=60000) for q, s in zip(ids, qs)]
+    for (idx, cnt, st), s in zip(res, qs):
+        ref = G.run_list(s, **kw)
+        assert np.array_equal(idx, ref.topk()[0]) and np.array_equal(cnt, ref.topk()[1])
+    with pytest.raises(ppr.PPRError):
+        ctx.submit(np.array([0, g.n], dtype=np.int32), **kw)  # source out of range
+    with pytest.raises(ppr.PPRError):
+        ctx.submit(np.arange(10, dtype=np.int32), alpha=0.0)
+    with pytest.raises(ppr.PPRError):
+        ctx.poll(123456789, 1, 5, timeout_ms=10)  # unknown query
+    big = np.arange(4000, dtype=np.int32)
+    q = ctx.submit(big, alpha=0.001, R=40, seed=1, topk=5)  # ~1000-step walks: still running after 0 ms
+    with pytest.raises(ppr.PPRError) as ei:
+        ctx.poll(q, len(big), 5, timeout_ms=0)
+    assert ei.value.code in (ppr.PPR_ETIMEOUT,)
+    ctx.poll(q, len(big), 5, timeout_ms=120000)
+    # stop with queries waiting: they are cancelled, running ones finish
+    for _ in range(6):
+        ctx.submit(big, **kw)
+    ctx.serve_stop()
+    with pytest.raises(ppr.PPRError):
+        ctx.poll(1, 1, 5, timeout_ms=10)
