@@ -74,7 +74,7 @@ def test_memory_admission_and_errors(env):
     with pytest.raises(ppr.PPRError):
         ctx.submit(np.arange(5, dtype=np.int32))  # not started
     # a budget that fits one large query at a time: queries wait for memory
-    ctx.serve_start(G, streams=4, memory_budget=2 << 20, max_sources=4000)
+    ctx.serve_start(G, streams=4, memory_budget=3 << 20, max_sources=4000)
     qs = _queries(g.n, 10, seed=2, smax=3000)
     kw = dict(alpha=0.2, R=40, seed=3, topk=5)
     ids = [ctx.submit(s, **kw) for s in qs]
@@ -88,6 +88,9 @@ def test_memory_admission_and_errors(env):
         ctx.submit(np.arange(10, dtype=np.int32), alpha=0.0)
     with pytest.raises(ppr.PPRError):
         ctx.poll(123456789, 1, 5, timeout_ms=10)  # unknown query
+    with pytest.raises(ppr.PPRError) as ei:
+        ctx.submit(np.arange(4000, dtype=np.int32), alpha=0.2, R=400, seed=1, topk=5)  # beyond the budget
+    assert ei.value.code == ppr.PPR_ERANGE
     big = np.arange(4000, dtype=np.int32)
     q = ctx.submit(big, alpha=0.001, R=40, seed=1, topk=5)  # ~1000-step walks: still running after 0 ms
     with pytest.raises(ppr.PPRError) as ei:
