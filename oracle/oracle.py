@@ -43,7 +43,8 @@ def build(force: bool = False) -> str:
 class _Graph(C.Structure):
     _fields_ = [("n", C.c_int64), ("row_ptr", C.c_void_p), ("col", C.c_void_p), ("P", C.c_void_p),
                 ("W", C.c_void_p), ("seg_off", C.c_void_p), ("seg_node", C.c_void_p),
-                ("seg_mark_len", C.c_void_p), ("seg_cum", C.c_void_p), ("w", C.c_void_p), ("lazy", C.c_void_p)]
+                ("seg_mark_len", C.c_void_p), ("seg_cum", C.c_void_p), ("w", C.c_void_p), ("lazy", C.c_void_p),
+                ("alias_thr", C.c_void_p), ("alias_idx", C.c_void_p)]
 
 
 class _Params(C.Structure):
@@ -76,6 +77,12 @@ def lib():
         L.ppr_oracle_lazy_new.argtypes = [C.c_int64]
         L.ppr_oracle_lazy_new.restype = C.c_void_p
         L.ppr_oracle_lazy_free.argtypes = [C.c_void_p]
+        L.ppr_oracle_alias_table.argtypes = [C.c_void_p, C.c_int64, C.c_void_p, C.c_void_p]
+        L.ppr_oracle_alias_table.restype = C.c_int
+        L.ppr_oracle_alias_pick.argtypes = [C.c_void_p, C.c_void_p, C.c_int64, C.c_uint64, C.c_uint64]
+        L.ppr_oracle_alias_pick.restype = C.c_int64
+        L.ppr_oracle_alias_tables.argtypes = [C.c_int64, C.c_void_p, C.c_void_p, C.c_void_p, C.c_void_p]
+        L.ppr_oracle_alias_tables.restype = C.c_int
         _lib = L
     return _lib
 
@@ -132,6 +139,8 @@ class OracleGraph:
     seg_weight: np.ndarray | None = None
     seg_cum: np.ndarray | None = None
     lazy: object = None  # on-demand segment tables (large graphs)
+    alias_thr: np.ndarray | None = None
+    alias_idx: np.ndarray | None = None
 
     def __del__(self):
         if self.lazy:
@@ -177,8 +186,34 @@ def build_segments(g: OracleGraph, T: int) -> OracleGraph:
     return g
 
 
+def alias_table(weights):
+    """Integer alias table of one row: (thr uint64[d], alias int64[d]) as Algorithm 1."""
+    w = np.ascontiguousarray(weights, dtype=np.uint32)
+    thr = np.zeros(len(w), dtype=np.uint64)
+    ali = np.zeros(len(w), dtype=np.int64)
+    if lib().ppr_oracle_alias_table(_p(w), len(w), _p(thr), _p(ali)) != 0:
+        raise MemoryError
+    return thr, ali
+
+
+def alias_pick(thr, ali, W: int, r: int) -> int:
+    thr = np.ascontiguousarray(thr, dtype=np.uint64)
+    ali = np.ascontiguousarray(ali, dtype=np.int64)
+    return int(lib().ppr_oracle_alias_pick(_p(thr), _p(ali), len(thr), W, r))
+
+
+def build_alias(g: OracleGraph) -> OracleGraph:
+    m = int(g.row_ptr[-1])
+    g.alias_thr = np.zeros(max(m, 1), dtype=np.uint64)
+    g.alias_idx = np.zeros(max(m, 1), dtype=np.int64)
+    if lib().ppr_oracle_alias_tables(g.n, _p(g.row_ptr), _p(g.w), _p(g.alias_thr), _p(g.alias_idx)) != 0:
+        raise MemoryError
+    return g
+
+
 def walks(g: OracleGraph, alpha: float, R: int, seed: int, s_begin: int = 0, s_end: int | None = None,
-          tag: int = 0, dangling: int = 0, segments: bool = False, lazy_segments: bool = False):
+          tag: int = 0, dangling: int = 0, segments: bool = False, lazy_segments: bool = False,
+          sampler: int = 0):
     """Endpoints uint32[S, R] and the number of draws consumed.  With
     lazy_segments, segment tables are built only for the nodes the walks
     visit (same tables; for sampled runs on large graphs)."""
@@ -187,6 +222,8 @@ def walks(g: OracleGraph, alpha: float, R: int, seed: int, s_begin: int = 0, s_e
     T = threshold(alpha)
     if T == 0:
         raise ValueError("alpha must satisfy floor(alpha * 2^32) >= 1 and alpha < 1")
+    if sampler == 1 and g.alias_thr is None:
+        build_alias(g)
     use_lazy = segments and lazy_segments
     if use_lazy and not g.lazy:
         g.lazy = lib().ppr_oracle_lazy_new(g.n)
@@ -201,7 +238,9 @@ def walks(g: OracleGraph, alpha: float, R: int, seed: int, s_begin: int = 0, s_e
                 g.seg_node.ctypes.data if flat else None,
                 g.seg_mark_len.ctypes.data if flat else None,
                 g.seg_cum.ctypes.data if flat else None,
-                g.w.ctypes.data, g.lazy if use_lazy else None)
+                g.w.ctypes.data, g.lazy if use_lazy else None,
+                g.alias_thr.ctypes.data if sampler == 1 else None,
+                g.alias_idx.ctypes.data if sampler == 1 else None)
     pr = _Params(T, R, seed, s_begin, s_end, 0, tag, dangling)
     if S > 0 and R > 0:
         rc = lib().ppr_oracle_walks(C.byref(gr), C.byref(pr), _p(ends), _p(steps))

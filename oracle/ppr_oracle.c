@@ -144,6 +144,82 @@ int64_t ppr_oracle_pick(const uint64_t *P, int64_t lo, int64_t hi, uint64_t x)
 }
 
 /* ------------------------------------------------------------------------ */
+/* Alias method (Algorithm 1) in integers.  For a row of d edges with         */
+/* weights w_e and total W, the switch probability p(e) = d * r(e) of the     */
+/* paper becomes the integer p_e = d * w_e out of a slot capacity of W (so    */
+/* sum_e p_e = d * W exactly).  S^l holds the e with p_e > W, S^s those with   */
+/* p_e < W, both in ascending edge order; each round takes the first x of S^s */
+/* and the first y of S^l ("select any" read as "the first"), sets a(x) = y,  */
+/* keeps thr(x) = p_x, and lowers p_y by W - p_x; y leaves S^l once p_y <= W  */
+/* and joins the end of S^s if p_y < W.  Edges never small keep thr = W and   */
+/* a(e) = e.  Selection with one 64-bit draw r: slot j = floor(r*d/2^64),      */
+/* y = floor(((r*d) mod 2^64) * W / 2^64); the edge is j if y < thr(j), else   */
+/* a(j).  Edge e is chosen for exactly (d * w_e) of the d * W (j, y) pairs.    */
+/* ------------------------------------------------------------------------ */
+
+/* thr/alias: d entries each (alias as an index within the row).  Work space
+ * of 2*d int64 is allocated here. */
+int ppr_oracle_alias_table(const uint32_t *w, int64_t d, uint64_t *thr, int64_t *alias)
+{
+    uint64_t W = 0;
+    for (int64_t e = 0; e < d; ++e)
+        W += w[e];
+    int64_t *small = (int64_t *)malloc(sizeof(int64_t) * (size_t)(d > 0 ? d : 1));
+    int64_t *large = (int64_t *)malloc(sizeof(int64_t) * (size_t)(d > 0 ? d : 1));
+    if (!small || !large) {
+        free(small);
+        free(large);
+        return -1;
+    }
+    int64_t s_head = 0, s_tail = 0, l_head = 0, l_tail = 0;
+    for (int64_t e = 0; e < d; ++e) {
+        thr[e] = (uint64_t)d * w[e];
+        alias[e] = e;
+        if (thr[e] < W)
+            small[s_tail++] = e;
+        else if (thr[e] > W)
+            large[l_tail++] = e;
+    }
+    while (l_head < l_tail) {
+        int64_t x = small[s_head++];
+        int64_t y = large[l_head];
+        alias[x] = y;
+        thr[y] -= W - thr[x];
+        if (thr[y] <= W) {
+            ++l_head;
+            if (thr[y] < W)
+                small[s_tail++] = y;
+        }
+    }
+    free(small);
+    free(large);
+    return 0;
+}
+
+/* Index (within the row) the alias rule selects for draw r. */
+int64_t ppr_oracle_alias_pick(const uint64_t *thr, const int64_t *alias, int64_t d, uint64_t W, uint64_t r)
+{
+    unsigned __int128 t = (unsigned __int128)r * (uint64_t)d;
+    int64_t j = (int64_t)(uint64_t)(t >> 64);
+    uint64_t frac = (uint64_t)t;
+    uint64_t y = ppr_oracle_mulhi64(frac, W);
+    return y < thr[j] ? j : alias[j];
+}
+
+/* Alias tables of every row: thr[e], alias[e] (index within e's row). */
+int ppr_oracle_alias_tables(int64_t n, const int64_t *row_ptr, const uint32_t *w, uint64_t *thr, int64_t *alias)
+{
+    for (int64_t u = 0; u < n; ++u) {
+        int64_t a = row_ptr[u], d = row_ptr[u + 1] - a;
+        if (d == 0)
+            continue;
+        if (ppr_oracle_alias_table(w + a, d, thr + a, alias + a) != 0)
+            return -1;
+    }
+    return 0;
+}
+
+/* ------------------------------------------------------------------------ */
 /* Segment tables: Algorithm 4 ("big moves") with the loop fixed at depth 3   */
 /* for nodes of out-degree 1..8.                                              */
 /*                                                                            */
@@ -375,6 +451,8 @@ typedef struct {
     const uint64_t *seg_cum; /* inclusive prefix of outcome weights within each table */
     const uint32_t *w;       /* edge weights (lazy segment tables) */
     void *lazy;              /* lazy_segments, or NULL */
+    const uint64_t *alias_thr;   /* alias sampler (NULL: first-prefix-above rule) */
+    const int64_t *alias_idx;
 } oracle_graph;
 
 /* Outcome table of v: returns its length (0 if v has none) and its arrays. */
@@ -478,6 +556,9 @@ int ppr_oracle_walks(const oracle_graph *g, const oracle_params *p, uint32_t *en
                 uint32_t next;
                 if (hi == lo) {
                     next = (uint32_t)s;
+                } else if (g->alias_thr) {
+                    int64_t j = ppr_oracle_alias_pick(g->alias_thr + lo, g->alias_idx + lo, hi - lo, g->W[u], r64);
+                    next = (uint32_t)g->col[lo + j];
                 } else {
                     uint64_t xp = ppr_oracle_mulhi64(r64, g->W[u]);
                     int64_t e = ppr_oracle_pick(g->P, lo, hi, xp);

@@ -358,3 +358,69 @@ def test_lazy_segment_tables_equal_full_tables(oracle):
         e1, s1 = oracle.walks(og, alpha, 50, 3, dangling=mode, segments=True)
         e2, s2 = oracle.walks(og, alpha, 50, 3, dangling=mode, segments=True, lazy_segments=True)
         assert np.array_equal(e1, e2) and s1 == s2
+
+
+# ------------------------------------------------------------- alias rule ----
+
+def _golden_example2():
+    rows = []
+    with open(os.path.join(GOLDEN, "example2_alias.txt")) as f:
+        for line in f:
+            if line.strip() and not line.startswith("#"):
+                e, p, a = line.split()
+                rows.append((int(e[1:]) - 1, Fraction(p), int(a[1:]) - 1))
+    return rows
+
+
+def test_example2_alias_setup_exact(oracle):
+    """Sec. 2.2 Example 2: weights in ratio 2:3:3 give switch probabilities
+    (0.75, 0.875, 1) and aliases (e2, e3, e3), exactly (thr / W)."""
+    for scale in (1, 7):
+        w = np.array([2, 3, 3]) * scale
+        thr, ali = oracle.alias_table(w)
+        W = int(w.sum())
+        for e, p, a in _golden_example2():
+            assert Fraction(int(thr[e]), W) == p
+            assert int(ali[e]) == a
+
+
+@pytest.mark.parametrize("weights", [[1], [3, 1], [2, 3, 3], [5, 1, 7, 1, 1, 9], [1000, 1, 1], [4, 4, 4, 4],
+                                     [1, 2, 3, 4, 5, 6, 7, 8, 9]])
+def test_alias_rule_realises_routing_probability_exactly(oracle, weights):
+    """Over all d * W (slot, y) pairs, edge e is chosen exactly d * w_e times:
+    the selection law is r(e) = w_e / W exactly (Sec. 2.2)."""
+    w = np.asarray(weights, dtype=np.uint64)
+    d, W = len(w), int(w.sum())
+    thr, ali = oracle.alias_table(w)
+    hits = np.zeros(d, dtype=np.int64)
+    for j in range(d):
+        for y in range(W):
+            hits[j if y < int(thr[j]) else int(ali[j])] += 1
+    assert hits.tolist() == [d * int(x) for x in w]
+    assert all(0 <= int(t) <= W for t in thr)
+
+
+def test_alias_pick_uses_slot_and_fraction(oracle):
+    """alias_pick with draw r equals the rule computed with exact integers."""
+    rng = np.random.Generator(np.random.PCG64(12))
+    w = rng.integers(1, 1000, 37).astype(np.uint64)
+    thr, ali = oracle.alias_table(w)
+    W = int(w.sum())
+    for _ in range(3000):
+        r = int(rng.integers(0, 2**64, dtype=np.uint64))
+        j, frac = divmod(r * len(w), 2**64)
+        y = (frac * W) >> 64
+        want = j if y < int(thr[j]) else int(ali[j])
+        assert oracle.alias_pick(thr, ali, W, r) == want
+
+
+@pytest.mark.parametrize("mode", [0, 1])
+def test_alias_sampler_law_matches_exact_pi(oracle, mode):
+    g = _small_graphs()[0]
+    alpha = 0.3
+    T = oracle.threshold(alpha)
+    pi = X.exact_pi(g.n, g.row_ptr, g.col, g.w, T, mode)
+    og = oracle.prepare(g.n, g.row_ptr, g.col, g.w)
+    R = 40000
+    ends, _ = oracle.walks(og, alpha, R, seed=15, dangling=mode, sampler=1)
+    _check_counts(ends, pi, R)
