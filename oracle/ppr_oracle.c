@@ -148,17 +148,20 @@ int64_t ppr_oracle_pick(const uint64_t *P, int64_t lo, int64_t hi, uint64_t x)
 /* weights w_e and total W, the switch probability p(e) = d * r(e) of the     */
 /* paper becomes the integer p_e = d * w_e out of a slot capacity of W (so    */
 /* sum_e p_e = d * W exactly).  S^l holds the e with p_e > W, S^s those with   */
-/* p_e < W, both in ascending edge order; each round takes the first x of S^s */
-/* and the first y of S^l ("select any" read as "the first"), sets a(x) = y,  */
-/* keeps thr(x) = p_x, and lowers p_y by W - p_x; y leaves S^l once p_y <= W  */
-/* and joins the end of S^s if p_y < W.  Edges never small keep thr = W and   */
-/* a(e) = e.  Selection with one 64-bit draw r: slot j = floor(r*d/2^64),      */
-/* y = floor(((r*d) mod 2^64) * W / 2^64); the edge is j if y < thr(j), else   */
-/* a(j).  Edge e is chosen for exactly (d * w_e) of the d * W (j, y) pairs.    */
+/* p_e < W.  Algorithm 1 lets each round take any x of S^s and any y of S^l;  */
+/* here y is always the first element of S^l in ascending edge order, and x   */
+/* is the element that joined S^s in the previous round if there is one,     */
+/* else the first not yet processed element of the initial S^s in ascending   */
+/* order.  Each round sets a(x) = y, keeps thr(x) = p_x and lowers p_y by      */
+/* W - p_x; y leaves S^l once p_y <= W and joins S^s if p_y < W.  Edges that  */
+/* are never in S^s keep thr = W and a(e) = e.  Selection with one 64-bit     */
+/* draw r: slot j = floor(r*d/2^64), y = floor(((r*d) mod 2^64) * W / 2^64);  */
+/* the edge is j if y < thr(j), else a(j).  Edge e is chosen for exactly      */
+/* d * w_e of the d * W (j, y) pairs.                                         */
 /* ------------------------------------------------------------------------ */
 
 /* thr/alias: d entries each (alias as an index within the row).  Work space
- * of 2*d int64 is allocated here. */
+ * of d int64 is allocated here. */
 int ppr_oracle_alias_table(const uint32_t *w, int64_t d, uint64_t *thr, int64_t *alias)
 {
     uint64_t W = 0;
@@ -171,24 +174,36 @@ int ppr_oracle_alias_table(const uint32_t *w, int64_t d, uint64_t *thr, int64_t 
         free(large);
         return -1;
     }
-    int64_t s_head = 0, s_tail = 0, l_head = 0, l_tail = 0;
+    int64_t n_small = 0, n_large = 0;
     for (int64_t e = 0; e < d; ++e) {
         thr[e] = (uint64_t)d * w[e];
         alias[e] = e;
         if (thr[e] < W)
-            small[s_tail++] = e;
+            small[n_small++] = e;
         else if (thr[e] > W)
-            large[l_tail++] = e;
+            large[n_large++] = e;
     }
-    while (l_head < l_tail) {
-        int64_t x = small[s_head++];
-        int64_t y = large[l_head];
+    int64_t next_small = 0, first_large = 0;
+    int64_t rejoined = -1; /* the element that joined S^s in the previous round */
+    while (first_large < n_large) {
+        int64_t x;
+        if (rejoined >= 0) {
+            x = rejoined;
+            rejoined = -1;
+        } else if (next_small < n_small) {
+            x = small[next_small++];
+        } else { /* unreachable: the sum of p is d * W exactly */
+            free(small);
+            free(large);
+            return -2;
+        }
+        int64_t y = large[first_large];
         alias[x] = y;
         thr[y] -= W - thr[x];
         if (thr[y] <= W) {
-            ++l_head;
+            ++first_large;
             if (thr[y] < W)
-                small[s_tail++] = y;
+                rejoined = y;
         }
     }
     free(small);

@@ -384,6 +384,58 @@ def test_example2_alias_setup_exact(oracle):
             assert int(ali[e]) == a
 
 
+def test_alias_pairing_order_worked_by_hand(oracle):
+    """The pairing order Algorithm 1 leaves open (any x of S^s, any y of S^l),
+    fixed as: y the first of S^l, x the element that just joined S^s, else the
+    next initial small one.  Weights (1,1,2,2,2): d = 5, W = 8, p = (5,5,10,10,10).
+    Round 1: x=e1, y=e3 -> a(e1)=e3, p(e3) = 10-3 = 7 < 8, e3 joins S^s.
+    Round 2: x=e3, y=e4 -> a(e3)=e4, p(e4) = 10-1 = 9.
+    Round 3: x=e2, y=e4 -> a(e2)=e4, p(e4) = 9-3 = 6 < 8, e4 joins S^s.
+    Round 4: x=e4, y=e5 -> a(e4)=e5, p(e5) = 10-2 = 8, S^l empty.
+    (A first-in first-out S^s would pair e3 with e5 instead.)"""
+    thr, ali = oracle.alias_table(np.array([1, 1, 2, 2, 2]))
+    assert [int(t) for t in thr] == [5, 5, 7, 6, 8]
+    assert [int(a) for a in ali][:4] == [2, 3, 3, 4]
+
+
+@pytest.mark.parametrize("seed", range(6))
+def test_alias_table_equals_prefix_sum_closed_form(oracle, seed):
+    """With that order the table has a closed form in prefix sums: for the
+    small edges (p < W, ascending) let D_i be the running sum of W - p, for the
+    large ones (p > W, ascending) E_j the running sum of p - W.  Small edge i
+    takes thr = p and the alias of the first large j with E_j > D_(i-1);
+    large edge j (not the last) takes thr = W - (D_q - E_j) for the first q
+    with D_q >= E_j and the alias of large j+1; the last large edge and the
+    edges with p = W keep thr = W."""
+    rng = np.random.Generator(np.random.PCG64(seed))
+    d = int(rng.integers(2, 300))
+    w = (I.zipf_weights(rng, d, s=1.1, wmax=10_000) if seed % 2 else rng.integers(1, 50, d)).astype(np.uint64)
+    if seed == 5:
+        w[:] = 7  # every p equals W
+    W = int(w.sum())
+    p = [d * int(x) for x in w]
+    small = [e for e in range(d) if p[e] < W]
+    large = [e for e in range(d) if p[e] > W]
+    D = np.cumsum([W - p[e] for e in small]).tolist()
+    E = np.cumsum([p[e] - W for e in large]).tolist()
+    thr, ali = oracle.alias_table(w)
+    want_thr = [W] * d
+    want_ali = {}
+    for i, e in enumerate(small):
+        prev = D[i - 1] if i else 0
+        j = next(j for j in range(len(large)) if E[j] > prev)
+        want_thr[e] = p[e]
+        want_ali[e] = large[j]
+    for j, e in enumerate(large[:-1]):
+        q = next(q for q in range(len(small)) if D[q] >= E[j])
+        want_thr[e] = W - (D[q] - E[j])
+        want_ali[e] = large[j + 1]
+    assert [int(t) for t in thr] == want_thr
+    for e, a in want_ali.items():
+        if want_thr[e] < W:
+            assert int(ali[e]) == a
+
+
 @pytest.mark.parametrize("weights", [[1], [3, 1], [2, 3, 3], [5, 1, 7, 1, 1, 9], [1000, 1, 1], [4, 4, 4, 4],
                                      [1, 2, 3, 4, 5, 6, 7, 8, 9]])
 def test_alias_rule_realises_routing_probability_exactly(oracle, weights):
