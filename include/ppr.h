@@ -79,6 +79,20 @@ int ppr_version(void);
  * threshold), or 0 if alpha is not in (0,1) or T would be 0.  Needs no GPU. */
 uint32_t ppr_alpha_threshold(double alpha);
 
+/* Walks per source for Definition 1 (fully approximate PPR): the smallest
+ * omega with
+ *     omega >= (2 + 2*eps/3) * ln(2 / p_f) / (eps^2 * delta),
+ * so that every pi(s,t) >= delta is estimated within eps * pi(s,t) with
+ * probability at least 1 - p_f.  The paper fixes omega only up to a constant,
+ * Omega(log(1/p_f) / (eps^2 delta)) (Sec. 2.1); the constant here is the
+ * two-sided Bernstein bound P(|X - mu| >= eps mu) <= 2 exp(-eps^2 mu / (2 + 2 eps/3))
+ * for X a sum of omega independent indicators with mean mu = omega * pi >=
+ * omega * delta.  Needs no GPU.  PPR_EINVAL unless eps > 0, 0 < delta <= 1,
+ * 0 < p_f < 1; PPR_ERANGE if omega >= 2^53.  An omega above PPR_MAX_R is
+ * reached by summing the rows of runs that differ only in their tag (the tag
+ * is a Philox counter word, so the runs' walks are independent). */
+int ppr_walks_for_accuracy(double eps, double delta, double p_f, uint64_t *omega);
+
 /* Message describing the last failure on the calling thread ("" if none).
  * Owned by the library; valid until the next call on this thread. */
 const char *ppr_last_error(void);
@@ -166,6 +180,12 @@ typedef struct {
     int64_t max_batch_sources;/* sources per device batch, 0 = sized to free device memory */
     int32_t stats;       /* 1: also count the algorithmic 32-byte sectors of every step (slower;
                             rows, counts and steps are unchanged) */
+    int32_t sampler;     /* neighbour choice: 0 = first prefix above floor(r*W/2^64) (default);
+                            1 = integer alias method (Algorithm 1): slot j = floor(r*d/2^64),
+                            y = floor(((r*d) mod 2^64) * W / 2^64), edge j if y < thr(j) else
+                            its alias.  Same law, different counts.  Alias tables are built on
+                            the first run that asks for them (every row total < 2^32; no
+                            segment mode) */
     void *stream;        /* cudaStream_t, NULL = legacy default stream */
 } ppr_run_args;
 

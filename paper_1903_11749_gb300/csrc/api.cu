@@ -110,6 +110,21 @@ uint32_t ppr_alpha_threshold(double alpha)
     return (uint32_t)t;
 }
 
+int ppr_walks_for_accuracy(double eps, double delta, double p_f, uint64_t *omega)
+{
+    if (!omega || !(eps > 0.0) || !(delta > 0.0) || !(delta <= 1.0) || !(p_f > 0.0) || !(p_f < 1.0)) {
+        set_error("need eps > 0, 0 < delta <= 1, 0 < p_f < 1 and an output pointer");
+        return PPR_EINVAL;
+    }
+    const double w = (2.0 + 2.0 * eps / 3.0) * std::log(2.0 / p_f) / (eps * eps * delta);
+    if (!(w < 9007199254740992.0)) {
+        set_error("omega = %g is beyond 2^53", w);
+        return PPR_ERANGE;
+    }
+    *omega = (uint64_t)std::ceil(w);
+    return PPR_OK;
+}
+
 const char *ppr_last_error(void) { return g_err; }
 
 int64_t ppr_kernel_launches(void) { return (int64_t)g_launches.load(); }
@@ -271,6 +286,8 @@ void ppr_free_graph(ppr_graph *g)
     dev_free(g->seg.node, g->stream);
     dev_free(g->seg.entries, g->stream);
     dev_free(g->d_node_off, g->stream);
+    dev_free(g->alias.node, g->stream);
+    dev_free(g->alias.slots, g->stream);
     delete g;
 }
 
@@ -335,9 +352,13 @@ static int check_run(const ppr_graph *g, const ppr_run_args *a, int64_t count, b
     if ((a->dangling != 0 && a->dangling != 1) || (a->segments != 0 && a->segments != 1) ||
         (a->kernel != PPR_KERNEL_PERSISTENT && a->kernel != PPR_KERNEL_PLAIN) || a->large_degree < 0 ||
         a->warps_per_block < 0 || a->warps_per_block > 32 || a->chunk_sources < 0 || a->max_batch_sources < 0 ||
-        (a->stats != 0 && a->stats != 1)) {
+        (a->stats != 0 && a->stats != 1) || (a->sampler != 0 && a->sampler != 1)) {
         set_error("invalid mode or tuning argument");
         return PPR_EINVAL;
+    }
+    if (a->sampler == 1 && a->segments) {
+        set_error("segment tables run with the prefix sampler only");
+        return PPR_ENOTSUP;
     }
     if (g->instances > 0 && a->tag != 0) {
         set_error("batched graphs use the instance id as tag; tag must be 0");
@@ -363,7 +384,17 @@ static int check_run(const ppr_graph *g, const ppr_run_args *a, int64_t count, b
     plan->warps_per_block = a->warps_per_block;
     plan->chunk_sources = a->chunk_sources;
     plan->stats = a->stats != 0;
+    plan->sampler = a->sampler;
     return PPR_OK;
+}
+
+// Device tables a run needs beyond the base layout (built once per graph).
+static int prepare_tables(const ppr_graph *g, const RunPlan &plan, cudaStream_t st)
+{
+    int rc = PPR_OK;
+    if (plan.segments) rc = build_segments(const_cast<ppr_graph *>(g), plan.T, st);
+    if (!rc && plan.sampler == 1) rc = build_alias(const_cast<ppr_graph *>(g), st);
+    return rc;
 }
 
 static uint32_t row_capacity(const ppr_graph *g, uint32_t R)
@@ -394,10 +425,7 @@ static int run_common(ppr_ctx *ctx, const ppr_graph *g, const ppr_run_args *a, c
     rc = set_device(ctx);
     if (rc) return rc;
     cudaStream_t st = (cudaStream_t)a->stream;
-    if (a->segments) {
-        rc = build_segments(const_cast<ppr_graph *>(g), plan.T, st);
-        if (rc) return rc;
-    }
+    if ((rc = prepare_tables(g, plan, st))) return rc;
     ppr_result *r = new (std::nothrow) ppr_result;
     if (!r) return PPR_ENOMEM;
     r->ctx = ctx;
@@ -522,6 +550,10 @@ int ppr_run_into(ppr_ctx *ctx, const ppr_graph *g, const ppr_run_args *a, void *
         set_error("segment tables for this alpha are not built (a ppr_run with segments=1 builds them)");
         return PPR_ENOTSUP;
     }
+    if (a->sampler == 1 && !g->alias.node) {
+        set_error("alias tables are not built (a ppr_run with sampler=1 builds them)");
+        return PPR_ENOTSUP;
+    }
     if (cap < row_capacity(g, a->R)) {
         set_error("row capacity %u < min(R, n) = %u", cap, row_capacity(g, a->R));
         return PPR_EINVAL;
@@ -554,7 +586,7 @@ int ppr_autotune(ppr_ctx *ctx, const ppr_graph *g, const ppr_run_args *a, int64_
     if (rc) return rc;
     if ((rc = set_device(ctx))) return rc;
     cudaStream_t st = (cudaStream_t)a->stream;
-    if (a->segments && (rc = build_segments(const_cast<ppr_graph *>(g), plan.T, st))) return rc;
+    if ((rc = prepare_tables(g, plan, st))) return rc;
     const int64_t S_all = a->src_end - a->src_begin;
     const int64_t S = std::max<int64_t>(1, std::min<int64_t>(S_all, sample_sources > 0 ? sample_sources : 65536));
     // batched graphs keep their instance structure: tune on a contiguous range

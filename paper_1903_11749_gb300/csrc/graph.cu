@@ -920,4 +920,337 @@ int build_segments(ppr_graph *g, uint32_t T, cudaStream_t st)
     return PPR_OK;
 }
 
+// --------------------------------------------------------- alias tables ----
+// Integer Algorithm 1 per row: p_e = d * w_e against a slot capacity of W.
+// The pairing order (free in Algorithm 1): y is the first edge of S^l in
+// ascending order; x is the edge that has just dropped into S^s if there is
+// one, else the next edge of the initial S^s in ascending order.  In that
+// order the whole table is a closed form of two running sums -- D_i over the
+// small edges of W - p, E_j over the large edges of p - W:
+//   small edge i: thr = p, alias = large edge min{j : E_j > D_(i-1)}
+//   large edge j (not the last): thr = W - (D_q - E_j) with q = min{q : D_q >= E_j},
+//                                alias = large edge j + 1
+//   last large edge, edges with p = W: thr = W, alias = itself.
+// Rows of at most 32 edges run the pairing rounds serially, one thread per
+// row; longer rows compute the closed form with a warp (up to 2048 edges) or
+// a block per row (alias_row_group).
+
+constexpr uint32_t kAliasSmall = 32, kAliasMid = 2048;
+
+struct AliasArgs {
+    int64_t n;
+    const NodeRec *node;
+    const EdgeN *edges;
+    const uint64_t *off;  // first slot of each row (exclusive scan of degrees)
+    NodeRec *anode;
+    AliasRec *slots;
+    uint32_t *idx;        // per slot of a long row: small edges from the front, large from the back
+    uint64_t *sum;        // their running sums D_i / E_j
+    uint32_t *list;       // long rows: warp rows from the front, block rows from the back
+    uint32_t *counts;     // [0] warp rows, [1] block rows
+};
+
+__device__ __forceinline__ uint32_t row_degree(const NodeRec &r) { return (uint32_t)(r.word0 >> 40) & kCountMask; }
+
+__global__ void __launch_bounds__(256) k_alias_small(AliasArgs A)
+{
+    for (int64_t u = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; u < A.n; u += (int64_t)gridDim.x * blockDim.x) {
+        const NodeRec nr = A.node[u];
+        const uint32_t d = row_degree(nr);
+        const uint64_t o = A.off[u];
+        NodeRec r;
+        r.word0 = pack_word0(o, d, false);
+        r.total = d < 2 ? nr.total : (nr.total & 0xffffffffull);  // 0, the single target, or W
+        A.anode[u] = r;
+        if (d < 2) continue;
+        if (d > kAliasSmall) {
+            if (d <= kAliasMid) A.list[atomicAdd(&A.counts[0], 1u)] = (uint32_t)u;
+            else A.list[A.n - 1 - atomicAdd(&A.counts[1], 1u)] = (uint32_t)u;
+            continue;
+        }
+        const uint64_t W = nr.total & 0xffffffffull;
+        const uint64_t eb = NarrowEdges::edge_base(nr.word0 & kBeginMask, d);
+        auto pw = [&](uint32_t i) -> uint64_t {
+            const uint32_t hi = A.edges[eb + i].P, lo = i ? A.edges[eb + i - 1].P : 0u;
+            return (uint64_t)d * (hi - lo);
+        };
+        for (uint32_t i = 0; i < d; ++i) {
+            const int32_t c = A.edges[eb + i].col;
+            A.slots[o + i] = AliasRec{(uint32_t)W, c, c, 0u};
+        }
+        auto next_small = [&](uint32_t i) { while (i < d && pw(i) >= W) ++i; return i; };
+        auto next_large = [&](uint32_t j) { while (j < d && pw(j) <= W) ++j; return j; };
+        uint32_t i = next_small(0), j = next_large(0);
+        if (j >= d) continue;
+        uint64_t py = pw(j);  // remaining p of the current large edge
+        for (uint32_t guard = 0; guard < 2 * d; ++guard) {
+            if (py > W) {  // x = next small edge, y = j
+                if (i >= d) break;
+                const uint64_t px = pw(i);
+                A.slots[o + i].thr = (uint32_t)px;
+                A.slots[o + i].alias_col = A.edges[eb + j].col;
+                py -= W - px;
+                i = next_small(i + 1);
+            } else {  // j leaves S^l; if it dropped below W it is the next x
+                const uint32_t j2 = next_large(j + 1);
+                if (j2 >= d) break;  // py == W here: the last large edge
+                if (py < W) {
+                    A.slots[o + j].thr = (uint32_t)py;
+                    A.slots[o + j].alias_col = A.edges[eb + j2].col;
+                }
+                py = pw(j2) - (W - py);
+                j = j2;
+            }
+        }
+    }
+}
+
+// Inclusive scan of three u64 values over a warp (NT = 32) or a block; `tot`
+// receives the group totals.  Block form: s holds 3 * (NT / 32) words.
+template <int NT>
+__device__ __forceinline__ void group_scan3(uint64_t v[3], uint64_t tot[3], uint64_t *s)
+{
+    const uint32_t lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
+#pragma unroll
+    for (int k = 0; k < 3; ++k) {
+#pragma unroll
+        for (int o = 1; o < 32; o <<= 1) {
+            const uint64_t y = __shfl_up_sync(0xffffffffu, v[k], o);
+            if (lane >= o) v[k] += y;
+        }
+    }
+    if constexpr (NT == 32) {
+#pragma unroll
+        for (int k = 0; k < 3; ++k) tot[k] = __shfl_sync(0xffffffffu, v[k], 31);
+    } else {
+        constexpr int NW = NT / 32;
+        if (lane == 31)
+            for (int k = 0; k < 3; ++k) s[k * NW + wid] = v[k];
+        __syncthreads();
+#pragma unroll
+        for (int k = 0; k < 3; ++k) {
+            uint64_t before = 0, all = 0;
+            for (int q = 0; q < NW; ++q) {
+                const uint64_t t = s[k * NW + q];
+                before += q < (int)wid ? t : 0ull;
+                all += t;
+            }
+            v[k] += before;
+            tot[k] = all;
+        }
+        __syncthreads();
+    }
+}
+
+template <int NT>
+__device__ __forceinline__ void group_sync()
+{
+    if constexpr (NT == 32) __syncwarp();
+    else __syncthreads();
+}
+
+// Closed-form alias table of one row of d > 32 edges by a group of NT threads
+// (rank = thread index within the group).  Each thread owns a contiguous run
+// of about d / NT edges: it totals its run, one group scan gives the run's
+// starting ranks and sums, and a second walk over the run writes the small
+// and large edges with their running sums to scratch.  The partners are then
+// a merge of the two sorted sequences D and E: each thread takes a contiguous
+// share of the small (and of the large) edges, finds its first partner by
+// bisection and advances linearly from there.
+template <int NT>
+__device__ void alias_row_group(const AliasArgs &A, int64_t u, uint32_t rank, uint64_t *s)
+{
+    const NodeRec nr = A.node[u];
+    const uint32_t d = row_degree(nr);
+    const uint64_t o = A.off[u];
+    const uint64_t W = nr.total & 0xffffffffull;
+    const uint64_t eb = NarrowEdges::edge_base(nr.word0 & kBeginMask, d);
+    const uint32_t run = (d + NT - 1) / NT;
+    const uint32_t lo = min(rank * run, d), hi = min(lo + run, d);
+    // totals of this thread's run
+    uint64_t v[3] = {0, 0, 0};  // small | large << 32 counts, sum of W - p, sum of p - W
+    {
+        uint32_t prevP = lo ? A.edges[eb + lo - 1].P : 0u;
+        for (uint32_t i = lo; i < hi; ++i) {
+            const uint32_t P = A.edges[eb + i].P;
+            const uint64_t p = (uint64_t)d * (P - prevP);
+            prevP = P;
+            if (p < W) {
+                v[0] += 1;
+                v[1] += W - p;
+            } else if (p > W) {
+                v[0] += 1ull << 32;
+                v[2] += p - W;
+            }
+        }
+    }
+    const uint64_t own[3] = {v[0], v[1], v[2]};
+    uint64_t tot[3];
+    group_scan3<NT>(v, tot, s);
+    uint64_t ks = (v[0] - own[0]) & 0xffffffffull, kl = (v[0] - own[0]) >> 32;
+    uint64_t Dr = v[1] - own[1], Er = v[2] - own[2];
+    {
+        uint32_t prevP = lo ? A.edges[eb + lo - 1].P : 0u;
+        for (uint32_t i = lo; i < hi; ++i) {
+            const EdgeN rec = A.edges[eb + i];
+            const uint64_t p = (uint64_t)d * (rec.P - prevP);
+            prevP = rec.P;
+            A.slots[o + i] = AliasRec{(uint32_t)W, rec.col, rec.col, 0u};
+            if (p < W && ks < d) {
+                Dr += W - p;
+                A.idx[o + ks] = i;
+                A.sum[o + ks] = Dr;
+                ++ks;
+            } else if (p > W && kl < d) {
+                Er += p - W;
+                A.idx[o + d - 1 - kl] = i;
+                A.sum[o + d - 1 - kl] = Er;
+                ++kl;
+            }
+        }
+    }
+    group_sync<NT>();
+    const uint32_t a = (uint32_t)(tot[0] & 0xffffffffull), b = (uint32_t)(tot[0] >> 32);
+    if (a == 0 || b == 0 || (uint64_t)a + b > d) return;  // every p equals W (the sums force a > 0 iff b > 0)
+    auto E = [&](uint32_t j) { return A.sum[o + d - 1 - j]; };
+    auto D = [&](uint32_t q) { return A.sum[o + q]; };
+    auto large_col = [&](uint32_t j) { return A.slots[o + A.idx[o + d - 1 - j]].col; };
+    // small edges t in [t0, t1): donor = first large j with E_j > D_(t-1)
+    {
+        const uint32_t share = (a + NT - 1) / NT;
+        const uint32_t t0 = min(rank * share, a), t1 = min(t0 + share, a);
+        if (t0 < t1) {
+            uint64_t prev = t0 ? D(t0 - 1) : 0ull;
+            uint32_t jl = 0, jh = b - 1;
+            while (jl < jh) {
+                const uint32_t mid = (jl + jh) >> 1;
+                if (E(mid) > prev) jh = mid;
+                else jl = mid + 1;
+            }
+            uint32_t j = jl;
+            for (uint32_t t = t0; t < t1; ++t) {
+                while (j + 1 < b && E(j) <= prev) ++j;
+                const uint64_t Dt = D(t);
+                const uint32_t e = A.idx[o + t];
+                A.slots[o + e].thr = (uint32_t)(W - (Dt - prev));
+                A.slots[o + e].alias_col = large_col(j);
+                prev = Dt;
+            }
+        }
+    }
+    // large edges j in [j0, j1) (not the last): q = first small with D_q >= E_j
+    {
+        const uint32_t nl = b - 1, share = (nl + NT - 1) / NT;
+        const uint32_t j0 = min(rank * share, nl), j1 = min(j0 + share, nl);
+        if (j0 < j1) {
+            uint64_t Ej = E(j0);
+            uint32_t ql = 0, qh = a - 1;
+            while (ql < qh) {
+                const uint32_t mid = (ql + qh) >> 1;
+                if (D(mid) >= Ej) qh = mid;
+                else ql = mid + 1;
+            }
+            uint32_t q = ql;
+            for (uint32_t j = j0; j < j1; ++j) {
+                Ej = E(j);
+                while (q + 1 < a && D(q) < Ej) ++q;
+                const uint64_t th = W - (D(q) - Ej);
+                if (th < W) {
+                    const uint32_t e = A.idx[o + d - 1 - j];
+                    A.slots[o + e].thr = (uint32_t)th;
+                    A.slots[o + e].alias_col = large_col(j + 1);
+                }
+            }
+        }
+    }
+}
+
+__global__ void __launch_bounds__(256) k_alias_mid(AliasArgs A)
+{
+    const uint32_t lane = threadIdx.x & 31;
+    const int64_t warps = (int64_t)gridDim.x * (blockDim.x >> 5);
+    const uint32_t rows = A.counts[0];
+    for (int64_t t = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5; t < rows; t += warps)
+        alias_row_group<32>(A, A.list[t], lane, nullptr);
+}
+
+__global__ void __launch_bounds__(512) k_alias_big(AliasArgs A)
+{
+    __shared__ uint64_t s[3 * 16];
+    const uint32_t rows = A.counts[1];
+    for (uint32_t t = blockIdx.x; t < rows; t += gridDim.x) {
+        alias_row_group<512>(A, A.list[A.n - 1 - t], threadIdx.x, s);
+        __syncthreads();
+    }
+}
+
+__global__ void k_alias_degrees(int64_t n, const NodeRec *node, uint32_t *deg)
+{
+    for (int64_t u = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; u < n; u += (int64_t)gridDim.x * blockDim.x)
+        deg[u] = row_degree(node[u]);
+}
+
+int build_alias(ppr_graph *g, cudaStream_t st)
+{
+    if (g->alias.node) return PPR_OK;
+    if (g->wide) {
+        set_error("the alias sampler needs every row total below 2^32");
+        return PPR_ENOTSUP;
+    }
+    const int64_t n = g->n, m = std::max<int64_t>(g->m, 1);
+    const int64_t tiles = (n + kScanTile - 1) / kScanTile;
+    uint32_t *deg = nullptr, *idx = nullptr, *list = nullptr, *counts = nullptr;
+    uint64_t *off = nullptr, *tmp = nullptr, *sum = nullptr;
+    int rc;
+    auto cleanup = [&]() {
+        dev_free(deg, st);
+        dev_free(off, st);
+        dev_free(tmp, st);
+        dev_free(idx, st);
+        dev_free(sum, st);
+        dev_free(list, st);
+        dev_free(counts, st);
+    };
+    if ((rc = dev_alloc((void **)&deg, sizeof(uint32_t) * n, "alias degrees", st)) ||
+        (rc = dev_alloc((void **)&off, sizeof(uint64_t) * (n + 1), "alias offsets", st)) ||
+        (rc = dev_alloc((void **)&tmp, sizeof(uint64_t) * (tiles + 2), "scan scratch", st)) ||
+        (rc = dev_alloc((void **)&idx, sizeof(uint32_t) * m, "alias scratch", st)) ||
+        (rc = dev_alloc((void **)&sum, sizeof(uint64_t) * m, "alias scratch", st)) ||
+        (rc = dev_alloc((void **)&list, sizeof(uint32_t) * n, "long-row list", st)) ||
+        (rc = dev_alloc((void **)&counts, sizeof(uint32_t) * 2, "long-row counts", st)))
+        return cleanup(), rc;
+    if ((rc = dev_alloc((void **)&g->alias.node, sizeof(NodeRec) * n, "alias node records", st))) return cleanup(), rc;
+    if ((rc = dev_alloc((void **)&g->alias.slots, sizeof(AliasRec) * m, "alias slots", st))) {
+        dev_free(g->alias.node, st);
+        g->alias.node = nullptr;
+        return cleanup(), rc;
+    }
+    cudaError_t e = cudaMemsetAsync(counts, 0, sizeof(uint32_t) * 2, st);
+    const int blocks = (int)std::max<int64_t>(1, std::min<int64_t>((n + 255) / 256, (int64_t)g->ctx->sms * 16));
+    if (e == cudaSuccess) {
+        k_alias_degrees<<<blocks, 256, 0, st>>>(n, g->node, deg);
+        note_launch();
+        exclusive_scan_u32(deg, n, off, tmp, st);
+        AliasArgs A{n, g->node, (const EdgeN *)g->edges, off, g->alias.node, g->alias.slots, idx, sum, list, counts};
+        k_alias_small<<<blocks, 256, 0, st>>>(A);
+        note_launch();
+        k_alias_mid<<<g->ctx->sms * 8, 256, 0, st>>>(A);
+        note_launch();
+        k_alias_big<<<g->ctx->sms, 512, 0, st>>>(A);
+        note_launch();
+        e = cudaGetLastError();
+    }
+    if (e == cudaSuccess) e = cudaStreamSynchronize(st);
+    cleanup();
+    if (e != cudaSuccess) {
+        dev_free(g->alias.node, st);
+        dev_free(g->alias.slots, st);
+        g->alias.node = nullptr;
+        g->alias.slots = nullptr;
+        return cuda_fail(e, "alias build");
+    }
+    g->device_bytes += (int64_t)(sizeof(NodeRec) * n + sizeof(AliasRec) * m);
+    return PPR_OK;
+}
+
 }  // namespace ppr

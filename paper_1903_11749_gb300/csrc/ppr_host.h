@@ -26,6 +26,11 @@ int cuda_fail(cudaError_t e, const char *what);
 int dev_alloc(void **p, size_t bytes, const char *what, cudaStream_t st);
 void dev_free(void *p, cudaStream_t st);
 
+struct AliasCache {
+    NodeRec *node = nullptr;   // node records pointing at alias slots
+    AliasRec *slots = nullptr; // one per edge
+};
+
 struct SegCache {
     uint32_t T = 0;               // threshold the tables were built for (0 = none)
     NodeRec *node = nullptr;      // node records with eligible nodes switched to their tables
@@ -59,6 +64,7 @@ struct ppr_graph {
     std::vector<int64_t> node_off;  // host copy, count+1
     int64_t *d_node_off = nullptr;  // device copy
     ppr::SegCache seg;
+    ppr::AliasCache alias;
     int64_t device_bytes = 0;
 };
 
@@ -93,6 +99,7 @@ namespace ppr {
 int build_graph(ppr_ctx *ctx, int64_t n, int64_t m, const int64_t *row_ptr, const int32_t *col,
                 const uint32_t *w, bool device_ptrs, cudaStream_t st, ppr_graph *g);
 int build_segments(ppr_graph *g, uint32_t T, cudaStream_t st);
+int build_alias(ppr_graph *g, cudaStream_t st);
 
 // walk.cu
 struct RunPlan {
@@ -106,6 +113,7 @@ struct RunPlan {
     int32_t warps_per_block;
     int32_t chunk_sources;
     bool stats;
+    int32_t sampler;  // 0 first-prefix-above rule, 1 integer alias method
 };
 // Enqueues the walks of sources [s_begin, s_end) writing output rows from
 // out_row0.  ends: S * R endpoint scratch for the plain kernel (else unused);

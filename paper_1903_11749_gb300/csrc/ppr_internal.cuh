@@ -54,6 +54,16 @@ struct __align__(16) EdgeW {
     uint32_t pad;
 };
 
+// Alias slot (integer Algorithm 1): edge j of the row is taken when the
+// draw's y < thr, else its alias; both targets are kept so that a step reads
+// one record.
+struct __align__(16) AliasRec {
+    uint32_t thr;
+    int32_t col;
+    int32_t alias_col;
+    uint32_t pad;
+};
+
 struct __align__(16) SegEntry {
     uint64_t cum;
     uint32_t node;
@@ -162,6 +172,16 @@ struct WideEdges {
     }
     __device__ __forceinline__ static uint64_t key(uint4 v) { return (uint64_t)v.x | ((uint64_t)v.y << 32); }
     __device__ __forceinline__ static uint32_t target(uint4 v) { return v.z; }
+    using Rec = uint4;
+};
+
+// Alias layout: begin/count of a node record index its alias slots.
+struct AliasEdges {
+    const AliasRec *e;
+    __host__ __device__ __forceinline__ static uint64_t edge_base(uint64_t begin, uint32_t) { return begin; }
+    __device__ __forceinline__ uint4 load(uint64_t i) const { return __ldg(reinterpret_cast<const uint4 *>(e) + i); }
+    __device__ __forceinline__ static uint64_t key(uint4 v) { return v.x; }
+    __device__ __forceinline__ static uint32_t target(uint4 v) { return v.y; }
     using Rec = uint4;
 };
 

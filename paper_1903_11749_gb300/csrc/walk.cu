@@ -17,6 +17,7 @@
 //                    whole warp, and aggregate a chunk in shared memory as soon
 //                    as its last walk ends.
 #include <algorithm>
+#include <type_traits>
 #include <mutex>
 
 #include "ppr_host.h"
@@ -76,6 +77,36 @@ __device__ __forceinline__ bool walk_step(const KParams &p, const E &edges, bool
     const uint64_t beg = w0 & kBeginMask;
     const bool segf = SEG && (w0 >> 63);
     const uint64_t r64 = (uint64_t)x.x | ((uint64_t)x.y << 32);
+    if constexpr (std::is_same<E, AliasEdges>::value) {
+        // integer alias method: slot j = floor(r*d / 2^64), y = floor(frac * W / 2^64)
+        if (!act) return false;
+        if (STATS) ++tl.sectors;  // the node record
+        uint32_t next;
+        if (cnt == 0) {
+            if (p.dangling == 1) {
+                end = u;
+                return true;
+            }
+            next = src;
+        } else if (cnt == 1) {
+            next = (uint32_t)total;
+        } else {
+            const uint64_t j = __umul64hi(r64, (uint64_t)cnt);
+            const uint64_t frac = r64 * (uint64_t)cnt;
+            const uint64_t y = mulhi64_by32((uint32_t)frac, (uint32_t)(frac >> 32), (uint32_t)total);
+            const uint4 rec = edges.load(beg + j);
+            next = y < rec.x ? rec.y : rec.z;
+            if (STATS) ++tl.sectors;
+        }
+        ++tl.steps;
+        ++k;
+        u = next;
+        if (x.z < p.T) {
+            end = u;
+            return true;
+        }
+        return false;
+    }
     uint64_t xr = 0;
     if (act && (cnt > 1 || segf)) {
         // narrow rows hold the summary shape above bit 32 (W < 2^32 there)
@@ -149,6 +180,11 @@ template <>
 __device__ __forceinline__ WideEdges make_edges<WideEdges>(const void *e)
 {
     return WideEdges{(const EdgeW *)e};
+}
+template <>
+__device__ __forceinline__ AliasEdges make_edges<AliasEdges>(const void *e)
+{
+    return AliasEdges{(const AliasRec *)e};
 }
 
 __device__ __forceinline__ void warp_add(unsigned long long *dst, uint32_t v)
@@ -450,8 +486,8 @@ int launch_walks(ppr_ctx *ctx, const ppr_graph *g, const RunPlan &plan, const Ou
 {
     if (S <= 0) return PPR_OK;
     KParams kp{};
-    kp.node = plan.segments ? g->seg.node : g->node;
-    kp.edges = g->edges;
+    kp.node = plan.segments ? g->seg.node : (plan.sampler == 1 ? g->alias.node : g->node);
+    kp.edges = plan.sampler == 1 ? (const void *)g->alias.slots : g->edges;
     kp.seg = g->seg.entries;
     kp.R = plan.R;
     kp.T = plan.T;
@@ -514,6 +550,9 @@ int launch_walks(ppr_ctx *ctx, const ppr_graph *g, const RunPlan &plan, const Ou
         }
         PPR_CUDA(cudaMemsetAsync(kp.queue, 0, sizeof(unsigned long long), st));
     }
+    if (plan.sampler == 1)
+        return plan.stats ? launch_typed<AliasEdges, false, true>(ctx, kp, plan, S, st, ev_owner)
+                          : launch_typed<AliasEdges, false, false>(ctx, kp, plan, S, st, ev_owner);
     if (plan.stats) {
         if (g->wide)
             return plan.segments ? launch_typed<WideEdges, true, true>(ctx, kp, plan, S, st, ev_owner)
@@ -601,6 +640,10 @@ extern "C" int ppr_run_noalloc(ppr_ctx *ctx, const ppr_graph *g, const ppr_run_a
         set_error("segment tables for this alpha are not built (a ppr_run with segments=1 builds them)");
         return PPR_ENOTSUP;
     }
+    if (a->sampler != 0 && (a->sampler != 1 || a->segments || !g->alias.node)) {
+        set_error("alias sampler: needs tables built by an earlier ppr_run with sampler=1, no segments");
+        return PPR_ENOTSUP;
+    }
     const uint32_t need_cap = (uint32_t)std::min<int64_t>((int64_t)a->R, g->n);
     if (cap < need_cap) {
         set_error("row capacity %u < min(R, n) = %u", cap, need_cap);
@@ -636,6 +679,7 @@ extern "C" int ppr_run_noalloc(ppr_ctx *ctx, const ppr_graph *g, const ppr_run_a
     plan.warps_per_block = a->warps_per_block;
     plan.chunk_sources = a->chunk_sources;
     plan.stats = false;
+    plan.sampler = a->sampler;
     Outputs out{nnz, cols, cnts, cap, topk_idx, topk_cnt, a->topk, reinterpret_cast<unsigned long long *>(scratch)};
     return launch_walks(ctx, g, plan, out, a->src_begin, a->src_end - a->src_begin, nullptr, 0,
                         scratch + kNoAllocHeader, st, nullptr);

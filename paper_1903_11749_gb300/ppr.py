@@ -39,7 +39,7 @@ class RunArgs(C.Structure):
                 ("src_end", C.c_int64), ("tag", C.c_uint32), ("dangling", C.c_int32), ("segments", C.c_int32),
                 ("topk", C.c_int32), ("kernel", C.c_int32), ("large_degree", C.c_int32),
                 ("warps_per_block", C.c_int32), ("chunk_sources", C.c_int32), ("max_batch_sources", C.c_int64),
-                ("stats", C.c_int32), ("stream", C.c_void_p)]
+                ("stats", C.c_int32), ("sampler", C.c_int32), ("stream", C.c_void_p)]
 
 
 class Tuning(C.Structure):
@@ -68,6 +68,7 @@ class ResultInfo(C.Structure):
 _SIGS = {
     "ppr_version": (C.c_int, []),
     "ppr_alpha_threshold": (C.c_uint32, [C.c_double]),
+    "ppr_walks_for_accuracy": (C.c_int, [C.c_double, C.c_double, C.c_double, C.POINTER(C.c_uint64)]),
     "ppr_last_error": (C.c_char_p, []),
     "ppr_kernel_launches": (C.c_int64, []),
     "ppr_create": (C.c_int, [C.c_int, C.POINTER(C.c_void_p)]),
@@ -133,6 +134,12 @@ def kernel_launches() -> int:
 
 def alpha_threshold(alpha: float) -> int:
     return int(lib().ppr_alpha_threshold(alpha))
+
+
+def walks_for_accuracy(eps: float, delta: float, p_f: float) -> int:
+    out = C.c_uint64()
+    _check(lib().ppr_walks_for_accuracy(eps, delta, p_f, C.byref(out)))
+    return out.value
 
 
 def _ptr(a):
@@ -250,7 +257,7 @@ class Graph:
 
     def _args(self, alpha=0.15, R=100, seed=1, src_begin=0, src_end=None, tag=0, dangling=0, segments=False,
               topk=0, kernel=KERNEL_PERSISTENT, large_degree=0, warps_per_block=0, chunk_sources=0,
-              max_batch_sources=0, stats=False, stream=None):
+              max_batch_sources=0, stats=False, stream=None, sampler=0):
         a = RunArgs()
         lib().ppr_run_args_init(C.byref(a))
         a.alpha, a.R, a.seed = alpha, R, seed
@@ -260,6 +267,7 @@ class Graph:
         a.large_degree, a.warps_per_block, a.chunk_sources = large_degree, warps_per_block, chunk_sources
         a.max_batch_sources = max_batch_sources
         a.stats = int(bool(stats))
+        a.sampler = sampler
         a.stream = _stream_ptr(stream)
         return a
 
@@ -299,7 +307,7 @@ class Graph:
 
     def run(self, alpha=0.15, R=100, seed=1, src_begin=0, src_end=None, tag=0, dangling=0, segments=False,
             topk=0, kernel=KERNEL_PERSISTENT, large_degree=0, warps_per_block=0, chunk_sources=0,
-            max_batch_sources=0, stats=False, stream=None, wait=True) -> "Result":
+            max_batch_sources=0, stats=False, stream=None, wait=True, sampler=0) -> "Result":
         a = RunArgs()
         lib().ppr_run_args_init(C.byref(a))
         a.alpha, a.R, a.seed = alpha, R, seed
@@ -309,6 +317,7 @@ class Graph:
         a.large_degree, a.warps_per_block, a.chunk_sources = large_degree, warps_per_block, chunk_sources
         a.max_batch_sources = max_batch_sources
         a.stats = int(bool(stats))
+        a.sampler = sampler
         a.stream = _stream_ptr(stream)
         h = C.c_void_p()
         _check(lib().ppr_run(self.ctx.h, self.h, C.byref(a), C.byref(h)))
