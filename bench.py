@@ -23,6 +23,7 @@ import os
 import statistics
 import subprocess
 import sys
+import tempfile
 import time
 
 import numpy as np
@@ -40,14 +41,32 @@ WORKLOADS = {
                         "depth-3 segments for out-degree <= 8"),
     "rmat24plain": dict(alpha=0.15, R=50, seed=1, topk=64, segments=False,
                         desc="R-MAT scale 24 as rmat24, plain steps only"),
+    "rmat20alias": dict(alpha=0.2, R=100, seed=1, topk=32, segments=False, sampler=1,
+                        desc="R-MAT scale 20 as rmat20, integer alias sampler (Algorithm 1 tables built every step)"),
+    "rmat24alias": dict(alpha=0.15, R=50, seed=1, topk=64, segments=False, sampler=1,
+                        desc="R-MAT scale 24 as rmat24, integer alias sampler (Algorithm 1 tables built every step)"),
     "serve": dict(alpha=0.15, R=100, seed=1, topk=32, segments=False,
                   desc="queries on the R-MAT scale-24 graph resident on the device: |S| log-uniform in [1, 1e5] "
                        "distinct uniform sources, Poisson arrivals at rho x measured capacity"),
+    "accuracy": dict(alpha=0.15, R=4096, seed=1, topk=1000, segments=False,
+                     desc="Chung-Lu n=50000 (exponent 2.3, mean degree 12, w U[1,100]), 100 sources; NDCG/MAP@k of "
+                          "the top-k rows against FP64 power iteration, R in {64, 256, 1024, 4096, 4x4096 tags}"),
+    "sweep_alpha": dict(alpha=0.2, R=100, seed=1, topk=32, segments=False,
+                        desc="rmat20 graph, alpha in {0.05, 0.1, 0.15, 0.2, 0.3, 0.5}: walker time and step rate"),
+    "sweep_chunk": dict(alpha=0.2, R=100, seed=1, topk=32, segments=False,
+                        desc="rmat20 graph, chunk_sources x warps_per_block grid against the autotuner's pick"),
     "chunglu2048": dict(alpha=0.15, R=200, seed=1, topk=32, segments=False,
                         desc="2048 Chung-Lu graphs (exponent 2.3, n log-uniform in [100, 50000], mean degree 12, "
                              "w U[1,100]) in one block-diagonal graph; one persistent launch replayed as a CUDA graph"),
 }
 L2_FLUSH_BYTES = 512 << 20
+
+
+def base_graph(workload: str) -> str:
+    """The graph a workload runs on (variants share their base graph)."""
+    for suffix in ("plain", "alias"):
+        workload = workload.replace(suffix, "")
+    return workload
 
 
 def env_rank():
@@ -82,7 +101,7 @@ class Clocks:
               "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
 
     def __init__(self, device: int, path: str | None):
-        self.path = path or os.path.join(ROOT, "gpurun_out", f"clocks_{os.getpid()}.csv")
+        self.path = path or os.path.join(tempfile.gettempdir(), f"ppr_clocks_{os.getpid()}.csv")
         self.device = device
         self.proc = None
 
@@ -161,7 +180,7 @@ def cpu_baseline(g, wl, budget_s: float = 15.0):
     og = O.prepare(g.n, g.row_ptr, g.col, g.w)
     # calibrate on a small sample, then size the sample to the budget
     t0 = time.perf_counter()
-    seg = dict(segments=wl["segments"], lazy_segments=True)
+    seg = dict(segments=wl["segments"], lazy_segments=True, sampler=wl.get("sampler", 0))
     ends, steps = O.walks(og, wl["alpha"], wl["R"], wl["seed"], 0, 200, **seg)
     dt = max(time.perf_counter() - t0, 1e-3)
     n_src = int(max(200, min(g.n, 200 * budget_s / dt)))
@@ -230,7 +249,7 @@ def run_reference(args):
     O.build()
     if args.workload == "chunglu2048":
         return run_reference_batched(args, wl, I, O)
-    g = I.workload_graph(args.workload.replace("plain", ""))
+    g = I.workload_graph(base_graph(args.workload))
     og = O.prepare(g.n, g.row_ptr, g.col, g.w)
     n_blk = 64
     per_step = []
@@ -241,7 +260,7 @@ def run_reference(args):
         st_step, wk = 0, 0
         for s in rng_src:
             e, st = O.walks(og, wl["alpha"], wl["R"], wl["seed"], int(s), int(s) + n_blk,
-                            segments=wl["segments"], lazy_segments=True)
+                            segments=wl["segments"], lazy_segments=True, sampler=wl.get("sampler", 0))
             rp, col, cnt = O.rows(e, g.n)
             O.topk(rp, col, cnt, wl["topk"])
             st_step += st
@@ -518,6 +537,150 @@ def run_serving(args):
     return 0
 
 
+def run_accuracy(args):
+    """Accuracy analog of the paper's NDCG/MAP experiment (Sec. 5.2): top-k
+    rows of the CUDA path against the exact ranking from FP64 power
+    iteration, for growing R, plus Definition 1 at the walk count of
+    ppr_walks_for_accuracy (eps 0.5, p_f 0.01)."""
+    import torch
+    from paper_1903_11749_gb300 import accuracy as A
+    from paper_1903_11749_gb300 import build as B
+    from paper_1903_11749_gb300 import inputs as I
+    B.build()
+    from paper_1903_11749_gb300 import ppr
+    rank, world, local = env_rank()
+    if rank != 0:
+        return 0
+    wl = WORKLOADS["accuracy"]
+    g = I.chung_lu_graph(50_000, avg_deg=12.0, exponent=2.3, wlo=1, whi=100, seed=5050)
+    src = np.linspace(0, g.n - 1, 100).astype(np.int32)
+    T = ppr.alpha_threshold(wl["alpha"])
+    t0 = time.perf_counter()
+    pi = A.exact_ppr_rows(g.n, g.row_ptr, g.col, g.w, src, T, tol=1e-12)
+    truth_s = time.perf_counter() - t0
+    ctx = ppr.Context(local)
+    G = ctx.load_graph(g.n, g.row_ptr, g.col, g.w)
+    ks = (10, 100, 1000)
+    eps, p_f = 0.5, 0.01
+    table = []
+    for R, runs in ((64, 1), (256, 1), (1024, 1), (4096, 1), (4096, 4)):
+        est = np.zeros((len(src), g.n))
+        idx = cnt = None
+        e0 = torch.cuda.Event(enable_timing=True)
+        e1 = torch.cuda.Event(enable_timing=True)
+        e0.record()
+        for tag in range(runs):
+            res = G.run_list(src, alpha=wl["alpha"], R=R, seed=wl["seed"], tag=tag, topk=max(ks))
+            rp, col, c = res.sparse_rows()
+            np.add.at(est, (np.repeat(np.arange(len(src)), np.diff(rp)), col), c)
+            if runs == 1:
+                idx, cnt = res.topk()
+        e1.record()
+        e1.synchronize()
+        est /= R * runs
+        row = {"R": R * runs, "runs": runs, "gpu_ms": e0.elapsed_time(e1)}
+        for k in ks:
+            nd, ap = [], []
+            for i in range(len(src)):
+                truth = A.exact_topk(pi[i], k)
+                if runs == 1:
+                    pred = A.estimated_ranking(idx[i], cnt[i])
+                else:
+                    pred = A.exact_topk(est[i], k)  # same order rule on the summed counts
+                nd.append(A.ndcg_at_k(pred, truth, k))
+                ap.append(A.average_precision_at_k(pred, truth, k))
+            row[f"ndcg@{k}"] = float(np.mean(nd))
+            row[f"map@{k}"] = float(np.mean(ap))
+        delta = A.delta_for_walks(R * runs, eps, p_f)
+        bad, pairs = A.definition1_violations(est, pi, eps, delta)
+        row.update({"def1_delta": delta, "def1_pairs": pairs, "def1_violations": bad})
+        table.append(row)
+    last = table[3]
+    line = {"metric": "NDCG@100", "value": last["ndcg@100"], "unit": "ratio", "n_gpus": 1, "steps": 1, "warmup": 0,
+            "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "u32", "data": "synthetic",
+            "config": {"workload": "accuracy", "desc": wl["desc"], "alpha": wl["alpha"], "n": g.n, "m": g.m,
+                       "sources": len(src), "eps": eps, "p_f": p_f},
+            "truth": f"FP64 power iteration to active mass < 1e-12 ({truth_s:.1f} s on the host)",
+            "table": table}
+    print(json.dumps(line))
+    return 0
+
+
+def run_sweep(args):
+    """Parameter sweeps on the rmat20 graph (analogs of the paper's gamma and
+    alpha experiments, Sec. 5.3-5.4): for each setting, the mean of --steps
+    runs after --warmup, walker time from the library's events and the whole
+    run (walks + reduction) from events on the stream."""
+    import torch
+    from paper_1903_11749_gb300 import build as B
+    from paper_1903_11749_gb300 import inputs as I
+    B.build()
+    from paper_1903_11749_gb300 import ppr
+    rank, world, local = env_rank()
+    if rank != 0:
+        return 0
+    wl = WORKLOADS[args.workload]
+    dev = torch.device("cuda", local)
+    g = I.workload_graph("rmat20")
+    ctx = ppr.Context(local)
+    G = ctx.load_graph(g.n, g.row_ptr, g.col, g.w)
+    flush = torch.empty(L2_FLUSH_BYTES // 4, dtype=torch.int32, device=dev)
+    stream = torch.cuda.current_stream(dev)
+
+    def timed(**kw):
+        for _ in range(args.warmup):
+            G.run(stream=stream, **kw)
+        walk, whole, steps = [], [], 0
+        for _ in range(max(1, args.steps)):
+            flush.fill_(1)
+            e0 = torch.cuda.Event(enable_timing=True)
+            e1 = torch.cuda.Event(enable_timing=True)
+            e0.record(stream)
+            r = G.run(stream=stream, wait=False, **kw)
+            e1.record(stream)
+            r.wait()
+            e1.synchronize()
+            whole.append(e0.elapsed_time(e1))
+            walk.append(r.info().kernel_ms)
+            steps = int(r.info().steps)
+        ms = statistics.mean(whole)
+        return {"walker_ms": statistics.mean(walk), "run_ms": ms, "steps": steps,
+                "steps_per_s": steps / (ms / 1e3)}
+
+    base = dict(R=wl["R"], seed=wl["seed"], topk=wl["topk"])
+    table = []
+    if args.workload == "sweep_alpha":
+        for alpha in (0.05, 0.1, 0.15, 0.2, 0.3, 0.5):
+            row = {"alpha": alpha}
+            row.update(timed(alpha=alpha, **base))
+            table.append(row)
+        best = max(table, key=lambda r: r["steps_per_s"])
+        metric, value, unit = "walk steps/s at alpha 0.2", next(r for r in table if r["alpha"] == 0.2)["steps_per_s"], \
+            "walk steps/s"
+    else:
+        for wpb in (4, 8):
+            for cs in (1, 2, 4, 8, 16, 32):
+                row = {"warps_per_block": wpb, "chunk_sources": cs}
+                row.update(timed(alpha=wl["alpha"], warps_per_block=wpb, chunk_sources=cs, **base))
+                table.append(row)
+        t = G.autotune(sample_sources=200_000, alpha=wl["alpha"], **base)
+        pick = {"warps_per_block": t["warps_per_block"], "chunk_sources": t["chunk_sources"],
+                "large_degree": t["large_degree"], "autotuner": True}
+        pick.update(timed(alpha=wl["alpha"], warps_per_block=t["warps_per_block"], chunk_sources=t["chunk_sources"],
+                          large_degree=t["large_degree"], **base))
+        table.append(pick)
+        best = max(table[:-1], key=lambda r: r["steps_per_s"])
+        metric, value, unit = "autotuned / best grid point", pick["steps_per_s"] / best["steps_per_s"], "ratio"
+    line = {"metric": metric, "value": value, "unit": unit, "n_gpus": 1, "steps": args.steps,
+            "warmup": args.warmup, "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
+            "dtype": "u32", "data": "synthetic",
+            "config": {"workload": args.workload, "desc": wl["desc"], "R": wl["R"], "topk": wl["topk"],
+                       "n": g.n, "m": g.m, "l2": "flushed before every run (512 MB write)"},
+            "best": best, "table": table}
+    print(json.dumps(line))
+    return 0
+
+
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
@@ -546,6 +709,10 @@ def main():
         return run_batched(args)
     if args.workload == "serve":
         return run_serving(args)
+    if args.workload == "accuracy":
+        return run_accuracy(args)
+    if args.workload.startswith("sweep_"):
+        return run_sweep(args)
 
     import torch
     import torch.distributed as dist
@@ -560,7 +727,7 @@ def main():
     torch.cuda.set_device(local)
     dev = torch.device("cuda", local)
     wl = WORKLOADS[args.workload]
-    g = I.workload_graph(args.workload.replace("plain", ""))
+    g = I.workload_graph(base_graph(args.workload))
     a, b, rank_tag = rank_workload(g.n, rank, world)
     tune = dict(warps_per_block=args.warps_per_block, chunk_sources=args.chunk_sources,
                 large_degree=args.large_degree)
@@ -577,7 +744,8 @@ def main():
     def step(kernel=ppr.KERNEL_PERSISTENT, stats=False):
         G = ctx.load_graph(g.n, d_rp, d_col, d_w, stream=stream, m=g.m)
         kw = dict(alpha=wl["alpha"], R=wl["R"], seed=wl["seed"], tag=rank_tag, topk=wl["topk"],
-                  segments=wl["segments"], kernel=kernel, stats=stats, stream=stream, wait=False, **tune)
+                  segments=wl["segments"], kernel=kernel, stats=stats, stream=stream, wait=False,
+                  sampler=wl.get("sampler", 0), **tune)
         if sample is not None:
             r = G.run_list(sample, **kw)
         else:
@@ -669,7 +837,8 @@ def main():
             t0 = time.perf_counter()
             G = ctx.load_graph(g.n, h_rp, h_col, h_w, stream=stream, m=g.m)
             r = G.run(alpha=wl["alpha"], R=wl["R"], seed=wl["seed"], src_begin=a, src_end=b, tag=rank_tag,
-                      topk=wl["topk"], segments=wl["segments"], stream=stream, **tune)
+                      topk=wl["topk"], segments=wl["segments"], stream=stream, sampler=wl.get("sampler", 0),
+                      **tune)
             nnz = r.sparse_rows_into(o_rp, o_col, o_cnt)
             if wl["topk"]:
                 r.topk_into(wl["topk"], o_ti, o_tc)
