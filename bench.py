@@ -831,24 +831,42 @@ def main():
         k = max(1, wl["topk"])
         o_ti = torch.empty((S, k), dtype=torch.int32).pin_memory()
         o_tc = torch.empty((S, k), dtype=torch.int32).pin_memory()
-        times, d2h = [], 0
-        for it in range(1 + min(3, args.steps)):
+        run_kw = dict(alpha=wl["alpha"], R=wl["R"], seed=wl["seed"], src_begin=a, src_end=b, tag=rank_tag,
+                      topk=wl["topk"], segments=wl["segments"], stream=stream, sampler=wl.get("sampler", 0), **tune)
+        ti_arg = (o_ti, o_tc) if wl["topk"] else (None, None)
+
+        def e2e_once(pipelined):
             torch.cuda.synchronize(dev)
             t0 = time.perf_counter()
             G = ctx.load_graph(g.n, h_rp, h_col, h_w, stream=stream, m=g.m)
-            r = G.run(alpha=wl["alpha"], R=wl["R"], seed=wl["seed"], src_begin=a, src_end=b, tag=rank_tag,
-                      topk=wl["topk"], segments=wl["segments"], stream=stream, sampler=wl.get("sampler", 0),
-                      **tune)
-            nnz = r.sparse_rows_into(o_rp, o_col, o_cnt)
-            if wl["topk"]:
-                r.topk_into(wl["topk"], o_ti, o_tc)
+            if pipelined:  # rows and top-k copied to the host batch by batch, behind the walks
+                nnz, _ = G.run_to_host(o_rp, o_col, o_cnt, *ti_arg, **run_kw)
+            else:  # run, then read everything back
+                r = G.run(**run_kw)
+                nnz = r.sparse_rows_into(o_rp, o_col, o_cnt)
+                if wl["topk"]:
+                    r.topk_into(wl["topk"], o_ti, o_tc)
+                del r
             t1 = time.perf_counter()
+            del G
+            return t1 - t0, nnz
+
+        times, serial_times, nnz = [], [], 0
+        for it in range(1 + min(3, args.steps)):
+            dt, nnz = e2e_once(True)
             if it > 0:
-                times.append(t1 - t0)
-            d2h = o_rp.numel() * 8 + nnz * 8 + (S * wl["topk"] * 8 if wl["topk"] else 0)
-            del r, G
+                times.append(dt)
+        for it in range(1 + min(2, args.steps)):
+            dt, _ = e2e_once(False)
+            if it > 0:
+                serial_times.append(dt)
+        d2h = o_rp.numel() * 8 + nnz * 8 + (S * wl["topk"] * 8 if wl["topk"] else 0)
         e2e = {"value": steps_per_pass / statistics.mean(times), "unit": "walk steps/s", "h2d_bytes_per_step": h2d,
-               "d2h_bytes_per_step": d2h, "ms_per_step": 1e3 * statistics.mean(times)}
+               "d2h_bytes_per_step": d2h, "ms_per_step": 1e3 * statistics.mean(times),
+               "call": "ppr_load_graph (pinned host CSR) + ppr_run_to_host (pinned host rows and top-k)",
+               "unpipelined": {"value": steps_per_pass / statistics.mean(serial_times),
+                               "ms_per_step": 1e3 * statistics.mean(serial_times),
+                               "call": "ppr_load_graph + ppr_run + ppr_sparse_rows + ppr_topk"}}
 
     peak, peak_kind = measured_peaks()
     kms = statistics.mean(kernel_ms)

@@ -268,6 +268,30 @@ typedef struct {
 int ppr_result_get_info(const ppr_result *r, ppr_result_info *info);
 
 /*
+ * Runs the walks of args (range of sources) and delivers the compacted rows
+ * and the top-k straight into host memory, pipelined against the walks
+ * (the batching of the paper's pipelines, Sec. 4.3, with the output stream
+ * of each batch overlapped with the next batch's walks): the sources are
+ * cut into `parts` batches (0 = the library's choice); while batch i+1 walks
+ * on args->stream, batch i's rows are compacted and copied to the host on a
+ * second stream of the library's own.  Returns when every row is in place.
+ *   row_ptr  int64[S+1] (row s = entries [row_ptr[s], row_ptr[s+1]))
+ *   col, cnt int32 / uint32 [cap]; cap >= nnz or PPR_ERANGE (nothing beyond
+ *            cap is written; row_ptr is then incomplete)
+ *   nnz      out: total entries (may be NULL)
+ *   topk_idx, topk_cnt  [S * args->topk] or NULL when args->topk == 0
+ *   info     out: steps, walks, walker time (may be NULL)
+ * Host buffers should be page-locked (cudaHostAlloc or cudaHostRegister) for
+ * the copies to overlap the walks; pageable buffers work, serialised.
+ * Plain and batched graphs; source lists are not taken here.  Errors as
+ * ppr_run, plus PPR_ERANGE for cap.
+ */
+int ppr_run_to_host(ppr_ctx *ctx, const ppr_graph *g, const ppr_run_args *args, int32_t parts, int64_t *row_ptr,
+                    int32_t *col, uint32_t *cnt, int64_t cap, int64_t *nnz, int32_t *topk_idx, uint32_t *topk_cnt,
+                    ppr_result_info *info);
+
+
+/*
  * Copies the sparse rows: row_ptr (S+1 entries), then col/cnt (nnz entries).
  * If col == NULL only row_ptr (may be NULL too) and *nnz are produced.
  * PPR_ERANGE if cap < nnz.  flags: PPR_PTRS_DEVICE for device outputs.

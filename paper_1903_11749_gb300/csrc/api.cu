@@ -172,6 +172,11 @@ void ppr_destroy(ppr_ctx *ctx)
 {
     if (!ctx) return;
     if (ctx->server) ppr_serve_stop(ctx);
+    if (ctx->copy_stream || ctx->pinned) {
+        cudaSetDevice(ctx->device);
+        if (ctx->copy_stream) cudaStreamDestroy(ctx->copy_stream);
+        if (ctx->pinned) cudaFreeHost(ctx->pinned);
+    }
     delete ctx;
 }
 
@@ -513,6 +518,176 @@ int ppr_run_list(ppr_ctx *ctx, const ppr_graph *g, const ppr_run_args *a, const 
     }
     *out = nullptr;
     return run_common(ctx, g, a, sources, count, out);
+}
+
+// Row starts of one batch made absolute: out[i] = in[i] + base.
+__global__ void k_add_base(int64_t n, uint64_t *off, uint64_t base)
+{
+    for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x)
+        off[i] += base;
+}
+
+int ppr_run_to_host(ppr_ctx *ctx, const ppr_graph *g, const ppr_run_args *a, int32_t parts, int64_t *row_ptr,
+                    int32_t *col, uint32_t *cnt, int64_t cap, int64_t *nnz, int32_t *topk_idx, uint32_t *topk_cnt,
+                    ppr_result_info *info)
+{
+    if (!ctx || !g || !a || !row_ptr || !col || !cnt || parts < 0) {
+        set_error("NULL argument or parts < 0");
+        return PPR_EINVAL;
+    }
+    if (a->topk > 0 && (!topk_idx || !topk_cnt)) {
+        set_error("topk > 0 needs topk_idx and topk_cnt");
+        return PPR_EINVAL;
+    }
+    RunPlan plan;
+    int rc = check_run(g, a, 0, false, &plan);
+    if (rc) return rc;
+    if ((rc = set_device(ctx))) return rc;
+    cudaStream_t st = (cudaStream_t)a->stream;
+    if ((rc = prepare_tables(g, plan, st))) return rc;
+    cudaError_t e = cudaSuccess;
+    if (!ctx->copy_stream && (e = cudaStreamCreateWithFlags(&ctx->copy_stream, cudaStreamNonBlocking)) != cudaSuccess)
+        return cuda_fail(e, "copy stream");
+    if (!ctx->pinned && (e = cudaHostAlloc((void **)&ctx->pinned, 4 * sizeof(unsigned long long), 0)) != cudaSuccess)
+        return cuda_fail(e, "page-locked words");
+    cudaStream_t cs = ctx->copy_stream;
+    const int64_t S = a->src_end - a->src_begin;
+    const uint32_t rcap = row_capacity(g, a->R);
+    const int32_t k = a->topk;
+    int64_t P = parts > 0 ? parts : std::min<int64_t>(8, std::max<int64_t>(1, (S + 131071) / 131072));
+    P = std::min<int64_t>(P, S);
+    int64_t B = (S + P - 1) / P;
+    {
+        size_t free_b = 0, total_b = 0;
+        cudaMemGetInfo(&free_b, &total_b);
+        // endpoints, two slots of rows (stored and compacted) and top-k per source
+        const size_t per = (size_t)a->R * 4 + 2 * ((size_t)rcap * 16 + (size_t)k * 8 + 16);
+        const int64_t fit = (int64_t)(free_b / 2 / per);
+        B = std::max<int64_t>(1, std::min<int64_t>(B, fit));
+    }
+    P = (S + B - 1) / B;
+    const int64_t tiles = (B + kScanTile - 1) / kScanTile;
+    struct Slot {
+        uint32_t *nnz = nullptr;
+        int32_t *cols = nullptr, *ccol = nullptr, *ti = nullptr;
+        uint32_t *cnts = nullptr, *ccnt = nullptr, *tc = nullptr;
+        uint64_t *off = nullptr, *tmp = nullptr;
+        cudaEvent_t ready = nullptr, copied = nullptr;
+    } slot[2];
+    ppr_result *r = new (std::nothrow) ppr_result;  // owns the walker events and counters
+    if (!r) return PPR_ENOMEM;
+    r->ctx = ctx;
+    r->stream = st;
+    unsigned char *ws = nullptr;
+    auto finish = [&](int code) {
+        cudaStreamSynchronize(cs);
+        cudaStreamSynchronize(st);
+        for (Slot &q : slot) {
+            dev_free(q.nnz, st);
+            dev_free(q.cols, st);
+            dev_free(q.cnts, st);
+            dev_free(q.ccol, st);
+            dev_free(q.ccnt, st);
+            dev_free(q.ti, st);
+            dev_free(q.tc, st);
+            dev_free(q.off, st);
+            dev_free(q.tmp, st);
+            if (q.ready) cudaEventDestroy(q.ready);
+            if (q.copied) cudaEventDestroy(q.copied);
+        }
+        dev_free(ws, st);
+        result_release(r);
+        return code;
+    };
+    for (Slot &q : slot) {
+        const size_t rows = (size_t)B * rcap;
+        if ((rc = dev_alloc((void **)&q.nnz, sizeof(uint32_t) * B, "row sizes", st)) ||
+            (rc = dev_alloc((void **)&q.cols, sizeof(int32_t) * rows, "row ids", st)) ||
+            (rc = dev_alloc((void **)&q.cnts, sizeof(uint32_t) * rows, "row counts", st)) ||
+            (rc = dev_alloc((void **)&q.ccol, sizeof(int32_t) * (rows + 1), "compacted ids", st)) ||
+            (rc = dev_alloc((void **)&q.ccnt, sizeof(uint32_t) * (rows + 1), "compacted counts", st)) ||
+            (rc = dev_alloc((void **)&q.off, sizeof(uint64_t) * (B + 1), "row offsets", st)) ||
+            (rc = dev_alloc((void **)&q.tmp, sizeof(uint64_t) * (tiles + 2), "scan scratch", st)))
+            return finish(rc);
+        if (k > 0 && ((rc = dev_alloc((void **)&q.ti, sizeof(int32_t) * B * k, "top-k ids", st)) ||
+                      (rc = dev_alloc((void **)&q.tc, sizeof(uint32_t) * B * k, "top-k counts", st))))
+            return finish(rc);
+        if ((e = cudaEventCreateWithFlags(&q.ready, cudaEventDisableTiming)) != cudaSuccess ||
+            (e = cudaEventCreateWithFlags(&q.copied, cudaEventDisableTiming)) != cudaSuccess)
+            return finish(cuda_fail(e, "cudaEventCreate"));
+    }
+    if ((rc = dev_alloc((void **)&r->d_steps, sizeof(unsigned long long) * 4, "counters", st))) return finish(rc);
+    if ((rc = dev_alloc((void **)&ws, launch_workspace_bytes(g, plan, B), "walk workspace", st))) return finish(rc);
+    if ((e = cudaMemsetAsync(r->d_steps, 0, sizeof(unsigned long long) * 4, st)) != cudaSuccess)
+        return finish(cuda_fail(e, "memset"));
+    const int cblocks = (int)std::min<int64_t>((B + 7) / 8, (int64_t)ctx->sms * 32);
+    uint64_t base = 0;
+    for (int64_t i = 0; i <= P; ++i) {
+        if (i < P) {  // batch i: walk, reduce, compact on the run's stream
+            Slot &q = slot[i & 1];
+            const int64_t b0 = i * B, nb = std::min<int64_t>(B, S - b0);
+            if (i >= 2 && (e = cudaStreamWaitEvent(st, q.copied, 0)) != cudaSuccess)
+                return finish(cuda_fail(e, "cudaStreamWaitEvent"));
+            const Outputs o{q.nnz, q.cols, q.cnts, rcap, q.ti, q.tc, k, r->d_steps};
+            if ((rc = launch_walks(ctx, g, plan, o, a->src_begin + b0, nb, nullptr, 0, ws, st, r))) return finish(rc);
+            exclusive_scan_u32(q.nnz, nb, q.off, q.tmp, st);
+            k_compact_rows<<<std::max(1, cblocks), 256, 0, st>>>(nb, rcap, q.nnz, q.off, q.cols, q.cnts, q.ccol, q.ccnt);
+            note_launch();
+            if ((e = cudaMemcpyAsync(&ctx->pinned[i & 1], q.off + nb, sizeof(uint64_t), cudaMemcpyDeviceToHost, st)) !=
+                    cudaSuccess ||
+                (e = cudaEventRecord(q.ready, st)) != cudaSuccess)
+                return finish(cuda_fail(e, "batch"));
+        }
+        if (i >= 1) {  // batch i - 1: its copies on the copy stream, overlapping batch i
+            const int64_t j = i - 1;
+            Slot &q = slot[j & 1];
+            const int64_t b0 = j * B, nb = std::min<int64_t>(B, S - b0);
+            if ((e = cudaEventSynchronize(q.ready)) != cudaSuccess) return finish(cuda_fail(e, "batch"));
+            const uint64_t tot = ctx->pinned[j & 1];
+            if ((uint64_t)cap < base + tot) {
+                set_error("capacity %lld < nnz (at least %llu)", (long long)cap, (unsigned long long)(base + tot));
+                return finish(PPR_ERANGE);
+            }
+            const int64_t nrp = nb + (j == P - 1 ? 1 : 0);  // the last batch also writes row_ptr[S]
+            k_add_base<<<(int)std::min<int64_t>((nrp + 255) / 256, (int64_t)ctx->sms * 8), 256, 0, cs>>>(nrp, q.off,
+                                                                                                         base);
+            note_launch();
+            e = cudaMemcpyAsync(row_ptr + b0, q.off, sizeof(int64_t) * nrp, cudaMemcpyDeviceToHost, cs);
+            if (e == cudaSuccess && tot > 0)
+                e = cudaMemcpyAsync(col + base, q.ccol, sizeof(int32_t) * tot, cudaMemcpyDeviceToHost, cs);
+            if (e == cudaSuccess && tot > 0)
+                e = cudaMemcpyAsync(cnt + base, q.ccnt, sizeof(uint32_t) * tot, cudaMemcpyDeviceToHost, cs);
+            if (e == cudaSuccess && k > 0)
+                e = cudaMemcpyAsync(topk_idx + b0 * k, q.ti, sizeof(int32_t) * nb * k, cudaMemcpyDeviceToHost, cs);
+            if (e == cudaSuccess && k > 0)
+                e = cudaMemcpyAsync(topk_cnt + b0 * k, q.tc, sizeof(uint32_t) * nb * k, cudaMemcpyDeviceToHost, cs);
+            if (e == cudaSuccess) e = cudaEventRecord(q.copied, cs);
+            if (e != cudaSuccess) return finish(cuda_fail(e, "output copies"));
+            base += tot;
+        }
+    }
+    if ((e = cudaStreamSynchronize(cs)) != cudaSuccess || (e = cudaStreamSynchronize(st)) != cudaSuccess)
+        return finish(cuda_fail(e, "run"));
+    if (nnz) *nnz = (int64_t)base;
+    if (info) {
+        unsigned long long c[4] = {0, 0, 0, 0};
+        if ((e = cudaMemcpy(c, r->d_steps, sizeof(c), cudaMemcpyDeviceToHost)) != cudaSuccess)
+            return finish(cuda_fail(e, "counters"));
+        float kms = 0.f, ms = 0.f;
+        for (size_t t = 0; t + 1 < r->walk_events.size(); t += 2) {
+            if (cudaEventElapsedTime(&ms, r->walk_events[t], r->walk_events[t + 1]) == cudaSuccess) kms += ms;
+        }
+        info->sources = S;
+        info->R = a->R;
+        info->topk = k;
+        info->nnz = (int64_t)base;
+        info->steps = c[0];
+        info->walks = (uint64_t)S * a->R;
+        info->kernel_ms = kms;
+        info->sectors = c[2];
+        info->run_ms = 0.f;
+    }
+    return finish(PPR_OK);
 }
 
 int ppr_workspace_size(const ppr_graph *g, const ppr_run_args *a, size_t *bytes)

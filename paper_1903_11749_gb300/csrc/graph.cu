@@ -931,11 +931,11 @@ int build_segments(ppr_graph *g, uint32_t T, cudaStream_t st)
 //   large edge j (not the last): thr = W - (D_q - E_j) with q = min{q : D_q >= E_j},
 //                                alias = large edge j + 1
 //   last large edge, edges with p = W: thr = W, alias = itself.
-// Rows of at most 32 edges run the pairing rounds serially, one thread per
-// row; longer rows compute the closed form with a warp (up to 2048 edges) or
+// Rows of at most 256 edges run the pairing rounds serially, one thread per
+// row; longer rows compute the closed form with a warp (up to 8192 edges) or
 // a block per row (alias_row_group).
 
-constexpr uint32_t kAliasSmall = 32, kAliasMid = 2048;
+constexpr uint32_t kAliasInline = 32, kAliasSerial = 256, kAliasMid = 8192;
 
 struct AliasArgs {
     int64_t n;
@@ -944,14 +944,56 @@ struct AliasArgs {
     const uint64_t *off;  // first slot of each row (exclusive scan of degrees)
     NodeRec *anode;
     AliasRec *slots;
-    uint32_t *idx;        // per slot of a long row: small edges from the front, large from the back
+    uint2 *ic;            // per slot of a long row: (edge, col) of the small edges from the front,
+                          // of the large edges from the back
     uint64_t *sum;        // their running sums D_i / E_j
-    uint32_t *list;       // long rows: warp rows from the front, block rows from the back
-    uint32_t *counts;     // [0] warp rows, [1] block rows
+    uint32_t *list;       // rows per tier: [0, n) one thread, [n, 2n) one warp, [2n, 3n) one block
+    uint32_t *counts;     // rows in each list
 };
 
 __device__ __forceinline__ uint32_t row_degree(const NodeRec &r) { return (uint32_t)(r.word0 >> 40) & kCountMask; }
 
+// The pairing rounds of one row, serially (row of d >= 2 edges, slots from o).
+__device__ void alias_row_serial(const AliasArgs &A, const NodeRec &nr, uint32_t d, uint64_t o)
+{
+    const uint64_t W = nr.total & 0xffffffffull;
+    const uint64_t eb = NarrowEdges::edge_base(nr.word0 & kBeginMask, d);
+    auto pw = [&](uint32_t i) -> uint64_t {
+        const uint32_t hi = A.edges[eb + i].P, lo = i ? A.edges[eb + i - 1].P : 0u;
+        return (uint64_t)d * (hi - lo);
+    };
+    for (uint32_t i = 0; i < d; ++i) {
+        const int32_t c = A.edges[eb + i].col;
+        A.slots[o + i] = AliasRec{(uint32_t)W, c, c, 0u};
+    }
+    auto next_small = [&](uint32_t i) { while (i < d && pw(i) >= W) ++i; return i; };
+    auto next_large = [&](uint32_t j) { while (j < d && pw(j) <= W) ++j; return j; };
+    uint32_t i = next_small(0), j = next_large(0);
+    if (j >= d) return;
+    uint64_t py = pw(j);  // remaining p of the current large edge
+    for (uint32_t guard = 0; guard < 2 * d; ++guard) {
+        if (py > W) {  // x = next small edge, y = j
+            if (i >= d) break;
+            const uint64_t px = pw(i);
+            A.slots[o + i].thr = (uint32_t)px;
+            A.slots[o + i].alias_col = A.edges[eb + j].col;
+            py -= W - px;
+            i = next_small(i + 1);
+        } else {  // j leaves S^l; if it dropped below W it is the next x
+            const uint32_t j2 = next_large(j + 1);
+            if (j2 >= d) break;  // py == W here: the last large edge
+            if (py < W) {
+                A.slots[o + j].thr = (uint32_t)py;
+                A.slots[o + j].alias_col = A.edges[eb + j2].col;
+            }
+            py = pw(j2) - (W - py);
+            j = j2;
+        }
+    }
+}
+
+// Node records of the alias layout for every row; rows of at most 32 edges
+// are built here, longer ones are listed for their tier.
 __global__ void __launch_bounds__(256) k_alias_small(AliasArgs A)
 {
     for (int64_t u = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; u < A.n; u += (int64_t)gridDim.x * blockDim.x) {
@@ -963,45 +1005,22 @@ __global__ void __launch_bounds__(256) k_alias_small(AliasArgs A)
         r.total = d < 2 ? nr.total : (nr.total & 0xffffffffull);  // 0, the single target, or W
         A.anode[u] = r;
         if (d < 2) continue;
-        if (d > kAliasSmall) {
-            if (d <= kAliasMid) A.list[atomicAdd(&A.counts[0], 1u)] = (uint32_t)u;
-            else A.list[A.n - 1 - atomicAdd(&A.counts[1], 1u)] = (uint32_t)u;
+        if (d > kAliasInline) {
+            const uint32_t tier = d <= kAliasSerial ? 0 : (d <= kAliasMid ? 1 : 2);
+            A.list[(int64_t)tier * A.n + atomicAdd(&A.counts[tier], 1u)] = (uint32_t)u;
             continue;
         }
-        const uint64_t W = nr.total & 0xffffffffull;
-        const uint64_t eb = NarrowEdges::edge_base(nr.word0 & kBeginMask, d);
-        auto pw = [&](uint32_t i) -> uint64_t {
-            const uint32_t hi = A.edges[eb + i].P, lo = i ? A.edges[eb + i - 1].P : 0u;
-            return (uint64_t)d * (hi - lo);
-        };
-        for (uint32_t i = 0; i < d; ++i) {
-            const int32_t c = A.edges[eb + i].col;
-            A.slots[o + i] = AliasRec{(uint32_t)W, c, c, 0u};
-        }
-        auto next_small = [&](uint32_t i) { while (i < d && pw(i) >= W) ++i; return i; };
-        auto next_large = [&](uint32_t j) { while (j < d && pw(j) <= W) ++j; return j; };
-        uint32_t i = next_small(0), j = next_large(0);
-        if (j >= d) continue;
-        uint64_t py = pw(j);  // remaining p of the current large edge
-        for (uint32_t guard = 0; guard < 2 * d; ++guard) {
-            if (py > W) {  // x = next small edge, y = j
-                if (i >= d) break;
-                const uint64_t px = pw(i);
-                A.slots[o + i].thr = (uint32_t)px;
-                A.slots[o + i].alias_col = A.edges[eb + j].col;
-                py -= W - px;
-                i = next_small(i + 1);
-            } else {  // j leaves S^l; if it dropped below W it is the next x
-                const uint32_t j2 = next_large(j + 1);
-                if (j2 >= d) break;  // py == W here: the last large edge
-                if (py < W) {
-                    A.slots[o + j].thr = (uint32_t)py;
-                    A.slots[o + j].alias_col = A.edges[eb + j2].col;
-                }
-                py = pw(j2) - (W - py);
-                j = j2;
-            }
-        }
+        alias_row_serial(A, nr, d, o);
+    }
+}
+
+__global__ void __launch_bounds__(256) k_alias_serial(AliasArgs A)
+{
+    const uint32_t rows = A.counts[0];
+    for (uint32_t t = blockIdx.x * blockDim.x + threadIdx.x; t < rows; t += gridDim.x * blockDim.x) {
+        const uint32_t u = A.list[t];
+        const NodeRec nr = A.node[u];
+        alias_row_serial(A, nr, row_degree(nr), A.off[u]);
     }
 }
 
@@ -1071,16 +1090,22 @@ __device__ void alias_row_group(const AliasArgs &A, int64_t u, uint32_t rank, ui
     uint64_t v[3] = {0, 0, 0};  // small | large << 32 counts, sum of W - p, sum of p - W
     {
         uint32_t prevP = lo ? A.edges[eb + lo - 1].P : 0u;
-        for (uint32_t i = lo; i < hi; ++i) {
-            const uint32_t P = A.edges[eb + i].P;
-            const uint64_t p = (uint64_t)d * (P - prevP);
-            prevP = P;
-            if (p < W) {
-                v[0] += 1;
-                v[1] += W - p;
-            } else if (p > W) {
-                v[0] += 1ull << 32;
-                v[2] += p - W;
+        for (uint32_t i0 = lo; i0 < hi; i0 += 8) {
+            uint32_t Pv[8];  // eight loads in flight before their use
+#pragma unroll
+            for (int q = 0; q < 8; ++q) Pv[q] = i0 + q < hi ? A.edges[eb + i0 + q].P : 0u;
+#pragma unroll
+            for (int q = 0; q < 8; ++q) {
+                if (i0 + q >= hi) break;
+                const uint64_t p = (uint64_t)d * (Pv[q] - prevP);
+                prevP = Pv[q];
+                if (p < W) {
+                    v[0] += 1;
+                    v[1] += W - p;
+                } else if (p > W) {
+                    v[0] += 1ull << 32;
+                    v[2] += p - W;
+                }
             }
         }
     }
@@ -1091,21 +1116,32 @@ __device__ void alias_row_group(const AliasArgs &A, int64_t u, uint32_t rank, ui
     uint64_t Dr = v[1] - own[1], Er = v[2] - own[2];
     {
         uint32_t prevP = lo ? A.edges[eb + lo - 1].P : 0u;
-        for (uint32_t i = lo; i < hi; ++i) {
-            const EdgeN rec = A.edges[eb + i];
-            const uint64_t p = (uint64_t)d * (rec.P - prevP);
-            prevP = rec.P;
-            A.slots[o + i] = AliasRec{(uint32_t)W, rec.col, rec.col, 0u};
-            if (p < W && ks < d) {
-                Dr += W - p;
-                A.idx[o + ks] = i;
-                A.sum[o + ks] = Dr;
-                ++ks;
-            } else if (p > W && kl < d) {
-                Er += p - W;
-                A.idx[o + d - 1 - kl] = i;
-                A.sum[o + d - 1 - kl] = Er;
-                ++kl;
+        for (uint32_t i0 = lo; i0 < hi; i0 += 8) {
+            EdgeN rv[8];
+#pragma unroll
+            for (int q = 0; q < 8; ++q) {
+                if (i0 + q < hi) rv[q] = A.edges[eb + i0 + q];
+                else rv[q] = EdgeN{0u, 0};
+            }
+#pragma unroll
+            for (int q = 0; q < 8; ++q) {
+                const uint32_t i = i0 + q;
+                if (i >= hi) break;
+                const EdgeN rec = rv[q];
+                const uint64_t p = (uint64_t)d * (rec.P - prevP);
+                prevP = rec.P;
+                A.slots[o + i] = AliasRec{(uint32_t)W, rec.col, rec.col, 0u};
+                if (p < W && ks < d) {
+                    Dr += W - p;
+                    A.ic[o + ks] = make_uint2(i, (uint32_t)rec.col);
+                    A.sum[o + ks] = Dr;
+                    ++ks;
+                } else if (p > W && kl < d) {
+                    Er += p - W;
+                    A.ic[o + d - 1 - kl] = make_uint2(i, (uint32_t)rec.col);
+                    A.sum[o + d - 1 - kl] = Er;
+                    ++kl;
+                }
             }
         }
     }
@@ -1114,7 +1150,7 @@ __device__ void alias_row_group(const AliasArgs &A, int64_t u, uint32_t rank, ui
     if (a == 0 || b == 0 || (uint64_t)a + b > d) return;  // every p equals W (the sums force a > 0 iff b > 0)
     auto E = [&](uint32_t j) { return A.sum[o + d - 1 - j]; };
     auto D = [&](uint32_t q) { return A.sum[o + q]; };
-    auto large_col = [&](uint32_t j) { return A.slots[o + A.idx[o + d - 1 - j]].col; };
+    auto large_col = [&](uint32_t j) { return (int32_t)A.ic[o + d - 1 - j].y; };
     // small edges t in [t0, t1): donor = first large j with E_j > D_(t-1)
     {
         const uint32_t share = (a + NT - 1) / NT;
@@ -1131,7 +1167,7 @@ __device__ void alias_row_group(const AliasArgs &A, int64_t u, uint32_t rank, ui
             for (uint32_t t = t0; t < t1; ++t) {
                 while (j + 1 < b && E(j) <= prev) ++j;
                 const uint64_t Dt = D(t);
-                const uint32_t e = A.idx[o + t];
+                const uint32_t e = A.ic[o + t].x;
                 A.slots[o + e].thr = (uint32_t)(W - (Dt - prev));
                 A.slots[o + e].alias_col = large_col(j);
                 prev = Dt;
@@ -1156,7 +1192,7 @@ __device__ void alias_row_group(const AliasArgs &A, int64_t u, uint32_t rank, ui
                 while (q + 1 < a && D(q) < Ej) ++q;
                 const uint64_t th = W - (D(q) - Ej);
                 if (th < W) {
-                    const uint32_t e = A.idx[o + d - 1 - j];
+                    const uint32_t e = A.ic[o + d - 1 - j].x;
                     A.slots[o + e].thr = (uint32_t)th;
                     A.slots[o + e].alias_col = large_col(j + 1);
                 }
@@ -1169,17 +1205,17 @@ __global__ void __launch_bounds__(256) k_alias_mid(AliasArgs A)
 {
     const uint32_t lane = threadIdx.x & 31;
     const int64_t warps = (int64_t)gridDim.x * (blockDim.x >> 5);
-    const uint32_t rows = A.counts[0];
+    const uint32_t rows = A.counts[1];
     for (int64_t t = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5; t < rows; t += warps)
-        alias_row_group<32>(A, A.list[t], lane, nullptr);
+        alias_row_group<32>(A, A.list[A.n + t], lane, nullptr);
 }
 
 __global__ void __launch_bounds__(512) k_alias_big(AliasArgs A)
 {
     __shared__ uint64_t s[3 * 16];
-    const uint32_t rows = A.counts[1];
+    const uint32_t rows = A.counts[2];
     for (uint32_t t = blockIdx.x; t < rows; t += gridDim.x) {
-        alias_row_group<512>(A, A.list[A.n - 1 - t], threadIdx.x, s);
+        alias_row_group<512>(A, A.list[2 * A.n + t], threadIdx.x, s);
         __syncthreads();
     }
 }
@@ -1199,14 +1235,15 @@ int build_alias(ppr_graph *g, cudaStream_t st)
     }
     const int64_t n = g->n, m = std::max<int64_t>(g->m, 1);
     const int64_t tiles = (n + kScanTile - 1) / kScanTile;
-    uint32_t *deg = nullptr, *idx = nullptr, *list = nullptr, *counts = nullptr;
+    uint32_t *deg = nullptr, *list = nullptr, *counts = nullptr;
+    uint2 *ic = nullptr;
     uint64_t *off = nullptr, *tmp = nullptr, *sum = nullptr;
     int rc;
     auto cleanup = [&]() {
         dev_free(deg, st);
         dev_free(off, st);
         dev_free(tmp, st);
-        dev_free(idx, st);
+        dev_free(ic, st);
         dev_free(sum, st);
         dev_free(list, st);
         dev_free(counts, st);
@@ -1214,10 +1251,10 @@ int build_alias(ppr_graph *g, cudaStream_t st)
     if ((rc = dev_alloc((void **)&deg, sizeof(uint32_t) * n, "alias degrees", st)) ||
         (rc = dev_alloc((void **)&off, sizeof(uint64_t) * (n + 1), "alias offsets", st)) ||
         (rc = dev_alloc((void **)&tmp, sizeof(uint64_t) * (tiles + 2), "scan scratch", st)) ||
-        (rc = dev_alloc((void **)&idx, sizeof(uint32_t) * m, "alias scratch", st)) ||
+        (rc = dev_alloc((void **)&ic, sizeof(uint2) * m, "alias scratch", st)) ||
         (rc = dev_alloc((void **)&sum, sizeof(uint64_t) * m, "alias scratch", st)) ||
-        (rc = dev_alloc((void **)&list, sizeof(uint32_t) * n, "long-row list", st)) ||
-        (rc = dev_alloc((void **)&counts, sizeof(uint32_t) * 2, "long-row counts", st)))
+        (rc = dev_alloc((void **)&list, sizeof(uint32_t) * 3 * n, "long-row lists", st)) ||
+        (rc = dev_alloc((void **)&counts, sizeof(uint32_t) * 3, "long-row counts", st)))
         return cleanup(), rc;
     if ((rc = dev_alloc((void **)&g->alias.node, sizeof(NodeRec) * n, "alias node records", st))) return cleanup(), rc;
     if ((rc = dev_alloc((void **)&g->alias.slots, sizeof(AliasRec) * m, "alias slots", st))) {
@@ -1225,18 +1262,20 @@ int build_alias(ppr_graph *g, cudaStream_t st)
         g->alias.node = nullptr;
         return cleanup(), rc;
     }
-    cudaError_t e = cudaMemsetAsync(counts, 0, sizeof(uint32_t) * 2, st);
+    cudaError_t e = cudaMemsetAsync(counts, 0, sizeof(uint32_t) * 3, st);
     const int blocks = (int)std::max<int64_t>(1, std::min<int64_t>((n + 255) / 256, (int64_t)g->ctx->sms * 16));
     if (e == cudaSuccess) {
         k_alias_degrees<<<blocks, 256, 0, st>>>(n, g->node, deg);
         note_launch();
         exclusive_scan_u32(deg, n, off, tmp, st);
-        AliasArgs A{n, g->node, (const EdgeN *)g->edges, off, g->alias.node, g->alias.slots, idx, sum, list, counts};
+        AliasArgs A{n, g->node, (const EdgeN *)g->edges, off, g->alias.node, g->alias.slots, ic, sum, list, counts};
         k_alias_small<<<blocks, 256, 0, st>>>(A);
+        note_launch();
+        k_alias_serial<<<g->ctx->sms * 8, 256, 0, st>>>(A);
         note_launch();
         k_alias_mid<<<g->ctx->sms * 8, 256, 0, st>>>(A);
         note_launch();
-        k_alias_big<<<g->ctx->sms, 512, 0, st>>>(A);
+        k_alias_big<<<g->ctx->sms * 2, 512, 0, st>>>(A);
         note_launch();
         e = cudaGetLastError();
     }

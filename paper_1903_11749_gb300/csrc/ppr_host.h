@@ -49,6 +49,8 @@ struct ppr_ctx {
     int sms = 0;
     size_t smem_optin = 0;
     ppr::Server *server = nullptr;  // serving state (ppr_serve_start)
+    cudaStream_t copy_stream = nullptr;  // output copies of ppr_run_to_host
+    unsigned long long *pinned = nullptr;  // page-locked words for per-batch totals
 };
 
 struct ppr_graph {

@@ -101,6 +101,9 @@ _SIGS = {
     "ppr_submit": (C.c_int, [C.c_void_p, C.c_void_p, C.c_int64, C.c_double, C.c_uint32, C.c_uint64, C.c_int32,
                              C.POINTER(C.c_uint64)]),
     "ppr_poll": (C.c_int, [C.c_void_p, C.c_uint64, C.c_void_p, C.c_void_p, C.c_int64, C.POINTER(QueryStats)]),
+    "ppr_run_to_host": (C.c_int, [C.c_void_p, C.c_void_p, C.POINTER(RunArgs), C.c_int32, C.c_void_p, C.c_void_p,
+                                  C.c_void_p, C.c_int64, C.POINTER(C.c_int64), C.c_void_p, C.c_void_p,
+                                  C.POINTER(ResultInfo)]),
     "ppr_run_into": (C.c_int, [C.c_void_p, C.c_void_p, C.POINTER(RunArgs), C.c_void_p, C.c_size_t, C.c_void_p,
                                C.c_void_p, C.c_void_p, C.c_uint32, C.c_void_p, C.c_void_p]),
 }
@@ -295,6 +298,22 @@ class Graph:
         n = C.c_size_t()
         _check(lib().ppr_workspace_size(self.h, C.byref(a), C.byref(n)))
         return n.value
+
+    def run_to_host(self, row_ptr, col, cnt, topk_idx=None, topk_cnt=None, parts=0, **kw):
+        """Runs a source range and writes rows (and top-k) into host arrays,
+        output copies pipelined against the walks; returns (nnz, info)."""
+        a = self._args(**kw)
+        for arr in (row_ptr, col, cnt, topk_idx, topk_cnt):
+            if arr is not None and _ptr(arr)[1]:
+                raise ValueError("run_to_host writes host memory")
+        ti = _ptr(topk_idx)[0] if topk_idx is not None else None
+        tc = _ptr(topk_cnt)[0] if topk_cnt is not None else None
+        cap = col.shape[0] if hasattr(col, "shape") else len(col)
+        nnz = C.c_int64()
+        info = ResultInfo()
+        _check(lib().ppr_run_to_host(self.ctx.h, self.h, C.byref(a), parts, _ptr(row_ptr)[0], _ptr(col)[0],
+                                     _ptr(cnt)[0], cap, C.byref(nnz), ti, tc, C.byref(info)))
+        return nnz.value, info
 
     def run_into(self, workspace, nnz, cols, cnts, cap, topk_idx=None, topk_cnt=None, **kw):
         """Enqueues a run into caller-owned device tensors (no allocation; capturable)."""
