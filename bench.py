@@ -20,6 +20,7 @@ import argparse
 import hashlib
 import json
 import os
+import platform
 import statistics
 import subprocess
 import sys
@@ -171,6 +172,30 @@ def recorded_traffic(workload: str):
     return e.get("dram_bytes_per_launch")
 
 
+def host_cpu():
+    """CPU model and logical core count of the host the oracle runs on."""
+    model = platform.processor() or platform.machine()
+    try:
+        with open("/proc/cpuinfo") as f:
+            for line in f:
+                key = line.split(":")[0].strip().lower()
+                if key in ("model name", "cpu model", "hardware"):
+                    model = line.split(":", 1)[1].strip()
+                    break
+    except OSError:
+        pass
+    if model in ("", platform.machine()):
+        try:
+            out = subprocess.run(["lscpu"], capture_output=True, text=True, timeout=10).stdout
+            for line in out.splitlines():
+                if line.lower().startswith("model name"):
+                    model = line.split(":", 1)[1].strip()
+                    break
+        except (OSError, subprocess.SubprocessError):
+            pass
+    return {"model": model, "machine": platform.machine(), "nproc": os.cpu_count()}
+
+
 def cpu_baseline(g, wl, budget_s: float = 15.0):
     """The oracle as it stands (single-threaded C + numpy counting) on an evenly
     strided sample of sources; returns steps/s and a description."""
@@ -198,6 +223,7 @@ def cpu_baseline(g, wl, budget_s: float = 15.0):
         total_walks += e.size
     t_all = time.perf_counter() - t0
     return {"value": total_steps / t_all, "unit": "walk steps/s", "cores": 1, "kind": "oracle",
+            "host": host_cpu(),
             "walks_per_s": total_walks / t_all,
             "sample": f"{total_walks // wl['R']} sources in blocks of 64 strided over all {g.n} sources, "
                       f"{total_walks} walks, {total_steps} steps, {t_all:.1f} s"}
@@ -696,6 +722,8 @@ def main():
     ap.add_argument("--warps-per-block", type=int, default=0)
     ap.add_argument("--chunk-sources", type=int, default=0)
     ap.add_argument("--large-degree", type=int, default=0)
+    ap.add_argument("--l2-persist", type=int, default=0, choices=[0, 1],
+                    help="walker launches keep the node records persisting in L2")
     ap.add_argument("--serve-queries", type=int, default=2000)
     ap.add_argument("--serve-warmup", type=int, default=200)
     ap.add_argument("--serve-streams", type=int, default=4)
@@ -730,7 +758,7 @@ def main():
     g = I.workload_graph(base_graph(args.workload))
     a, b, rank_tag = rank_workload(g.n, rank, world)
     tune = dict(warps_per_block=args.warps_per_block, chunk_sources=args.chunk_sources,
-                large_degree=args.large_degree)
+                large_degree=args.large_degree, l2_persist=args.l2_persist)
 
     ctx = ppr.Context(local)
     stream = torch.cuda.current_stream(dev)
@@ -878,6 +906,25 @@ def main():
                 "alg_bytes_per_launch": alg_bytes, "kernel_ms": kms, "walk_and_reduce_ms": statistics.mean(run_ms),
                 "sectors_per_draw": sectors_per_pass / max(draws_per_pass, 1)}
 
+    # practical ceilings: dependent random 32-byte sector reads over a buffer
+    # the size of the walked layout, and Philox draws with no memory traffic
+    G = ctx.load_graph(g.n, d_rp, d_col, d_w, stream=stream, m=g.m)
+    if wl.get("sampler", 0) == 1:
+        G.run(alpha=wl["alpha"], R=1, seed=1, src_begin=0, src_end=1, sampler=1, stream=stream)  # alias tables
+    footprint = max(int(G.info().device_bytes), 64 << 20)
+    del G
+    chains_s, _ = ctx.probe_rate(0, footprint)
+    gather_s, _ = ctx.probe_rate(2, footprint)
+    philox_s, _ = ctx.probe_rate(1)
+    walker_sectors_s = sectors_per_pass / (kms / 1e3)
+    probe = {"buffer_bytes": footprint,
+             "gather_sectors_per_s": gather_s, "gather_gbs": gather_s * 32 / 1e9,
+             "chains_sectors_per_s": chains_s, "chains_gbs": chains_s * 32 / 1e9,
+             "philox_draws_per_s": philox_s, "walker_sectors_per_s": walker_sectors_s,
+             "walker_frac_of_gather": walker_sectors_s / gather_s,
+             "walker_draws_per_s_over_philox": (draws_per_pass / (kms / 1e3)) / philox_s,
+             "note": "uniform addresses over a buffer the size of the graph layout; the walks revisit hot nodes"}
+
     cpu = None
     if rank == 0 and world == 1 and not args.no_cpu_baseline:
         cpu = cpu_baseline(g, wl, args.cpu_budget)
@@ -894,7 +941,7 @@ def main():
                 "walks_per_s": walks_s, "steps_per_walk": steps_per_pass / max(walks_per_pass, 1),
                 "draws_per_s": draws_per_pass * args.steps * world / T_max,
                 "steps_counted": "plain-equivalent walks*2^32/T" if wl["segments"] else "draws (one per step)",
-                "roofline": roofline, "cpu_baseline": cpu, "e2e": e2e, "plain_kernel": plain,
+                "roofline": roofline, "probe": probe, "cpu_baseline": cpu, "e2e": e2e, "plain_kernel": plain,
                 "gpu_launches": launches, "clocks": clk}
         print(json.dumps(line))
     if world > 1:

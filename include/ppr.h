@@ -104,6 +104,9 @@ int64_t ppr_kernel_launches(void);
 /* Creates a context on CUDA device `device`; *out receives it.
  * PPR_ECUDA if the device cannot be used. */
 int ppr_create(int device, ppr_ctx **out);
+/* Stops serving and drops the caller's handle.  Graphs and results made in
+ * the context keep it alive until they are freed, so handles may be freed
+ * in any order; the handle itself must not be used again. */
 void ppr_destroy(ppr_ctx *ctx);
 
 /* Number of streaming multiprocessors of the context's device. */
@@ -153,6 +156,8 @@ typedef struct {
 } ppr_graph_info;
 
 int ppr_graph_get_info(const ppr_graph *g, ppr_graph_info *info);
+/* Frees the graph's device memory after waiting for the device to go idle
+ * (runs on any stream may still read it). */
 void ppr_free_graph(ppr_graph *g);
 
 /* Walker kernels. */
@@ -186,6 +191,9 @@ typedef struct {
                             its alias.  Same law, different counts.  Alias tables are built on
                             the first run that asks for them (every row total < 2^32; no
                             segment mode) */
+    int32_t l2_persist;  /* 1: walker launches mark the node records persisting in L2 (an
+                            access-policy window; the device's persisting set-aside is raised
+                            for this context on first use); 0: off.  Results are unchanged */
     void *stream;        /* cudaStream_t, NULL = legacy default stream */
 } ppr_run_args;
 
@@ -339,6 +347,32 @@ void ppr_free_result(ppr_result *r);
  */
 int ppr_run_noalloc(ppr_ctx *ctx, const ppr_graph *g, const ppr_run_args *args, uint32_t *nnz, int32_t *cols,
                     uint32_t *cnts, uint32_t cap, int32_t *topk_idx, uint32_t *topk_cnt);
+
+/* Fault injection for tests (host side; no device fault): after `after`
+ * further device allocations by this library, every allocation fails with
+ * PPR_ENOMEM as if the device were full, until the next call; after < 0
+ * turns it off.  Process-wide. */
+void ppr_debug_fail_allocs(int64_t after);
+
+/* ------------------------------------------------------------- probes ----
+ * Measurement beside the walk path; neither is part of a run.
+ *
+ * ppr_probe_philox: the device's Philox4x32-10 words (the generator of every
+ * walk step, Salmon et al., SC'11) for counters (c0 + i mod 2^32, c1, c2, c3),
+ * i in [0, count), key (seed mod 2^32, seed >> 32); out: host uint32[4*count],
+ * words x0..x3 of each counter in turn.  1 <= count <= 2^28.
+ *
+ * ppr_probe_rate: kind 0 = chains of dependent random 32-byte sector reads
+ * over a device buffer of `bytes` (the access pattern of a walk step on
+ * uniform addresses; one resident wave of threads, 256 reads per thread);
+ * kind 2 = independent random 32-byte sector reads, four in flight per
+ * thread (the random-access bandwidth for sector-sized reads); both give
+ * *per_second = sectors read per second.  kind 1 = Philox4x32-10 draws per
+ * second (bytes ignored).  *ms (may be NULL) = the timed kernel's duration.
+ * Allocates and frees its buffer on the legacy default stream.
+ */
+int ppr_probe_philox(ppr_ctx *ctx, uint64_t seed, const uint32_t counter[4], int64_t count, uint32_t *out);
+int ppr_probe_rate(ppr_ctx *ctx, int32_t kind, int64_t bytes, double *per_second, float *ms);
 
 /* ---------------------------------------------------------------- serving
  * Multi-source queries with continuous batching: a scheduler thread admits

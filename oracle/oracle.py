@@ -59,6 +59,7 @@ def lib():
         path = build()
         L = C.CDLL(path)
         L.ppr_oracle_philox4x32.argtypes = [C.c_void_p, C.c_void_p, C.c_int, C.c_void_p]
+        L.ppr_oracle_philox4x32_run.argtypes = [C.c_void_p, C.c_void_p, C.c_int64, C.c_void_p]
         L.ppr_oracle_philox4x64.argtypes = [C.c_void_p, C.c_void_p, C.c_int, C.c_void_p]
         L.ppr_oracle_mulhi64.argtypes = [C.c_uint64, C.c_uint64]
         L.ppr_oracle_mulhi64.restype = C.c_uint64
@@ -98,6 +99,15 @@ def philox4x32(ctr, key, rounds: int = 10) -> np.ndarray:
     k = np.ascontiguousarray(key, dtype=np.uint32)
     out = np.zeros(4, dtype=np.uint32)
     lib().ppr_oracle_philox4x32(_p(c), _p(k), rounds, _p(out))
+    return out
+
+
+def philox4x32_run(ctr, key, count: int) -> np.ndarray:
+    """Philox4x32-10 words uint32[count, 4] for counters (ctr[0] + i, ctr[1], ctr[2], ctr[3])."""
+    c = np.ascontiguousarray(ctr, dtype=np.uint32)
+    k = np.ascontiguousarray(key, dtype=np.uint32)
+    out = np.zeros((count, 4), dtype=np.uint32)
+    lib().ppr_oracle_philox4x32_run(_p(c), _p(k), count, _p(out))
     return out
 
 

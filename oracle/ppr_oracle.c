@@ -91,6 +91,15 @@ void ppr_oracle_philox4x32(const uint32_t ctr[4], const uint32_t key[2], int rou
     philox4x32(ctr, key, rounds, out);
 }
 
+/* Words of `count` consecutive counters: counter word 0 = ctr[0] + i (mod 2^32). */
+void ppr_oracle_philox4x32_run(const uint32_t ctr[4], const uint32_t key[2], int64_t count, uint32_t *out)
+{
+    for (int64_t i = 0; i < count; ++i) {
+        uint32_t c[4] = {ctr[0] + (uint32_t)i, ctr[1], ctr[2], ctr[3]};
+        philox4x32(c, key, 10, out + 4 * i);
+    }
+}
+
 void ppr_oracle_philox4x64(const uint64_t ctr[4], const uint64_t key[2], int rounds, uint64_t out[4])
 {
     philox4x64(ctr, key, rounds, out);

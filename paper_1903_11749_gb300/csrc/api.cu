@@ -41,9 +41,18 @@ int cuda_fail(cudaError_t e, const char *what)
 // Device memory comes from the device's default stream-ordered pool, which
 // the context sets to keep freed memory reserved: repeated runs reuse it
 // without cudaMalloc/cudaFree round trips to the driver.
+// Host-side fault injection (ppr_debug_fail_allocs): allocations left before
+// every further one fails; negative = off.
+static std::atomic<long long> g_allocs_left{-1};
+
 int dev_alloc(void **p, size_t bytes, const char *what, cudaStream_t st)
 {
     *p = nullptr;
+    if (g_allocs_left.load(std::memory_order_relaxed) >= 0 && g_allocs_left.fetch_sub(1) <= 0) {
+        g_allocs_left.store(0);
+        set_error("cannot allocate %zu bytes of device memory for %s: injected failure", bytes, what);
+        return PPR_ENOMEM;
+    }
     cudaError_t e = cudaMallocAsync(p, bytes > 0 ? bytes : 1, st);
     if (e != cudaSuccess) {
         cudaGetLastError();  // clear the sticky-free allocation error
@@ -76,6 +85,13 @@ __global__ void k_compact_rows(int64_t S, uint32_t cap, const uint32_t *nnz, con
     }
 }
 
+// Row starts of one batch made absolute: off[i] += base.
+__global__ void k_add_base(int64_t n, uint64_t *off, uint64_t base)
+{
+    for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x)
+        off[i] += base;
+}
+
 __global__ void k_dense(int64_t S, int64_t n, uint32_t cap, const uint32_t *nnz, const int32_t *cols,
                         const uint32_t *cnts, uint32_t *out)
 {
@@ -88,6 +104,22 @@ __global__ void k_dense(int64_t S, int64_t n, uint32_t cap, const uint32_t *nnz,
     }
 }
 
+void ctx_retain(ppr_ctx *ctx)
+{
+    if (ctx) ctx->refs.fetch_add(1);
+}
+
+void ctx_release(ppr_ctx *ctx)
+{
+    if (!ctx || ctx->refs.fetch_sub(1) != 1) return;
+    if (ctx->copy_stream || ctx->pinned) {
+        cudaSetDevice(ctx->device);
+        if (ctx->copy_stream) cudaStreamDestroy(ctx->copy_stream);
+        if (ctx->pinned) cudaFreeHost(ctx->pinned);
+        cudaGetLastError();
+    }
+    delete ctx;
+}
 }  // namespace ppr
 
 using namespace ppr;
@@ -96,6 +128,10 @@ static int set_device(const ppr_ctx *ctx)
 {
     cudaError_t e = cudaSetDevice(ctx->device);
     if (e != cudaSuccess) return cuda_fail(e, "cudaSetDevice");
+    // a sticky error means the context is lost; anything else is left over from
+    // an unchecked call (a release path) and must not fail this one
+    e = cudaGetLastError();
+    if (e != cudaSuccess && cudaPeekAtLastError() != cudaSuccess) return cuda_fail(e, "device");
     return PPR_OK;
 }
 
@@ -109,6 +145,8 @@ uint32_t ppr_alpha_threshold(double alpha)
     double t = alpha * 4294967296.0;  // exact: scaling by a power of two
     return (uint32_t)t;
 }
+
+void ppr_debug_fail_allocs(int64_t after) { g_allocs_left.store(after < 0 ? -1 : after); }
 
 int ppr_walks_for_accuracy(double eps, double delta, double p_f, uint64_t *omega)
 {
@@ -159,6 +197,18 @@ int ppr_create(int device, ppr_ctx **out)
     c->sms = v;
     cudaDeviceGetAttribute(&v, cudaDevAttrMaxSharedMemoryPerBlockOptin, device);
     c->smem_optin = (size_t)v;
+    cudaDeviceGetAttribute(&v, cudaDevAttrMaxPersistingL2CacheSize, device);
+    c->l2_persist_max = (size_t)v;
+    cudaDeviceGetAttribute(&v, cudaDevAttrMaxAccessPolicyWindowSize, device);
+    c->l2_window_max = (size_t)v;
+    ppr::preload_run_kernels();
+    {
+        cudaFuncAttributes fa;
+        cudaFuncGetAttributes(&fa, k_compact_rows);
+        cudaFuncGetAttributes(&fa, k_dense);
+        cudaFuncGetAttributes(&fa, k_add_base);
+        cudaGetLastError();
+    }
     cudaMemPool_t pool;
     if (cudaDeviceGetDefaultMemPool(&pool, device) == cudaSuccess) {
         uint64_t keep = ~0ull;  // keep freed blocks reserved for reuse
@@ -168,16 +218,12 @@ int ppr_create(int device, ppr_ctx **out)
     return PPR_OK;
 }
 
+
 void ppr_destroy(ppr_ctx *ctx)
 {
     if (!ctx) return;
     if (ctx->server) ppr_serve_stop(ctx);
-    if (ctx->copy_stream || ctx->pinned) {
-        cudaSetDevice(ctx->device);
-        if (ctx->copy_stream) cudaStreamDestroy(ctx->copy_stream);
-        if (ctx->pinned) cudaFreeHost(ctx->pinned);
-    }
-    delete ctx;
+    ctx_release(ctx);
 }
 
 int ppr_device_sms(const ppr_ctx *ctx) { return ctx ? ctx->sms : 0; }
@@ -203,7 +249,9 @@ static int load_common(ppr_ctx *ctx, int64_t n, int64_t m, const int64_t *row_pt
     }
     int rc = set_device(ctx);
     if (rc) return rc;
+    Range range("ppr_load_graph");
     g->ctx = ctx;
+    ctx_retain(ctx);
     g->n = n;
     g->m = m;
     g->stream = (cudaStream_t)stream;
@@ -285,7 +333,10 @@ int ppr_graph_get_info(const ppr_graph *g, ppr_graph_info *info)
 void ppr_free_graph(ppr_graph *g)
 {
     if (!g) return;
-    if (g->ctx) cudaSetDevice(g->ctx->device);
+    if (g->ctx) {
+        cudaSetDevice(g->ctx->device);
+        cudaDeviceSynchronize();  // runs on any stream may still read the graph
+    }
     dev_free(g->node, g->stream);
     dev_free(g->edges, g->stream);
     dev_free(g->seg.node, g->stream);
@@ -293,6 +344,8 @@ void ppr_free_graph(ppr_graph *g)
     dev_free(g->d_node_off, g->stream);
     dev_free(g->alias.node, g->stream);
     dev_free(g->alias.slots, g->stream);
+    cudaGetLastError();  // a failed free must not surface in a later call
+    ctx_release(g->ctx);
     delete g;
 }
 
@@ -321,6 +374,8 @@ static void result_release(ppr_result *r)
     if (r->ev_walk_end) cudaEventDestroy(r->ev_walk_end);
     if (r->ev_done) cudaEventDestroy(r->ev_done);
     for (cudaEvent_t ev : r->walk_events) cudaEventDestroy(ev);
+    cudaGetLastError();  // a failed free must not surface in a later call
+    ctx_release(r->ctx);
     delete r;
 }
 
@@ -357,7 +412,8 @@ static int check_run(const ppr_graph *g, const ppr_run_args *a, int64_t count, b
     if ((a->dangling != 0 && a->dangling != 1) || (a->segments != 0 && a->segments != 1) ||
         (a->kernel != PPR_KERNEL_PERSISTENT && a->kernel != PPR_KERNEL_PLAIN) || a->large_degree < 0 ||
         a->warps_per_block < 0 || a->warps_per_block > 32 || a->chunk_sources < 0 || a->max_batch_sources < 0 ||
-        (a->stats != 0 && a->stats != 1) || (a->sampler != 0 && a->sampler != 1)) {
+        (a->stats != 0 && a->stats != 1) || (a->sampler != 0 && a->sampler != 1) ||
+        (a->l2_persist != 0 && a->l2_persist != 1)) {
         set_error("invalid mode or tuning argument");
         return PPR_EINVAL;
     }
@@ -390,6 +446,7 @@ static int check_run(const ppr_graph *g, const ppr_run_args *a, int64_t count, b
     plan->chunk_sources = a->chunk_sources;
     plan->stats = a->stats != 0;
     plan->sampler = a->sampler;
+    plan->l2_persist = a->l2_persist == 1;
     return PPR_OK;
 }
 
@@ -420,6 +477,7 @@ static int run_common(ppr_ctx *ctx, const ppr_graph *g, const ppr_run_args *a, c
     RunPlan plan;
     int rc = check_run(g, a, count, list != nullptr, &plan);
     if (rc) return rc;
+    Range range(list ? "ppr_run_list" : "ppr_run");
     if (list) {
         for (int64_t i = 0; i < count; ++i)
             if (list[i] < 0 || list[i] >= g->n) {
@@ -434,6 +492,7 @@ static int run_common(ppr_ctx *ctx, const ppr_graph *g, const ppr_run_args *a, c
     ppr_result *r = new (std::nothrow) ppr_result;
     if (!r) return PPR_ENOMEM;
     r->ctx = ctx;
+    ctx_retain(ctx);
     r->g = g;
     r->stream = st;
     r->S = list ? count : a->src_end - a->src_begin;
@@ -520,13 +579,6 @@ int ppr_run_list(ppr_ctx *ctx, const ppr_graph *g, const ppr_run_args *a, const 
     return run_common(ctx, g, a, sources, count, out);
 }
 
-// Row starts of one batch made absolute: out[i] = in[i] + base.
-__global__ void k_add_base(int64_t n, uint64_t *off, uint64_t base)
-{
-    for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x)
-        off[i] += base;
-}
-
 int ppr_run_to_host(ppr_ctx *ctx, const ppr_graph *g, const ppr_run_args *a, int32_t parts, int64_t *row_ptr,
                     int32_t *col, uint32_t *cnt, int64_t cap, int64_t *nnz, int32_t *topk_idx, uint32_t *topk_cnt,
                     ppr_result_info *info)
@@ -543,6 +595,7 @@ int ppr_run_to_host(ppr_ctx *ctx, const ppr_graph *g, const ppr_run_args *a, int
     int rc = check_run(g, a, 0, false, &plan);
     if (rc) return rc;
     if ((rc = set_device(ctx))) return rc;
+    Range range("ppr_run_to_host");
     cudaStream_t st = (cudaStream_t)a->stream;
     if ((rc = prepare_tables(g, plan, st))) return rc;
     cudaError_t e = cudaSuccess;
@@ -577,6 +630,7 @@ int ppr_run_to_host(ppr_ctx *ctx, const ppr_graph *g, const ppr_run_args *a, int
     ppr_result *r = new (std::nothrow) ppr_result;  // owns the walker events and counters
     if (!r) return PPR_ENOMEM;
     r->ctx = ctx;
+    ctx_retain(ctx);
     r->stream = st;
     unsigned char *ws = nullptr;
     auto finish = [&](int code) {
@@ -624,6 +678,7 @@ int ppr_run_to_host(ppr_ctx *ctx, const ppr_graph *g, const ppr_run_args *a, int
     uint64_t base = 0;
     for (int64_t i = 0; i <= P; ++i) {
         if (i < P) {  // batch i: walk, reduce, compact on the run's stream
+            Range batch_range("batch");
             Slot &q = slot[i & 1];
             const int64_t b0 = i * B, nb = std::min<int64_t>(B, S - b0);
             if (i >= 2 && (e = cudaStreamWaitEvent(st, q.copied, 0)) != cudaSuccess)
@@ -934,6 +989,7 @@ int ppr_sparse_rows(const ppr_result *rc_, int64_t *row_ptr, int32_t *col, uint3
 {
     int rc = need_done(rc_);
     if (rc) return rc;
+    Range range("ppr_sparse_rows");
     ppr_result *r = const_cast<ppr_result *>(rc_);
     const bool dev_out = (flags & PPR_PTRS_DEVICE) != 0;
     cudaStream_t st = r->stream;

@@ -845,6 +845,7 @@ __global__ void k_seg_write(RowView<E> G, int64_t n, uint32_t T, const uint64_t 
 int build_segments(ppr_graph *g, uint32_t T, cudaStream_t st)
 {
     if (g->seg.T == T && g->seg.node) return PPR_OK;
+    Range range("segment tables");
     dev_free(g->seg.node, st);
     dev_free(g->seg.entries, st);
     g->seg = SegCache{};
@@ -935,7 +936,9 @@ int build_segments(ppr_graph *g, uint32_t T, cudaStream_t st)
 // row; longer rows compute the closed form with a warp (up to 8192 edges) or
 // a block per row (alias_row_group).
 
-constexpr uint32_t kAliasInline = 32, kAliasSerial = 256, kAliasMid = 8192;
+constexpr uint32_t kAliasInline = 32, kAliasSerial = 256, kAliasMid = 8192, kAliasHuge = 65536;
+constexpr uint32_t kAliasMaxHuge = 4096;  // rows taken by the tile path; more go to the block tier
+constexpr uint32_t kTileEdges = 8192;     // edges per tile block (256 threads x 32)
 
 struct AliasArgs {
     int64_t n;
@@ -948,7 +951,8 @@ struct AliasArgs {
                           // of the large edges from the back
     uint64_t *sum;        // their running sums D_i / E_j
     uint32_t *list;       // rows per tier: [0, n) one thread, [n, 2n) one warp, [2n, 3n) one block
-    uint32_t *counts;     // rows in each list
+    uint32_t *counts;     // rows in each list; [3] rows offered to the tile path
+    uint2 *huge;          // tile-path rows (node, degree), kAliasMaxHuge entries
 };
 
 __device__ __forceinline__ uint32_t row_degree(const NodeRec &r) { return (uint32_t)(r.word0 >> 40) & kCountMask; }
@@ -1006,6 +1010,13 @@ __global__ void __launch_bounds__(256) k_alias_small(AliasArgs A)
         A.anode[u] = r;
         if (d < 2) continue;
         if (d > kAliasInline) {
+            if (d > kAliasHuge) {
+                const uint32_t k = atomicAdd(&A.counts[3], 1u);
+                if (k < kAliasMaxHuge) {
+                    A.huge[k] = make_uint2((uint32_t)u, d);
+                    continue;
+                }
+            }
             const uint32_t tier = d <= kAliasSerial ? 0 : (d <= kAliasMid ? 1 : 2);
             A.list[(int64_t)tier * A.n + atomicAdd(&A.counts[tier], 1u)] = (uint32_t)u;
             continue;
@@ -1220,6 +1231,209 @@ __global__ void __launch_bounds__(512) k_alias_big(AliasArgs A)
     }
 }
 
+// ------------------------------------------------ alias tables: tile path ----
+// Rows above kAliasHuge edges are cut into tiles of kTileEdges edges, one
+// block per tile, so a hub does not leave one block working while the GPU
+// idles: (1) every tile totals its small/large counts and running-sum parts,
+// (2) one warp per row scans its tiles' totals, (3) every tile writes its
+// small and large edges with their running sums to scratch, (4) merge chunks
+// of kTileEdges small (or large) edges each find their partners as in
+// alias_row_group.
+
+struct HugeRow {
+    uint32_t u, d;
+    uint32_t tile0, ntiles;  // tiles of the row in the tile table
+    uint32_t chunk0;         // first merge chunk (2 * ntiles chunks: small edges, then large edges)
+};
+
+struct TileVal {
+    uint64_t cnt, D, E;  // small | large << 32 counts, sum of W - p, sum of p - W
+};
+
+struct TileArgs {
+    AliasArgs A;
+    const HugeRow *rows;
+    uint32_t nrows;
+    const uint2 *tiles;      // (row index, first edge of the tile within the row)
+    TileVal *tile_val;       // per tile: its totals, then (after the row scan) its exclusive offsets
+    ulonglong2 *row_ab;      // per row: small count, large count
+};
+
+// Per-thread run of up to 32 edges of a tile: fills the three totals.
+__device__ __forceinline__ void tile_run_totals(const AliasArgs &A, uint64_t eb, uint32_t d, uint64_t W, uint32_t lo,
+                                                uint32_t hi, uint64_t v[3])
+{
+    uint32_t prevP = lo ? A.edges[eb + lo - 1].P : 0u;
+    for (uint32_t i0 = lo; i0 < hi; i0 += 8) {
+        uint32_t Pv[8];
+#pragma unroll
+        for (int q = 0; q < 8; ++q) Pv[q] = i0 + q < hi ? A.edges[eb + i0 + q].P : 0u;
+#pragma unroll
+        for (int q = 0; q < 8; ++q) {
+            if (i0 + q >= hi) break;
+            const uint64_t p = (uint64_t)d * (Pv[q] - prevP);
+            prevP = Pv[q];
+            if (p < W) {
+                v[0] += 1;
+                v[1] += W - p;
+            } else if (p > W) {
+                v[0] += 1ull << 32;
+                v[2] += p - W;
+            }
+        }
+    }
+}
+
+__global__ void __launch_bounds__(256) k_alias_tile_totals(TileArgs T)
+{
+    __shared__ uint64_t s[3 * 8];
+    const AliasArgs &A = T.A;
+    const uint2 tl = T.tiles[blockIdx.x];
+    const HugeRow hr = T.rows[tl.x];
+    const NodeRec nr = A.node[hr.u];
+    const uint64_t W = nr.total & 0xffffffffull;
+    const uint64_t eb = NarrowEdges::edge_base(nr.word0 & kBeginMask, hr.d);
+    const uint32_t end = min(tl.y + kTileEdges, hr.d);
+    const uint32_t lo = min(tl.y + threadIdx.x * 32, end), hi = min(lo + 32, end);
+    uint64_t v[3] = {0, 0, 0};
+    tile_run_totals(A, eb, hr.d, W, lo, hi, v);
+    uint64_t tot[3];
+    group_scan3<256>(v, tot, s);
+    if (threadIdx.x == 0) T.tile_val[blockIdx.x] = TileVal{tot[0], tot[1], tot[2]};
+}
+
+// One warp per row: exclusive scan of its tiles' totals (in place), row counts.
+__global__ void k_alias_tile_scan(TileArgs T)
+{
+    const uint32_t r = blockIdx.x * (blockDim.x >> 5) + (threadIdx.x >> 5);
+    if (r >= T.nrows) return;
+    const uint32_t lane = threadIdx.x & 31;
+    const HugeRow hr = T.rows[r];
+    uint64_t carry[3] = {0, 0, 0};
+    for (uint32_t t0 = 0; t0 < hr.ntiles; t0 += 32) {
+        const uint32_t t = t0 + lane;
+        TileVal tv{0, 0, 0};
+        if (t < hr.ntiles) tv = T.tile_val[hr.tile0 + t];
+        uint64_t v[3] = {tv.cnt, tv.D, tv.E}, tot[3];
+        const uint64_t own[3] = {v[0], v[1], v[2]};
+        group_scan3<32>(v, tot, nullptr);
+        if (t < hr.ntiles)
+            T.tile_val[hr.tile0 + t] = TileVal{carry[0] + v[0] - own[0], carry[1] + v[1] - own[1],
+                                               carry[2] + v[2] - own[2]};
+        for (int k = 0; k < 3; ++k) carry[k] += tot[k];
+    }
+    if (lane == 0) T.row_ab[r] = make_ulonglong2(carry[0] & 0xffffffffull, carry[0] >> 32);
+}
+
+__global__ void __launch_bounds__(256) k_alias_tile_write(TileArgs T)
+{
+    __shared__ uint64_t s[3 * 8];
+    const AliasArgs &A = T.A;
+    const uint2 tl = T.tiles[blockIdx.x];
+    const HugeRow hr = T.rows[tl.x];
+    const uint32_t d = hr.d;
+    const NodeRec nr = A.node[hr.u];
+    const uint64_t W = nr.total & 0xffffffffull;
+    const uint64_t eb = NarrowEdges::edge_base(nr.word0 & kBeginMask, d);
+    const uint64_t o = A.off[hr.u];
+    const uint32_t end = min(tl.y + kTileEdges, d);
+    const uint32_t lo = min(tl.y + threadIdx.x * 32, end), hi = min(lo + 32, end);
+    uint64_t v[3] = {0, 0, 0};
+    tile_run_totals(A, eb, d, W, lo, hi, v);
+    const uint64_t own[3] = {v[0], v[1], v[2]};
+    uint64_t tot[3];
+    group_scan3<256>(v, tot, s);
+    const TileVal base = T.tile_val[blockIdx.x];  // the tile's exclusive offsets within the row
+    uint64_t ks = (base.cnt & 0xffffffffull) + ((v[0] - own[0]) & 0xffffffffull);
+    uint64_t kl = (base.cnt >> 32) + ((v[0] - own[0]) >> 32);
+    uint64_t Dr = base.D + v[1] - own[1], Er = base.E + v[2] - own[2];
+    uint32_t prevP = lo ? A.edges[eb + lo - 1].P : 0u;
+    for (uint32_t i = lo; i < hi; ++i) {
+        const EdgeN rec = A.edges[eb + i];
+        const uint64_t p = (uint64_t)d * (rec.P - prevP);
+        prevP = rec.P;
+        A.slots[o + i] = AliasRec{(uint32_t)W, rec.col, rec.col, 0u};
+        if (p < W && ks < d) {
+            Dr += W - p;
+            A.ic[o + ks] = make_uint2(i, (uint32_t)rec.col);
+            A.sum[o + ks] = Dr;
+            ++ks;
+        } else if (p > W && kl < d) {
+            Er += p - W;
+            A.ic[o + d - 1 - kl] = make_uint2(i, (uint32_t)rec.col);
+            A.sum[o + d - 1 - kl] = Er;
+            ++kl;
+        }
+    }
+}
+
+// Merge chunk c of a row: chunks [0, ntiles) cover small edges
+// [c * kTileEdges, ...), chunks [ntiles, 2 ntiles) cover large edges (the
+// last large edge keeps thr = W).  Each thread takes 32 consecutive ones.
+__global__ void __launch_bounds__(256) k_alias_tile_merge(TileArgs T)
+{
+    const AliasArgs &A = T.A;
+    uint32_t lo = 0, hi = T.nrows;  // row of this chunk: last row with chunk0 <= blockIdx.x
+    while (hi - lo > 1) {
+        const uint32_t mid = (lo + hi) >> 1;
+        if (T.rows[mid].chunk0 <= blockIdx.x) lo = mid;
+        else hi = mid;
+    }
+    const HugeRow hr = T.rows[lo];
+    const uint32_t c = blockIdx.x - hr.chunk0;
+    if (c >= 2 * hr.ntiles) return;
+    const ulonglong2 ab = T.row_ab[lo];
+    const uint32_t a = (uint32_t)ab.x, b = (uint32_t)ab.y, d = hr.d;
+    if (a == 0 || b == 0 || (uint64_t)a + b > d) return;
+    const NodeRec nr = A.node[hr.u];
+    const uint64_t W = nr.total & 0xffffffffull;
+    const uint64_t o = A.off[hr.u];
+    auto E = [&](uint32_t j) { return A.sum[o + d - 1 - j]; };
+    auto D = [&](uint32_t q) { return A.sum[o + q]; };
+    if (c < hr.ntiles) {  // small edges t in [t0, t1): donor = first large j with E_j > D_(t-1)
+        const uint32_t t0 = min(c * kTileEdges + threadIdx.x * 32, a), t1 = min(t0 + 32, min((c + 1) * kTileEdges, a));
+        if (t0 >= t1) return;
+        uint64_t prev = t0 ? D(t0 - 1) : 0ull;
+        uint32_t jl = 0, jh = b - 1;
+        while (jl < jh) {
+            const uint32_t mid = (jl + jh) >> 1;
+            if (E(mid) > prev) jh = mid;
+            else jl = mid + 1;
+        }
+        uint32_t j = jl;
+        for (uint32_t t = t0; t < t1; ++t) {
+            while (j + 1 < b && E(j) <= prev) ++j;
+            const uint64_t Dt = D(t);
+            const uint32_t e = A.ic[o + t].x;
+            A.slots[o + e].thr = (uint32_t)(W - (Dt - prev));
+            A.slots[o + e].alias_col = (int32_t)A.ic[o + d - 1 - j].y;
+            prev = Dt;
+        }
+    } else {  // large edges j in [j0, j1), not the last: q = first small with D_q >= E_j
+        const uint32_t cl = c - hr.ntiles, nl = b - 1;
+        const uint32_t j0 = min(cl * kTileEdges + threadIdx.x * 32, nl), j1 = min(j0 + 32, min((cl + 1) * kTileEdges, nl));
+        if (j0 >= j1) return;
+        uint64_t Ej = E(j0);
+        uint32_t ql = 0, qh = a - 1;
+        while (ql < qh) {
+            const uint32_t mid = (ql + qh) >> 1;
+            if (D(mid) >= Ej) qh = mid;
+            else ql = mid + 1;
+        }
+        uint32_t q = ql;
+        for (uint32_t j = j0; j < j1; ++j) {
+            Ej = E(j);
+            while (q + 1 < a && D(q) < Ej) ++q;
+            const uint64_t th = W - (D(q) - Ej);
+            if (th < W) {
+                const uint32_t e = A.ic[o + d - 1 - j].x;
+                A.slots[o + e].thr = (uint32_t)th;
+                A.slots[o + e].alias_col = (int32_t)A.ic[o + d - 2 - j].y;
+            }
+        }
+    }
+}
+
 __global__ void k_alias_degrees(int64_t n, const NodeRec *node, uint32_t *deg)
 {
     for (int64_t u = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; u < n; u += (int64_t)gridDim.x * blockDim.x)
@@ -1229,6 +1443,7 @@ __global__ void k_alias_degrees(int64_t n, const NodeRec *node, uint32_t *deg)
 int build_alias(ppr_graph *g, cudaStream_t st)
 {
     if (g->alias.node) return PPR_OK;
+    Range range("alias tables");
     if (g->wide) {
         set_error("the alias sampler needs every row total below 2^32");
         return PPR_ENOTSUP;
@@ -1236,8 +1451,11 @@ int build_alias(ppr_graph *g, cudaStream_t st)
     const int64_t n = g->n, m = std::max<int64_t>(g->m, 1);
     const int64_t tiles = (n + kScanTile - 1) / kScanTile;
     uint32_t *deg = nullptr, *list = nullptr, *counts = nullptr;
-    uint2 *ic = nullptr;
+    uint2 *ic = nullptr, *huge = nullptr, *d_tiles = nullptr;
     uint64_t *off = nullptr, *tmp = nullptr, *sum = nullptr;
+    HugeRow *d_rows = nullptr;
+    TileVal *tile_val = nullptr;
+    ulonglong2 *row_ab = nullptr;
     int rc;
     auto cleanup = [&]() {
         dev_free(deg, st);
@@ -1247,6 +1465,20 @@ int build_alias(ppr_graph *g, cudaStream_t st)
         dev_free(sum, st);
         dev_free(list, st);
         dev_free(counts, st);
+        dev_free(huge, st);
+        dev_free(d_rows, st);
+        dev_free(d_tiles, st);
+        dev_free(tile_val, st);
+        dev_free(row_ab, st);
+    };
+    auto fail = [&](int code) {
+        cudaStreamSynchronize(st);
+        cleanup();
+        dev_free(g->alias.node, st);
+        dev_free(g->alias.slots, st);
+        g->alias.node = nullptr;
+        g->alias.slots = nullptr;
+        return code;
     };
     if ((rc = dev_alloc((void **)&deg, sizeof(uint32_t) * n, "alias degrees", st)) ||
         (rc = dev_alloc((void **)&off, sizeof(uint64_t) * (n + 1), "alias offsets", st)) ||
@@ -1254,40 +1486,77 @@ int build_alias(ppr_graph *g, cudaStream_t st)
         (rc = dev_alloc((void **)&ic, sizeof(uint2) * m, "alias scratch", st)) ||
         (rc = dev_alloc((void **)&sum, sizeof(uint64_t) * m, "alias scratch", st)) ||
         (rc = dev_alloc((void **)&list, sizeof(uint32_t) * 3 * n, "long-row lists", st)) ||
-        (rc = dev_alloc((void **)&counts, sizeof(uint32_t) * 3, "long-row counts", st)))
+        (rc = dev_alloc((void **)&counts, sizeof(uint32_t) * 4, "long-row counts", st)) ||
+        (rc = dev_alloc((void **)&huge, sizeof(uint2) * kAliasMaxHuge, "tile-path rows", st)))
         return cleanup(), rc;
     if ((rc = dev_alloc((void **)&g->alias.node, sizeof(NodeRec) * n, "alias node records", st))) return cleanup(), rc;
-    if ((rc = dev_alloc((void **)&g->alias.slots, sizeof(AliasRec) * m, "alias slots", st))) {
-        dev_free(g->alias.node, st);
-        g->alias.node = nullptr;
-        return cleanup(), rc;
-    }
-    cudaError_t e = cudaMemsetAsync(counts, 0, sizeof(uint32_t) * 3, st);
+    if ((rc = dev_alloc((void **)&g->alias.slots, sizeof(AliasRec) * m, "alias slots", st))) return fail(rc);
+    cudaError_t e = cudaMemsetAsync(counts, 0, sizeof(uint32_t) * 4, st);
+    if (e != cudaSuccess) return fail(cuda_fail(e, "memset"));
     const int blocks = (int)std::max<int64_t>(1, std::min<int64_t>((n + 255) / 256, (int64_t)g->ctx->sms * 16));
-    if (e == cudaSuccess) {
-        k_alias_degrees<<<blocks, 256, 0, st>>>(n, g->node, deg);
+    k_alias_degrees<<<blocks, 256, 0, st>>>(n, g->node, deg);
+    note_launch();
+    exclusive_scan_u32(deg, n, off, tmp, st);
+    AliasArgs A{n, g->node, (const EdgeN *)g->edges, off, g->alias.node, g->alias.slots, ic, sum, list, counts, huge};
+    k_alias_small<<<blocks, 256, 0, st>>>(A);
+    note_launch();
+    // rows for the tile path: their count and degrees decide the tile grid
+    uint32_t hc[4] = {0, 0, 0, 0};
+    e = cudaMemcpyAsync(hc, counts, sizeof(hc), cudaMemcpyDeviceToHost, st);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(st);
+    if (e != cudaSuccess) return fail(cuda_fail(e, "alias build"));
+    const uint32_t nh = std::min(hc[3], kAliasMaxHuge);
+    if (nh > 0) {
+        std::vector<uint2> hl(nh);
+        e = cudaMemcpy(hl.data(), huge, sizeof(uint2) * nh, cudaMemcpyDeviceToHost);
+        if (e != cudaSuccess) return fail(cuda_fail(e, "alias build"));
+        std::vector<HugeRow> rows(nh);
+        std::vector<uint2> tl;
+        uint32_t chunks = 0;
+        for (uint32_t r = 0; r < nh; ++r) {
+            const uint32_t d = hl[r].y, nt = (d + kTileEdges - 1) / kTileEdges;
+            rows[r] = HugeRow{hl[r].x, d, (uint32_t)tl.size(), nt, chunks};
+            for (uint32_t t = 0; t < nt; ++t) tl.push_back(make_uint2(r, t * kTileEdges));
+            chunks += 2 * nt;
+        }
+        const uint32_t nt = (uint32_t)tl.size();
+        if ((rc = dev_alloc((void **)&d_rows, sizeof(HugeRow) * nh, "tile-path rows", st)) ||
+            (rc = dev_alloc((void **)&d_tiles, sizeof(uint2) * nt, "tile table", st)) ||
+            (rc = dev_alloc((void **)&tile_val, sizeof(TileVal) * nt, "tile totals", st)) ||
+            (rc = dev_alloc((void **)&row_ab, sizeof(ulonglong2) * nh, "tile-path counts", st)))
+            return fail(rc);
+        e = cudaMemcpyAsync(d_rows, rows.data(), sizeof(HugeRow) * nh, cudaMemcpyHostToDevice, st);
+        if (e == cudaSuccess) e = cudaMemcpyAsync(d_tiles, tl.data(), sizeof(uint2) * nt, cudaMemcpyHostToDevice, st);
+        if (e != cudaSuccess) return fail(cuda_fail(e, "tile table upload"));
+        TileArgs T{A, d_rows, nh, d_tiles, tile_val, row_ab};
+        k_alias_tile_totals<<<nt, 256, 0, st>>>(T);
         note_launch();
-        exclusive_scan_u32(deg, n, off, tmp, st);
-        AliasArgs A{n, g->node, (const EdgeN *)g->edges, off, g->alias.node, g->alias.slots, ic, sum, list, counts};
-        k_alias_small<<<blocks, 256, 0, st>>>(A);
+        k_alias_tile_scan<<<(nh + 7) / 8, 256, 0, st>>>(T);
         note_launch();
+        k_alias_tile_write<<<nt, 256, 0, st>>>(T);
+        note_launch();
+        k_alias_tile_merge<<<chunks, 256, 0, st>>>(T);
+        note_launch();
+        // the host vectors must outlive the asynchronous uploads
+        e = cudaStreamSynchronize(st);
+        if (e != cudaSuccess) return fail(cuda_fail(e, "alias build"));
+    }
+    if (hc[0]) {
         k_alias_serial<<<g->ctx->sms * 8, 256, 0, st>>>(A);
         note_launch();
+    }
+    if (hc[1]) {
         k_alias_mid<<<g->ctx->sms * 8, 256, 0, st>>>(A);
         note_launch();
-        k_alias_big<<<g->ctx->sms * 2, 512, 0, st>>>(A);
+    }
+    if (hc[2]) {
+        k_alias_big<<<(int)std::min<uint32_t>(hc[2], (uint32_t)g->ctx->sms * 2), 512, 0, st>>>(A);
         note_launch();
-        e = cudaGetLastError();
     }
+    e = cudaGetLastError();
     if (e == cudaSuccess) e = cudaStreamSynchronize(st);
+    if (e != cudaSuccess) return fail(cuda_fail(e, "alias build"));
     cleanup();
-    if (e != cudaSuccess) {
-        dev_free(g->alias.node, st);
-        dev_free(g->alias.slots, st);
-        g->alias.node = nullptr;
-        g->alias.slots = nullptr;
-        return cuda_fail(e, "alias build");
-    }
     g->device_bytes += (int64_t)(sizeof(NodeRec) * n + sizeof(AliasRec) * m);
     return PPR_OK;
 }

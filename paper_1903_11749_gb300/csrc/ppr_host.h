@@ -1,16 +1,26 @@
 // ppr_host.h -- host-side objects behind the C ABI (not part of the ABI).
 #pragma once
 
+#include <atomic>
 #include <cstdint>
 #include <string>
 #include <vector>
 
 #include <cuda_runtime.h>
+#include <nvtx3/nvToolsExt.h>
 
 #include "../../include/ppr.h"
 #include "ppr_internal.cuh"
 
 namespace ppr {
+
+// Named range on the profiler timeline (NVTX) for the lifetime of the object.
+struct Range {
+    explicit Range(const char *name) { nvtxRangePushA(name); }
+    ~Range() { nvtxRangePop(); }
+    Range(const Range &) = delete;
+    Range &operator=(const Range &) = delete;
+};
 
 void set_error(const char *fmt, ...);
 void note_launch();  // counts every kernel launch of the library (ppr_kernel_launches)
@@ -49,9 +59,20 @@ struct ppr_ctx {
     int sms = 0;
     size_t smem_optin = 0;
     ppr::Server *server = nullptr;  // serving state (ppr_serve_start)
+    size_t l2_persist_max = 0;    // device limits for L2 access-policy windows
+    size_t l2_window_max = 0;
+    size_t l2_persist_set = 0;    // persisting set-aside this context asked for
     cudaStream_t copy_stream = nullptr;  // output copies of ppr_run_to_host
     unsigned long long *pinned = nullptr;  // page-locked words for per-batch totals
+    std::atomic<int> refs{1};  // the caller's handle plus every live graph and result
 };
+
+namespace ppr {
+// A graph or result keeps its context alive: ppr_destroy only drops the
+// caller's reference, so handles may be freed in any order.
+void ctx_retain(ppr_ctx *ctx);
+void ctx_release(ppr_ctx *ctx);
+}  // namespace ppr
 
 struct ppr_graph {
     ppr_ctx *ctx = nullptr;
@@ -104,6 +125,7 @@ int build_segments(ppr_graph *g, uint32_t T, cudaStream_t st);
 int build_alias(ppr_graph *g, cudaStream_t st);
 
 // walk.cu
+void preload_run_kernels();  // loads every kernel a run launches (once per device)
 struct RunPlan {
     uint32_t T, R;
     uint64_t seed;
@@ -116,6 +138,7 @@ struct RunPlan {
     int32_t chunk_sources;
     bool stats;
     int32_t sampler;  // 0 first-prefix-above rule, 1 integer alias method
+    bool l2_persist;  // walker launches keep the node records in L2 (access-policy window)
 };
 // Enqueues the walks of sources [s_begin, s_end) writing output rows from
 // out_row0.  ends: S * R endpoint scratch for the plain kernel (else unused);

@@ -34,7 +34,9 @@ struct KParams {
     uint32_t large;
     int64_t s_begin, s_end;   // sources of this launch (global ids)
     int64_t out_row0;         // output row of s_begin
-    uint32_t CS;              // sources per chunk
+    uint32_t CS;              // sources per chunk (batched graphs)
+    uint32_t CW;              // walks per chunk (plain graphs; a chunk may start inside a source)
+    uint64_t walks;           // S * R
     uint32_t nchunks;
     const unsigned long long *nchunks_dev;  // batched graphs: chunk count written on the device
     const int4 *chunks;       // batched graphs: {position, nsrc, instance, 0}; else null
@@ -47,6 +49,7 @@ struct KParams {
     unsigned long long *steps;    // [0] draws consumed, [2] algorithmic sectors (statistics launch)
     uint32_t P2;              // next_pow2(R)
     uint64_t r_magic;         // ceil(2^40 / R): walk index -> source index by multiply-shift
+    int64_t n_nodes;          // node records (for the L2 window)
 };
 
 // One step of one walk.  Returns true when the walk has ended (end is set).
@@ -271,6 +274,7 @@ __global__ void __launch_bounds__(128) k_aggregate(KParams p)
 // state, so L1 keeps its full size.
 struct WarpQueue {
     uint32_t base, ctr_base, tag;  // current chunk: first position, counter base, tag
+    uint32_t j0;                   // walk index (within source `base`) of the chunk's first walk
     uint32_t issued, total;
 };
 
@@ -310,22 +314,25 @@ __global__ void __launch_bounds__(256, PPR_WALK_MINB) k_walk_persistent(KParams 
                     break;
                 }
                 if (lane == 0) {
-                    uint32_t nsrc;
-                    if (p.chunks) {
+                    uint32_t nwalks;
+                    if (p.chunks) {  // whole sources of one instance
                         const int4 d = p.chunks[c];
                         wq.base = (uint32_t)d.x;
-                        nsrc = (uint32_t)d.y;
                         wq.ctr_base = (uint32_t)p.inst_off[d.z];
                         wq.tag = (uint32_t)d.z;
-                    } else {
-                        const int64_t b = (int64_t)c * p.CS;
-                        wq.base = (uint32_t)b;
-                        nsrc = (uint32_t)std::min<int64_t>((int64_t)p.CS, (p.s_end - p.s_begin) - b);
+                        wq.j0 = 0;
+                        nwalks = (uint32_t)d.y * p.R;
+                    } else {  // walks [c * CW, ...) of the whole launch
+                        const uint64_t b = c * (uint64_t)p.CW;
+                        const uint64_t i0 = b / p.R;
+                        wq.base = (uint32_t)i0;
+                        wq.j0 = (uint32_t)(b - i0 * p.R);
+                        nwalks = (uint32_t)min((uint64_t)p.CW, p.walks - b);
                         wq.ctr_base = 0;
                         wq.tag = p.tag;
                     }
                     wq.issued = 0;
-                    wq.total = nsrc * p.R;
+                    wq.total = nwalks;
                 }
                 __syncwarp();
             }
@@ -333,7 +340,7 @@ __global__ void __launch_bounds__(256, PPR_WALK_MINB) k_walk_persistent(KParams 
             const uint32_t take = min(wq.total - issued, (uint32_t)__popc(idle));
             const uint32_t rank = __popc(idle & ((1u << lane) - 1));
             if (((idle >> lane) & 1) && rank < take) {
-                const uint32_t w = issued + rank;
+                const uint32_t w = wq.j0 + issued + rank;  // < 2^20: CW <= 2^19, j0 < R <= 4096
                 const uint32_t i = div_by_R(w, p.r_magic);
                 j = w - i * p.R;
                 const uint32_t pos = wq.base + i;
@@ -428,7 +435,29 @@ static int launch_typed(ppr_ctx *ctx, const KParams &kp, const RunPlan &plan, in
     int64_t needed = ((int64_t)kp.nchunks + wpb - 1) / wpb;
     if (blocks > needed) blocks = std::max<int64_t>(needed, 1);
     if ((rc = walker_event(r, st))) return rc;
-    k_walk_persistent<E, SEG, STATS><<<(unsigned)blocks, 32 * wpb, 0, st>>>(kp);
+    cudaLaunchConfig_t cfg = {};
+    cfg.gridDim = dim3((unsigned)blocks);
+    cfg.blockDim = dim3(32 * wpb);
+    cfg.stream = st;
+    cudaLaunchAttribute attr[1];
+    if (plan.l2_persist && ctx->l2_persist_max > 0 && ctx->l2_window_max > 0) {
+        // node records persisting in L2: every step reads one, the rows'
+        // records stream past them
+        const size_t bytes = std::min((size_t)kp.n_nodes * sizeof(NodeRec), ctx->l2_window_max);
+        if (ctx->l2_persist_set < std::min(bytes, ctx->l2_persist_max)) {
+            ctx->l2_persist_set = std::min(bytes, ctx->l2_persist_max);
+            PPR_CUDA(cudaDeviceSetLimit(cudaLimitPersistingL2CacheSize, ctx->l2_persist_set));
+        }
+        attr[0].id = cudaLaunchAttributeAccessPolicyWindow;
+        attr[0].val.accessPolicyWindow.base_ptr = (void *)kp.node;
+        attr[0].val.accessPolicyWindow.num_bytes = bytes;
+        attr[0].val.accessPolicyWindow.hitRatio = std::min(1.0f, (float)ctx->l2_persist_set / (float)bytes);
+        attr[0].val.accessPolicyWindow.hitProp = cudaAccessPropertyPersisting;
+        attr[0].val.accessPolicyWindow.missProp = cudaAccessPropertyStreaming;
+        cfg.attrs = attr;
+        cfg.numAttrs = 1;
+    }
+    PPR_CUDA(cudaLaunchKernelEx(&cfg, k_walk_persistent<E, SEG, STATS>, kp));
     note_launch();
     PPR_CUDA(cudaGetLastError());
     if ((rc = walker_event(r, st))) return rc;
@@ -459,9 +488,12 @@ __global__ void k_chunk_fill(int32_t count, const int64_t *node_off, int64_t s_b
     }
 }
 
+// sources per chunk; a chunk holds at most 2^19 walks (walk indices within a
+// chunk stay below 2^20 for the multiply-shift division by R)
 static uint32_t chunk_sources(const RunPlan &plan)
 {
-    return plan.chunk_sources > 0 ? (uint32_t)plan.chunk_sources : std::max(1u, 400u / plan.R);
+    const uint32_t cs = plan.chunk_sources > 0 ? (uint32_t)plan.chunk_sources : std::max(1u, 400u / plan.R);
+    return std::min(cs, std::max(1u, (1u << 19) / plan.R));
 }
 
 static size_t align256(size_t x) { return (x + 255) & ~(size_t)255; }
@@ -479,6 +511,45 @@ size_t launch_workspace_bytes(const ppr_graph *g, const RunPlan &plan, int64_t S
         b += align256(sizeof(uint64_t) * (size_t)(tiles + 2));              // scan scratch
     }
     return b;
+}
+
+// Every kernel a run can launch is loaded here, once per device.  With lazy
+// module loading the first launch of a kernel may wait for the device to go
+// idle; loaded up front, a run's launches stay asynchronous.
+template <class E, bool SEG, bool STATS>
+static void preload_walkers()
+{
+    cudaFuncAttributes a;
+    cudaFuncGetAttributes(&a, k_walk_plain<E, SEG, STATS>);
+    cudaFuncGetAttributes(&a, k_walk_persistent<E, SEG, STATS>);
+}
+
+void preload_run_kernels()
+{
+    preload_walkers<NarrowEdges, false, false>();
+    preload_walkers<NarrowEdges, true, false>();
+    preload_walkers<NarrowEdges, false, true>();
+    preload_walkers<NarrowEdges, true, true>();
+    preload_walkers<WideEdges, false, false>();
+    preload_walkers<WideEdges, true, false>();
+    preload_walkers<WideEdges, false, true>();
+    preload_walkers<WideEdges, true, true>();
+    preload_walkers<AliasEdges, false, false>();
+    preload_walkers<AliasEdges, false, true>();
+    cudaFuncAttributes a;
+    cudaFuncGetAttributes(&a, k_aggregate<0>);
+    cudaFuncGetAttributes(&a, k_aggregate<1>);
+    cudaFuncGetAttributes(&a, k_aggregate<2>);
+    cudaFuncGetAttributes(&a, k_aggregate<4>);
+    cudaFuncGetAttributes(&a, k_aggregate<8>);
+    cudaFuncGetAttributes(&a, k_aggregate<16>);
+    cudaFuncGetAttributes(&a, k_aggregate<32>);
+    cudaFuncGetAttributes(&a, k_chunk_count);
+    cudaFuncGetAttributes(&a, k_chunk_fill);
+    cudaFuncGetAttributes(&a, k_scan_tile_sums);
+    cudaFuncGetAttributes(&a, k_scan_tile_offsets);
+    cudaFuncGetAttributes(&a, k_scan_apply);
+    cudaGetLastError();
 }
 
 int launch_walks(ppr_ctx *ctx, const ppr_graph *g, const RunPlan &plan, const Outputs &o, int64_t s_begin, int64_t S,
@@ -513,6 +584,7 @@ int launch_walks(ppr_ctx *ctx, const ppr_graph *g, const RunPlan &plan, const Ou
     while (P2 < plan.R) P2 <<= 1;
     kp.P2 = P2;
     kp.r_magic = ((1ull << 40) + plan.R - 1) / plan.R;
+    kp.n_nodes = g->n;
     kp.ends = reinterpret_cast<uint32_t *>(ws);
     size_t off = align256((size_t)S * plan.R * sizeof(uint32_t));
 
@@ -546,7 +618,16 @@ int launch_walks(ppr_ctx *ctx, const ppr_graph *g, const RunPlan &plan, const Ou
             kp.nchunks_dev = o.counters + 3;
             kp.nchunks = (uint32_t)((S + CS - 1) / CS + cnt);  // upper bound, for the grid size
         } else {
-            kp.nchunks = (uint32_t)((S + CS - 1) / CS);
+            // walks per chunk: CS sources' worth, smaller when that leaves warps
+            // idle (a small run still spreads over every resident warp)
+            const uint64_t walks = (uint64_t)S * plan.R;
+            const uint64_t warps = (uint64_t)ctx->sms * 48;
+            uint64_t cw = std::min<uint64_t>((uint64_t)CS * plan.R, 1u << 19);
+            if ((walks + cw - 1) / cw < warps) cw = std::max<uint64_t>(32, (walks + warps - 1) / warps);
+            cw = std::min<uint64_t>(cw, 1u << 19);
+            kp.CW = (uint32_t)cw;
+            kp.walks = walks;
+            kp.nchunks = (uint32_t)((walks + cw - 1) / cw);
         }
         PPR_CUDA(cudaMemsetAsync(kp.queue, 0, sizeof(unsigned long long), st));
     }
@@ -680,6 +761,7 @@ extern "C" int ppr_run_noalloc(ppr_ctx *ctx, const ppr_graph *g, const ppr_run_a
     plan.chunk_sources = a->chunk_sources;
     plan.stats = false;
     plan.sampler = a->sampler;
+    plan.l2_persist = false;  // no device-limit change from the allocation-free path
     Outputs out{nnz, cols, cnts, cap, topk_idx, topk_cnt, a->topk, reinterpret_cast<unsigned long long *>(scratch)};
     return launch_walks(ctx, g, plan, out, a->src_begin, a->src_end - a->src_begin, nullptr, 0,
                         scratch + kNoAllocHeader, st, nullptr);

@@ -39,7 +39,8 @@ class RunArgs(C.Structure):
                 ("src_end", C.c_int64), ("tag", C.c_uint32), ("dangling", C.c_int32), ("segments", C.c_int32),
                 ("topk", C.c_int32), ("kernel", C.c_int32), ("large_degree", C.c_int32),
                 ("warps_per_block", C.c_int32), ("chunk_sources", C.c_int32), ("max_batch_sources", C.c_int64),
-                ("stats", C.c_int32), ("sampler", C.c_int32), ("stream", C.c_void_p)]
+                ("stats", C.c_int32), ("sampler", C.c_int32), ("l2_persist", C.c_int32),
+                ("stream", C.c_void_p)]
 
 
 class Tuning(C.Structure):
@@ -101,6 +102,9 @@ _SIGS = {
     "ppr_submit": (C.c_int, [C.c_void_p, C.c_void_p, C.c_int64, C.c_double, C.c_uint32, C.c_uint64, C.c_int32,
                              C.POINTER(C.c_uint64)]),
     "ppr_poll": (C.c_int, [C.c_void_p, C.c_uint64, C.c_void_p, C.c_void_p, C.c_int64, C.POINTER(QueryStats)]),
+    "ppr_debug_fail_allocs": (None, [C.c_int64]),
+    "ppr_probe_philox": (C.c_int, [C.c_void_p, C.c_uint64, C.c_void_p, C.c_int64, C.c_void_p]),
+    "ppr_probe_rate": (C.c_int, [C.c_void_p, C.c_int32, C.c_int64, C.POINTER(C.c_double), C.POINTER(C.c_float)]),
     "ppr_run_to_host": (C.c_int, [C.c_void_p, C.c_void_p, C.POINTER(RunArgs), C.c_int32, C.c_void_p, C.c_void_p,
                                   C.c_void_p, C.c_int64, C.POINTER(C.c_int64), C.c_void_p, C.c_void_p,
                                   C.POINTER(ResultInfo)]),
@@ -137,6 +141,11 @@ def kernel_launches() -> int:
 
 def alpha_threshold(alpha: float) -> int:
     return int(lib().ppr_alpha_threshold(alpha))
+
+
+def debug_fail_allocs(after: int) -> None:
+    """Test hook: device allocations fail with PPR_ENOMEM after `after` more (negative: off)."""
+    lib().ppr_debug_fail_allocs(after)
 
 
 def walks_for_accuracy(eps: float, delta: float, p_f: float) -> int:
@@ -185,6 +194,22 @@ class Context:
             pass
 
     # ---- serving
+    def probe_philox(self, seed: int, counter, count: int) -> np.ndarray:
+        """Device Philox4x32-10 words uint32[count, 4] for counters (c0 + i, c1, c2, c3)."""
+        ctr = np.ascontiguousarray(counter, dtype=np.uint32)
+        out = np.empty((count, 4), dtype=np.uint32)
+        _check(lib().ppr_probe_philox(self.h, seed, ctr.ctypes.data, count, out.ctypes.data))
+        return out
+
+    def probe_rate(self, kind: int, nbytes: int = 0):
+        """(units per second, kernel ms): kind 0 dependent random 32-byte sector
+        reads over nbytes, kind 1 Philox draws, kind 2 independent random
+        32-byte sector reads over nbytes."""
+        v = C.c_double()
+        ms = C.c_float()
+        _check(lib().ppr_probe_rate(self.h, kind, nbytes, C.byref(v), C.byref(ms)))
+        return v.value, ms.value
+
     def serve_start(self, graph: "Graph", **cfg):
         c = ServeCfg()
         lib().ppr_serve_cfg_init(C.byref(c))
@@ -260,7 +285,7 @@ class Graph:
 
     def _args(self, alpha=0.15, R=100, seed=1, src_begin=0, src_end=None, tag=0, dangling=0, segments=False,
               topk=0, kernel=KERNEL_PERSISTENT, large_degree=0, warps_per_block=0, chunk_sources=0,
-              max_batch_sources=0, stats=False, stream=None, sampler=0):
+              max_batch_sources=0, stats=False, stream=None, sampler=0, l2_persist=0):
         a = RunArgs()
         lib().ppr_run_args_init(C.byref(a))
         a.alpha, a.R, a.seed = alpha, R, seed
@@ -271,6 +296,7 @@ class Graph:
         a.max_batch_sources = max_batch_sources
         a.stats = int(bool(stats))
         a.sampler = sampler
+        a.l2_persist = l2_persist
         a.stream = _stream_ptr(stream)
         return a
 
@@ -326,7 +352,7 @@ class Graph:
 
     def run(self, alpha=0.15, R=100, seed=1, src_begin=0, src_end=None, tag=0, dangling=0, segments=False,
             topk=0, kernel=KERNEL_PERSISTENT, large_degree=0, warps_per_block=0, chunk_sources=0,
-            max_batch_sources=0, stats=False, stream=None, wait=True, sampler=0) -> "Result":
+            max_batch_sources=0, stats=False, stream=None, wait=True, sampler=0, l2_persist=0) -> "Result":
         a = RunArgs()
         lib().ppr_run_args_init(C.byref(a))
         a.alpha, a.R, a.seed = alpha, R, seed
@@ -337,6 +363,7 @@ class Graph:
         a.max_batch_sources = max_batch_sources
         a.stats = int(bool(stats))
         a.sampler = sampler
+        a.l2_persist = l2_persist
         a.stream = _stream_ptr(stream)
         h = C.c_void_p()
         _check(lib().ppr_run(self.ctx.h, self.h, C.byref(a), C.byref(h)))
