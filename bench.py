@@ -498,7 +498,7 @@ def run_serving(args):
         return [rng.choice(g.n, size=int(s), replace=False).astype(np.int32) for s in sizes]
 
     kw = dict(alpha=wl["alpha"], R=wl["R"], seed=wl["seed"], topk=wl["topk"])
-    ctx.serve_start(G, streams=args.serve_streams, max_sources=smax, max_topk=wl["topk"])
+    ctx.serve_start(G, streams=args.serve_streams, max_sources=smax, max_topk=wl["topk"], sampler=args.serve_sampler)
 
     def run_stream(queries, rate):
         """Submit at Poisson times (rate queries/s; 0 = back to back), poll all."""
@@ -554,6 +554,7 @@ def run_serving(args):
             "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "u32", "data": "synthetic",
             "config": {"workload": "serve", "desc": wl["desc"], "alpha": wl["alpha"], "R": wl["R"], "topk": wl["topk"],
                        "n": g.n, "m": g.m, "streams": args.serve_streams,
+                       "sampler": "alias" if args.serve_sampler == 1 else "prefix",
                        "steps_counted": "expected steps walks*2^32/T of the delivered walks",
                        "step": "one query (ms_per_step = mean latency)"},
             "p50_ms": main_r["p50_ms"], "p99_ms": main_r["p99_ms"], "walks_per_s": main_r["walks_per_s"],
@@ -728,6 +729,8 @@ def main():
     ap.add_argument("--serve-warmup", type=int, default=200)
     ap.add_argument("--serve-streams", type=int, default=4)
     ap.add_argument("--serve-rho", type=float, nargs="+", default=[0.5, 0.8])
+    ap.add_argument("--serve-sampler", type=int, default=0, choices=[0, 1],
+                    help="neighbour choice of the served queries (1: integer alias tables)")
     ap.add_argument("--sample-every", type=int, default=0,
                     help="profiling case: walk only every k-th source (an explicit source list)")
     args = ap.parse_args()
@@ -795,6 +798,7 @@ def main():
     for _ in range(args.warmup):
         G, r = step()
         r.wait()
+        del r, G  # freed here, not inside the first timed step
     kernel_ms = []
     run_ms = []
     step_ms = []
@@ -830,6 +834,7 @@ def main():
     if not args.no_plain:
         G, r = step(kernel=ppr.KERNEL_PLAIN)
         r.wait()
+        del r, G
         pm = []
         for _ in range(max(1, min(3, args.steps))):
             flush.fill_(1)
@@ -841,6 +846,7 @@ def main():
             r.wait()
             e1.synchronize()
             pm.append(e0.elapsed_time(e1))
+            del r, G
         plain = {"value": steps_per_pass / (statistics.mean(pm) / 1e3), "unit": "walk steps/s",
                  "ms_per_step": statistics.mean(pm), "kernel": "one thread per walk + separate aggregation"}
 
@@ -938,7 +944,8 @@ def main():
                            "topk": wl["topk"], "n": g.n, "m": g.m, "sources": g.n,
                            "parallelism": f"{world} independent replicas (tag = rank)" if world > 1 else "1 GPU",
                            "l2": "flushed between steps (512 MB write)"},
-                "walks_per_s": walks_s, "steps_per_walk": steps_per_pass / max(walks_per_pass, 1),
+                "step_ms_each": step_ms, "walks_per_s": walks_s,
+                "steps_per_walk": steps_per_pass / max(walks_per_pass, 1),
                 "draws_per_s": draws_per_pass * args.steps * world / T_max,
                 "steps_counted": "plain-equivalent walks*2^32/T" if wl["segments"] else "draws (one per step)",
                 "roofline": roofline, "probe": probe, "cpu_baseline": cpu, "e2e": e2e, "plain_kernel": plain,

@@ -389,6 +389,8 @@ typedef struct {
     int64_t memory_budget;  /* device bytes for queries in flight (0 = a quarter of free memory) */
     int64_t max_pending;    /* queries waiting for admission before ppr_submit returns PPR_EBUSY (0 = no limit) */
     int32_t chunk_sources, large_degree, warps_per_block; /* walker tuning (0 = defaults) */
+    int32_t sampler;        /* neighbour choice of every query, as ppr_run_args.sampler; with 1
+                               the graph's alias tables are built by ppr_serve_start */
 } ppr_serve_cfg;
 
 typedef struct {

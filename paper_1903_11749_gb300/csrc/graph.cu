@@ -140,13 +140,14 @@ __global__ void k_rows_pass2(int64_t n, const int64_t *row_ptr, const int32_t *c
 // k_build_big (one block per row).  A row total >= 2^32 sets kWide and the
 // graph is rebuilt in the wide layout.
 enum : uint32_t { kWide = 8u, kBigDegree = 16u };
-constexpr uint32_t kSmallRow = 32, kMidRow = 8192;
+constexpr uint32_t kSmallRow = 32, kMidRow = 8192, kHugeRow = 65536;
+constexpr uint32_t kBuildTile = 8192;  // edges per tile block of a huge row (256 threads x 32)
 
 struct LayoutStats {
     unsigned long long max_degree;
     unsigned long long dangling;
     unsigned int status;
-    unsigned int n_mid, n_big;
+    unsigned int n_mid, n_big, n_huge;
 };
 
 __device__ __forceinline__ void block_stats(LayoutStats *st, uint32_t deg_max, uint32_t dang, uint32_t flags)
@@ -178,7 +179,7 @@ __device__ __forceinline__ void block_stats(LayoutStats *st, uint32_t deg_max, u
 }
 
 __global__ void __launch_bounds__(256) k_layout(int64_t n, int64_t m, const int64_t *row_ptr, uint32_t *sizes,
-                                                LayoutStats *st)
+                                                LayoutStats *st, uint2 *huge, uint32_t huge_cap)
 {
     uint32_t dmax = 0, dang = 0, flags = 0;
     for (int64_t u = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; u < n; u += (int64_t)gridDim.x * blockDim.x) {
@@ -194,6 +195,10 @@ __global__ void __launch_bounds__(256) k_layout(int64_t n, int64_t m, const int6
             dmax = max(dmax, d);
             dang += d == 0;
             sz = blocked_row_records(d);
+            if (d > kHugeRow) {  // a valid row_ptr has at most m / kHugeRow of them
+                const uint32_t k = atomicAdd(&st->n_huge, 1u);
+                if (k < huge_cap) huge[k] = make_uint2((uint32_t)u, d);
+            }
         }
         sizes[u] = sz;
     }
@@ -268,8 +273,8 @@ __global__ void __launch_bounds__(256) k_build_small(BuildArgs A)
         const uint32_t d = (uint32_t)(A.row_ptr[u + 1] - a);
         if (d > kSmallRow) {
             if (d <= kMidRow) A.list[atomicAdd(&A.st->n_mid, 1u)] = (uint32_t)u;
-            else A.list[A.n - 1 - atomicAdd(&A.st->n_big, 1u)] = (uint32_t)u;
-            continue;
+            else if (d <= kHugeRow) A.list[A.n - 1 - atomicAdd(&A.st->n_big, 1u)] = (uint32_t)u;
+            continue;  // rows above kHugeRow: tile kernels
         }
         int64_t hi_id;
         const int64_t base_id = instance_base(A, u, hi_id);
@@ -440,6 +445,145 @@ __global__ void __launch_bounds__(512) k_build_big(BuildArgs A)
     if (tid == 0 && s_flags) atomicOr(&A.st->status, s_flags);
 }
 
+// Rows above kHugeRow edges are built by tiles of kBuildTile edges, one block
+// each, so a hub row does not leave one block working while the GPU idles:
+// tile weight totals, a scan of each row's tiles, tile writes of the prefix
+// records and level-1 keys, then one block per row for the padding, the upper
+// summary levels and the node record.
+struct BuildTiles {
+    BuildArgs A;
+    const uint4 *rows;   // (node, degree, first tile, tiles)
+    const uint2 *tiles;  // (row index, first edge of the tile)
+    uint64_t *tile_sum;  // per tile: weight total, then its exclusive offset in the row
+    uint64_t *row_total; // per row: W
+    uint32_t nrows;
+};
+
+__device__ __forceinline__ uint64_t block_sum_u64(uint64_t v, uint64_t *s)  // 256 threads
+{
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
+    if ((threadIdx.x & 31) == 0) s[threadIdx.x >> 5] = v;
+    __syncthreads();
+    uint64_t t = 0;
+    for (int q = 0; q < 8; ++q) t += s[q];
+    __syncthreads();
+    return t;
+}
+
+__global__ void __launch_bounds__(256) k_build_tile_totals(BuildTiles T)
+{
+    __shared__ uint64_t s[8];
+    const BuildArgs &A = T.A;
+    const uint2 tl = T.tiles[blockIdx.x];
+    const uint4 rw = T.rows[tl.x];
+    const int64_t a = A.row_ptr[rw.x];
+    int64_t hi_id;
+    instance_base(A, rw.x, hi_id);
+    const uint32_t end = min(tl.y + kBuildTile, rw.y);
+    const uint32_t lo = min(tl.y + threadIdx.x * 32, end), hi = min(lo + 32, end);
+    uint64_t sum = 0;
+    uint32_t flags = 0;
+    for (uint32_t i = lo; i < hi; ++i) {
+        const uint32_t wi = A.w[a + i];
+        const int64_t c = A.col[a + i];
+        if (wi == 0) flags |= kBadWeight;
+        if (c < 0 || c >= hi_id) flags |= kBadCol;
+        sum += wi;
+    }
+    if (flags) atomicOr(&A.st->status, flags);
+    const uint64_t t = block_sum_u64(sum, s);
+    if (threadIdx.x == 0) T.tile_sum[blockIdx.x] = t;
+}
+
+__global__ void k_build_tile_scan(BuildTiles T)
+{
+    const uint32_t r = blockIdx.x * (blockDim.x >> 5) + (threadIdx.x >> 5);
+    if (r >= T.nrows) return;
+    const uint32_t lane = threadIdx.x & 31;
+    const uint4 rw = T.rows[r];
+    uint64_t carry = 0;
+    for (uint32_t t0 = 0; t0 < rw.w; t0 += 32) {
+        const uint32_t t = t0 + lane;
+        uint64_t v = t < rw.w ? T.tile_sum[rw.z + t] : 0ull;
+        const uint64_t own = v;
+#pragma unroll
+        for (int o = 1; o < 32; o <<= 1) {
+            const uint64_t y = __shfl_up_sync(0xffffffffu, v, o);
+            if (lane >= o) v += y;
+        }
+        if (t < rw.w) T.tile_sum[rw.z + t] = carry + v - own;
+        carry += __shfl_sync(0xffffffffu, v, 31);
+    }
+    if (lane == 0) {
+        T.row_total[r] = carry;
+        if (carry >= (1ull << 32)) atomicOr(&T.A.st->status, kWide);
+    }
+}
+
+__global__ void __launch_bounds__(256) k_build_tile_write(BuildTiles T)
+{
+    __shared__ uint64_t s[8];
+    const BuildArgs &A = T.A;
+    uint32_t *K = reinterpret_cast<uint32_t *>(A.E);
+    const uint2 tl = T.tiles[blockIdx.x];
+    const uint4 rw = T.rows[tl.x];
+    const uint32_t d = rw.y;
+    const int64_t a = A.row_ptr[rw.x];
+    int64_t hi_id;
+    const int64_t base_id = instance_base(A, rw.x, hi_id);
+    const uint64_t reg = A.region[rw.x];
+    const uint32_t L = tree_levels(d);
+    const uint64_t eb = reg + 4ull * summary_sectors(d);
+    const uint32_t end = min(tl.y + kBuildTile, d);
+    const uint32_t lo = min(tl.y + threadIdx.x * 32, end), hi = min(lo + 32, end);
+    uint64_t own = 0;
+    for (uint32_t i = lo; i < hi; ++i) own += A.w[a + i];
+    // exclusive offset of this thread's run within the tile
+    const uint32_t lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
+    uint64_t v = own;
+#pragma unroll
+    for (int o = 1; o < 32; o <<= 1) {
+        const uint64_t y = __shfl_up_sync(0xffffffffu, v, o);
+        if (lane >= o) v += y;
+    }
+    if (lane == 31) s[wid] = v;
+    __syncthreads();
+    uint64_t before = 0;
+    for (uint32_t q = 0; q < wid; ++q) before += s[q];
+    uint64_t P = T.tile_sum[blockIdx.x] + before + v - own;
+    for (uint32_t i = lo; i < hi; ++i) {
+        P += A.w[a + i];
+        EdgeN r;
+        r.P = (uint32_t)P;
+        r.col = (int32_t)(A.col[a + i] + base_id);
+        A.E[eb + i] = r;
+        if ((i & 7) == 7 || i == d - 1) K[key_slot(reg, d, L, 1, i >> 3)] = (uint32_t)P;
+    }
+}
+
+__global__ void __launch_bounds__(512) k_build_tile_finish(BuildTiles T)
+{
+    const BuildArgs &A = T.A;
+    uint32_t *K = reinterpret_cast<uint32_t *>(A.E);
+    const uint4 rw = T.rows[blockIdx.x];
+    const uint32_t d = rw.y, tid = threadIdx.x;
+    const uint64_t reg = A.region[rw.x];
+    const uint32_t L = tree_levels(d);
+    const uint64_t eb = reg + 4ull * summary_sectors(d);
+    for (uint32_t i = d + tid; i < 4 * ceil_shift(d, 2); i += blockDim.x) {
+        EdgeN r;
+        r.P = 0xffffffffu;
+        r.col = 0;
+        A.E[eb + i] = r;
+    }
+    for (uint32_t i = ceil_shift(d, 3) + tid; i < 8 * level_sectors(d, 1); i += blockDim.x)
+        K[key_slot(reg, d, L, 1, i)] = 0xffffffffu;
+    __syncthreads();
+    write_upper_levels(K, reg, d, L, tid, blockDim.x, true);
+    if (tid == 0) write_node(A, rw.x, reg, d, T.row_total[blockIdx.x], 0);
+}
+
 // Narrow layout in one pass.  Returns PPR_OK, an error, or 1 when a row total
 // reaches 2^32 (the caller then builds the wide layout).
 static int build_narrow(ppr_ctx *ctx, int64_t n, int64_t m, const int64_t *d_rp, const int32_t *d_col,
@@ -462,10 +606,14 @@ static int build_narrow(ppr_ctx *ctx, int64_t n, int64_t m, const int64_t *d_rp,
     tmp.push_back(d_ls);
     if ((rc = dev_alloc((void **)&d_list, sizeof(uint32_t) * n, "long-row list", st))) return rc;
     tmp.push_back(d_list);
+    const uint32_t huge_cap = (uint32_t)(m / kHugeRow + 1);
+    uint2 *d_huge;
+    if ((rc = dev_alloc((void **)&d_huge, sizeof(uint2) * huge_cap, "huge-row list", st))) return rc;
+    tmp.push_back(d_huge);
     cudaError_t e = cudaMemsetAsync(d_ls, 0, sizeof(LayoutStats), st);
     if (e != cudaSuccess) return cuda_fail(e, "memset");
     const int tblocks = (int)std::max<int64_t>(1, std::min<int64_t>((n + 255) / 256, (int64_t)ctx->sms * 16));
-    k_layout<<<tblocks, 256, 0, st>>>(n, m, d_rp, d_sizes, d_ls);
+    k_layout<<<tblocks, 256, 0, st>>>(n, m, d_rp, d_sizes, d_ls, d_huge, huge_cap);
     note_launch();
     exclusive_scan_u32(d_sizes, n, d_region, d_scan, st);
     LayoutStats hs;
@@ -499,6 +647,44 @@ static int build_narrow(ppr_ctx *ctx, int64_t n, int64_t m, const int64_t *d_rp,
     note_launch();
     k_build_big<<<ctx->sms, 512, 0, st>>>(A);
     note_launch();
+    std::vector<uint4> hrows;  // host tables must outlive their uploads (synchronised below)
+    std::vector<uint2> htiles;
+    if (hs.n_huge > 0) {
+        const uint32_t nh = std::min(hs.n_huge, huge_cap);
+        std::vector<uint2> hl(nh);
+        e = cudaMemcpyAsync(hl.data(), d_huge, sizeof(uint2) * nh, cudaMemcpyDeviceToHost, st);
+        if (e == cudaSuccess) e = cudaStreamSynchronize(st);
+        if (e != cudaSuccess) return cuda_fail(e, "huge rows");
+        for (uint32_t r = 0; r < nh; ++r) {
+            const uint32_t d = hl[r].y, nt = (d + kBuildTile - 1) / kBuildTile;
+            hrows.push_back(make_uint4(hl[r].x, d, (uint32_t)htiles.size(), nt));
+            for (uint32_t t = 0; t < nt; ++t) htiles.push_back(make_uint2(r, t * kBuildTile));
+        }
+        const uint32_t nt = (uint32_t)htiles.size();
+        uint4 *d_rows;
+        uint2 *d_tiles;
+        uint64_t *d_tsum, *d_rtot;
+        if ((rc = dev_alloc((void **)&d_rows, sizeof(uint4) * nh, "huge rows", st))) return rc;
+        tmp.push_back(d_rows);
+        if ((rc = dev_alloc((void **)&d_tiles, sizeof(uint2) * nt, "tile table", st))) return rc;
+        tmp.push_back(d_tiles);
+        if ((rc = dev_alloc((void **)&d_tsum, sizeof(uint64_t) * nt, "tile sums", st))) return rc;
+        tmp.push_back(d_tsum);
+        if ((rc = dev_alloc((void **)&d_rtot, sizeof(uint64_t) * nh, "row totals", st))) return rc;
+        tmp.push_back(d_rtot);
+        e = cudaMemcpyAsync(d_rows, hrows.data(), sizeof(uint4) * nh, cudaMemcpyHostToDevice, st);
+        if (e == cudaSuccess) e = cudaMemcpyAsync(d_tiles, htiles.data(), sizeof(uint2) * nt, cudaMemcpyHostToDevice, st);
+        if (e != cudaSuccess) return cuda_fail(e, "tile table upload");
+        BuildTiles T{A, d_rows, d_tiles, d_tsum, d_rtot, nh};
+        k_build_tile_totals<<<nt, 256, 0, st>>>(T);
+        note_launch();
+        k_build_tile_scan<<<(nh + 7) / 8, 256, 0, st>>>(T);
+        note_launch();
+        k_build_tile_write<<<nt, 256, 0, st>>>(T);
+        note_launch();
+        k_build_tile_finish<<<nh, 512, 0, st>>>(T);
+        note_launch();
+    }
     e = cudaMemcpyAsync(&hs, d_ls, sizeof(hs), cudaMemcpyDeviceToHost, st);
     if (e == cudaSuccess) e = cudaStreamSynchronize(st);
     if (e != cudaSuccess) return cuda_fail(e, "graph build");

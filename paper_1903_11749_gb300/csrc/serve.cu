@@ -225,13 +225,17 @@ int ppr_serve_start(ppr_ctx *ctx, const ppr_graph *g, const ppr_serve_cfg *cfg_i
     ppr_serve_cfg_init(&cfg);
     if (cfg_in) cfg = *cfg_in;
     if (cfg.streams < 1 || cfg.streams > 64 || cfg.max_sources < 1 || cfg.memory_budget < 0 || cfg.max_pending < 0 ||
-        cfg.max_topk < 0 || cfg.max_topk > (int32_t)PPR_MAX_R) {
+        cfg.max_topk < 0 || cfg.max_topk > (int32_t)PPR_MAX_R || (cfg.sampler != 0 && cfg.sampler != 1)) {
         set_error("invalid serving configuration");
         return PPR_EINVAL;
     }
     if (cfg.max_topk == 0) cfg.max_topk = 64;
     cudaError_t e = cudaSetDevice(ctx->device);
     if (e != cudaSuccess) return cuda_fail(e, "cudaSetDevice");
+    if (cfg.sampler == 1) {
+        const int rc = build_alias(const_cast<ppr_graph *>(g), g->stream);
+        if (rc) return rc;
+    }
     Server *sv = new (std::nothrow) Server;
     if (!sv) return PPR_ENOMEM;
     sv->ctx = ctx;
@@ -333,6 +337,7 @@ int ppr_submit(ppr_ctx *ctx, const int32_t *srcs, int64_t ns, double alpha, uint
     q->plan.large_degree = sv->cfg.large_degree;
     q->plan.warps_per_block = sv->cfg.warps_per_block;
     q->plan.chunk_sources = sv->cfg.chunk_sources;
+    q->plan.sampler = sv->cfg.sampler;
     q->plan.stats = false;
     q->topk = topk;
     const uint32_t cap = (uint32_t)std::min<int64_t>((int64_t)R, sv->g->n);

@@ -118,7 +118,7 @@ __device__ __forceinline__ bool walk_step(const KParams &p, const E &edges, bool
     }
     uint32_t next = 0;
     bool big = false;
-    if (COOP && !STATS) {
+    if (COOP && !STATS && p.large != 0xffffffffu) {  // uniform: skipped whole when the path is off
         big = act && !segf && cnt > p.large;
         uint32_t bigmask = __ballot_sync(0xffffffffu, big);
         const uint32_t lane = threadIdx.x & 31;

@@ -51,7 +51,7 @@ class Tuning(C.Structure):
 class ServeCfg(C.Structure):
     _fields_ = [("streams", C.c_int32), ("max_sources", C.c_int64), ("max_topk", C.c_int32),
                 ("memory_budget", C.c_int64), ("max_pending", C.c_int64), ("chunk_sources", C.c_int32),
-                ("large_degree", C.c_int32), ("warps_per_block", C.c_int32)]
+                ("large_degree", C.c_int32), ("warps_per_block", C.c_int32), ("sampler", C.c_int32)]
 
 
 class QueryStats(C.Structure):

@@ -139,6 +139,34 @@ def test_large_rows_cooperative_search(ppr, ctx, oracle):
         assert_same(G.run(alpha=0.15, R=50, seed=3, src_end=2000, topk=8, large_degree=large), ref, topk=8)
 
 
+def test_huge_rows_built_by_tiles(ppr, ctx, oracle):
+    """Rows above 65,536 edges are built by tiles of 8,192 edges (a hub of
+    150,001 edges, a row of 65,537, and one just below the cut), in a plain
+    and in a batched graph; every count equals the oracle's."""
+    rng = np.random.Generator(np.random.PCG64(5))
+    n = 40000
+    edges = []
+    for u, d in ((0, 150_001), (1, 65_537), (2, 65_536)):
+        edges += [(u, int(t), int(w)) for t, w in zip(rng.integers(0, n, d), rng.integers(1, 3000, d))]
+    for u in range(3, n):
+        edges.append((u, int(rng.integers(0, 3)), int(rng.integers(1, 9))))
+        edges.append((u, int(rng.integers(0, n)), int(rng.integers(1, 9))))
+    g = I.from_edges(n, edges)
+    G = ctx.load_graph(g.n, g.row_ptr, g.col, g.w)
+    ref = oracle_rows(oracle, g, 0.2, 40, 6, 0, 600, topk=5)
+    for kernel in (0, 1):
+        assert_same(G.run(alpha=0.2, R=40, seed=6, src_end=600, topk=5, kernel=kernel), ref, topk=5)
+    # the same graph twice as a batched graph: each instance as its own run
+    rp2 = np.concatenate([g.row_ptr[:-1], g.row_ptr + g.m])
+    Gb = ctx.load_graph_batch(np.array([0, n, 2 * n]), rp2, np.concatenate([g.col, g.col]),
+                              np.concatenate([g.w, g.w]))
+    res = Gb.run(alpha=0.2, R=40, seed=6, src_begin=n, src_end=n + 600, topk=5)
+    ref1 = oracle_rows(oracle, g, 0.2, 40, 6, 0, 600, tag=1, topk=5)
+    rp, col, cnt = res.sparse_rows()
+    orp, ocol, ocnt = ref1["rows"]
+    assert np.array_equal(rp, orp) and np.array_equal(col, ocol) and np.array_equal(cnt, ocnt)  # instance-local ids
+
+
 def test_segment_mode_matches_segment_oracle(ppr, ctx, oracle):
     g = I.random_small_graph(400, 1100, seed=21, wmax=30, dangling=20)
     G = ctx.load_graph(g.n, g.row_ptr, g.col, g.w)

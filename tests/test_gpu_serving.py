@@ -103,3 +103,18 @@ def test_memory_admission_and_errors(env):
     ctx.serve_stop()
     with pytest.raises(ppr.PPRError):
         ctx.poll(1, 1, 5, timeout_ms=10)
+
+
+def test_alias_sampler_queries_equal_list_runs(env):
+    ppr, g = env
+    ctx = ppr.Context(0)
+    G = ctx.load_graph(g.n, g.row_ptr, g.col, g.w)
+    ctx.serve_start(G, streams=2, sampler=1)
+    qs = _queries(g.n, 6, seed=9, smax=800)
+    kw = dict(alpha=0.15, R=50, seed=11, topk=6)
+    ids = [ctx.submit(src, **kw) for src in qs]
+    got = [ctx.poll(q, len(src), kw["topk"], timeout_ms=60000)[:2] for q, src in zip(ids, qs)]
+    ctx.serve_stop()
+    for (idx, cnt), src in zip(got, qs):
+        ridx, rcnt = G.run_list(src, sampler=1, **kw).topk()
+        assert np.array_equal(idx, ridx) and np.array_equal(cnt, rcnt)
