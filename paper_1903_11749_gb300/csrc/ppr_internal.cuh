@@ -262,6 +262,18 @@ __host__ __device__ __forceinline__ uint64_t pack_blocked_total(uint64_t W, uint
     return W | ((uint64_t)summary_sectors(d) << 32) | ((uint64_t)tree_levels(d) << 56);
 }
 
+// Number of the 8 keys k[0..7] that are <= x, for keys in ascending order with
+// k[7] > x (a summary sector's last key is its parent's key, above x; missing
+// keys are 0xFFFFFFFF): three comparisons of a binary search, 0..7.
+__device__ __forceinline__ uint32_t rank8(uint32_t k0, uint32_t k1, uint32_t k2, uint32_t k3, uint32_t k4, uint32_t k5,
+                                          uint32_t k6, uint32_t x)
+{
+    uint32_t c = k3 <= x ? 4u : 0u;
+    c += (c ? k5 : k1) <= x ? 2u : 0u;
+    const uint32_t kk = (c & 4u) ? ((c & 2u) ? k6 : k4) : ((c & 2u) ? k2 : k0);
+    return c + (kk <= x ? 1u : 0u);
+}
+
 // Search of a blocked narrow row (layout above) whose region starts at record
 // `begin`, with S summary sectors over L levels: the target of the first edge
 // with P > x.  TALLY counts the 32-byte sectors read.
@@ -273,9 +285,7 @@ __device__ __forceinline__ uint32_t search_blocked(const EdgeN *E, uint64_t begi
     uint32_t b = 0, off = 0;
     for (uint32_t l = L; l >= 1; --l) {
         const Sector k = ld_sector(base + 32ull * (off + b));
-        uint32_t c = 0;
-#pragma unroll
-        for (int i = 0; i < 8; ++i) c += (uint32_t)(k.v[i] <= x);
+        const uint32_t c = rank8(k.v[0], k.v[1], k.v[2], k.v[3], k.v[4], k.v[5], k.v[6], x);
         off += level_sectors(d, l);
         b = b * 8 + c;
         if (TALLY) ++sectors;
@@ -290,16 +300,11 @@ __device__ __forceinline__ uint32_t search_blocked(const EdgeN *E, uint64_t begi
         for (int i = 0; i < 8; ++i) r1.v[i] = 0xffffffffu;
     }
     if (TALLY) sectors += len > 4 ? 2 : 1;
-    uint32_t c = 0;
-#pragma unroll
-    for (int i = 0; i < 4; ++i) c += (uint32_t)(r0.v[2 * i] <= x) + (uint32_t)(r1.v[2 * i] <= x);
-    uint32_t t = r1.v[7];
-#pragma unroll
-    for (int i = 6; i >= 0; --i) {
-        const uint32_t cand = i < 4 ? r0.v[2 * i + 1] : r1.v[2 * (i - 4) + 1];
-        if (c == (uint32_t)i) t = cand;
-    }
-    return t;
+    // record i holds (P, col) in words 2i, 2i+1 of r0 (i < 4) or r1 (i >= 4)
+    const uint32_t c = rank8(r0.v[0], r0.v[2], r0.v[4], r0.v[6], r1.v[0], r1.v[2], r1.v[4], x);
+    const Sector &h = (c & 4u) ? r1 : r0;
+    const uint32_t lo = (c & 1u) ? h.v[3] : h.v[1], hi = (c & 1u) ? h.v[7] : h.v[5];
+    return (c & 2u) ? hi : lo;
 }
 
 // Same result, computed by the whole warp for one lane's search (all 32 lanes
