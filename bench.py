@@ -897,6 +897,7 @@ def main():
         d2h = o_rp.numel() * 8 + nnz * 8 + (S * wl["topk"] * 8 if wl["topk"] else 0)
         e2e = {"value": steps_per_pass / statistics.mean(times), "unit": "walk steps/s", "h2d_bytes_per_step": h2d,
                "d2h_bytes_per_step": d2h, "ms_per_step": 1e3 * statistics.mean(times),
+               "ms_each": [1e3 * t for t in times],
                "call": "ppr_load_graph (pinned host CSR) + ppr_run_to_host (pinned host rows and top-k)",
                "unpipelined": {"value": steps_per_pass / statistics.mean(serial_times),
                                "ms_per_step": 1e3 * statistics.mean(serial_times),

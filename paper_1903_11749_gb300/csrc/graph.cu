@@ -1118,11 +1118,13 @@ int build_segments(ppr_graph *g, uint32_t T, cudaStream_t st)
 //   large edge j (not the last): thr = W - (D_q - E_j) with q = min{q : D_q >= E_j},
 //                                alias = large edge j + 1
 //   last large edge, edges with p = W: thr = W, alias = itself.
-// Rows of at most 256 edges run the pairing rounds serially, one thread per
-// row; longer rows compute the closed form with a warp (up to 8192 edges) or
-// a block per row (alias_row_group).
+// Rows of at most 32 edges run the pairing rounds serially, one thread per
+// row; longer rows compute the closed form: one warp per row with the row in
+// shared memory (up to 512 edges), one warp (up to 8192) or block (up to
+// 65,536) per row with scratch in global memory (alias_row_group), and tiles
+// of blocks above that.
 
-constexpr uint32_t kAliasInline = 32, kAliasSerial = 256, kAliasMid = 8192, kAliasHuge = 65536;
+constexpr uint32_t kAliasInline = 32, kAliasSerial = 512, kAliasMid = 8192, kAliasHuge = 65536;
 constexpr uint32_t kAliasMaxHuge = 4096;  // rows taken by the tile path; more go to the block tier
 constexpr uint32_t kTileEdges = 8192;     // edges per tile block (256 threads x 32)
 
@@ -1211,13 +1213,122 @@ __global__ void __launch_bounds__(256) k_alias_small(AliasArgs A)
     }
 }
 
-__global__ void __launch_bounds__(256) k_alias_serial(AliasArgs A)
+// Rows of 33..512 edges, one warp per row, the row staged in shared memory:
+// a coalesced pass classifies the edges, ranks them with ballots and forms
+// the running sums D and E with warp scans; each lane then merges a
+// contiguous share of the small (and of the large) edges against the other
+// sequence, as alias_row_group does, with every probe in shared memory.
+constexpr int kSmemWarps = 4;
+struct RowSmem {
+    int32_t col[kAliasSerial];
+    uint16_t idx[kAliasSerial];  // edge of each small (from the front) and large (from the back) entry
+    uint64_t sum[kAliasSerial];  // D_i / E_j
+};
+
+__global__ void __launch_bounds__(32 * kSmemWarps) k_alias_serial(AliasArgs A)
 {
+    __shared__ RowSmem sm_all[kSmemWarps];
+    RowSmem &sm = sm_all[threadIdx.x >> 5];
+    const uint32_t lane = threadIdx.x & 31;
     const uint32_t rows = A.counts[0];
-    for (uint32_t t = blockIdx.x * blockDim.x + threadIdx.x; t < rows; t += gridDim.x * blockDim.x) {
+    const uint32_t warps = gridDim.x * kSmemWarps;
+    for (uint32_t t = blockIdx.x * kSmemWarps + (threadIdx.x >> 5); t < rows; t += warps) {
         const uint32_t u = A.list[t];
         const NodeRec nr = A.node[u];
-        alias_row_serial(A, nr, row_degree(nr), A.off[u]);
+        const uint32_t d = row_degree(nr);  // 33..512
+        const uint64_t o = A.off[u];
+        const uint64_t W = nr.total & 0xffffffffull;
+        const uint64_t eb = NarrowEdges::edge_base(nr.word0 & kBeginMask, d);
+        uint32_t ns = 0, nl = 0;
+        uint64_t Dc = 0, Ec = 0;
+        for (uint32_t e0 = 0; e0 < d; e0 += 32) {
+            const uint32_t i = e0 + lane;
+            uint64_t p = 0;
+            int32_t c = 0;
+            if (i < d) {
+                const EdgeN rec = A.edges[eb + i];
+                const uint32_t lo = i ? A.edges[eb + i - 1].P : 0u;
+                p = (uint64_t)d * (rec.P - lo);
+                c = rec.col;
+                sm.col[i] = c;
+                A.slots[o + i] = AliasRec{(uint32_t)W, c, c, 0u};
+            }
+            const bool isS = i < d && p < W, isL = i < d && p > W;
+            const uint32_t bs = __ballot_sync(0xffffffffu, isS), bl = __ballot_sync(0xffffffffu, isL);
+            const uint32_t lt = (1u << lane) - 1;
+            uint64_t dv = isS ? W - p : 0ull, ev = isL ? p - W : 0ull;
+#pragma unroll
+            for (int q = 1; q < 32; q <<= 1) {
+                const uint64_t yd = __shfl_up_sync(0xffffffffu, dv, q), ye = __shfl_up_sync(0xffffffffu, ev, q);
+                if (lane >= (uint32_t)q) {
+                    dv += yd;
+                    ev += ye;
+                }
+            }
+            if (isS) {
+                const uint32_t k = ns + __popc(bs & lt);
+                sm.idx[k] = (uint16_t)i;
+                sm.sum[k] = Dc + dv;
+            } else if (isL) {
+                const uint32_t k = d - 1 - (nl + __popc(bl & lt));
+                sm.idx[k] = (uint16_t)i;
+                sm.sum[k] = Ec + ev;
+            }
+            ns += __popc(bs);
+            nl += __popc(bl);
+            Dc += __shfl_sync(0xffffffffu, dv, 31);
+            Ec += __shfl_sync(0xffffffffu, ev, 31);
+        }
+        __syncwarp();
+        const uint32_t a = ns, b = nl;
+        if (a > 0 && b > 0 && a + b <= d) {
+            auto E = [&](uint32_t j) { return sm.sum[d - 1 - j]; };
+            auto D = [&](uint32_t q) { return sm.sum[q]; };
+            // small edges t: donor = first large j with E_j > D_(t-1)
+            const uint32_t shs = (a + 31) / 32, t0 = min(lane * shs, a), t1 = min(t0 + shs, a);
+            if (t0 < t1) {
+                uint64_t prev = t0 ? D(t0 - 1) : 0ull;
+                uint32_t jl = 0, jh = b - 1;
+                while (jl < jh) {
+                    const uint32_t mid = (jl + jh) >> 1;
+                    if (E(mid) > prev) jh = mid;
+                    else jl = mid + 1;
+                }
+                uint32_t j = jl;
+                for (uint32_t tt = t0; tt < t1; ++tt) {
+                    while (j + 1 < b && E(j) <= prev) ++j;
+                    const uint64_t Dt = D(tt);
+                    const uint32_t e = sm.idx[tt];
+                    A.slots[o + e].thr = (uint32_t)(W - (Dt - prev));
+                    A.slots[o + e].alias_col = sm.col[sm.idx[d - 1 - j]];
+                    prev = Dt;
+                }
+            }
+            // large edges j (not the last): q = first small with D_q >= E_j
+            const uint32_t nlm = b - 1, shl = (nlm + 31) / 32;
+            const uint32_t j0 = min(lane * shl, nlm), j1 = min(j0 + shl, nlm);
+            if (j0 < j1) {
+                uint64_t Ej = E(j0);
+                uint32_t ql = 0, qh = a - 1;
+                while (ql < qh) {
+                    const uint32_t mid = (ql + qh) >> 1;
+                    if (D(mid) >= Ej) qh = mid;
+                    else ql = mid + 1;
+                }
+                uint32_t q = ql;
+                for (uint32_t j = j0; j < j1; ++j) {
+                    Ej = E(j);
+                    while (q + 1 < a && D(q) < Ej) ++q;
+                    const uint64_t th = W - (D(q) - Ej);
+                    if (th < W) {
+                        const uint32_t e = sm.idx[d - 1 - j];
+                        A.slots[o + e].thr = (uint32_t)th;
+                        A.slots[o + e].alias_col = sm.col[sm.idx[d - 2 - j]];
+                    }
+                }
+            }
+        }
+        __syncwarp();  // the next row reuses the warp's shared memory
     }
 }
 
@@ -1728,7 +1839,7 @@ int build_alias(ppr_graph *g, cudaStream_t st)
         if (e != cudaSuccess) return fail(cuda_fail(e, "alias build"));
     }
     if (hc[0]) {
-        k_alias_serial<<<g->ctx->sms * 8, 256, 0, st>>>(A);
+        k_alias_serial<<<g->ctx->sms * 16, 32 * kSmemWarps, 0, st>>>(A);
         note_launch();
     }
     if (hc[1]) {
