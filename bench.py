@@ -56,6 +56,9 @@ WORKLOADS = {
                         desc="rmat20 graph, alpha in {0.05, 0.1, 0.15, 0.2, 0.3, 0.5}: walker time and step rate"),
     "sweep_chunk": dict(alpha=0.2, R=100, seed=1, topk=32, segments=False,
                         desc="rmat20 graph, chunk_sources x warps_per_block grid against the autotuner's pick"),
+    "chunglu2048alias": dict(alpha=0.15, R=200, seed=1, topk=32, segments=False, sampler=1,
+                             desc="the 2048 Chung-Lu graphs of chunglu2048 with integer alias tables (built once, "
+                                  "outside the replayed step)"),
     "chunglu2048": dict(alpha=0.15, R=200, seed=1, topk=32, segments=False,
                         desc="2048 Chung-Lu graphs (exponent 2.3, n log-uniform in [100, 50000], mean degree 12, "
                              "w U[1,100]) in one block-diagonal graph; one persistent launch replayed as a CUDA graph"),
@@ -240,7 +243,8 @@ def run_reference_batched(args, wl, I, O):
         t0 = time.perf_counter()
         st = wk = 0
         for gi, og, n in ogs:
-            e, stp = O.walks(og, wl["alpha"], wl["R"], wl["seed"], 0, min(n, 64), tag=gi)
+            e, stp = O.walks(og, wl["alpha"], wl["R"], wl["seed"], 0, min(n, 64), tag=gi,
+                             sampler=wl.get("sampler", 0))
             rp, c, cn = O.rows(e, n)
             O.topk(rp, c, cn, wl["topk"])
             st += stp
@@ -273,8 +277,12 @@ def run_reference(args):
     sys.path.insert(0, os.path.join(ROOT, "oracle"))
     import oracle as O
     O.build()
-    if args.workload == "chunglu2048":
+    if args.workload.startswith("chunglu2048"):
         return run_reference_batched(args, wl, I, O)
+    if args.workload in ("serve", "accuracy") or args.workload.startswith("sweep_"):
+        print(json.dumps({"impl": "reference", "unavailable": f"the {args.workload} workload has no oracle arm; "
+                          "its graph workloads (rmat24, rmat20) do"}))
+        return 0
     g = I.workload_graph(base_graph(args.workload))
     og = O.prepare(g.n, g.row_ptr, g.col, g.w)
     n_blk = 64
@@ -334,7 +342,7 @@ def run_batched(args):
     N = int(inst.node_off[-1])
     ctx = ppr.Context(local)
     G = ctx.load_graph_batch(inst.node_off, inst.row_ptr, inst.col, inst.w)
-    run_kw = dict(alpha=wl["alpha"], R=wl["R"], seed=wl["seed"], topk=wl["topk"])
+    run_kw = dict(alpha=wl["alpha"], R=wl["R"], seed=wl["seed"], topk=wl["topk"], sampler=wl.get("sampler", 0))
     t0 = time.perf_counter()
     tun = tune.tuned(G, torch.cuda.get_device_name(dev), sample_sources=400_000, **run_kw)
     tune_s = time.perf_counter() - t0
@@ -436,7 +444,8 @@ def run_batched(args):
         for gi in range(0, inst.count, 128):
             sub = inst.instance(gi)
             og = O.prepare(sub.n, sub.row_ptr, sub.col, sub.w)
-            e, stp = O.walks(og, wl["alpha"], wl["R"], wl["seed"], 0, min(sub.n, 64), tag=gi)
+            e, stp = O.walks(og, wl["alpha"], wl["R"], wl["seed"], 0, min(sub.n, 64), tag=gi,
+                             sampler=wl.get("sampler", 0))
             rp_, c_, n_ = O.rows(e, sub.n)
             O.topk(rp_, c_, n_, k)
             st += stp
@@ -736,7 +745,7 @@ def main():
     args = ap.parse_args()
     if args.impl == "reference":
         return run_reference(args)
-    if args.workload == "chunglu2048":
+    if args.workload.startswith("chunglu2048"):
         return run_batched(args)
     if args.workload == "serve":
         return run_serving(args)

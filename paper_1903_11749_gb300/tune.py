@@ -17,7 +17,8 @@ def cache_path() -> str:
 def key(G, device_name: str, **run) -> str:
     info = G.info()
     return (f"n={info.n};m={info.m};inst={info.instances};R={run.get('R')};alpha={run.get('alpha')};"
-            f"seg={int(bool(run.get('segments', False)))};topk={run.get('topk', 0)};dev={device_name}")
+            f"seg={int(bool(run.get('segments', False)))};sampler={run.get('sampler', 0)};topk={run.get('topk', 0)};"
+            f"dev={device_name}")
 
 
 def tuned(G, device_name: str, sample_sources: int = 0, refresh: bool = False, **run) -> dict:

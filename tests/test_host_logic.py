@@ -1,0 +1,75 @@
+"""Host-side logic that needs no GPU: the tuning cache, workload naming and
+the benchmark's host description."""
+import json
+
+import pytest
+
+import bench
+from paper_1903_11749_gb300 import tune
+
+
+class _Info:
+    n, m, instances = 1000, 12000, 0
+
+
+class _FakeGraph:
+    """Stands in for a loaded graph: counts the tuner calls."""
+
+    def __init__(self):
+        self.calls = 0
+
+    def info(self):
+        return _Info()
+
+    def autotune(self, sample_sources=0, **run):
+        self.calls += 1
+        return {"chunk_sources": 4, "large_degree": 0, "warps_per_block": 8, "ms": 1.5, "candidates": 18,
+                "sample_sources": sample_sources}
+
+
+def test_tuning_cache_hits_and_keys(tmp_path, monkeypatch):
+    monkeypatch.setenv("PPR_TUNE_CACHE", str(tmp_path / "tune.json"))
+    G = _FakeGraph()
+    run = dict(alpha=0.15, R=200, seed=1, topk=32)
+    t1 = tune.tuned(G, "GB300", sample_sources=1000, **run)
+    t2 = tune.tuned(G, "GB300", sample_sources=1000, **run)
+    assert G.calls == 1 and not t1["cached"] and t2["cached"]
+    # another sampler, R or device is another entry
+    tune.tuned(G, "GB300", sample_sources=1000, sampler=1, **run)
+    tune.tuned(G, "other", sample_sources=1000, **run)
+    tune.tuned(G, "GB300", sample_sources=1000, **dict(run, R=100))
+    assert G.calls == 4
+    assert len(json.load(open(tmp_path / "tune.json"))) == 4
+    tune.tuned(G, "GB300", sample_sources=1000, refresh=True, **run)
+    assert G.calls == 5
+    assert tune.launch_kwargs(t1) == {"chunk_sources": 4, "large_degree": 0, "warps_per_block": 8}
+
+
+def test_tuning_cache_survives_a_corrupt_file(tmp_path, monkeypatch):
+    path = tmp_path / "tune.json"
+    path.write_text("{not json")
+    monkeypatch.setenv("PPR_TUNE_CACHE", str(path))
+    G = _FakeGraph()
+    t = tune.tuned(G, "GB300", R=10, alpha=0.2)
+    assert not t["cached"] and G.calls == 1
+    assert len(json.load(open(path))) == 1
+
+
+@pytest.mark.parametrize("name,graph", [("rmat20", "rmat20"), ("rmat20alias", "rmat20"), ("rmat24plain", "rmat24"),
+                                        ("rmat24alias", "rmat24"), ("er1k", "er1k")])
+def test_workload_variants_share_their_graph(name, graph):
+    assert bench.base_graph(name) == graph
+    assert name in bench.WORKLOADS
+
+
+def test_every_workload_is_described():
+    for name, wl in bench.WORKLOADS.items():
+        assert {"alpha", "R", "seed", "topk", "segments", "desc"} <= set(wl), name
+        assert wl.get("sampler", 0) in (0, 1)
+        assert not (wl["segments"] and wl.get("sampler", 0) == 1), name  # segment tables use the prefix rule
+
+
+def test_replica_workload_and_host_description():
+    assert bench.rank_workload(1000, 3, 8) == (0, 1000, 3)  # every source, the rank as the tag
+    h = bench.host_cpu()
+    assert h["nproc"] >= 1 and h["model"] and h["machine"]
