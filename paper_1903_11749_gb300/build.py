@@ -37,16 +37,23 @@ def _deps():
     return out
 
 
-def build(force: bool = False, verbose: bool = False, extra=None) -> str:
-    os.makedirs(BUILD, exist_ok=True)
+LIB_CHECKED = os.path.join(HERE, "libppr_checked.so")
+
+
+def build(force: bool = False, verbose: bool = False, extra=None, checked: bool = False) -> str:
+    """Compiles libppr.so; with checked=True, libppr_checked.so (-DPPR_CHECKED:
+    every node index and row extent a walk step reads is tested first)."""
+    lib = LIB_CHECKED if checked else LIB
+    bdir = BUILD + ("_checked" if checked else "")
+    os.makedirs(bdir, exist_ok=True)
     newest = max(os.path.getmtime(p) for p in _deps())
-    if not force and os.path.exists(LIB) and os.path.getmtime(LIB) >= newest and not extra:
-        return LIB
+    if not force and os.path.exists(lib) and os.path.getmtime(lib) >= newest and not extra:
+        return lib
     cc = nvcc()
-    extra = list(extra or [])
+    extra = list(extra or []) + (["-DPPR_CHECKED"] if checked else [])
 
     def compile_one(src):
-        obj = os.path.join(BUILD, os.path.basename(src)[:-3] + ".o")
+        obj = os.path.join(bdir, os.path.basename(src)[:-3] + ".o")
         cmd = [cc, *ARCH, *FLAGS, *extra, "-c", src, "-o", obj]
         res = subprocess.run(cmd, capture_output=True, text=True)
         if res.returncode != 0:
@@ -59,13 +66,13 @@ def build(force: bool = False, verbose: bool = False, extra=None) -> str:
         for _, err in results:
             if err:
                 print(err)
-    tmp = LIB + f".tmp{os.getpid()}"
+    tmp = lib + f".tmp{os.getpid()}"
     cmd = [cc, *ARCH, "-shared", "-o", tmp, *[o for o, _ in results], "-lcudart_static", "-ldl", "-lrt", "-lpthread"]
     res = subprocess.run(cmd, capture_output=True, text=True)
     if res.returncode != 0:
         raise RuntimeError(f"link failed:\n{res.stderr}")
-    os.replace(tmp, LIB)
-    return LIB
+    os.replace(tmp, lib)
+    return lib
 
 
 if __name__ == "__main__":

@@ -512,7 +512,7 @@ static int run_common(ppr_ctx *ctx, const ppr_graph *g, const ppr_run_args *a, c
         if ((rc = dev_alloc((void **)&r->d_topk_idx, sizeof(int32_t) * S * r->topk, "top-k ids", st))) return fail(rc);
         if ((rc = dev_alloc((void **)&r->d_topk_cnt, sizeof(uint32_t) * S * r->topk, "top-k counts", st))) return fail(rc);
     }
-    if ((rc = dev_alloc((void **)&r->d_steps, sizeof(unsigned long long) * 4, "counters", st))) return fail(rc);
+    if ((rc = dev_alloc((void **)&r->d_steps, sizeof(unsigned long long) * 8, "counters", st))) return fail(rc);
     uint32_t *d_list = nullptr;
     if (list) {
         if ((rc = dev_alloc((void **)&d_list, sizeof(uint32_t) * S, "source list", st))) return fail(rc);
@@ -540,7 +540,7 @@ static int run_common(ppr_ctx *ctx, const ppr_graph *g, const ppr_run_args *a, c
     unsigned char *ws = nullptr;
     if ((rc = dev_alloc((void **)&ws, launch_workspace_bytes(g, plan, batch), "walk workspace", st))) return fail(rc);
     r->scratch.push_back(ws);
-    if ((e = cudaMemsetAsync(r->d_steps, 0, sizeof(unsigned long long) * 4, st)) != cudaSuccess)
+    if ((e = cudaMemsetAsync(r->d_steps, 0, sizeof(unsigned long long) * 8, st)) != cudaSuccess)
         return fail(cuda_fail(e, "memset"));
     if ((e = cudaEventRecord(r->ev_start, st)) != cudaSuccess) return fail(cuda_fail(e, "cudaEventRecord"));
     const Outputs o{r->d_nnz, r->d_cols, r->d_cnts, r->cap, r->d_topk_idx, r->d_topk_cnt, r->topk, r->d_steps};
@@ -670,9 +670,9 @@ int ppr_run_to_host(ppr_ctx *ctx, const ppr_graph *g, const ppr_run_args *a, int
             (e = cudaEventCreateWithFlags(&q.copied, cudaEventDisableTiming)) != cudaSuccess)
             return finish(cuda_fail(e, "cudaEventCreate"));
     }
-    if ((rc = dev_alloc((void **)&r->d_steps, sizeof(unsigned long long) * 4, "counters", st))) return finish(rc);
+    if ((rc = dev_alloc((void **)&r->d_steps, sizeof(unsigned long long) * 8, "counters", st))) return finish(rc);
     if ((rc = dev_alloc((void **)&ws, launch_workspace_bytes(g, plan, B), "walk workspace", st))) return finish(rc);
-    if ((e = cudaMemsetAsync(r->d_steps, 0, sizeof(unsigned long long) * 4, st)) != cudaSuccess)
+    if ((e = cudaMemsetAsync(r->d_steps, 0, sizeof(unsigned long long) * 8, st)) != cudaSuccess)
         return finish(cuda_fail(e, "memset"));
     const int cblocks = (int)std::min<int64_t>((B + 7) / 8, (int64_t)ctx->sms * 32);
     uint64_t base = 0;
@@ -724,10 +724,14 @@ int ppr_run_to_host(ppr_ctx *ctx, const ppr_graph *g, const ppr_run_args *a, int
     if ((e = cudaStreamSynchronize(cs)) != cudaSuccess || (e = cudaStreamSynchronize(st)) != cudaSuccess)
         return finish(cuda_fail(e, "run"));
     if (nnz) *nnz = (int64_t)base;
+    unsigned long long c[5] = {0, 0, 0, 0, 0};
+    if ((e = cudaMemcpy(c, r->d_steps, sizeof(c), cudaMemcpyDeviceToHost)) != cudaSuccess)
+        return finish(cuda_fail(e, "counters"));
+    if (c[4]) {  // only a checked build sets it
+        set_error("checked build: an index left its array (flags 0x%llx)", c[4]);
+        return finish(PPR_ECUDA);
+    }
     if (info) {
-        unsigned long long c[4] = {0, 0, 0, 0};
-        if ((e = cudaMemcpy(c, r->d_steps, sizeof(c), cudaMemcpyDeviceToHost)) != cudaSuccess)
-            return finish(cuda_fail(e, "counters"));
         float kms = 0.f, ms = 0.f;
         for (size_t t = 0; t + 1 < r->walk_events.size(); t += 2) {
             if (cudaEventElapsedTime(&ms, r->walk_events[t], r->walk_events[t + 1]) == cudaSuccess) kms += ms;
@@ -936,10 +940,15 @@ int ppr_wait(ppr_result *r, int64_t timeout_ms)
         }
         std::this_thread::sleep_for(std::chrono::microseconds(50));
     }
-    unsigned long long cnt[3] = {0, 0, 0};
+    unsigned long long cnt[5] = {0, 0, 0, 0, 0};
     PPR_CUDA(cudaMemcpy(cnt, r->d_steps, sizeof(cnt), cudaMemcpyDeviceToHost));
     r->steps = cnt[0];
     r->sectors = cnt[2];
+    if (cnt[4]) {  // only a checked build sets it
+        set_error("checked build: an index left its array (flags 0x%llx: 1 node, 2 edge row, 4 segment table, "
+                  "8 endpoint)", cnt[4]);
+        return PPR_ECUDA;
+    }
     float ms = 0.f;
     PPR_CUDA(cudaEventElapsedTime(&ms, r->ev_start, r->ev_walk_end));
     r->run_ms = ms;

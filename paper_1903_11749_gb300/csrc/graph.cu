@@ -639,6 +639,7 @@ static int build_narrow(ppr_ctx *ctx, int64_t n, int64_t m, const int64_t *d_rp,
     if ((rc = dev_alloc((void **)&g->node, sizeof(NodeRec) * n, "node records", st))) return rc;
     const size_t edge_bytes = (size_t)(slots > 0 ? slots : 2) * sizeof(EdgeN);
     if ((rc = dev_alloc(&g->edges, edge_bytes, "edge records", st))) return rc;
+    g->edge_records = (int64_t)slots;
     g->device_bytes = (int64_t)(sizeof(NodeRec) * n + edge_bytes);
     BuildArgs A{n, d_rp, d_col, d_w, d_off, g->instances, d_region, g->node, (EdgeN *)g->edges, d_ls, d_list};
     k_build_small<<<tblocks, 256, 0, st>>>(A);
@@ -796,6 +797,7 @@ int build_graph(ppr_ctx *ctx, int64_t n, int64_t m, const int64_t *row_ptr, cons
     {
         size_t edge_bytes = (size_t)m * sizeof(EdgeW);
         if ((rc = dev_alloc(&g->edges, edge_bytes > 0 ? edge_bytes : 16, "edge records", st))) return cleanup(), rc;
+        g->edge_records = m;
         g->device_bytes = (int64_t)(sizeof(NodeRec) * n + edge_bytes);
         k_rows_pass2<true><<<blocks, threads, 0, st>>>(n, d_rp, d_col, d_w, d_off, g->instances, d_W, g->node, g->edges);
         note_launch();

@@ -82,6 +82,7 @@ struct ppr_graph {
     bool wide = false;
     ppr::NodeRec *node = nullptr;
     void *edges = nullptr;  // EdgeN[m] or EdgeW[m]
+    int64_t edge_records = 0;  // records the edge layout holds (blocked narrow rows: with padding)
     // block-diagonal instances
     int32_t instances = 0;
     std::vector<int64_t> node_off;  // host copy, count+1

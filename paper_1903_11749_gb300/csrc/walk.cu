@@ -49,8 +49,30 @@ struct KParams {
     unsigned long long *steps;    // [0] draws consumed, [2] algorithmic sectors (statistics launch)
     uint32_t P2;              // next_pow2(R)
     uint64_t r_magic;         // ceil(2^40 / R): walk index -> source index by multiply-shift
-    int64_t n_nodes;          // node records (for the L2 window)
+    int64_t n_nodes;          // node records (for the L2 window and the checked build)
+    uint64_t n_records;       // checked build: records of the edge layout walked (alias: slots)
+    uint64_t n_seg;           // checked build: segment entries
+    unsigned long long *err;  // checked build: flags of indices that left their array
 };
+
+// Checked build (-DPPR_CHECKED): every node index and every row extent a step
+// is about to read is tested against its array first; a bad one sets a flag
+// in p.err (1 node, 2 edge row, 4 segment table, 8 endpoint slot) and ends the
+// walk instead of reading, so the host reports the run as failed; nothing traps.
+#ifdef PPR_CHECKED
+#define PPR_CHECK(cond, flag)                                  \
+    do {                                                       \
+        if (!(cond)) {                                         \
+            atomicOr(p.err, (unsigned long long)(flag));       \
+            end = 0;                                           \
+            return true;                                       \
+        }                                                      \
+    } while (0)
+#else
+#define PPR_CHECK(cond, flag) \
+    do {                      \
+    } while (0)
+#endif
 
 // One step of one walk.  Returns true when the walk has ended (end is set).
 // With COOP, every lane of the warp calls it (inactive lanes with act=false)
@@ -70,8 +92,18 @@ __device__ __forceinline__ bool walk_step(const KParams &p, const E &edges, bool
 {
     uint4 x = make_uint4(0, 0, 0, 0);
     uint64_t w0 = 0, total = 0;
+#ifdef PPR_CHECKED
+    bool bad_node = false;
+#endif
     if (act) {
         x = philox4x32_10(make_uint4(sctr, j, k, tag), p.k0, p.k1);
+#ifdef PPR_CHECKED
+        if ((uint64_t)u >= (uint64_t)p.n_nodes) {
+            atomicOr(p.err, 1ull);
+            bad_node = true;
+            u = 0;  // read a valid record; the walk ends at this step
+        }
+#endif
         NodeRec r = load_node(p.node, u);
         w0 = r.word0;
         total = r.total;
@@ -80,9 +112,16 @@ __device__ __forceinline__ bool walk_step(const KParams &p, const E &edges, bool
     const uint64_t beg = w0 & kBeginMask;
     const bool segf = SEG && (w0 >> 63);
     const uint64_t r64 = (uint64_t)x.x | ((uint64_t)x.y << 32);
+#ifdef PPR_CHECKED
+    if (act && bad_node) {  // flagged above
+        end = 0;
+        return true;
+    }
+#endif
     if constexpr (std::is_same<E, AliasEdges>::value) {
         // integer alias method: slot j = floor(r*d / 2^64), y = floor(frac * W / 2^64)
         if (!act) return false;
+        PPR_CHECK(cnt < 2 || beg + cnt <= p.n_records, 2);
         if (STATS) ++tl.sectors;  // the node record
         uint32_t next;
         if (cnt == 0) {
@@ -134,6 +173,10 @@ __device__ __forceinline__ bool walk_step(const KParams &p, const E &edges, bool
     }
     if (!act) return false;
     if (STATS) ++tl.sectors;  // the node record
+    PPR_CHECK(!segf || beg + cnt <= p.n_seg, 4);
+    PPR_CHECK(segf || cnt < 2 ||
+                  beg + (sizeof(typename E::Rec) == 8 ? (uint64_t)blocked_row_records(cnt) : (uint64_t)cnt) <= p.n_records,
+              2);
     if (segf) {
         SegTable tab{p.seg};
         uint4 o = STATS ? search_serial_tally(tab, beg, cnt, xr, tl.sectors) : search_serial(tab, beg, cnt, xr);
@@ -362,6 +405,10 @@ __global__ void __launch_bounds__(256, PPR_WALK_MINB) k_walk_persistent(KParams 
 
         uint32_t end = 0;
         if (walk_step<E, SEG, true, STATS>(p, edges, active, src, sctr, j, tag, k, u, end, tl)) {
+#ifdef PPR_CHECKED
+            if (slot >= (uint64_t)(p.s_end - p.s_begin) * p.R) atomicOr(p.err, 8ull);
+            else
+#endif
             p.ends[slot] = end - ctr_base;
             active = false;
         }
@@ -585,6 +632,9 @@ int launch_walks(ppr_ctx *ctx, const ppr_graph *g, const RunPlan &plan, const Ou
     kp.P2 = P2;
     kp.r_magic = ((1ull << 40) + plan.R - 1) / plan.R;
     kp.n_nodes = g->n;
+    kp.n_records = plan.sampler == 1 ? (uint64_t)g->m : (uint64_t)g->edge_records;
+    kp.n_seg = (uint64_t)g->seg.entries_n;
+    kp.err = o.counters + 4;
     kp.ends = reinterpret_cast<uint32_t *>(ws);
     size_t off = align256((size_t)S * plan.R * sizeof(uint32_t));
 

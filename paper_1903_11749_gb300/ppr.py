@@ -14,7 +14,8 @@ import os
 import numpy as np
 
 _HERE = os.path.dirname(os.path.abspath(__file__))
-LIB_PATH = os.path.join(_HERE, "libppr.so")
+# PPR_LIBRARY_PATH selects another build of the library (the checked build)
+LIB_PATH = os.environ.get("PPR_LIBRARY_PATH") or os.path.join(_HERE, "libppr.so")
 
 PPR_OK, PPR_EINVAL, PPR_ENOMEM, PPR_ECUDA, PPR_ETIMEOUT, PPR_ERANGE, PPR_EBUSY, PPR_ENOTSUP = 0, -1, -2, -3, -4, -5, -6, -7
 PPR_PTRS_DEVICE = 1
