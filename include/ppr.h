@@ -19,6 +19,10 @@
  *                    k = steps taken so far (mod 2^32).
  *   r64 = x0 | x1 << 32; next edge = smallest e of the row with
  *   P[e] > floor(r64 * W_u / 2^64), P the inclusive row prefix of weights.
+ *   With sampler = 1 the next edge comes from the row's integer alias table
+ *   instead (Algorithm 1, Sec. 2.2): slot j = floor(r64 * d / 2^64),
+ *   y = floor(((r64 * d) mod 2^64) * W_u / 2^64), edge j if y < thr(j), else
+ *   its alias; the same law, a different map from draws to edges.
  *   A node with no out-edge restarts the walk at its source (Sec. 2.1;
  *   dangling = 0) or ends the walk there without a step (dangling = 1).
  *   Segment mode (Algorithm 4, "big moves", fixed depth 3, out-degree <= 8)
