@@ -955,7 +955,7 @@ def main():
                            "topk": wl["topk"], "n": g.n, "m": g.m, "sources": g.n,
                            "parallelism": f"{world} independent replicas (tag = rank)" if world > 1 else "1 GPU",
                            "l2": "flushed between steps (512 MB write)"},
-                "step_ms_each": step_ms, "walks_per_s": walks_s,
+                "step_ms_each": step_ms, "ms_per_step_median": statistics.median(step_ms), "walks_per_s": walks_s,
                 "steps_per_walk": steps_per_pass / max(walks_per_pass, 1),
                 "draws_per_s": draws_per_pass * args.steps * world / T_max,
                 "steps_counted": "plain-equivalent walks*2^32/T" if wl["segments"] else "draws (one per step)",

@@ -59,3 +59,49 @@ def test_rmat20_every_source_equals_threaded_oracle(oracle, graph, sampler):
     assert not bad, f"ranges differing from the oracle: {bad[:5]}"
     assert sum(s for _, s in out) == steps_gpu
     print(f"oracle over {g.n} sources on {threads} threads: {dt:.1f} s ({steps_gpu / dt / 1e6:.1f} M steps/s)")
+
+
+@pytest.mark.skipif(os.environ.get("PPR_FULLSIZE_C3") != "1",
+                    reason="several minutes of host oracle time; set PPR_FULLSIZE_C3=1 to run")
+@pytest.mark.parametrize("mode", ["segments", "alias"])
+def test_rmat24_every_source_equals_threaded_oracle(oracle, mode):
+    """The scale-24 workload (16,777,216 sources, R 50, alpha 0.15, hub of
+    1.57 M edges): every source against the oracle in source ranges on host
+    threads, with depth-3 segment tables (the oracle builds every table up
+    front, so the threads only read them) or with alias tables."""
+    from paper_1903_11749_gb300 import build as B
+    B.build()
+    from paper_1903_11749_gb300 import ppr
+    g = I.workload_graph("rmat24")
+    kw = dict(alpha=0.15, R=50, seed=1)
+    seg, sampler = (True, 0) if mode == "segments" else (False, 1)
+    G = ppr.Context(0).load_graph(g.n, g.row_ptr, g.col, g.w)
+    res = G.run(segments=seg, sampler=sampler, **kw)
+    rp, col, cnt = res.sparse_rows()
+    steps_gpu = res.info().steps
+    del res, G
+    og = oracle.prepare(g.n, g.row_ptr, g.col, g.w)
+    if seg:
+        oracle.build_segments(og, oracle.threshold(kw["alpha"]))
+    else:
+        oracle.build_alias(og)
+    block = 1 << 16
+    ranges = [(a, min(g.n, a + block)) for a in range(0, g.n, block)]
+
+    def check(r):
+        a, b = r
+        ends, steps = oracle.walks(og, kw["alpha"], kw["R"], kw["seed"], a, b, segments=seg, sampler=sampler)
+        orp, ocol, ocnt = oracle.rows(ends, g.n)
+        ok = (np.array_equal(rp[a:b + 1] - rp[a], orp) and np.array_equal(col[rp[a]:rp[b]], ocol)
+              and np.array_equal(cnt[rp[a]:rp[b]], ocnt))
+        return ok, steps
+
+    threads = min(32, os.cpu_count() or 1)
+    t0 = time.perf_counter()
+    with ThreadPoolExecutor(threads) as ex:
+        out = list(ex.map(check, ranges))
+    dt = time.perf_counter() - t0
+    bad = [r for r, (ok, _) in zip(ranges, out) if not ok]
+    assert not bad, f"ranges differing from the oracle: {bad[:5]}"
+    assert sum(s for _, s in out) == steps_gpu
+    print(f"oracle over {g.n} sources ({mode}) on {threads} threads: {dt:.1f} s ({steps_gpu / dt / 1e6:.1f} M draws/s)")

@@ -77,6 +77,26 @@ def test_small_graphs_ragged(ppr, ctx, oracle, R, kernel):
         assert_same(res, ref, topk=min(R, 5))
 
 
+@pytest.mark.parametrize("R,topk", [(1025, 40), (1500, 1500), (4096, 4096), (2048, 7)])
+def test_large_R_shared_memory_reduction(ppr, ctx, oracle, R, topk):
+    """R above 1024 takes the shared-memory reduction (next_pow2(R) > 1024);
+    top-k up to the largest k (4096), both kernels, both samplers."""
+    g = I.random_small_graph(600, 3000, seed=R, wmax=30, dangling=6)
+    G = ctx.load_graph(g.n, g.row_ptr, g.col, g.w)
+    og = oracle.prepare(g.n, g.row_ptr, g.col, g.w)
+    for sampler in (0, 1):
+        ends, steps = oracle.walks(og, 0.25, R, 3, 0, 40, sampler=sampler)
+        orp, ocol, ocnt = oracle.rows(ends, g.n)
+        oidx, otc = oracle.topk(orp, ocol, ocnt, topk)
+        for kernel in (0, 1):
+            res = G.run(alpha=0.25, R=R, seed=3, src_end=40, topk=topk, kernel=kernel, sampler=sampler)
+            rp, col, cnt = res.sparse_rows()
+            assert np.array_equal(rp, orp) and np.array_equal(col, ocol) and np.array_equal(cnt, ocnt)
+            idx, tc = res.topk(topk)
+            assert np.array_equal(idx, oidx) and np.array_equal(tc, otc)
+            assert res.info().steps == steps
+
+
 def test_topk_larger_than_R(ppr, ctx, oracle):
     """k above R (and above next_pow2(R)) returns the whole row by count, padded."""
     g = I.er_graph(300, 2000, seed=6)
