@@ -105,3 +105,47 @@ def test_rmat24_every_source_equals_threaded_oracle(oracle, mode):
     assert not bad, f"ranges differing from the oracle: {bad[:5]}"
     assert sum(s for _, s in out) == steps_gpu
     print(f"oracle over {g.n} sources ({mode}) on {threads} threads: {dt:.1f} s ({steps_gpu / dt / 1e6:.1f} M draws/s)")
+
+
+@pytest.mark.skipif(os.environ.get("PPR_FULLSIZE_C4") != "1",
+                    reason="several minutes of host oracle time; set PPR_FULLSIZE_C4=1 to run")
+@pytest.mark.parametrize("sampler", [0, 1])
+def test_chunglu2048_every_source_equals_threaded_oracle(oracle, sampler):
+    """The 2,048-instance batched workload (16.3 M sources, R 200, alpha 0.15,
+    top-32) in one fused launch: every instance against the oracle run on
+    that instance alone with its id as the tag, instances spread over host
+    threads."""
+    from paper_1903_11749_gb300 import build as B
+    B.build()
+    from paper_1903_11749_gb300 import ppr
+    inst = I.chung_lu_instances(2048, 100, 50_000, 12.0, 2.3, 1, 100, seed=4242)
+    kw = dict(alpha=0.15, R=200, seed=1)
+    G = ppr.Context(0).load_graph_batch(inst.node_off, inst.row_ptr, inst.col, inst.w)
+    res = G.run(topk=32, sampler=sampler, **kw)
+    rp, col, cnt = res.sparse_rows()
+    idx, tc = res.topk()
+    steps_gpu = res.info().steps
+    del res, G
+
+    def check(gi):
+        sub = inst.instance(gi)
+        og = oracle.prepare(sub.n, sub.row_ptr, sub.col, sub.w)
+        ends, steps = oracle.walks(og, kw["alpha"], kw["R"], kw["seed"], tag=gi, sampler=sampler)
+        orp, ocol, ocnt = oracle.rows(ends, sub.n)
+        oidx, otc = oracle.topk(orp, ocol, ocnt, 32)
+        a, b = int(inst.node_off[gi]), int(inst.node_off[gi + 1])
+        ok = (np.array_equal(rp[a:b + 1] - rp[a], orp) and np.array_equal(col[rp[a]:rp[b]], ocol)
+              and np.array_equal(cnt[rp[a]:rp[b]], ocnt) and np.array_equal(idx[a:b], oidx)
+              and np.array_equal(tc[a:b], otc))
+        return ok, steps
+
+    threads = min(32, os.cpu_count() or 1)
+    t0 = time.perf_counter()
+    with ThreadPoolExecutor(threads) as ex:
+        out = list(ex.map(check, range(inst.count)))
+    dt = time.perf_counter() - t0
+    bad = [gi for gi, (ok, _) in enumerate(out) if not ok]
+    assert not bad, f"instances differing from the oracle: {bad[:5]}"
+    assert sum(s for _, s in out) == steps_gpu
+    print(f"oracle over {inst.count} instances ({int(inst.node_off[-1])} sources, sampler {sampler}) on "
+          f"{threads} threads: {dt:.1f} s ({steps_gpu / dt / 1e6:.1f} M draws/s)")
