@@ -490,6 +490,66 @@ __device__ __forceinline__ void warp_sort_reg(uint32_t (&v)[E])
     }
 }
 
+// Top-K of one row without sorting every run, for K <= 32 and K < nrun:
+// kv holds the keys (R - count) << 12 | run of runs e * 32 + lane (0xFFFFFFFF
+// past nrun), and the answer is the K smallest keys in ascending order.  The
+// count rank q = key >> 12 of the K-th smallest key is found by bisection
+// over [0, R - 1] with ballot counts; every key with q below it is taken (fewer
+// than K, sorted in one register per lane), then the first keys with q equal
+// to it in run order (= ascending key, as runs are numbered in id order)
+// fill the remaining places.  cbuf: 32 uint32 of per-warp shared memory.
+template <int E>
+__device__ __forceinline__ void topk_select_reg(const uint32_t (&kv)[E], uint32_t K, uint32_t R,
+                                                const uint32_t *run_id, uint32_t *cbuf, const AggOut &o, uint64_t tb)
+{
+    const uint32_t lane = threadIdx.x & 31, below = (1u << lane) - 1;
+    auto count_le = [&](uint32_t t) {
+        uint32_t c = 0;
+#pragma unroll
+        for (int e = 0; e < E; ++e) c += __popc(__ballot_sync(0xffffffffu, (kv[e] >> 12) <= t));
+        return c;
+    };
+    // smallest t with count_le(t) >= K; count_le(R - 1) = nrun > K.  Most rows
+    // have fewer than K runs of count >= 2, so t = R - 1 is tried first.
+    uint32_t lo = 0, hi = R - 1;
+    if (R >= 2 && count_le(R - 2) < K) lo = R - 1;
+    else hi = R >= 2 ? R - 2 : 0;
+    while (lo < hi) {
+        const uint32_t mid = (lo + hi) >> 1;
+        if (count_le(mid) >= K) hi = mid;
+        else lo = mid + 1;
+    }
+    const uint32_t t = lo;
+    uint32_t nlt = 0;  // keys below t, gathered into cbuf in run order
+#pragma unroll
+    for (int e = 0; e < E; ++e) {
+        const bool lt = (kv[e] >> 12) < t;
+        const uint32_t ml = __ballot_sync(0xffffffffu, lt);
+        if (lt) cbuf[nlt + __popc(ml & below)] = kv[e];
+        nlt += __popc(ml);
+    }
+    __syncwarp();
+    // nlt < K places for the keys below t, sorted; then K - nlt keys equal to t
+    uint32_t v[1] = {lane < nlt ? cbuf[lane] : 0xffffffffu};
+    warp_sort_reg<1>(v);
+    if (lane < nlt) {
+        o.topk_idx[tb + lane] = (int32_t)run_id[v[0] & 0xfffu];
+        o.topk_cnt[tb + lane] = R - (v[0] >> 12);
+    }
+    uint32_t seen = 0;
+#pragma unroll
+    for (int e = 0; e < E; ++e) {
+        const bool eq = (kv[e] >> 12) == t;
+        const uint32_t me = __ballot_sync(0xffffffffu, eq);
+        const uint32_t pos = nlt + seen + __popc(me & below);
+        if (eq && pos < K) {
+            o.topk_idx[tb + pos] = (int32_t)run_id[kv[e] & 0xfffu];
+            o.topk_cnt[tb + pos] = R - t;
+        }
+        seen += __popc(me);
+    }
+}
+
 // scratch: 3 * R uint32 of per-warp shared memory
 template <int E>
 __device__ inline void aggregate_source_reg(const uint32_t *ends, uint32_t R, uint32_t *scratch, const AggOut &o,
@@ -542,25 +602,30 @@ __device__ inline void aggregate_source_reg(const uint32_t *ends, uint32_t R, ui
             const uint32_t i = (uint32_t)e * 32 + lane;
             kv[e] = i < nrun ? kbuf[i] : 0xffffffffu;
         }
-        warp_sort_reg<E>(kv);
         const uint64_t tb = out_row * (uint64_t)o.topk;
+        const uint32_t K = (uint32_t)o.topk;
+        if (E > 1 && K <= 32 && K < nrun) {
+            topk_select_reg<E>(kv, K, R, run_id, start_pos, o, tb);
+        } else {
+            warp_sort_reg<E>(kv);
 #pragma unroll
-        for (int e = 0; e < E; ++e) {
-            const uint32_t i = (uint32_t)e * 32 + lane;
-            if (i < (uint32_t)o.topk) {
-                if (i < nrun) {
-                    o.topk_idx[tb + i] = (int32_t)run_id[kv[e] & 0xfffu];
-                    o.topk_cnt[tb + i] = R - (kv[e] >> 12);
-                } else {
-                    o.topk_idx[tb + i] = -1;
-                    o.topk_cnt[tb + i] = 0;
+            for (int e = 0; e < E; ++e) {
+                const uint32_t i = (uint32_t)e * 32 + lane;
+                if (i < K) {
+                    if (i < nrun) {
+                        o.topk_idx[tb + i] = (int32_t)run_id[kv[e] & 0xfffu];
+                        o.topk_cnt[tb + i] = R - (kv[e] >> 12);
+                    } else {
+                        o.topk_idx[tb + i] = -1;
+                        o.topk_cnt[tb + i] = 0;
+                    }
                 }
             }
-        }
-        // k may exceed the sorted block (k > next_pow2(R) >= nnz): pad the rest
-        for (uint32_t i = 32u * E + lane; i < (uint32_t)o.topk; i += 32) {
-            o.topk_idx[tb + i] = -1;
-            o.topk_cnt[tb + i] = 0;
+            // k may exceed the sorted block (k > next_pow2(R) >= nnz): pad the rest
+            for (uint32_t i = 32u * E + lane; i < K; i += 32) {
+                o.topk_idx[tb + i] = -1;
+                o.topk_cnt[tb + i] = 0;
+            }
         }
     }
     __syncwarp();

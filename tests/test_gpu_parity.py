@@ -107,6 +107,22 @@ def test_topk_larger_than_R(ppr, ctx, oracle):
             assert_same(G.run(alpha=0.15, R=R, seed=2, topk=k, kernel=kernel), ref, topk=k)
 
 
+@pytest.mark.parametrize("R", [33, 64, 100, 200, 513, 1024])
+def test_topk_selection_at_count_ties(ppr, ctx, oracle, R):
+    """Top-k below the number of distinct endpoints (k <= 32, R > 32) is
+    selected by a count threshold instead of a full sort: rows where many
+    endpoints tie at the threshold count (a 40-node dense graph, a few counts
+    shared by many ids) and rows of mostly singletons (a 3,000-node graph)
+    give the oracle's order, count descending then id ascending."""
+    for g, alpha in ((I.er_graph(40, 600, 1, 3, seed=R), 0.2), (I.random_small_graph(3000, 20000, seed=R, wmax=5), 0.1)):
+        G = ctx.load_graph(g.n, g.row_ptr, g.col, g.w)
+        og = oracle.prepare(g.n, g.row_ptr, g.col, g.w)
+        for k in (1, 2, 17, 31, 32):
+            ref = oracle_rows(oracle, g, alpha, R, 9, s_end=min(g.n, 300), topk=k, og=og)
+            res = G.run(alpha=alpha, R=R, seed=9, src_end=min(g.n, 300), topk=k)
+            assert_same(res, ref, topk=k)
+
+
 def test_self_loops_parallel_edges_and_skew(ppr, ctx, oracle):
     g = I.from_edges(6, [(0, 1, 1000), (0, 2, 1), (0, 1, 3), (1, 1, 2), (1, 3, 5), (2, 0, 1), (2, 4, 7), (3, 0, 1),
                          (3, 5, 1), (4, 2, 2)])
