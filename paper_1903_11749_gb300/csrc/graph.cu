@@ -136,11 +136,13 @@ __global__ void k_rows_pass2(int64_t n, const int64_t *row_ptr, const int32_t *c
 // The narrow (32-bit prefix) layout is built in one validating pass over the
 // input: k_layout checks row_ptr and sizes every blocked row; after the scan
 // of those sizes, k_build_small builds every row of at most 32 edges with one
-// thread, and queues longer rows for k_build_mid (one warp per row) and
-// k_build_big (one block per row).  A row total >= 2^32 sets kWide and the
-// graph is rebuilt in the wide layout.
+// thread, and queues longer rows for k_build_mid (one warp per row, up to
+// 1,024 edges) and k_build_big (one block per row, up to 8,192); longer rows
+// are cut into tiles.  The limits keep every row within a few passes of its
+// group, so no single long row leaves the GPU idle behind it.  A row total
+// >= 2^32 sets kWide and the graph is rebuilt in the wide layout.
 enum : uint32_t { kWide = 8u, kBigDegree = 16u };
-constexpr uint32_t kSmallRow = 32, kMidRow = 8192, kHugeRow = 65536;
+constexpr uint32_t kSmallRow = 32, kMidRow = 1024, kHugeRow = 8192;
 constexpr uint32_t kBuildTile = 8192;  // edges per tile block of a huge row (256 threads x 32)
 
 struct LayoutStats {
@@ -264,6 +266,67 @@ __device__ void write_upper_levels(uint32_t *K, uint64_t reg, uint32_t d, uint32
     }
 }
 
+// Each thread of a row's group takes a run of kRun consecutive edges per pass:
+// its kRun loads are independent, so a pass costs one memory latency for
+// 32 * kRun (warp) or 512 * kRun (block) edges.
+constexpr uint32_t kRun = 4;
+
+struct EdgeRun {
+    uint32_t w[kRun];
+    int32_t c[kRun];
+    uint64_t sum;
+};
+
+// Loads edges [i0, i0 + kRun) of row (a, d); missing ones read as weight 0.
+__device__ __forceinline__ EdgeRun load_run(const BuildArgs &A, int64_t a, uint32_t d, uint32_t i0, int64_t hi_id,
+                                            uint32_t &flags)
+{
+    EdgeRun r;
+    r.sum = 0;
+#pragma unroll
+    for (uint32_t q = 0; q < kRun; ++q) {
+        const uint32_t i = i0 + q;
+        r.w[q] = 0;
+        r.c[q] = 0;
+        if (i < d) {
+            r.w[q] = A.w[a + i];
+            r.c[q] = A.col[a + i];
+        }
+    }
+#pragma unroll
+    for (uint32_t q = 0; q < kRun; ++q) {
+        if (i0 + q < d) {
+            if (r.w[q] == 0) flags |= kBadWeight;
+            if (r.c[q] < 0 || (int64_t)r.c[q] >= hi_id) flags |= kBadCol;
+        }
+        r.sum += r.w[q];
+    }
+    return r;
+}
+
+// Writes the run's records (P after each edge, target) from the exclusive
+// prefix P0, padding records past d included (a row's region is padded to a
+// multiple of 4 records, and i0 is a multiple of 4), and its level-1 keys.
+__device__ __forceinline__ void write_run(const BuildArgs &A, uint32_t *K, const EdgeRun &r, uint64_t P0, uint64_t reg,
+                                          uint64_t eb, uint32_t d, uint32_t L, uint32_t i0, int64_t base_id)
+{
+    if (i0 >= d) return;
+    uint32_t v[8];
+    uint64_t P = P0;
+#pragma unroll
+    for (uint32_t q = 0; q < kRun; ++q) {
+        const uint32_t i = i0 + q;
+        P += r.w[q];
+        const bool in = i < d;
+        v[2 * q] = in ? (uint32_t)P : 0xffffffffu;
+        v[2 * q + 1] = in ? (uint32_t)(r.c[q] + base_id) : 0u;
+        if (in && ((i & 7) == 7 || i == d - 1)) K[key_slot(reg, d, L, 1, i >> 3)] = (uint32_t)P;
+    }
+    uint4 *dst = reinterpret_cast<uint4 *>(A.E + eb + i0);  // 32-byte aligned
+    dst[0] = make_uint4(v[0], v[1], v[2], v[3]);
+    dst[1] = make_uint4(v[4], v[5], v[6], v[7]);
+}
+
 __global__ void __launch_bounds__(256) k_build_small(BuildArgs A)
 {
     uint32_t *K = reinterpret_cast<uint32_t *>(A.E);
@@ -331,38 +394,19 @@ __global__ void __launch_bounds__(256) k_build_mid(BuildArgs A)
         const uint32_t L = tree_levels(d);
         const uint64_t eb = reg + 4ull * summary_sectors(d);
         uint64_t carry = 0;
-        for (uint32_t e0 = 0; e0 < d; e0 += 32) {
-            const uint32_t i = e0 + lane;
-            uint64_t v = 0;
-            int64_t c = 0;
-            if (i < d) {
-                v = A.w[a + i];
-                c = A.col[a + i];
-                if (v == 0) flags |= kBadWeight;
-                if (c < 0 || c >= hi_id) flags |= kBadCol;
-            }
+        for (uint32_t e0 = 0; e0 < d; e0 += 32 * kRun) {
+            const uint32_t i0 = e0 + lane * kRun;
+            const EdgeRun r = load_run(A, a, d, i0, hi_id, flags);
+            uint64_t v = r.sum;
 #pragma unroll
             for (int o = 1; o < 32; o <<= 1) {
                 const uint64_t y = __shfl_up_sync(0xffffffffu, v, o);
                 if (lane >= o) v += y;
             }
-            const uint64_t P = carry + v;
-            if (i < d) {
-                EdgeN r;
-                r.P = (uint32_t)P;
-                r.col = (int32_t)(c + base_id);
-                A.E[eb + i] = r;
-                if ((i & 7) == 7 || i == d - 1) K[key_slot(reg, d, L, 1, i >> 3)] = (uint32_t)P;
-            }
+            write_run(A, K, r, carry + v - r.sum, reg, eb, d, L, i0, base_id);
             carry += __shfl_sync(0xffffffffu, v, 31);
         }
         if (carry >= (1ull << 32)) flags |= kWide;
-        for (uint32_t i = d + lane; i < 4 * ceil_shift(d, 2); i += 32) {
-            EdgeN r;
-            r.P = 0xffffffffu;
-            r.col = 0;
-            A.E[eb + i] = r;
-        }
         for (uint32_t i = ceil_shift(d, 3) + lane; i < 8 * level_sectors(d, 1); i += 32)
             K[key_slot(reg, d, L, 1, i)] = 0xffffffffu;
         __syncwarp();
@@ -389,16 +433,10 @@ __global__ void __launch_bounds__(512) k_build_big(BuildArgs A)
         const uint32_t L = tree_levels(d);
         const uint64_t eb = reg + 4ull * summary_sectors(d);
         uint64_t carry = 0;
-        for (uint32_t e0 = 0; e0 < d; e0 += blockDim.x) {
-            const uint32_t i = e0 + tid;
-            uint64_t v = 0;
-            int64_t c = 0;
-            if (i < d) {
-                v = A.w[a + i];
-                c = A.col[a + i];
-                if (v == 0) flags |= kBadWeight;
-                if (c < 0 || c >= hi_id) flags |= kBadCol;
-            }
+        for (uint32_t e0 = 0; e0 < d; e0 += blockDim.x * kRun) {
+            const uint32_t i0 = e0 + tid * kRun;
+            const EdgeRun r = load_run(A, a, d, i0, hi_id, flags);
+            uint64_t v = r.sum;
 #pragma unroll
             for (int o = 1; o < 32; o <<= 1) {
                 const uint64_t y = __shfl_up_sync(0xffffffffu, v, o);
@@ -411,24 +449,11 @@ __global__ void __launch_bounds__(512) k_build_big(BuildArgs A)
                 if (q < wid) before += s_warp[q];
                 chunk += s_warp[q];
             }
-            const uint64_t P = carry + before + v;
-            if (i < d) {
-                EdgeN r;
-                r.P = (uint32_t)P;
-                r.col = (int32_t)(c + base_id);
-                A.E[eb + i] = r;
-                if ((i & 7) == 7 || i == d - 1) K[key_slot(reg, d, L, 1, i >> 3)] = (uint32_t)P;
-            }
+            write_run(A, K, r, carry + before + v - r.sum, reg, eb, d, L, i0, base_id);
             carry += chunk;
             __syncthreads();
         }
         if (carry >= (1ull << 32)) flags |= kWide;
-        for (uint32_t i = d + tid; i < 4 * ceil_shift(d, 2); i += blockDim.x) {
-            EdgeN r;
-            r.P = 0xffffffffu;
-            r.col = 0;
-            A.E[eb + i] = r;
-        }
         for (uint32_t i = ceil_shift(d, 3) + tid; i < 8 * level_sectors(d, 1); i += blockDim.x)
             K[key_slot(reg, d, L, 1, i)] = 0xffffffffu;
         __syncthreads();
@@ -1122,12 +1147,13 @@ int build_segments(ppr_graph *g, uint32_t T, cudaStream_t st)
 //   last large edge, edges with p = W: thr = W, alias = itself.
 // Rows of at most 32 edges run the pairing rounds serially, one thread per
 // row; longer rows compute the closed form: one warp per row with the row in
-// shared memory (up to 512 edges), one warp (up to 8192) or block (up to
-// 65,536) per row with scratch in global memory (alias_row_group), and tiles
-// of blocks above that.
+// shared memory (up to 512 edges), one warp (up to 1,024) or block (up to
+// 8,192) per row with scratch in global memory (alias_row_group), and tiles
+// of blocks above that.  The limits keep each row's merge to a few dozen
+// dependent probes per thread, so no long row is left running alone.
 
-constexpr uint32_t kAliasInline = 32, kAliasSerial = 512, kAliasMid = 8192, kAliasHuge = 65536;
-constexpr uint32_t kAliasMaxHuge = 4096;  // rows taken by the tile path; more go to the block tier
+constexpr uint32_t kAliasInline = 32, kAliasSerial = 512, kAliasMid = 1024, kAliasHuge = 8192;
+constexpr uint32_t kAliasMaxHuge = 65536;  // rows taken by the tile path; more go to the block tier
 constexpr uint32_t kTileEdges = 8192;     // edges per tile block (256 threads x 32)
 
 struct AliasArgs {

@@ -384,251 +384,4 @@ __device__ __forceinline__ void warp_bitonic_sort(T *a, uint32_t n_pow2)
     }
 }
 
-struct AggOut {
-    uint32_t *nnz;       // [S]
-    int32_t *cols;       // [S * cap]
-    uint32_t *cnts;      // [S * cap]
-    int32_t *topk_idx;   // [S * topk]
-    uint32_t *topk_cnt;  // [S * topk]
-    uint32_t cap;
-    int32_t topk;
-};
-
-// ends: the R endpoints of one source (shared memory).  sortbuf: next_pow2(R)
-// uint32 and keys: next_pow2(R) uint64 of per-warp shared scratch.  Writes
-// row `out_row` of the outputs.  All 32 lanes call it.
-__device__ inline void aggregate_source(const uint32_t *ends, uint32_t R, uint32_t *sortbuf, uint64_t *keys,
-                                        const AggOut &o, uint64_t out_row)
-{
-    const uint32_t lane = threadIdx.x & 31;
-    const uint32_t P2 = next_pow2(R);
-    for (uint32_t i = lane; i < P2; i += 32) sortbuf[i] = i < R ? ends[i] : 0xffffffffu;
-    __syncwarp();
-    warp_bitonic_sort(sortbuf, P2);
-    // One run per distinct endpoint.  A run is found at its last element;
-    // its first element comes from a lower-bound search of the sorted buffer.
-    const uint64_t rbase = out_row * o.cap;
-    uint32_t nrun = 0;
-    for (uint32_t base = 0; base < R; base += 32) {
-        uint32_t i = base + lane;
-        uint32_t v = i < R ? sortbuf[i] : 0u;
-        bool tail = i < R && (i == R - 1 || sortbuf[i + 1] != v);
-        uint32_t m = __ballot_sync(0xffffffffu, tail);
-        if (tail) {
-            uint32_t r = nrun + __popc(m & ((1u << lane) - 1));
-            uint32_t lo = 0, hi = i;
-            while (lo < hi) {
-                uint32_t mid = (lo + hi) >> 1;
-                if (sortbuf[mid] < v) lo = mid + 1;
-                else hi = mid;
-            }
-            uint32_t c = i - lo + 1;
-            o.cols[rbase + r] = (int32_t)v;
-            o.cnts[rbase + r] = c;
-            if (o.topk > 0) keys[r] = ((uint64_t)(~c) << 32) | v;
-        }
-        nrun += __popc(m);
-    }
-    if (lane == 0) o.nnz[out_row] = nrun;
-    if (o.topk > 0) {
-        uint32_t K2 = next_pow2(nrun);
-        for (uint32_t i = nrun + lane; i < K2; i += 32) keys[i] = ~0ull;
-        __syncwarp();
-        warp_bitonic_sort(keys, K2);
-        const uint64_t tb = out_row * (uint64_t)o.topk;
-        for (uint32_t i = lane; i < (uint32_t)o.topk; i += 32) {
-            if (i < nrun) {
-                uint64_t k = keys[i];
-                o.topk_idx[tb + i] = (int32_t)(uint32_t)k;
-                o.topk_cnt[tb + i] = ~(uint32_t)(k >> 32);
-            } else {
-                o.topk_idx[tb + i] = -1;
-                o.topk_cnt[tb + i] = 0;
-            }
-        }
-    }
-    __syncwarp();
-}
-
-// Register-resident variant for next_pow2(R) = 32 * E <= 1024: the sorted
-// block lives in registers in striped order (element i = e * 32 + lane), a
-// bitonic network runs on shuffles (partner distance < 32) and in-register
-// exchanges (distance >= 32).  Runs are found from neighbour values; the
-// top-k sorts 32-bit keys (R - count) << 12 | run, whose order is count
-// descending then end id ascending because runs are numbered in id order.
-template <int E>
-__device__ __forceinline__ void warp_sort_reg(uint32_t (&v)[E])
-{
-    const uint32_t lane = threadIdx.x & 31;
-    constexpr int N = 32 * E;
-#pragma unroll
-    for (int k = 2; k <= N; k <<= 1) {
-#pragma unroll
-        for (int j = k >> 1; j > 0; j >>= 1) {
-            if (j >= 32) {
-#pragma unroll
-                for (int e = 0; e < E; ++e) {
-                    const int f = e ^ (j >> 5);
-                    if (f > e) {
-                        const bool up = (((uint32_t)e * 32 + lane) & (uint32_t)k) == 0;
-                        const uint32_t a = v[e], b = v[f];
-                        const bool sw = (a > b) == up;
-                        v[e] = sw ? b : a;
-                        v[f] = sw ? a : b;
-                    }
-                }
-            } else {
-#pragma unroll
-                for (int e = 0; e < E; ++e) {
-                    const uint32_t o = __shfl_xor_sync(0xffffffffu, v[e], j);
-                    const bool up = (((uint32_t)e * 32 + lane) & (uint32_t)k) == 0;
-                    const bool lower = (lane & (uint32_t)j) == 0;
-                    v[e] = (lower == up) ? min(v[e], o) : max(v[e], o);
-                }
-            }
-        }
-    }
-}
-
-// Top-K of one row without sorting every run, for K <= 32 and K < nrun:
-// kv holds the keys (R - count) << 12 | run of runs e * 32 + lane (0xFFFFFFFF
-// past nrun), and the answer is the K smallest keys in ascending order.  The
-// count rank q = key >> 12 of the K-th smallest key is found by bisection
-// over [0, R - 1] with ballot counts; every key with q below it is taken (fewer
-// than K, sorted in one register per lane), then the first keys with q equal
-// to it in run order (= ascending key, as runs are numbered in id order)
-// fill the remaining places.  cbuf: 32 uint32 of per-warp shared memory.
-template <int E>
-__device__ __forceinline__ void topk_select_reg(const uint32_t (&kv)[E], uint32_t K, uint32_t R,
-                                                const uint32_t *run_id, uint32_t *cbuf, const AggOut &o, uint64_t tb)
-{
-    const uint32_t lane = threadIdx.x & 31, below = (1u << lane) - 1;
-    auto count_le = [&](uint32_t t) {
-        uint32_t c = 0;
-#pragma unroll
-        for (int e = 0; e < E; ++e) c += __popc(__ballot_sync(0xffffffffu, (kv[e] >> 12) <= t));
-        return c;
-    };
-    // smallest t with count_le(t) >= K; count_le(R - 1) = nrun > K.  Most rows
-    // have fewer than K runs of count >= 2, so t = R - 1 is tried first.
-    uint32_t lo = 0, hi = R - 1;
-    if (R >= 2 && count_le(R - 2) < K) lo = R - 1;
-    else hi = R >= 2 ? R - 2 : 0;
-    while (lo < hi) {
-        const uint32_t mid = (lo + hi) >> 1;
-        if (count_le(mid) >= K) hi = mid;
-        else lo = mid + 1;
-    }
-    const uint32_t t = lo;
-    uint32_t nlt = 0;  // keys below t, gathered into cbuf in run order
-#pragma unroll
-    for (int e = 0; e < E; ++e) {
-        const bool lt = (kv[e] >> 12) < t;
-        const uint32_t ml = __ballot_sync(0xffffffffu, lt);
-        if (lt) cbuf[nlt + __popc(ml & below)] = kv[e];
-        nlt += __popc(ml);
-    }
-    __syncwarp();
-    // nlt < K places for the keys below t, sorted; then K - nlt keys equal to t
-    uint32_t v[1] = {lane < nlt ? cbuf[lane] : 0xffffffffu};
-    warp_sort_reg<1>(v);
-    if (lane < nlt) {
-        o.topk_idx[tb + lane] = (int32_t)run_id[v[0] & 0xfffu];
-        o.topk_cnt[tb + lane] = R - (v[0] >> 12);
-    }
-    uint32_t seen = 0;
-#pragma unroll
-    for (int e = 0; e < E; ++e) {
-        const bool eq = (kv[e] >> 12) == t;
-        const uint32_t me = __ballot_sync(0xffffffffu, eq);
-        const uint32_t pos = nlt + seen + __popc(me & below);
-        if (eq && pos < K) {
-            o.topk_idx[tb + pos] = (int32_t)run_id[kv[e] & 0xfffu];
-            o.topk_cnt[tb + pos] = R - t;
-        }
-        seen += __popc(me);
-    }
-}
-
-// scratch: 3 * R uint32 of per-warp shared memory
-template <int E>
-__device__ inline void aggregate_source_reg(const uint32_t *ends, uint32_t R, uint32_t *scratch, const AggOut &o,
-                                            uint64_t out_row)
-{
-    const uint32_t lane = threadIdx.x & 31;
-    uint32_t *start_pos = scratch, *run_id = scratch + R, *kbuf = scratch + 2 * R;
-    uint32_t v[E];
-#pragma unroll
-    for (int e = 0; e < E; ++e) {
-        const uint32_t i = (uint32_t)e * 32 + lane;
-        v[e] = i < R ? ends[i] : 0xffffffffu;
-    }
-    warp_sort_reg<E>(v);
-    const uint64_t rbase = out_row * o.cap;
-    uint32_t nrun = 0;
-#pragma unroll
-    for (int e = 0; e < E; ++e) {
-        const uint32_t i = (uint32_t)e * 32 + lane;
-        const uint32_t pu = __shfl_up_sync(0xffffffffu, v[e], 1);
-        const uint32_t pe = __shfl_sync(0xffffffffu, v[e > 0 ? e - 1 : 0], 31);
-        const uint32_t nd = __shfl_down_sync(0xffffffffu, v[e], 1);
-        const uint32_t ne = __shfl_sync(0xffffffffu, v[e + 1 < E ? e + 1 : e], 0);
-        const uint32_t prev = lane == 0 ? pe : pu;
-        const uint32_t next = lane == 31 ? ne : nd;
-        const bool valid = i < R;
-        const bool head = valid && (i == 0 || prev != v[e]);
-        const bool tail = valid && (i == R - 1 || next != v[e]);
-        const uint32_t hb = __ballot_sync(0xffffffffu, head);
-        const uint32_t run = nrun + __popc(hb & ((2u << lane) - 1)) - 1;  // run of element i
-        if (head) {
-            start_pos[run] = i;
-            run_id[run] = v[e];
-        }
-        __syncwarp();
-        if (tail) {
-            const uint32_t c = i - start_pos[run] + 1;
-            o.cols[rbase + run] = (int32_t)v[e];
-            o.cnts[rbase + run] = c;
-            kbuf[run] = ((R - c) << 12) | run;
-        }
-        nrun += __popc(hb);
-    }
-    if (lane == 0) o.nnz[out_row] = nrun;
-    if (o.topk > 0) {
-        __syncwarp();
-        uint32_t kv[E];
-#pragma unroll
-        for (int e = 0; e < E; ++e) {
-            const uint32_t i = (uint32_t)e * 32 + lane;
-            kv[e] = i < nrun ? kbuf[i] : 0xffffffffu;
-        }
-        const uint64_t tb = out_row * (uint64_t)o.topk;
-        const uint32_t K = (uint32_t)o.topk;
-        if (E > 1 && K <= 32 && K < nrun) {
-            topk_select_reg<E>(kv, K, R, run_id, start_pos, o, tb);
-        } else {
-            warp_sort_reg<E>(kv);
-#pragma unroll
-            for (int e = 0; e < E; ++e) {
-                const uint32_t i = (uint32_t)e * 32 + lane;
-                if (i < K) {
-                    if (i < nrun) {
-                        o.topk_idx[tb + i] = (int32_t)run_id[kv[e] & 0xfffu];
-                        o.topk_cnt[tb + i] = R - (kv[e] >> 12);
-                    } else {
-                        o.topk_idx[tb + i] = -1;
-                        o.topk_cnt[tb + i] = 0;
-                    }
-                }
-            }
-            // k may exceed the sorted block (k > next_pow2(R) >= nnz): pad the rest
-            for (uint32_t i = 32u * E + lane; i < K; i += 32) {
-                o.topk_idx[tb + i] = -1;
-                o.topk_cnt[tb + i] = 0;
-            }
-        }
-    }
-    __syncwarp();
-}
-
 }  // namespace ppr

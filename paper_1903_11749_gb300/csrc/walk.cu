@@ -9,19 +9,20 @@
 // outcome ends the walk, an active one moves the walk and advances k by the
 // outcome's length.
 //
-// k_walk_plain:      one thread per walk, endpoint to HBM (baseline), then
-// k_aggregate:       one warp per source sorts its R endpoints into a row.
-// k_walk_persistent: persistent warps pull source chunks from a global queue,
-//                    refill lanes as walks end (the paper's pipelines keep
-//                    the cluster busy the same way), search large rows with the
-//                    whole warp, and aggregate a chunk in shared memory as soon
-//                    as its last walk ends.
+// k_walk_plain:      one thread per walk, endpoint to HBM (baseline).
+// k_walk_persistent: persistent warps pull chunks of walks from a global
+//                    queue and refill lanes as walks end (the paper's
+//                    pipelines keep the cluster busy the same way); rows above
+//                    a set degree may be searched by the whole warp.
+// Both write one endpoint per walk to HBM; k_aggregate (aggregate.cuh) then
+// turns each source's R endpoints into its count row and top-k.
 #include <algorithm>
 #include <type_traits>
 #include <mutex>
 
 #include "ppr_host.h"
 #include "scan.cuh"
+#include "aggregate.cuh"
 
 namespace ppr {
 
@@ -284,27 +285,6 @@ __global__ void __launch_bounds__(256, PPR_WALK_MINB) k_walk_plain(KParams p)
     warp_add_tally<STATS>(p.steps, tl);
 }
 
-// E > 0: register-resident reduction for next_pow2(R) = 32 * E; E = 0:
-// shared-memory reduction (any R).
-template <int E>
-__global__ void __launch_bounds__(128) k_aggregate(KParams p)
-{
-    extern __shared__ __align__(16) unsigned char smem_raw[];
-    const uint32_t wid = threadIdx.x >> 5, nw = blockDim.x >> 5;
-    unsigned char *scratch = smem_raw + (size_t)wid * p.P2 * 12;
-    const uint64_t S = (uint64_t)(p.s_end - p.s_begin);
-    for (uint64_t i = (uint64_t)blockIdx.x * nw + wid; i < S; i += (uint64_t)gridDim.x * nw) {
-        if constexpr (E > 0) {
-            aggregate_source_reg<E>(p.ends + i * p.R, p.R, reinterpret_cast<uint32_t *>(scratch), p.out,
-                                    (uint64_t)p.out_row0 + i);
-        } else {
-            uint64_t *keys = reinterpret_cast<uint64_t *>(scratch);
-            aggregate_source(p.ends + i * p.R, p.R, reinterpret_cast<uint32_t *>(keys + p.P2), keys, p.out,
-                             (uint64_t)p.out_row0 + i);
-        }
-    }
-}
-
 // ------------------------------------------------------- persistent (K5) ----
 // Persistent warps.  Each warp pulls chunks of sources from a global queue
 // (one atomic per chunk) and keeps all 32 lanes busy: a lane whose walk ends
@@ -418,34 +398,6 @@ __global__ void __launch_bounds__(256, PPR_WALK_MINB) k_walk_persistent(KParams 
 
 // ------------------------------------------------------------- launcher ----
 
-template <int E>
-static int launch_aggregate_e(ppr_ctx *ctx, const KParams &kp, int64_t S, cudaStream_t st)
-{
-    const int aw = 4;
-    size_t smem = (size_t)aw * kp.P2 * 12;
-    if (smem > 48 * 1024)
-        PPR_CUDA(cudaFuncSetAttribute(k_aggregate<E>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
-    int ablocks = (int)std::min<int64_t>((S + aw - 1) / aw, (int64_t)ctx->sms * 16);
-    if (ablocks < 1) ablocks = 1;
-    k_aggregate<E><<<ablocks, aw * 32, smem, st>>>(kp);
-    note_launch();
-    PPR_CUDA(cudaGetLastError());
-    return PPR_OK;
-}
-
-static int launch_aggregate(ppr_ctx *ctx, const KParams &kp, int64_t S, cudaStream_t st)
-{
-    switch (kp.P2) {
-    case 1: case 2: case 4: case 8: case 16: case 32: return launch_aggregate_e<1>(ctx, kp, S, st);
-    case 64: return launch_aggregate_e<2>(ctx, kp, S, st);
-    case 128: return launch_aggregate_e<4>(ctx, kp, S, st);
-    case 256: return launch_aggregate_e<8>(ctx, kp, S, st);
-    case 512: return launch_aggregate_e<16>(ctx, kp, S, st);
-    case 1024: return launch_aggregate_e<32>(ctx, kp, S, st);
-    default: return launch_aggregate_e<0>(ctx, kp, S, st);
-    }
-}
-
 // Events around a walker launch, for the walker-only device time.
 static int walker_event(ppr_result *r, cudaStream_t st)
 {
@@ -471,7 +423,7 @@ static int launch_typed(ppr_ctx *ctx, const KParams &kp, const RunPlan &plan, in
         note_launch();
         PPR_CUDA(cudaGetLastError());
         if ((rc = walker_event(r, st))) return rc;
-        return launch_aggregate(ctx, kp, S, st);
+        return launch_aggregate(ctx, AggParams{kp.ends, kp.R, kp.P2, S, kp.out_row0, kp.out}, st);
     }
     int per_sm = 0;
     // walkers per CTA: 32 * warps_per_block (4 or 8 warps; default 8)
@@ -508,7 +460,7 @@ static int launch_typed(ppr_ctx *ctx, const KParams &kp, const RunPlan &plan, in
     note_launch();
     PPR_CUDA(cudaGetLastError());
     if ((rc = walker_event(r, st))) return rc;
-    return launch_aggregate(ctx, kp, S, st);
+    return launch_aggregate(ctx, AggParams{kp.ends, kp.R, kp.P2, S, kp.out_row0, kp.out}, st);
 }
 
 // Chunk table of a batched graph, built on the device: chunks of at most CS

@@ -78,20 +78,21 @@ def test_alias_differs_from_prefix_but_same_rows_sum(ppr, ctx, oracle):
 
 
 def test_alias_long_rows_skew_self_loops(ppr, ctx, oracle):
-    """Rows in every build tier (inline up to 32 edges, one thread up to 256,
-    one warp up to 8192, one block up to 65536, tiles of blocks above) with
-    Zipf weights (long pairing
-    chains, edges re-entering S^s many times), a heavy self-loop, parallel
-    edges, single-edge rows and a dangling node."""
+    """Rows in every build tier (inline up to 32 edges, one warp with the row
+    in shared memory up to 512, one warp up to 1024, one block up to 8192,
+    tiles of blocks above) and on each side of its limits, with Zipf weights
+    (long pairing chains, edges re-entering S^s many times), a heavy
+    self-loop, parallel edges, single-edge rows and a dangling node."""
     rng = np.random.Generator(np.random.PCG64(17))
     n = 1200
     edges = []
-    for u, d in ((0, 20000), (1, 2500), (2, 700), (4, 256), (5, 257), (6, 100), (7, 33), (8, 70001)):
+    for u, d in ((0, 20000), (1, 2500), (2, 700), (4, 256), (5, 257), (6, 100), (7, 33), (8, 70001),
+                 (9, 512), (10, 513), (11, 1024), (12, 1025), (13, 8192), (14, 8193)):
         ws = I.zipf_weights(rng, d, s=1.2, wmax=5000)
         dst = rng.integers(0, n, d)
         edges += [(u, int(v), int(x)) for v, x in zip(dst, ws)]
     edges += [(3, 3, 1000), (3, 4, 1), (3, 4, 1), (3, 5, 7)]  # self-loop, parallel edges
-    edges += [(u, (u * 7) % n, 3) for u in range(9, 200)]  # single-edge rows
+    edges += [(u, (u * 7) % n, 3) for u in range(15, 200)]  # single-edge rows
     edges += [(u, int(v), int(x)) for u in range(200, n - 1)
               for v, x in zip(rng.integers(0, n, 5), rng.integers(1, 30, 5))]
     g = I.from_edges(n, edges)  # node n-1 dangling

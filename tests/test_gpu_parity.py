@@ -176,9 +176,9 @@ def test_large_rows_cooperative_search(ppr, ctx, oracle):
 
 
 def test_huge_rows_built_by_tiles(ppr, ctx, oracle):
-    """Rows above 65,536 edges are built by tiles of 8,192 edges (a hub of
-    150,001 edges, a row of 65,537, and one just below the cut), in a plain
-    and in a batched graph; every count equals the oracle's."""
+    """Rows above 8,192 edges are built by tiles of 8,192 edges (a hub of
+    150,001 edges, rows of 65,537 and 65,536 edges), in a plain and in a
+    batched graph; every count equals the oracle's."""
     rng = np.random.Generator(np.random.PCG64(5))
     n = 40000
     edges = []
@@ -201,6 +201,48 @@ def test_huge_rows_built_by_tiles(ppr, ctx, oracle):
     rp, col, cnt = res.sparse_rows()
     orp, ocol, ocnt = ref1["rows"]
     assert np.array_equal(rp, orp) and np.array_equal(col, ocol) and np.array_equal(cnt, ocnt)  # instance-local ids
+
+
+def test_rows_at_every_build_tier_boundary(ppr, ctx, oracle):
+    """Rows whose degrees sit on each side of every build tier (thread per row
+    up to 32 edges, warp per row up to 1,024, block per row up to 8,192, tiles
+    of 8,192 edges above) and of the 8-ary summary levels (8, 64, 512, 4,096),
+    in a plain and in a batched graph: the walks return to those rows often
+    enough to draw from most of their edges, and every count equals the
+    oracle's."""
+    rng = np.random.Generator(np.random.PCG64(17))
+    degs = [2, 8, 9, 31, 32, 33, 64, 65, 127, 128, 129, 512, 513, 1023, 1024, 1025, 4096, 4097, 8191, 8192, 8193,
+            16384, 16385, 24577]
+    h = len(degs)
+    n = 6000
+    edges = []
+    for u, d in enumerate(degs):
+        edges += [(u, int(t), int(w)) for t, w in zip(rng.integers(h, n, d), rng.integers(1, 4000, d))]
+    for u in range(h, n):  # small rows lead back to the tier rows
+        edges.append((u, int(rng.integers(0, h)), int(rng.integers(1, 9))))
+        if u % 3 == 0:
+            edges.append((u, int(rng.integers(0, n)), int(rng.integers(1, 9))))
+    g = I.from_edges(n, edges)
+    assert [int(g.row_ptr[u + 1] - g.row_ptr[u]) for u in range(h)] == degs
+    G = ctx.load_graph(g.n, g.row_ptr, g.col, g.w)
+    ref = oracle_rows(oracle, g, 0.15, 1000, 8, 0, 400, topk=6)
+    for sampler in (0, 1):
+        og = oracle.prepare(g.n, g.row_ptr, g.col, g.w)
+        ends, steps = oracle.walks(og, 0.15, 1000, 8, 0, 400, sampler=sampler)
+        orp, ocol, ocnt = oracle.rows(ends, g.n)
+        res = G.run(alpha=0.15, R=1000, seed=8, src_end=400, sampler=sampler)
+        rp, col, cnt = res.sparse_rows()
+        assert np.array_equal(rp, orp) and np.array_equal(col, ocol) and np.array_equal(cnt, ocnt), sampler
+        assert res.info().steps == steps
+    assert_same(G.run(alpha=0.15, R=1000, seed=8, src_end=400, topk=6), ref, topk=6)
+    # the same rows in the second instance of a batched graph (instance-local ids, tag 1)
+    rp2 = np.concatenate([g.row_ptr[:-1], g.row_ptr + g.m])
+    Gb = ctx.load_graph_batch(np.array([0, n, 2 * n]), rp2, np.concatenate([g.col, g.col]), np.concatenate([g.w, g.w]))
+    res = Gb.run(alpha=0.15, R=1000, seed=8, src_begin=n, src_end=n + 400)
+    ref1 = oracle_rows(oracle, g, 0.15, 1000, 8, 0, 400, tag=1)
+    rp, col, cnt = res.sparse_rows()
+    orp, ocol, ocnt = ref1["rows"]
+    assert np.array_equal(rp, orp) and np.array_equal(col, ocol) and np.array_equal(cnt, ocnt)
 
 
 def test_segment_mode_matches_segment_oracle(ppr, ctx, oracle):
