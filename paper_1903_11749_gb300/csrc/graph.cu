@@ -215,7 +215,7 @@ struct BuildArgs {
     const int64_t *node_off;
     int32_t count;
     const uint64_t *region;
-    NodeRec *node;
+    NodeRecN *node;
     EdgeN *E;
     LayoutStats *st;
     uint32_t *list;  // mid rows from the front, big rows from the back
@@ -229,12 +229,20 @@ __device__ __forceinline__ uint64_t key_slot(uint64_t reg, uint32_t d, uint32_t 
     return (reg + 4ull * off) * 2 + i;
 }
 
+// Node record of a built row; a row whose top summary level fits the record
+// (root_in_record) gets that level's first four keys, read back from the
+// level the calling group has just written.
 __device__ __forceinline__ void write_node(const BuildArgs &A, int64_t u, uint64_t reg, uint32_t d, uint64_t W,
                                            uint32_t first_target)
 {
-    NodeRec r;
+    NodeRecN r;
     r.word0 = pack_word0(reg, d, false);
     r.total = d == 1 ? (uint64_t)first_target : (d == 0 ? 0ull : pack_blocked_total(W, d));
+    const uint32_t L = d >= 2 ? tree_levels(d) : 0;
+    const bool root = root_in_record(d, L);
+    const uint32_t *K = reinterpret_cast<const uint32_t *>(A.E);
+#pragma unroll
+    for (uint32_t i = 0; i < 4; ++i) r.key[i] = root ? K[key_slot(reg, d, L, L, i)] : 0xffffffffu;
     A.node[u] = r;
 }
 
@@ -661,12 +669,13 @@ static int build_narrow(ppr_ctx *ctx, int64_t n, int64_t m, const int64_t *d_rp,
     }
     g->max_degree = (int64_t)hs.max_degree;
     g->dangling = (int64_t)hs.dangling;
-    if ((rc = dev_alloc((void **)&g->node, sizeof(NodeRec) * n, "node records", st))) return rc;
+    if ((rc = dev_alloc((void **)&g->node, sizeof(NodeRecN) * n, "node records", st))) return rc;
     const size_t edge_bytes = (size_t)(slots > 0 ? slots : 2) * sizeof(EdgeN);
     if ((rc = dev_alloc(&g->edges, edge_bytes, "edge records", st))) return rc;
     g->edge_records = (int64_t)slots;
-    g->device_bytes = (int64_t)(sizeof(NodeRec) * n + edge_bytes);
-    BuildArgs A{n, d_rp, d_col, d_w, d_off, g->instances, d_region, g->node, (EdgeN *)g->edges, d_ls, d_list};
+    g->device_bytes = (int64_t)(sizeof(NodeRecN) * n + edge_bytes);
+    BuildArgs A{n, d_rp, d_col, d_w, d_off, g->instances, d_region, static_cast<NodeRecN *>(g->node),
+                (EdgeN *)g->edges, d_ls, d_list};
     k_build_small<<<tblocks, 256, 0, st>>>(A);
     note_launch();
     k_build_mid<<<ctx->sms * 8, 256, 0, st>>>(A);
@@ -824,7 +833,8 @@ int build_graph(ppr_ctx *ctx, int64_t n, int64_t m, const int64_t *row_ptr, cons
         if ((rc = dev_alloc(&g->edges, edge_bytes > 0 ? edge_bytes : 16, "edge records", st))) return cleanup(), rc;
         g->edge_records = m;
         g->device_bytes = (int64_t)(sizeof(NodeRec) * n + edge_bytes);
-        k_rows_pass2<true><<<blocks, threads, 0, st>>>(n, d_rp, d_col, d_w, d_off, g->instances, d_W, g->node, g->edges);
+        k_rows_pass2<true><<<blocks, threads, 0, st>>>(n, d_rp, d_col, d_w, d_off, g->instances, d_W,
+                                                       static_cast<NodeRec *>(g->node), g->edges);
         note_launch();
     }
     e = cudaGetLastError();
@@ -856,7 +866,7 @@ __device__ __forceinline__ uint64_t mul_div(uint64_t q, uint64_t num, uint64_t d
 
 template <class E>
 struct RowView {
-    const NodeRec *node;
+    const typename E::Node *node;
     E edges;
     __device__ __forceinline__ uint32_t deg(uint32_t u) const { return (uint32_t)(node[u].word0 >> 40) & kCountMask; }
     __device__ __forceinline__ uint64_t begin(uint32_t u) const { return node[u].word0 & kBeginMask; }
@@ -1020,7 +1030,7 @@ __global__ void k_seg_count(RowView<E> G, int64_t n, uint32_t T, uint32_t *count
 
 template <class E>
 __global__ void k_seg_write(RowView<E> G, int64_t n, uint32_t T, const uint64_t *offs, SegEntry *ent,
-                            NodeRec *seg_node)
+                            typename E::Node *seg_node)
 {
     extern __shared__ __align__(16) unsigned char smem_raw[];
     SegScratch *sc = reinterpret_cast<SegScratch *>(smem_raw) + (threadIdx.x >> 5);
@@ -1046,7 +1056,7 @@ __global__ void k_seg_write(RowView<E> G, int64_t n, uint32_t T, const uint64_t 
                 s.mark_len = ((uint32_t)(k >> 63) << 8) | (uint32_t)(k & 0xff);
                 ent[o + i] = s;
             }
-            NodeRec r;
+            typename E::Node r = G.node[v];  // a NodeRecN keeps its (unused) top-level keys
             r.word0 = pack_word0(o, c, true);
             r.total = acc;
             seg_node[v] = r;
@@ -1083,12 +1093,12 @@ int build_segments(ppr_graph *g, uint32_t T, cudaStream_t st)
     if (blocks < 1) blocks = 1;
     cudaError_t e;
     if (g->wide) {
-        RowView<WideEdges> G{g->node, WideEdges{(const EdgeW *)g->edges}};
+        RowView<WideEdges> G{static_cast<const NodeRec *>(g->node), WideEdges{(const EdgeW *)g->edges}};
         cudaFuncSetAttribute(k_seg_count<WideEdges>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
         k_seg_count<WideEdges><<<blocks, wpb * 32, smem, st>>>(G, n, T, d_cnt);
         note_launch();
     } else {
-        RowView<NarrowEdges> G{g->node, NarrowEdges{(const EdgeN *)g->edges}};
+        RowView<NarrowEdges> G{static_cast<const NodeRecN *>(g->node), NarrowEdges{(const EdgeN *)g->edges}};
         cudaFuncSetAttribute(k_seg_count<NarrowEdges>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
         k_seg_count<NarrowEdges><<<blocks, wpb * 32, smem, st>>>(G, n, T, d_cnt);
         note_launch();
@@ -1098,21 +1108,24 @@ int build_segments(ppr_graph *g, uint32_t T, cudaStream_t st)
     e = cudaMemcpyAsync(&total, d_off + n, sizeof(uint64_t), cudaMemcpyDeviceToHost, st);
     if (e == cudaSuccess) e = cudaStreamSynchronize(st);
     if (e != cudaSuccess) return fail(cuda_fail(e, "segment count"));
-    if ((rc = dev_alloc((void **)&g->seg.node, sizeof(NodeRec) * n, "segment node records", st))) return fail(rc);
+    const size_t node_bytes = g->wide ? sizeof(NodeRec) : sizeof(NodeRecN);
+    if ((rc = dev_alloc((void **)&g->seg.node, node_bytes * n, "segment node records", st))) return fail(rc);
     if ((rc = dev_alloc((void **)&g->seg.entries, sizeof(SegEntry) * (total > 0 ? total : 1), "segment tables", st))) {
         dev_free(g->seg.node, st);
         g->seg.node = nullptr;
         return fail(rc);
     }
     if (g->wide) {
-        RowView<WideEdges> G{g->node, WideEdges{(const EdgeW *)g->edges}};
+        RowView<WideEdges> G{static_cast<const NodeRec *>(g->node), WideEdges{(const EdgeW *)g->edges}};
         cudaFuncSetAttribute(k_seg_write<WideEdges>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
-        k_seg_write<WideEdges><<<blocks, wpb * 32, smem, st>>>(G, n, T, d_off, g->seg.entries, g->seg.node);
+        k_seg_write<WideEdges><<<blocks, wpb * 32, smem, st>>>(G, n, T, d_off, g->seg.entries,
+                                                              static_cast<NodeRec *>(g->seg.node));
         note_launch();
     } else {
-        RowView<NarrowEdges> G{g->node, NarrowEdges{(const EdgeN *)g->edges}};
+        RowView<NarrowEdges> G{static_cast<const NodeRecN *>(g->node), NarrowEdges{(const EdgeN *)g->edges}};
         cudaFuncSetAttribute(k_seg_write<NarrowEdges>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
-        k_seg_write<NarrowEdges><<<blocks, wpb * 32, smem, st>>>(G, n, T, d_off, g->seg.entries, g->seg.node);
+        k_seg_write<NarrowEdges><<<blocks, wpb * 32, smem, st>>>(G, n, T, d_off, g->seg.entries,
+                                                                static_cast<NodeRecN *>(g->seg.node));
         note_launch();
     }
     e = cudaGetLastError();
@@ -1129,7 +1142,7 @@ int build_segments(ppr_graph *g, uint32_t T, cudaStream_t st)
         for (uint32_t c : hc) nz += c > 0;
         g->seg.nodes = nz;
     }
-    g->device_bytes += (int64_t)(sizeof(NodeRec) * n + sizeof(SegEntry) * total);
+    g->device_bytes += (int64_t)(node_bytes * n + sizeof(SegEntry) * total);
     fail(PPR_OK);
     return PPR_OK;
 }
@@ -1158,7 +1171,7 @@ constexpr uint32_t kTileEdges = 8192;     // edges per tile block (256 threads x
 
 struct AliasArgs {
     int64_t n;
-    const NodeRec *node;
+    const NodeRecN *node;  // the narrow layout's records (begin, count, W)
     const EdgeN *edges;
     const uint64_t *off;  // first slot of each row (exclusive scan of degrees)
     NodeRec *anode;
@@ -1171,10 +1184,11 @@ struct AliasArgs {
     uint2 *huge;          // tile-path rows (node, degree), kAliasMaxHuge entries
 };
 
-__device__ __forceinline__ uint32_t row_degree(const NodeRec &r) { return (uint32_t)(r.word0 >> 40) & kCountMask; }
+template <class N>
+__device__ __forceinline__ uint32_t row_degree(const N &r) { return (uint32_t)(r.word0 >> 40) & kCountMask; }
 
 // The pairing rounds of one row, serially (row of d >= 2 edges, slots from o).
-__device__ void alias_row_serial(const AliasArgs &A, const NodeRec &nr, uint32_t d, uint64_t o)
+__device__ void alias_row_serial(const AliasArgs &A, const NodeRecN &nr, uint32_t d, uint64_t o)
 {
     const uint64_t W = nr.total & 0xffffffffull;
     const uint64_t eb = NarrowEdges::edge_base(nr.word0 & kBeginMask, d);
@@ -1217,7 +1231,7 @@ __device__ void alias_row_serial(const AliasArgs &A, const NodeRec &nr, uint32_t
 __global__ void __launch_bounds__(256) k_alias_small(AliasArgs A)
 {
     for (int64_t u = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; u < A.n; u += (int64_t)gridDim.x * blockDim.x) {
-        const NodeRec nr = A.node[u];
+        const NodeRecN nr = A.node[u];
         const uint32_t d = row_degree(nr);
         const uint64_t o = A.off[u];
         NodeRec r;
@@ -1262,7 +1276,7 @@ __global__ void __launch_bounds__(32 * kSmemWarps) k_alias_serial(AliasArgs A)
     const uint32_t warps = gridDim.x * kSmemWarps;
     for (uint32_t t = blockIdx.x * kSmemWarps + (threadIdx.x >> 5); t < rows; t += warps) {
         const uint32_t u = A.list[t];
-        const NodeRec nr = A.node[u];
+        const NodeRecN nr = A.node[u];
         const uint32_t d = row_degree(nr);  // 33..512
         const uint64_t o = A.off[u];
         const uint64_t W = nr.total & 0xffffffffull;
@@ -1415,7 +1429,7 @@ __device__ __forceinline__ void group_sync()
 template <int NT>
 __device__ void alias_row_group(const AliasArgs &A, int64_t u, uint32_t rank, uint64_t *s)
 {
-    const NodeRec nr = A.node[u];
+    const NodeRecN nr = A.node[u];
     const uint32_t d = row_degree(nr);
     const uint64_t o = A.off[u];
     const uint64_t W = nr.total & 0xffffffffull;
@@ -1615,7 +1629,7 @@ __global__ void __launch_bounds__(256) k_alias_tile_totals(TileArgs T)
     const AliasArgs &A = T.A;
     const uint2 tl = T.tiles[blockIdx.x];
     const HugeRow hr = T.rows[tl.x];
-    const NodeRec nr = A.node[hr.u];
+    const NodeRecN nr = A.node[hr.u];
     const uint64_t W = nr.total & 0xffffffffull;
     const uint64_t eb = NarrowEdges::edge_base(nr.word0 & kBeginMask, hr.d);
     const uint32_t end = min(tl.y + kTileEdges, hr.d);
@@ -1657,7 +1671,7 @@ __global__ void __launch_bounds__(256) k_alias_tile_write(TileArgs T)
     const uint2 tl = T.tiles[blockIdx.x];
     const HugeRow hr = T.rows[tl.x];
     const uint32_t d = hr.d;
-    const NodeRec nr = A.node[hr.u];
+    const NodeRecN nr = A.node[hr.u];
     const uint64_t W = nr.total & 0xffffffffull;
     const uint64_t eb = NarrowEdges::edge_base(nr.word0 & kBeginMask, d);
     const uint64_t o = A.off[hr.u];
@@ -1710,7 +1724,7 @@ __global__ void __launch_bounds__(256) k_alias_tile_merge(TileArgs T)
     const ulonglong2 ab = T.row_ab[lo];
     const uint32_t a = (uint32_t)ab.x, b = (uint32_t)ab.y, d = hr.d;
     if (a == 0 || b == 0 || (uint64_t)a + b > d) return;
-    const NodeRec nr = A.node[hr.u];
+    const NodeRecN nr = A.node[hr.u];
     const uint64_t W = nr.total & 0xffffffffull;
     const uint64_t o = A.off[hr.u];
     auto E = [&](uint32_t j) { return A.sum[o + d - 1 - j]; };
@@ -1759,7 +1773,7 @@ __global__ void __launch_bounds__(256) k_alias_tile_merge(TileArgs T)
     }
 }
 
-__global__ void k_alias_degrees(int64_t n, const NodeRec *node, uint32_t *deg)
+__global__ void k_alias_degrees(int64_t n, const NodeRecN *node, uint32_t *deg)
 {
     for (int64_t u = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; u < n; u += (int64_t)gridDim.x * blockDim.x)
         deg[u] = row_degree(node[u]);
@@ -1819,10 +1833,11 @@ int build_alias(ppr_graph *g, cudaStream_t st)
     cudaError_t e = cudaMemsetAsync(counts, 0, sizeof(uint32_t) * 4, st);
     if (e != cudaSuccess) return fail(cuda_fail(e, "memset"));
     const int blocks = (int)std::max<int64_t>(1, std::min<int64_t>((n + 255) / 256, (int64_t)g->ctx->sms * 16));
-    k_alias_degrees<<<blocks, 256, 0, st>>>(n, g->node, deg);
+    k_alias_degrees<<<blocks, 256, 0, st>>>(n, static_cast<const NodeRecN *>(g->node), deg);
     note_launch();
     exclusive_scan_u32(deg, n, off, tmp, st);
-    AliasArgs A{n, g->node, (const EdgeN *)g->edges, off, g->alias.node, g->alias.slots, ic, sum, list, counts, huge};
+    AliasArgs A{n, static_cast<const NodeRecN *>(g->node), (const EdgeN *)g->edges, off, g->alias.node, g->alias.slots, ic,
+                sum, list, counts, huge};
     k_alias_small<<<blocks, 256, 0, st>>>(A);
     note_launch();
     // rows for the tile path: their count and degrees decide the tile grid

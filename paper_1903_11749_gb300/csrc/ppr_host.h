@@ -43,7 +43,7 @@ struct AliasCache {
 
 struct SegCache {
     uint32_t T = 0;               // threshold the tables were built for (0 = none)
-    NodeRec *node = nullptr;      // node records with eligible nodes switched to their tables
+    void *node = nullptr;         // node records (the graph's type) with eligible nodes switched to their tables
     SegEntry *entries = nullptr;  // all tables
     int64_t nodes = 0, entries_n = 0;
 };
@@ -80,7 +80,7 @@ struct ppr_graph {
     int64_t n = 0, m = 0;
     int64_t max_degree = 0, dangling = 0;
     bool wide = false;
-    ppr::NodeRec *node = nullptr;
+    void *node = nullptr;   // NodeRecN[n] (narrow layout) or NodeRec[n] (wide layout)
     void *edges = nullptr;  // EdgeN[m] or EdgeW[m]
     int64_t edge_records = 0;  // records the edge layout holds (blocked narrow rows: with padding)
     // block-diagonal instances

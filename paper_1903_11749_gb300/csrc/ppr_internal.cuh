@@ -1,13 +1,17 @@
 // ppr_internal.cuh -- device-side building blocks of libppr.so (sm_103a).
 //
 // Graph layout in HBM
-//   NodeRec (16 B, one aligned half-sector per node)
+//   NodeRec (16 B, one aligned half-sector per node; wide layout, alias tables)
 //     word0 = begin (bits 0..39) | count (bits 40..62) | segment flag (bit 63)
 //     word1 = W_u, the row's total weight (Sec. 2.1 routing denominator), or
 //             the target id when the row has exactly one edge (no search), or
 //             Q_v, the total fixed-point mass of a segment table (Algorithm 4);
 //             narrow blocked rows keep W_u in bits 0..31 and their summary
 //             size S (bits 32..55) and level count L (bits 56..59) above it
+//   NodeRecN (32 B, one sector per node; narrow layout): a NodeRec and the
+//     first four keys of the row's top summary level when that level has at
+//     most five keys (the fifth is W_u), so the step that reads the record
+//     ranks the draw within the top level and skips that sector
 //   plain rows:  begin/count index the edge-record array
 //   segment rows: begin/count index the segment-entry array
 //   EdgeN (8 B): {uint32 P, int32 col}  -- narrow layout, every W_u < 2^32
@@ -41,6 +45,12 @@ constexpr uint64_t kSegFlag = 1ull << 63;
 struct __align__(16) NodeRec {
     uint64_t word0;
     uint64_t total;
+};
+
+struct __align__(32) NodeRecN {
+    uint64_t word0;
+    uint64_t total;
+    uint32_t key[4];  // top-level keys 0..3 (see root_in_record), else 0xFFFFFFFF
 };
 
 struct __align__(8) EdgeN {
@@ -146,8 +156,38 @@ __device__ __forceinline__ NodeRec load_node(const NodeRec *node, uint32_t u)
     return r;
 }
 
+// One 32-byte sector in a single 256-bit load (sm_100+ vector width).
+struct Sector {
+    uint32_t v[8];
+};
+__device__ __forceinline__ Sector ld_sector(const void *p)
+{
+    Sector s;
+    asm("ld.global.nc.v8.u32 {%0,%1,%2,%3,%4,%5,%6,%7}, [%8];"
+                 : "=r"(s.v[0]), "=r"(s.v[1]), "=r"(s.v[2]), "=r"(s.v[3]), "=r"(s.v[4]), "=r"(s.v[5]), "=r"(s.v[6]),
+                   "=r"(s.v[7])
+                 : "l"(p));
+    return s;
+}
+
+
+// A blocked row of d edges with L >= 1 summary levels keeps its top level's
+// keys in the node record when that level has at most five keys
+// (ceil(d / 8^L) <= 5): keys 0..3 in NodeRecN::key, the fifth being W_u.
+__host__ __device__ __forceinline__ bool root_in_record(uint32_t d, uint32_t L)
+{
+    return L >= 1 && d <= (5u << (3 * L));
+}
+
 struct NarrowEdges {
     using Key = uint32_t;
+    using Node = NodeRecN;
+    // the record half of the sector; search_blocked reads the key half when
+    // it needs it (then an L1 hit: the first load brought the whole sector)
+    __device__ __forceinline__ static NodeRec load_node(const void *node, uint32_t u)
+    {
+        return ppr::load_node(reinterpret_cast<const NodeRec *>(static_cast<const NodeRecN *>(node) + u), 0);
+    }
     const EdgeN *e;
     // record index of edge 0 of a row whose region starts at `begin`
     __host__ __device__ __forceinline__ static uint64_t edge_base(uint64_t begin, uint32_t d)
@@ -164,6 +204,11 @@ struct NarrowEdges {
 };
 
 struct WideEdges {
+    using Node = NodeRec;
+    __device__ __forceinline__ static NodeRec load_node(const void *node, uint32_t u)
+    {
+        return ppr::load_node(static_cast<const NodeRec *>(node), u);
+    }
     const EdgeW *e;
     __host__ __device__ __forceinline__ static uint64_t edge_base(uint64_t begin, uint32_t) { return begin; }
     __device__ __forceinline__ uint4 load(uint64_t i) const
@@ -177,6 +222,11 @@ struct WideEdges {
 
 // Alias layout: begin/count of a node record index its alias slots.
 struct AliasEdges {
+    using Node = NodeRec;
+    __device__ __forceinline__ static NodeRec load_node(const void *node, uint32_t u)
+    {
+        return ppr::load_node(static_cast<const NodeRec *>(node), u);
+    }
     const AliasRec *e;
     __host__ __device__ __forceinline__ static uint64_t edge_base(uint64_t begin, uint32_t) { return begin; }
     __device__ __forceinline__ uint4 load(uint64_t i) const { return __ldg(reinterpret_cast<const uint4 *>(e) + i); }
@@ -243,19 +293,6 @@ __device__ __forceinline__ typename E::Rec search_serial_tally(const E &edges, u
     return edges.load(lo);
 }
 
-// One 32-byte sector in a single 256-bit load (sm_100+ vector width).
-struct Sector {
-    uint32_t v[8];
-};
-__device__ __forceinline__ Sector ld_sector(const void *p)
-{
-    Sector s;
-    asm("ld.global.nc.v8.u32 {%0,%1,%2,%3,%4,%5,%6,%7}, [%8];"
-                 : "=r"(s.v[0]), "=r"(s.v[1]), "=r"(s.v[2]), "=r"(s.v[3]), "=r"(s.v[4]), "=r"(s.v[5]), "=r"(s.v[6]),
-                   "=r"(s.v[7])
-                 : "l"(p));
-    return s;
-}
 
 __host__ __device__ __forceinline__ uint64_t pack_blocked_total(uint64_t W, uint32_t d)
 {
@@ -279,11 +316,17 @@ __device__ __forceinline__ uint32_t rank8(uint32_t k0, uint32_t k1, uint32_t k2,
 // with P > x.  TALLY counts the 32-byte sectors read.
 template <bool TALLY>
 __device__ __forceinline__ uint32_t search_blocked(const EdgeN *E, uint64_t begin, uint32_t d, uint32_t S, uint32_t L,
-                                                   uint32_t x, uint32_t &sectors)
+                                                   uint32_t x, const NodeRecN *rec, uint32_t &sectors)
 {
     const unsigned char *base = reinterpret_cast<const unsigned char *>(E + begin);  // sector-aligned
-    uint32_t b = 0, off = 0;
-    for (uint32_t l = L; l >= 1; --l) {
+    uint32_t b = 0, off = 0, l = L;
+    if (root_in_record(d, L)) {  // the top level (one sector) is ranked from the node record
+        const uint4 k = __ldg(reinterpret_cast<const uint4 *>(rec->key));
+        b = min(rank8(k.x, k.y, k.z, k.w, 0xffffffffu, 0xffffffffu, 0xffffffffu, x), (d - 1) >> (3 * L));
+        off = 1;
+        --l;
+    }
+    for (; l >= 1; --l) {
         const Sector k = ld_sector(base + 32ull * (off + b));
         const uint32_t c = rank8(k.v[0], k.v[1], k.v[2], k.v[3], k.v[4], k.v[5], k.v[6], x);
         off += level_sectors(d, l);

@@ -27,7 +27,7 @@
 namespace ppr {
 
 struct KParams {
-    const NodeRec *node;
+    const void *node;         // NodeRecN (narrow layout) or NodeRec (wide layout, alias tables)
     const void *edges;
     const SegEntry *seg;
     uint32_t k0, k1, T, R, tag;
@@ -92,7 +92,7 @@ __device__ __forceinline__ bool walk_step(const KParams &p, const E &edges, bool
                                           Tally &tl)
 {
     uint4 x = make_uint4(0, 0, 0, 0);
-    uint64_t w0 = 0, total = 0;
+    NodeRec r{};
 #ifdef PPR_CHECKED
     bool bad_node = false;
 #endif
@@ -105,10 +105,9 @@ __device__ __forceinline__ bool walk_step(const KParams &p, const E &edges, bool
             u = 0;  // read a valid record; the walk ends at this step
         }
 #endif
-        NodeRec r = load_node(p.node, u);
-        w0 = r.word0;
-        total = r.total;
+        r = E::load_node(p.node, u);
     }
+    const uint64_t w0 = r.word0, total = r.total;
     const uint32_t cnt = (uint32_t)(w0 >> 40) & kCountMask;
     const uint64_t beg = w0 & kBeginMask;
     const bool segf = SEG && (w0 >> 63);
@@ -201,7 +200,7 @@ __device__ __forceinline__ bool walk_step(const KParams &p, const E &edges, bool
     } else if (!big) {
         if constexpr (sizeof(typename E::Rec) == 8) {
             next = search_blocked<STATS>(edges.e, beg, cnt, (uint32_t)(total >> 32) & 0xffffffu, (uint32_t)(total >> 56),
-                                         (uint32_t)xr, tl.sectors);
+                                         (uint32_t)xr, static_cast<const NodeRecN *>(p.node) + u, tl.sectors);
         } else {
             next = E::target(STATS ? search_serial_tally(edges, beg, cnt, xr, tl.sectors) : search_serial(edges, beg, cnt, xr));
         }
@@ -442,7 +441,7 @@ static int launch_typed(ppr_ctx *ctx, const KParams &kp, const RunPlan &plan, in
     if (plan.l2_persist && ctx->l2_persist_max > 0 && ctx->l2_window_max > 0) {
         // node records persisting in L2: every step reads one, the rows'
         // records stream past them
-        const size_t bytes = std::min((size_t)kp.n_nodes * sizeof(NodeRec), ctx->l2_window_max);
+        const size_t bytes = std::min((size_t)kp.n_nodes * sizeof(typename E::Node), ctx->l2_window_max);
         if (ctx->l2_persist_set < std::min(bytes, ctx->l2_persist_max)) {
             ctx->l2_persist_set = std::min(bytes, ctx->l2_persist_max);
             PPR_CUDA(cudaDeviceSetLimit(cudaLimitPersistingL2CacheSize, ctx->l2_persist_set));

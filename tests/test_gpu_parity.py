@@ -206,13 +206,14 @@ def test_huge_rows_built_by_tiles(ppr, ctx, oracle):
 def test_rows_at_every_build_tier_boundary(ppr, ctx, oracle):
     """Rows whose degrees sit on each side of every build tier (thread per row
     up to 32 edges, warp per row up to 1,024, block per row up to 8,192, tiles
-    of 8,192 edges above) and of the 8-ary summary levels (8, 64, 512, 4,096),
-    in a plain and in a batched graph: the walks return to those rows often
-    enough to draw from most of their edges, and every count equals the
-    oracle's."""
+    of 8,192 edges above), of the 8-ary summary levels (8, 64, 512, 4,096) and
+    of the top levels kept in the node record (at most five keys: 40, 320,
+    2,560, 20,480), in a plain and in a batched graph: the walks return to
+    those rows often enough to draw from most of their edges, and every count
+    equals the oracle's."""
     rng = np.random.Generator(np.random.PCG64(17))
-    degs = [2, 8, 9, 31, 32, 33, 64, 65, 127, 128, 129, 512, 513, 1023, 1024, 1025, 4096, 4097, 8191, 8192, 8193,
-            16384, 16385, 24577]
+    degs = [2, 8, 9, 31, 32, 33, 40, 41, 64, 65, 127, 128, 129, 320, 321, 512, 513, 1023, 1024, 1025, 2560, 2561,
+            4096, 4097, 8191, 8192, 8193, 16384, 16385, 20480, 20481, 24577]
     h = len(degs)
     n = 6000
     edges = []
