@@ -118,9 +118,10 @@ int ppr_device_sms(const ppr_ctx *ctx);
 
 /*
  * Loads a weighted directed graph G = (V, E, w), w(e) > 0 (Sec. 2.1), in CSR
- * form and builds its device layout: 16-byte node records and per-row
- * inclusive 64-bit weight prefix sums (stored as 32-bit values when every row
- * total is below 2^32), built by device kernels.
+ * form and builds its device layout: node records (32 bytes, with the top
+ * level of the row's search tree, when every row total is below 2^32; else
+ * 16 bytes) and per-row inclusive 64-bit weight prefix sums (stored as
+ * 32-bit values when every row total is below 2^32), built by device kernels.
  *   n        number of nodes, 1 <= n <= PPR_MAX_NODES
  *   m        number of edges, 0 <= m <= PPR_MAX_EDGES
  *   row_ptr  int64[n+1], row_ptr[0] = 0, non-decreasing, row_ptr[n] = m
