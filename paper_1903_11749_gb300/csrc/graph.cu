@@ -848,7 +848,6 @@ int build_graph(ppr_ctx *ctx, int64_t n, int64_t m, const int64_t *row_ptr, cons
 
 constexpr int kSegMaxDeg = 8;
 constexpr int kSegMaxOut = 64;
-constexpr int kSegMaxContrib = 2048;  // >= 2 * (8 + 64 + 512)
 
 __device__ __forceinline__ uint64_t mul_shift32(uint64_t q, uint32_t f)
 {
@@ -895,174 +894,297 @@ struct RowView {
     }
 };
 
-struct SegScratch {
-    uint64_t key[kSegMaxContrib];
-    uint64_t val[kSegMaxContrib];
-    unsigned int count;
-    unsigned int flags;
+// Segment tables in two passes.  k_seg_scan (one warp per node, every node)
+// copies the plain record into the segment record array, tests the shape
+// (degree <= 8 at depths 0, 1 and 2) and counts the raw contributions the
+// path enumeration will make; eligible nodes are listed by that count.
+// k_seg_fill (one warp per listed node) enumerates the paths once, sums equal
+// outcomes in a shared-memory hash table, drops zero masses, rejects a node
+// with more than 64 outcomes, puts the rest in canonical order (terminated
+// before active, then node, then length) by ranking, and appends the table
+// at an atomically reserved offset.  A table's place in the entry array is
+// free (its record holds begin and count), so only its content is fixed.
+
+constexpr unsigned long long kSegEmpty = ~0ull;  // free hash slot (an outcome key's node field is below 2^31)
+constexpr uint32_t kSegSmallRaw = 128;  // raw contributions up to which the small table (256 slots) serves
+constexpr int kSegLargeSlots = 2048;    // the largest raw count is 8 * (1 + 8 * (1 + 2 * 8)) = 1,096
+
+struct SegCounters {
+    unsigned int listed[2];       // nodes listed: [0] small table, [1] large table
+    unsigned long long bound;     // sum over listed nodes of min(raw, 64): entries to allocate
+    unsigned long long used;      // entries written
+    unsigned long long tables;    // nodes given a table
 };
 
-// Builds v's outcome list in shared memory (sorted by key, reduced, zero
-// weights dropped).  Returns the number of outcomes, 0 if v is not eligible.
-// All lanes call it; the result is the same on every lane.
+// Hash table of one warp: more slots than the tier's largest raw count, so it never fills.
+template <int SLOTS>
+struct SegHash {
+    unsigned long long key[SLOTS];
+    unsigned long long val[SLOTS];
+    uint16_t used[SLOTS];          // claimed slots, in claim order
+    unsigned long long sk[kSegMaxOut], sq[kSegMaxOut];  // compacted, then ranked outcomes
+    unsigned int count;
+    unsigned int full;  // a probe found no slot (cannot happen when the scan's count is right): no table
+};
+
 template <class E>
-__device__ uint32_t seg_build_node(const RowView<E> &G, uint32_t v, uint32_t T, SegScratch *sc)
+__global__ void __launch_bounds__(256) k_seg_scan(RowView<E> G, int64_t n, typename E::Node *seg_node, uint32_t *list,
+                                                  SegCounters *ct)
 {
     const uint32_t lane = threadIdx.x & 31;
-    const uint32_t d1 = G.deg(v);
-    if (d1 < 1 || d1 > kSegMaxDeg) return 0;
-    // eligibility: depth-1 and depth-2 nodes have out-degree <= 8
-    bool ok = true;
-    for (uint32_t p = lane; p < d1 * kSegMaxDeg; p += 32) {
-        uint32_t i1 = p / kSegMaxDeg, i2 = p % kSegMaxDeg;
-        uint64_t wt;
-        uint32_t a;
-        G.edge(v, i1, wt, a);
-        uint32_t da = G.deg(a);
-        if (da > kSegMaxDeg) ok = false;
-        else if (i2 < da) {
-            uint32_t b;
-            G.edge(a, i2, wt, b);
-            if (G.deg(b) > kSegMaxDeg) ok = false;
-        }
-    }
-    if (!__all_sync(0xffffffffu, ok)) return 0;
-    if (lane == 0) sc->count = 0;
-    __syncwarp();
-    const uint32_t cont = (uint32_t)(0x100000000ull - T);  // 2^32 - T, T >= 1
-    const uint64_t Wv = G.total(v);
-    auto push = [&](uint32_t node, uint32_t active, uint32_t len, uint64_t q) {
-        unsigned int i = atomicAdd(&sc->count, 1u);
-        sc->key[i] = ((uint64_t)active << 63) | ((uint64_t)node << 8) | len;
-        sc->val[i] = q;
-    };
-    // all paths of length 1, 2, 3: enumerate (i1, i2, i3) with the shorter
-    // paths emitted by the combinations whose trailing indices are 0
-    for (uint32_t p = lane; p < d1 * kSegMaxDeg * kSegMaxDeg; p += 32) {
-        uint32_t i1 = p / (kSegMaxDeg * kSegMaxDeg), i2 = (p / kSegMaxDeg) % kSegMaxDeg, i3 = p % kSegMaxDeg;
-        uint64_t w1;
-        uint32_t a;
-        G.edge(v, i1, w1, a);
-        uint64_t q1 = mul_div(1ull << 62, w1, Wv);
-        uint32_t da = G.deg(a);
-        if (i2 == 0 && i3 == 0) {
-            push(a, 0, 0, mul_shift32(q1, T));
-            if (da == 0) push(a, 1, 1, mul_shift32(q1, cont));
-        }
-        if (da == 0 || i2 >= da) continue;
-        uint64_t w2;
-        uint32_t b;
-        G.edge(a, i2, w2, b);
-        uint64_t q2 = mul_div(mul_shift32(q1, cont), w2, G.total(a));
-        uint32_t db = G.deg(b);
-        if (i3 == 0) {
-            push(b, 0, 0, mul_shift32(q2, T));
-            if (db == 0) push(b, 1, 2, mul_shift32(q2, cont));
-        }
-        if (db == 0 || i3 >= db) continue;
-        uint64_t w3;
-        uint32_t c;
-        G.edge(b, i3, w3, c);
-        uint64_t q3 = mul_div(mul_shift32(q2, cont), w3, G.total(b));
-        push(c, 0, 0, mul_shift32(q3, T));
-        push(c, 1, 3, mul_shift32(q3, cont));
-    }
-    __syncwarp();
-    const uint32_t cnt = sc->count;
-    const uint32_t P2 = next_pow2(cnt);
-    for (uint32_t i = cnt + lane; i < P2; i += 32) {
-        sc->key[i] = ~0ull;
-        sc->val[i] = 0;
-    }
-    __syncwarp();
-    // bitonic sort of (key, val) pairs by key
-    for (uint32_t k = 2; k <= P2; k <<= 1) {
-        for (uint32_t j = k >> 1; j > 0; j >>= 1) {
-            for (uint32_t i = lane; i < P2; i += 32) {
-                uint32_t l = i ^ j;
-                if (l > i) {
-                    uint64_t x = sc->key[i], y = sc->key[l];
-                    bool up = (i & k) == 0;
-                    if ((x > y) == up) {
-                        sc->key[i] = y;
-                        sc->key[l] = x;
-                        uint64_t t = sc->val[i];
-                        sc->val[i] = sc->val[l];
-                        sc->val[l] = t;
-                    }
-                }
+    const int64_t warps = (int64_t)gridDim.x * (blockDim.x >> 5);
+    for (int64_t v = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5; v < n; v += warps) {
+        if (lane == 0) seg_node[v] = G.node[v];  // plain record unless a table replaces it
+        const uint32_t d1 = G.deg((uint32_t)v);
+        if (d1 < 1 || d1 > (uint32_t)kSegMaxDeg) continue;
+        bool ok = true;
+        uint32_t raw = 0;
+        for (uint32_t p = lane; p < d1 * kSegMaxDeg; p += 32) {
+            const uint32_t i1 = p / kSegMaxDeg, i2 = p % kSegMaxDeg;
+            uint64_t wt;
+            uint32_t a;
+            G.edge((uint32_t)v, i1, wt, a);
+            const uint32_t da = G.deg(a);
+            if (da > (uint32_t)kSegMaxDeg) {
+                ok = false;
+                continue;
             }
-            __syncwarp();
+            if (i2 == 0) raw += 1 + (da == 0);  // (a, terminated), and (a, active, 1) at a dead end
+            if (i2 < da) {
+                uint32_t b;
+                G.edge(a, i2, wt, b);
+                const uint32_t db = G.deg(b);
+                if (db > (uint32_t)kSegMaxDeg) ok = false;
+                else raw += 1 + (db == 0) + 2 * db;  // (b, terminated), dead end, both outcomes at each c
+            }
+        }
+        if (!__all_sync(0xffffffffu, ok)) continue;
+#pragma unroll
+        for (int o = 16; o > 0; o >>= 1) raw += __shfl_xor_sync(0xffffffffu, raw, o);
+        if (lane == 0) {
+            const int tier = raw <= kSegSmallRaw ? 0 : 1;
+            const uint32_t k = atomicAdd(&ct->listed[tier], 1u);
+            list[tier ? n - 1 - k : k] = (uint32_t)v;  // small tier from the front, large from the back
+            atomicAdd(&ct->bound, (unsigned long long)min(raw, (uint32_t)kSegMaxOut));
         }
     }
-    // reduce equal keys (integer sums: order free) -- lane 0, at most 2048 entries
+}
+
+template <int SLOTS>
+__device__ __forceinline__ void seg_insert(SegHash<SLOTS> *h, uint32_t node, uint32_t active, uint32_t len, uint64_t q)
+{
+    const unsigned long long key = ((unsigned long long)active << 63) | ((unsigned long long)node << 8) | len;
+    uint32_t s = (node * 0x9E3779B1u ^ (len << 29) ^ (active << 31)) & (SLOTS - 1);
+    for (uint32_t probe = 0; probe < (uint32_t)SLOTS; ++probe) {
+        const unsigned long long prev = atomicCAS(&h->key[s], kSegEmpty, key);
+        if (prev == kSegEmpty) h->used[atomicAdd(&h->count, 1u)] = (uint16_t)s;  // each claim takes a new slot
+        if (prev == kSegEmpty || prev == key) {
+            atomicAdd(&h->val[s], (unsigned long long)q);
+            return;
+        }
+        s = (s + 1) & (SLOTS - 1);
+    }
+    h->full = 1;
+}
+
+// Tables of the nodes of one tier of `list`; SLOTS is above the tier's
+// largest raw count.  Each warp's hash table is cleared once and restored
+// slot by slot after each node.
+template <class E, int SLOTS, int WARPS>
+__global__ void __launch_bounds__(32 * WARPS) k_seg_fill(RowView<E> G, uint32_t T, const uint32_t *list, int tier,
+                                                         int64_t n, SegCounters *ct, SegEntry *ent,
+                                                         typename E::Node *seg_node)
+{
+    extern __shared__ __align__(16) unsigned char smem_raw[];
+    SegHash<SLOTS> *h = reinterpret_cast<SegHash<SLOTS> *>(smem_raw) + (threadIdx.x >> 5);
+    const uint32_t lane = threadIdx.x & 31, below = (1u << lane) - 1;
+    for (uint32_t i = lane; i < (uint32_t)SLOTS; i += 32) {
+        h->key[i] = kSegEmpty;
+        h->val[i] = 0;
+    }
     if (lane == 0) {
-        uint32_t outn = 0;
-        uint32_t i = 0;
-        while (i < cnt) {
-            uint64_t k = sc->key[i], s = 0;
-            while (i < cnt && sc->key[i] == k) s += sc->val[i++];
-            if (s > 0) {
-                sc->key[outn] = k;
-                sc->val[outn] = s;
-                ++outn;
+        h->count = 0;
+        h->full = 0;
+    }
+    __syncwarp();
+    const uint32_t listed = ct->listed[tier];
+    const uint32_t cont = (uint32_t)(0x100000000ull - T);  // 2^32 - T, T >= 1
+    const int64_t warps = (int64_t)gridDim.x * WARPS;
+    for (int64_t t = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5; t < listed; t += warps) {
+        const uint32_t v = list[tier ? n - 1 - t : t];
+        const uint32_t d1 = G.deg(v);
+        const uint64_t Wv = G.total(v);
+        // all paths of length 1, 2, 3: (i1, i2, i3), the shorter ones emitted by
+        // the combinations whose trailing indices are 0 (the paper's masses in
+        // 2^62 fixed point, the same arithmetic as the oracle's)
+        for (uint32_t p = lane; p < d1 * kSegMaxDeg * kSegMaxDeg; p += 32) {
+            const uint32_t i1 = p / (kSegMaxDeg * kSegMaxDeg), i2 = (p / kSegMaxDeg) % kSegMaxDeg, i3 = p % kSegMaxDeg;
+            uint64_t w1;
+            uint32_t a;
+            G.edge(v, i1, w1, a);
+            const uint64_t q1 = mul_div(1ull << 62, w1, Wv);
+            const uint32_t da = G.deg(a);
+            if (i2 == 0 && i3 == 0) {
+                seg_insert(h, a, 0, 0, mul_shift32(q1, T));
+                if (da == 0) seg_insert(h, a, 1, 1, mul_shift32(q1, cont));
             }
+            if (da == 0 || i2 >= da) continue;
+            uint64_t w2;
+            uint32_t b;
+            G.edge(a, i2, w2, b);
+            const uint64_t q2 = mul_div(mul_shift32(q1, cont), w2, G.total(a));
+            const uint32_t db = G.deg(b);
+            if (i3 == 0) {
+                seg_insert(h, b, 0, 0, mul_shift32(q2, T));
+                if (db == 0) seg_insert(h, b, 1, 2, mul_shift32(q2, cont));
+            }
+            if (db == 0 || i3 >= db) continue;
+            uint64_t w3;
+            uint32_t c;
+            G.edge(b, i3, w3, c);
+            const uint64_t q3 = mul_div(mul_shift32(q2, cont), w3, G.total(b));
+            seg_insert(h, c, 0, 0, mul_shift32(q3, T));
+            seg_insert(h, c, 1, 3, mul_shift32(q3, cont));
         }
-        sc->flags = outn;
-    }
-    __syncwarp();
-    uint32_t outn = sc->flags;
-    __syncwarp();
-    return outn <= (uint32_t)kSegMaxOut ? outn : 0u;
-}
-
-template <class E>
-__global__ void k_seg_count(RowView<E> G, int64_t n, uint32_t T, uint32_t *counts)
-{
-    extern __shared__ __align__(16) unsigned char smem_raw[];
-    SegScratch *sc = reinterpret_cast<SegScratch *>(smem_raw) + (threadIdx.x >> 5);
-    const int64_t warps = (int64_t)gridDim.x * (blockDim.x >> 5);
-    for (int64_t v = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5; v < n; v += warps) {
-        uint32_t c = seg_build_node(G, (uint32_t)v, T, sc);
-        if ((threadIdx.x & 31) == 0) counts[v] = c;
-    }
-}
-
-template <class E>
-__global__ void k_seg_write(RowView<E> G, int64_t n, uint32_t T, const uint64_t *offs, SegEntry *ent,
-                            typename E::Node *seg_node)
-{
-    extern __shared__ __align__(16) unsigned char smem_raw[];
-    SegScratch *sc = reinterpret_cast<SegScratch *>(smem_raw) + (threadIdx.x >> 5);
-    const uint32_t lane = threadIdx.x & 31;
-    const int64_t warps = (int64_t)gridDim.x * (blockDim.x >> 5);
-    for (int64_t v = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5; v < n; v += warps) {
-        uint64_t o = offs[v];
-        uint32_t c = (uint32_t)(offs[v + 1] - o);
-        if (c == 0) {
-            if (lane == 0) seg_node[v] = G.node[v];  // not eligible: plain record
+        __syncwarp();
+        // outcomes of nonzero mass, compacted (the first 64 kept); slots restored
+        const uint32_t D = h->count;
+        uint32_t K = 0;
+        for (uint32_t i0 = 0; i0 < D; i0 += 32) {
+            const uint32_t i = i0 + lane;
+            unsigned long long k = 0, q = 0;
+            if (i < D) {
+                const uint32_t s = h->used[i];
+                k = h->key[s];
+                q = h->val[s];
+                h->key[s] = kSegEmpty;
+                h->val[s] = 0;
+            }
+            const bool nzero = i < D && q > 0;
+            const uint32_t m = __ballot_sync(0xffffffffu, nzero);
+            const uint32_t pos = K + __popc(m & below);
+            if (nzero && pos < (uint32_t)kSegMaxOut) {
+                h->sk[pos] = k;
+                h->sq[pos] = q;
+            }
+            K += __popc(m);
+        }
+        const bool full = h->full != 0;
+        __syncwarp();
+        if (lane == 0) {
+            h->count = 0;
+            h->full = 0;
+        }
+        if (K == 0 || K > (uint32_t)kSegMaxOut || full) {  // no table: the plain record stays
+            __syncwarp();
             continue;
         }
-        uint32_t c2 = seg_build_node(G, (uint32_t)v, T, sc);
-        (void)c2;  // identical to the counting pass
-        if (lane == 0) {
-            uint64_t acc = 0;
-            for (uint32_t i = 0; i < c; ++i) {
-                uint64_t k = sc->key[i];
-                acc += sc->val[i];
-                SegEntry s;
-                s.cum = acc;
-                s.node = (uint32_t)((k >> 8) & 0x7fffffffull);
-                s.mark_len = ((uint32_t)(k >> 63) << 8) | (uint32_t)(k & 0xff);
-                ent[o + i] = s;
+        // canonical order: rank of each key among the K distinct keys
+        unsigned long long mk[2], mq[2];
+        uint32_t rk[2];
+#pragma unroll
+        for (int e = 0; e < 2; ++e) {
+            const uint32_t i = (uint32_t)e * 32 + lane;
+            mk[e] = i < K ? h->sk[i] : ~0ull;
+            mq[e] = i < K ? h->sq[i] : 0ull;
+            uint32_t r = 0;
+            for (uint32_t j = 0; j < K; ++j) r += h->sk[j] < mk[e];
+            rk[e] = r;
+        }
+        __syncwarp();
+#pragma unroll
+        for (int e = 0; e < 2; ++e)
+            if ((uint32_t)e * 32 + lane < K) {
+                h->sk[rk[e]] = mk[e];
+                h->sq[rk[e]] = mq[e];
             }
+        __syncwarp();
+        // inclusive prefix of the masses in that order
+        unsigned long long cum[2];
+        unsigned long long carry = 0;
+#pragma unroll
+        for (int e = 0; e < 2; ++e) {
+            const uint32_t i = (uint32_t)e * 32 + lane;
+            unsigned long long x = i < K ? h->sq[i] : 0ull;
+#pragma unroll
+            for (int o = 1; o < 32; o <<= 1) {
+                const unsigned long long y = __shfl_up_sync(0xffffffffu, x, o);
+                if (lane >= (uint32_t)o) x += y;
+            }
+            cum[e] = carry + x;
+            carry += __shfl_sync(0xffffffffu, x, 31);
+        }
+        unsigned long long base = 0;
+        if (lane == 0) {
+            base = atomicAdd(&ct->used, (unsigned long long)K);
+            atomicAdd(&ct->tables, 1ull);
+        }
+        base = __shfl_sync(0xffffffffu, base, 0);
+#pragma unroll
+        for (int e = 0; e < 2; ++e) {
+            const uint32_t i = (uint32_t)e * 32 + lane;
+            if (i < K) {
+                const unsigned long long k = h->sk[i];
+                SegEntry se;
+                se.cum = cum[e];
+                se.node = (uint32_t)((k >> 8) & 0x7fffffffull);
+                se.mark_len = ((uint32_t)(k >> 63) << 8) | (uint32_t)(k & 0xff);
+                ent[base + i] = se;
+            }
+        }
+        if (lane == 0) {
             typename E::Node r = G.node[v];  // a NodeRecN keeps its (unused) top-level keys
-            r.word0 = pack_word0(o, c, true);
-            r.total = acc;
+            r.word0 = pack_word0(base, K, true);
+            r.total = carry;  // Q_v, the table's total mass
             seg_node[v] = r;
         }
         __syncwarp();
     }
+}
+
+template <class E>
+static int seg_build_typed(ppr_graph *g, uint32_t T, cudaStream_t st, const RowView<E> &G, uint32_t *list,
+                           SegCounters *d_ct)
+{
+    const int64_t n = g->n;
+    typename E::Node *seg_node = static_cast<typename E::Node *>(g->seg.node);
+    const int blocks = (int)std::max<int64_t>(1, std::min<int64_t>((n + 7) / 8, (int64_t)g->ctx->sms * 32));
+    k_seg_scan<E><<<blocks, 256, 0, st>>>(G, n, seg_node, list, d_ct);
+    note_launch();
+    SegCounters hc;
+    cudaError_t e = cudaMemcpyAsync(&hc, d_ct, sizeof(hc), cudaMemcpyDeviceToHost, st);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(st);
+    if (e != cudaSuccess) return cuda_fail(e, "segment scan");
+    int rc;
+    if ((rc = dev_alloc((void **)&g->seg.entries, sizeof(SegEntry) * (hc.bound > 0 ? hc.bound : 1), "segment tables",
+                        st)))
+        return rc;
+    if (hc.listed[0]) {
+        constexpr int W = 8;
+        const size_t smem = sizeof(SegHash<2 * kSegSmallRaw>) * W;
+        PPR_CUDA(cudaFuncSetAttribute(k_seg_fill<E, 2 * kSegSmallRaw, W>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                      (int)smem));
+        const int fb = (int)std::min<int64_t>((hc.listed[0] + W - 1) / W, (int64_t)g->ctx->sms * 16);
+        k_seg_fill<E, 2 * kSegSmallRaw, W><<<fb, 32 * W, smem, st>>>(G, T, list, 0, n, d_ct, g->seg.entries, seg_node);
+        note_launch();
+    }
+    if (hc.listed[1]) {
+        constexpr int W = 2;
+        const size_t smem = sizeof(SegHash<kSegLargeSlots>) * W;
+        PPR_CUDA(cudaFuncSetAttribute(k_seg_fill<E, kSegLargeSlots, W>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                      (int)smem));
+        const int fb = (int)std::min<int64_t>((hc.listed[1] + W - 1) / W, (int64_t)g->ctx->sms * 8);
+        k_seg_fill<E, kSegLargeSlots, W><<<fb, 32 * W, smem, st>>>(G, T, list, 1, n, d_ct, g->seg.entries, seg_node);
+        note_launch();
+    }
+    PPR_CUDA(cudaGetLastError());
+    e = cudaMemcpyAsync(&hc, d_ct, sizeof(hc), cudaMemcpyDeviceToHost, st);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(st);
+    if (e != cudaSuccess) return cuda_fail(e, "segment build");
+    g->seg.nodes = (int64_t)hc.tables;
+    g->seg.entries_n = (int64_t)hc.used;
+    g->device_bytes += (int64_t)(sizeof(typename E::Node) * n + sizeof(SegEntry) * hc.bound);
+    return PPR_OK;
 }
 
 int build_segments(ppr_graph *g, uint32_t T, cudaStream_t st)
@@ -1073,78 +1195,37 @@ int build_segments(ppr_graph *g, uint32_t T, cudaStream_t st)
     dev_free(g->seg.entries, st);
     g->seg = SegCache{};
     const int64_t n = g->n;
-    uint32_t *d_cnt = nullptr;
-    uint64_t *d_off = nullptr, *d_tmp = nullptr;
+    uint32_t *list = nullptr;
+    SegCounters *d_ct = nullptr;
     int rc;
-    int64_t tiles = (n + kScanTile - 1) / kScanTile;
-    if ((rc = dev_alloc((void **)&d_cnt, sizeof(uint32_t) * n, "segment counts", st))) return rc;
-    if ((rc = dev_alloc((void **)&d_off, sizeof(uint64_t) * (n + 1), "segment offsets", st))) return dev_free(d_cnt, st), rc;
-    if ((rc = dev_alloc((void **)&d_tmp, sizeof(uint64_t) * (tiles + 2), "scan scratch", st)))
-        return dev_free(d_cnt, st), dev_free(d_off, st), rc;
-    auto fail = [&](int code) {
-        dev_free(d_cnt, st);
-        dev_free(d_off, st);
-        dev_free(d_tmp, st);
+    auto done = [&](int code) {
+        dev_free(list, st);
+        dev_free(d_ct, st);
+        if (code != PPR_OK) {
+            cudaStreamSynchronize(st);
+            dev_free(g->seg.node, st);
+            dev_free(g->seg.entries, st);
+            g->seg = SegCache{};
+        }
         return code;
     };
-    const int wpb = 2;
-    const size_t smem = sizeof(SegScratch) * wpb;
-    int blocks = (int)std::min<int64_t>((n + wpb - 1) / wpb, (int64_t)g->ctx->sms * 32);
-    if (blocks < 1) blocks = 1;
-    cudaError_t e;
-    if (g->wide) {
-        RowView<WideEdges> G{static_cast<const NodeRec *>(g->node), WideEdges{(const EdgeW *)g->edges}};
-        cudaFuncSetAttribute(k_seg_count<WideEdges>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
-        k_seg_count<WideEdges><<<blocks, wpb * 32, smem, st>>>(G, n, T, d_cnt);
-        note_launch();
-    } else {
-        RowView<NarrowEdges> G{static_cast<const NodeRecN *>(g->node), NarrowEdges{(const EdgeN *)g->edges}};
-        cudaFuncSetAttribute(k_seg_count<NarrowEdges>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
-        k_seg_count<NarrowEdges><<<blocks, wpb * 32, smem, st>>>(G, n, T, d_cnt);
-        note_launch();
-    }
-    exclusive_scan_u32(d_cnt, n, d_off, d_tmp, st);
-    uint64_t total = 0;
-    e = cudaMemcpyAsync(&total, d_off + n, sizeof(uint64_t), cudaMemcpyDeviceToHost, st);
-    if (e == cudaSuccess) e = cudaStreamSynchronize(st);
-    if (e != cudaSuccess) return fail(cuda_fail(e, "segment count"));
     const size_t node_bytes = g->wide ? sizeof(NodeRec) : sizeof(NodeRecN);
-    if ((rc = dev_alloc((void **)&g->seg.node, node_bytes * n, "segment node records", st))) return fail(rc);
-    if ((rc = dev_alloc((void **)&g->seg.entries, sizeof(SegEntry) * (total > 0 ? total : 1), "segment tables", st))) {
-        dev_free(g->seg.node, st);
-        g->seg.node = nullptr;
-        return fail(rc);
-    }
+    if ((rc = dev_alloc((void **)&list, sizeof(uint32_t) * n, "segment node list", st)) ||
+        (rc = dev_alloc((void **)&d_ct, sizeof(SegCounters), "segment counters", st)) ||
+        (rc = dev_alloc((void **)&g->seg.node, node_bytes * n, "segment node records", st)))
+        return done(rc);
+    cudaError_t e = cudaMemsetAsync(d_ct, 0, sizeof(SegCounters), st);
+    if (e != cudaSuccess) return done(cuda_fail(e, "memset"));
     if (g->wide) {
         RowView<WideEdges> G{static_cast<const NodeRec *>(g->node), WideEdges{(const EdgeW *)g->edges}};
-        cudaFuncSetAttribute(k_seg_write<WideEdges>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
-        k_seg_write<WideEdges><<<blocks, wpb * 32, smem, st>>>(G, n, T, d_off, g->seg.entries,
-                                                              static_cast<NodeRec *>(g->seg.node));
-        note_launch();
+        rc = seg_build_typed(g, T, st, G, list, d_ct);
     } else {
         RowView<NarrowEdges> G{static_cast<const NodeRecN *>(g->node), NarrowEdges{(const EdgeN *)g->edges}};
-        cudaFuncSetAttribute(k_seg_write<NarrowEdges>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
-        k_seg_write<NarrowEdges><<<blocks, wpb * 32, smem, st>>>(G, n, T, d_off, g->seg.entries,
-                                                                static_cast<NodeRecN *>(g->seg.node));
-        note_launch();
+        rc = seg_build_typed(g, T, st, G, list, d_ct);
     }
-    e = cudaGetLastError();
-    if (e == cudaSuccess) e = cudaStreamSynchronize(st);
-    if (e != cudaSuccess) return fail(cuda_fail(e, "segment build"));
+    if (rc != PPR_OK) return done(rc);
     g->seg.T = T;
-    g->seg.entries_n = (int64_t)total;
-    {
-        // number of nodes with a table, for the info query
-        std::vector<uint32_t> hc((size_t)n);
-        e = cudaMemcpy(hc.data(), d_cnt, sizeof(uint32_t) * n, cudaMemcpyDeviceToHost);
-        if (e != cudaSuccess) return fail(cuda_fail(e, "segment count copy"));
-        int64_t nz = 0;
-        for (uint32_t c : hc) nz += c > 0;
-        g->seg.nodes = nz;
-    }
-    g->device_bytes += (int64_t)(node_bytes * n + sizeof(SegEntry) * total);
-    fail(PPR_OK);
-    return PPR_OK;
+    return done(PPR_OK);
 }
 
 // --------------------------------------------------------- alias tables ----

@@ -261,6 +261,34 @@ def test_segment_mode_matches_segment_oracle(ppr, ctx, oracle):
         assert info.segment_entries == int(og.seg_off[-1])
 
 
+@pytest.mark.parametrize("n,dmin", [(12, 8), (40, 1), (400, 4)])
+def test_segment_tables_every_tier(ppr, ctx, oracle, n, dmin):
+    """Segment tables where every node is eligible (all degrees <= 8): 12
+    nodes of degree 8 give 1,096 raw path contributions per table (the large
+    hash tier) folded into at most 48 outcomes; 40 nodes of degree 1..8 mix
+    both tiers with tables above 64 outcomes (rejected); 400 nodes of degree
+    4..8 reject most.  Tables, rows and counts equal the oracle's."""
+    rng = np.random.Generator(np.random.PCG64(n))
+    edges = []
+    for u in range(n):
+        for _ in range(int(rng.integers(dmin, 9))):
+            edges.append((u, int(rng.integers(0, n)), int(rng.integers(1, 1000))))
+    g = I.from_edges(n, edges)
+    G = ctx.load_graph(g.n, g.row_ptr, g.col, g.w)
+    og = oracle.prepare(g.n, g.row_ptr, g.col, g.w)
+    for alpha in (0.15, 0.6):
+        ref = oracle_rows(oracle, g, alpha, 300, 4, segments=True, topk=6, og=og)
+        for kernel in (0, 1):
+            assert_same(G.run(alpha=alpha, R=300, seed=4, segments=True, topk=6, kernel=kernel), ref, topk=6)
+        info = G.info()
+        assert info.segment_nodes == int((np.diff(og.seg_off) > 0).sum())
+        assert info.segment_entries == int(og.seg_off[-1])
+    if n == 12:
+        assert info.segment_nodes == n  # every table kept
+    if n == 40:
+        assert 0 < info.segment_nodes < n  # some tables above 64 outcomes
+
+
 def test_batched_instances_equal_each_instance_alone(ppr, ctx, oracle):
     inst = I.chung_lu_instances(count=12, nmin=20, nmax=400, seed=5)
     G = ctx.load_graph_batch(inst.node_off, inst.row_ptr, inst.col, inst.w)
