@@ -543,6 +543,7 @@ def run_serving(args):
     results = {}
     clocks = Clocks(local, None)
     clocks.start()
+    launches0 = ppr.kernel_launches()
     for rho in args.serve_rho:
         qs = make_queries(n_meas)
         rate = rho * cap_walks / (((smax - 1) / np.log(smax)) * wl["R"])
@@ -555,6 +556,7 @@ def run_serving(args):
                              "p99_ms": float(np.percentile(lat, 99)), "mean_ms": float(lat.mean()),
                              "walks_per_s": walks / ((t1 - t0) / 1e9), "seconds": (t1 - t0) / 1e9}
     clk = clocks.stop()
+    launches = ppr.kernel_launches() - launches0  # every measured stream (all rho)
     ctx.serve_stop()
     T = ppr.alpha_threshold(wl["alpha"])
     main_r = results[str(args.serve_rho[0])]
@@ -568,7 +570,7 @@ def run_serving(args):
                        "step": "one query (ms_per_step = mean latency)"},
             "p50_ms": main_r["p50_ms"], "p99_ms": main_r["p99_ms"], "walks_per_s": main_r["walks_per_s"],
             "capacity_walks_per_s": cap_walks, "mean_walks_per_query": mean_walks, "by_rho": results,
-            "clocks": clk, "gpu_launches": None}
+            "clocks": clk, "gpu_launches": launches}
     print(json.dumps(line))
     return 0
 

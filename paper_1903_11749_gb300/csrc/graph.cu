@@ -894,8 +894,8 @@ struct RowView {
     }
 };
 
-// Segment tables in two passes.  k_seg_scan (one warp per node, every node)
-// copies the plain record into the segment record array, tests the shape
+// Segment tables in two passes.  k_seg_scan (every node; a warp takes 32 at a
+// time) copies the plain record into the segment record array, tests the shape
 // (degree <= 8 at depths 0, 1 and 2) and counts the raw contributions the
 // path enumeration will make; eligible nodes are listed by that count.
 // k_seg_fill (one warp per listed node) enumerates the paths once, sums equal
@@ -932,40 +932,61 @@ __global__ void __launch_bounds__(256) k_seg_scan(RowView<E> G, int64_t n, typen
                                                   SegCounters *ct)
 {
     const uint32_t lane = threadIdx.x & 31;
-    const int64_t warps = (int64_t)gridDim.x * (blockDim.x >> 5);
-    for (int64_t v = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5; v < n; v += warps) {
-        if (lane == 0) seg_node[v] = G.node[v];  // plain record unless a table replaces it
-        const uint32_t d1 = G.deg((uint32_t)v);
-        if (d1 < 1 || d1 > (uint32_t)kSegMaxDeg) continue;
-        bool ok = true;
-        uint32_t raw = 0;
-        for (uint32_t p = lane; p < d1 * kSegMaxDeg; p += 32) {
-            const uint32_t i1 = p / kSegMaxDeg, i2 = p % kSegMaxDeg;
-            uint64_t wt;
-            uint32_t a;
-            G.edge((uint32_t)v, i1, wt, a);
-            const uint32_t da = G.deg(a);
-            if (da > (uint32_t)kSegMaxDeg) {
-                ok = false;
-                continue;
-            }
-            if (i2 == 0) raw += 1 + (da == 0);  // (a, terminated), and (a, active, 1) at a dead end
-            if (i2 < da) {
-                uint32_t b;
-                G.edge(a, i2, wt, b);
-                const uint32_t db = G.deg(b);
-                if (db > (uint32_t)kSegMaxDeg) ok = false;
-                else raw += 1 + (db == 0) + 2 * db;  // (b, terminated), dead end, both outcomes at each c
-            }
+    const int64_t stride = (int64_t)gridDim.x * blockDim.x;
+    // each warp takes 32 consecutive nodes (coalesced record copy and degree
+    // test), then examines the candidates among them one by one with all lanes
+    for (int64_t base = (int64_t)blockIdx.x * blockDim.x + (threadIdx.x & ~31u); base < n; base += stride) {
+        const int64_t vl = base + lane;
+        uint32_t dl = 0;
+        if (vl < n) {
+            const typename E::Node r = G.node[vl];
+            seg_node[vl] = r;  // plain record unless a table replaces it
+            dl = (uint32_t)(r.word0 >> 40) & kCountMask;
         }
-        if (!__all_sync(0xffffffffu, ok)) continue;
+        uint32_t cand = __ballot_sync(0xffffffffu, vl < n && dl >= 1 && dl <= (uint32_t)kSegMaxDeg);
+        while (cand) {
+            const uint32_t src_lane = __ffs(cand) - 1;
+            cand &= cand - 1;
+            const uint32_t v = (uint32_t)(base + src_lane);
+            const uint32_t d1 = __shfl_sync(0xffffffffu, dl, src_lane);
+            // depth 1 first: most candidates have a neighbour above the limit
+            bool ok = true;
+            if (lane < d1) {
+                uint64_t wt;
+                uint32_t a;
+                G.edge(v, lane, wt, a);
+                ok = G.deg(a) <= (uint32_t)kSegMaxDeg;
+            }
+            if (!__all_sync(0xffffffffu, ok)) continue;
+            uint32_t raw = 0;
+            for (uint32_t p = lane; p < d1 * kSegMaxDeg; p += 32) {
+                const uint32_t i1 = p / kSegMaxDeg, i2 = p % kSegMaxDeg;
+                uint64_t wt;
+                uint32_t a;
+                G.edge(v, i1, wt, a);
+                const uint32_t da = G.deg(a);
+                if (da > (uint32_t)kSegMaxDeg) {
+                    ok = false;
+                    continue;
+                }
+                if (i2 == 0) raw += 1 + (da == 0);  // (a, terminated), and (a, active, 1) at a dead end
+                if (i2 < da) {
+                    uint32_t b;
+                    G.edge(a, i2, wt, b);
+                    const uint32_t db = G.deg(b);
+                    if (db > (uint32_t)kSegMaxDeg) ok = false;
+                    else raw += 1 + (db == 0) + 2 * db;  // (b, terminated), dead end, both outcomes at each c
+                }
+            }
+            if (!__all_sync(0xffffffffu, ok)) continue;
 #pragma unroll
-        for (int o = 16; o > 0; o >>= 1) raw += __shfl_xor_sync(0xffffffffu, raw, o);
-        if (lane == 0) {
-            const int tier = raw <= kSegSmallRaw ? 0 : 1;
-            const uint32_t k = atomicAdd(&ct->listed[tier], 1u);
-            list[tier ? n - 1 - k : k] = (uint32_t)v;  // small tier from the front, large from the back
-            atomicAdd(&ct->bound, (unsigned long long)min(raw, (uint32_t)kSegMaxOut));
+            for (int o = 16; o > 0; o >>= 1) raw += __shfl_xor_sync(0xffffffffu, raw, o);
+            if (lane == 0) {
+                const int tier = raw <= kSegSmallRaw ? 0 : 1;
+                const uint32_t k = atomicAdd(&ct->listed[tier], 1u);
+                list[tier ? n - 1 - k : k] = v;  // small tier from the front, large from the back
+                atomicAdd(&ct->bound, (unsigned long long)min(raw, (uint32_t)kSegMaxOut));
+            }
         }
     }
 }
@@ -1148,7 +1169,7 @@ static int seg_build_typed(ppr_graph *g, uint32_t T, cudaStream_t st, const RowV
 {
     const int64_t n = g->n;
     typename E::Node *seg_node = static_cast<typename E::Node *>(g->seg.node);
-    const int blocks = (int)std::max<int64_t>(1, std::min<int64_t>((n + 7) / 8, (int64_t)g->ctx->sms * 32));
+    const int blocks = (int)std::max<int64_t>(1, std::min<int64_t>((n + 255) / 256, (int64_t)g->ctx->sms * 16));
     k_seg_scan<E><<<blocks, 256, 0, st>>>(G, n, seg_node, list, d_ct);
     note_launch();
     SegCounters hc;
