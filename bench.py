@@ -37,10 +37,10 @@ WORKLOADS = {
                    desc="R-MAT scale 20, 16.8M edges (a=.57 b=.19 c=.19), Zipf(1.5) w in [1,1000], 5% dangling"),
     "er1k": dict(alpha=0.15, R=1000, seed=1, topk=32, segments=False,
                  desc="Erdos-Renyi n=1000 m=10000, w U[1,10], dense n x n counts"),
-    "rmat24": dict(alpha=0.15, R=50, seed=1, topk=64, segments=True,
+    "rmat24": dict(alpha=0.15, R=50, seed=1, topk=64, segments=True, launch=dict(refill_lanes=24),
                    desc="R-MAT scale 24, 268M edges + hub > 1e6, Zipf(1.5) w in [1,1000], 5% dangling, "
                         "depth-3 segments for out-degree <= 8"),
-    "rmat24plain": dict(alpha=0.15, R=50, seed=1, topk=64, segments=False,
+    "rmat24plain": dict(alpha=0.15, R=50, seed=1, topk=64, segments=False, launch=dict(refill_lanes=24),
                         desc="R-MAT scale 24 as rmat24, plain steps only"),
     "rmat20alias": dict(alpha=0.2, R=100, seed=1, topk=32, segments=False, sampler=1,
                         desc="R-MAT scale 20 as rmat20, integer alias sampler (Algorithm 1 tables built every step)"),
@@ -162,15 +162,17 @@ def kernel_source_hash():
     return h.hexdigest()[:16]
 
 
-def recorded_traffic(workload: str):
+def recorded_traffic(workload: str, launch: dict):
     """DRAM bytes per walker launch from the committed ncu summary, if it was
-    taken on the current kernel source; else None."""
+    taken on the current kernel source with the same launch shape; else None."""
     p = os.path.join(ROOT, "profiles", "walker_traffic.json")
     if not os.path.exists(p):
         return None
     d = json.load(open(p))
     e = d.get(workload)
     if not e or e.get("kernel_hash") != kernel_source_hash():
+        return None
+    if e.get("launch", {}) != {k: v for k, v in launch.items() if v}:
         return None
     return e.get("dram_bytes_per_launch")
 
@@ -507,7 +509,10 @@ def run_serving(args):
         return [rng.choice(g.n, size=int(s), replace=False).astype(np.int32) for s in sizes]
 
     kw = dict(alpha=wl["alpha"], R=wl["R"], seed=wl["seed"], topk=wl["topk"])
-    ctx.serve_start(G, streams=args.serve_streams, max_sources=smax, max_topk=wl["topk"], sampler=args.serve_sampler)
+    # the launch shape of the scale-24 workload of the same sampler
+    launch = WORKLOADS["rmat24plain" if args.serve_sampler == 0 else "rmat24alias"].get("launch", {})
+    ctx.serve_start(G, streams=args.serve_streams, max_sources=smax, max_topk=wl["topk"], sampler=args.serve_sampler,
+                    **launch)
 
     def run_stream(queries, rate):
         """Submit at Poisson times (rate queries/s; 0 = back to back), poll all."""
@@ -565,7 +570,7 @@ def run_serving(args):
             "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "u32", "data": "synthetic",
             "config": {"workload": "serve", "desc": wl["desc"], "alpha": wl["alpha"], "R": wl["R"], "topk": wl["topk"],
                        "n": g.n, "m": g.m, "streams": args.serve_streams,
-                       "sampler": "alias" if args.serve_sampler == 1 else "prefix",
+                       "sampler": "alias" if args.serve_sampler == 1 else "prefix", "launch": launch,
                        "steps_counted": "expected steps walks*2^32/T of the delivered walks",
                        "step": "one query (ms_per_step = mean latency)"},
             "p50_ms": main_r["p50_ms"], "p99_ms": main_r["p99_ms"], "walks_per_s": main_r["walks_per_s"],
@@ -734,6 +739,10 @@ def main():
     ap.add_argument("--warps-per-block", type=int, default=0)
     ap.add_argument("--chunk-sources", type=int, default=0)
     ap.add_argument("--large-degree", type=int, default=0)
+    ap.add_argument("--refill-lanes", type=int, default=0,
+                    help="persistent walker: idle lanes before a warp starts new walks (0 = 1)")
+    ap.add_argument("--tune", action="store_true",
+                    help="graph workloads: launch shape from the autotuner (cached) instead of the workload's")
     ap.add_argument("--l2-persist", type=int, default=0, choices=[0, 1],
                     help="walker launches keep the node records persisting in L2")
     ap.add_argument("--serve-queries", type=int, default=2000)
@@ -772,7 +781,7 @@ def main():
     g = I.workload_graph(base_graph(args.workload))
     a, b, rank_tag = rank_workload(g.n, rank, world)
     tune = dict(warps_per_block=args.warps_per_block, chunk_sources=args.chunk_sources,
-                large_degree=args.large_degree, l2_persist=args.l2_persist)
+                large_degree=args.large_degree, l2_persist=args.l2_persist, refill_lanes=args.refill_lanes)
 
     ctx = ppr.Context(local)
     stream = torch.cuda.current_stream(dev)
@@ -780,6 +789,22 @@ def main():
     d_col = torch.from_numpy(g.col).to(dev)
     d_w = torch.from_numpy(g.w.view(np.int32)).to(dev)
     flush = torch.empty(L2_FLUSH_BYTES // 4, dtype=torch.int32, device=dev)
+
+    # launch shape: the workload's (picked offline by the autotuner and the
+    # refill sweep), or the command line's, or the autotuner's now (--tune);
+    # tuning never changes results
+    tuning = None
+    if not any((args.warps_per_block, args.chunk_sources, args.large_degree, args.refill_lanes)):
+        tune.update(wl.get("launch", {}))
+    if args.tune:
+        from paper_1903_11749_gb300 import tune as tuner
+        Gt = ctx.load_graph(g.n, d_rp, d_col, d_w, stream=stream, m=g.m)
+        t0 = time.perf_counter()
+        tuning = tuner.tuned(Gt, torch.cuda.get_device_name(dev), sample_sources=400_000, alpha=wl["alpha"], R=wl["R"],
+                             seed=wl["seed"], topk=wl["topk"], segments=wl["segments"], sampler=wl.get("sampler", 0))
+        tuning = dict(tuning, seconds=time.perf_counter() - t0)
+        tune.update(tuner.launch_kwargs(tuning))
+        del Gt
 
     sample = np.arange(a, b, args.sample_every, dtype=np.int32) if args.sample_every > 0 else None
 
@@ -919,7 +944,7 @@ def main():
     kms = statistics.mean(kernel_ms)
     alg_bytes = sectors_per_pass * 32.0
     achieved = alg_bytes / (kms / 1e3) / 1e9
-    traffic = recorded_traffic(args.workload)
+    traffic = recorded_traffic(args.workload, tune)
     roofline = {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s", "frac": achieved / peak,
                 "traffic": traffic, "peak_kind": peak_kind, "kernel": "k_walk_persistent",
                 "alg_bytes_per_launch": alg_bytes, "kernel_ms": kms, "walk_and_reduce_ms": statistics.mean(run_ms),
@@ -956,7 +981,7 @@ def main():
                 "config": {"workload": args.workload, "desc": wl["desc"], "alpha": wl["alpha"], "R": wl["R"],
                            "topk": wl["topk"], "n": g.n, "m": g.m, "sources": g.n,
                            "parallelism": f"{world} independent replicas (tag = rank)" if world > 1 else "1 GPU",
-                           "l2": "flushed between steps (512 MB write)"},
+                           "l2": "flushed between steps (512 MB write)", "launch": tune, "tuning": tuning},
                 "step_ms_each": step_ms, "ms_per_step_median": statistics.median(step_ms), "walks_per_s": walks_s,
                 "steps_per_walk": steps_per_pass / max(walks_per_pass, 1),
                 "draws_per_s": draws_per_pass * args.steps * world / T_max,

@@ -199,6 +199,11 @@ typedef struct {
     int32_t l2_persist;  /* 1: walker launches mark the node records persisting in L2 (an
                             access-policy window; the device's persisting set-aside is raised
                             for this context on first use); 0: off.  Results are unchanged */
+    int32_t refill_lanes;/* persistent kernel: a warp starts new walks once at least this many of
+                            its 32 lanes are idle, and then fills every idle lane (1..32; 0 = 1,
+                            at once).  32 starts a warp's walks together, like one thread per
+                            walk, so the first steps of a source's walks share their loads.
+                            Results are unchanged */
     void *stream;        /* cudaStream_t, NULL = legacy default stream */
 } ppr_run_args;
 
@@ -249,6 +254,7 @@ typedef struct {
     float ms;                /* device time of the best candidate on the sample */
     int32_t candidates;      /* candidates timed */
     int64_t sample_sources;  /* sources in the sample */
+    int32_t refill_lanes;    /* idle lanes before a warp starts new walks (1..32) */
 } ppr_tuning;
 
 /*
@@ -256,8 +262,9 @@ typedef struct {
  * sample_sources, 0 = 65536; evenly strided for plain graphs, a leading range
  * for batched graphs) for each candidate of walkers per CTA (128, 256), queue
  * chunk (1/4x .. 4x of 400/R sources) and cooperative threshold (off, 4096,
- * 65536), and returns the fastest.  Synchronous; allocates scratch for the
- * sample.  Tuning never changes results.
+ * 65536), then, with the fastest of those, for refill thresholds of 8, 16,
+ * 24 and 32 idle lanes (against 1), and returns the fastest.  Synchronous;
+ * allocates scratch for the sample.  Tuning never changes results.
  */
 int ppr_autotune(ppr_ctx *ctx, const ppr_graph *g, const ppr_run_args *args, int64_t sample_sources, ppr_tuning *best);
 
@@ -396,6 +403,7 @@ typedef struct {
     int32_t chunk_sources, large_degree, warps_per_block; /* walker tuning (0 = defaults) */
     int32_t sampler;        /* neighbour choice of every query, as ppr_run_args.sampler; with 1
                                the graph's alias tables are built by ppr_serve_start */
+    int32_t refill_lanes;   /* as ppr_run_args.refill_lanes (0 = 1) */
 } ppr_serve_cfg;
 
 typedef struct {

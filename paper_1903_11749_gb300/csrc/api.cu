@@ -413,7 +413,7 @@ static int check_run(const ppr_graph *g, const ppr_run_args *a, int64_t count, b
         (a->kernel != PPR_KERNEL_PERSISTENT && a->kernel != PPR_KERNEL_PLAIN) || a->large_degree < 0 ||
         a->warps_per_block < 0 || a->warps_per_block > 32 || a->chunk_sources < 0 || a->max_batch_sources < 0 ||
         (a->stats != 0 && a->stats != 1) || (a->sampler != 0 && a->sampler != 1) ||
-        (a->l2_persist != 0 && a->l2_persist != 1)) {
+        (a->l2_persist != 0 && a->l2_persist != 1) || a->refill_lanes < 0 || a->refill_lanes > 32) {
         set_error("invalid mode or tuning argument");
         return PPR_EINVAL;
     }
@@ -444,6 +444,7 @@ static int check_run(const ppr_graph *g, const ppr_run_args *a, int64_t count, b
     plan->large_degree = a->large_degree;
     plan->warps_per_block = a->warps_per_block;
     plan->chunk_sources = a->chunk_sources;
+    plan->refill_lanes = a->refill_lanes;
     plan->stats = a->stats != 0;
     plan->sampler = a->sampler;
     plan->l2_persist = a->l2_persist == 1;
@@ -903,9 +904,44 @@ int ppr_autotune(ppr_ctx *ctx, const ppr_graph *g, const ppr_run_args *a, int64_
                     bt.chunk_sources = cs;
                     bt.large_degree = lg;
                     bt.warps_per_block = wpb;
+                    bt.refill_lanes = plan.refill_lanes > 0 ? plan.refill_lanes : 1;
                     bt.ms = ms_best;
                 }
             }
+    // refill thresholds with the fastest launch shape
+    const int rf_cands[] = {8, 16, 24, 32};
+    for (int rf : rf_cands) {
+        if (rc || bt.ms < 0) break;
+        RunPlan pl = plan;
+        pl.kernel = PPR_KERNEL_PERSISTENT;
+        pl.stats = false;
+        pl.chunk_sources = bt.chunk_sources;
+        pl.large_degree = bt.large_degree;
+        pl.warps_per_block = bt.warps_per_block;
+        pl.refill_lanes = rf;
+        float ms_best = 1e30f;
+        for (int rep = 0; rep < 2; ++rep) {
+            cudaMemsetAsync(o.counters, 0, 256, st);
+            cudaEventRecord(e0, st);
+            rc = launch_walks(ctx, g, pl, o, use_list ? 0 : a->src_begin, S, d_list, 0, ws, st, nullptr);
+            cudaEventRecord(e1, st);
+            if (rc) break;
+            e = cudaEventSynchronize(e1);
+            if (e != cudaSuccess) {
+                rc = cuda_fail(e, "autotune run");
+                break;
+            }
+            float ms = 0.f;
+            cudaEventElapsedTime(&ms, e0, e1);
+            if (rep > 0) ms_best = std::min(ms_best, ms);
+        }
+        if (rc) break;
+        ++tried;
+        if (ms_best < bt.ms) {
+            bt.refill_lanes = rf;
+            bt.ms = ms_best;
+        }
+    }
     cudaEventDestroy(e0);
     cudaEventDestroy(e1);
     cudaStreamSynchronize(st);

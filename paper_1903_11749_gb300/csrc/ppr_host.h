@@ -137,6 +137,7 @@ struct RunPlan {
     int32_t large_degree;
     int32_t warps_per_block;
     int32_t chunk_sources;
+    int32_t refill_lanes;  // persistent kernel: idle lanes before a warp refills (0 = 1)
     bool stats;
     int32_t sampler;  // 0 first-prefix-above rule, 1 integer alias method
     bool l2_persist;  // walker launches keep the node records in L2 (access-policy window)

@@ -225,7 +225,8 @@ int ppr_serve_start(ppr_ctx *ctx, const ppr_graph *g, const ppr_serve_cfg *cfg_i
     ppr_serve_cfg_init(&cfg);
     if (cfg_in) cfg = *cfg_in;
     if (cfg.streams < 1 || cfg.streams > 64 || cfg.max_sources < 1 || cfg.memory_budget < 0 || cfg.max_pending < 0 ||
-        cfg.max_topk < 0 || cfg.max_topk > (int32_t)PPR_MAX_R || (cfg.sampler != 0 && cfg.sampler != 1)) {
+        cfg.max_topk < 0 || cfg.max_topk > (int32_t)PPR_MAX_R || (cfg.sampler != 0 && cfg.sampler != 1) ||
+        cfg.refill_lanes < 0 || cfg.refill_lanes > 32) {
         set_error("invalid serving configuration");
         return PPR_EINVAL;
     }
@@ -336,6 +337,7 @@ int ppr_submit(ppr_ctx *ctx, const int32_t *srcs, int64_t ns, double alpha, uint
     q->plan.kernel = PPR_KERNEL_PERSISTENT;
     q->plan.large_degree = sv->cfg.large_degree;
     q->plan.warps_per_block = sv->cfg.warps_per_block;
+    q->plan.refill_lanes = sv->cfg.refill_lanes;
     q->plan.chunk_sources = sv->cfg.chunk_sources;
     q->plan.sampler = sv->cfg.sampler;
     q->plan.stats = false;

@@ -37,6 +37,7 @@ struct KParams {
     int64_t out_row0;         // output row of s_begin
     uint32_t CS;              // sources per chunk (batched graphs)
     uint32_t CW;              // walks per chunk (plain graphs; a chunk may start inside a source)
+    uint32_t refill;          // idle lanes before a warp starts new walks (1..32)
     uint64_t walks;           // S * R
     uint32_t nchunks;
     const unsigned long long *nchunks_dev;  // batched graphs: chunk count written on the device
@@ -325,6 +326,8 @@ __global__ void __launch_bounds__(256, PPR_WALK_MINB) k_walk_persistent(KParams 
 
     for (;;) {
         uint32_t idle = __ballot_sync(0xffffffffu, !active);
+        // refill once p.refill lanes are idle, then every idle lane
+        if ((uint32_t)__popc(idle) < p.refill) idle = 0;
         while (idle && !queue_empty) {
             if (wq.issued == wq.total) {
                 unsigned long long c = 0;
@@ -582,6 +585,7 @@ int launch_walks(ppr_ctx *ctx, const ppr_graph *g, const RunPlan &plan, const Ou
     while (P2 < plan.R) P2 <<= 1;
     kp.P2 = P2;
     kp.r_magic = ((1ull << 40) + plan.R - 1) / plan.R;
+    kp.refill = plan.refill_lanes > 0 ? (uint32_t)std::min(plan.refill_lanes, 32) : 1u;
     kp.n_nodes = g->n;
     kp.n_records = plan.sampler == 1 ? (uint64_t)g->m : (uint64_t)g->edge_records;
     kp.n_seg = (uint64_t)g->seg.entries_n;
@@ -760,6 +764,7 @@ extern "C" int ppr_run_noalloc(ppr_ctx *ctx, const ppr_graph *g, const ppr_run_a
     plan.large_degree = a->large_degree;
     plan.warps_per_block = a->warps_per_block;
     plan.chunk_sources = a->chunk_sources;
+    plan.refill_lanes = a->refill_lanes;
     plan.stats = false;
     plan.sampler = a->sampler;
     plan.l2_persist = false;  // no device-limit change from the allocation-free path

@@ -41,18 +41,20 @@ class RunArgs(C.Structure):
                 ("topk", C.c_int32), ("kernel", C.c_int32), ("large_degree", C.c_int32),
                 ("warps_per_block", C.c_int32), ("chunk_sources", C.c_int32), ("max_batch_sources", C.c_int64),
                 ("stats", C.c_int32), ("sampler", C.c_int32), ("l2_persist", C.c_int32),
-                ("stream", C.c_void_p)]
+                ("refill_lanes", C.c_int32), ("stream", C.c_void_p)]
 
 
 class Tuning(C.Structure):
     _fields_ = [("chunk_sources", C.c_int32), ("large_degree", C.c_int32), ("warps_per_block", C.c_int32),
-                ("ms", C.c_float), ("candidates", C.c_int32), ("sample_sources", C.c_int64)]
+                ("ms", C.c_float), ("candidates", C.c_int32), ("sample_sources", C.c_int64),
+                ("refill_lanes", C.c_int32)]
 
 
 class ServeCfg(C.Structure):
     _fields_ = [("streams", C.c_int32), ("max_sources", C.c_int64), ("max_topk", C.c_int32),
                 ("memory_budget", C.c_int64), ("max_pending", C.c_int64), ("chunk_sources", C.c_int32),
-                ("large_degree", C.c_int32), ("warps_per_block", C.c_int32), ("sampler", C.c_int32)]
+                ("large_degree", C.c_int32), ("warps_per_block", C.c_int32), ("sampler", C.c_int32),
+                ("refill_lanes", C.c_int32)]
 
 
 class QueryStats(C.Structure):
@@ -286,7 +288,7 @@ class Graph:
 
     def _args(self, alpha=0.15, R=100, seed=1, src_begin=0, src_end=None, tag=0, dangling=0, segments=False,
               topk=0, kernel=KERNEL_PERSISTENT, large_degree=0, warps_per_block=0, chunk_sources=0,
-              max_batch_sources=0, stats=False, stream=None, sampler=0, l2_persist=0):
+              max_batch_sources=0, stats=False, stream=None, sampler=0, l2_persist=0, refill_lanes=0):
         a = RunArgs()
         lib().ppr_run_args_init(C.byref(a))
         a.alpha, a.R, a.seed = alpha, R, seed
@@ -298,6 +300,7 @@ class Graph:
         a.stats = int(bool(stats))
         a.sampler = sampler
         a.l2_persist = l2_persist
+        a.refill_lanes = refill_lanes
         a.stream = _stream_ptr(stream)
         return a
 
@@ -317,8 +320,8 @@ class Graph:
         t = Tuning()
         _check(lib().ppr_autotune(self.ctx.h, self.h, C.byref(a), sample_sources, C.byref(t)))
         return {"chunk_sources": t.chunk_sources, "large_degree": t.large_degree,
-                "warps_per_block": t.warps_per_block, "ms": t.ms, "candidates": t.candidates,
-                "sample_sources": t.sample_sources}
+                "warps_per_block": t.warps_per_block, "refill_lanes": t.refill_lanes, "ms": t.ms,
+                "candidates": t.candidates, "sample_sources": t.sample_sources}
 
     def workspace_size(self, **kw) -> int:
         a = self._args(**kw)
@@ -353,7 +356,8 @@ class Graph:
 
     def run(self, alpha=0.15, R=100, seed=1, src_begin=0, src_end=None, tag=0, dangling=0, segments=False,
             topk=0, kernel=KERNEL_PERSISTENT, large_degree=0, warps_per_block=0, chunk_sources=0,
-            max_batch_sources=0, stats=False, stream=None, wait=True, sampler=0, l2_persist=0) -> "Result":
+            max_batch_sources=0, stats=False, stream=None, wait=True, sampler=0, l2_persist=0,
+            refill_lanes=0) -> "Result":
         a = RunArgs()
         lib().ppr_run_args_init(C.byref(a))
         a.alpha, a.R, a.seed = alpha, R, seed
@@ -365,6 +369,7 @@ class Graph:
         a.stats = int(bool(stats))
         a.sampler = sampler
         a.l2_persist = l2_persist
+        a.refill_lanes = refill_lanes
         a.stream = _stream_ptr(stream)
         h = C.c_void_p()
         _check(lib().ppr_run(self.ctx.h, self.h, C.byref(a), C.byref(h)))

@@ -45,4 +45,4 @@ def tuned(G, device_name: str, sample_sources: int = 0, refresh: bool = False, *
 
 def launch_kwargs(t: dict) -> dict:
     return {"chunk_sources": t["chunk_sources"], "large_degree": t["large_degree"],
-            "warps_per_block": t["warps_per_block"]}
+            "warps_per_block": t["warps_per_block"], "refill_lanes": t.get("refill_lanes", 0)}

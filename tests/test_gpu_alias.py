@@ -63,6 +63,9 @@ def test_alias_small_graphs(ppr, ctx, oracle, R, kernel):
         ref = ref_rows(oracle, g, 0.25, R, seed=9 + R, dangling=dangling, topk=min(R, 6), og=og)
         res = G.run(alpha=0.25, R=R, seed=9 + R, dangling=dangling, topk=min(R, 6), kernel=kernel, sampler=1)
         assert_same(res, ref, topk=min(R, 6))
+        if kernel == 0:  # lanes refilled in groups: the same walks
+            res = G.run(alpha=0.25, R=R, seed=9 + R, dangling=dangling, topk=min(R, 6), sampler=1, refill_lanes=20)
+            assert_same(res, ref, topk=min(R, 6))
 
 
 def test_alias_differs_from_prefix_but_same_rows_sum(ppr, ctx, oracle):

@@ -149,7 +149,8 @@ def test_batches_and_chunking_do_not_change_results(ppr, ctx, oracle):
     ref = oracle_rows(oracle, g, 0.15, 60, 7, topk=4)
     for kw in (dict(kernel=1, max_batch_sources=33), dict(chunk_sources=1), dict(chunk_sources=13, warps_per_block=2),
                dict(chunk_sources=64, warps_per_block=1), dict(max_batch_sources=250),
-               dict(chunk_sources=3, max_batch_sources=101)):
+               dict(chunk_sources=3, max_batch_sources=101), dict(refill_lanes=32), dict(refill_lanes=7, chunk_sources=3),
+               dict(refill_lanes=24, warps_per_block=4), dict(refill_lanes=16, chunk_sources=64)):
         assert_same(G.run(alpha=0.15, R=60, seed=7, topk=4, **kw), ref, topk=4)
 
 
@@ -294,6 +295,7 @@ def test_batched_instances_equal_each_instance_alone(ppr, ctx, oracle):
     G = ctx.load_graph_batch(inst.node_off, inst.row_ptr, inst.col, inst.w)
     for kernel in (0, 1):
         _check_instances(oracle, inst, G.run(alpha=0.15, R=40, seed=1, topk=4, kernel=kernel))
+    _check_instances(oracle, inst, G.run(alpha=0.15, R=40, seed=1, topk=4, refill_lanes=24))
     # a sub-range cutting through instances
     a, b = int(inst.node_off[3]) + 5, int(inst.node_off[7]) - 3
     res = G.run(alpha=0.15, R=40, seed=1, topk=4, src_begin=a, src_end=b, chunk_sources=2)

@@ -118,3 +118,20 @@ def test_alias_sampler_queries_equal_list_runs(env):
     for (idx, cnt), src in zip(got, qs):
         ridx, rcnt = G.run_list(src, sampler=1, **kw).topk()
         assert np.array_equal(idx, ridx) and np.array_equal(cnt, rcnt)
+
+
+def test_refilled_warps_serve_the_same_counts(env):
+    """A server whose warps start new walks 24 lanes at a time returns the
+    counts of plain list runs."""
+    ppr, g = env
+    ctx = ppr.Context(0)
+    G = ctx.load_graph(g.n, g.row_ptr, g.col, g.w)
+    ctx.serve_start(G, streams=2, refill_lanes=24)
+    qs = _queries(g.n, 5, seed=13, smax=900)
+    kw = dict(alpha=0.15, R=50, seed=12, topk=6)
+    ids = [ctx.submit(src, **kw) for src in qs]
+    got = [ctx.poll(q, len(src), kw["topk"], timeout_ms=60000)[:2] for q, src in zip(ids, qs)]
+    ctx.serve_stop()
+    for (idx, cnt), src in zip(got, qs):
+        ridx, rcnt = G.run_list(src, **kw).topk()
+        assert np.array_equal(idx, ridx) and np.array_equal(cnt, rcnt)

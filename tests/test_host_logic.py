@@ -23,8 +23,8 @@ class _FakeGraph:
 
     def autotune(self, sample_sources=0, **run):
         self.calls += 1
-        return {"chunk_sources": 4, "large_degree": 0, "warps_per_block": 8, "ms": 1.5, "candidates": 18,
-                "sample_sources": sample_sources}
+        return {"chunk_sources": 4, "large_degree": 0, "warps_per_block": 8, "refill_lanes": 16, "ms": 1.5,
+                "candidates": 33, "sample_sources": sample_sources}
 
 
 def test_tuning_cache_hits_and_keys(tmp_path, monkeypatch):
@@ -42,7 +42,9 @@ def test_tuning_cache_hits_and_keys(tmp_path, monkeypatch):
     assert len(json.load(open(tmp_path / "tune.json"))) == 4
     tune.tuned(G, "GB300", sample_sources=1000, refresh=True, **run)
     assert G.calls == 5
-    assert tune.launch_kwargs(t1) == {"chunk_sources": 4, "large_degree": 0, "warps_per_block": 8}
+    assert tune.launch_kwargs(t1) == {"chunk_sources": 4, "large_degree": 0, "warps_per_block": 8, "refill_lanes": 16}
+    # entries cached before the refill threshold existed default to refilling at once
+    assert tune.launch_kwargs({"chunk_sources": 2, "large_degree": 0, "warps_per_block": 4})["refill_lanes"] == 0
 
 
 def test_tuning_cache_survives_a_corrupt_file(tmp_path, monkeypatch):
