@@ -708,9 +708,9 @@ def run_sweep(args):
                 table.append(row)
         t = G.autotune(sample_sources=200_000, alpha=wl["alpha"], **base)
         pick = {"warps_per_block": t["warps_per_block"], "chunk_sources": t["chunk_sources"],
-                "large_degree": t["large_degree"], "autotuner": True}
+                "large_degree": t["large_degree"], "refill_lanes": t["refill_lanes"], "autotuner": True}
         pick.update(timed(alpha=wl["alpha"], warps_per_block=t["warps_per_block"], chunk_sources=t["chunk_sources"],
-                          large_degree=t["large_degree"], **base))
+                          large_degree=t["large_degree"], refill_lanes=t["refill_lanes"], **base))
         table.append(pick)
         best = max(table[:-1], key=lambda r: r["steps_per_s"])
         metric, value, unit = "autotuned / best grid point", pick["steps_per_s"] / best["steps_per_s"], "ratio"
