@@ -122,7 +122,7 @@ def test_chunglu2048_every_source_equals_threaded_oracle(oracle, sampler):
     inst = I.chung_lu_instances(2048, 100, 50_000, 12.0, 2.3, 1, 100, seed=4242)
     kw = dict(alpha=0.15, R=200, seed=1)
     G = ppr.Context(0).load_graph_batch(inst.node_off, inst.row_ptr, inst.col, inst.w)
-    res = G.run(topk=32, sampler=sampler, **kw)
+    res = G.run(topk=32, sampler=sampler, chunk_sources=8, refill_lanes=8, **kw)  # the tuner's launch shape
     rp, col, cnt = res.sparse_rows()
     idx, tc = res.topk()
     steps_gpu = res.info().steps
