@@ -1276,7 +1276,7 @@ struct AliasArgs {
     const NodeRecN *node;  // the narrow layout's records (begin, count, W)
     const EdgeN *edges;
     const uint64_t *off;  // first slot of each row (exclusive scan of degrees)
-    NodeRec *anode;
+    AliasNode *anode;
     AliasRec *slots;
     uint2 *ic;            // per slot of a long row: (edge, col) of the small edges from the front,
                           // of the large edges from the back
@@ -1300,7 +1300,7 @@ __device__ void alias_row_serial(const AliasArgs &A, const NodeRecN &nr, uint32_
     };
     for (uint32_t i = 0; i < d; ++i) {
         const int32_t c = A.edges[eb + i].col;
-        A.slots[o + i] = AliasRec{(uint32_t)W, c, c, 0u};
+        A.slots[o + i] = AliasRec{(uint32_t)W, c, c, (uint32_t)W};
     }
     auto next_small = [&](uint32_t i) { while (i < d && pw(i) >= W) ++i; return i; };
     auto next_large = [&](uint32_t j) { while (j < d && pw(j) <= W) ++j; return j; };
@@ -1336,10 +1336,8 @@ __global__ void __launch_bounds__(256) k_alias_small(AliasArgs A)
         const NodeRecN nr = A.node[u];
         const uint32_t d = row_degree(nr);
         const uint64_t o = A.off[u];
-        NodeRec r;
-        r.word0 = pack_word0(o, d, false);
-        r.total = d < 2 ? nr.total : (nr.total & 0xffffffffull);  // 0, the single target, or W
-        A.anode[u] = r;
+        // first slot and degree; a single-edge row keeps its target instead
+        A.anode[u] = AliasNode{pack_word0(d == 1 ? (nr.total & 0xffffffffull) : o, d, false)};
         if (d < 2) continue;
         if (d > kAliasInline) {
             if (d > kAliasHuge) {
@@ -1395,7 +1393,7 @@ __global__ void __launch_bounds__(32 * kSmemWarps) k_alias_serial(AliasArgs A)
                 p = (uint64_t)d * (rec.P - lo);
                 c = rec.col;
                 sm.col[i] = c;
-                A.slots[o + i] = AliasRec{(uint32_t)W, c, c, 0u};
+                A.slots[o + i] = AliasRec{(uint32_t)W, c, c, (uint32_t)W};
             }
             const bool isS = i < d && p < W, isL = i < d && p > W;
             const uint32_t bs = __ballot_sync(0xffffffffu, isS), bl = __ballot_sync(0xffffffffu, isL);
@@ -1582,7 +1580,7 @@ __device__ void alias_row_group(const AliasArgs &A, int64_t u, uint32_t rank, ui
                 const EdgeN rec = rv[q];
                 const uint64_t p = (uint64_t)d * (rec.P - prevP);
                 prevP = rec.P;
-                A.slots[o + i] = AliasRec{(uint32_t)W, rec.col, rec.col, 0u};
+                A.slots[o + i] = AliasRec{(uint32_t)W, rec.col, rec.col, (uint32_t)W};
                 if (p < W && ks < d) {
                     Dr += W - p;
                     A.ic[o + ks] = make_uint2(i, (uint32_t)rec.col);
@@ -1793,7 +1791,7 @@ __global__ void __launch_bounds__(256) k_alias_tile_write(TileArgs T)
         const EdgeN rec = A.edges[eb + i];
         const uint64_t p = (uint64_t)d * (rec.P - prevP);
         prevP = rec.P;
-        A.slots[o + i] = AliasRec{(uint32_t)W, rec.col, rec.col, 0u};
+        A.slots[o + i] = AliasRec{(uint32_t)W, rec.col, rec.col, (uint32_t)W};
         if (p < W && ks < d) {
             Dr += W - p;
             A.ic[o + ks] = make_uint2(i, (uint32_t)rec.col);
@@ -1930,7 +1928,7 @@ int build_alias(ppr_graph *g, cudaStream_t st)
         (rc = dev_alloc((void **)&counts, sizeof(uint32_t) * 4, "long-row counts", st)) ||
         (rc = dev_alloc((void **)&huge, sizeof(uint2) * kAliasMaxHuge, "tile-path rows", st)))
         return cleanup(), rc;
-    if ((rc = dev_alloc((void **)&g->alias.node, sizeof(NodeRec) * n, "alias node records", st))) return cleanup(), rc;
+    if ((rc = dev_alloc((void **)&g->alias.node, sizeof(AliasNode) * n, "alias node records", st))) return cleanup(), rc;
     if ((rc = dev_alloc((void **)&g->alias.slots, sizeof(AliasRec) * m, "alias slots", st))) return fail(rc);
     cudaError_t e = cudaMemsetAsync(counts, 0, sizeof(uint32_t) * 4, st);
     if (e != cudaSuccess) return fail(cuda_fail(e, "memset"));
@@ -1999,7 +1997,7 @@ int build_alias(ppr_graph *g, cudaStream_t st)
     if (e == cudaSuccess) e = cudaStreamSynchronize(st);
     if (e != cudaSuccess) return fail(cuda_fail(e, "alias build"));
     cleanup();
-    g->device_bytes += (int64_t)(sizeof(NodeRec) * n + sizeof(AliasRec) * m);
+    g->device_bytes += (int64_t)(sizeof(AliasNode) * n + sizeof(AliasRec) * m);
     return PPR_OK;
 }
 

@@ -37,7 +37,7 @@ int dev_alloc(void **p, size_t bytes, const char *what, cudaStream_t st);
 void dev_free(void *p, cudaStream_t st);
 
 struct AliasCache {
-    NodeRec *node = nullptr;   // node records pointing at alias slots
+    AliasNode *node = nullptr; // node records pointing at alias slots
     AliasRec *slots = nullptr; // one per edge
 };
 

@@ -65,13 +65,20 @@ struct __align__(16) EdgeW {
 };
 
 // Alias slot (integer Algorithm 1): edge j of the row is taken when the
-// draw's y < thr, else its alias; both targets are kept so that a step reads
-// one record.
+// draw's y < thr, else its alias; both targets and the row total W (the slot
+// capacity y is scaled to) are kept so that a step reads one record after
+// an 8-byte node record.
 struct __align__(16) AliasRec {
     uint32_t thr;
     int32_t col;
     int32_t alias_col;
-    uint32_t pad;
+    uint32_t W;
+};
+
+// Node record of the alias layout: first slot (bits 0..39) | degree (bits
+// 40..62); a single-edge row keeps its target in the slot field.
+struct __align__(8) AliasNode {
+    uint64_t word;
 };
 
 struct __align__(16) SegEntry {
@@ -222,10 +229,14 @@ struct WideEdges {
 
 // Alias layout: begin/count of a node record index its alias slots.
 struct AliasEdges {
-    using Node = NodeRec;
+    using Node = AliasNode;
     __device__ __forceinline__ static NodeRec load_node(const void *node, uint32_t u)
     {
-        return ppr::load_node(static_cast<const NodeRec *>(node), u);
+        const uint2 v = __ldg(reinterpret_cast<const uint2 *>(node) + u);
+        NodeRec r;
+        r.word0 = (uint64_t)v.x | ((uint64_t)v.y << 32);
+        r.total = 0;
+        return r;
     }
     const AliasRec *e;
     __host__ __device__ __forceinline__ static uint64_t edge_base(uint64_t begin, uint32_t) { return begin; }

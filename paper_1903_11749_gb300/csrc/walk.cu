@@ -132,12 +132,12 @@ __device__ __forceinline__ bool walk_step(const KParams &p, const E &edges, bool
             }
             next = src;
         } else if (cnt == 1) {
-            next = (uint32_t)total;
+            next = (uint32_t)beg;  // single out-edge: target kept in the record
         } else {
             const uint64_t j = __umul64hi(r64, (uint64_t)cnt);
             const uint64_t frac = r64 * (uint64_t)cnt;
-            const uint64_t y = mulhi64_by32((uint32_t)frac, (uint32_t)(frac >> 32), (uint32_t)total);
-            const uint4 rec = edges.load(beg + j);
+            const uint4 rec = edges.load(beg + j);  // {thr, col, alias col, W}
+            const uint64_t y = mulhi64_by32((uint32_t)frac, (uint32_t)(frac >> 32), rec.w);
             next = y < rec.x ? rec.y : rec.z;
             if (STATS) ++tl.sectors;
         }
