@@ -488,7 +488,8 @@ def test_invalid_inputs_are_rejected(ppr, ctx):
                      (dict(alpha=2.0**-40), ppr.PPR_EINVAL), (dict(R=0), ppr.PPR_EINVAL),
                      (dict(R=5000), ppr.PPR_ERANGE), (dict(src_begin=10, src_end=10), ppr.PPR_EINVAL),
                      (dict(src_end=51), ppr.PPR_EINVAL), (dict(topk=4097), ppr.PPR_EINVAL),
-                     (dict(dangling=2), ppr.PPR_EINVAL)):
+                     (dict(dangling=2), ppr.PPR_EINVAL), (dict(refill_lanes=33), ppr.PPR_EINVAL),
+                     (dict(refill_lanes=-1), ppr.PPR_EINVAL), (dict(warps_per_block=33), ppr.PPR_EINVAL)):
         with pytest.raises(E) as ei:
             G.run(**kw)
         assert ei.value.code == code, kw
