@@ -85,12 +85,17 @@ __global__ void k_compact_rows(int64_t S, uint32_t cap, const uint32_t *nnz, con
     }
 }
 
-// Row starts of one batch made absolute: off[i] += base.
-__global__ void k_add_base(int64_t n, uint64_t *off, uint64_t base)
+// Row starts of one batch made absolute: off[i] += *base, the entries of the
+// batches before it (kept on the device, so the batch needs no host round trip).
+__global__ void k_add_base(int64_t n, uint64_t *off, const unsigned long long *base)
 {
+    const uint64_t b = *base;
     for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x)
-        off[i] += base;
+        off[i] += b;
 }
+
+// The running base after a batch: its last absolute row start.
+__global__ void k_next_base(unsigned long long *base, const uint64_t *off_end) { *base = *off_end; }
 
 __global__ void k_dense(int64_t S, int64_t n, uint32_t cap, const uint32_t *nnz, const int32_t *cols,
                         const uint32_t *cnts, uint32_t *out)
@@ -207,6 +212,7 @@ int ppr_create(int device, ppr_ctx **out)
         cudaFuncGetAttributes(&fa, k_compact_rows);
         cudaFuncGetAttributes(&fa, k_dense);
         cudaFuncGetAttributes(&fa, k_add_base);
+        cudaFuncGetAttributes(&fa, k_next_base);
         cudaGetLastError();
     }
     cudaMemPool_t pool;
@@ -671,10 +677,12 @@ int ppr_run_to_host(ppr_ctx *ctx, const ppr_graph *g, const ppr_run_args *a, int
             (e = cudaEventCreateWithFlags(&q.copied, cudaEventDisableTiming)) != cudaSuccess)
             return finish(cuda_fail(e, "cudaEventCreate"));
     }
+    // counters: [0..4] as ppr_run's, [7] the running row base of the batches so far
     if ((rc = dev_alloc((void **)&r->d_steps, sizeof(unsigned long long) * 8, "counters", st))) return finish(rc);
     if ((rc = dev_alloc((void **)&ws, launch_workspace_bytes(g, plan, B), "walk workspace", st))) return finish(rc);
     if ((e = cudaMemsetAsync(r->d_steps, 0, sizeof(unsigned long long) * 8, st)) != cudaSuccess)
         return finish(cuda_fail(e, "memset"));
+    unsigned long long *d_base = r->d_steps + 7;
     const int cblocks = (int)std::min<int64_t>((B + 7) / 8, (int64_t)ctx->sms * 32);
     uint64_t base = 0;
     for (int64_t i = 0; i <= P; ++i) {
@@ -689,6 +697,13 @@ int ppr_run_to_host(ppr_ctx *ctx, const ppr_graph *g, const ppr_run_args *a, int
             exclusive_scan_u32(q.nnz, nb, q.off, q.tmp, st);
             k_compact_rows<<<std::max(1, cblocks), 256, 0, st>>>(nb, rcap, q.nnz, q.off, q.cols, q.cnts, q.ccol, q.ccnt);
             note_launch();
+            // row starts made absolute here, so the copy stream runs copies only:
+            // a kernel there would wait for SMs behind the next batch's walker
+            k_add_base<<<(int)std::min<int64_t>((nb + 256) / 256, (int64_t)ctx->sms * 8), 256, 0, st>>>(nb + 1, q.off,
+                                                                                                      d_base);
+            note_launch();
+            k_next_base<<<1, 1, 0, st>>>(d_base, q.off + nb);
+            note_launch();
             if ((e = cudaMemcpyAsync(&ctx->pinned[i & 1], q.off + nb, sizeof(uint64_t), cudaMemcpyDeviceToHost, st)) !=
                     cudaSuccess ||
                 (e = cudaEventRecord(q.ready, st)) != cudaSuccess)
@@ -699,15 +714,12 @@ int ppr_run_to_host(ppr_ctx *ctx, const ppr_graph *g, const ppr_run_args *a, int
             Slot &q = slot[j & 1];
             const int64_t b0 = j * B, nb = std::min<int64_t>(B, S - b0);
             if ((e = cudaEventSynchronize(q.ready)) != cudaSuccess) return finish(cuda_fail(e, "batch"));
-            const uint64_t tot = ctx->pinned[j & 1];
+            const uint64_t tot = ctx->pinned[j & 1] - base;  // the batch's last absolute row start, less the base
             if ((uint64_t)cap < base + tot) {
                 set_error("capacity %lld < nnz (at least %llu)", (long long)cap, (unsigned long long)(base + tot));
                 return finish(PPR_ERANGE);
             }
             const int64_t nrp = nb + (j == P - 1 ? 1 : 0);  // the last batch also writes row_ptr[S]
-            k_add_base<<<(int)std::min<int64_t>((nrp + 255) / 256, (int64_t)ctx->sms * 8), 256, 0, cs>>>(nrp, q.off,
-                                                                                                         base);
-            note_launch();
             e = cudaMemcpyAsync(row_ptr + b0, q.off, sizeof(int64_t) * nrp, cudaMemcpyDeviceToHost, cs);
             if (e == cudaSuccess && tot > 0)
                 e = cudaMemcpyAsync(col + base, q.ccol, sizeof(int32_t) * tot, cudaMemcpyDeviceToHost, cs);
