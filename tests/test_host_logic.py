@@ -75,3 +75,21 @@ def test_replica_workload_and_host_description():
     assert bench.rank_workload(1000, 3, 8) == (0, 1000, 3)  # every source, the rank as the tag
     h = bench.host_cpu()
     assert h["nproc"] >= 1 and h["model"] and h["machine"]
+
+
+def test_recorded_traffic_needs_the_same_kernel_and_launch(tmp_path, monkeypatch):
+    """The recorded DRAM traffic of a walker launch is reported only for the
+    kernel source and the launch shape it was captured with."""
+    prof = tmp_path / "profiles"
+    prof.mkdir()
+    entry = {"kernel_hash": bench.kernel_source_hash(), "launch": {"refill_lanes": 24},
+             "dram_bytes_per_launch": 123.0}
+    (prof / "walker_traffic.json").write_text(json.dumps({"w": entry, "old": dict(entry, kernel_hash="0" * 16)}))
+    h = bench.kernel_source_hash()
+    monkeypatch.setattr(bench, "ROOT", str(tmp_path))
+    monkeypatch.setattr(bench, "kernel_source_hash", lambda: h)
+    shape = {"warps_per_block": 0, "chunk_sources": 0, "large_degree": 0, "l2_persist": 0, "refill_lanes": 24}
+    assert bench.recorded_traffic("w", shape) == 123.0
+    assert bench.recorded_traffic("w", dict(shape, refill_lanes=0)) is None  # another launch shape
+    assert bench.recorded_traffic("old", shape) is None  # another kernel source
+    assert bench.recorded_traffic("missing", shape) is None
