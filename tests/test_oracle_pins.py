@@ -1,5 +1,5 @@
-"""Pins of the CPU oracle against things other than itself: a library routine
-(numpy's Philox), exact integer arithmetic, exact rational PPR, brute-force
+"""Pins of the CPU oracle against things other than itself: library routines
+(numpy's Philox4x64, cuRAND's host Philox4x32), exact integer arithmetic, exact rational PPR, brute-force
 path enumeration, FP64 power iteration, the paper's worked examples, and the
 invariants the paper states (Lemma 2, expected walk length 1/alpha)."""
 import math
@@ -49,6 +49,48 @@ def test_philox_weyl_constants_are_the_published_irrationals(oracle):
         out = fn(np.zeros(4, dtype=dt), np.zeros(2, dtype=dt), rounds=2)
         assert int(out[0]) == w0
         assert int(out[2]) == w1
+
+
+def _curand_host():
+    """The CUDA toolkit's host-side random number library (runs on the CPU), or None."""
+    import ctypes
+    import ctypes.util
+    cands = [ctypes.util.find_library("curand")]
+    for root in (os.environ.get("CUDA_HOME"), os.environ.get("CUDA_PATH"), "/usr/local/cuda"):
+        if root:
+            cands += [os.path.join(root, d, "libcurand.so") for d in ("lib64", "lib", "targets/sbsa-linux/lib")]
+    for c in cands:
+        if c:
+            try:
+                return ctypes.CDLL(c)
+            except OSError:
+                pass
+    return None
+
+
+def test_philox4x32_matches_curand_host_generator(oracle):
+    """cuRAND's host generator of type PHILOX4_32_10 (computed on the CPU) is
+    an independent Philox4x32-10: seeded with s, its i-th block of four words
+    is the block of counter (0, 0, i, 0) under key (s mod 2^32, s >> 32).
+    This pins the 4x32 instance itself -- its multipliers, key bumps and word
+    order -- over 4,096 blocks for each of four seeds."""
+    import ctypes
+    lib = _curand_host()
+    if lib is None:
+        pytest.skip("the CUDA random number library is not installed")
+    PHILOX4_32_10 = 161  # curandRngType_t
+    for seed in (0, 5, 0xDEADBEEF12345678, 2**64 - 1):
+        gen = ctypes.c_void_p()
+        assert lib.curandCreateGeneratorHost(ctypes.byref(gen), PHILOX4_32_10) == 0
+        try:
+            assert lib.curandSetPseudoRandomGeneratorSeed(gen, ctypes.c_ulonglong(seed)) == 0
+            ref = np.zeros(4 * 4096, dtype=np.uint32)
+            assert lib.curandGenerate(gen, ref.ctypes.data_as(ctypes.c_void_p), ctypes.c_size_t(ref.size)) == 0
+        finally:
+            lib.curandDestroyGenerator(gen)
+        key = [seed & 0xFFFFFFFF, seed >> 32]
+        got = np.stack([oracle.philox4x32([0, 0, i, 0], key) for i in range(4096)])
+        assert np.array_equal(got, ref.reshape(-1, 4)), hex(seed)
 
 
 def test_philox4x32_words_are_uniform(oracle):
