@@ -283,6 +283,12 @@ typedef struct {
     uint64_t sectors;      /* stats runs: 32-byte sectors the row searches read, node records
                               included (0 otherwise) */
     float run_ms;          /* device time of the whole run: walkers and reductions */
+    uint64_t model_sectors; /* stats runs: the same draws costed on a flat CSR searched by
+                               bisection, in 32-byte sectors without reuse: per draw at a node
+                               of out-degree d >= 1, one row_ptr sector, max(1, ceil(log2 d) - 1)
+                               prefix-probe sectors and one col sector; 1 at a dangling node;
+                               1 + (1 or 2) table sectors for a segment draw (<= 2 outcomes: 1);
+                               the alias sampler's node and slot sectors as counted (0 otherwise) */
 } ppr_result_info;
 
 int ppr_result_get_info(const ppr_result *r, ppr_result_info *info);
@@ -347,12 +353,18 @@ void ppr_free_result(ppr_result *r);
  *   topk_idx, topk_cnt  S * topk entries as ppr_topk, or NULL when topk = 0
  * S * R may be at most 16,777,152 walks (64 MiB minus a 256-byte header, 4 B
  * per walk); larger calls fail with PPR_ERANGE before any work is queued.
- * Plain graphs and args->kernel = PPR_KERNEL_PERSISTENT only; segment mode
- * needs tables already built for this alpha by an earlier ppr_run.
+ * Arguments are checked as ppr_run checks them (same limits, same codes),
+ * then: plain graphs and args->kernel = PPR_KERNEL_PERSISTENT only, no
+ * statistics; segment mode needs tables already built for this alpha, and
+ * the alias sampler tables already built, by an earlier ppr_run (else
+ * PPR_ENOTSUP: building them would allocate).
  * The work is queued on args->stream and the call returns at once: the
  * outputs are valid after that stream is synchronized.  The first call on a
  * device looks up the scratch array's device address (cudaGetSymbolAddress)
- * for that device; make that first call before any stream capture.  Every
+ * for that device; make that first call before any stream capture.  The
+ * address is kept per device ordinal for the life of the process, so it
+ * assumes the device's primary context is never reset (cudaDeviceReset, or
+ * a framework's equivalent) while the library is loaded.  Every
  * call shares the one scratch array, whose counters each call clears and
  * whose contents a later call overwrites: calls whose work overlaps on the
  * GPU (other streams, or without a synchronization between them) race.

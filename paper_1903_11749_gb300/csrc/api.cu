@@ -385,9 +385,12 @@ static void result_release(ppr_result *r)
     delete r;
 }
 
+}  // extern "C"
+
+namespace ppr {
 // Checks shared by every run entry point; count = number of sources (from the
 // range, or of an explicit list).  Fills *plan.
-static int check_run(const ppr_graph *g, const ppr_run_args *a, int64_t count, bool list, RunPlan *plan)
+int check_run(const ppr_graph *g, const ppr_run_args *a, int64_t count, bool list, RunPlan *plan)
 {
     const uint32_t T = ppr_alpha_threshold(a->alpha);
     if (T == 0) {
@@ -456,6 +459,9 @@ static int check_run(const ppr_graph *g, const ppr_run_args *a, int64_t count, b
     plan->l2_persist = a->l2_persist == 1;
     return PPR_OK;
 }
+}  // namespace ppr
+
+extern "C" {
 
 // Device tables a run needs beyond the base layout (built once per graph).
 static int prepare_tables(const ppr_graph *g, const RunPlan &plan, cudaStream_t st)
@@ -737,7 +743,7 @@ int ppr_run_to_host(ppr_ctx *ctx, const ppr_graph *g, const ppr_run_args *a, int
     if ((e = cudaStreamSynchronize(cs)) != cudaSuccess || (e = cudaStreamSynchronize(st)) != cudaSuccess)
         return finish(cuda_fail(e, "run"));
     if (nnz) *nnz = (int64_t)base;
-    unsigned long long c[5] = {0, 0, 0, 0, 0};
+    unsigned long long c[6] = {0, 0, 0, 0, 0, 0};
     if ((e = cudaMemcpy(c, r->d_steps, sizeof(c), cudaMemcpyDeviceToHost)) != cudaSuccess)
         return finish(cuda_fail(e, "counters"));
     if (c[4]) {  // only a checked build sets it
@@ -758,6 +764,7 @@ int ppr_run_to_host(ppr_ctx *ctx, const ppr_graph *g, const ppr_run_args *a, int
         info->kernel_ms = kms;
         info->sectors = c[2];
         info->run_ms = 0.f;
+        info->model_sectors = c[5];
     }
     return finish(PPR_OK);
 }
@@ -988,10 +995,11 @@ int ppr_wait(ppr_result *r, int64_t timeout_ms)
         }
         std::this_thread::sleep_for(std::chrono::microseconds(50));
     }
-    unsigned long long cnt[5] = {0, 0, 0, 0, 0};
+    unsigned long long cnt[6] = {0, 0, 0, 0, 0, 0};
     PPR_CUDA(cudaMemcpy(cnt, r->d_steps, sizeof(cnt), cudaMemcpyDeviceToHost));
     r->steps = cnt[0];
     r->sectors = cnt[2];
+    r->model_sectors = cnt[5];
     if (cnt[4]) {  // only a checked build sets it
         set_error("checked build: an index left its array (flags 0x%llx: 1 node, 2 edge row, 4 segment table, "
                   "8 endpoint)", cnt[4]);
@@ -1038,6 +1046,7 @@ int ppr_result_get_info(const ppr_result *r, ppr_result_info *info)
     info->kernel_ms = r->kernel_ms;
     info->run_ms = r->run_ms;
     info->sectors = r->sectors;
+    info->model_sectors = r->model_sectors;
     return PPR_OK;
 }
 

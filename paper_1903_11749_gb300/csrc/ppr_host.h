@@ -106,11 +106,12 @@ struct ppr_result {
     uint32_t *d_cnts = nullptr;
     int32_t *d_topk_idx = nullptr;
     uint32_t *d_topk_cnt = nullptr;
-    unsigned long long *d_steps = nullptr;  // counters: [0] steps, [1] work queue, [2] sectors, [3] chunks
+    unsigned long long *d_steps = nullptr;  // counters: [0] steps, [1] work queue, [2] sectors, [3] chunks,
+                                            // [4] checked-build flags, [5] flat-CSR model sectors
     cudaEvent_t ev_start = nullptr, ev_walk_end = nullptr, ev_done = nullptr;
     std::vector<cudaEvent_t> walk_events;  // (before, after) each walker launch
     bool waited = false;
-    uint64_t steps = 0, sectors = 0;
+    uint64_t steps = 0, sectors = 0, model_sectors = 0;
     float kernel_ms = 0.f;  // walker launches only
     float run_ms = 0.f;     // walkers, reductions and everything between
     int64_t nnz_total = -1;
@@ -157,6 +158,11 @@ struct Outputs {
     int32_t topk;
     unsigned long long *counters;
 };
+
+// Argument checks shared by every run entry point (api.cu); count = number of
+// sources of an explicit list (list = true), else the range is checked.
+// Fills *plan; returns a PPR_* status with the message set.
+int check_run(const ppr_graph *g, const ppr_run_args *a, int64_t count, bool list, RunPlan *plan);
 
 // Device workspace one launch of S sources needs (endpoints, chunk table).
 size_t launch_workspace_bytes(const ppr_graph *g, const RunPlan &p, int64_t S);

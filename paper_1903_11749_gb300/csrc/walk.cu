@@ -48,7 +48,7 @@ struct KParams {
     AggOut out;
     uint32_t *ends;           // S * R endpoints (instance-local ids)
     unsigned long long *queue;
-    unsigned long long *steps;    // [0] draws consumed, [2] algorithmic sectors (statistics launch)
+    unsigned long long *steps;    // [0] draws consumed, [2] layout sectors, [5] flat-CSR model sectors (statistics launch)
     uint32_t P2;              // next_pow2(R)
     uint64_t r_magic;         // ceil(2^40 / R): walk index -> source index by multiply-shift
     int64_t n_nodes;          // node records (for the L2 window and the checked build)
@@ -82,7 +82,19 @@ struct KParams {
 struct Tally {
     uint32_t steps = 0;
     uint32_t sectors = 0;
+    uint32_t model = 0;  // the same draws on a flat CSR searched by bisection (statistics launch)
 };
+
+// 32-byte sectors a draw at a node of out-degree d costs on a flat CSR
+// searched by bisection, without reuse: the row_ptr pair, max(1, ceil(log2 d) - 1)
+// sectors of prefix probes (the last few probes share a sector), the col
+// entry; a dangling node reads its row_ptr pair only.
+__device__ __forceinline__ uint32_t flat_model_sectors(uint32_t d)
+{
+    if (d == 0) return 1;
+    const uint32_t lg = d > 1 ? 32u - __clz(d - 1) : 0u;  // ceil(log2 d)
+    return 2u + max(1u, lg > 0 ? lg - 1 : 0u);
+}
 
 // STATS: count, per step, the 32-byte sectors a thread-serial bisection must
 // touch (node record + distinct probe sectors); rows are then searched by
@@ -123,7 +135,7 @@ __device__ __forceinline__ bool walk_step(const KParams &p, const E &edges, bool
         // integer alias method: slot j = floor(r*d / 2^64), y = floor(frac * W / 2^64)
         if (!act) return false;
         PPR_CHECK(cnt < 2 || beg + cnt <= p.n_records, 2);
-        if (STATS) ++tl.sectors;  // the node record
+        if (STATS) ++tl.sectors, ++tl.model;  // the node record
         uint32_t next;
         if (cnt == 0) {
             if (p.dangling == 1) {
@@ -139,7 +151,7 @@ __device__ __forceinline__ bool walk_step(const KParams &p, const E &edges, bool
             const uint4 rec = edges.load(beg + j);  // {thr, col, alias col, W}
             const uint64_t y = mulhi64_by32((uint32_t)frac, (uint32_t)(frac >> 32), rec.w);
             next = y < rec.x ? rec.y : rec.z;
-            if (STATS) ++tl.sectors;
+            if (STATS) ++tl.sectors, ++tl.model;
         }
         ++tl.steps;
         ++k;
@@ -173,7 +185,10 @@ __device__ __forceinline__ bool walk_step(const KParams &p, const E &edges, bool
         }
     }
     if (!act) return false;
-    if (STATS) ++tl.sectors;  // the node record
+    if (STATS) {
+        ++tl.sectors;  // the node record
+        tl.model += segf ? 1u + (cnt <= 2 ? 1u : 2u) : flat_model_sectors(cnt);
+    }
     PPR_CHECK(!segf || beg + cnt <= p.n_seg, 4);
     PPR_CHECK(segf || cnt < 2 ||
                   beg + (sizeof(typename E::Rec) == 8 ? (uint64_t)blocked_row_records(cnt) : (uint64_t)cnt) <= p.n_records,
@@ -246,7 +261,10 @@ template <bool STATS>
 __device__ __forceinline__ void warp_add_tally(unsigned long long *dst, const Tally &t)
 {
     warp_add(dst, t.steps);
-    if (STATS) warp_add(dst + 2, t.sectors);
+    if (STATS) {
+        warp_add(dst + 2, t.sectors);
+        warp_add(dst + 5, t.model);
+    }
 }
 
 // ------------------------------------------------------------ plain (K4) ----
@@ -695,26 +713,16 @@ extern "C" int ppr_run_noalloc(ppr_ctx *ctx, const ppr_graph *g, const ppr_run_a
         set_error("NULL argument");
         return PPR_EINVAL;
     }
-    const uint32_t T = ppr_alpha_threshold(a->alpha);
-    if (T == 0) {
-        set_error("alpha = %g: need 0 < alpha < 1 and floor(alpha * 2^32) >= 1", a->alpha);
+    // the checks every run entry point shares (ranges, modes, tuning limits)
+    RunPlan plan;
+    int rc = check_run(g, a, 0, false, &plan);
+    if (rc) return rc;
+    // and those of this entry point: one persistent launch into caller buffers
+    if (a->topk > 0 && (!topk_idx || !topk_cnt)) {
+        set_error("topk = %d needs the top-k outputs", a->topk);
         return PPR_EINVAL;
     }
-    if (a->R < 1 || a->R > PPR_MAX_R) {
-        set_error("R = %u outside [1, %u]", a->R, PPR_MAX_R);
-        return a->R < 1 ? PPR_EINVAL : PPR_ERANGE;
-    }
-    if (a->src_begin < 0 || a->src_end > g->n || a->src_begin >= a->src_end) {
-        set_error("source range [%lld, %lld) must be non-empty and inside [0, %lld)", (long long)a->src_begin,
-                  (long long)a->src_end, (long long)g->n);
-        return PPR_EINVAL;
-    }
-    if (a->topk < 0 || (uint32_t)a->topk > PPR_MAX_R || (a->topk > 0 && (!topk_idx || !topk_cnt))) {
-        set_error("topk = %d outside [0, %u], or top-k outputs missing", a->topk, PPR_MAX_R);
-        return PPR_EINVAL;
-    }
-    if ((a->dangling != 0 && a->dangling != 1) || (a->segments != 0 && a->segments != 1) || a->large_degree < 0 ||
-        a->chunk_sources < 0 || a->kernel != PPR_KERNEL_PERSISTENT || a->stats != 0) {
+    if (a->kernel != PPR_KERNEL_PERSISTENT || a->stats != 0) {
         set_error("invalid mode for the allocation-free run (persistent kernel, no statistics)");
         return PPR_EINVAL;
     }
@@ -722,12 +730,12 @@ extern "C" int ppr_run_noalloc(ppr_ctx *ctx, const ppr_graph *g, const ppr_run_a
         set_error("the allocation-free run takes plain graphs only");
         return PPR_ENOTSUP;
     }
-    if (a->segments && !(g->seg.T == T && g->seg.node)) {
+    if (plan.segments && !(g->seg.T == plan.T && g->seg.node)) {
         set_error("segment tables for this alpha are not built (a ppr_run with segments=1 builds them)");
         return PPR_ENOTSUP;
     }
-    if (a->sampler != 0 && (a->sampler != 1 || a->segments || !g->alias.node)) {
-        set_error("alias sampler: needs tables built by an earlier ppr_run with sampler=1, no segments");
+    if (plan.sampler == 1 && !g->alias.node) {
+        set_error("alias sampler: needs tables built by an earlier ppr_run with sampler=1");
         return PPR_ENOTSUP;
     }
     const uint32_t need_cap = (uint32_t)std::min<int64_t>((int64_t)a->R, g->n);
@@ -746,27 +754,13 @@ extern "C" int ppr_run_noalloc(ppr_ctx *ctx, const ppr_graph *g, const ppr_run_a
     cudaError_t e = cudaSetDevice(ctx->device);
     if (e != cudaSuccess) return cuda_fail(e, "cudaSetDevice");
     unsigned char *scratch = nullptr;
-    int rc = noalloc_scratch(ctx->device, &scratch);
+    rc = noalloc_scratch(ctx->device, &scratch);
     if (rc) return rc;
     cudaStream_t st = (cudaStream_t)a->stream;
     // the counters must start at zero on every call; endpoints are overwritten
     e = cudaMemsetAsync(scratch, 0, kNoAllocHeader, st);
     if (e != cudaSuccess) return cuda_fail(e, "cudaMemsetAsync(scratch header)");
 
-    RunPlan plan{};
-    plan.T = T;
-    plan.R = a->R;
-    plan.seed = a->seed;
-    plan.tag = a->tag;
-    plan.dangling = a->dangling;
-    plan.segments = a->segments != 0;
-    plan.kernel = PPR_KERNEL_PERSISTENT;
-    plan.large_degree = a->large_degree;
-    plan.warps_per_block = a->warps_per_block;
-    plan.chunk_sources = a->chunk_sources;
-    plan.refill_lanes = a->refill_lanes;
-    plan.stats = false;
-    plan.sampler = a->sampler;
     plan.l2_persist = false;  // no device-limit change from the allocation-free path
     Outputs out{nnz, cols, cnts, cap, topk_idx, topk_cnt, a->topk, reinterpret_cast<unsigned long long *>(scratch)};
     return launch_walks(ctx, g, plan, out, a->src_begin, a->src_end - a->src_begin, nullptr, 0,

@@ -65,7 +65,7 @@ class QueryStats(C.Structure):
 class ResultInfo(C.Structure):
     _fields_ = [("sources", C.c_int64), ("R", C.c_uint32), ("topk", C.c_int32), ("nnz", C.c_int64),
                 ("steps", C.c_uint64), ("walks", C.c_uint64), ("kernel_ms", C.c_float), ("sectors", C.c_uint64),
-                ("run_ms", C.c_float)]
+                ("run_ms", C.c_float), ("model_sectors", C.c_uint64)]
 
 
 # Every symbol include/ppr.h declares, with its ctypes signature.
@@ -378,17 +378,10 @@ class Graph:
             r.wait()
         return r
 
-    def run_noalloc(self, nnz, cols, cnts, cap, topk_idx=None, topk_cnt=None, alpha=0.15, R=100, seed=1,
-                    src_begin=0, src_end=None, tag=0, dangling=0, segments=False, topk=0, stream=None):
+    def run_noalloc(self, nnz, cols, cnts, cap, topk_idx=None, topk_cnt=None, **kw):
         """Allocation-free run into caller-owned device tensors (see ppr_run_noalloc in include/ppr.h);
-        returns once the work is queued on `stream`."""
-        a = RunArgs()
-        lib().ppr_run_args_init(C.byref(a))
-        a.alpha, a.R, a.seed = alpha, R, seed
-        a.src_begin = src_begin
-        a.src_end = self.info().n if src_end is None else src_end
-        a.tag, a.dangling, a.segments, a.topk = tag, dangling, int(bool(segments)), topk
-        a.stream = _stream_ptr(stream)
+        takes the arguments of run(); returns once the work is queued on `stream`."""
+        a = self._args(**kw)
         ti = _ptr(topk_idx)[0] if topk_idx is not None else None
         tc = _ptr(topk_cnt)[0] if topk_cnt is not None else None
         _check(lib().ppr_run_noalloc(self.ctx.h, self.h, C.byref(a), _ptr(nnz)[0], _ptr(cols)[0], _ptr(cnts)[0],

@@ -423,7 +423,7 @@ def _rows_from_fixed(nnz, cols, cnts, cap):
 
 @pytest.mark.parametrize("batched", [False, True])
 def test_run_into_and_cuda_graph_replay(ppr, ctx, oracle, batched):
-    """ppr_run_into (caller workspace, no allocation) gives ppr_run's rows,
+    """ppr_run_into (caller workspace, no allocation) gives the oracle's rows,
     also when recorded into a CUDA graph and replayed twice."""
     import torch
     dev = torch.device("cuda:0")
@@ -436,9 +436,17 @@ def test_run_into_and_cuda_graph_replay(ppr, ctx, oracle, batched):
         G = ctx.load_graph(g.n, g.row_ptr, g.col, g.w)
         n, cap = g.n, 64
     kw = dict(alpha=0.15, R=64, seed=9, topk=5, chunk_sources=3)
-    ref = G.run(**kw)
-    rp0, col0, cnt0 = ref.sparse_rows()
-    ti0, tc0 = ref.topk()
+    # expected rows from the oracle: batched instances walk alone with their id as tag
+    if batched:
+        parts = [oracle_rows(oracle, inst.instance(gi), 0.15, 64, 9, tag=gi, topk=5) for gi in range(inst.count)]
+        rp0 = np.concatenate([[0], np.cumsum(np.concatenate([np.diff(p["rows"][0]) for p in parts]))])
+        col0 = np.concatenate([p["rows"][1] for p in parts])
+        cnt0 = np.concatenate([p["rows"][2] for p in parts])
+        ti0 = np.concatenate([p["topk"][0] for p in parts])
+        tc0 = np.concatenate([p["topk"][1] for p in parts])
+    else:
+        ref = oracle_rows(oracle, g, 0.15, 64, 9, topk=5)
+        (rp0, col0, cnt0), (ti0, tc0) = ref["rows"], ref["topk"]
     ws = torch.zeros(G.workspace_size(**kw), dtype=torch.uint8, device=dev)
     nnz = torch.zeros(n, dtype=torch.int32, device=dev)
     cols = torch.zeros(n * cap, dtype=torch.int32, device=dev)

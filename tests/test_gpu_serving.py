@@ -1,8 +1,9 @@
 """Serving: multi-source queries admitted by continuous batching.
 
-Each query's top-k must be the same when it runs alone, when it runs in a
-mix of overlapping queries (tolerance 0: the counts are integers), and as a
-ppr_run_list of the same sources."""
+Each query's top-k must equal the CPU oracle's (walks from each listed
+source at tag 0, Sec. 2.1 estimator, top-k order of count then id) when it
+runs alone, when it runs in a mix of overlapping queries, and as a
+ppr_run_list of the same sources (tolerance 0: the counts are integers)."""
 import threading
 
 import numpy as np
@@ -22,23 +23,38 @@ def env():
     return ppr, g
 
 
+def _oracle_topk(oracle, g, alpha, R, seed, k, sampler=0):
+    """Top-k of every node as a source under the oracle; a query's answer is
+    the rows of its sources, in the order listed."""
+    og = oracle.prepare(g.n, g.row_ptr, g.col, g.w)
+    ends, _ = oracle.walks(og, alpha, R, seed, sampler=sampler)
+    rp, col, cnt = oracle.rows(ends, g.n)
+    return oracle.topk(rp, col, cnt, k)
+
+
+def _same_as_oracle(ref, src, idx, cnt):
+    return np.array_equal(idx, ref[0][src]) and np.array_equal(cnt, ref[1][src])
+
+
 def _queries(n, count, seed, smax=3000):
     rng = np.random.Generator(np.random.PCG64(seed))
     sizes = np.floor(np.exp(rng.uniform(0, np.log(smax), count))).astype(int)
     return [rng.choice(n, size=int(s), replace=False).astype(np.int32) for s in sizes]
 
 
-def test_alone_equals_mix_equals_run_list(env):
+def test_alone_equals_mix_equals_oracle(env, oracle):
     ppr, g = env
     ctx = ppr.Context(0)
     G = ctx.load_graph(g.n, g.row_ptr, g.col, g.w)
     qs = _queries(g.n, 24, seed=1)
     kw = dict(alpha=0.15, R=60, seed=7, topk=8)
+    ref = _oracle_topk(oracle, g, 0.15, 60, 7, 8)
     ctx.serve_start(G, streams=3)
     alone = []
     for src in qs:
         qid = ctx.submit(src, **kw)
         alone.append(ctx.poll(qid, len(src), kw["topk"], timeout_ms=60000)[:2])
+        assert _same_as_oracle(ref, src, *alone[-1])
     # the mix: two submitting threads, then poll everything
     ids = [None] * len(qs)
 
@@ -55,6 +71,7 @@ def test_alone_equals_mix_equals_run_list(env):
     for i, src in enumerate(qs):
         idx, cnt, st = ctx.poll(ids[i], len(src), kw["topk"], timeout_ms=60000)
         assert np.array_equal(idx, alone[i][0]) and np.array_equal(cnt, alone[i][1])
+        assert _same_as_oracle(ref, src, idx, cnt)
         stats.append(st)
     assert all(st["done_ns"] >= st["admit_ns"] >= st["submit_ns"] for st in stats)
     # several queries were in flight at once
@@ -67,7 +84,7 @@ def test_alone_equals_mix_equals_run_list(env):
         assert np.array_equal(ridx, alone[i][0]) and np.array_equal(rcnt, alone[i][1])
 
 
-def test_memory_admission_and_errors(env):
+def test_memory_admission_and_errors(env, oracle):
     ppr, g = env
     ctx = ppr.Context(0)
     G = ctx.load_graph(g.n, g.row_ptr, g.col, g.w)
@@ -77,11 +94,11 @@ def test_memory_admission_and_errors(env):
     ctx.serve_start(G, streams=4, memory_budget=3 << 20, max_sources=4000)
     qs = _queries(g.n, 10, seed=2, smax=3000)
     kw = dict(alpha=0.2, R=40, seed=3, topk=5)
+    ref = _oracle_topk(oracle, g, 0.2, 40, 3, 5)
     ids = [ctx.submit(s, **kw) for s in qs]
     res = [ctx.poll(q, len(s), 5, timeout_ms=60000) for q, s in zip(ids, qs)]
     for (idx, cnt, st), s in zip(res, qs):
-        ref = G.run_list(s, **kw)
-        assert np.array_equal(idx, ref.topk()[0]) and np.array_equal(cnt, ref.topk()[1])
+        assert _same_as_oracle(ref, s, idx, cnt)
     with pytest.raises(ppr.PPRError):
         ctx.submit(np.array([0, g.n], dtype=np.int32), **kw)  # source out of range
     with pytest.raises(ppr.PPRError):
@@ -105,7 +122,7 @@ def test_memory_admission_and_errors(env):
         ctx.poll(1, 1, 5, timeout_ms=10)
 
 
-def test_alias_sampler_queries_equal_list_runs(env):
+def test_alias_sampler_queries_equal_oracle(env, oracle):
     ppr, g = env
     ctx = ppr.Context(0)
     G = ctx.load_graph(g.n, g.row_ptr, g.col, g.w)
@@ -115,12 +132,14 @@ def test_alias_sampler_queries_equal_list_runs(env):
     ids = [ctx.submit(src, **kw) for src in qs]
     got = [ctx.poll(q, len(src), kw["topk"], timeout_ms=60000)[:2] for q, src in zip(ids, qs)]
     ctx.serve_stop()
+    ref = _oracle_topk(oracle, g, 0.15, 50, 11, 6, sampler=1)
     for (idx, cnt), src in zip(got, qs):
+        assert _same_as_oracle(ref, src, idx, cnt)
         ridx, rcnt = G.run_list(src, sampler=1, **kw).topk()
         assert np.array_equal(idx, ridx) and np.array_equal(cnt, rcnt)
 
 
-def test_refilled_warps_serve_the_same_counts(env):
+def test_refilled_warps_serve_the_same_counts(env, oracle):
     """A server whose warps start new walks 24 lanes at a time returns the
     counts of plain list runs."""
     ppr, g = env
@@ -132,6 +151,6 @@ def test_refilled_warps_serve_the_same_counts(env):
     ids = [ctx.submit(src, **kw) for src in qs]
     got = [ctx.poll(q, len(src), kw["topk"], timeout_ms=60000)[:2] for q, src in zip(ids, qs)]
     ctx.serve_stop()
+    ref = _oracle_topk(oracle, g, 0.15, 50, 12, 6)
     for (idx, cnt), src in zip(got, qs):
-        ridx, rcnt = G.run_list(src, **kw).topk()
-        assert np.array_equal(idx, ridx) and np.array_equal(cnt, rcnt)
+        assert _same_as_oracle(ref, src, idx, cnt)
