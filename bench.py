@@ -7,9 +7,18 @@ endpoints into sparse count rows and top-k.  The metric is walk steps per
 second (draws consumed); walks per second and the roofline of the walker
 kernel are reported beside it.
 
-Default workload: R-MAT scale 20 (1,048,576 nodes, 16.8M edges plus the
-dangling repair), Zipf(1.5) weights in [1, 1000], ~5 % dangling nodes,
-alpha = 0.2, R = 100, top-32 per source, Philox seed 1.
+Default workload: R-MAT scale 24 (16,777,216 nodes, 277M edges with the
+dangling repair and a planted hub of 1.57M out-edges), Zipf(1.5) weights in
+[1, 1000], ~5 % dangling nodes, alpha = 0.15, R = 50, depth-3 segment tables
+for out-degree <= 8, top-64 per source, Philox seed 1: the largest
+single-GPU graph workload.  rmat20 (scale 20, alpha 0.2, R 100, top-32),
+er1k, the 2048-instance batched workload and serving are the other lines.
+
+Roofline of the walker: `frac` = DRAM bytes per launch (ncu, read + write,
+per draw on a block-sampled capture of the same kernel source and launch
+shape, times this launch's draws) / walker CUDA-event time / measured copy
+peak.  Beside it, the 32-byte sectors the layout's searches read (counted
+by a statistics launch) and the flat-CSR bisection model of the same draws.
 
 --impl reference times the CPU oracle (single-threaded C) on a bounded sample
 of the same workload and prints the same line with "impl": "reference".
@@ -37,10 +46,10 @@ WORKLOADS = {
                    desc="R-MAT scale 20, 16.8M edges (a=.57 b=.19 c=.19), Zipf(1.5) w in [1,1000], 5% dangling"),
     "er1k": dict(alpha=0.15, R=1000, seed=1, topk=32, segments=False,
                  desc="Erdos-Renyi n=1000 m=10000, w U[1,10], dense n x n counts"),
-    "rmat24": dict(alpha=0.15, R=50, seed=1, topk=64, segments=True, launch=dict(refill_lanes=24),
+    "rmat24": dict(alpha=0.15, R=50, seed=1, topk=64, segments=True, launch=dict(refill_lanes=24, step_loads=5),
                    desc="R-MAT scale 24, 268M edges + hub > 1e6, Zipf(1.5) w in [1,1000], 5% dangling, "
                         "depth-3 segments for out-degree <= 8"),
-    "rmat24plain": dict(alpha=0.15, R=50, seed=1, topk=64, segments=False, launch=dict(refill_lanes=24),
+    "rmat24plain": dict(alpha=0.15, R=50, seed=1, topk=64, segments=False, launch=dict(refill_lanes=24, step_loads=5),
                         desc="R-MAT scale 24 as rmat24, plain steps only"),
     "rmat20alias": dict(alpha=0.2, R=100, seed=1, topk=32, segments=False, sampler=1,
                         desc="R-MAT scale 20 as rmat20, integer alias sampler (Algorithm 1 tables built every step)"),
@@ -156,15 +165,17 @@ def measured_peaks():
 
 
 def kernel_source_hash():
+    """Hash of the walker's source files (the launch, the step, the layout)."""
     h = hashlib.sha256()
-    for f in ("walk.cu", "ppr_internal.cuh"):
+    for f in ("walk.cu", "walk_step.cuh", "ppr_internal.cuh"):
         h.update(open(os.path.join(ROOT, "paper_1903_11749_gb300", "csrc", f), "rb").read())
     return h.hexdigest()[:16]
 
 
 def recorded_traffic(workload: str, launch: dict):
-    """DRAM bytes per walker launch from the committed ncu summary, if it was
-    taken on the current kernel source with the same launch shape; else None."""
+    """The committed ncu DRAM figure of the walker (bytes per draw, read +
+    write) for this workload, if it was taken on the current kernel source
+    with the same launch shape; else None."""
     p = os.path.join(ROOT, "profiles", "walker_traffic.json")
     if not os.path.exists(p):
         return None
@@ -174,7 +185,48 @@ def recorded_traffic(workload: str, launch: dict):
         return None
     if e.get("launch", {}) != {k: v for k, v in launch.items() if v}:
         return None
-    return e.get("dram_bytes_per_launch")
+    return e
+
+
+def sample_sources(n: int, every: int, block: int):
+    """Profiling case: one block of `block` consecutive sources in every
+    `every` blocks (block 1: every `every`-th source)."""
+    if block <= 1:
+        return np.arange(0, n, every, dtype=np.int32)
+    starts = np.arange(0, n, block * every, dtype=np.int64)
+    return np.concatenate([np.arange(s, min(n, s + block), dtype=np.int32) for s in starts])
+
+
+def walker_roofline(workload, launch, sampled, draws, sectors, model_sectors, kernel_ms, peak, peak_kind):
+    """Roofline of the walker launch.  frac is DRAM-based: the ncu DRAM
+    bytes per draw recorded for this kernel source and launch shape, times
+    the launch's draws, over the walker's CUDA-event time.  Without a current
+    ncu record the counted layout sectors stand in and `basis` says so."""
+    s = kernel_ms / 1e3
+    counted = sectors * 32.0
+    model = model_sectors * 32.0
+    rec = None if sampled else recorded_traffic(workload, launch)
+    if rec is not None:
+        traffic = rec["dram_bytes_per_draw"] * draws
+        achieved, basis = traffic / s / 1e9, "ncu DRAM bytes (read + write) per draw x draws / walker time"
+    else:
+        traffic = None
+        achieved, basis = counted / s / 1e9, "counted layout sectors / walker time (no current ncu DRAM record)"
+    out = {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s", "frac": achieved / peak,
+           "traffic": traffic, "basis": basis, "peak_kind": peak_kind, "kernel": "k_walk_persistent",
+           "kernel_ms": kernel_ms, "draws": draws,
+           "counted_sector_frac": counted / s / 1e9 / peak,
+           "counted": {"bytes_per_launch": counted, "sectors_per_draw": sectors / max(draws, 1),
+                       "model": "32-byte sectors the walker's own layout reads per draw: node record, one per "
+                                "search-tree level below the record, 1-2 sectors of the bottom block (alias: "
+                                "node record + slot), counted by a statistics launch"},
+           "flat_csr_model": {"bytes_per_launch": model, "sectors_per_draw": model_sectors / max(draws, 1),
+                              "frac": model / s / 1e9 / peak,
+                              "model": "the same draws on a flat CSR searched by bisection without reuse: row_ptr "
+                                       "sector + max(1, ceil(log2 d) - 1) probe sectors + col sector per draw"}}
+    if rec is not None:
+        out["traffic_record"] = {k: rec[k] for k in ("case", "dram_bytes_per_draw", "summary") if k in rec}
+    return out
 
 
 def host_cpu():
@@ -353,6 +405,7 @@ def run_batched(args):
     r = G.run(stats=True, **run_kw, **lk)
     info = r.info()
     draws, sectors, walks = int(info.steps), int(info.sectors), int(info.walks)
+    model_sectors = int(info.model_sectors)
     del r
     # walker-only time (for the roofline) from an eager run
     kms = []
@@ -412,7 +465,7 @@ def run_batched(args):
     per_inst_wall = time.perf_counter() - t0
     peak, peak_kind = measured_peaks()
     kms_ = statistics.mean(kms)
-    achieved = sectors * 32.0 / (kms_ / 1e3) / 1e9
+    roofline = walker_roofline(args.workload, lk, False, draws, sectors, model_sectors, kms_, peak, peak_kind)
     # end to end: host CSR in (pinned), one run, rows + top-k out (pinned)
     e2e = None
     if not args.no_e2e:
@@ -466,10 +519,7 @@ def run_batched(args):
                            "step": "one CUDA-graph replay: chunk table, fused persistent walker, reduction",
                            "tuning": tun, "tune_seconds": tune_s},
                 "walks_per_s": units[1] / T_max, "steps_per_walk": draws / max(walks, 1),
-                "roofline": {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s", "frac": achieved / peak,
-                             "traffic": None, "peak_kind": peak_kind, "kernel": "k_walk_persistent",
-                             "alg_bytes_per_launch": sectors * 32.0, "kernel_ms": kms_,
-                             "sectors_per_draw": sectors / max(draws, 1)},
+                "roofline": roofline,
                 "plain_kernel": {"value": draws / (plain_ms / 1e3), "unit": "walk steps/s", "ms_per_step": plain_ms,
                                  "kernel": "one thread per walk over all instances + reduction"},
                 "unfused_per_instance": {"value": draws / (per_inst_ms / 1e3), "unit": "walk steps/s",
@@ -511,8 +561,7 @@ def run_serving(args):
     kw = dict(alpha=wl["alpha"], R=wl["R"], seed=wl["seed"], topk=wl["topk"])
     # the launch shape of the scale-24 workload of the same sampler
     launch = WORKLOADS["rmat24plain" if args.serve_sampler == 0 else "rmat24alias"].get("launch", {})
-    ctx.serve_start(G, streams=args.serve_streams, max_sources=smax, max_topk=wl["topk"], sampler=args.serve_sampler,
-                    **launch)
+    launch = {k: v for k, v in launch.items() if k in ("refill_lanes", "chunk_sources")}
 
     def run_stream(queries, rate):
         """Submit at Poisson times (rate queries/s; 0 = back to back), poll all."""
@@ -539,43 +588,67 @@ def run_serving(args):
         th.join()
         return stats
 
-    warm = make_queries(n_warm)
-    st = run_stream(warm, 0)  # back to back: the service capacity
-    t0 = min(x["submit_ns"] for x in st)
-    t1 = max(x["done_ns"] for x in st)
-    cap_walks = sum(x["walks"] for x in st) / ((t1 - t0) / 1e9)
-    mean_walks = np.mean([len(q) for q in warm]) * wl["R"]
-    results = {}
-    clocks = Clocks(local, None)
-    clocks.start()
-    launches0 = ppr.kernel_launches()
-    for rho in args.serve_rho:
-        qs = make_queries(n_meas)
-        rate = rho * cap_walks / (((smax - 1) / np.log(smax)) * wl["R"])
-        st = run_stream(qs, rate)
-        lat = np.array([(x["done_ns"] - x["submit_ns"]) / 1e6 for x in st])
+    def measure(mode):
+        """Capacity (queries back to back), then a Poisson stream at each rho."""
+        ctx.serve_start(G, streams=args.serve_streams, max_sources=smax, max_topk=wl["topk"],
+                        sampler=args.serve_sampler, mode=mode, **launch)
+        warm = make_queries(n_warm)
+        st = run_stream(warm, 0)  # back to back: the service capacity
         t0 = min(x["submit_ns"] for x in st)
         t1 = max(x["done_ns"] for x in st)
-        walks = sum(x["walks"] for x in st)
-        results[str(rho)] = {"queries": len(qs), "rate_qps": rate, "p50_ms": float(np.percentile(lat, 50)),
-                             "p99_ms": float(np.percentile(lat, 99)), "mean_ms": float(lat.mean()),
-                             "walks_per_s": walks / ((t1 - t0) / 1e9), "seconds": (t1 - t0) / 1e9}
-    clk = clocks.stop()
-    launches = ppr.kernel_launches() - launches0  # every measured stream (all rho)
-    ctx.serve_stop()
+        cap_walks = sum(x["walks"] for x in st) / ((t1 - t0) / 1e9)
+        results = {}
+        clocks = Clocks(local, None)
+        clocks.start()
+        launches0 = ppr.kernel_launches()
+        for rho in args.serve_rho:
+            qs = make_queries(n_meas)
+            rate = rho * cap_walks / (((smax - 1) / np.log(smax)) * wl["R"])
+            st = run_stream(qs, rate)
+            lat = np.array([(x["done_ns"] - x["submit_ns"]) / 1e6 for x in st])
+            t0 = min(x["submit_ns"] for x in st)
+            t1 = max(x["done_ns"] for x in st)
+            walks = sum(x["walks"] for x in st)
+            small = np.array([x["sources"] <= 100 for x in st])
+            results[str(rho)] = {"queries": len(qs), "rate_qps": rate, "p50_ms": float(np.percentile(lat, 50)),
+                                 "p99_ms": float(np.percentile(lat, 99)), "mean_ms": float(lat.mean()),
+                                 "p99_ms_small_queries": float(np.percentile(lat[small], 99)) if small.any() else None,
+                                 "walks_per_s": walks / ((t1 - t0) / 1e9), "seconds": (t1 - t0) / 1e9}
+        clk = clocks.stop()
+        launches = ppr.kernel_launches() - launches0  # every measured stream (all rho)
+        info = ctx.serve_info()
+        ctx.serve_stop()
+        return {"capacity_walks_per_s": cap_walks, "by_rho": results, "clocks": clk, "gpu_launches": launches,
+                "loop_launches": info["launches"] if mode == ppr.SERVE_DEVICE_LOOP else None,
+                "loop_activity": ({k: info[k] for k in ("draws", "iterations", "claims", "claim_misses", "sleeps",
+                                                         "reduced", "idle_exits", "cycles_claim", "cycles_step",
+                                                         "cycles_sleep", "cycles_total", "grid_blocks")}
+                                  if mode == ppr.SERVE_DEVICE_LOOP else None)}
+
+    mode = ppr.SERVE_STREAMS if args.serve_mode == "streams" else ppr.SERVE_DEVICE_LOOP
+    res = measure(mode)
+    other = None
+    if args.serve_compare:
+        other = measure(ppr.SERVE_DEVICE_LOOP if mode == ppr.SERVE_STREAMS else ppr.SERVE_STREAMS)
     T = ppr.alpha_threshold(wl["alpha"])
-    main_r = results[str(args.serve_rho[0])]
+    main_r = res["by_rho"][str(args.serve_rho[0])]
+    mean_walks = (((smax - 1) / np.log(smax))) * wl["R"]
     line = {"metric": "walk steps/s", "value": main_r["walks_per_s"] * (2.0 ** 32 / T), "unit": "walk steps/s",
             "n_gpus": 1, "steps": n_meas, "warmup": n_warm, "ms_per_step": main_r["mean_ms"],
             "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "u32", "data": "synthetic",
             "config": {"workload": "serve", "desc": wl["desc"], "alpha": wl["alpha"], "R": wl["R"], "topk": wl["topk"],
-                       "n": g.n, "m": g.m, "streams": args.serve_streams,
+                       "n": g.n, "m": g.m, "mode": args.serve_mode,
+                       "streams": args.serve_streams if mode == ppr.SERVE_STREAMS else None,
                        "sampler": "alias" if args.serve_sampler == 1 else "prefix", "launch": launch,
                        "steps_counted": "expected steps walks*2^32/T of the delivered walks",
-                       "step": "one query (ms_per_step = mean latency)"},
+                       "step": "one query (ms_per_step = mean latency, submit to completion)"},
             "p50_ms": main_r["p50_ms"], "p99_ms": main_r["p99_ms"], "walks_per_s": main_r["walks_per_s"],
-            "capacity_walks_per_s": cap_walks, "mean_walks_per_query": mean_walks, "by_rho": results,
-            "clocks": clk, "gpu_launches": launches}
+            "capacity_walks_per_s": res["capacity_walks_per_s"], "mean_walks_per_query": mean_walks,
+            "by_rho": res["by_rho"], "loop_launches": res["loop_launches"], "loop_activity": res["loop_activity"],
+            "other_mode": ({"mode": "streams" if mode == ppr.SERVE_DEVICE_LOOP else "device_loop",
+                            "capacity_walks_per_s": other["capacity_walks_per_s"], "by_rho": other["by_rho"]}
+                           if other else None),
+            "clocks": res["clocks"], "gpu_launches": res["gpu_launches"]}
     print(json.dumps(line))
     return 0
 
@@ -730,7 +803,7 @@ def main():
     ap.add_argument("--steps", type=int, default=5)
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", default="gb300", choices=["gb300", "reference"])
-    ap.add_argument("--workload", default="rmat20", choices=sorted(WORKLOADS))
+    ap.add_argument("--workload", default="rmat24", choices=sorted(WORKLOADS))
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--no-plain", action="store_true")
@@ -741,6 +814,9 @@ def main():
     ap.add_argument("--large-degree", type=int, default=0)
     ap.add_argument("--refill-lanes", type=int, default=0,
                     help="persistent walker: idle lanes before a warp starts new walks (0 = 1)")
+    ap.add_argument("--step-loads", type=int, default=0,
+                    help="persistent walker: dependent loads per lane per warp iteration (0 = library default, -1 = "
+                         "no bound)")
     ap.add_argument("--tune", action="store_true",
                     help="graph workloads: launch shape from the autotuner (cached) instead of the workload's")
     ap.add_argument("--l2-persist", type=int, default=0, choices=[0, 1],
@@ -751,8 +827,14 @@ def main():
     ap.add_argument("--serve-rho", type=float, nargs="+", default=[0.5, 0.8])
     ap.add_argument("--serve-sampler", type=int, default=0, choices=[0, 1],
                     help="neighbour choice of the served queries (1: integer alias tables)")
+    ap.add_argument("--serve-mode", default="device_loop", choices=["device_loop", "streams"],
+                    help="serving: the resident device loop, or one launch per query on a few streams")
+    ap.add_argument("--serve-compare", action="store_true",
+                    help="serving: also measure the other mode on the same queries' distribution")
     ap.add_argument("--sample-every", type=int, default=0,
-                    help="profiling case: walk only every k-th source (an explicit source list)")
+                    help="profiling case: walk only one source (or block of sources) in every k (an explicit list)")
+    ap.add_argument("--sample-block", type=int, default=1,
+                    help="profiling case: consecutive sources per sampled block")
     args = ap.parse_args()
     if args.impl == "reference":
         return run_reference(args)
@@ -781,7 +863,8 @@ def main():
     g = I.workload_graph(base_graph(args.workload))
     a, b, rank_tag = rank_workload(g.n, rank, world)
     tune = dict(warps_per_block=args.warps_per_block, chunk_sources=args.chunk_sources,
-                large_degree=args.large_degree, l2_persist=args.l2_persist, refill_lanes=args.refill_lanes)
+                large_degree=args.large_degree, l2_persist=args.l2_persist, refill_lanes=args.refill_lanes,
+                step_loads=args.step_loads)
 
     ctx = ppr.Context(local)
     stream = torch.cuda.current_stream(dev)
@@ -794,7 +877,7 @@ def main():
     # refill sweep), or the command line's, or the autotuner's now (--tune);
     # tuning never changes results
     tuning = None
-    if not any((args.warps_per_block, args.chunk_sources, args.large_degree, args.refill_lanes)):
+    if not any((args.warps_per_block, args.chunk_sources, args.large_degree, args.refill_lanes, args.step_loads)):
         tune.update(wl.get("launch", {}))
     if args.tune:
         from paper_1903_11749_gb300 import tune as tuner
@@ -806,7 +889,7 @@ def main():
         tune.update(tuner.launch_kwargs(tuning))
         del Gt
 
-    sample = np.arange(a, b, args.sample_every, dtype=np.int32) if args.sample_every > 0 else None
+    sample = sample_sources(b, args.sample_every, args.sample_block) if args.sample_every > 0 else None
 
     def step(kernel=ppr.KERNEL_PERSISTENT, stats=False):
         G = ctx.load_graph(g.n, d_rp, d_col, d_w, stream=stream, m=g.m)
@@ -824,6 +907,7 @@ def main():
     r0.wait()
     info0 = r0.info()
     draws_per_pass, sectors_per_pass, walks_per_pass = int(info0.steps), int(info0.sectors), int(info0.walks)
+    model_per_pass = int(info0.model_sectors)
     # walk steps of one pass: the counted steps; with segment tables one draw
     # stands for up to three steps, so the plain-equivalent count walks * 2^32/T
     # (the expected number of steps) is used instead
@@ -942,13 +1026,9 @@ def main():
 
     peak, peak_kind = measured_peaks()
     kms = statistics.mean(kernel_ms)
-    alg_bytes = sectors_per_pass * 32.0
-    achieved = alg_bytes / (kms / 1e3) / 1e9
-    traffic = recorded_traffic(args.workload, tune)
-    roofline = {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s", "frac": achieved / peak,
-                "traffic": traffic, "peak_kind": peak_kind, "kernel": "k_walk_persistent",
-                "alg_bytes_per_launch": alg_bytes, "kernel_ms": kms, "walk_and_reduce_ms": statistics.mean(run_ms),
-                "sectors_per_draw": sectors_per_pass / max(draws_per_pass, 1)}
+    roofline = walker_roofline(args.workload, tune, sample is not None, draws_per_pass, sectors_per_pass,
+                               model_per_pass, kms, peak, peak_kind)
+    roofline["walk_and_reduce_ms"] = statistics.mean(run_ms)
 
     # practical ceilings: dependent random 32-byte sector reads over a buffer
     # the size of the walked layout, and Philox draws with no memory traffic

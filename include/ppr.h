@@ -205,6 +205,13 @@ typedef struct {
                             walk, so the first steps of a source's walks share their loads.
                             Results are unchanged */
     void *stream;        /* cudaStream_t, NULL = legacy default stream */
+    int32_t step_loads;  /* persistent kernel, prefix sampler on 32-bit rows, no cooperative
+                            search, no statistics: the dependent loads one lane may spend on a
+                            draw in one warp iteration (the node record counts as one); a
+                            deeper search resumes in the next iteration while the warp's other
+                            lanes start new draws.  0 = the library's choice (6); -1 = none
+                            (each iteration finishes every lane's draw); 2..16.  Results are
+                            unchanged */
 } ppr_run_args;
 
 /* Fills *args with defaults (alpha 0.15, R 100, seed 1, all sources of
@@ -406,25 +413,87 @@ int ppr_probe_rate(ppr_ctx *ctx, int32_t kind, int64_t bytes, double *per_second
  * the top-k of every one of its sources (same counts as ppr_run_list with
  * the same alpha, R and seed; tag 0, dangling mode 0, plain steps).
  */
+/*
+ * Serving (continuous batching of multi-source queries, Sec. 3's pipelines
+ * applied to a query stream).  Two modes:
+ *   PPR_SERVE_DEVICE_LOOP (default): one persistent kernel stays resident and
+ *     serves every query.  The host admits queries in arrival order as device
+ *     memory and one of 64 ring slots allow, copies their sources to the
+ *     device and publishes them through host-mapped memory; walker warps take
+ *     chunks of walks from all published queries (each warp starting at its
+ *     own query, so small queries are not held behind large ones) and refill
+ *     lanes as walks end, a lane carrying walks of different queries at once;
+ *     a query whose walks are all done is reduced source by source by the
+ *     loop's aggregator warps, which write its top-k rows straight into pinned
+ *     host memory and mark it done.  Every wait on the device is bounded: the
+ *     loop exits after `idle_us` without work and is launched again with the
+ *     next query.  R <= 1024 per query.
+ *   PPR_SERVE_STREAMS: a host scheduler runs each admitted query as its own
+ *     persistent walker launch and reduction on one of `streams` streams.
+ * Results are identical in both modes: query rows are ppr_run_list's rows of
+ * the same sources (tag 0, dangling mode 0, no segment tables).
+ */
+enum { PPR_SERVE_DEVICE_LOOP = 0, PPR_SERVE_STREAMS = 1 };
+
 typedef struct {
-    int32_t streams;        /* concurrent queries on the device (default 4) */
+    int32_t streams;        /* stream mode: concurrent queries on the device (default 4) */
     int64_t max_sources;    /* sources per query (default 100000) */
     int32_t max_topk;       /* largest k a query may ask for (0 = 64) */
     int64_t memory_budget;  /* device bytes for queries in flight (0 = a quarter of free memory) */
     int64_t max_pending;    /* queries waiting for admission before ppr_submit returns PPR_EBUSY (0 = no limit) */
-    int32_t chunk_sources, large_degree, warps_per_block; /* walker tuning (0 = defaults) */
+    int32_t chunk_sources, large_degree, warps_per_block; /* walker tuning (0 = defaults; the device loop
+                               takes chunk_sources only) */
     int32_t sampler;        /* neighbour choice of every query, as ppr_run_args.sampler; with 1
                                the graph's alias tables are built by ppr_serve_start */
     int32_t refill_lanes;   /* as ppr_run_args.refill_lanes (0 = 1) */
+    int32_t mode;           /* PPR_SERVE_DEVICE_LOOP (0) or PPR_SERVE_STREAMS (1) */
+    int64_t idle_us;        /* device loop: idle time after which the resident kernel exits
+                               (0 = 200,000 us); the next query launches it again */
 } ppr_serve_cfg;
 
 typedef struct {
     int64_t submit_ns, admit_ns, done_ns; /* steady-clock times of submission, admission, completion */
     uint64_t walks;
     int64_t sources;
+    int64_t device_walk_ns;   /* device loop: from its first chunk taken to its last walk counted */
+    int64_t device_reduce_ns; /* device loop: from its last walk counted to its last top-k row */
 } ppr_query_stats;
 
+typedef struct {
+    int32_t mode;           /* the serving mode */
+    uint32_t status;        /* device loop: exit reasons of its last launch (PPR_LOOP_*) */
+    int64_t launches;       /* device loop launches so far */
+    int64_t idle_exits;     /* launches that ended on the idle bound */
+    int64_t in_flight;      /* queries admitted and not finished */
+    int64_t completed;      /* queries finished */
+    int32_t running;        /* the device loop is on the GPU now */
+    /* device loop activity since serving started (each warp adds its counts about once a
+       millisecond and when it exits): */
+    uint64_t draws;         /* draws (walk steps) taken */
+    uint64_t iterations;    /* walker-warp iterations that stepped at least one walk */
+    uint64_t claims;        /* attempts of a walker warp to take a chunk of walks */
+    uint64_t claim_misses;  /* attempts that found none */
+    uint64_t sleeps;        /* waits of a walker warp with no walk and no chunk */
+    uint64_t reduced;       /* sources reduced to their top-k */
+    uint64_t cycles_claim, cycles_step, cycles_sleep, cycles_total; /* walker-warp SM clock cycles:
+                               taking chunks, stepping walks, waiting, and in all */
+    int32_t grid_blocks;    /* blocks of the device loop (8 warps each: 7 walk, 1 reduces) */
+} ppr_serve_info;
+
+/* Device loop exit reasons (ppr_serve_info.status). */
+enum { PPR_LOOP_STOPPED = 1, PPR_LOOP_IDLE = 2, PPR_LOOP_SLOT_TIMEOUT = 4, PPR_LOOP_BUSY_TIMEOUT = 8 };
+
 void ppr_serve_cfg_init(ppr_serve_cfg *cfg);
+
+/* State of the server of ctx (PPR_EINVAL if serving is not started). */
+int ppr_serve_get_info(ppr_ctx *ctx, ppr_serve_info *info);
+
+/* Test hook (device loop; host side, no device fault): publishes a ring slot
+ * that the host never wrote.  The loop's bounded wait for that slot's
+ * descriptor (one second) runs out, the loop exits with
+ * PPR_LOOP_SLOT_TIMEOUT, queries in flight fail with PPR_ECUDA and the server
+ * accepts no more queries until ppr_serve_stop; the context stays usable. */
+int ppr_debug_serve_publish_unwritten(ppr_ctx *ctx);
 
 /* Starts serving graph g (plain graphs) on the context; one server per context. */
 int ppr_serve_start(ppr_ctx *ctx, const ppr_graph *g, const ppr_serve_cfg *cfg);

@@ -9,8 +9,8 @@
 namespace ppr {
 
 struct AggOut {
-    uint32_t *nnz;       // [S]
-    int32_t *cols;       // [S * cap]
+    uint32_t *nnz;       // [S], or null: no rows (top-k only)
+    int32_t *cols;       // [S * cap], or null with cnts
     uint32_t *cnts;      // [S * cap]
     int32_t *topk_idx;   // [S * topk]
     uint32_t *topk_cnt;  // [S * topk]
@@ -47,13 +47,15 @@ __device__ inline void aggregate_source(const uint32_t *ends, uint32_t R, uint32
                 else hi = mid;
             }
             uint32_t c = i - lo + 1;
-            o.cols[rbase + r] = (int32_t)v;
-            o.cnts[rbase + r] = c;
+            if (o.cols) {
+                o.cols[rbase + r] = (int32_t)v;
+                o.cnts[rbase + r] = c;
+            }
             if (o.topk > 0) keys[r] = ((uint64_t)(~c) << 32) | v;
         }
         nrun += __popc(m);
     }
-    if (lane == 0) o.nnz[out_row] = nrun;
+    if (lane == 0 && o.nnz) o.nnz[out_row] = nrun;
     if (o.topk > 0) {
         uint32_t K2 = next_pow2(nrun);
         for (uint32_t i = nrun + lane; i < K2; i += 32) keys[i] = ~0ull;
@@ -211,13 +213,15 @@ __device__ inline void aggregate_source_reg(const uint32_t *ends, uint32_t R, ui
         __syncwarp();
         if (tail) {
             const uint32_t c = i - start_pos[run] + 1;
-            o.cols[rbase + run] = (int32_t)v[e];
-            o.cnts[rbase + run] = c;
+            if (o.cols) {
+                o.cols[rbase + run] = (int32_t)v[e];
+                o.cnts[rbase + run] = c;
+            }
             kbuf[run] = ((R - c) << 12) | run;
         }
         nrun += __popc(hb);
     }
-    if (lane == 0) o.nnz[out_row] = nrun;
+    if (lane == 0 && o.nnz) o.nnz[out_row] = nrun;
     if (o.topk > 0) {
         __syncwarp();
         uint32_t kv[E];

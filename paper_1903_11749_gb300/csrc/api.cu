@@ -422,7 +422,8 @@ int check_run(const ppr_graph *g, const ppr_run_args *a, int64_t count, bool lis
         (a->kernel != PPR_KERNEL_PERSISTENT && a->kernel != PPR_KERNEL_PLAIN) || a->large_degree < 0 ||
         a->warps_per_block < 0 || a->warps_per_block > 32 || a->chunk_sources < 0 || a->max_batch_sources < 0 ||
         (a->stats != 0 && a->stats != 1) || (a->sampler != 0 && a->sampler != 1) ||
-        (a->l2_persist != 0 && a->l2_persist != 1) || a->refill_lanes < 0 || a->refill_lanes > 32) {
+        (a->l2_persist != 0 && a->l2_persist != 1) || a->refill_lanes < 0 || a->refill_lanes > 32 ||
+        a->step_loads < -1 || a->step_loads == 1 || a->step_loads > 16) {
         set_error("invalid mode or tuning argument");
         return PPR_EINVAL;
     }
@@ -457,6 +458,7 @@ int check_run(const ppr_graph *g, const ppr_run_args *a, int64_t count, bool lis
     plan->stats = a->stats != 0;
     plan->sampler = a->sampler;
     plan->l2_persist = a->l2_persist == 1;
+    plan->step_loads = a->step_loads == 0 ? kDefaultStepLoads : (a->step_loads < 0 ? 0 : a->step_loads);
     return PPR_OK;
 }
 }  // namespace ppr

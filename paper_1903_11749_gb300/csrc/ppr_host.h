@@ -142,7 +142,9 @@ struct RunPlan {
     bool stats;
     int32_t sampler;  // 0 first-prefix-above rule, 1 integer alias method
     bool l2_persist;  // walker launches keep the node records in L2 (access-policy window)
+    int32_t step_loads;  // bounded step: dependent loads per lane per warp iteration (0 = unbounded)
 };
+constexpr int32_t kDefaultStepLoads = 6;
 // Enqueues the walks of sources [s_begin, s_end) writing output rows from
 // out_row0.  ends: S * R endpoint scratch for the plain kernel (else unused);
 // queue: one device counter for the persistent kernel's work queue.

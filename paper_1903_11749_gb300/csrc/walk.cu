@@ -1,13 +1,4 @@
-// walk.cu -- the walker kernels.
-//
-// One step (Sec. 2.1, Algorithm 2): draw Philox4x32-10 at counter
-// (s_local, j, k, tag); at a node with out-edges take the first edge whose
-// inclusive weight prefix exceeds floor(r64 * W_u / 2^64) and move to its
-// target; at a node without out-edges restart at the source (or end the walk,
-// dangling mode 1); then stop iff x2 < T.  At a node carrying a segment table
-// (Algorithm 4, depth 3) the same draw selects one outcome: a terminated
-// outcome ends the walk, an active one moves the walk and advances k by the
-// outcome's length.
+// walk.cu -- the batch walker kernels (one step of a walk: walk_step.cuh).
 //
 // k_walk_plain:      one thread per walk, endpoint to HBM (baseline).
 // k_walk_persistent: persistent warps pull chunks of walks from a global
@@ -23,231 +14,9 @@
 #include "ppr_host.h"
 #include "scan.cuh"
 #include "aggregate.cuh"
+#include "walk_step.cuh"
 
 namespace ppr {
-
-struct KParams {
-    const void *node;         // NodeRecN (narrow layout) or NodeRec (wide layout, alias tables)
-    const void *edges;
-    const SegEntry *seg;
-    uint32_t k0, k1, T, R, tag;
-    int32_t dangling;
-    uint32_t large;
-    int64_t s_begin, s_end;   // sources of this launch (global ids)
-    int64_t out_row0;         // output row of s_begin
-    uint32_t CS;              // sources per chunk (batched graphs)
-    uint32_t CW;              // walks per chunk (plain graphs; a chunk may start inside a source)
-    uint32_t refill;          // idle lanes before a warp starts new walks (1..32)
-    uint64_t walks;           // S * R
-    uint32_t nchunks;
-    const unsigned long long *nchunks_dev;  // batched graphs: chunk count written on the device
-    const int4 *chunks;       // batched graphs: {position, nsrc, instance, 0}; else null
-    const uint32_t *src_list; // explicit sources (position -> node id); null: s_begin + position
-    const int64_t *inst_off;  // batched graphs: node_off
-    int32_t instances;
-    AggOut out;
-    uint32_t *ends;           // S * R endpoints (instance-local ids)
-    unsigned long long *queue;
-    unsigned long long *steps;    // [0] draws consumed, [2] layout sectors, [5] flat-CSR model sectors (statistics launch)
-    uint32_t P2;              // next_pow2(R)
-    uint64_t r_magic;         // ceil(2^40 / R): walk index -> source index by multiply-shift
-    int64_t n_nodes;          // node records (for the L2 window and the checked build)
-    uint64_t n_records;       // checked build: records of the edge layout walked (alias: slots)
-    uint64_t n_seg;           // checked build: segment entries
-    unsigned long long *err;  // checked build: flags of indices that left their array
-};
-
-// Checked build (-DPPR_CHECKED): every node index and every row extent a step
-// is about to read is tested against its array first; a bad one sets a flag
-// in p.err (1 node, 2 edge row, 4 segment table, 8 endpoint slot) and ends the
-// walk instead of reading, so the host reports the run as failed; nothing traps.
-#ifdef PPR_CHECKED
-#define PPR_CHECK(cond, flag)                                  \
-    do {                                                       \
-        if (!(cond)) {                                         \
-            atomicOr(p.err, (unsigned long long)(flag));       \
-            end = 0;                                           \
-            return true;                                       \
-        }                                                      \
-    } while (0)
-#else
-#define PPR_CHECK(cond, flag) \
-    do {                      \
-    } while (0)
-#endif
-
-// One step of one walk.  Returns true when the walk has ended (end is set).
-// With COOP, every lane of the warp calls it (inactive lanes with act=false)
-// and rows longer than p.large are searched by the whole warp.
-struct Tally {
-    uint32_t steps = 0;
-    uint32_t sectors = 0;
-    uint32_t model = 0;  // the same draws on a flat CSR searched by bisection (statistics launch)
-};
-
-// 32-byte sectors a draw at a node of out-degree d costs on a flat CSR
-// searched by bisection, without reuse: the row_ptr pair, max(1, ceil(log2 d) - 1)
-// sectors of prefix probes (the last few probes share a sector), the col
-// entry; a dangling node reads its row_ptr pair only.
-__device__ __forceinline__ uint32_t flat_model_sectors(uint32_t d)
-{
-    if (d == 0) return 1;
-    const uint32_t lg = d > 1 ? 32u - __clz(d - 1) : 0u;  // ceil(log2 d)
-    return 2u + max(1u, lg > 0 ? lg - 1 : 0u);
-}
-
-// STATS: count, per step, the 32-byte sectors a thread-serial bisection must
-// touch (node record + distinct probe sectors); rows are then searched by
-// bisection only, which returns the same edge as the cooperative search.
-template <class E, bool SEG, bool COOP, bool STATS>
-__device__ __forceinline__ bool walk_step(const KParams &p, const E &edges, bool act, uint32_t src, uint32_t sctr,
-                                          uint32_t j, uint32_t tag, uint32_t &k, uint32_t &u, uint32_t &end,
-                                          Tally &tl)
-{
-    uint4 x = make_uint4(0, 0, 0, 0);
-    NodeRec r{};
-#ifdef PPR_CHECKED
-    bool bad_node = false;
-#endif
-    if (act) {
-        x = philox4x32_10(make_uint4(sctr, j, k, tag), p.k0, p.k1);
-#ifdef PPR_CHECKED
-        if ((uint64_t)u >= (uint64_t)p.n_nodes) {
-            atomicOr(p.err, 1ull);
-            bad_node = true;
-            u = 0;  // read a valid record; the walk ends at this step
-        }
-#endif
-        r = E::load_node(p.node, u);
-    }
-    const uint64_t w0 = r.word0, total = r.total;
-    const uint32_t cnt = (uint32_t)(w0 >> 40) & kCountMask;
-    const uint64_t beg = w0 & kBeginMask;
-    const bool segf = SEG && (w0 >> 63);
-    const uint64_t r64 = (uint64_t)x.x | ((uint64_t)x.y << 32);
-#ifdef PPR_CHECKED
-    if (act && bad_node) {  // flagged above
-        end = 0;
-        return true;
-    }
-#endif
-    if constexpr (std::is_same<E, AliasEdges>::value) {
-        // integer alias method: slot j = floor(r*d / 2^64), y = floor(frac * W / 2^64)
-        if (!act) return false;
-        PPR_CHECK(cnt < 2 || beg + cnt <= p.n_records, 2);
-        if (STATS) ++tl.sectors, ++tl.model;  // the node record
-        uint32_t next;
-        if (cnt == 0) {
-            if (p.dangling == 1) {
-                end = u;
-                return true;
-            }
-            next = src;
-        } else if (cnt == 1) {
-            next = (uint32_t)beg;  // single out-edge: target kept in the record
-        } else {
-            const uint64_t j = __umul64hi(r64, (uint64_t)cnt);
-            const uint64_t frac = r64 * (uint64_t)cnt;
-            const uint4 rec = edges.load(beg + j);  // {thr, col, alias col, W}
-            const uint64_t y = mulhi64_by32((uint32_t)frac, (uint32_t)(frac >> 32), rec.w);
-            next = y < rec.x ? rec.y : rec.z;
-            if (STATS) ++tl.sectors, ++tl.model;
-        }
-        ++tl.steps;
-        ++k;
-        u = next;
-        if (x.z < p.T) {
-            end = u;
-            return true;
-        }
-        return false;
-    }
-    uint64_t xr = 0;
-    if (act && (cnt > 1 || segf)) {
-        // narrow rows hold the summary shape above bit 32 (W < 2^32 there)
-        if (segf || sizeof(typename E::Rec) != 8) xr = mulhi64(r64, total);
-        else xr = mulhi64_by32(x.x, x.y, (uint32_t)total);
-    }
-    uint32_t next = 0;
-    bool big = false;
-    if (COOP && !STATS && p.large != 0xffffffffu) {  // uniform: skipped whole when the path is off
-        big = act && !segf && cnt > p.large;
-        uint32_t bigmask = __ballot_sync(0xffffffffu, big);
-        const uint32_t lane = threadIdx.x & 31;
-        while (bigmask) {
-            const uint32_t L = __ffs(bigmask) - 1;
-            bigmask &= bigmask - 1;
-            const uint32_t n = __shfl_sync(0xffffffffu, cnt, L);
-            const uint64_t lo = E::edge_base(__shfl_sync(0xffffffffu, beg, L), n);
-            const uint64_t xx = __shfl_sync(0xffffffffu, xr, L);
-            auto rec = search_warp(edges, lo, n, xx);
-            if (lane == L) next = E::target(rec);
-        }
-    }
-    if (!act) return false;
-    if (STATS) {
-        ++tl.sectors;  // the node record
-        tl.model += segf ? 1u + (cnt <= 2 ? 1u : 2u) : flat_model_sectors(cnt);
-    }
-    PPR_CHECK(!segf || beg + cnt <= p.n_seg, 4);
-    PPR_CHECK(segf || cnt < 2 ||
-                  beg + (sizeof(typename E::Rec) == 8 ? (uint64_t)blocked_row_records(cnt) : (uint64_t)cnt) <= p.n_records,
-              2);
-    if (segf) {
-        SegTable tab{p.seg};
-        uint4 o = STATS ? search_serial_tally(tab, beg, cnt, xr, tl.sectors) : search_serial(tab, beg, cnt, xr);
-        ++tl.steps;
-        if ((o.w >> 8) == 0) {
-            end = o.z;
-            return true;
-        }
-        u = o.z;
-        k += o.w & 0xffu;
-        return false;
-    }
-    if (cnt == 0) {
-        if (p.dangling == 1) {
-            end = u;
-            return true;
-        }
-        next = src;
-    } else if (cnt == 1) {
-        next = (uint32_t)total;  // single out-edge: target kept in the node record
-    } else if (!big) {
-        if constexpr (sizeof(typename E::Rec) == 8) {
-            next = search_blocked<STATS>(edges.e, beg, cnt, (uint32_t)(total >> 32) & 0xffffffu, (uint32_t)(total >> 56),
-                                         (uint32_t)xr, static_cast<const NodeRecN *>(p.node) + u, tl.sectors);
-        } else {
-            next = E::target(STATS ? search_serial_tally(edges, beg, cnt, xr, tl.sectors) : search_serial(edges, beg, cnt, xr));
-        }
-    }
-    ++tl.steps;
-    ++k;
-    u = next;
-    if (x.z < p.T) {
-        end = u;
-        return true;
-    }
-    return false;
-}
-
-template <class E>
-__device__ __forceinline__ E make_edges(const void *e);
-template <>
-__device__ __forceinline__ NarrowEdges make_edges<NarrowEdges>(const void *e)
-{
-    return NarrowEdges{(const EdgeN *)e};
-}
-template <>
-__device__ __forceinline__ WideEdges make_edges<WideEdges>(const void *e)
-{
-    return WideEdges{(const EdgeW *)e};
-}
-template <>
-__device__ __forceinline__ AliasEdges make_edges<AliasEdges>(const void *e)
-{
-    return AliasEdges{(const AliasRec *)e};
-}
 
 __device__ __forceinline__ void warp_add(unsigned long long *dst, uint32_t v)
 {
@@ -296,7 +65,8 @@ __global__ void __launch_bounds__(256, PPR_WALK_MINB) k_walk_plain(KParams p)
             tag = (uint32_t)lo;
         }
         uint32_t k = 0, u = src, end = 0;
-        while (!walk_step<E, SEG, false, STATS>(p, edges, true, src, src - ctr_base, j, tag, k, u, end, tl)) {
+        while (!walk_step<E, SEG, false, STATS>(p, StepKey{p.k0, p.k1, p.T}, edges, true, src, src - ctr_base, j, tag, k, u,
+                                                 end, tl)) {
         }
         p.ends[t] = end - ctr_base;
     }
@@ -324,10 +94,11 @@ __device__ __forceinline__ uint32_t div_by_R(uint32_t w, uint64_t magic)
     return (uint32_t)(((uint64_t)w * magic) >> 40);  // exact for w < 2^20, R <= 4096
 }
 
-template <class E, bool SEG, bool STATS>
+template <class E, bool SEG, bool STATS, bool BOUNDED = false>
 __global__ void __launch_bounds__(256, PPR_WALK_MINB) k_walk_persistent(KParams p)
 {
     __shared__ WarpQueue wq_all[8];
+    __shared__ uint32_t ps_all[BOUNDED ? 8 * 256 : 1];  // bounded step: each lane's pending search
     const uint32_t lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
     WarpQueue &wq = wq_all[wid];
     const E edges = make_edges<E>(p.edges);
@@ -340,6 +111,7 @@ __global__ void __launch_bounds__(256, PPR_WALK_MINB) k_walk_persistent(KParams 
     bool active = false;
     uint32_t src = 0, sctr = 0, j = 0, k = 0, u = 0, tag = 0, ctr_base = 0;
     uint64_t slot = 0;  // endpoint index: (src - s_begin) * R + j
+    bool pend = false;  // bounded step: this lane's draw has a search in progress
     Tally tl;
 
     for (;;) {
@@ -404,7 +176,15 @@ __global__ void __launch_bounds__(256, PPR_WALK_MINB) k_walk_persistent(KParams 
         if (__ballot_sync(0xffffffffu, active) == 0) break;  // queue drained and every walk done
 
         uint32_t end = 0;
-        if (walk_step<E, SEG, true, STATS>(p, edges, active, src, sctr, j, tag, k, u, end, tl)) {
+        bool ended;
+        if constexpr (BOUNDED) {
+            ended = active && walk_step_bounded<SEG>(p, StepKey{p.k0, p.k1, p.T}, edges, src, sctr, j, tag, k, u, end,
+                                                     pend, PendRef{ps_all, blockDim.x, threadIdx.x}, tl);
+        } else {
+            ended = walk_step<E, SEG, true, STATS>(p, StepKey{p.k0, p.k1, p.T}, edges, active, src, sctr, j, tag, k, u,
+                                                   end, tl);
+        }
+        if (ended) {
 #ifdef PPR_CHECKED
             if (slot >= (uint64_t)(p.s_end - p.s_begin) * p.R) atomicOr(p.err, 8ull);
             else
@@ -429,7 +209,7 @@ static int walker_event(ppr_result *r, cudaStream_t st)
     return PPR_OK;
 }
 
-template <class E, bool SEG, bool STATS>
+template <class E, bool SEG, bool STATS, bool BOUNDED = false>
 static int launch_typed(ppr_ctx *ctx, const KParams &kp, const RunPlan &plan, int64_t S, cudaStream_t st,
                         ppr_result *r)
 {
@@ -448,7 +228,7 @@ static int launch_typed(ppr_ctx *ctx, const KParams &kp, const RunPlan &plan, in
     int per_sm = 0;
     // walkers per CTA: 32 * warps_per_block (4 or 8 warps; default 8)
     const int wpb = plan.warps_per_block == 4 ? 4 : 8;
-    PPR_CUDA(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_walk_persistent<E, SEG, STATS>, 32 * wpb, 0));
+    PPR_CUDA(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_walk_persistent<E, SEG, STATS, BOUNDED>, 32 * wpb, 0));
     if (per_sm < 1) per_sm = 1;
     int64_t blocks = (int64_t)ctx->sms * per_sm;
     int64_t needed = ((int64_t)kp.nchunks + wpb - 1) / wpb;
@@ -476,7 +256,7 @@ static int launch_typed(ppr_ctx *ctx, const KParams &kp, const RunPlan &plan, in
         cfg.attrs = attr;
         cfg.numAttrs = 1;
     }
-    PPR_CUDA(cudaLaunchKernelEx(&cfg, k_walk_persistent<E, SEG, STATS>, kp));
+    PPR_CUDA(cudaLaunchKernelEx(&cfg, k_walk_persistent<E, SEG, STATS, BOUNDED>, kp));
     note_launch();
     PPR_CUDA(cudaGetLastError());
     if ((rc = walker_event(r, st))) return rc;
@@ -549,6 +329,9 @@ void preload_run_kernels()
     preload_walkers<NarrowEdges, true, false>();
     preload_walkers<NarrowEdges, false, true>();
     preload_walkers<NarrowEdges, true, true>();
+    cudaFuncAttributes fa;
+    cudaFuncGetAttributes(&fa, k_walk_persistent<NarrowEdges, false, false, true>);
+    cudaFuncGetAttributes(&fa, k_walk_persistent<NarrowEdges, true, false, true>);
     preload_walkers<WideEdges, false, false>();
     preload_walkers<WideEdges, true, false>();
     preload_walkers<WideEdges, false, true>();
@@ -604,6 +387,7 @@ int launch_walks(ppr_ctx *ctx, const ppr_graph *g, const RunPlan &plan, const Ou
     kp.P2 = P2;
     kp.r_magic = ((1ull << 40) + plan.R - 1) / plan.R;
     kp.refill = plan.refill_lanes > 0 ? (uint32_t)std::min(plan.refill_lanes, 32) : 1u;
+    kp.step_loads = (uint32_t)std::max(plan.step_loads, 0);
     kp.n_nodes = g->n;
     kp.n_records = plan.sampler == 1 ? (uint64_t)g->m : (uint64_t)g->edge_records;
     kp.n_seg = (uint64_t)g->seg.entries_n;
@@ -667,6 +451,10 @@ int launch_walks(ppr_ctx *ctx, const ppr_graph *g, const RunPlan &plan, const Ou
     if (g->wide)
         return plan.segments ? launch_typed<WideEdges, true, false>(ctx, kp, plan, S, st, ev_owner)
                              : launch_typed<WideEdges, false, false>(ctx, kp, plan, S, st, ev_owner);
+    // the bounded step: persistent kernel, no cooperative search (statistics launches took the branch above)
+    if (plan.step_loads > 0 && plan.kernel == PPR_KERNEL_PERSISTENT && kp.large == 0xffffffffu)
+        return plan.segments ? launch_typed<NarrowEdges, true, false, true>(ctx, kp, plan, S, st, ev_owner)
+                             : launch_typed<NarrowEdges, false, false, true>(ctx, kp, plan, S, st, ev_owner);
     return plan.segments ? launch_typed<NarrowEdges, true, false>(ctx, kp, plan, S, st, ev_owner)
                          : launch_typed<NarrowEdges, false, false>(ctx, kp, plan, S, st, ev_owner);
 }

@@ -230,7 +230,7 @@ WORKLOADS = {
 }
 
 
-def workload_graph(name: str):
+def _make_workload_graph(name: str) -> Graph:
     if name == "er1k":
         return er_graph(1000, 10_000, 1, 10, seed=12345)
     if name == "rmat20":
@@ -238,3 +238,24 @@ def workload_graph(name: str):
     if name == "rmat24":
         return rmat_graph(24, 16, seed=2424, hub_degree=1_200_000)
     raise KeyError(name)
+
+
+def workload_graph(name: str) -> Graph:
+    """The named workload's graph.  With PPR_GRAPH_CACHE set to a directory,
+    a generated graph is saved there (raw .npy arrays) and later calls load it
+    instead of generating it again; the arrays are the generator's, unchanged."""
+    cache = os.environ.get("PPR_GRAPH_CACHE")
+    if not cache:
+        return _make_workload_graph(name)
+    d = os.path.join(cache, name)
+    parts = ("row_ptr", "col", "w")
+    if all(os.path.exists(os.path.join(d, p + ".npy")) for p in parts):
+        a = [np.load(os.path.join(d, p + ".npy")) for p in parts]
+        return Graph(len(a[0]) - 1, a[0], a[1], a[2], name=name, meta={"cached": d})
+    g = _make_workload_graph(name)
+    os.makedirs(d, exist_ok=True)
+    for p_, arr in zip(parts, (g.row_ptr, g.col, g.w)):
+        tmp = os.path.join(d, f"{p_}.tmp{os.getpid()}.npy")
+        np.save(tmp, arr)
+        os.replace(tmp, os.path.join(d, p_ + ".npy"))
+    return g

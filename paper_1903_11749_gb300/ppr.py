@@ -20,6 +20,8 @@ LIB_PATH = os.environ.get("PPR_LIBRARY_PATH") or os.path.join(_HERE, "libppr.so"
 PPR_OK, PPR_EINVAL, PPR_ENOMEM, PPR_ECUDA, PPR_ETIMEOUT, PPR_ERANGE, PPR_EBUSY, PPR_ENOTSUP = 0, -1, -2, -3, -4, -5, -6, -7
 PPR_PTRS_DEVICE = 1
 KERNEL_PERSISTENT, KERNEL_PLAIN = 0, 1
+SERVE_DEVICE_LOOP, SERVE_STREAMS = 0, 1
+LOOP_STOPPED, LOOP_IDLE, LOOP_SLOT_TIMEOUT, LOOP_BUSY_TIMEOUT = 1, 2, 4, 8
 _NAMES = {-1: "EINVAL", -2: "ENOMEM", -3: "ECUDA", -4: "ETIMEOUT", -5: "ERANGE", -6: "EBUSY", -7: "ENOTSUP"}
 
 
@@ -41,7 +43,7 @@ class RunArgs(C.Structure):
                 ("topk", C.c_int32), ("kernel", C.c_int32), ("large_degree", C.c_int32),
                 ("warps_per_block", C.c_int32), ("chunk_sources", C.c_int32), ("max_batch_sources", C.c_int64),
                 ("stats", C.c_int32), ("sampler", C.c_int32), ("l2_persist", C.c_int32),
-                ("refill_lanes", C.c_int32), ("stream", C.c_void_p)]
+                ("refill_lanes", C.c_int32), ("stream", C.c_void_p), ("step_loads", C.c_int32)]
 
 
 class Tuning(C.Structure):
@@ -54,12 +56,21 @@ class ServeCfg(C.Structure):
     _fields_ = [("streams", C.c_int32), ("max_sources", C.c_int64), ("max_topk", C.c_int32),
                 ("memory_budget", C.c_int64), ("max_pending", C.c_int64), ("chunk_sources", C.c_int32),
                 ("large_degree", C.c_int32), ("warps_per_block", C.c_int32), ("sampler", C.c_int32),
-                ("refill_lanes", C.c_int32)]
+                ("refill_lanes", C.c_int32), ("mode", C.c_int32), ("idle_us", C.c_int64)]
+
+
+class ServeInfo(C.Structure):
+    _fields_ = [("mode", C.c_int32), ("status", C.c_uint32), ("launches", C.c_int64), ("idle_exits", C.c_int64),
+                ("in_flight", C.c_int64), ("completed", C.c_int64), ("running", C.c_int32),
+                ("draws", C.c_uint64), ("iterations", C.c_uint64), ("claims", C.c_uint64),
+                ("claim_misses", C.c_uint64), ("sleeps", C.c_uint64), ("reduced", C.c_uint64),
+                ("cycles_claim", C.c_uint64), ("cycles_step", C.c_uint64), ("cycles_sleep", C.c_uint64),
+                ("cycles_total", C.c_uint64), ("grid_blocks", C.c_int32)]
 
 
 class QueryStats(C.Structure):
     _fields_ = [("submit_ns", C.c_int64), ("admit_ns", C.c_int64), ("done_ns", C.c_int64), ("walks", C.c_uint64),
-                ("sources", C.c_int64)]
+                ("sources", C.c_int64), ("device_walk_ns", C.c_int64), ("device_reduce_ns", C.c_int64)]
 
 
 class ResultInfo(C.Structure):
@@ -102,6 +113,8 @@ _SIGS = {
     "ppr_serve_cfg_init": (None, [C.POINTER(ServeCfg)]),
     "ppr_serve_start": (C.c_int, [C.c_void_p, C.c_void_p, C.POINTER(ServeCfg)]),
     "ppr_serve_stop": (C.c_int, [C.c_void_p]),
+    "ppr_serve_get_info": (C.c_int, [C.c_void_p, C.POINTER(ServeInfo)]),
+    "ppr_debug_serve_publish_unwritten": (C.c_int, [C.c_void_p]),
     "ppr_submit": (C.c_int, [C.c_void_p, C.c_void_p, C.c_int64, C.c_double, C.c_uint32, C.c_uint64, C.c_int32,
                              C.POINTER(C.c_uint64)]),
     "ppr_poll": (C.c_int, [C.c_void_p, C.c_uint64, C.c_void_p, C.c_void_p, C.c_int64, C.POINTER(QueryStats)]),
@@ -223,6 +236,15 @@ class Context:
 
     def serve_stop(self):
         _check(lib().ppr_serve_stop(self.h))
+
+    def serve_info(self) -> dict:
+        i = ServeInfo()
+        _check(lib().ppr_serve_get_info(self.h, C.byref(i)))
+        return {f: getattr(i, f) for f, _ in ServeInfo._fields_}
+
+    def debug_serve_publish_unwritten(self):
+        """Test hook: publishes a ring slot the host never wrote (see include/ppr.h)."""
+        _check(lib().ppr_debug_serve_publish_unwritten(self.h))
         self._serving = None
 
     def submit(self, sources, alpha=0.15, R=100, seed=1, topk=32) -> int:
@@ -238,7 +260,8 @@ class Context:
         st = QueryStats()
         _check(lib().ppr_poll(self.h, qid, idx.ctypes.data, cnt.ctypes.data, timeout_ms, C.byref(st)))
         return idx, cnt, {"submit_ns": st.submit_ns, "admit_ns": st.admit_ns, "done_ns": st.done_ns,
-                          "walks": st.walks, "sources": st.sources}
+                          "walks": st.walks, "sources": st.sources, "device_walk_ns": st.device_walk_ns,
+                          "device_reduce_ns": st.device_reduce_ns}
 
     def load_graph(self, n, row_ptr, col, w, stream=None, m=None) -> "Graph":
         rp, dev = _ptr(row_ptr)
@@ -288,7 +311,7 @@ class Graph:
 
     def _args(self, alpha=0.15, R=100, seed=1, src_begin=0, src_end=None, tag=0, dangling=0, segments=False,
               topk=0, kernel=KERNEL_PERSISTENT, large_degree=0, warps_per_block=0, chunk_sources=0,
-              max_batch_sources=0, stats=False, stream=None, sampler=0, l2_persist=0, refill_lanes=0):
+              max_batch_sources=0, stats=False, stream=None, sampler=0, l2_persist=0, refill_lanes=0, step_loads=0):
         a = RunArgs()
         lib().ppr_run_args_init(C.byref(a))
         a.alpha, a.R, a.seed = alpha, R, seed
@@ -301,6 +324,7 @@ class Graph:
         a.sampler = sampler
         a.l2_persist = l2_persist
         a.refill_lanes = refill_lanes
+        a.step_loads = step_loads
         a.stream = _stream_ptr(stream)
         return a
 
@@ -354,26 +378,13 @@ class Graph:
         _check(lib().ppr_run_into(self.ctx.h, self.h, C.byref(a), _ptr(workspace)[0], nbytes, _ptr(nnz)[0],
                                   _ptr(cols)[0], _ptr(cnts)[0], cap, ti, tc))
 
-    def run(self, alpha=0.15, R=100, seed=1, src_begin=0, src_end=None, tag=0, dangling=0, segments=False,
-            topk=0, kernel=KERNEL_PERSISTENT, large_degree=0, warps_per_block=0, chunk_sources=0,
-            max_batch_sources=0, stats=False, stream=None, wait=True, sampler=0, l2_persist=0,
-            refill_lanes=0) -> "Result":
-        a = RunArgs()
-        lib().ppr_run_args_init(C.byref(a))
-        a.alpha, a.R, a.seed = alpha, R, seed
-        a.src_begin = src_begin
-        a.src_end = self.info().n if src_end is None else src_end
-        a.tag, a.dangling, a.segments, a.topk, a.kernel = tag, dangling, int(bool(segments)), topk, kernel
-        a.large_degree, a.warps_per_block, a.chunk_sources = large_degree, warps_per_block, chunk_sources
-        a.max_batch_sources = max_batch_sources
-        a.stats = int(bool(stats))
-        a.sampler = sampler
-        a.l2_persist = l2_persist
-        a.refill_lanes = refill_lanes
-        a.stream = _stream_ptr(stream)
+    def run(self, wait=True, **kw) -> "Result":
+        """Walks from every source of [src_begin, src_end) (default: all); takes
+        the arguments of ppr_run_args by name (include/ppr.h)."""
+        a = self._args(**kw)
         h = C.c_void_p()
         _check(lib().ppr_run(self.ctx.h, self.h, C.byref(a), C.byref(h)))
-        r = Result(self, h, a.src_end - a.src_begin, topk)
+        r = Result(self, h, a.src_end - a.src_begin, kw.get("topk", 0))
         if wait:
             r.wait()
         return r

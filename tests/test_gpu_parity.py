@@ -176,6 +176,39 @@ def test_large_rows_cooperative_search(ppr, ctx, oracle):
         assert_same(G.run(alpha=0.15, R=50, seed=3, src_end=2000, topk=8, large_degree=large), ref, topk=8)
 
 
+def _mixed_depth_graph(seed=17):
+    """Rows of every search depth (1 to 150,000 edges), dangling nodes, and
+    small rows whose 3-step neighbourhoods carry segment tables."""
+    rng = np.random.Generator(np.random.PCG64(seed))
+    n = 6000
+    degs = np.concatenate([[150_000, 40_000, 9000, 3000, 2561, 600, 321, 70, 41, 9],
+                           rng.integers(0, 9, n - 10)])
+    degs[-40:] = 0  # dangling
+    src = np.repeat(np.arange(n), degs)
+    dst = rng.integers(0, n, len(src))
+    w = rng.integers(1, 1000, len(src))
+    row_ptr, col, ww = I._csr_from_pairs(n, src, dst, w)
+    return I.Graph(n, row_ptr, col, ww)
+
+
+@pytest.mark.parametrize("segments", [False, True])
+def test_step_bound_does_not_change_results(ppr, ctx, oracle, segments):
+    """The bounded step (a deep search resumes in the next warp iteration)
+    gives the oracle's rows, steps and top-k for every bound, including 2 (the
+    node record and one more load per iteration: every search of two or more
+    loads resumes), and without a bound; both dangling modes."""
+    g = _mixed_depth_graph()
+    G = ctx.load_graph(g.n, g.row_ptr, g.col, g.w)
+    for dangling in (0, 1):
+        ref = oracle_rows(oracle, g, 0.2, 40, 9, dangling=dangling, segments=segments, topk=6)
+        for sl in (0, -1, 2, 3, 5, 16):
+            res = G.run(alpha=0.2, R=40, seed=9, dangling=dangling, segments=segments, topk=6, step_loads=sl,
+                        refill_lanes=24 if sl == 3 else 0)
+            assert_same(res, ref, topk=6)
+    with pytest.raises(ppr.PPRError):
+        G.run(alpha=0.2, R=4, step_loads=1)
+
+
 def test_huge_rows_built_by_tiles(ppr, ctx, oracle):
     """Rows above 8,192 edges are built by tiles of 8,192 edges (a hub of
     150,001 edges, rows of 65,537 and 65,536 edges), in a plain and in a

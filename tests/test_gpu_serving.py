@@ -1,9 +1,14 @@
-"""Serving: multi-source queries admitted by continuous batching.
+"""Serving: multi-source queries admitted by continuous batching, in both
+modes (the resident device loop, and one launch per query on a few streams).
 
 Each query's top-k must equal the CPU oracle's (walks from each listed
 source at tag 0, Sec. 2.1 estimator, top-k order of count then id) when it
 runs alone, when it runs in a mix of overlapping queries, and as a
-ppr_run_list of the same sources (tolerance 0: the counts are integers)."""
+ppr_run_list of the same sources (tolerance 0: the counts are integers).
+The device loop's bounded waits are exercised from the host: an idle loop
+exits and is launched again by the next query, and a published slot that
+was never written makes the loop exit with an error status while the
+context stays usable."""
 import threading
 
 import numpy as np
@@ -42,14 +47,18 @@ def _queries(n, count, seed, smax=3000):
     return [rng.choice(n, size=int(s), replace=False).astype(np.int32) for s in sizes]
 
 
-def test_alone_equals_mix_equals_oracle(env, oracle):
+MODES = [0, 1]  # ppr.SERVE_DEVICE_LOOP, ppr.SERVE_STREAMS
+
+
+@pytest.mark.parametrize("mode", MODES)
+def test_alone_equals_mix_equals_oracle(env, oracle, mode):
     ppr, g = env
     ctx = ppr.Context(0)
     G = ctx.load_graph(g.n, g.row_ptr, g.col, g.w)
     qs = _queries(g.n, 24, seed=1)
     kw = dict(alpha=0.15, R=60, seed=7, topk=8)
     ref = _oracle_topk(oracle, g, 0.15, 60, 7, 8)
-    ctx.serve_start(G, streams=3)
+    ctx.serve_start(G, streams=3, mode=mode)
     alone = []
     for src in qs:
         qid = ctx.submit(src, **kw)
@@ -84,14 +93,15 @@ def test_alone_equals_mix_equals_oracle(env, oracle):
         assert np.array_equal(ridx, alone[i][0]) and np.array_equal(rcnt, alone[i][1])
 
 
-def test_memory_admission_and_errors(env, oracle):
+@pytest.mark.parametrize("mode", MODES)
+def test_memory_admission_and_errors(env, oracle, mode):
     ppr, g = env
     ctx = ppr.Context(0)
     G = ctx.load_graph(g.n, g.row_ptr, g.col, g.w)
     with pytest.raises(ppr.PPRError):
         ctx.submit(np.arange(5, dtype=np.int32))  # not started
     # a budget that fits one large query at a time: queries wait for memory
-    ctx.serve_start(G, streams=4, memory_budget=3 << 20, max_sources=4000)
+    ctx.serve_start(G, streams=4, memory_budget=3 << 20, max_sources=4000, mode=mode)
     qs = _queries(g.n, 10, seed=2, smax=3000)
     kw = dict(alpha=0.2, R=40, seed=3, topk=5)
     ref = _oracle_topk(oracle, g, 0.2, 40, 3, 5)
@@ -122,11 +132,12 @@ def test_memory_admission_and_errors(env, oracle):
         ctx.poll(1, 1, 5, timeout_ms=10)
 
 
-def test_alias_sampler_queries_equal_oracle(env, oracle):
+@pytest.mark.parametrize("mode", MODES)
+def test_alias_sampler_queries_equal_oracle(env, oracle, mode):
     ppr, g = env
     ctx = ppr.Context(0)
     G = ctx.load_graph(g.n, g.row_ptr, g.col, g.w)
-    ctx.serve_start(G, streams=2, sampler=1)
+    ctx.serve_start(G, streams=2, sampler=1, mode=mode)
     qs = _queries(g.n, 6, seed=9, smax=800)
     kw = dict(alpha=0.15, R=50, seed=11, topk=6)
     ids = [ctx.submit(src, **kw) for src in qs]
@@ -139,13 +150,14 @@ def test_alias_sampler_queries_equal_oracle(env, oracle):
         assert np.array_equal(idx, ridx) and np.array_equal(cnt, rcnt)
 
 
-def test_refilled_warps_serve_the_same_counts(env, oracle):
+@pytest.mark.parametrize("mode", MODES)
+def test_refilled_warps_serve_the_same_counts(env, oracle, mode):
     """A server whose warps start new walks 24 lanes at a time returns the
-    counts of plain list runs."""
+    oracle's counts."""
     ppr, g = env
     ctx = ppr.Context(0)
     G = ctx.load_graph(g.n, g.row_ptr, g.col, g.w)
-    ctx.serve_start(G, streams=2, refill_lanes=24)
+    ctx.serve_start(G, streams=2, refill_lanes=24, mode=mode)
     qs = _queries(g.n, 5, seed=13, smax=900)
     kw = dict(alpha=0.15, R=50, seed=12, topk=6)
     ids = [ctx.submit(src, **kw) for src in qs]
@@ -154,3 +166,72 @@ def test_refilled_warps_serve_the_same_counts(env, oracle):
     ref = _oracle_topk(oracle, g, 0.15, 50, 12, 6)
     for (idx, cnt), src in zip(got, qs):
         assert _same_as_oracle(ref, src, idx, cnt)
+
+
+def test_device_loop_idle_exit_and_relaunch(env, oracle):
+    """The resident loop exits after its idle bound with no work; the next
+    query launches it again and is served exactly."""
+    import time
+    ppr, g = env
+    ctx = ppr.Context(0)
+    G = ctx.load_graph(g.n, g.row_ptr, g.col, g.w)
+    ctx.serve_start(G, idle_us=20_000)
+    deadline = time.time() + 10
+    while ctx.serve_info()["running"] and time.time() < deadline:
+        time.sleep(0.01)
+    info = ctx.serve_info()
+    assert info["running"] == 0 and info["idle_exits"] >= 1 and info["status"] & ppr.LOOP_IDLE
+    launches = info["launches"]
+    kw = dict(alpha=0.2, R=30, seed=5, topk=4)
+    ref = _oracle_topk(oracle, g, 0.2, 30, 5, 4)
+    for src in _queries(g.n, 3, seed=21, smax=500):
+        idx, cnt, st = ctx.poll(ctx.submit(src, **kw), len(src), 4, timeout_ms=60000)
+        assert _same_as_oracle(ref, src, idx, cnt)
+    assert ctx.serve_info()["launches"] > launches
+    ctx.serve_stop()
+
+
+def test_device_loop_slot_wait_runs_out(env, oracle):
+    """A ring slot published without its descriptor (a host-side test hook):
+    the loop's bounded wait ends it with PPR_LOOP_SLOT_TIMEOUT, no GPU fault;
+    the server refuses further queries and the context keeps working."""
+    import time
+    ppr, g = env
+    ctx = ppr.Context(0)
+    G = ctx.load_graph(g.n, g.row_ptr, g.col, g.w)
+    ctx.serve_start(G)
+    ctx.debug_serve_publish_unwritten()
+    deadline = time.time() + 20
+    while time.time() < deadline:
+        info = ctx.serve_info()
+        if not info["running"] and info["status"] & ppr.LOOP_SLOT_TIMEOUT:
+            break
+        time.sleep(0.05)
+    assert info["status"] & ppr.LOOP_SLOT_TIMEOUT and not info["running"]
+    with pytest.raises(ppr.PPRError) as ei:
+        ctx.submit(np.arange(5, dtype=np.int32))
+    assert ei.value.code == ppr.PPR_ECUDA
+    with pytest.raises(ppr.PPRError):
+        ctx.serve_stop()  # reports the failed loop, and stops serving
+    ref = _oracle_topk(oracle, g, 0.15, 20, 3, 4)
+    idx, cnt = G.run(alpha=0.15, R=20, seed=3, topk=4).topk()
+    assert np.array_equal(idx, ref[0]) and np.array_equal(cnt, ref[1])
+    ctx.serve_start(G)  # serving starts again on the same context
+    src = np.arange(0, 50, dtype=np.int32)
+    idx, cnt, _ = ctx.poll(ctx.submit(src, alpha=0.15, R=20, seed=3, topk=4), 50, 4, timeout_ms=60000)
+    assert _same_as_oracle(ref, src, idx, cnt)
+    ctx.serve_stop()
+
+
+def test_device_loop_limits(env):
+    ppr, g = env
+    ctx = ppr.Context(0)
+    G = ctx.load_graph(g.n, g.row_ptr, g.col, g.w)
+    ctx.serve_start(G)
+    with pytest.raises(ppr.PPRError) as ei:
+        ctx.submit(np.arange(10, dtype=np.int32), R=1025)  # the loop's reduction takes R <= 1024
+    assert ei.value.code == ppr.PPR_ERANGE
+    assert ctx.serve_info()["mode"] == ppr.SERVE_DEVICE_LOOP
+    ctx.serve_stop()
+    with pytest.raises(ppr.PPRError):
+        ctx.serve_start(G, mode=2)

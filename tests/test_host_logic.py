@@ -83,13 +83,22 @@ def test_recorded_traffic_needs_the_same_kernel_and_launch(tmp_path, monkeypatch
     prof = tmp_path / "profiles"
     prof.mkdir()
     entry = {"kernel_hash": bench.kernel_source_hash(), "launch": {"refill_lanes": 24},
-             "dram_bytes_per_launch": 123.0}
+             "dram_bytes_per_draw": 123.0}
     (prof / "walker_traffic.json").write_text(json.dumps({"w": entry, "old": dict(entry, kernel_hash="0" * 16)}))
     h = bench.kernel_source_hash()
     monkeypatch.setattr(bench, "ROOT", str(tmp_path))
     monkeypatch.setattr(bench, "kernel_source_hash", lambda: h)
     shape = {"warps_per_block": 0, "chunk_sources": 0, "large_degree": 0, "l2_persist": 0, "refill_lanes": 24}
-    assert bench.recorded_traffic("w", shape) == 123.0
+    assert bench.recorded_traffic("w", shape)["dram_bytes_per_draw"] == 123.0
     assert bench.recorded_traffic("w", dict(shape, refill_lanes=0)) is None  # another launch shape
     assert bench.recorded_traffic("old", shape) is None  # another kernel source
     assert bench.recorded_traffic("missing", shape) is None
+    # the roofline scales the per-draw figure to the launch and reports it as the DRAM fraction
+    r = bench.walker_roofline("w", shape, False, draws=1000, sectors=2500, model_sectors=4000, kernel_ms=1.0,
+                              peak=1000.0, peak_kind="measured")
+    assert r["traffic"] == 123000.0 and abs(r["achieved"] - 123000.0 / 1e-3 / 1e9) < 1e-9
+    assert abs(r["frac"] - r["achieved"] / 1000.0) < 1e-12 and r["basis"].startswith("ncu DRAM")
+    assert abs(r["counted_sector_frac"] - 2500 * 32 / 1e-3 / 1e9 / 1000.0) < 1e-12
+    assert abs(r["flat_csr_model"]["frac"] - 4000 * 32 / 1e-3 / 1e9 / 1000.0) < 1e-12
+    r = bench.walker_roofline("old", shape, False, 1000, 2500, 4000, 1.0, 1000.0, "measured")
+    assert r["traffic"] is None and r["frac"] == r["counted_sector_frac"] and "no current ncu" in r["basis"]
