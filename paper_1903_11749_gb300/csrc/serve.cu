@@ -78,10 +78,12 @@ struct __align__(16) SDesc {
 
 // Counters of a ring slot (device memory; the host writes them before
 // publishing).  claim and agg hold the low 32 bits of (sequence number + 1)
-// above the number of chunks / sources still to hand out: one load tells a
+// above the number of chunks / sources handed out so far: one load tells a
 // warp whether the slot holds the query it looks for and whether work is
-// left, and a warp holding a stale view of the ring cannot take work of a
-// later query that reuses the slot (its compare-and-swap fails on the tag).
+// left, and work is taken with one atomic add (no retries under contention);
+// the tag of the word an add returns says whose work it took, so a warp with
+// a stale view of the ring that lands on a reused slot takes work of the
+// query that holds it now (never work that no one else will do).
 struct __align__(64) SSlot {
     unsigned long long claim;       // chunks still to hand out
     unsigned long long agg;         // sources still to hand to aggregators
@@ -217,11 +219,45 @@ struct WalkChunk {
     uint32_t slot, g0, issued, total, R, T, k0, k1;
 };
 
+// Lane 0: fills *c with chunk ci of the query whose descriptor is in slot s
+// (sequence number + 1 = tag), once that descriptor is in place (the host
+// writes it before the slot's counters; bounded wait).  1, or -1 when the
+// wait ran out.
+__device__ int take_chunk(const LoopParams &P, uint32_t s, uint32_t tag, uint32_t ci, WalkChunk *c)
+{
+    const SDesc *d = P.desc + s;
+    const uint64_t t0 = gtime_ns();
+    while ((uint32_t)__ldcg(&d->seq1) != tag) {
+        if (gtime_ns() - t0 > kSlotWaitNs) {
+            flag_exit(P, PPR_LOOP_SLOT_TIMEOUT);
+            return -1;
+        }
+        __nanosleep(500);
+    }
+    atomicCAS(&P.slot[s].t_claim, 0ull, (unsigned long long)gtime_ns());
+    const uint32_t cw = __ldcg(&d->cw), walks = __ldcg(&d->walks);
+    c->id = __ldcg(&d->seq1) - 1;
+    c->slot = s;
+    c->g0 = ci * cw;
+    c->total = min(cw, walks - ci * cw);
+    c->issued = 0;
+    c->R = __ldcg(&d->R);
+    c->T = __ldcg(&d->T);
+    c->k0 = __ldcg(&d->k0);
+    c->k1 = __ldcg(&d->k1);
+    c->magic = __ldcg(&d->r_magic);
+    c->src = reinterpret_cast<const uint32_t *>(__ldcg(reinterpret_cast<const unsigned long long *>(&d->src)));
+    return 1;
+}
+
 // Whole warp: hands out one chunk of some published query into *c (written by
 // lane 0).  The lanes read the claim words of the queries in [head, tail) in
 // parallel; among those with chunks left the warp takes the start-th (mod
-// their number), so the walker warps share themselves out over the queries
-// in flight.  Returns 1 (a chunk), 0 (none now), -1 (the loop must end: a
+// their number), so the walker warps share themselves out over the queries in
+// flight, and takes the next chunk of it with one atomic add (no retries under
+// contention).  The word's tag says which query the add landed on: if the
+// slot was reused in the meantime, the warp takes the chunk of the query that
+// now holds it.  Returns 1 (a chunk), 0 (none now), -1 (the loop must end: a
 // published slot stayed unwritten).
 __device__ int claim_chunk(const LoopParams &P, uint32_t start, WalkChunk *c, unsigned long long *s_tail)
 {
@@ -240,11 +276,13 @@ __device__ int claim_chunk(const LoopParams &P, uint32_t start, WalkChunk *c, un
             bool o = false;
             if (i < n) {
                 const uint64_t id = h + i;
-                const unsigned long long w = __ldcg(&P.slot[id % kRing].claim);
+                const uint32_t s = (uint32_t)(id % kRing);
+                const unsigned long long w = __ldcg(&P.slot[s].claim);
                 const int rel = tag_rel(w, id);
-                o = rel == 0 && (uint32_t)w > 0;
+                const bool left = rel == 0 && (uint32_t)w < __ldcg(&P.desc[s].nchunks);
+                o = left;
                 if (rel < 0) unwritten = (int)i;
-                if (i == 0 && (rel > 0 || (rel == 0 && (uint32_t)w == 0))) bump(&P.glob->head, h);
+                if (i == 0 && (rel > 0 || (rel == 0 && !left))) bump(&P.glob->head, h);
             }
             ok[r] = __ballot_sync(0xffffffffu, o);
         }
@@ -275,35 +313,19 @@ __device__ int claim_chunk(const LoopParams &P, uint32_t start, WalkChunk *c, un
         }
         int got = 0;
         if (lane == 0) {
-            const uint64_t id = h + i;
-            const uint32_t s = (uint32_t)(id % kRing);
-            unsigned long long cur = __ldcg(&P.slot[s].claim);
-            while (tag_rel(cur, id) == 0 && (uint32_t)cur > 0) {
-                const unsigned long long old = atomicCAS(&P.slot[s].claim, cur, cur - 1);
-                if (old == cur) {
-                    const SDesc *d = P.desc + s;
-                    atomicCAS(&P.slot[s].t_claim, 0ull, (unsigned long long)gtime_ns());
-                    const uint32_t cw = __ldcg(&d->cw), walks = __ldcg(&d->walks);
-                    const uint32_t ci = __ldcg(&d->nchunks) - (uint32_t)cur;
-                    c->id = id;
-                    c->slot = s;
-                    c->g0 = ci * cw;
-                    c->total = min(cw, walks - ci * cw);
-                    c->issued = 0;
-                    c->R = __ldcg(&d->R);
-                    c->T = __ldcg(&d->T);
-                    c->k0 = __ldcg(&d->k0);
-                    c->k1 = __ldcg(&d->k1);
-                    c->magic = __ldcg(&d->r_magic);
-                    c->src = reinterpret_cast<const uint32_t *>(
-                        __ldcg(reinterpret_cast<const unsigned long long *>(&d->src)));
-                    got = 1;
-                    break;
-                }
-                cur = old;
+            const uint32_t s = (uint32_t)((h + i) % kRing);
+            const unsigned long long old = atomicAdd(&P.slot[s].claim, 1ull);
+            const uint32_t tag = (uint32_t)(old >> 32), ci = (uint32_t)old;
+            // the chunk exists if ci is below the chunk count of the query that holds the slot now
+            const SDesc *d = P.desc + s;
+            if (tag != 0) {
+                const uint64_t t0 = gtime_ns();
+                while ((uint32_t)__ldcg(&d->seq1) != tag && gtime_ns() - t0 < kSlotWaitNs) __nanosleep(500);
+                if ((uint32_t)__ldcg(&d->seq1) == tag && ci < __ldcg(&d->nchunks)) got = take_chunk(P, s, tag, ci, c);
             }
         }
-        if (__shfl_sync(0xffffffffu, got, 0)) return 1;
+        got = __shfl_sync(0xffffffffu, got, 0);
+        if (got) return got;
     }
     return 0;
 }
@@ -478,8 +500,8 @@ __device__ void walker_warp(const LoopParams &P, WalkChunk &wc, uint32_t **ends_
 // done.  Returns 1 (query id, slot, source i on every lane), 0 (none now),
 // -1 (the loop must end); *in_flight tells whether published queries still
 // have sources to hand out (ready or not).
-__device__ int claim_source(const LoopParams &P, unsigned long long *s_tail, bool refresh, uint64_t &id_out,
-                            uint32_t &slot_out, uint32_t &i_out, bool &in_flight)
+__device__ int claim_source(const LoopParams &P, unsigned long long *s_tail, bool refresh, uint32_t max_R,
+                            uint64_t &id_out, uint32_t &slot_out, uint32_t &i_out, uint32_t &n_out, bool &in_flight)
 {
     const uint32_t lane = threadIdx.x & 31;
     const uint64_t t = block_tail(P, s_tail, refresh);
@@ -498,12 +520,13 @@ __device__ int claim_source(const LoopParams &P, unsigned long long *s_tail, boo
             const unsigned long long a = __ldcg(&P.slot[s].agg);
             const unsigned long long wd = __ldcg(&P.slot[s].walks_done);
             const uint32_t wk = __ldcg(&P.desc[s].walks);
+            const uint32_t S = __ldcg(&P.desc[s].S);
             const int rel = tag_rel(a, id);
-            const bool has = rel == 0 && (uint32_t)a > 0;
-            o = has && wd >= wk;
+            const bool has = rel == 0 && (uint32_t)a < S;
+            o = has && wd >= wk && __ldcg(&P.desc[s].R) <= max_R;
             left |= has;
             if (rel < 0) unwritten = (int)i;
-            if (i == 0 && (rel > 0 || (rel == 0 && (uint32_t)a == 0))) bump(&P.glob->agg_head, h);
+            if (i == 0 && (rel > 0 || (rel == 0 && !has))) bump(&P.glob->agg_head, h);
         }
         ready[r] = __ballot_sync(0xffffffffu, o);
     }
@@ -521,25 +544,45 @@ __device__ int claim_source(const LoopParams &P, unsigned long long *s_tail, boo
             const uint32_t i = r * 32 + __ffs(m) - 1;
             m &= m - 1;
             int got = 0;
-            uint32_t src_i = 0;
+            uint32_t src_i = 0, take = 0, slot = 0;
+            uint64_t qid = 0;
             if (lane == 0) {
-                const uint64_t id = h + i;
-                const uint32_t s = (uint32_t)(id % kRing);
-                unsigned long long cur = __ldcg(&P.slot[s].agg);
-                while (tag_rel(cur, id) == 0 && (uint32_t)cur > 0) {
-                    const unsigned long long old = atomicCAS(&P.slot[s].agg, cur, cur - 1);
-                    if (old == cur) {
-                        src_i = __ldcg(&P.desc[s].S) - (uint32_t)cur;
+                const uint32_t s = (uint32_t)((h + i) % kRing);
+                const SDesc *d = P.desc + s;
+                const uint32_t S = __ldcg(&d->S);
+                // a batch of sources per claim: a few batches per aggregating warp of the loop
+                const uint32_t batch = max(1u, min(32u, S / (4u * (P.walker_warps / (kLoopWarps - 1)))));
+                const unsigned long long old = atomicAdd(&P.slot[s].agg, (unsigned long long)batch);
+                const uint32_t tag = (uint32_t)(old >> 32), c = (uint32_t)old;
+                // the sources are those of the query that holds the slot now (another one if it was reused)
+                if (tag != 0 && (uint32_t)__ldcg(&d->seq1) == tag) {
+                    const uint32_t S2 = __ldcg(&d->S);
+                    if (c < S2) {
+                        src_i = c;
+                        take = min(batch, S2 - c);
+                        slot = s;
+                        qid = tag - 1;
                         got = 1;
-                        break;
+                        // its walks may still be running if the slot was reused: wait for them (bounded)
+                        const uint64_t t0 = gtime_ns();
+                        while (__ldcg(&P.slot[s].walks_done) < __ldcg(&d->walks)) {
+                            if (gtime_ns() - t0 > kBusyWaitNs) {
+                                flag_exit(P, PPR_LOOP_BUSY_TIMEOUT);
+                                got = -1;
+                                break;
+                            }
+                            __nanosleep(1000);
+                        }
                     }
-                    cur = old;
                 }
             }
-            if (__shfl_sync(0xffffffffu, got, 0)) {
-                id_out = h + i;
-                slot_out = (uint32_t)((h + i) % kRing);
+            got = __shfl_sync(0xffffffffu, got, 0);
+            if (got < 0) return -1;
+            if (got) {
+                id_out = __shfl_sync(0xffffffffu, qid, 0);
+                slot_out = __shfl_sync(0xffffffffu, slot, 0);
                 i_out = __shfl_sync(0xffffffffu, src_i, 0);
+                n_out = __shfl_sync(0xffffffffu, take, 0);
                 return 1;
             }
         }
@@ -548,8 +591,8 @@ __device__ int claim_source(const LoopParams &P, unsigned long long *s_tail, boo
 }
 
 // Reduction of source i of query slot s into its top-k row (host memory).
-// smem: kLoopMaxR endpoints + the reduction's scratch (12 * 1024 bytes).
-__device__ void reduce_source(const LoopParams &P, uint32_t s, uint32_t i, uint32_t *smem)
+// smem: cap endpoints, then the reduction's scratch (3 * cap words); cap >= R.
+__device__ void reduce_source(const LoopParams &P, uint32_t s, uint32_t i, uint32_t *smem, uint32_t cap)
 {
     const uint32_t lane = threadIdx.x & 31;
     const SDesc *d = P.desc + s;
@@ -562,7 +605,7 @@ __device__ void reduce_source(const LoopParams &P, uint32_t s, uint32_t i, uint3
     uint32_t *e = smem;  // the endpoints, read past L1 (the arena is reused by later queries)
     for (uint32_t r = lane; r < R; r += 32) e[r] = __ldcg(ends + (uint64_t)i * R + r);
     __syncwarp();
-    uint32_t *scratch = smem + kLoopMaxR;
+    uint32_t *scratch = smem + cap;
     switch (P2) {
     case 1: case 2: case 4: case 8: case 16: case 32: aggregate_source_reg<1>(e, R, scratch, o, i); break;
     case 64: aggregate_source_reg<2>(e, R, scratch, o, i); break;
@@ -574,6 +617,23 @@ __device__ void reduce_source(const LoopParams &P, uint32_t s, uint32_t i, uint3
     }
 }
 
+// After a warp has written source i's row: counts it; the last source of the
+// query marks it done for the host.
+__device__ void finish_source(const LoopParams &P, uint64_t id, uint32_t s, uint32_t n)
+{
+    __threadfence_system();  // these rows are in host memory before the count says so
+    __syncwarp();
+    if ((threadIdx.x & 31) == 0) {
+        atomicAdd(&P.glob->reduced, (unsigned long long)n);
+        const unsigned long long old = atomicAdd(&P.slot[s].agg_done, (unsigned long long)n);
+        if (old + n == __ldcg(&P.desc[s].S)) {
+            P.slot[s].t_done = gtime_ns();
+            __threadfence_system();
+            st_release_sys(&P.ctl->done[s], id + 1);
+        }
+    }
+}
+
 __device__ void aggregator_warp(const LoopParams &P, uint32_t *smem, unsigned long long *s_tail)
 {
     const uint32_t lane = threadIdx.x & 31;
@@ -582,23 +642,13 @@ __device__ void aggregator_warp(const LoopParams &P, uint32_t *smem, unsigned lo
     bool refresh = true;
     for (;;) {
         uint64_t id = 0;
-        uint32_t s = 0, i = 0;
+        uint32_t s = 0, i = 0, nb = 0;
         bool in_flight = false;
-        const int r = claim_source(P, s_tail, refresh, id, s, i, in_flight);
+        const int r = claim_source(P, s_tail, refresh, kLoopMaxR, id, s, i, nb, in_flight);
         if (r < 0) break;
         if (r > 0) {
-            reduce_source(P, s, i, smem);
-            __threadfence_system();  // this row is in host memory before the count says so
-            __syncwarp();
-            if (lane == 0) {
-                atomicAdd(&P.glob->reduced, 1ull);
-                const unsigned long long old = atomicAdd(&P.slot[s].agg_done, 1ull);
-                if (old + 1 == __ldcg(&P.desc[s].S)) {
-                    P.slot[s].t_done = gtime_ns();
-                    __threadfence_system();
-                    st_release_sys(&P.ctl->done[s], id + 1);
-                }
-            }
+            for (uint32_t b = 0; b < nb; ++b) reduce_source(P, s, i + b, smem, kLoopMaxR);
+            finish_source(P, id, s, nb);
             idle_t0 = busy_t0 = 0;
             backoff = 256;
             refresh = false;
@@ -1054,16 +1104,17 @@ static void scheduler_loop(Server *sv)
                 d.nchunks = (uint32_t)((d.walks + cw - 1) / cw);
                 SSlot &c = sv->h_slot[s];
                 const unsigned long long tag = (unsigned long long)(uint32_t)(f->seq + 1) << 32;
-                c.claim = tag | d.nchunks;
-                c.agg = tag | d.S;
+                c.claim = tag;  // chunks handed out so far (counts up)
+                c.agg = tag;    // sources handed out so far (counts up)
                 c.walks_done = 0;
                 c.agg_done = 0;
                 if (e == cudaSuccess)
                     e = cudaMemcpyAsync((void *)d.src, pin, 4 * (size_t)S, cudaMemcpyHostToDevice, sv->ctl_stream);
-                if (e == cudaSuccess)
-                    e = cudaMemcpyAsync(sv->d_slot + s, &c, sizeof(SSlot), cudaMemcpyHostToDevice, sv->ctl_stream);
+                // the descriptor first: a warp whose claim lands on the new counters finds it in place
                 if (e == cudaSuccess)
                     e = cudaMemcpyAsync(sv->d_desc + s, &d, sizeof(SDesc), cudaMemcpyHostToDevice, sv->ctl_stream);
+                if (e == cudaSuccess)
+                    e = cudaMemcpyAsync(sv->d_slot + s, &c, sizeof(SSlot), cudaMemcpyHostToDevice, sv->ctl_stream);
             }
             if (e == cudaSuccess) e = cudaStreamSynchronize(sv->ctl_stream);
             std::lock_guard<std::mutex> lock(sv->mu);
