@@ -164,18 +164,21 @@ def measured_peaks():
     return 6800.0, "fallback"
 
 
+RENUMBER = {"auto": None, "on": True, "off": False}  # --renumber -> ppr load_graph(renumber=...)
+
+
 def kernel_source_hash():
-    """Hash of the walker's source files (the launch, the step, the layout)."""
+    """Hash of the walker's source files (the launch, the step, the layout, its numbering)."""
     h = hashlib.sha256()
-    for f in ("walk.cu", "walk_step.cuh", "ppr_internal.cuh"):
+    for f in ("walk.cu", "walk_step.cuh", "ppr_internal.cuh", "renumber.cu"):
         h.update(open(os.path.join(ROOT, "paper_1903_11749_gb300", "csrc", f), "rb").read())
     return h.hexdigest()[:16]
 
 
-def recorded_traffic(workload: str, launch: dict):
+def recorded_traffic(workload: str, launch: dict, renumbered: bool = False):
     """The committed ncu DRAM figure of the walker (bytes per draw, read +
     write) for this workload, if it was taken on the current kernel source
-    with the same launch shape; else None."""
+    with the same launch shape and node numbering; else None."""
     p = os.path.join(ROOT, "profiles", "walker_traffic.json")
     if not os.path.exists(p):
         return None
@@ -184,6 +187,8 @@ def recorded_traffic(workload: str, launch: dict):
     if not e or e.get("kernel_hash") != kernel_source_hash():
         return None
     if e.get("launch", {}) != {k: v for k, v in launch.items() if v}:
+        return None
+    if bool(e.get("renumbered", False)) != bool(renumbered):
         return None
     return e
 
@@ -197,7 +202,8 @@ def sample_sources(n: int, every: int, block: int):
     return np.concatenate([np.arange(s, min(n, s + block), dtype=np.int32) for s in starts])
 
 
-def walker_roofline(workload, launch, sampled, draws, sectors, model_sectors, kernel_ms, peak, peak_kind):
+def walker_roofline(workload, launch, sampled, draws, sectors, model_sectors, kernel_ms, peak, peak_kind,
+                    renumbered=False):
     """Roofline of the walker launch.  frac is DRAM-based: the ncu DRAM
     bytes per draw recorded for this kernel source and launch shape, times
     the launch's draws, over the walker's CUDA-event time.  Without a current
@@ -205,7 +211,7 @@ def walker_roofline(workload, launch, sampled, draws, sectors, model_sectors, ke
     s = kernel_ms / 1e3
     counted = sectors * 32.0
     model = model_sectors * 32.0
-    rec = None if sampled else recorded_traffic(workload, launch)
+    rec = None if sampled else recorded_traffic(workload, launch, renumbered)
     if rec is not None:
         traffic = rec["dram_bytes_per_draw"] * draws
         achieved, basis = traffic / s / 1e9, "ncu DRAM bytes (read + write) per draw x draws / walker time"
@@ -549,7 +555,7 @@ def run_serving(args):
     wl = WORKLOADS["serve"]
     g = I.workload_graph("rmat24")
     ctx = ppr.Context(local)
-    G = ctx.load_graph(g.n, g.row_ptr, g.col, g.w)
+    G = ctx.load_graph(g.n, g.row_ptr, g.col, g.w, renumber=RENUMBER[args.renumber])
     rng = np.random.Generator(np.random.PCG64(777))
     smax = 100_000
     n_warm, n_meas = args.serve_warmup, args.serve_queries
@@ -821,6 +827,8 @@ def main():
                     help="graph workloads: launch shape from the autotuner (cached) instead of the workload's")
     ap.add_argument("--l2-persist", type=int, default=0, choices=[0, 1],
                     help="walker launches keep the node records persisting in L2")
+    ap.add_argument("--renumber", default="auto", choices=["auto", "on", "off"],
+                    help="layout node numbering: by in-degree (on), the generator's (off), or the library's choice")
     ap.add_argument("--serve-queries", type=int, default=2000)
     ap.add_argument("--serve-warmup", type=int, default=200)
     ap.add_argument("--serve-streams", type=int, default=4)
@@ -860,6 +868,7 @@ def main():
     torch.cuda.set_device(local)
     dev = torch.device("cuda", local)
     wl = WORKLOADS[args.workload]
+    renum = RENUMBER[args.renumber]
     g = I.workload_graph(base_graph(args.workload))
     a, b, rank_tag = rank_workload(g.n, rank, world)
     tune = dict(warps_per_block=args.warps_per_block, chunk_sources=args.chunk_sources,
@@ -881,7 +890,7 @@ def main():
         tune.update(wl.get("launch", {}))
     if args.tune:
         from paper_1903_11749_gb300 import tune as tuner
-        Gt = ctx.load_graph(g.n, d_rp, d_col, d_w, stream=stream, m=g.m)
+        Gt = ctx.load_graph(g.n, d_rp, d_col, d_w, stream=stream, m=g.m, renumber=renum)
         t0 = time.perf_counter()
         tuning = tuner.tuned(Gt, torch.cuda.get_device_name(dev), sample_sources=400_000, alpha=wl["alpha"], R=wl["R"],
                              seed=wl["seed"], topk=wl["topk"], segments=wl["segments"], sampler=wl.get("sampler", 0))
@@ -892,7 +901,7 @@ def main():
     sample = sample_sources(b, args.sample_every, args.sample_block) if args.sample_every > 0 else None
 
     def step(kernel=ppr.KERNEL_PERSISTENT, stats=False):
-        G = ctx.load_graph(g.n, d_rp, d_col, d_w, stream=stream, m=g.m)
+        G = ctx.load_graph(g.n, d_rp, d_col, d_w, stream=stream, m=g.m, renumber=renum)
         kw = dict(alpha=wl["alpha"], R=wl["R"], seed=wl["seed"], tag=rank_tag, topk=wl["topk"],
                   segments=wl["segments"], kernel=kernel, stats=stats, stream=stream, wait=False,
                   sampler=wl.get("sampler", 0), **tune)
@@ -908,6 +917,7 @@ def main():
     info0 = r0.info()
     draws_per_pass, sectors_per_pass, walks_per_pass = int(info0.steps), int(info0.sectors), int(info0.walks)
     model_per_pass = int(info0.model_sectors)
+    renumbered = bool(G0.info().renumbered)
     # walk steps of one pass: the counted steps; with segment tables one draw
     # stands for up to three steps, so the plain-equivalent count walks * 2^32/T
     # (the expected number of steps) is used instead
@@ -992,7 +1002,7 @@ def main():
         def e2e_once(pipelined):
             torch.cuda.synchronize(dev)
             t0 = time.perf_counter()
-            G = ctx.load_graph(g.n, h_rp, h_col, h_w, stream=stream, m=g.m)
+            G = ctx.load_graph(g.n, h_rp, h_col, h_w, stream=stream, m=g.m, renumber=renum)
             if pipelined:  # rows and top-k copied to the host batch by batch, behind the walks
                 nnz, _ = G.run_to_host(o_rp, o_col, o_cnt, *ti_arg, **run_kw)
             else:  # run, then read everything back
@@ -1027,12 +1037,12 @@ def main():
     peak, peak_kind = measured_peaks()
     kms = statistics.mean(kernel_ms)
     roofline = walker_roofline(args.workload, tune, sample is not None, draws_per_pass, sectors_per_pass,
-                               model_per_pass, kms, peak, peak_kind)
+                               model_per_pass, kms, peak, peak_kind, renumbered)
     roofline["walk_and_reduce_ms"] = statistics.mean(run_ms)
 
     # practical ceilings: dependent random 32-byte sector reads over a buffer
     # the size of the walked layout, and Philox draws with no memory traffic
-    G = ctx.load_graph(g.n, d_rp, d_col, d_w, stream=stream, m=g.m)
+    G = ctx.load_graph(g.n, d_rp, d_col, d_w, stream=stream, m=g.m, renumber=renum)
     if wl.get("sampler", 0) == 1:
         G.run(alpha=wl["alpha"], R=1, seed=1, src_begin=0, src_end=1, sampler=1, stream=stream)  # alias tables
     footprint = max(int(G.info().device_bytes), 64 << 20)
@@ -1061,7 +1071,8 @@ def main():
                 "config": {"workload": args.workload, "desc": wl["desc"], "alpha": wl["alpha"], "R": wl["R"],
                            "topk": wl["topk"], "n": g.n, "m": g.m, "sources": g.n,
                            "parallelism": f"{world} independent replicas (tag = rank)" if world > 1 else "1 GPU",
-                           "l2": "flushed between steps (512 MB write)", "launch": tune, "tuning": tuning},
+                           "l2": "flushed between steps (512 MB write)", "launch": tune, "tuning": tuning,
+                           "numbering": args.renumber, "renumbered": renumbered},
                 "step_ms_each": step_ms, "ms_per_step_median": statistics.median(step_ms), "walks_per_s": walks_s,
                 "steps_per_walk": steps_per_pass / max(walks_per_pass, 1),
                 "draws_per_s": draws_per_pass * args.steps * world / T_max,

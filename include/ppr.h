@@ -65,6 +65,16 @@ enum {
 
 /* flags */
 #define PPR_PTRS_DEVICE 0x1u /* pointer arguments are device pointers */
+/* Node numbering of the device layout (ppr_load_graph; plain graphs only).
+ * With PPR_RENUMBER the layout numbers nodes by descending in-degree (eight
+ * classes per power of two, ties in caller order) so that the records and
+ * rows of the most visited nodes are contiguous; PPR_KEEP_IDS keeps the
+ * caller's order; with neither, the layout renumbers when its node records
+ * (32 bytes a node) exceed twice the device's L2.  The numbering is internal:
+ * sources, rows and top-k use the caller's ids, walks draw by the caller's
+ * source id, and every result is the same either way. */
+#define PPR_RENUMBER 0x2u
+#define PPR_KEEP_IDS 0x4u
 
 /* Documented limits. */
 #define PPR_MAX_NODES 2147483647LL        /* n < 2^31 */
@@ -127,7 +137,9 @@ int ppr_device_sms(const ppr_ctx *ctx);
  *   row_ptr  int64[n+1], row_ptr[0] = 0, non-decreasing, row_ptr[n] = m
  *   col      int32[m], each in [0, n)      (edge targets, row order kept)
  *   w        uint32[m], each >= 1          (integer edge weights)
- *   flags    PPR_PTRS_DEVICE if the three arrays are device pointers
+ *   flags    PPR_PTRS_DEVICE if the three arrays are device pointers;
+ *            PPR_RENUMBER or PPR_KEEP_IDS (not both) to force the layout's
+ *            node numbering (above)
  *   stream   cudaStream_t for the build, or NULL for the legacy stream
  * Errors: PPR_EINVAL (malformed CSR, col out of range, w = 0),
  *         PPR_ERANGE (n, m or an out-degree beyond the limits), PPR_ENOMEM.
@@ -158,6 +170,8 @@ typedef struct {
     int64_t device_bytes;    /* device memory held by the graph */
     int64_t segment_nodes;   /* nodes with a segment table (last built threshold) */
     int64_t segment_entries;
+    int32_t renumbered;      /* 1 if the layout numbers nodes by in-degree (PPR_RENUMBER) */
+    int32_t reserved;
 } ppr_graph_info;
 
 int ppr_graph_get_info(const ppr_graph *g, ppr_graph_info *info);

@@ -18,15 +18,22 @@ struct AggOut {
     int32_t topk;
 };
 
+// Caller id of an endpoint the walker wrote in the layout's numbering
+// (order: the renumbered layout's order array, else null).
+__device__ __forceinline__ uint32_t caller_id(const int32_t *order, uint32_t v)
+{
+    return order ? (uint32_t)order[v] : v;
+}
+
 // ends: the R endpoints of one source (shared memory).  sortbuf: next_pow2(R)
 // uint32 and keys: next_pow2(R) uint64 of per-warp shared scratch.  Writes
 // row `out_row` of the outputs.  All 32 lanes call it.
 __device__ inline void aggregate_source(const uint32_t *ends, uint32_t R, uint32_t *sortbuf, uint64_t *keys,
-                                        const AggOut &o, uint64_t out_row)
+                                        const AggOut &o, uint64_t out_row, const int32_t *order = nullptr)
 {
     const uint32_t lane = threadIdx.x & 31;
     const uint32_t P2 = next_pow2(R);
-    for (uint32_t i = lane; i < P2; i += 32) sortbuf[i] = i < R ? ends[i] : 0xffffffffu;
+    for (uint32_t i = lane; i < P2; i += 32) sortbuf[i] = i < R ? caller_id(order, ends[i]) : 0xffffffffu;
     __syncwarp();
     warp_bitonic_sort(sortbuf, P2);
     // One run per distinct endpoint.  A run is found at its last element;
@@ -179,7 +186,7 @@ __device__ __forceinline__ void topk_select_reg(const uint32_t (&kv)[E], uint32_
 // scratch: 3 * R uint32 of per-warp shared memory
 template <int E>
 __device__ inline void aggregate_source_reg(const uint32_t *ends, uint32_t R, uint32_t *scratch, const AggOut &o,
-                                            uint64_t out_row)
+                                            uint64_t out_row, const int32_t *order = nullptr)
 {
     const uint32_t lane = threadIdx.x & 31;
     uint32_t *start_pos = scratch, *run_id = scratch + R, *kbuf = scratch + 2 * R;
@@ -188,6 +195,11 @@ __device__ inline void aggregate_source_reg(const uint32_t *ends, uint32_t R, ui
     for (int e = 0; e < E; ++e) {
         const uint32_t i = (uint32_t)e * 32 + lane;
         v[e] = i < R ? ends[i] : 0xffffffffu;
+    }
+    if (order) {
+#pragma unroll
+        for (int e = 0; e < E; ++e)
+            if ((uint32_t)e * 32 + lane < R) v[e] = (uint32_t)order[v[e]];
     }
     warp_sort_reg<E>(v);
     const uint64_t rbase = out_row * o.cap;
@@ -266,6 +278,7 @@ struct AggParams {
     int64_t S;
     int64_t out_row0;   // output row of the first source
     AggOut out;
+    const int32_t *order;  // renumbered layout: caller id of an internal node, else null
 };
 
 // E > 0: register-resident reduction for next_pow2(R) = 32 * E; E = 0:
@@ -281,11 +294,11 @@ __global__ void __launch_bounds__(128) k_aggregate(AggParams p)
     for (uint64_t i = (uint64_t)blockIdx.x * nw + wid; i < S; i += (uint64_t)gridDim.x * nw) {
         if constexpr (E > 0) {
             aggregate_source_reg<E>(p.ends + i * p.R, p.R, reinterpret_cast<uint32_t *>(scratch), p.out,
-                                    (uint64_t)p.out_row0 + i);
+                                    (uint64_t)p.out_row0 + i, p.order);
         } else {
             uint64_t *keys = reinterpret_cast<uint64_t *>(scratch);
             aggregate_source(p.ends + i * p.R, p.R, reinterpret_cast<uint32_t *>(keys + p.P2), keys, p.out,
-                             (uint64_t)p.out_row0 + i);
+                             (uint64_t)p.out_row0 + i, p.order);
         }
     }
 }

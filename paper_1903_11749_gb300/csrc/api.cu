@@ -206,6 +206,8 @@ int ppr_create(int device, ppr_ctx **out)
     c->l2_persist_max = (size_t)v;
     cudaDeviceGetAttribute(&v, cudaDevAttrMaxAccessPolicyWindowSize, device);
     c->l2_window_max = (size_t)v;
+    cudaDeviceGetAttribute(&v, cudaDevAttrL2CacheSize, device);
+    c->l2_bytes = (size_t)v;
     ppr::preload_run_kernels();
     {
         cudaFuncAttributes fa;
@@ -249,8 +251,16 @@ static int load_common(ppr_ctx *ctx, int64_t n, int64_t m, const int64_t *row_pt
         set_error("row_ptr, col and w must be non-NULL");
         return PPR_EINVAL;
     }
-    if (flags & ~PPR_PTRS_DEVICE) {
+    if (flags & ~(PPR_PTRS_DEVICE | PPR_RENUMBER | PPR_KEEP_IDS)) {
         set_error("unknown flags 0x%x", flags);
+        return PPR_EINVAL;
+    }
+    if ((flags & PPR_RENUMBER) && (flags & PPR_KEEP_IDS)) {
+        set_error("PPR_RENUMBER and PPR_KEEP_IDS exclude each other");
+        return PPR_EINVAL;
+    }
+    if ((flags & PPR_RENUMBER) && g->instances > 0) {
+        set_error("PPR_RENUMBER applies to plain graphs (batched instances keep their numbering)");
         return PPR_EINVAL;
     }
     int rc = set_device(ctx);
@@ -261,7 +271,10 @@ static int load_common(ppr_ctx *ctx, int64_t n, int64_t m, const int64_t *row_pt
     g->n = n;
     g->m = m;
     g->stream = (cudaStream_t)stream;
-    return build_graph(ctx, n, m, row_ptr, col, w, (flags & PPR_PTRS_DEVICE) != 0, (cudaStream_t)stream, g);
+    // node records of 32 bytes: renumber when they would take more than twice the L2
+    const bool renumber = g->instances == 0 && ((flags & PPR_RENUMBER) != 0 ||
+                                                ((flags & PPR_KEEP_IDS) == 0 && (uint64_t)n * 32 > 2 * ctx->l2_bytes));
+    return build_graph(ctx, n, m, row_ptr, col, w, (flags & PPR_PTRS_DEVICE) != 0, renumber, (cudaStream_t)stream, g);
 }
 
 int ppr_load_graph(ppr_ctx *ctx, int64_t n, int64_t m, const int64_t *row_ptr, const int32_t *col,
@@ -333,6 +346,8 @@ int ppr_graph_get_info(const ppr_graph *g, ppr_graph_info *info)
     info->device_bytes = g->device_bytes;
     info->segment_nodes = g->seg.nodes;
     info->segment_entries = g->seg.entries_n;
+    info->renumbered = g->order ? 1 : 0;
+    info->reserved = 0;
     return PPR_OK;
 }
 
@@ -348,6 +363,8 @@ void ppr_free_graph(ppr_graph *g)
     dev_free(g->seg.node, g->stream);
     dev_free(g->seg.entries, g->stream);
     dev_free(g->d_node_off, g->stream);
+    dev_free(g->order, g->stream);
+    dev_free(g->rank, g->stream);
     dev_free(g->alias.node, g->stream);
     dev_free(g->alias.slots, g->stream);
     cudaGetLastError();  // a failed free must not surface in a later call

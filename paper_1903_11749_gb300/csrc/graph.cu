@@ -180,13 +180,15 @@ __device__ __forceinline__ void block_stats(LayoutStats *st, uint32_t deg_max, u
     }
 }
 
-__global__ void __launch_bounds__(256) k_layout(int64_t n, int64_t m, const int64_t *row_ptr, uint32_t *sizes,
-                                                LayoutStats *st, uint2 *huge, uint32_t huge_cap)
+// order: the caller's row of internal node u (renumbered layout), or null.
+__global__ void __launch_bounds__(256) k_layout(int64_t n, int64_t m, const int64_t *row_ptr, const int32_t *order,
+                                                uint32_t *sizes, LayoutStats *st, uint2 *huge, uint32_t huge_cap)
 {
     uint32_t dmax = 0, dang = 0, flags = 0;
     for (int64_t u = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; u < n; u += (int64_t)gridDim.x * blockDim.x) {
-        const int64_t a = row_ptr[u], b = row_ptr[u + 1];
-        const bool bad = a < 0 || b < a || b > m || (u == 0 && a != 0) || (u == n - 1 && b != m);
+        const int64_t o = order ? (int64_t)order[u] : u;
+        const int64_t a = row_ptr[o], b = row_ptr[o + 1];
+        const bool bad = a < 0 || b < a || b > m || (o == 0 && a != 0) || (o == n - 1 && b != m);
         uint32_t sz = 0;
         if (bad) {
             flags |= kBadRowPtr;
@@ -219,7 +221,14 @@ struct BuildArgs {
     EdgeN *E;
     LayoutStats *st;
     uint32_t *list;  // mid rows from the front, big rows from the back
+    const int32_t *order;  // renumbered layout: caller row of internal node u, else null
+    const int32_t *rank;   // renumbered layout: internal id of caller node v, else null
 };
+
+// Input row (caller numbering) of internal node u, and the internal id of a
+// target the caller numbered c (c already checked to lie in [0, n)).
+__device__ __forceinline__ int64_t in_row(const BuildArgs &A, int64_t u) { return A.order ? (int64_t)A.order[u] : u; }
+__device__ __forceinline__ int64_t map_col(const BuildArgs &A, int64_t c) { return A.rank ? (int64_t)A.rank[c] : c; }
 
 // u32 slot of key i of level l of a blocked row (region reg, degree d, L levels)
 __device__ __forceinline__ uint64_t key_slot(uint64_t reg, uint32_t d, uint32_t L, uint32_t l, uint32_t i)
@@ -306,6 +315,7 @@ __device__ __forceinline__ EdgeRun load_run(const BuildArgs &A, int64_t a, uint3
         if (i0 + q < d) {
             if (r.w[q] == 0) flags |= kBadWeight;
             if (r.c[q] < 0 || (int64_t)r.c[q] >= hi_id) flags |= kBadCol;
+            else if (A.rank) r.c[q] = A.rank[r.c[q]];
         }
         r.sum += r.w[q];
     }
@@ -340,8 +350,9 @@ __global__ void __launch_bounds__(256) k_build_small(BuildArgs A)
     uint32_t *K = reinterpret_cast<uint32_t *>(A.E);
     uint32_t flags = 0;
     for (int64_t u = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; u < A.n; u += (int64_t)gridDim.x * blockDim.x) {
-        const int64_t a = A.row_ptr[u];
-        const uint32_t d = (uint32_t)(A.row_ptr[u + 1] - a);
+        const int64_t o = in_row(A, u);
+        const int64_t a = A.row_ptr[o];
+        const uint32_t d = (uint32_t)(A.row_ptr[o + 1] - a);
         if (d > kSmallRow) {
             if (d <= kMidRow) A.list[atomicAdd(&A.st->n_mid, 1u)] = (uint32_t)u;
             else if (d <= kHugeRow) A.list[A.n - 1 - atomicAdd(&A.st->n_big, 1u)] = (uint32_t)u;
@@ -356,9 +367,10 @@ __global__ void __launch_bounds__(256) k_build_small(BuildArgs A)
         uint32_t first = 0;
         for (uint32_t i = 0; i < d; ++i) {
             const uint32_t wi = A.w[a + i];
-            const int64_t c = A.col[a + i];
+            int64_t c = A.col[a + i];
             if (wi == 0) flags |= kBadWeight;
             if (c < 0 || c >= hi_id) flags |= kBadCol;
+            else c = map_col(A, c);
             P += wi;
             if (i == 0) first = (uint32_t)(c + base_id);
             if (d >= 2) {
@@ -394,8 +406,9 @@ __global__ void __launch_bounds__(256) k_build_mid(BuildArgs A)
     const uint32_t nmid = A.st->n_mid;
     for (int64_t t = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5; t < nmid; t += warps) {
         const int64_t u = A.list[t];
-        const int64_t a = A.row_ptr[u];
-        const uint32_t d = (uint32_t)(A.row_ptr[u + 1] - a);
+        const int64_t o = in_row(A, u);
+        const int64_t a = A.row_ptr[o];
+        const uint32_t d = (uint32_t)(A.row_ptr[o + 1] - a);
         int64_t hi_id;
         const int64_t base_id = instance_base(A, u, hi_id);
         const uint64_t reg = A.region[u];
@@ -433,8 +446,9 @@ __global__ void __launch_bounds__(512) k_build_big(BuildArgs A)
     const uint32_t nbig = A.st->n_big;
     for (uint32_t t = blockIdx.x; t < nbig; t += gridDim.x) {
         const int64_t u = A.list[A.n - 1 - t];
-        const int64_t a = A.row_ptr[u];
-        const uint32_t d = (uint32_t)(A.row_ptr[u + 1] - a);
+        const int64_t o = in_row(A, u);
+        const int64_t a = A.row_ptr[o];
+        const uint32_t d = (uint32_t)(A.row_ptr[o + 1] - a);
         int64_t hi_id;
         const int64_t base_id = instance_base(A, u, hi_id);
         const uint64_t reg = A.region[u];
@@ -510,7 +524,7 @@ __global__ void __launch_bounds__(256) k_build_tile_totals(BuildTiles T)
     const BuildArgs &A = T.A;
     const uint2 tl = T.tiles[blockIdx.x];
     const uint4 rw = T.rows[tl.x];
-    const int64_t a = A.row_ptr[rw.x];
+    const int64_t a = A.row_ptr[in_row(A, rw.x)];
     int64_t hi_id;
     instance_base(A, rw.x, hi_id);
     const uint32_t end = min(tl.y + kBuildTile, rw.y);
@@ -562,7 +576,7 @@ __global__ void __launch_bounds__(256) k_build_tile_write(BuildTiles T)
     const uint2 tl = T.tiles[blockIdx.x];
     const uint4 rw = T.rows[tl.x];
     const uint32_t d = rw.y;
-    const int64_t a = A.row_ptr[rw.x];
+    const int64_t a = A.row_ptr[in_row(A, rw.x)];
     int64_t hi_id;
     const int64_t base_id = instance_base(A, rw.x, hi_id);
     const uint64_t reg = A.region[rw.x];
@@ -587,9 +601,10 @@ __global__ void __launch_bounds__(256) k_build_tile_write(BuildTiles T)
     uint64_t P = T.tile_sum[blockIdx.x] + before + v - own;
     for (uint32_t i = lo; i < hi; ++i) {
         P += A.w[a + i];
+        const int64_t c = A.col[a + i];  // checked by k_build_tile_totals (the build fails if it is out of range)
         EdgeN r;
         r.P = (uint32_t)P;
-        r.col = (int32_t)(A.col[a + i] + base_id);
+        r.col = (int32_t)((c >= 0 && c < hi_id ? map_col(A, c) : c) + base_id);
         A.E[eb + i] = r;
         if ((i & 7) == 7 || i == d - 1) K[key_slot(reg, d, L, 1, i >> 3)] = (uint32_t)P;
     }
@@ -646,7 +661,7 @@ static int build_narrow(ppr_ctx *ctx, int64_t n, int64_t m, const int64_t *d_rp,
     cudaError_t e = cudaMemsetAsync(d_ls, 0, sizeof(LayoutStats), st);
     if (e != cudaSuccess) return cuda_fail(e, "memset");
     const int tblocks = (int)std::max<int64_t>(1, std::min<int64_t>((n + 255) / 256, (int64_t)ctx->sms * 16));
-    k_layout<<<tblocks, 256, 0, st>>>(n, m, d_rp, d_sizes, d_ls, d_huge, huge_cap);
+    k_layout<<<tblocks, 256, 0, st>>>(n, m, d_rp, g->order, d_sizes, d_ls, d_huge, huge_cap);
     note_launch();
     exclusive_scan_u32(d_sizes, n, d_region, d_scan, st);
     LayoutStats hs;
@@ -675,7 +690,7 @@ static int build_narrow(ppr_ctx *ctx, int64_t n, int64_t m, const int64_t *d_rp,
     g->edge_records = (int64_t)slots;
     g->device_bytes = (int64_t)(sizeof(NodeRecN) * n + edge_bytes);
     BuildArgs A{n, d_rp, d_col, d_w, d_off, g->instances, d_region, static_cast<NodeRecN *>(g->node),
-                (EdgeN *)g->edges, d_ls, d_list};
+                (EdgeN *)g->edges, d_ls, d_list, g->order, g->rank};
     k_build_small<<<tblocks, 256, 0, st>>>(A);
     note_launch();
     k_build_mid<<<ctx->sms * 8, 256, 0, st>>>(A);
@@ -742,7 +757,7 @@ static int build_narrow(ppr_ctx *ctx, int64_t n, int64_t m, const int64_t *d_rp,
 }
 
 int build_graph(ppr_ctx *ctx, int64_t n, int64_t m, const int64_t *row_ptr, const int32_t *col,
-                const uint32_t *w, bool device_ptrs, cudaStream_t st, ppr_graph *g)
+                const uint32_t *w, bool device_ptrs, bool renumber, cudaStream_t st, ppr_graph *g)
 {
     const int64_t *d_rp = row_ptr;
     const int32_t *d_col = col;
@@ -782,11 +797,24 @@ int build_graph(ppr_ctx *ctx, int64_t n, int64_t m, const int64_t *row_ptr, cons
                                         cudaMemcpyHostToDevice, st);
         if (e != cudaSuccess) return cleanup(), cuda_fail(e, "node_off upload");
     }
+    if (renumber && g->instances == 0) {
+        if ((rc = dev_alloc((void **)&g->order, sizeof(int32_t) * n, "node order", st)) ||
+            (rc = dev_alloc((void **)&g->rank, sizeof(int32_t) * n, "node rank", st)) ||
+            (rc = renumber_by_indegree(ctx, n, m, d_col, st, g->order, g->rank, tmp)))
+            return cleanup(), rc;
+        g->device_bytes_extra = (int64_t)(2 * sizeof(int32_t) * n);
+    }
     rc = build_narrow(ctx, n, m, d_rp, d_col, d_w, d_off, st, g, tmp);
     if (rc != 1) {
+        if (rc == PPR_OK) g->device_bytes += g->device_bytes_extra;
         cleanup();
         return rc;
     }
+    // the wide layout keeps the caller's numbering
+    dev_free(g->order, st);
+    dev_free(g->rank, st);
+    g->order = g->rank = nullptr;
+    g->device_bytes_extra = 0;
     // some row total reaches 2^32: 64-bit prefixes in flat rows
     void *p;
     if ((rc = dev_alloc(&p, sizeof(uint64_t) * n, "row totals", st))) return cleanup(), rc;
@@ -923,6 +951,7 @@ struct SegHash {
     unsigned long long val[SLOTS];
     uint16_t used[SLOTS];          // claimed slots, in claim order
     unsigned long long sk[kSegMaxOut], sq[kSegMaxOut];  // compacted, then ranked outcomes
+    unsigned long long so[kSegMaxOut];  // renumbered layout: the keys with the caller's node ids (ranking)
     unsigned int count;
     unsigned int full;  // a probe found no slot (cannot happen when the scan's count is right): no table
 };
@@ -1011,10 +1040,19 @@ __device__ __forceinline__ void seg_insert(SegHash<SLOTS> *h, uint32_t node, uin
 // Tables of the nodes of one tier of `list`; SLOTS is above the tier's
 // largest raw count.  Each warp's hash table is cleared once and restored
 // slot by slot after each node.
+// An outcome key with its node field replaced by the caller's id of that node.
+__device__ __forceinline__ unsigned long long seg_key_caller(unsigned long long k, const int32_t *order)
+{
+    const uint32_t node = (uint32_t)((k >> 8) & 0x7fffffffull);
+    return (k & ~(0x7fffffffull << 8)) | ((unsigned long long)(uint32_t)order[node] << 8);
+}
+
+// order: the renumbered layout's order array (the canonical order ranks
+// outcomes by the caller's node ids), or null.
 template <class E, int SLOTS, int WARPS>
 __global__ void __launch_bounds__(32 * WARPS) k_seg_fill(RowView<E> G, uint32_t T, const uint32_t *list, int tier,
                                                          int64_t n, SegCounters *ct, SegEntry *ent,
-                                                         typename E::Node *seg_node)
+                                                         typename E::Node *seg_node, const int32_t *order)
 {
     extern __shared__ __align__(16) unsigned char smem_raw[];
     SegHash<SLOTS> *h = reinterpret_cast<SegHash<SLOTS> *>(smem_raw) + (threadIdx.x >> 5);
@@ -1100,16 +1138,24 @@ __global__ void __launch_bounds__(32 * WARPS) k_seg_fill(RowView<E> G, uint32_t 
             __syncwarp();
             continue;
         }
-        // canonical order: rank of each key among the K distinct keys
-        unsigned long long mk[2], mq[2];
+        // canonical order: rank of each key among the K distinct keys (node
+        // ids as the caller numbers them)
+        unsigned long long mk[2], mq[2], mo[2];
         uint32_t rk[2];
 #pragma unroll
         for (int e = 0; e < 2; ++e) {
             const uint32_t i = (uint32_t)e * 32 + lane;
             mk[e] = i < K ? h->sk[i] : ~0ull;
             mq[e] = i < K ? h->sq[i] : 0ull;
+            mo[e] = (order && i < K) ? seg_key_caller(mk[e], order) : mk[e];
+            if (order && i < K) h->so[i] = mo[e];
+        }
+        __syncwarp();
+        const unsigned long long *cmp = order ? h->so : h->sk;
+#pragma unroll
+        for (int e = 0; e < 2; ++e) {
             uint32_t r = 0;
-            for (uint32_t j = 0; j < K; ++j) r += h->sk[j] < mk[e];
+            for (uint32_t j = 0; j < K; ++j) r += cmp[j] < mo[e];
             rk[e] = r;
         }
         __syncwarp();
@@ -1186,7 +1232,8 @@ static int seg_build_typed(ppr_graph *g, uint32_t T, cudaStream_t st, const RowV
         PPR_CUDA(cudaFuncSetAttribute(k_seg_fill<E, 2 * kSegSmallRaw, W>, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                       (int)smem));
         const int fb = (int)std::min<int64_t>((hc.listed[0] + W - 1) / W, (int64_t)g->ctx->sms * 16);
-        k_seg_fill<E, 2 * kSegSmallRaw, W><<<fb, 32 * W, smem, st>>>(G, T, list, 0, n, d_ct, g->seg.entries, seg_node);
+        k_seg_fill<E, 2 * kSegSmallRaw, W><<<fb, 32 * W, smem, st>>>(G, T, list, 0, n, d_ct, g->seg.entries, seg_node,
+                                                                     g->order);
         note_launch();
     }
     if (hc.listed[1]) {
@@ -1195,7 +1242,8 @@ static int seg_build_typed(ppr_graph *g, uint32_t T, cudaStream_t st, const RowV
         PPR_CUDA(cudaFuncSetAttribute(k_seg_fill<E, kSegLargeSlots, W>, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                       (int)smem));
         const int fb = (int)std::min<int64_t>((hc.listed[1] + W - 1) / W, (int64_t)g->ctx->sms * 8);
-        k_seg_fill<E, kSegLargeSlots, W><<<fb, 32 * W, smem, st>>>(G, T, list, 1, n, d_ct, g->seg.entries, seg_node);
+        k_seg_fill<E, kSegLargeSlots, W><<<fb, 32 * W, smem, st>>>(G, T, list, 1, n, d_ct, g->seg.entries, seg_node,
+                                                                   g->order);
         note_launch();
     }
     PPR_CUDA(cudaGetLastError());

@@ -62,6 +62,7 @@ struct ppr_ctx {
     size_t l2_persist_max = 0;    // device limits for L2 access-policy windows
     size_t l2_window_max = 0;
     size_t l2_persist_set = 0;    // persisting set-aside this context asked for
+    size_t l2_bytes = 0;          // L2 size (the layout's renumbering policy)
     cudaStream_t copy_stream = nullptr;  // output copies of ppr_run_to_host
     unsigned long long *pinned = nullptr;  // page-locked words for per-batch totals
     std::atomic<int> refs{1};  // the caller's handle plus every live graph and result
@@ -83,6 +84,10 @@ struct ppr_graph {
     void *node = nullptr;   // NodeRecN[n] (narrow layout) or NodeRec[n] (wide layout)
     void *edges = nullptr;  // EdgeN[m] or EdgeW[m]
     int64_t edge_records = 0;  // records the edge layout holds (blocked narrow rows: with padding)
+    // internal numbering of the layout (renumber.cu), or null: caller ids
+    int32_t *order = nullptr;  // [n] caller id of internal node i
+    int32_t *rank = nullptr;   // [n] internal id of caller node v
+    int64_t device_bytes_extra = 0;  // order and rank
     // block-diagonal instances
     int32_t instances = 0;
     std::vector<int64_t> node_off;  // host copy, count+1
@@ -122,7 +127,10 @@ namespace ppr {
 
 // graph.cu
 int build_graph(ppr_ctx *ctx, int64_t n, int64_t m, const int64_t *row_ptr, const int32_t *col,
-                const uint32_t *w, bool device_ptrs, cudaStream_t st, ppr_graph *g);
+                const uint32_t *w, bool device_ptrs, bool renumber, cudaStream_t st, ppr_graph *g);
+// renumber.cu: order and rank of the in-degree numbering (see ppr_graph)
+int renumber_by_indegree(ppr_ctx *ctx, int64_t n, int64_t m, const int32_t *d_col, cudaStream_t st, int32_t *order,
+                         int32_t *rank, std::vector<void *> &tmp);
 int build_segments(ppr_graph *g, uint32_t T, cudaStream_t st);
 int build_alias(ppr_graph *g, cudaStream_t st);
 

@@ -346,6 +346,7 @@ __device__ void walker_warp(const LoopParams &P, WalkChunk &wc, uint32_t **ends_
     const E edges = make_edges<E>(P.kp.edges);
     bool active = false;
     uint32_t q = 0, g = 0, src = 0, j = 0, k = 0, u = 0;
+    uint32_t s0 = 0;  // the walk's start (and restart) node in the layout's numbering
     StepKey key{0, 0, 0};
     uint32_t pend_q = 0xffffffffu, pend_n = 0;  // uniform: walks of pend_q finished, not yet counted
     bool have = false;                          // uniform: wc holds walks left to issue
@@ -416,11 +417,12 @@ __device__ void walker_warp(const LoopParams &P, WalkChunk &wc, uint32_t **ends_
                 g = wc.g0 + issued + rank;
                 const uint32_t pos = (uint32_t)(((uint64_t)g * wc.magic) >> 40);
                 j = g - pos * wc.R;
-                src = __ldcg(wc.src + pos);
+                src = __ldcg(wc.src + pos);  // the caller's id keys the draws
+                s0 = P.kp.rank ? (uint32_t)P.kp.rank[src] : src;
                 q = wc.slot;
                 key = StepKey{wc.k0, wc.k1, wc.T};
                 k = 0;
-                u = src;
+                u = s0;
                 active = true;
             }
             __syncwarp();
@@ -461,7 +463,7 @@ __device__ void walker_warp(const LoopParams &P, WalkChunk &wc, uint32_t **ends_
         uint32_t end = 0;
         bool fin = false;
         const long long c0 = clock64();
-        if (walk_step<E, false, false, false>(P.kp, key, edges, active, src, src, j, 0, k, u, end, tl)) {
+        if (walk_step<E, false, false, false>(P.kp, key, edges, active, s0, src, j, 0, k, u, end, tl)) {
             ends_of[q][g] = end;
             active = false;
             fin = true;
@@ -603,7 +605,7 @@ __device__ void reduce_source(const LoopParams &P, uint32_t s, uint32_t i, uint3
     o.topk_cnt = reinterpret_cast<uint32_t *>(__ldcg(reinterpret_cast<const unsigned long long *>(&d->out_cnt)));
     o.topk = (int32_t)topk;
     uint32_t *e = smem;  // the endpoints, read past L1 (the arena is reused by later queries)
-    for (uint32_t r = lane; r < R; r += 32) e[r] = __ldcg(ends + (uint64_t)i * R + r);
+    for (uint32_t r = lane; r < R; r += 32) e[r] = caller_id(P.kp.order, __ldcg(ends + (uint64_t)i * R + r));
     __syncwarp();
     uint32_t *scratch = smem + cap;
     switch (P2) {
@@ -948,6 +950,8 @@ static int launch_loop_typed(Server *sv)
     P.kp.edges = sv->cfg.sampler == 1 ? (const void *)g->alias.slots : g->edges;
     P.kp.large = 0xffffffffu;
     P.kp.n_nodes = g->n;
+    P.kp.rank = g->rank;
+    P.kp.order = g->order;
     P.kp.n_records = sv->cfg.sampler == 1 ? (uint64_t)g->m : (uint64_t)g->edge_records;
     P.kp.err = &sv->d_glob->err;
     P.desc = sv->d_desc;

@@ -64,8 +64,11 @@ __global__ void __launch_bounds__(256, PPR_WALK_MINB) k_walk_plain(KParams p)
             ctr_base = (uint32_t)p.inst_off[lo];
             tag = (uint32_t)lo;
         }
-        uint32_t k = 0, u = src, end = 0;
-        while (!walk_step<E, SEG, false, STATS>(p, StepKey{p.k0, p.k1, p.T}, edges, true, src, src - ctr_base, j, tag, k, u,
+        // the draw is keyed by the caller's source id; the walk starts (and
+        // restarts) at its node of the layout
+        const uint32_t s0 = p.rank ? (uint32_t)p.rank[src] : src;
+        uint32_t k = 0, u = s0, end = 0;
+        while (!walk_step<E, SEG, false, STATS>(p, StepKey{p.k0, p.k1, p.T}, edges, true, s0, src - ctr_base, j, tag, k, u,
                                                  end, tl)) {
         }
         p.ends[t] = end - ctr_base;
@@ -161,7 +164,8 @@ __global__ void __launch_bounds__(256, PPR_WALK_MINB) k_walk_persistent(KParams 
                 const uint32_t pos = wq.base + i;
                 src = p.src_list ? p.src_list[pos] : (uint32_t)(p.s_begin + pos);
                 ctr_base = wq.ctr_base;
-                sctr = src - ctr_base;
+                sctr = src - ctr_base;  // draws keyed by the caller's source id
+                if (p.rank) src = (uint32_t)p.rank[src];  // start and restart node of the layout
                 tag = wq.tag;
                 slot = (uint64_t)pos * p.R + j;
                 k = 0;
@@ -223,7 +227,7 @@ static int launch_typed(ppr_ctx *ctx, const KParams &kp, const RunPlan &plan, in
         note_launch();
         PPR_CUDA(cudaGetLastError());
         if ((rc = walker_event(r, st))) return rc;
-        return launch_aggregate(ctx, AggParams{kp.ends, kp.R, kp.P2, S, kp.out_row0, kp.out}, st);
+        return launch_aggregate(ctx, AggParams{kp.ends, kp.R, kp.P2, S, kp.out_row0, kp.out, kp.order}, st);
     }
     int per_sm = 0;
     // walkers per CTA: 32 * warps_per_block (4 or 8 warps; default 8)
@@ -260,7 +264,7 @@ static int launch_typed(ppr_ctx *ctx, const KParams &kp, const RunPlan &plan, in
     note_launch();
     PPR_CUDA(cudaGetLastError());
     if ((rc = walker_event(r, st))) return rc;
-    return launch_aggregate(ctx, AggParams{kp.ends, kp.R, kp.P2, S, kp.out_row0, kp.out}, st);
+    return launch_aggregate(ctx, AggParams{kp.ends, kp.R, kp.P2, S, kp.out_row0, kp.out, kp.order}, st);
 }
 
 // Chunk table of a batched graph, built on the device: chunks of at most CS
@@ -372,6 +376,8 @@ int launch_walks(ppr_ctx *ctx, const ppr_graph *g, const RunPlan &plan, const Ou
     kp.s_begin = s_begin;
     kp.s_end = s_begin + S;
     kp.src_list = src_list;
+    kp.rank = g->rank;
+    kp.order = g->order;
     kp.out_row0 = out_row0;
     kp.out.nnz = o.nnz;
     kp.out.cols = o.cols;

@@ -34,6 +34,8 @@ struct KParams {
     const unsigned long long *nchunks_dev;  // batched graphs: chunk count written on the device
     const int4 *chunks;       // batched graphs: {position, nsrc, instance, 0}; else null
     const uint32_t *src_list; // explicit sources (position -> node id); null: s_begin + position
+    const int32_t *rank;      // renumbered layout: internal id of a caller node (the walk's start), else null
+    const int32_t *order;     // renumbered layout: caller id of an internal node (endpoints), else null
     const int64_t *inst_off;  // batched graphs: node_off
     int32_t instances;
     AggOut out;

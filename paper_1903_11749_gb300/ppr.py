@@ -19,6 +19,8 @@ LIB_PATH = os.environ.get("PPR_LIBRARY_PATH") or os.path.join(_HERE, "libppr.so"
 
 PPR_OK, PPR_EINVAL, PPR_ENOMEM, PPR_ECUDA, PPR_ETIMEOUT, PPR_ERANGE, PPR_EBUSY, PPR_ENOTSUP = 0, -1, -2, -3, -4, -5, -6, -7
 PPR_PTRS_DEVICE = 1
+PPR_RENUMBER = 2
+PPR_KEEP_IDS = 4
 KERNEL_PERSISTENT, KERNEL_PLAIN = 0, 1
 SERVE_DEVICE_LOOP, SERVE_STREAMS = 0, 1
 LOOP_STOPPED, LOOP_IDLE, LOOP_SLOT_TIMEOUT, LOOP_BUSY_TIMEOUT = 1, 2, 4, 8
@@ -34,7 +36,8 @@ class PPRError(RuntimeError):
 class GraphInfo(C.Structure):
     _fields_ = [("n", C.c_int64), ("m", C.c_int64), ("max_degree", C.c_int64), ("dangling", C.c_int64),
                 ("wide", C.c_int32), ("instances", C.c_int32), ("device_bytes", C.c_int64),
-                ("segment_nodes", C.c_int64), ("segment_entries", C.c_int64)]
+                ("segment_nodes", C.c_int64), ("segment_entries", C.c_int64), ("renumbered", C.c_int32),
+                ("reserved", C.c_int32)]
 
 
 class RunArgs(C.Structure):
@@ -263,7 +266,9 @@ class Context:
                           "walks": st.walks, "sources": st.sources, "device_walk_ns": st.device_walk_ns,
                           "device_reduce_ns": st.device_reduce_ns}
 
-    def load_graph(self, n, row_ptr, col, w, stream=None, m=None) -> "Graph":
+    def load_graph(self, n, row_ptr, col, w, stream=None, m=None, renumber=None) -> "Graph":
+        """renumber: None lets the library decide (by the layout's size against
+        L2), True / False force PPR_RENUMBER / PPR_KEEP_IDS."""
         rp, dev = _ptr(row_ptr)
         cp, dev2 = _ptr(col)
         wp, dev3 = _ptr(w)
@@ -271,9 +276,11 @@ class Context:
             raise ValueError("row_ptr, col and w must all be host arrays or all device tensors")
         if m is None:
             m = int(row_ptr[-1]) if not dev else int(row_ptr[-1].item())
+        flags = PPR_PTRS_DEVICE if dev else 0
+        if renumber is not None:
+            flags |= PPR_RENUMBER if renumber else PPR_KEEP_IDS
         h = C.c_void_p()
-        _check(lib().ppr_load_graph(self.h, n, m, rp, cp, wp, PPR_PTRS_DEVICE if dev else 0, _stream_ptr(stream),
-                                    C.byref(h)))
+        _check(lib().ppr_load_graph(self.h, n, m, rp, cp, wp, flags, _stream_ptr(stream), C.byref(h)))
         return Graph(self, h)
 
     def load_graph_batch(self, node_off, row_ptr, col, w, stream=None) -> "Graph":
