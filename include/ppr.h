@@ -66,11 +66,12 @@ enum {
 /* flags */
 #define PPR_PTRS_DEVICE 0x1u /* pointer arguments are device pointers */
 /* Node numbering of the device layout (ppr_load_graph; plain graphs only).
- * With PPR_RENUMBER the layout numbers nodes by descending in-degree (eight
- * classes per power of two, ties in caller order) so that the records and
- * rows of the most visited nodes are contiguous; PPR_KEEP_IDS keeps the
- * caller's order; with neither, the layout renumbers when its node records
- * (32 bytes a node) exceed twice the device's L2.  The numbering is internal:
+ * With PPR_RENUMBER the layout numbers nodes by descending in-degree (counted
+ * on every fourth edge, eight classes per power of two, ties in caller
+ * order) so that the records and rows of the most visited nodes are
+ * contiguous; PPR_KEEP_IDS keeps the caller's order; with neither, the
+ * layout renumbers when its node records (32 bytes a node) exceed twice the
+ * device's L2.  The numbering is internal:
  * sources, rows and top-k use the caller's ids, walks draw by the caller's
  * source id, and every result is the same either way. */
 #define PPR_RENUMBER 0x2u

@@ -183,6 +183,57 @@ __device__ __forceinline__ void topk_select_reg(const uint32_t (&kv)[E], uint32_
     }
 }
 
+// The whole row in top-k order (K >= nrun): kv as in topk_select_reg.  Runs
+// counted once come last (count 1 is the smallest) and already in run order,
+// so only the runs counted twice or more are sorted -- in one register per
+// lane when at most 32 of them (always when R <= 65) -- and the rest are
+// placed by ballot prefix counts.  Returns false (nothing written) when more
+// than 32 runs repeat; the caller then sorts every key.
+template <int E>
+__device__ __forceinline__ bool topk_all_reg(const uint32_t (&kv)[E], uint32_t nrun, uint32_t K, uint32_t R,
+                                             const uint32_t *run_id, uint32_t *cbuf, const AggOut &o, uint64_t tb)
+{
+    const uint32_t lane = threadIdx.x & 31, below = (1u << lane) - 1;
+    const uint32_t t1 = (R - 1) << 12;  // keys from here on: count 1 (or no run)
+    uint32_t nm = 0;
+#pragma unroll
+    for (int e = 0; e < E; ++e) nm += __popc(__ballot_sync(0xffffffffu, kv[e] < t1));
+    if (nm > 32) return false;
+    uint32_t seen = 0;
+#pragma unroll
+    for (int e = 0; e < E; ++e) {
+        const bool rep = kv[e] < t1;
+        const uint32_t mr = __ballot_sync(0xffffffffu, rep);
+        if (rep) cbuf[seen + __popc(mr & below)] = kv[e];
+        seen += __popc(mr);
+    }
+    __syncwarp();
+    uint32_t v[1] = {lane < nm ? cbuf[lane] : 0xffffffffu};
+    warp_sort_reg<1>(v);
+    if (lane < nm && lane < K) {
+        o.topk_idx[tb + lane] = (int32_t)run_id[v[0] & 0xfffu];
+        o.topk_cnt[tb + lane] = R - (v[0] >> 12);
+    }
+    uint32_t ones = 0;
+#pragma unroll
+    for (int e = 0; e < E; ++e) {
+        const uint32_t i = (uint32_t)e * 32 + lane;
+        const bool one = i < nrun && kv[e] >= t1;
+        const uint32_t m1 = __ballot_sync(0xffffffffu, one);
+        const uint32_t pos = nm + ones + __popc(m1 & below);
+        if (one && pos < K) {
+            o.topk_idx[tb + pos] = (int32_t)run_id[kv[e] & 0xfffu];
+            o.topk_cnt[tb + pos] = 1;
+        }
+        ones += __popc(m1);
+    }
+    for (uint32_t i = nrun + lane; i < K; i += 32) {
+        o.topk_idx[tb + i] = -1;
+        o.topk_cnt[tb + i] = 0;
+    }
+    return true;
+}
+
 // scratch: 3 * R uint32 of per-warp shared memory
 template <int E>
 __device__ inline void aggregate_source_reg(const uint32_t *ends, uint32_t R, uint32_t *scratch, const AggOut &o,
@@ -246,6 +297,8 @@ __device__ inline void aggregate_source_reg(const uint32_t *ends, uint32_t R, ui
         const uint32_t K = (uint32_t)o.topk;
         if (E > 1 && K <= 32 && K < nrun) {
             topk_select_reg<E>(kv, K, R, run_id, start_pos, o, tb);
+        } else if (E > 1 && E <= 8 && K >= nrun && topk_all_reg<E>(kv, nrun, K, R, run_id, start_pos, o, tb)) {
+            // the whole row, in top-k order (R <= 256)
         } else {
             warp_sort_reg<E>(kv);
 #pragma unroll

@@ -695,7 +695,7 @@ static int build_narrow(ppr_ctx *ctx, int64_t n, int64_t m, const int64_t *d_rp,
     note_launch();
     k_build_mid<<<ctx->sms * 8, 256, 0, st>>>(A);
     note_launch();
-    k_build_big<<<ctx->sms, 512, 0, st>>>(A);
+    k_build_big<<<ctx->sms * 3, 512, 0, st>>>(A);  // three resident 512-thread blocks per SM (39 registers)
     note_launch();
     std::vector<uint4> hrows;  // host tables must outlive their uploads (synchronised below)
     std::vector<uint2> htiles;
@@ -923,15 +923,19 @@ struct RowView {
 };
 
 // Segment tables in two passes.  k_seg_scan (every node; a warp takes 32 at a
-// time) copies the plain record into the segment record array, tests the shape
-// (degree <= 8 at depths 0, 1 and 2) and counts the raw contributions the
-// path enumeration will make; eligible nodes are listed by that count.
-// k_seg_fill (one warp per listed node) enumerates the paths once, sums equal
-// outcomes in a shared-memory hash table, drops zero masses, rejects a node
-// with more than 64 outcomes, puts the rest in canonical order (terminated
-// before active, then node, then length) by ranking, and appends the table
-// at an atomically reserved offset.  A table's place in the entry array is
-// free (its record holds begin and count), so only its content is fixed.
+// time) copies the plain record into the segment record array, tests the
+// depth-1 shape of all 32 nodes at once (degree <= 8 of the node and of its
+// targets), then for each candidate left the depth-2 shape, and counts the
+// raw contributions the path enumeration will make; eligible nodes are listed
+// by that count (one reservation per warp and tier), with min(raw, 64)
+// entries each, whose scan gives every listed node a fixed slot range.
+// k_seg_fill (one warp per listed node) enumerates the paths once, level by
+// level, sums equal outcomes in a shared-memory hash table, drops zero
+// masses, rejects a node with more than 64 outcomes, puts the rest in
+// canonical order (terminated before active, then node, then length) by
+// ranking, and writes the table at the node's slot.  A table's place in the
+// entry array is free (its record holds begin and count; a shorter table
+// leaves a gap), so only its content is fixed.
 
 constexpr unsigned long long kSegEmpty = ~0ull;  // free hash slot (an outcome key's node field is below 2^31)
 constexpr uint32_t kSegSmallRaw = 128;  // raw contributions up to which the small table (256 slots) serves
@@ -944,21 +948,40 @@ struct SegCounters {
     unsigned long long tables;    // nodes given a table
 };
 
+// Path enumeration by level: depth-1 targets, then the pairs (i1, i2).
+struct SegStage {
+    unsigned long long s1_q[kSegMaxDeg], s1_W[kSegMaxDeg];
+    unsigned long long s2_q[kSegMaxDeg * kSegMaxDeg], s2_W[kSegMaxDeg * kSegMaxDeg];
+    uint32_t s1_node[kSegMaxDeg], s1_deg[kSegMaxDeg];
+    uint32_t s2_node[kSegMaxDeg * kSegMaxDeg], s2_deg[kSegMaxDeg * kSegMaxDeg], s2_pre[kSegMaxDeg * kSegMaxDeg + 1];
+};
+
+// Compacted, then ranked outcomes; so: the keys with the caller's node ids
+// (ranking on a renumbered layout).
+struct SegRank {
+    unsigned long long sk[kSegMaxOut], sq[kSegMaxOut], so[kSegMaxOut];
+};
+
 // Hash table of one warp: more slots than the tier's largest raw count, so it never fills.
 template <int SLOTS>
 struct SegHash {
     unsigned long long key[SLOTS];
     unsigned long long val[SLOTS];
     uint16_t used[SLOTS];          // claimed slots, in claim order
-    unsigned long long sk[kSegMaxOut], sq[kSegMaxOut];  // compacted, then ranked outcomes
-    unsigned long long so[kSegMaxOut];  // renumbered layout: the keys with the caller's node ids (ranking)
+    union {  // one node at a time: the enumeration's staging, then the ranking's outcomes
+        SegStage e;
+        SegRank r;
+    } u;
     unsigned int count;
     unsigned int full;  // a probe found no slot (cannot happen when the scan's count is right): no table
 };
 
+// list: listed nodes, small tier from the front, large from the back;
+// lbound[list position]: min(raw contributions, 64), the entries the node's
+// table may take (its slot range in the entry array comes from a scan of these).
 template <class E>
 __global__ void __launch_bounds__(256) k_seg_scan(RowView<E> G, int64_t n, typename E::Node *seg_node, uint32_t *list,
-                                                  SegCounters *ct)
+                                                  uint32_t *lbound, SegCounters *ct)
 {
     const uint32_t lane = threadIdx.x & 31;
     const int64_t stride = (int64_t)gridDim.x * blockDim.x;
@@ -967,26 +990,33 @@ __global__ void __launch_bounds__(256) k_seg_scan(RowView<E> G, int64_t n, typen
     for (int64_t base = (int64_t)blockIdx.x * blockDim.x + (threadIdx.x & ~31u); base < n; base += stride) {
         const int64_t vl = base + lane;
         uint32_t dl = 0;
+        bool c = false;
         if (vl < n) {
             const typename E::Node r = G.node[vl];
             seg_node[vl] = r;  // plain record unless a table replaces it
             dl = (uint32_t)(r.word0 >> 40) & kCountMask;
+            // depth 1, every lane its own node at once (most candidates have
+            // a neighbour above the limit): the row's targets, then their degrees
+            c = dl >= 1 && dl <= (uint32_t)kSegMaxDeg;
+            if (c) {
+                uint32_t tg[kSegMaxDeg];
+                const uint64_t eb = E::edge_base(r.word0 & kBeginMask, dl);
+#pragma unroll
+                for (uint32_t i = 0; i < (uint32_t)kSegMaxDeg; ++i)
+                    tg[i] = i >= dl ? 0u : (dl == 1 ? (uint32_t)r.total : E::target(G.edges.load(eb + i)));
+#pragma unroll
+                for (uint32_t i = 0; i < (uint32_t)kSegMaxDeg; ++i)
+                    if (i < dl && G.deg(tg[i]) > (uint32_t)kSegMaxDeg) c = false;
+            }
         }
-        uint32_t cand = __ballot_sync(0xffffffffu, vl < n && dl >= 1 && dl <= (uint32_t)kSegMaxDeg);
+        uint32_t cand = __ballot_sync(0xffffffffu, c);
+        uint32_t listed_mask[2] = {0u, 0u}, my_bound = 0;  // this group's listed nodes (lane = node), per tier
         while (cand) {
             const uint32_t src_lane = __ffs(cand) - 1;
             cand &= cand - 1;
             const uint32_t v = (uint32_t)(base + src_lane);
             const uint32_t d1 = __shfl_sync(0xffffffffu, dl, src_lane);
-            // depth 1 first: most candidates have a neighbour above the limit
             bool ok = true;
-            if (lane < d1) {
-                uint64_t wt;
-                uint32_t a;
-                G.edge(v, lane, wt, a);
-                ok = G.deg(a) <= (uint32_t)kSegMaxDeg;
-            }
-            if (!__all_sync(0xffffffffu, ok)) continue;
             uint32_t raw = 0;
             for (uint32_t p = lane; p < d1 * kSegMaxDeg; p += 32) {
                 const uint32_t i1 = p / kSegMaxDeg, i2 = p % kSegMaxDeg;
@@ -1010,11 +1040,29 @@ __global__ void __launch_bounds__(256) k_seg_scan(RowView<E> G, int64_t n, typen
             if (!__all_sync(0xffffffffu, ok)) continue;
 #pragma unroll
             for (int o = 16; o > 0; o >>= 1) raw += __shfl_xor_sync(0xffffffffu, raw, o);
-            if (lane == 0) {
-                const int tier = raw <= kSegSmallRaw ? 0 : 1;
-                const uint32_t k = atomicAdd(&ct->listed[tier], 1u);
-                list[tier ? n - 1 - k : k] = v;  // small tier from the front, large from the back
-                atomicAdd(&ct->bound, (unsigned long long)min(raw, (uint32_t)kSegMaxOut));
+            listed_mask[raw <= kSegSmallRaw ? 0 : 1] |= 1u << src_lane;
+            if (lane == src_lane) my_bound = min(raw, (uint32_t)kSegMaxOut);
+        }
+        // one reservation per tier for the group's listed nodes (not one
+        // atomic per node: every warp would queue on the same counters)
+        uint32_t res[2] = {0u, 0u};
+        unsigned long long bsum = my_bound;
+#pragma unroll
+        for (int o = 16; o > 0; o >>= 1) bsum += __shfl_xor_sync(0xffffffffu, bsum, o);
+        if (lane == 0) {
+            if (listed_mask[0]) res[0] = atomicAdd(&ct->listed[0], (uint32_t)__popc(listed_mask[0]));
+            if (listed_mask[1]) res[1] = atomicAdd(&ct->listed[1], (uint32_t)__popc(listed_mask[1]));
+            if (bsum) atomicAdd(&ct->bound, bsum);
+        }
+        res[0] = __shfl_sync(0xffffffffu, res[0], 0);
+        res[1] = __shfl_sync(0xffffffffu, res[1], 0);
+#pragma unroll
+        for (int tier = 0; tier < 2; ++tier) {
+            if ((listed_mask[tier] >> lane) & 1u) {
+                const uint32_t k = res[tier] + __popc(listed_mask[tier] & ((1u << lane) - 1));
+                const int64_t pos = tier ? n - 1 - k : k;  // small tier from the front, large from the back
+                list[pos] = (uint32_t)vl;
+                lbound[pos] = my_bound;
             }
         }
     }
@@ -1049,10 +1097,13 @@ __device__ __forceinline__ unsigned long long seg_key_caller(unsigned long long 
 
 // order: the renumbered layout's order array (the canonical order ranks
 // outcomes by the caller's node ids), or null.
+// slot: first entry of the table of list position pos (exclusive scan of
+// lbound), so a table is written without a shared counter.
 template <class E, int SLOTS, int WARPS>
 __global__ void __launch_bounds__(32 * WARPS) k_seg_fill(RowView<E> G, uint32_t T, const uint32_t *list, int tier,
                                                          int64_t n, SegCounters *ct, SegEntry *ent,
-                                                         typename E::Node *seg_node, const int32_t *order)
+                                                         typename E::Node *seg_node, const int32_t *order,
+                                                         const uint64_t *slot)
 {
     extern __shared__ __align__(16) unsigned char smem_raw[];
     SegHash<SLOTS> *h = reinterpret_cast<SegHash<SLOTS> *>(smem_raw) + (threadIdx.x >> 5);
@@ -1069,39 +1120,74 @@ __global__ void __launch_bounds__(32 * WARPS) k_seg_fill(RowView<E> G, uint32_t 
     const uint32_t listed = ct->listed[tier];
     const uint32_t cont = (uint32_t)(0x100000000ull - T);  // 2^32 - T, T >= 1
     const int64_t warps = (int64_t)gridDim.x * WARPS;
+    unsigned long long w_used = 0, w_tables = 0;  // this warp's tables and their entries
     for (int64_t t = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5; t < listed; t += warps) {
         const uint32_t v = list[tier ? n - 1 - t : t];
         const uint32_t d1 = G.deg(v);
         const uint64_t Wv = G.total(v);
-        // all paths of length 1, 2, 3: (i1, i2, i3), the shorter ones emitted by
-        // the combinations whose trailing indices are 0 (the paper's masses in
-        // 2^62 fixed point, the same arithmetic as the oracle's)
-        for (uint32_t p = lane; p < d1 * kSegMaxDeg * kSegMaxDeg; p += 32) {
-            const uint32_t i1 = p / (kSegMaxDeg * kSegMaxDeg), i2 = (p / kSegMaxDeg) % kSegMaxDeg, i3 = p % kSegMaxDeg;
+        // all paths of length 1, 2, 3, level by level (the paper's masses in
+        // 2^62 fixed point, the same arithmetic as the oracle's): the d1 edges
+        // of v, then the pairs (i1, i2), then the triples, each level's
+        // targets, masses and row totals staged in shared memory so that a
+        // level costs one round of dependent loads for all its paths
+        if (lane < d1) {
             uint64_t w1;
             uint32_t a;
-            G.edge(v, i1, w1, a);
+            G.edge(v, lane, w1, a);
             const uint64_t q1 = mul_div(1ull << 62, w1, Wv);
             const uint32_t da = G.deg(a);
-            if (i2 == 0 && i3 == 0) {
-                seg_insert(h, a, 0, 0, mul_shift32(q1, T));
-                if (da == 0) seg_insert(h, a, 1, 1, mul_shift32(q1, cont));
-            }
-            if (da == 0 || i2 >= da) continue;
-            uint64_t w2;
-            uint32_t b;
-            G.edge(a, i2, w2, b);
-            const uint64_t q2 = mul_div(mul_shift32(q1, cont), w2, G.total(a));
-            const uint32_t db = G.deg(b);
-            if (i3 == 0) {
+            seg_insert(h, a, 0, 0, mul_shift32(q1, T));
+            if (da == 0) seg_insert(h, a, 1, 1, mul_shift32(q1, cont));
+            h->u.e.s1_node[lane] = a;
+            h->u.e.s1_deg[lane] = da;
+            h->u.e.s1_q[lane] = mul_shift32(q1, cont);  // the mass that continues past a
+            h->u.e.s1_W[lane] = da ? G.total(a) : 1ull;
+        }
+        __syncwarp();
+        const uint32_t np = d1 * kSegMaxDeg;  // pair slots (i1, i2), i2 < deg(a_i1) valid
+        for (uint32_t p = lane; p < np; p += 32) {
+            const uint32_t i1 = p / kSegMaxDeg, i2 = p % kSegMaxDeg;
+            uint32_t db = 0;
+            if (i2 < h->u.e.s1_deg[i1]) {
+                uint64_t w2;
+                uint32_t b;
+                G.edge(h->u.e.s1_node[i1], i2, w2, b);
+                const uint64_t q2 = mul_div(h->u.e.s1_q[i1], w2, h->u.e.s1_W[i1]);
+                db = G.deg(b);
                 seg_insert(h, b, 0, 0, mul_shift32(q2, T));
                 if (db == 0) seg_insert(h, b, 1, 2, mul_shift32(q2, cont));
+                h->u.e.s2_node[p] = b;
+                h->u.e.s2_q[p] = mul_shift32(q2, cont);
+                h->u.e.s2_W[p] = db ? G.total(b) : 1ull;
             }
-            if (db == 0 || i3 >= db) continue;
+            h->u.e.s2_deg[p] = db;
+        }
+        __syncwarp();
+        // triples packed: pair p owns [pre[p], pre[p + 1])
+        uint32_t n3 = 0;  // triples
+        for (uint32_t p0 = 0; p0 < np; p0 += 32) {
+            uint32_t x = p0 + lane < np ? h->u.e.s2_deg[p0 + lane] : 0u;
+#pragma unroll
+            for (int o = 1; o < 32; o <<= 1) {
+                const uint32_t y = __shfl_up_sync(0xffffffffu, x, o);
+                if (lane >= (uint32_t)o) x += y;
+            }
+            if (p0 + lane < np) h->u.e.s2_pre[p0 + lane + 1] = n3 + x;
+            n3 += __shfl_sync(0xffffffffu, x, 31);
+        }
+        if (lane == 0) h->u.e.s2_pre[0] = 0;
+        __syncwarp();
+        for (uint32_t t3 = lane; t3 < n3; t3 += 32) {
+            uint32_t lo = 0, hi = np;  // the pair p with pre[p] <= t3 < pre[p + 1]
+            while (hi - lo > 1) {
+                const uint32_t mid = (lo + hi) >> 1;
+                if (h->u.e.s2_pre[mid] <= t3) lo = mid;
+                else hi = mid;
+            }
             uint64_t w3;
             uint32_t c;
-            G.edge(b, i3, w3, c);
-            const uint64_t q3 = mul_div(mul_shift32(q2, cont), w3, G.total(b));
+            G.edge(h->u.e.s2_node[lo], t3 - h->u.e.s2_pre[lo], w3, c);
+            const uint64_t q3 = mul_div(h->u.e.s2_q[lo], w3, h->u.e.s2_W[lo]);
             seg_insert(h, c, 0, 0, mul_shift32(q3, T));
             seg_insert(h, c, 1, 3, mul_shift32(q3, cont));
         }
@@ -1123,8 +1209,8 @@ __global__ void __launch_bounds__(32 * WARPS) k_seg_fill(RowView<E> G, uint32_t 
             const uint32_t m = __ballot_sync(0xffffffffu, nzero);
             const uint32_t pos = K + __popc(m & below);
             if (nzero && pos < (uint32_t)kSegMaxOut) {
-                h->sk[pos] = k;
-                h->sq[pos] = q;
+                h->u.r.sk[pos] = k;
+                h->u.r.sq[pos] = q;
             }
             K += __popc(m);
         }
@@ -1145,13 +1231,13 @@ __global__ void __launch_bounds__(32 * WARPS) k_seg_fill(RowView<E> G, uint32_t 
 #pragma unroll
         for (int e = 0; e < 2; ++e) {
             const uint32_t i = (uint32_t)e * 32 + lane;
-            mk[e] = i < K ? h->sk[i] : ~0ull;
-            mq[e] = i < K ? h->sq[i] : 0ull;
+            mk[e] = i < K ? h->u.r.sk[i] : ~0ull;
+            mq[e] = i < K ? h->u.r.sq[i] : 0ull;
             mo[e] = (order && i < K) ? seg_key_caller(mk[e], order) : mk[e];
-            if (order && i < K) h->so[i] = mo[e];
+            if (order && i < K) h->u.r.so[i] = mo[e];
         }
         __syncwarp();
-        const unsigned long long *cmp = order ? h->so : h->sk;
+        const unsigned long long *cmp = order ? h->u.r.so : h->u.r.sk;
 #pragma unroll
         for (int e = 0; e < 2; ++e) {
             uint32_t r = 0;
@@ -1162,8 +1248,8 @@ __global__ void __launch_bounds__(32 * WARPS) k_seg_fill(RowView<E> G, uint32_t 
 #pragma unroll
         for (int e = 0; e < 2; ++e)
             if ((uint32_t)e * 32 + lane < K) {
-                h->sk[rk[e]] = mk[e];
-                h->sq[rk[e]] = mq[e];
+                h->u.r.sk[rk[e]] = mk[e];
+                h->u.r.sq[rk[e]] = mq[e];
             }
         __syncwarp();
         // inclusive prefix of the masses in that order
@@ -1172,7 +1258,7 @@ __global__ void __launch_bounds__(32 * WARPS) k_seg_fill(RowView<E> G, uint32_t 
 #pragma unroll
         for (int e = 0; e < 2; ++e) {
             const uint32_t i = (uint32_t)e * 32 + lane;
-            unsigned long long x = i < K ? h->sq[i] : 0ull;
+            unsigned long long x = i < K ? h->u.r.sq[i] : 0ull;
 #pragma unroll
             for (int o = 1; o < 32; o <<= 1) {
                 const unsigned long long y = __shfl_up_sync(0xffffffffu, x, o);
@@ -1181,17 +1267,14 @@ __global__ void __launch_bounds__(32 * WARPS) k_seg_fill(RowView<E> G, uint32_t 
             cum[e] = carry + x;
             carry += __shfl_sync(0xffffffffu, x, 31);
         }
-        unsigned long long base = 0;
-        if (lane == 0) {
-            base = atomicAdd(&ct->used, (unsigned long long)K);
-            atomicAdd(&ct->tables, 1ull);
-        }
-        base = __shfl_sync(0xffffffffu, base, 0);
+        const unsigned long long base = slot[tier ? n - 1 - t : t];
+        w_used += K;
+        ++w_tables;
 #pragma unroll
         for (int e = 0; e < 2; ++e) {
             const uint32_t i = (uint32_t)e * 32 + lane;
             if (i < K) {
-                const unsigned long long k = h->sk[i];
+                const unsigned long long k = h->u.r.sk[i];
                 SegEntry se;
                 se.cum = cum[e];
                 se.node = (uint32_t)((k >> 8) & 0x7fffffffull);
@@ -1207,6 +1290,10 @@ __global__ void __launch_bounds__(32 * WARPS) k_seg_fill(RowView<E> G, uint32_t 
         }
         __syncwarp();
     }
+    if (lane == 0 && w_tables) {
+        atomicAdd(&ct->used, w_used);
+        atomicAdd(&ct->tables, w_tables);
+    }
 }
 
 template <class E>
@@ -1215,45 +1302,64 @@ static int seg_build_typed(ppr_graph *g, uint32_t T, cudaStream_t st, const RowV
 {
     const int64_t n = g->n;
     typename E::Node *seg_node = static_cast<typename E::Node *>(g->seg.node);
-    const int blocks = (int)std::max<int64_t>(1, std::min<int64_t>((n + 255) / 256, (int64_t)g->ctx->sms * 16));
-    k_seg_scan<E><<<blocks, 256, 0, st>>>(G, n, seg_node, list, d_ct);
-    note_launch();
-    SegCounters hc;
-    cudaError_t e = cudaMemcpyAsync(&hc, d_ct, sizeof(hc), cudaMemcpyDeviceToHost, st);
-    if (e == cudaSuccess) e = cudaStreamSynchronize(st);
-    if (e != cudaSuccess) return cuda_fail(e, "segment scan");
+    uint32_t *lbound = nullptr;
+    uint64_t *slot = nullptr, *scan_tmp = nullptr;
+    auto done = [&](int code) {
+        dev_free(lbound, st);
+        dev_free(slot, st);
+        dev_free(scan_tmp, st);
+        return code;
+    };
     int rc;
+    if ((rc = dev_alloc((void **)&lbound, sizeof(uint32_t) * n, "segment bounds", st)) ||
+        (rc = dev_alloc((void **)&slot, sizeof(uint64_t) * (n + 1), "segment slots", st)) ||
+        (rc = dev_alloc((void **)&scan_tmp, sizeof(uint64_t) * ((n + kScanTile - 1) / kScanTile + 2), "scan scratch",
+                        st)))
+        return done(rc);
+    cudaError_t e = cudaMemsetAsync(lbound, 0, sizeof(uint32_t) * n, st);  // unlisted positions take no entries
+    if (e != cudaSuccess) return done(cuda_fail(e, "memset"));
+    const int blocks = (int)std::max<int64_t>(1, std::min<int64_t>((n + 255) / 256, (int64_t)g->ctx->sms * 16));
+    k_seg_scan<E><<<blocks, 256, 0, st>>>(G, n, seg_node, list, lbound, d_ct);
+    note_launch();
+    exclusive_scan_u32(lbound, n, slot, scan_tmp, st);  // each listed node's slot range in the entry array
+    SegCounters hc;
+    e = cudaMemcpyAsync(&hc, d_ct, sizeof(hc), cudaMemcpyDeviceToHost, st);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(st);
+    if (e != cudaSuccess) return done(cuda_fail(e, "segment scan"));
     if ((rc = dev_alloc((void **)&g->seg.entries, sizeof(SegEntry) * (hc.bound > 0 ? hc.bound : 1), "segment tables",
                         st)))
-        return rc;
+        return done(rc);
     if (hc.listed[0]) {
         constexpr int W = 8;
         const size_t smem = sizeof(SegHash<2 * kSegSmallRaw>) * W;
-        PPR_CUDA(cudaFuncSetAttribute(k_seg_fill<E, 2 * kSegSmallRaw, W>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                      (int)smem));
+        e = cudaFuncSetAttribute(k_seg_fill<E, 2 * kSegSmallRaw, W>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                 (int)smem);
+        if (e != cudaSuccess) return done(cuda_fail(e, "cudaFuncSetAttribute(k_seg_fill)"));
         const int fb = (int)std::min<int64_t>((hc.listed[0] + W - 1) / W, (int64_t)g->ctx->sms * 16);
         k_seg_fill<E, 2 * kSegSmallRaw, W><<<fb, 32 * W, smem, st>>>(G, T, list, 0, n, d_ct, g->seg.entries, seg_node,
-                                                                     g->order);
+                                                                     g->order, slot);
         note_launch();
     }
     if (hc.listed[1]) {
         constexpr int W = 2;
         const size_t smem = sizeof(SegHash<kSegLargeSlots>) * W;
-        PPR_CUDA(cudaFuncSetAttribute(k_seg_fill<E, kSegLargeSlots, W>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                      (int)smem));
+        e = cudaFuncSetAttribute(k_seg_fill<E, kSegLargeSlots, W>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                 (int)smem);
+        if (e != cudaSuccess) return done(cuda_fail(e, "cudaFuncSetAttribute(k_seg_fill)"));
         const int fb = (int)std::min<int64_t>((hc.listed[1] + W - 1) / W, (int64_t)g->ctx->sms * 8);
         k_seg_fill<E, kSegLargeSlots, W><<<fb, 32 * W, smem, st>>>(G, T, list, 1, n, d_ct, g->seg.entries, seg_node,
-                                                                   g->order);
+                                                                   g->order, slot);
         note_launch();
     }
-    PPR_CUDA(cudaGetLastError());
-    e = cudaMemcpyAsync(&hc, d_ct, sizeof(hc), cudaMemcpyDeviceToHost, st);
+    e = cudaGetLastError();
+    if (e == cudaSuccess) e = cudaMemcpyAsync(&hc, d_ct, sizeof(hc), cudaMemcpyDeviceToHost, st);
     if (e == cudaSuccess) e = cudaStreamSynchronize(st);
-    if (e != cudaSuccess) return cuda_fail(e, "segment build");
+    if (e != cudaSuccess) return done(cuda_fail(e, "segment build"));
     g->seg.nodes = (int64_t)hc.tables;
     g->seg.entries_n = (int64_t)hc.used;
+    g->seg.entries_cap = (int64_t)hc.bound;
     g->device_bytes += (int64_t)(sizeof(typename E::Node) * n + sizeof(SegEntry) * hc.bound);
-    return PPR_OK;
+    return done(PPR_OK);
 }
 
 int build_segments(ppr_graph *g, uint32_t T, cudaStream_t st)

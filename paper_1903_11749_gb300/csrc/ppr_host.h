@@ -45,7 +45,8 @@ struct SegCache {
     uint32_t T = 0;               // threshold the tables were built for (0 = none)
     void *node = nullptr;         // node records (the graph's type) with eligible nodes switched to their tables
     SegEntry *entries = nullptr;  // all tables
-    int64_t nodes = 0, entries_n = 0;
+    int64_t nodes = 0, entries_n = 0;  // tables, and the entries they hold
+    int64_t entries_cap = 0;           // entries allocated (tables sit at fixed slots, with gaps)
 };
 
 }  // namespace ppr

@@ -178,6 +178,21 @@ __device__ __forceinline__ Sector ld_sector(const void *p)
 }
 
 
+// One 32-byte sector of a row's bottom block, with an evict-first L2 policy:
+// a bottom block serves the one draw that picked it and is rarely read again
+// before it leaves L2, while node records and summary sectors are shared by
+// every draw that passes the same node, so blocks should be the first to go.
+__device__ __forceinline__ Sector ld_block_sector(const void *p)
+{
+    uint64_t pol;
+    asm("createpolicy.fractional.L2::evict_first.b64 %0, 1.0;" : "=l"(pol));
+    Sector s;
+    asm("ld.global.nc.L2::cache_hint.v8.u32 {%0,%1,%2,%3,%4,%5,%6,%7}, [%8], %9;"
+        : "=r"(s.v[0]), "=r"(s.v[1]), "=r"(s.v[2]), "=r"(s.v[3]), "=r"(s.v[4]), "=r"(s.v[5]), "=r"(s.v[6]), "=r"(s.v[7])
+        : "l"(p), "l"(pol));
+    return s;
+}
+
 // A blocked row of d edges with L >= 1 summary levels keeps its top level's
 // keys in the node record when that level has at most five keys
 // (ceil(d / 8^L) <= 5): keys 0..3 in NodeRecN::key, the fifth being W_u.
@@ -346,9 +361,9 @@ __device__ __forceinline__ uint32_t search_blocked(const EdgeN *E, uint64_t begi
     }
     const uint32_t len = min(8u, d - 8 * b);
     const unsigned char *q = base + 32ull * (S + 2 * b);  // 8-record block b: (P, col) pairs
-    const Sector r0 = ld_sector(q);
+    const Sector r0 = ld_block_sector(q);
     Sector r1;
-    if (len > 4) r1 = ld_sector(q + 32);
+    if (len > 4) r1 = ld_block_sector(q + 32);
     else {
 #pragma unroll
         for (int i = 0; i < 8; ++i) r1.v[i] = 0xffffffffu;

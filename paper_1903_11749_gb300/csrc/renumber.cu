@@ -5,10 +5,10 @@
 // to its PageRank (Sec. 2.1: the walks of all sources together follow the
 // random surfer with teleport alpha), which on a power-law graph is led by
 // its in-degree.  The layout numbers nodes in descending order of in-degree
-// (eight classes per power of two, ties in input order), so the records and
-// rows of the most visited nodes sit together at the front of their arrays:
-// their 32-byte sectors share 128-byte L2 lines and DRAM pages instead of
-// being spread over gigabytes.  The numbering is internal: sources, result
+// (counted on every fourth edge; eight classes per power of two, ties in
+// input order), so the records and rows of the most visited nodes sit
+// together at the front of their arrays: their 32-byte sectors share
+// 128-byte L2 lines and DRAM pages instead of being spread over gigabytes.  The numbering is internal: sources, result
 // rows and top-k use the caller's ids, and the draw of a walk is keyed by the
 // caller's source id, so every count is the same with and without it.
 //   order[i]: caller id of internal node i;  rank[v]: internal id of caller node v.
@@ -20,15 +20,21 @@ namespace ppr {
 constexpr int kRnBuckets = 1 + 32 * 8;  // in-degree 0, then 8 classes per power of two
 constexpr int kRnTile = 1024;           // nodes per warp tile of the counting sort
 
-// In-degree of every node; edges whose target lies outside [0, n) are skipped
-// (the layout build reports them).  Equal targets within a warp are summed
-// first, so a hub takes one atomic per warp and not one per edge.
+// In-degree of every node, counted on every kRnEvery-th edge (the ordering
+// needs the classes of the well-visited nodes, whose counts a quarter of the
+// edges already fixes to within a class or two; the atomics, not the read,
+// set this kernel's time).  Edges whose target lies outside [0, n) are
+// skipped (the layout build reports them).  Equal targets within a warp are
+// summed first, so a hub takes one atomic per warp and not one per edge.
+constexpr int64_t kRnEvery = 4;
+
 __global__ void __launch_bounds__(256) k_rn_indegree(int64_t n, int64_t m, const int32_t *col, uint32_t *indeg)
 {
     const uint32_t lane = threadIdx.x & 31;
     const int64_t stride = (int64_t)gridDim.x * blockDim.x;
-    for (int64_t base = (int64_t)blockIdx.x * blockDim.x; base < m; base += stride) {
-        const int64_t e = base + threadIdx.x;
+    const int64_t ms = (m + kRnEvery - 1) / kRnEvery;
+    for (int64_t base = (int64_t)blockIdx.x * blockDim.x; base < ms; base += stride) {
+        const int64_t e = (base + threadIdx.x) * kRnEvery;
         int32_t c = -1;
         if (e < m) c = col[e];
         const bool ok = c >= 0 && (int64_t)c < n;
@@ -118,7 +124,8 @@ int renumber_by_indegree(ppr_ctx *ctx, int64_t n, int64_t m, const int32_t *d_co
     tmp.push_back(scan_tmp);
     PPR_CUDA(cudaMemsetAsync(indeg, 0, sizeof(uint32_t) * n, st));
     if (m > 0) {
-        const int eb = (int)std::max<int64_t>(1, std::min<int64_t>((m + 255) / 256, (int64_t)ctx->sms * 32));
+        const int64_t ms = (m + kRnEvery - 1) / kRnEvery;
+        const int eb = (int)std::max<int64_t>(1, std::min<int64_t>((ms + 255) / 256, (int64_t)ctx->sms * 32));
         k_rn_indegree<<<eb, 256, 0, st>>>(n, m, d_col, indeg);
         note_launch();
     }

@@ -396,7 +396,7 @@ int launch_walks(ppr_ctx *ctx, const ppr_graph *g, const RunPlan &plan, const Ou
     kp.step_loads = (uint32_t)std::max(plan.step_loads, 0);
     kp.n_nodes = g->n;
     kp.n_records = plan.sampler == 1 ? (uint64_t)g->m : (uint64_t)g->edge_records;
-    kp.n_seg = (uint64_t)g->seg.entries_n;
+    kp.n_seg = (uint64_t)g->seg.entries_cap;
     kp.err = o.counters + 4;
     kp.ends = reinterpret_cast<uint32_t *>(ws);
     size_t off = align256((size_t)S * plan.R * sizeof(uint32_t));

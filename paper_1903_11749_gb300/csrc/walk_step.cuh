@@ -46,7 +46,7 @@ struct KParams {
     uint64_t r_magic;         // ceil(2^40 / R): walk index -> source index by multiply-shift
     int64_t n_nodes;          // node records (for the L2 window and the checked build)
     uint64_t n_records;       // checked build: records of the edge layout walked (alias: slots)
-    uint64_t n_seg;           // checked build: segment entries
+    uint64_t n_seg;           // checked build: segment entries allocated
     unsigned long long *err;  // checked build: flags of indices that left their array
 };
 
@@ -373,9 +373,9 @@ __device__ __forceinline__ bool walk_step_bounded(const KParams &p, const StepKe
     if (budget > 0) {
         const uint32_t len = min(8u, d - 8 * b);
         const unsigned char *q = base + 32ull * (S + 2 * b);
-        const Sector r0 = ld_sector(q);
+        const Sector r0 = ld_block_sector(q);
         Sector r1;
-        if (len > 4) r1 = ld_sector(q + 32);
+        if (len > 4) r1 = ld_block_sector(q + 32);
         else {
 #pragma unroll
             for (int i = 0; i < 8; ++i) r1.v[i] = 0xffffffffu;

@@ -107,6 +107,25 @@ def test_topk_larger_than_R(ppr, ctx, oracle):
             assert_same(G.run(alpha=0.15, R=R, seed=2, topk=k, kernel=kernel), ref, topk=k)
 
 
+@pytest.mark.parametrize("R", [2, 33, 50, 64, 65, 100, 200, 256])
+def test_whole_row_in_topk_order(ppr, ctx, oracle, R):
+    """k at or above the row length returns the whole row in top-k order:
+    runs counted twice or more sorted, runs counted once after them in id
+    order (the fast path when at most 32 runs repeat), and the full sort
+    when more repeat (an 80-node graph at R >= 100); every padding slot is
+    (-1, 0)."""
+    for g, alpha in ((I.er_graph(30, 300, 1, 4, seed=R), 0.25), (I.er_graph(80, 900, 1, 4, seed=R + 1), 0.15),
+                     (I.random_small_graph(3000, 20000, seed=R, wmax=5), 0.1)):
+        G = ctx.load_graph(g.n, g.row_ptr, g.col, g.w)
+        og = oracle.prepare(g.n, g.row_ptr, g.col, g.w)
+        for k in (R, R + 7, 64, 300):
+            if k < min(R, g.n):
+                continue
+            ref = oracle_rows(oracle, g, alpha, R, 5, s_end=min(g.n, 200), topk=k, og=og)
+            res = G.run(alpha=alpha, R=R, seed=5, src_end=min(g.n, 200), topk=k)
+            assert_same(res, ref, topk=k)
+
+
 @pytest.mark.parametrize("R", [33, 64, 100, 200, 513, 1024])
 def test_topk_selection_at_count_ties(ppr, ctx, oracle, R):
     """Top-k below the number of distinct endpoints (k <= 32, R > 32) is
