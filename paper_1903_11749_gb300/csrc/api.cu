@@ -360,6 +360,7 @@ void ppr_free_graph(ppr_graph *g)
     }
     dev_free(g->node, g->stream);
     dev_free(g->edges, g->stream);
+    dev_free(g->sum, g->stream);
     dev_free(g->seg.node, g->stream);
     dev_free(g->seg.entries, g->stream);
     dev_free(g->d_node_off, g->stream);

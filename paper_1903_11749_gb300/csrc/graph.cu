@@ -181,15 +181,18 @@ __device__ __forceinline__ void block_stats(LayoutStats *st, uint32_t deg_max, u
 }
 
 // order: the caller's row of internal node u (renumbered layout), or null.
+// sizes: the row's block records in the edge array; ssizes: its summary
+// sectors in the summary array.
 __global__ void __launch_bounds__(256) k_layout(int64_t n, int64_t m, const int64_t *row_ptr, const int32_t *order,
-                                                uint32_t *sizes, LayoutStats *st, uint2 *huge, uint32_t huge_cap)
+                                                uint32_t *sizes, uint32_t *ssizes, LayoutStats *st, uint2 *huge,
+                                                uint32_t huge_cap)
 {
     uint32_t dmax = 0, dang = 0, flags = 0;
     for (int64_t u = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; u < n; u += (int64_t)gridDim.x * blockDim.x) {
         const int64_t o = order ? (int64_t)order[u] : u;
         const int64_t a = row_ptr[o], b = row_ptr[o + 1];
         const bool bad = a < 0 || b < a || b > m || (o == 0 && a != 0) || (o == n - 1 && b != m);
-        uint32_t sz = 0;
+        uint32_t sz = 0, ssz = 0;
         if (bad) {
             flags |= kBadRowPtr;
         } else if (b - a > PPR_MAX_DEGREE) {
@@ -199,12 +202,14 @@ __global__ void __launch_bounds__(256) k_layout(int64_t n, int64_t m, const int6
             dmax = max(dmax, d);
             dang += d == 0;
             sz = blocked_row_records(d);
+            ssz = d >= 2 ? summary_sectors(d) : 0u;
             if (d > kHugeRow) {  // a valid row_ptr has at most m / kHugeRow of them
                 const uint32_t k = atomicAdd(&st->n_huge, 1u);
                 if (k < huge_cap) huge[k] = make_uint2((uint32_t)u, d);
             }
         }
         sizes[u] = sz;
+        ssizes[u] = ssz;
     }
     block_stats(st, dmax, dang, flags);
 }
@@ -216,9 +221,11 @@ struct BuildArgs {
     const uint32_t *w;
     const int64_t *node_off;
     int32_t count;
-    const uint64_t *region;
+    const uint64_t *region;   // first block record of each row in E
+    const uint64_t *sregion;  // first summary sector of each row in K
     NodeRecN *node;
     EdgeN *E;
+    uint32_t *K;              // the summary array (8 keys a sector)
     LayoutStats *st;
     uint32_t *list;  // mid rows from the front, big rows from the back
     const int32_t *order;  // renumbered layout: caller row of internal node u, else null
@@ -230,28 +237,28 @@ struct BuildArgs {
 __device__ __forceinline__ int64_t in_row(const BuildArgs &A, int64_t u) { return A.order ? (int64_t)A.order[u] : u; }
 __device__ __forceinline__ int64_t map_col(const BuildArgs &A, int64_t c) { return A.rank ? (int64_t)A.rank[c] : c; }
 
-// u32 slot of key i of level l of a blocked row (region reg, degree d, L levels)
-__device__ __forceinline__ uint64_t key_slot(uint64_t reg, uint32_t d, uint32_t L, uint32_t l, uint32_t i)
+// u32 slot in the summary array of key i of level l of a blocked row (first
+// summary sector sreg, degree d, L levels; the top level comes first)
+__device__ __forceinline__ uint64_t key_slot(uint64_t sreg, uint32_t d, uint32_t L, uint32_t l, uint32_t i)
 {
     uint32_t off = 0;
     for (uint32_t q = L; q > l; --q) off += level_sectors(d, q);
-    return (reg + 4ull * off) * 2 + i;
+    return (sreg + off) * 8ull + i;
 }
 
 // Node record of a built row; a row whose top summary level fits the record
 // (root_in_record) gets that level's first four keys, read back from the
 // level the calling group has just written.
-__device__ __forceinline__ void write_node(const BuildArgs &A, int64_t u, uint64_t reg, uint32_t d, uint64_t W,
-                                           uint32_t first_target)
+__device__ __forceinline__ void write_node(const BuildArgs &A, int64_t u, uint64_t reg, uint64_t sreg, uint32_t d,
+                                           uint64_t W, uint32_t first_target)
 {
     NodeRecN r;
     r.word0 = pack_word0(reg, d, false);
-    r.total = d == 1 ? (uint64_t)first_target : (d == 0 ? 0ull : pack_blocked_total(W, d));
+    r.total = d == 1 ? (uint64_t)first_target : (d == 0 ? 0ull : pack_blocked_total(W, d > 8 ? sreg : 0, d));
     const uint32_t L = d >= 2 ? tree_levels(d) : 0;
     const bool root = root_in_record(d, L);
-    const uint32_t *K = reinterpret_cast<const uint32_t *>(A.E);
 #pragma unroll
-    for (uint32_t i = 0; i < 4; ++i) r.key[i] = root ? K[key_slot(reg, d, L, L, i)] : 0xffffffffu;
+    for (uint32_t i = 0; i < 4; ++i) r.key[i] = root ? A.K[key_slot(sreg, d, L, L, i)] : 0xffffffffu;
     A.node[u] = r;
 }
 
@@ -268,15 +275,15 @@ __device__ __forceinline__ int64_t instance_base(const BuildArgs &A, int64_t u, 
 
 // summary levels 2..L from level 1 (already written), padding included;
 // the calling group (warp or block) strides over keys with `rank`/`size`
-__device__ void write_upper_levels(uint32_t *K, uint64_t reg, uint32_t d, uint32_t L, uint32_t rank, uint32_t size,
+__device__ void write_upper_levels(uint32_t *K, uint64_t sreg, uint32_t d, uint32_t L, uint32_t rank, uint32_t size,
                                    bool block)
 {
     for (uint32_t l = 2; l <= L; ++l) {
         const uint32_t nl = ceil_shift(d, 3 * l), np = ceil_shift(d, 3 * (l - 1));
         for (uint32_t i = rank; i < 8 * level_sectors(d, l); i += size) {
             uint32_t kv = 0xffffffffu;
-            if (i < nl) kv = K[key_slot(reg, d, L, l - 1, min(8 * i + 8, np) - 1)];
-            K[key_slot(reg, d, L, l, i)] = kv;
+            if (i < nl) kv = K[key_slot(sreg, d, L, l - 1, min(8 * i + 8, np) - 1)];
+            K[key_slot(sreg, d, L, l, i)] = kv;
         }
         if (block) __syncthreads();
         else __syncwarp();
@@ -325,7 +332,7 @@ __device__ __forceinline__ EdgeRun load_run(const BuildArgs &A, int64_t a, uint3
 // Writes the run's records (P after each edge, target) from the exclusive
 // prefix P0, padding records past d included (a row's region is padded to a
 // multiple of 4 records, and i0 is a multiple of 4), and its level-1 keys.
-__device__ __forceinline__ void write_run(const BuildArgs &A, uint32_t *K, const EdgeRun &r, uint64_t P0, uint64_t reg,
+__device__ __forceinline__ void write_run(const BuildArgs &A, uint32_t *K, const EdgeRun &r, uint64_t P0, uint64_t sreg,
                                           uint64_t eb, uint32_t d, uint32_t L, uint32_t i0, int64_t base_id)
 {
     if (i0 >= d) return;
@@ -338,7 +345,7 @@ __device__ __forceinline__ void write_run(const BuildArgs &A, uint32_t *K, const
         const bool in = i < d;
         v[2 * q] = in ? (uint32_t)P : 0xffffffffu;
         v[2 * q + 1] = in ? (uint32_t)(r.c[q] + base_id) : 0u;
-        if (in && ((i & 7) == 7 || i == d - 1)) K[key_slot(reg, d, L, 1, i >> 3)] = (uint32_t)P;
+        if (in && ((i & 7) == 7 || i == d - 1)) K[key_slot(sreg, d, L, 1, i >> 3)] = (uint32_t)P;
     }
     uint4 *dst = reinterpret_cast<uint4 *>(A.E + eb + i0);  // 32-byte aligned
     dst[0] = make_uint4(v[0], v[1], v[2], v[3]);
@@ -347,7 +354,7 @@ __device__ __forceinline__ void write_run(const BuildArgs &A, uint32_t *K, const
 
 __global__ void __launch_bounds__(256) k_build_small(BuildArgs A)
 {
-    uint32_t *K = reinterpret_cast<uint32_t *>(A.E);
+    uint32_t *K = A.K;
     uint32_t flags = 0;
     for (int64_t u = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; u < A.n; u += (int64_t)gridDim.x * blockDim.x) {
         const int64_t o = in_row(A, u);
@@ -360,9 +367,9 @@ __global__ void __launch_bounds__(256) k_build_small(BuildArgs A)
         }
         int64_t hi_id;
         const int64_t base_id = instance_base(A, u, hi_id);
-        const uint64_t reg = A.region[u];
+        const uint64_t reg = A.region[u], sreg = A.sregion[u];
         const uint32_t L = tree_levels(d);  // 0 or 1 here
-        const uint64_t eb = reg + 4ull * summary_sectors(d);
+        const uint64_t eb = reg;
         uint64_t P = 0;
         uint32_t first = 0;
         for (uint32_t i = 0; i < d; ++i) {
@@ -378,7 +385,7 @@ __global__ void __launch_bounds__(256) k_build_small(BuildArgs A)
                 r.P = (uint32_t)P;
                 r.col = (int32_t)(c + base_id);
                 A.E[eb + i] = r;
-                if (L > 0 && ((i & 7) == 7 || i == d - 1)) K[key_slot(reg, d, L, 1, i >> 3)] = (uint32_t)P;
+                if (L > 0 && ((i & 7) == 7 || i == d - 1)) K[key_slot(sreg, d, L, 1, i >> 3)] = (uint32_t)P;
             }
         }
         if (P >= (1ull << 32)) flags |= kWide;
@@ -390,16 +397,16 @@ __global__ void __launch_bounds__(256) k_build_small(BuildArgs A)
                 A.E[eb + i] = r;
             }
             if (L > 0)
-                for (uint32_t i = ceil_shift(d, 3); i < 8 * level_sectors(d, 1); ++i) K[key_slot(reg, d, L, 1, i)] = 0xffffffffu;
+                for (uint32_t i = ceil_shift(d, 3); i < 8 * level_sectors(d, 1); ++i) K[key_slot(sreg, d, L, 1, i)] = 0xffffffffu;
         }
-        write_node(A, u, reg, d, P, first);
+        write_node(A, u, reg, sreg, d, P, first);
     }
     block_stats(A.st, 0, 0, flags);
 }
 
 __global__ void __launch_bounds__(256) k_build_mid(BuildArgs A)
 {
-    uint32_t *K = reinterpret_cast<uint32_t *>(A.E);
+    uint32_t *K = A.K;
     const uint32_t lane = threadIdx.x & 31;
     const int64_t warps = (int64_t)gridDim.x * (blockDim.x >> 5);
     uint32_t flags = 0;
@@ -411,9 +418,9 @@ __global__ void __launch_bounds__(256) k_build_mid(BuildArgs A)
         const uint32_t d = (uint32_t)(A.row_ptr[o + 1] - a);
         int64_t hi_id;
         const int64_t base_id = instance_base(A, u, hi_id);
-        const uint64_t reg = A.region[u];
+        const uint64_t reg = A.region[u], sreg = A.sregion[u];
         const uint32_t L = tree_levels(d);
-        const uint64_t eb = reg + 4ull * summary_sectors(d);
+        const uint64_t eb = reg;
         uint64_t carry = 0;
         for (uint32_t e0 = 0; e0 < d; e0 += 32 * kRun) {
             const uint32_t i0 = e0 + lane * kRun;
@@ -424,15 +431,15 @@ __global__ void __launch_bounds__(256) k_build_mid(BuildArgs A)
                 const uint64_t y = __shfl_up_sync(0xffffffffu, v, o);
                 if (lane >= o) v += y;
             }
-            write_run(A, K, r, carry + v - r.sum, reg, eb, d, L, i0, base_id);
+            write_run(A, K, r, carry + v - r.sum, sreg, eb, d, L, i0, base_id);
             carry += __shfl_sync(0xffffffffu, v, 31);
         }
         if (carry >= (1ull << 32)) flags |= kWide;
         for (uint32_t i = ceil_shift(d, 3) + lane; i < 8 * level_sectors(d, 1); i += 32)
-            K[key_slot(reg, d, L, 1, i)] = 0xffffffffu;
+            K[key_slot(sreg, d, L, 1, i)] = 0xffffffffu;
         __syncwarp();
-        write_upper_levels(K, reg, d, L, lane, 32, false);
-        if (lane == 0) write_node(A, u, reg, d, carry, 0);
+        write_upper_levels(K, sreg, d, L, lane, 32, false);
+        if (lane == 0) write_node(A, u, reg, sreg, d, carry, 0);
     }
     block_stats(A.st, 0, 0, flags);
 }
@@ -440,7 +447,7 @@ __global__ void __launch_bounds__(256) k_build_mid(BuildArgs A)
 __global__ void __launch_bounds__(512) k_build_big(BuildArgs A)
 {
     __shared__ uint64_t s_warp[16];
-    uint32_t *K = reinterpret_cast<uint32_t *>(A.E);
+    uint32_t *K = A.K;
     const uint32_t tid = threadIdx.x, lane = tid & 31, wid = tid >> 5, nw = blockDim.x >> 5;
     uint32_t flags = 0;
     const uint32_t nbig = A.st->n_big;
@@ -451,9 +458,9 @@ __global__ void __launch_bounds__(512) k_build_big(BuildArgs A)
         const uint32_t d = (uint32_t)(A.row_ptr[o + 1] - a);
         int64_t hi_id;
         const int64_t base_id = instance_base(A, u, hi_id);
-        const uint64_t reg = A.region[u];
+        const uint64_t reg = A.region[u], sreg = A.sregion[u];
         const uint32_t L = tree_levels(d);
-        const uint64_t eb = reg + 4ull * summary_sectors(d);
+        const uint64_t eb = reg;
         uint64_t carry = 0;
         for (uint32_t e0 = 0; e0 < d; e0 += blockDim.x * kRun) {
             const uint32_t i0 = e0 + tid * kRun;
@@ -471,16 +478,16 @@ __global__ void __launch_bounds__(512) k_build_big(BuildArgs A)
                 if (q < wid) before += s_warp[q];
                 chunk += s_warp[q];
             }
-            write_run(A, K, r, carry + before + v - r.sum, reg, eb, d, L, i0, base_id);
+            write_run(A, K, r, carry + before + v - r.sum, sreg, eb, d, L, i0, base_id);
             carry += chunk;
             __syncthreads();
         }
         if (carry >= (1ull << 32)) flags |= kWide;
         for (uint32_t i = ceil_shift(d, 3) + tid; i < 8 * level_sectors(d, 1); i += blockDim.x)
-            K[key_slot(reg, d, L, 1, i)] = 0xffffffffu;
+            K[key_slot(sreg, d, L, 1, i)] = 0xffffffffu;
         __syncthreads();
-        write_upper_levels(K, reg, d, L, tid, blockDim.x, true);
-        if (tid == 0) write_node(A, u, reg, d, carry, 0);
+        write_upper_levels(K, sreg, d, L, tid, blockDim.x, true);
+        if (tid == 0) write_node(A, u, reg, sreg, d, carry, 0);
         __syncthreads();
     }
     // one status word per block
@@ -572,16 +579,16 @@ __global__ void __launch_bounds__(256) k_build_tile_write(BuildTiles T)
 {
     __shared__ uint64_t s[8];
     const BuildArgs &A = T.A;
-    uint32_t *K = reinterpret_cast<uint32_t *>(A.E);
+    uint32_t *K = A.K;
     const uint2 tl = T.tiles[blockIdx.x];
     const uint4 rw = T.rows[tl.x];
     const uint32_t d = rw.y;
     const int64_t a = A.row_ptr[in_row(A, rw.x)];
     int64_t hi_id;
     const int64_t base_id = instance_base(A, rw.x, hi_id);
-    const uint64_t reg = A.region[rw.x];
+    const uint64_t reg = A.region[rw.x], sreg = A.sregion[rw.x];
     const uint32_t L = tree_levels(d);
-    const uint64_t eb = reg + 4ull * summary_sectors(d);
+    const uint64_t eb = reg;
     const uint32_t end = min(tl.y + kBuildTile, d);
     const uint32_t lo = min(tl.y + threadIdx.x * 32, end), hi = min(lo + 32, end);
     uint64_t own = 0;
@@ -606,19 +613,19 @@ __global__ void __launch_bounds__(256) k_build_tile_write(BuildTiles T)
         r.P = (uint32_t)P;
         r.col = (int32_t)((c >= 0 && c < hi_id ? map_col(A, c) : c) + base_id);
         A.E[eb + i] = r;
-        if ((i & 7) == 7 || i == d - 1) K[key_slot(reg, d, L, 1, i >> 3)] = (uint32_t)P;
+        if ((i & 7) == 7 || i == d - 1) K[key_slot(sreg, d, L, 1, i >> 3)] = (uint32_t)P;
     }
 }
 
 __global__ void __launch_bounds__(512) k_build_tile_finish(BuildTiles T)
 {
     const BuildArgs &A = T.A;
-    uint32_t *K = reinterpret_cast<uint32_t *>(A.E);
+    uint32_t *K = A.K;
     const uint4 rw = T.rows[blockIdx.x];
     const uint32_t d = rw.y, tid = threadIdx.x;
-    const uint64_t reg = A.region[rw.x];
+    const uint64_t reg = A.region[rw.x], sreg = A.sregion[rw.x];
     const uint32_t L = tree_levels(d);
-    const uint64_t eb = reg + 4ull * summary_sectors(d);
+    const uint64_t eb = reg;
     for (uint32_t i = d + tid; i < 4 * ceil_shift(d, 2); i += blockDim.x) {
         EdgeN r;
         r.P = 0xffffffffu;
@@ -626,10 +633,10 @@ __global__ void __launch_bounds__(512) k_build_tile_finish(BuildTiles T)
         A.E[eb + i] = r;
     }
     for (uint32_t i = ceil_shift(d, 3) + tid; i < 8 * level_sectors(d, 1); i += blockDim.x)
-        K[key_slot(reg, d, L, 1, i)] = 0xffffffffu;
+        K[key_slot(sreg, d, L, 1, i)] = 0xffffffffu;
     __syncthreads();
-    write_upper_levels(K, reg, d, L, tid, blockDim.x, true);
-    if (tid == 0) write_node(A, rw.x, reg, d, T.row_total[blockIdx.x], 0);
+    write_upper_levels(K, sreg, d, L, tid, blockDim.x, true);
+    if (tid == 0) write_node(A, rw.x, reg, sreg, d, T.row_total[blockIdx.x], 0);
 }
 
 // Narrow layout in one pass.  Returns PPR_OK, an error, or 1 when a row total
@@ -639,8 +646,8 @@ static int build_narrow(ppr_ctx *ctx, int64_t n, int64_t m, const int64_t *d_rp,
                         std::vector<void *> &tmp)
 {
     int rc;
-    uint32_t *d_sizes;
-    uint64_t *d_region, *d_scan;
+    uint32_t *d_sizes, *d_ssizes;
+    uint64_t *d_region, *d_sregion, *d_scan;
     LayoutStats *d_ls;
     uint32_t *d_list;
     const int64_t tiles = (n + kScanTile - 1) / kScanTile;
@@ -648,6 +655,10 @@ static int build_narrow(ppr_ctx *ctx, int64_t n, int64_t m, const int64_t *d_rp,
     tmp.push_back(d_sizes);
     if ((rc = dev_alloc((void **)&d_region, sizeof(uint64_t) * (n + 1), "row regions", st))) return rc;
     tmp.push_back(d_region);
+    if ((rc = dev_alloc((void **)&d_ssizes, sizeof(uint32_t) * n, "summary sizes", st))) return rc;
+    tmp.push_back(d_ssizes);
+    if ((rc = dev_alloc((void **)&d_sregion, sizeof(uint64_t) * (n + 1), "summary regions", st))) return rc;
+    tmp.push_back(d_sregion);
     if ((rc = dev_alloc((void **)&d_scan, sizeof(uint64_t) * (tiles + 2), "scan scratch", st))) return rc;
     tmp.push_back(d_scan);
     if ((rc = dev_alloc((void **)&d_ls, sizeof(LayoutStats), "layout stats", st))) return rc;
@@ -661,13 +672,15 @@ static int build_narrow(ppr_ctx *ctx, int64_t n, int64_t m, const int64_t *d_rp,
     cudaError_t e = cudaMemsetAsync(d_ls, 0, sizeof(LayoutStats), st);
     if (e != cudaSuccess) return cuda_fail(e, "memset");
     const int tblocks = (int)std::max<int64_t>(1, std::min<int64_t>((n + 255) / 256, (int64_t)ctx->sms * 16));
-    k_layout<<<tblocks, 256, 0, st>>>(n, m, d_rp, g->order, d_sizes, d_ls, d_huge, huge_cap);
+    k_layout<<<tblocks, 256, 0, st>>>(n, m, d_rp, g->order, d_sizes, d_ssizes, d_ls, d_huge, huge_cap);
     note_launch();
     exclusive_scan_u32(d_sizes, n, d_region, d_scan, st);
+    exclusive_scan_u32(d_ssizes, n, d_sregion, d_scan, st);  // same scratch, after the first scan in stream order
     LayoutStats hs;
-    uint64_t slots = 0;
+    uint64_t slots = 0, sum_sectors = 0;
     e = cudaMemcpyAsync(&hs, d_ls, sizeof(hs), cudaMemcpyDeviceToHost, st);
     if (e == cudaSuccess) e = cudaMemcpyAsync(&slots, d_region + n, sizeof(uint64_t), cudaMemcpyDeviceToHost, st);
+    if (e == cudaSuccess) e = cudaMemcpyAsync(&sum_sectors, d_sregion + n, sizeof(uint64_t), cudaMemcpyDeviceToHost, st);
     if (e == cudaSuccess) e = cudaStreamSynchronize(st);
     if (e != cudaSuccess) return cuda_fail(e, "graph layout");
     if (hs.status & kBadRowPtr) {
@@ -682,15 +695,22 @@ static int build_narrow(ppr_ctx *ctx, int64_t n, int64_t m, const int64_t *d_rp,
         set_error("edge layout needs %llu record slots, beyond 2^40", (unsigned long long)slots);
         return PPR_ERANGE;
     }
+    if (sum_sectors >= kSumSectorsMax) {
+        set_error("the rows' search-tree summaries need %llu sectors, beyond 2^28", (unsigned long long)sum_sectors);
+        return PPR_ERANGE;
+    }
     g->max_degree = (int64_t)hs.max_degree;
     g->dangling = (int64_t)hs.dangling;
     if ((rc = dev_alloc((void **)&g->node, sizeof(NodeRecN) * n, "node records", st))) return rc;
     const size_t edge_bytes = (size_t)(slots > 0 ? slots : 2) * sizeof(EdgeN);
     if ((rc = dev_alloc(&g->edges, edge_bytes, "edge records", st))) return rc;
     g->edge_records = (int64_t)slots;
-    g->device_bytes = (int64_t)(sizeof(NodeRecN) * n + edge_bytes);
-    BuildArgs A{n, d_rp, d_col, d_w, d_off, g->instances, d_region, static_cast<NodeRecN *>(g->node),
-                (EdgeN *)g->edges, d_ls, d_list, g->order, g->rank};
+    const size_t sum_bytes = (size_t)(sum_sectors > 0 ? sum_sectors : 1) * 32;
+    if ((rc = dev_alloc((void **)&g->sum, sum_bytes, "row summaries", st))) return rc;
+    g->sum_sectors = (int64_t)sum_sectors;
+    g->device_bytes = (int64_t)(sizeof(NodeRecN) * n + edge_bytes + sum_bytes);
+    BuildArgs A{n, d_rp, d_col, d_w, d_off, g->instances, d_region, d_sregion, static_cast<NodeRecN *>(g->node),
+                (EdgeN *)g->edges, g->sum, d_ls, d_list, g->order, g->rank};
     k_build_small<<<tblocks, 256, 0, st>>>(A);
     note_launch();
     k_build_mid<<<ctx->sms * 8, 256, 0, st>>>(A);
@@ -749,8 +769,11 @@ static int build_narrow(ppr_ctx *ctx, int64_t n, int64_t m, const int64_t *d_rp,
     if (hs.status & kWide) {
         dev_free(g->node, st);
         dev_free(g->edges, st);
+        dev_free(g->sum, st);
         g->node = nullptr;
         g->edges = nullptr;
+        g->sum = nullptr;
+        g->sum_sectors = 0;
         return 1;
     }
     return PPR_OK;

@@ -85,6 +85,8 @@ struct ppr_graph {
     void *node = nullptr;   // NodeRecN[n] (narrow layout) or NodeRec[n] (wide layout)
     void *edges = nullptr;  // EdgeN[m] or EdgeW[m]
     int64_t edge_records = 0;  // records the edge layout holds (blocked narrow rows: with padding)
+    uint32_t *sum = nullptr;   // narrow layout: the blocked rows' summary levels (8 keys a sector)
+    int64_t sum_sectors = 0;
     // internal numbering of the layout (renumber.cu), or null: caller ids
     int32_t *order = nullptr;  // [n] caller id of internal node i
     int32_t *rank = nullptr;   // [n] internal id of caller node v

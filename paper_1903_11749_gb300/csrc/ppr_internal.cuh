@@ -6,8 +6,9 @@
 //     word1 = W_u, the row's total weight (Sec. 2.1 routing denominator), or
 //             the target id when the row has exactly one edge (no search), or
 //             Q_v, the total fixed-point mass of a segment table (Algorithm 4);
-//             narrow blocked rows keep W_u in bits 0..31 and their summary
-//             size S (bits 32..55) and level count L (bits 56..59) above it
+//             narrow blocked rows keep W_u in bits 0..31, the first sector
+//             of their summary in the summary array (bits 32..59) and their
+//             level count L (bits 60..63) above it
 //   NodeRecN (32 B, one sector per node; narrow layout): a NodeRec and the
 //     first four keys of the row's top summary level when that level has at
 //     most five keys (the fifth is W_u), so the step that reads the record
@@ -17,12 +18,16 @@
 //   EdgeN (8 B): {uint32 P, int32 col}  -- narrow layout, every W_u < 2^32
 //   EdgeW (16 B): {uint64 P, int32 col, pad} -- wide layout (flat rows)
 //
-// Narrow rows are stored as static search trees ("blocked" rows): a row with
-// d >= 2 edges starts on a 32-byte sector; its region holds the summary
-// levels (top level first), then the edge records in blocks of 8 (the area
-// rounded up to whole sectors, padding keys 0xFFFFFFFF).  Level 1 keeps the
-// last prefix of every 8-record block, level l+1 the last key of every
-// 8-key sector of level l, up to a top level of at most 8 keys (one sector).
+// Narrow rows are stored as static search trees ("blocked" rows).  A row with
+// d >= 2 edges has its edge records in blocks of 8 in the edge array,
+// starting on a 32-byte sector (the area rounded up to whole sectors, padding
+// keys 0xFFFFFFFF), and, when d > 8, its summary levels (top level first) in
+// the summary array, which holds nothing else: the summary sectors that every
+// draw at a node passes through sit densely in L2 lines and DRAM pages
+// instead of one per row between the blocks, which a draw reads once.  Level
+// 1 keeps the last prefix of every 8-record block, level l+1 the last key of
+// every 8-key sector of level l, up to a top level of at most 8 keys (one
+// sector).
 // A search reads one sector per level and one 8-record block: the same edge
 // as bisection of the flat prefix (the first P > x is unique), found with
 // ceil(log8 d) + 1 dependent loads instead of ceil(log2 d) + 1.  The alias
@@ -113,13 +118,21 @@ __host__ __device__ __forceinline__ uint32_t summary_sectors(uint32_t d)
     return S;
 }
 
-// 8-byte record slots a blocked row occupies (a one-edge row keeps its target
-// in the node record and needs none).
+// 8-byte record slots a blocked row's blocks occupy in the edge array (a
+// one-edge row keeps its target in the node record and needs none); its
+// summary levels (summary_sectors) sit in the summary array.
 __host__ __device__ __forceinline__ uint32_t blocked_row_records(uint32_t d)
 {
     if (d <= 1) return 0;
-    return 4 * summary_sectors(d) + 4 * ceil_shift(d, 2);
+    return 4 * ceil_shift(d, 2);
 }
+
+// A blocked row's record keeps, above W_u, the first sector of its summary
+// in the summary array (28 bits) and its level count (4 bits).
+constexpr uint32_t kSumBits = 28;
+constexpr uint64_t kSumSectorsMax = 1ull << kSumBits;
+__host__ __device__ __forceinline__ uint32_t blocked_sum(uint64_t total) { return (uint32_t)(total >> 32) & (uint32_t)(kSumSectorsMax - 1); }
+__host__ __device__ __forceinline__ uint32_t blocked_levels(uint64_t total) { return (uint32_t)(total >> 60); }
 
 // ---------------------------------------------------------------- Philox ----
 // Philox4x32-10 (Salmon, Moraes, Dror, Shaw, SC'11): ten rounds; each round
@@ -212,9 +225,9 @@ struct NarrowEdges {
     }
     const EdgeN *e;
     // record index of edge 0 of a row whose region starts at `begin`
-    __host__ __device__ __forceinline__ static uint64_t edge_base(uint64_t begin, uint32_t d)
+    __host__ __device__ __forceinline__ static uint64_t edge_base(uint64_t begin, uint32_t)
     {
-        return begin + 4ull * summary_sectors(d);
+        return begin;  // the summary levels live in their own array
     }
     __device__ __forceinline__ uint2 load(uint64_t i) const
     {
@@ -320,9 +333,10 @@ __device__ __forceinline__ typename E::Rec search_serial_tally(const E &edges, u
 }
 
 
-__host__ __device__ __forceinline__ uint64_t pack_blocked_total(uint64_t W, uint32_t d)
+// sreg: the row's first summary sector (below 2^28)
+__host__ __device__ __forceinline__ uint64_t pack_blocked_total(uint64_t W, uint64_t sreg, uint32_t d)
 {
-    return W | ((uint64_t)summary_sectors(d) << 32) | ((uint64_t)tree_levels(d) << 56);
+    return W | (sreg << 32) | ((uint64_t)tree_levels(d) << 60);
 }
 
 // Number of the 8 keys k[0..7] that are <= x, for keys in ascending order with
@@ -337,14 +351,16 @@ __device__ __forceinline__ uint32_t rank8(uint32_t k0, uint32_t k1, uint32_t k2,
     return c + (kk <= x ? 1u : 0u);
 }
 
-// Search of a blocked narrow row (layout above) whose region starts at record
-// `begin`, with S summary sectors over L levels: the target of the first edge
-// with P > x.  TALLY counts the 32-byte sectors read.
+// Search of a blocked narrow row (layout above) whose blocks start at record
+// `begin` of E and whose L summary levels start at sector `S` of the summary
+// array SUM: the target of the first edge with P > x.  TALLY counts the
+// 32-byte sectors read.
 template <bool TALLY>
-__device__ __forceinline__ uint32_t search_blocked(const EdgeN *E, uint64_t begin, uint32_t d, uint32_t S, uint32_t L,
-                                                   uint32_t x, const NodeRecN *rec, uint32_t &sectors)
+__device__ __forceinline__ uint32_t search_blocked(const EdgeN *E, const uint32_t *SUM, uint64_t begin, uint32_t d,
+                                                   uint32_t S, uint32_t L, uint32_t x, const NodeRecN *rec,
+                                                   uint32_t &sectors)
 {
-    const unsigned char *base = reinterpret_cast<const unsigned char *>(E + begin);  // sector-aligned
+    const unsigned char *base = reinterpret_cast<const unsigned char *>(SUM + 8ull * S);  // the row's top level
     uint32_t b = 0, off = 0, l = L;
     if (root_in_record(d, L)) {  // the top level (one sector) is ranked from the node record
         const uint4 k = __ldg(reinterpret_cast<const uint4 *>(rec->key));
@@ -360,7 +376,7 @@ __device__ __forceinline__ uint32_t search_blocked(const EdgeN *E, uint64_t begi
         if (TALLY) ++sectors;
     }
     const uint32_t len = min(8u, d - 8 * b);
-    const unsigned char *q = base + 32ull * (S + 2 * b);  // 8-record block b: (P, col) pairs
+    const unsigned char *q = reinterpret_cast<const unsigned char *>(E + begin) + 64ull * b;  // block b: (P, col) pairs
     const Sector r0 = ld_block_sector(q);
     Sector r1;
     if (len > 4) r1 = ld_block_sector(q + 32);

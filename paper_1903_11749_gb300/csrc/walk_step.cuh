@@ -19,6 +19,7 @@ namespace ppr {
 struct KParams {
     const void *node;         // NodeRecN (narrow layout) or NodeRec (wide layout, alias tables)
     const void *edges;
+    const uint32_t *sum;      // narrow layout: the summary levels of the blocked rows
     const SegEntry *seg;
     uint32_t k0, k1, T, R, tag;
     int32_t dangling;
@@ -46,6 +47,7 @@ struct KParams {
     uint64_t r_magic;         // ceil(2^40 / R): walk index -> source index by multiply-shift
     int64_t n_nodes;          // node records (for the L2 window and the checked build)
     uint64_t n_records;       // checked build: records of the edge layout walked (alias: slots)
+    uint64_t n_sum;           // checked build: summary sectors
     uint64_t n_seg;           // checked build: segment entries allocated
     unsigned long long *err;  // checked build: flags of indices that left their array
 };
@@ -193,6 +195,9 @@ __device__ __forceinline__ bool walk_step(const KParams &p, const StepKey &key, 
     PPR_CHECK(segf || cnt < 2 ||
                   beg + (sizeof(typename E::Rec) == 8 ? (uint64_t)blocked_row_records(cnt) : (uint64_t)cnt) <= p.n_records,
               2);
+    PPR_CHECK(segf || cnt < 2 || sizeof(typename E::Rec) != 8 ||
+                  (uint64_t)blocked_sum(total) + summary_sectors(cnt) <= p.n_sum,
+              2);
     if (segf) {
         SegTable tab{p.seg};
         uint4 o = STATS ? search_serial_tally(tab, beg, cnt, xr, tl.sectors) : search_serial(tab, beg, cnt, xr);
@@ -215,8 +220,8 @@ __device__ __forceinline__ bool walk_step(const KParams &p, const StepKey &key, 
         next = (uint32_t)total;  // single out-edge: target kept in the node record
     } else if (!big) {
         if constexpr (sizeof(typename E::Rec) == 8) {
-            next = search_blocked<STATS>(edges.e, beg, cnt, (uint32_t)(total >> 32) & 0xffffffu, (uint32_t)(total >> 56),
-                                         (uint32_t)xr, static_cast<const NodeRecN *>(p.node) + u, tl.sectors);
+            next = search_blocked<STATS>(edges.e, p.sum, beg, cnt, blocked_sum(total), blocked_levels(total), (uint32_t)xr,
+                                         static_cast<const NodeRecN *>(p.node) + u, tl.sectors);
         } else {
             next = E::target(STATS ? search_serial_tally(edges, beg, cnt, xr, tl.sectors) : search_serial(edges, beg, cnt, xr));
         }
@@ -242,8 +247,8 @@ __device__ __forceinline__ bool walk_step(const KParams &p, const StepKey &key, 
 // walk_step; only the schedule of the loads changes.
 // Pending search of one lane: word i of lane t at ps[i * stride + t]
 // (structure of arrays: no bank conflicts).  Rows: beg (w0, w1), d (w2),
-// flags | levels left (w3), S (w4), sector offset (w5), block b (w6), key x
-// (w7).  Segment tables: bisection base (w0, w1), range n (w2), flags (w3),
+// flags | levels left (w3), first summary sector S (w4), sector offset (w5),
+// block b (w6), key x (w7).  Segment tables: bisection base (w0, w1), range n (w2), flags (w3),
 // key (w6, w7).  Flags: bit 31 the draw stops at the found target, bit 30 a
 // segment table.
 struct PendRef {
@@ -298,9 +303,10 @@ __device__ __forceinline__ bool walk_step_bounded(const KParams &p, const StepKe
             return false;
         } else {
             PPR_CHECK(beg + (uint64_t)blocked_row_records(cnt) <= p.n_records, 2);
+            PPR_CHECK((uint64_t)blocked_sum(r.total) + summary_sectors(cnt) <= p.n_sum, 2);
             d = cnt;
-            S = (uint32_t)(r.total >> 32) & 0xffffffu;
-            l = (uint32_t)(r.total >> 56);
+            S = blocked_sum(r.total);
+            l = blocked_levels(r.total);
             x = (uint32_t)mulhi64_by32(xv.x, xv.y, (uint32_t)r.total);
             if (root_in_record(d, l)) {  // the top level is ranked from the record's own sector
                 const uint4 kk = __ldg(reinterpret_cast<const uint4 *>(static_cast<const NodeRecN *>(p.node)[u].key));
@@ -360,8 +366,8 @@ __device__ __forceinline__ bool walk_step_bounded(const KParams &p, const StepKe
         pend = true;
         return false;
     }
-    // the row's search tree: levels l .. 1, then the 8-record block
-    const unsigned char *base = reinterpret_cast<const unsigned char *>(edges.e + beg);
+    // the row's search tree: levels l .. 1 (summary array), then the 8-record block
+    const unsigned char *base = reinterpret_cast<const unsigned char *>(p.sum + 8ull * S);
     while (l >= 1 && budget > 0) {
         const Sector kv = ld_sector(base + 32ull * (off + b));
         const uint32_t c = rank8(kv.v[0], kv.v[1], kv.v[2], kv.v[3], kv.v[4], kv.v[5], kv.v[6], x);
@@ -372,7 +378,7 @@ __device__ __forceinline__ bool walk_step_bounded(const KParams &p, const StepKe
     }
     if (budget > 0) {
         const uint32_t len = min(8u, d - 8 * b);
-        const unsigned char *q = base + 32ull * (S + 2 * b);
+        const unsigned char *q = reinterpret_cast<const unsigned char *>(edges.e + beg) + 64ull * b;
         const Sector r0 = ld_block_sector(q);
         Sector r1;
         if (len > 4) r1 = ld_block_sector(q + 32);
