@@ -181,11 +181,11 @@ __device__ __forceinline__ void block_stats(LayoutStats *st, uint32_t deg_max, u
 }
 
 // order: the caller's row of internal node u (renumbered layout), or null.
-// sizes: the row's block records in the edge array; ssizes: its summary
-// sectors in the summary array.
+// sizes: the row's records in the edge array (its blocks, and with
+// interleave its summary sectors before them); ssizes: its summary sectors.
 __global__ void __launch_bounds__(256) k_layout(int64_t n, int64_t m, const int64_t *row_ptr, const int32_t *order,
-                                                uint32_t *sizes, uint32_t *ssizes, LayoutStats *st, uint2 *huge,
-                                                uint32_t huge_cap)
+                                                bool interleave, uint32_t *sizes, uint32_t *ssizes, LayoutStats *st,
+                                                uint2 *huge, uint32_t huge_cap)
 {
     uint32_t dmax = 0, dang = 0, flags = 0;
     for (int64_t u = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; u < n; u += (int64_t)gridDim.x * blockDim.x) {
@@ -201,8 +201,8 @@ __global__ void __launch_bounds__(256) k_layout(int64_t n, int64_t m, const int6
             const uint32_t d = (uint32_t)(b - a);
             dmax = max(dmax, d);
             dang += d == 0;
-            sz = blocked_row_records(d);
             ssz = d >= 2 ? summary_sectors(d) : 0u;
+            sz = blocked_row_records(d) + (interleave ? 4 * ssz : 0u);
             if (d > kHugeRow) {  // a valid row_ptr has at most m / kHugeRow of them
                 const uint32_t k = atomicAdd(&st->n_huge, 1u);
                 if (k < huge_cap) huge[k] = make_uint2((uint32_t)u, d);
@@ -221,8 +221,8 @@ struct BuildArgs {
     const uint32_t *w;
     const int64_t *node_off;
     int32_t count;
-    const uint64_t *region;   // first block record of each row in E
-    const uint64_t *sregion;  // first summary sector of each row in K
+    const uint64_t *region;   // first record of each row's area in E
+    const uint64_t *sregion;  // first summary sector of each row in K, or null: summary at the start of the row's area
     NodeRecN *node;
     EdgeN *E;
     uint32_t *K;              // the summary array (8 keys a sector)
@@ -231,6 +231,19 @@ struct BuildArgs {
     const int32_t *order;  // renumbered layout: caller row of internal node u, else null
     const int32_t *rank;   // renumbered layout: internal id of caller node v, else null
 };
+
+// First block record (reg) and first summary sector (sreg) of row u of degree
+// d: separate arrays, or one area in E holding the summary, then the blocks.
+__device__ __forceinline__ void row_regions(const BuildArgs &A, int64_t u, uint32_t d, uint64_t &reg, uint64_t &sreg)
+{
+    if (A.sregion) {
+        reg = A.region[u];
+        sreg = A.sregion[u];
+    } else {
+        sreg = A.region[u] / 4;  // areas start on a 32-byte sector
+        reg = A.region[u] + (d >= 2 ? 4ull * summary_sectors(d) : 0ull);
+    }
+}
 
 // Input row (caller numbering) of internal node u, and the internal id of a
 // target the caller numbered c (c already checked to lie in [0, n)).
@@ -367,7 +380,8 @@ __global__ void __launch_bounds__(256) k_build_small(BuildArgs A)
         }
         int64_t hi_id;
         const int64_t base_id = instance_base(A, u, hi_id);
-        const uint64_t reg = A.region[u], sreg = A.sregion[u];
+        uint64_t reg, sreg;
+        row_regions(A, u, d, reg, sreg);
         const uint32_t L = tree_levels(d);  // 0 or 1 here
         const uint64_t eb = reg;
         uint64_t P = 0;
@@ -418,7 +432,8 @@ __global__ void __launch_bounds__(256) k_build_mid(BuildArgs A)
         const uint32_t d = (uint32_t)(A.row_ptr[o + 1] - a);
         int64_t hi_id;
         const int64_t base_id = instance_base(A, u, hi_id);
-        const uint64_t reg = A.region[u], sreg = A.sregion[u];
+        uint64_t reg, sreg;
+        row_regions(A, u, d, reg, sreg);
         const uint32_t L = tree_levels(d);
         const uint64_t eb = reg;
         uint64_t carry = 0;
@@ -458,7 +473,8 @@ __global__ void __launch_bounds__(512) k_build_big(BuildArgs A)
         const uint32_t d = (uint32_t)(A.row_ptr[o + 1] - a);
         int64_t hi_id;
         const int64_t base_id = instance_base(A, u, hi_id);
-        const uint64_t reg = A.region[u], sreg = A.sregion[u];
+        uint64_t reg, sreg;
+        row_regions(A, u, d, reg, sreg);
         const uint32_t L = tree_levels(d);
         const uint64_t eb = reg;
         uint64_t carry = 0;
@@ -586,7 +602,8 @@ __global__ void __launch_bounds__(256) k_build_tile_write(BuildTiles T)
     const int64_t a = A.row_ptr[in_row(A, rw.x)];
     int64_t hi_id;
     const int64_t base_id = instance_base(A, rw.x, hi_id);
-    const uint64_t reg = A.region[rw.x], sreg = A.sregion[rw.x];
+    uint64_t reg, sreg;
+    row_regions(A, rw.x, d, reg, sreg);
     const uint32_t L = tree_levels(d);
     const uint64_t eb = reg;
     const uint32_t end = min(tl.y + kBuildTile, d);
@@ -623,7 +640,8 @@ __global__ void __launch_bounds__(512) k_build_tile_finish(BuildTiles T)
     uint32_t *K = A.K;
     const uint4 rw = T.rows[blockIdx.x];
     const uint32_t d = rw.y, tid = threadIdx.x;
-    const uint64_t reg = A.region[rw.x], sreg = A.sregion[rw.x];
+    uint64_t reg, sreg;
+    row_regions(A, rw.x, d, reg, sreg);
     const uint32_t L = tree_levels(d);
     const uint64_t eb = reg;
     for (uint32_t i = d + tid; i < 4 * ceil_shift(d, 2); i += blockDim.x) {
@@ -672,15 +690,24 @@ static int build_narrow(ppr_ctx *ctx, int64_t n, int64_t m, const int64_t *d_rp,
     cudaError_t e = cudaMemsetAsync(d_ls, 0, sizeof(LayoutStats), st);
     if (e != cudaSuccess) return cuda_fail(e, "memset");
     const int tblocks = (int)std::max<int64_t>(1, std::min<int64_t>((n + 255) / 256, (int64_t)ctx->sms * 16));
-    k_layout<<<tblocks, 256, 0, st>>>(n, m, d_rp, g->order, d_sizes, d_ssizes, d_ls, d_huge, huge_cap);
+    // Summary levels in an array of their own on a renumbered layout (graphs
+    // far larger than L2: the summaries every draw passes through then pack
+    // L2 lines instead of sharing them with blocks a draw reads once); at the
+    // start of each row's area, before its blocks, otherwise (the summary
+    // sector of a small row shares a DRAM page with its blocks).  The record's
+    // 28-bit summary offset bounds the shared area: 2 m + 4 n records cover
+    // every row's blocks and summary.
+    const bool interleave = g->order == nullptr && (uint64_t)(2 * m + 4 * n) / 4 < kSumSectorsMax;
+    k_layout<<<tblocks, 256, 0, st>>>(n, m, d_rp, g->order, interleave, d_sizes, d_ssizes, d_ls, d_huge, huge_cap);
     note_launch();
     exclusive_scan_u32(d_sizes, n, d_region, d_scan, st);
-    exclusive_scan_u32(d_ssizes, n, d_sregion, d_scan, st);  // same scratch, after the first scan in stream order
+    if (!interleave) exclusive_scan_u32(d_ssizes, n, d_sregion, d_scan, st);  // same scratch, in stream order
     LayoutStats hs;
     uint64_t slots = 0, sum_sectors = 0;
     e = cudaMemcpyAsync(&hs, d_ls, sizeof(hs), cudaMemcpyDeviceToHost, st);
     if (e == cudaSuccess) e = cudaMemcpyAsync(&slots, d_region + n, sizeof(uint64_t), cudaMemcpyDeviceToHost, st);
-    if (e == cudaSuccess) e = cudaMemcpyAsync(&sum_sectors, d_sregion + n, sizeof(uint64_t), cudaMemcpyDeviceToHost, st);
+    if (e == cudaSuccess && !interleave)
+        e = cudaMemcpyAsync(&sum_sectors, d_sregion + n, sizeof(uint64_t), cudaMemcpyDeviceToHost, st);
     if (e == cudaSuccess) e = cudaStreamSynchronize(st);
     if (e != cudaSuccess) return cuda_fail(e, "graph layout");
     if (hs.status & kBadRowPtr) {
@@ -705,12 +732,16 @@ static int build_narrow(ppr_ctx *ctx, int64_t n, int64_t m, const int64_t *d_rp,
     const size_t edge_bytes = (size_t)(slots > 0 ? slots : 2) * sizeof(EdgeN);
     if ((rc = dev_alloc(&g->edges, edge_bytes, "edge records", st))) return rc;
     g->edge_records = (int64_t)slots;
-    const size_t sum_bytes = (size_t)(sum_sectors > 0 ? sum_sectors : 1) * 32;
-    if ((rc = dev_alloc((void **)&g->sum, sum_bytes, "row summaries", st))) return rc;
-    g->sum_sectors = (int64_t)sum_sectors;
+    size_t sum_bytes = 0;
+    if (!interleave) {
+        sum_bytes = (size_t)(sum_sectors > 0 ? sum_sectors : 1) * 32;
+        if ((rc = dev_alloc((void **)&g->sum, sum_bytes, "row summaries", st))) return rc;
+        g->sum_sectors = (int64_t)sum_sectors;
+    }
     g->device_bytes = (int64_t)(sizeof(NodeRecN) * n + edge_bytes + sum_bytes);
-    BuildArgs A{n, d_rp, d_col, d_w, d_off, g->instances, d_region, d_sregion, static_cast<NodeRecN *>(g->node),
-                (EdgeN *)g->edges, g->sum, d_ls, d_list, g->order, g->rank};
+    BuildArgs A{n, d_rp, d_col, d_w, d_off, g->instances, d_region, interleave ? nullptr : d_sregion,
+                static_cast<NodeRecN *>(g->node), (EdgeN *)g->edges,
+                interleave ? reinterpret_cast<uint32_t *>(g->edges) : g->sum, d_ls, d_list, g->order, g->rank};
     k_build_small<<<tblocks, 256, 0, st>>>(A);
     note_launch();
     k_build_mid<<<ctx->sms * 8, 256, 0, st>>>(A);

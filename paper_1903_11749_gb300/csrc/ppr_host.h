@@ -85,8 +85,11 @@ struct ppr_graph {
     void *node = nullptr;   // NodeRecN[n] (narrow layout) or NodeRec[n] (wide layout)
     void *edges = nullptr;  // EdgeN[m] or EdgeW[m]
     int64_t edge_records = 0;  // records the edge layout holds (blocked narrow rows: with padding)
-    uint32_t *sum = nullptr;   // narrow layout: the blocked rows' summary levels (8 keys a sector)
-    int64_t sum_sectors = 0;
+    uint32_t *sum = nullptr;   // narrow layout: the blocked rows' summary levels (8 keys a sector), or
+    int64_t sum_sectors = 0;   // null: each row's summary precedes its blocks in the edge array
+    // where the walkers read summary sectors (the summary array or the edge array) and how many there are
+    const uint32_t *sum_base() const { return sum ? sum : static_cast<const uint32_t *>(edges); }
+    uint64_t sum_extent() const { return sum ? (uint64_t)sum_sectors : (uint64_t)edge_records / 4; }
     // internal numbering of the layout (renumber.cu), or null: caller ids
     int32_t *order = nullptr;  // [n] caller id of internal node i
     int32_t *rank = nullptr;   // [n] internal id of caller node v

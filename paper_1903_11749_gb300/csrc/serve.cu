@@ -953,8 +953,8 @@ static int launch_loop_typed(Server *sv)
     P.kp.rank = g->rank;
     P.kp.order = g->order;
     P.kp.n_records = sv->cfg.sampler == 1 ? (uint64_t)g->m : (uint64_t)g->edge_records;
-    P.kp.sum = g->sum;
-    P.kp.n_sum = (uint64_t)g->sum_sectors;
+    P.kp.sum = g->sum_base();
+    P.kp.n_sum = g->sum_extent();
     P.kp.err = &sv->d_glob->err;
     P.desc = sv->d_desc;
     P.slot = sv->d_slot;

@@ -396,8 +396,8 @@ int launch_walks(ppr_ctx *ctx, const ppr_graph *g, const RunPlan &plan, const Ou
     kp.step_loads = (uint32_t)std::max(plan.step_loads, 0);
     kp.n_nodes = g->n;
     kp.n_records = plan.sampler == 1 ? (uint64_t)g->m : (uint64_t)g->edge_records;
-    kp.sum = g->sum;
-    kp.n_sum = (uint64_t)g->sum_sectors;
+    kp.sum = g->sum_base();
+    kp.n_sum = g->sum_extent();
     kp.n_seg = (uint64_t)g->seg.entries_cap;
     kp.err = o.counters + 4;
     kp.ends = reinterpret_cast<uint32_t *>(ws);
