@@ -965,8 +965,8 @@ def main():
         G, r = step(kernel=ppr.KERNEL_PLAIN)
         r.wait()
         del r, G
-        pm = []
-        for _ in range(max(1, min(3, args.steps))):
+        pm, pk = [], []
+        for _ in range(max(1, min(10 if step_ms and statistics.mean(step_ms) < 10 else 3, args.steps))):
             flush.fill_(1)
             e0 = torch.cuda.Event(enable_timing=True)
             e1 = torch.cuda.Event(enable_timing=True)
@@ -976,8 +976,10 @@ def main():
             r.wait()
             e1.synchronize()
             pm.append(e0.elapsed_time(e1))
+            pk.append(r.info().kernel_ms)
             del r, G
         plain = {"value": steps_per_pass / (statistics.mean(pm) / 1e3), "unit": "walk steps/s",
+                 "kernel_ms": statistics.mean(pk),
                  "ms_per_step": statistics.mean(pm), "kernel": "one thread per walk + separate aggregation"}
 
     # end to end through the C ABI with host buffers: pinned CSR in, rows + top-k out to pinned memory

@@ -267,7 +267,10 @@ __device__ __forceinline__ void write_node(const BuildArgs &A, int64_t u, uint64
 {
     NodeRecN r;
     r.word0 = pack_word0(reg, d, false);
-    r.total = d == 1 ? (uint64_t)first_target : (d == 0 ? 0ull : pack_blocked_total(W, d > 8 ? sreg : 0, d));
+    // summary field: the first sector in the summary array (split layout), or
+    // the number of summary sectors before the blocks (see blocked_sum)
+    const uint64_t field = d <= 8 ? 0ull : (A.sregion ? sreg : (uint64_t)summary_sectors(d));
+    r.total = d == 1 ? (uint64_t)first_target : (d == 0 ? 0ull : pack_blocked_total(W, field, d));
     const uint32_t L = d >= 2 ? tree_levels(d) : 0;
     const bool root = root_in_record(d, L);
 #pragma unroll

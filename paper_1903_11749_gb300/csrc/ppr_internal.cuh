@@ -127,8 +127,11 @@ __host__ __device__ __forceinline__ uint32_t blocked_row_records(uint32_t d)
     return 4 * ceil_shift(d, 2);
 }
 
-// A blocked row's record keeps, above W_u, the first sector of its summary
-// in the summary array (28 bits) and its level count (4 bits).
+// A blocked row's record keeps, above W_u, a 28-bit summary field and its
+// level count (4 bits).  The field is the row's first sector in the summary
+// array on a split layout (renumbered graphs far larger than L2), and the
+// number of summary sectors that precede the row's blocks in the edge array
+// otherwise; the record's begin points at the blocks either way.
 constexpr uint32_t kSumBits = 28;
 constexpr uint64_t kSumSectorsMax = 1ull << kSumBits;
 __host__ __device__ __forceinline__ uint32_t blocked_sum(uint64_t total) { return (uint32_t)(total >> 32) & (uint32_t)(kSumSectorsMax - 1); }
@@ -191,19 +194,28 @@ __device__ __forceinline__ Sector ld_sector(const void *p)
 }
 
 
-// One 32-byte sector of a row's bottom block, with an evict-first L2 policy:
-// a bottom block serves the one draw that picked it and is rarely read again
-// before it leaves L2, while node records and summary sectors are shared by
-// every draw that passes the same node, so blocks should be the first to go.
+// One 32-byte sector of a row's bottom block.  EF (layouts of graphs far
+// larger than L2) loads it with an evict-first L2 policy: a bottom block
+// serves the one draw that picked it and is rarely read again before it would
+// leave L2, while node records and summary sectors are shared by every draw
+// that passes the same node, so blocks should be the first to go.  On a graph
+// about the size of L2 the blocks are reused (evict-first there cost the
+// 2,048-graph batch 3 %), so they keep the normal policy.
+template <bool EF>
 __device__ __forceinline__ Sector ld_block_sector(const void *p)
 {
-    uint64_t pol;
-    asm("createpolicy.fractional.L2::evict_first.b64 %0, 1.0;" : "=l"(pol));
-    Sector s;
-    asm("ld.global.nc.L2::cache_hint.v8.u32 {%0,%1,%2,%3,%4,%5,%6,%7}, [%8], %9;"
-        : "=r"(s.v[0]), "=r"(s.v[1]), "=r"(s.v[2]), "=r"(s.v[3]), "=r"(s.v[4]), "=r"(s.v[5]), "=r"(s.v[6]), "=r"(s.v[7])
-        : "l"(p), "l"(pol));
-    return s;
+    if constexpr (!EF) {
+        return ld_sector(p);
+    } else {
+        uint64_t pol;
+        asm("createpolicy.fractional.L2::evict_first.b64 %0, 1.0;" : "=l"(pol));
+        Sector s;
+        asm("ld.global.nc.L2::cache_hint.v8.u32 {%0,%1,%2,%3,%4,%5,%6,%7}, [%8], %9;"
+            : "=r"(s.v[0]), "=r"(s.v[1]), "=r"(s.v[2]), "=r"(s.v[3]), "=r"(s.v[4]), "=r"(s.v[5]), "=r"(s.v[6]),
+              "=r"(s.v[7])
+            : "l"(p), "l"(pol));
+        return s;
+    }
 }
 
 // A blocked row of d edges with L >= 1 summary levels keeps its top level's
@@ -333,10 +345,10 @@ __device__ __forceinline__ typename E::Rec search_serial_tally(const E &edges, u
 }
 
 
-// sreg: the row's first summary sector (below 2^28)
-__host__ __device__ __forceinline__ uint64_t pack_blocked_total(uint64_t W, uint64_t sreg, uint32_t d)
+// field: the row's summary field (below 2^28; see blocked_sum)
+__host__ __device__ __forceinline__ uint64_t pack_blocked_total(uint64_t W, uint64_t field, uint32_t d)
 {
-    return W | (sreg << 32) | ((uint64_t)tree_levels(d) << 60);
+    return W | (field << 32) | ((uint64_t)tree_levels(d) << 60);
 }
 
 // Number of the 8 keys k[0..7] that are <= x, for keys in ascending order with
@@ -351,16 +363,25 @@ __device__ __forceinline__ uint32_t rank8(uint32_t k0, uint32_t k1, uint32_t k2,
     return c + (kk <= x ? 1u : 0u);
 }
 
+// First byte of a blocked row's summary (its top level): sector S of the
+// summary array SUM (SPLIT), or the S sectors before the row's blocks.
+template <bool SPLIT>
+__device__ __forceinline__ const unsigned char *summary_base(const EdgeN *E, const uint32_t *SUM, uint64_t begin,
+                                                             uint32_t S)
+{
+    if constexpr (SPLIT) return reinterpret_cast<const unsigned char *>(SUM + 8ull * S);
+    else return reinterpret_cast<const unsigned char *>(E + begin) - 32ull * S;
+}
+
 // Search of a blocked narrow row (layout above) whose blocks start at record
-// `begin` of E and whose L summary levels start at sector `S` of the summary
-// array SUM: the target of the first edge with P > x.  TALLY counts the
-// 32-byte sectors read.
-template <bool TALLY>
+// `begin` of E, with summary field S and L summary levels: the target of the
+// first edge with P > x.  TALLY counts the 32-byte sectors read.
+template <bool TALLY, bool SPLIT>
 __device__ __forceinline__ uint32_t search_blocked(const EdgeN *E, const uint32_t *SUM, uint64_t begin, uint32_t d,
                                                    uint32_t S, uint32_t L, uint32_t x, const NodeRecN *rec,
                                                    uint32_t &sectors)
 {
-    const unsigned char *base = reinterpret_cast<const unsigned char *>(SUM + 8ull * S);  // the row's top level
+    const unsigned char *base = summary_base<SPLIT>(E, SUM, begin, S);  // the row's top level
     uint32_t b = 0, off = 0, l = L;
     if (root_in_record(d, L)) {  // the top level (one sector) is ranked from the node record
         const uint4 k = __ldg(reinterpret_cast<const uint4 *>(rec->key));
@@ -377,9 +398,9 @@ __device__ __forceinline__ uint32_t search_blocked(const EdgeN *E, const uint32_
     }
     const uint32_t len = min(8u, d - 8 * b);
     const unsigned char *q = reinterpret_cast<const unsigned char *>(E + begin) + 64ull * b;  // block b: (P, col) pairs
-    const Sector r0 = ld_block_sector(q);
+    const Sector r0 = ld_block_sector<SPLIT>(q);
     Sector r1;
-    if (len > 4) r1 = ld_block_sector(q + 32);
+    if (len > 4) r1 = ld_block_sector<SPLIT>(q + 32);
     else {
 #pragma unroll
         for (int i = 0; i < 8; ++i) r1.v[i] = 0xffffffffu;

@@ -338,7 +338,7 @@ __device__ __forceinline__ void count_walks(const LoopParams &P, uint32_t q, uin
     if (old + n == __ldcg(&P.desc[q].walks)) P.slot[q].t_walks = gtime_ns();
 }
 
-template <class E>
+template <class E, bool SPLIT>
 __device__ void walker_warp(const LoopParams &P, WalkChunk &wc, uint32_t **ends_of, uint32_t gwarp,
                             unsigned long long *s_tail)
 {
@@ -463,7 +463,7 @@ __device__ void walker_warp(const LoopParams &P, WalkChunk &wc, uint32_t **ends_
         uint32_t end = 0;
         bool fin = false;
         const long long c0 = clock64();
-        if (walk_step<E, false, false, false>(P.kp, key, edges, active, s0, src, j, 0, k, u, end, tl)) {
+        if (walk_step<E, false, false, false, SPLIT>(P.kp, key, edges, active, s0, src, j, 0, k, u, end, tl)) {
             ends_of[q][g] = end;
             active = false;
             fin = true;
@@ -683,7 +683,8 @@ __device__ void aggregator_warp(const LoopParams &P, uint32_t *smem, unsigned lo
     }
 }
 
-template <class E>
+// SPLIT: the narrow layout of a renumbered graph (see search_blocked)
+template <class E, bool SPLIT = false>
 __global__ void __launch_bounds__(32 * kLoopWarps, 4) k_serve_loop(LoopParams P)
 {
     __shared__ WalkChunk wc[kLoopWarps - 1];
@@ -697,7 +698,7 @@ __global__ void __launch_bounds__(32 * kLoopWarps, 4) k_serve_loop(LoopParams P)
         aggregator_warp(P, smem, s_tail);
         return;
     }
-    walker_warp<E>(P, wc[wid], ends_of, blockIdx.x * (kLoopWarps - 1) + wid, s_tail);
+    walker_warp<E, SPLIT>(P, wc[wid], ends_of, blockIdx.x * (kLoopWarps - 1) + wid, s_tail);
 }
 
 // ============================================================ queries ====
@@ -941,7 +942,7 @@ static void scheduler_streams(Server *sv)
 
 // ---------------------------------------------------------- device loop ----
 
-template <class E>
+template <class E, bool SPLIT = false>
 static int launch_loop_typed(Server *sv)
 {
     const ppr_graph *g = sv->g;
@@ -964,11 +965,11 @@ static int launch_loop_typed(Server *sv)
     P.idle_ns = (uint64_t)(sv->cfg.idle_us > 0 ? sv->cfg.idle_us : 200000) * 1000ull;
     if (!sv->grid) {
         int per_sm = 0;
-        PPR_CUDA(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_serve_loop<E>, 32 * kLoopWarps, 0));
+        PPR_CUDA(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_serve_loop<E, SPLIT>, 32 * kLoopWarps, 0));
         sv->grid = (uint32_t)(sv->ctx->sms * std::max(per_sm, 1));
     }
     P.walker_warps = sv->grid * (kLoopWarps - 1);
-    k_serve_loop<E><<<sv->grid, 32 * kLoopWarps, 0, sv->loop_stream>>>(P);
+    k_serve_loop<E, SPLIT><<<sv->grid, 32 * kLoopWarps, 0, sv->loop_stream>>>(P);
     note_launch();
     PPR_CUDA(cudaGetLastError());
     PPR_CUDA(cudaEventRecord(sv->loop_done, sv->loop_stream));
@@ -981,6 +982,7 @@ static int launch_loop(Server *sv)
     int rc;
     if (sv->cfg.sampler == 1) rc = launch_loop_typed<AliasEdges>(sv);
     else if (sv->g->wide) rc = launch_loop_typed<WideEdges>(sv);
+    else if (sv->g->sum) rc = launch_loop_typed<NarrowEdges, true>(sv);
     else rc = launch_loop_typed<NarrowEdges>(sv);
     if (rc == PPR_OK) {
         sv->loop_running = true;

@@ -41,7 +41,7 @@ __device__ __forceinline__ void warp_add_tally(unsigned long long *dst, const Ta
 #define PPR_WALK_MINB 6  // resident 256-thread blocks per SM asked of ptxas (6: 40 registers, no spills)
 #endif
 
-template <class E, bool SEG, bool STATS>
+template <class E, bool SEG, bool STATS, bool SPLIT = false>
 __global__ void __launch_bounds__(256, PPR_WALK_MINB) k_walk_plain(KParams p)
 {
     const E edges = make_edges<E>(p.edges);
@@ -68,8 +68,8 @@ __global__ void __launch_bounds__(256, PPR_WALK_MINB) k_walk_plain(KParams p)
         // restarts) at its node of the layout
         const uint32_t s0 = p.rank ? (uint32_t)p.rank[src] : src;
         uint32_t k = 0, u = s0, end = 0;
-        while (!walk_step<E, SEG, false, STATS>(p, StepKey{p.k0, p.k1, p.T}, edges, true, s0, src - ctr_base, j, tag, k, u,
-                                                 end, tl)) {
+        while (!walk_step<E, SEG, false, STATS, SPLIT>(p, StepKey{p.k0, p.k1, p.T}, edges, true, s0, src - ctr_base, j,
+                                                        tag, k, u, end, tl)) {
         }
         p.ends[t] = end - ctr_base;
     }
@@ -97,7 +97,7 @@ __device__ __forceinline__ uint32_t div_by_R(uint32_t w, uint64_t magic)
     return (uint32_t)(((uint64_t)w * magic) >> 40);  // exact for w < 2^20, R <= 4096
 }
 
-template <class E, bool SEG, bool STATS, bool BOUNDED = false>
+template <class E, bool SEG, bool STATS, bool BOUNDED = false, bool SPLIT = false>
 __global__ void __launch_bounds__(256, PPR_WALK_MINB) k_walk_persistent(KParams p)
 {
     __shared__ WarpQueue wq_all[8];
@@ -182,10 +182,10 @@ __global__ void __launch_bounds__(256, PPR_WALK_MINB) k_walk_persistent(KParams 
         uint32_t end = 0;
         bool ended;
         if constexpr (BOUNDED) {
-            ended = active && walk_step_bounded<SEG>(p, StepKey{p.k0, p.k1, p.T}, edges, src, sctr, j, tag, k, u, end,
+            ended = active && walk_step_bounded<SEG, SPLIT>(p, StepKey{p.k0, p.k1, p.T}, edges, src, sctr, j, tag, k, u, end,
                                                      pend, PendRef{ps_all, blockDim.x, threadIdx.x}, tl);
         } else {
-            ended = walk_step<E, SEG, true, STATS>(p, StepKey{p.k0, p.k1, p.T}, edges, active, src, sctr, j, tag, k, u,
+            ended = walk_step<E, SEG, true, STATS, SPLIT>(p, StepKey{p.k0, p.k1, p.T}, edges, active, src, sctr, j, tag, k, u,
                                                    end, tl);
         }
         if (ended) {
@@ -213,7 +213,7 @@ static int walker_event(ppr_result *r, cudaStream_t st)
     return PPR_OK;
 }
 
-template <class E, bool SEG, bool STATS, bool BOUNDED = false>
+template <class E, bool SEG, bool STATS, bool BOUNDED = false, bool SPLIT = false>
 static int launch_typed(ppr_ctx *ctx, const KParams &kp, const RunPlan &plan, int64_t S, cudaStream_t st,
                         ppr_result *r)
 {
@@ -223,7 +223,7 @@ static int launch_typed(ppr_ctx *ctx, const KParams &kp, const RunPlan &plan, in
         int blocks = (int)std::min<uint64_t>((total + 255) / 256, (uint64_t)ctx->sms * 64);
         if (blocks < 1) blocks = 1;
         if ((rc = walker_event(r, st))) return rc;
-        k_walk_plain<E, SEG, STATS><<<blocks, 256, 0, st>>>(kp);
+        k_walk_plain<E, SEG, STATS, SPLIT><<<blocks, 256, 0, st>>>(kp);
         note_launch();
         PPR_CUDA(cudaGetLastError());
         if ((rc = walker_event(r, st))) return rc;
@@ -232,7 +232,8 @@ static int launch_typed(ppr_ctx *ctx, const KParams &kp, const RunPlan &plan, in
     int per_sm = 0;
     // walkers per CTA: 32 * warps_per_block (4 or 8 warps; default 8)
     const int wpb = plan.warps_per_block == 4 ? 4 : 8;
-    PPR_CUDA(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_walk_persistent<E, SEG, STATS, BOUNDED>, 32 * wpb, 0));
+    PPR_CUDA(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_walk_persistent<E, SEG, STATS, BOUNDED, SPLIT>,
+                                                           32 * wpb, 0));
     if (per_sm < 1) per_sm = 1;
     int64_t blocks = (int64_t)ctx->sms * per_sm;
     int64_t needed = ((int64_t)kp.nchunks + wpb - 1) / wpb;
@@ -260,7 +261,7 @@ static int launch_typed(ppr_ctx *ctx, const KParams &kp, const RunPlan &plan, in
         cfg.attrs = attr;
         cfg.numAttrs = 1;
     }
-    PPR_CUDA(cudaLaunchKernelEx(&cfg, k_walk_persistent<E, SEG, STATS, BOUNDED>, kp));
+    PPR_CUDA(cudaLaunchKernelEx(&cfg, k_walk_persistent<E, SEG, STATS, BOUNDED, SPLIT>, kp));
     note_launch();
     PPR_CUDA(cudaGetLastError());
     if ((rc = walker_event(r, st))) return rc;
@@ -319,12 +320,12 @@ size_t launch_workspace_bytes(const ppr_graph *g, const RunPlan &plan, int64_t S
 // Every kernel a run can launch is loaded here, once per device.  With lazy
 // module loading the first launch of a kernel may wait for the device to go
 // idle; loaded up front, a run's launches stay asynchronous.
-template <class E, bool SEG, bool STATS>
+template <class E, bool SEG, bool STATS, bool SPLIT = false>
 static void preload_walkers()
 {
     cudaFuncAttributes a;
-    cudaFuncGetAttributes(&a, k_walk_plain<E, SEG, STATS>);
-    cudaFuncGetAttributes(&a, k_walk_persistent<E, SEG, STATS>);
+    cudaFuncGetAttributes(&a, k_walk_plain<E, SEG, STATS, SPLIT>);
+    cudaFuncGetAttributes(&a, k_walk_persistent<E, SEG, STATS, false, SPLIT>);
 }
 
 void preload_run_kernels()
@@ -336,6 +337,12 @@ void preload_run_kernels()
     cudaFuncAttributes fa;
     cudaFuncGetAttributes(&fa, k_walk_persistent<NarrowEdges, false, false, true>);
     cudaFuncGetAttributes(&fa, k_walk_persistent<NarrowEdges, true, false, true>);
+    preload_walkers<NarrowEdges, false, false, true>();
+    preload_walkers<NarrowEdges, true, false, true>();
+    preload_walkers<NarrowEdges, false, true, true>();
+    preload_walkers<NarrowEdges, true, true, true>();
+    cudaFuncGetAttributes(&fa, k_walk_persistent<NarrowEdges, false, false, true, true>);
+    cudaFuncGetAttributes(&fa, k_walk_persistent<NarrowEdges, true, false, true, true>);
     preload_walkers<WideEdges, false, false>();
     preload_walkers<WideEdges, true, false>();
     preload_walkers<WideEdges, false, true>();
@@ -356,6 +363,23 @@ void preload_run_kernels()
     cudaFuncGetAttributes(&a, k_scan_tile_offsets);
     cudaFuncGetAttributes(&a, k_scan_apply);
     cudaGetLastError();
+}
+
+// Narrow layout: SPLIT for a renumbered graph's layout (summary array,
+// evict-first bottom blocks), else summaries before each row's blocks.
+template <bool SPLIT>
+static int launch_narrow(ppr_ctx *ctx, const KParams &kp, const RunPlan &plan, int64_t S, cudaStream_t st,
+                         ppr_result *ev_owner)
+{
+    if (plan.stats)
+        return plan.segments ? launch_typed<NarrowEdges, true, true, false, SPLIT>(ctx, kp, plan, S, st, ev_owner)
+                             : launch_typed<NarrowEdges, false, true, false, SPLIT>(ctx, kp, plan, S, st, ev_owner);
+    // the bounded step: persistent kernel, no cooperative search (statistics launches took the branch above)
+    if (plan.step_loads > 0 && plan.kernel == PPR_KERNEL_PERSISTENT && kp.large == 0xffffffffu)
+        return plan.segments ? launch_typed<NarrowEdges, true, false, true, SPLIT>(ctx, kp, plan, S, st, ev_owner)
+                             : launch_typed<NarrowEdges, false, false, true, SPLIT>(ctx, kp, plan, S, st, ev_owner);
+    return plan.segments ? launch_typed<NarrowEdges, true, false, false, SPLIT>(ctx, kp, plan, S, st, ev_owner)
+                         : launch_typed<NarrowEdges, false, false, false, SPLIT>(ctx, kp, plan, S, st, ev_owner);
 }
 
 int launch_walks(ppr_ctx *ctx, const ppr_graph *g, const RunPlan &plan, const Outputs &o, int64_t s_begin, int64_t S,
@@ -449,22 +473,15 @@ int launch_walks(ppr_ctx *ctx, const ppr_graph *g, const RunPlan &plan, const Ou
     if (plan.sampler == 1)
         return plan.stats ? launch_typed<AliasEdges, false, true>(ctx, kp, plan, S, st, ev_owner)
                           : launch_typed<AliasEdges, false, false>(ctx, kp, plan, S, st, ev_owner);
-    if (plan.stats) {
-        if (g->wide)
+    if (g->wide) {
+        if (plan.stats)
             return plan.segments ? launch_typed<WideEdges, true, true>(ctx, kp, plan, S, st, ev_owner)
                                  : launch_typed<WideEdges, false, true>(ctx, kp, plan, S, st, ev_owner);
-        return plan.segments ? launch_typed<NarrowEdges, true, true>(ctx, kp, plan, S, st, ev_owner)
-                             : launch_typed<NarrowEdges, false, true>(ctx, kp, plan, S, st, ev_owner);
-    }
-    if (g->wide)
         return plan.segments ? launch_typed<WideEdges, true, false>(ctx, kp, plan, S, st, ev_owner)
                              : launch_typed<WideEdges, false, false>(ctx, kp, plan, S, st, ev_owner);
-    // the bounded step: persistent kernel, no cooperative search (statistics launches took the branch above)
-    if (plan.step_loads > 0 && plan.kernel == PPR_KERNEL_PERSISTENT && kp.large == 0xffffffffu)
-        return plan.segments ? launch_typed<NarrowEdges, true, false, true>(ctx, kp, plan, S, st, ev_owner)
-                             : launch_typed<NarrowEdges, false, false, true>(ctx, kp, plan, S, st, ev_owner);
-    return plan.segments ? launch_typed<NarrowEdges, true, false>(ctx, kp, plan, S, st, ev_owner)
-                         : launch_typed<NarrowEdges, false, false>(ctx, kp, plan, S, st, ev_owner);
+    }
+    return g->sum ? launch_narrow<true>(ctx, kp, plan, S, st, ev_owner)
+                  : launch_narrow<false>(ctx, kp, plan, S, st, ev_owner);
 }
 
 // ------------------------------------------------ allocation-free run ----

@@ -101,7 +101,9 @@ struct StepKey {
     uint32_t k0, k1, T;
 };
 
-template <class E, bool SEG, bool COOP, bool STATS>
+// SPLIT: the narrow layout of a renumbered graph (summaries in their own
+// array, evict-first bottom blocks); see search_blocked.
+template <class E, bool SEG, bool COOP, bool STATS, bool SPLIT = false>
 __device__ __forceinline__ bool walk_step(const KParams &p, const StepKey &key, const E &edges, bool act, uint32_t src,
                                           uint32_t sctr, uint32_t j, uint32_t tag, uint32_t &k, uint32_t &u,
                                           uint32_t &end, Tally &tl)
@@ -196,7 +198,8 @@ __device__ __forceinline__ bool walk_step(const KParams &p, const StepKey &key, 
                   beg + (sizeof(typename E::Rec) == 8 ? (uint64_t)blocked_row_records(cnt) : (uint64_t)cnt) <= p.n_records,
               2);
     PPR_CHECK(segf || cnt < 2 || sizeof(typename E::Rec) != 8 ||
-                  (uint64_t)blocked_sum(total) + summary_sectors(cnt) <= p.n_sum,
+                  (SPLIT ? (uint64_t)blocked_sum(total) + summary_sectors(cnt) <= p.n_sum
+                         : blocked_sum(total) == summary_sectors(cnt) && 4ull * blocked_sum(total) <= beg),
               2);
     if (segf) {
         SegTable tab{p.seg};
@@ -220,8 +223,8 @@ __device__ __forceinline__ bool walk_step(const KParams &p, const StepKey &key, 
         next = (uint32_t)total;  // single out-edge: target kept in the node record
     } else if (!big) {
         if constexpr (sizeof(typename E::Rec) == 8) {
-            next = search_blocked<STATS>(edges.e, p.sum, beg, cnt, blocked_sum(total), blocked_levels(total), (uint32_t)xr,
-                                         static_cast<const NodeRecN *>(p.node) + u, tl.sectors);
+            next = search_blocked<STATS, SPLIT>(edges.e, p.sum, beg, cnt, blocked_sum(total), blocked_levels(total),
+                                                (uint32_t)xr, static_cast<const NodeRecN *>(p.node) + u, tl.sectors);
         } else {
             next = E::target(STATS ? search_serial_tally(edges, beg, cnt, xr, tl.sectors) : search_serial(edges, beg, cnt, xr));
         }
@@ -247,7 +250,7 @@ __device__ __forceinline__ bool walk_step(const KParams &p, const StepKey &key, 
 // walk_step; only the schedule of the loads changes.
 // Pending search of one lane: word i of lane t at ps[i * stride + t]
 // (structure of arrays: no bank conflicts).  Rows: beg (w0, w1), d (w2),
-// flags | levels left (w3), first summary sector S (w4), sector offset (w5),
+// flags | levels left (w3), summary field S (w4), sector offset (w5),
 // block b (w6), key x (w7).  Segment tables: bisection base (w0, w1), range n (w2), flags (w3),
 // key (w6, w7).  Flags: bit 31 the draw stops at the found target, bit 30 a
 // segment table.
@@ -257,7 +260,7 @@ struct PendRef {
     __device__ __forceinline__ uint32_t &operator[](int i) const { return ps[i * stride + t]; }
 };
 
-template <bool SEG>
+template <bool SEG, bool SPLIT>
 __device__ __forceinline__ bool walk_step_bounded(const KParams &p, const StepKey &key, const NarrowEdges &edges,
                                                   uint32_t src, uint32_t sctr, uint32_t j, uint32_t tag, uint32_t &k,
                                                   uint32_t &u, uint32_t &end, bool &pend, const PendRef &ps, Tally &tl)
@@ -303,7 +306,9 @@ __device__ __forceinline__ bool walk_step_bounded(const KParams &p, const StepKe
             return false;
         } else {
             PPR_CHECK(beg + (uint64_t)blocked_row_records(cnt) <= p.n_records, 2);
-            PPR_CHECK((uint64_t)blocked_sum(r.total) + summary_sectors(cnt) <= p.n_sum, 2);
+            PPR_CHECK(SPLIT ? (uint64_t)blocked_sum(r.total) + summary_sectors(cnt) <= p.n_sum
+                            : blocked_sum(r.total) == summary_sectors(cnt) && 4ull * blocked_sum(r.total) <= beg,
+                      2);
             d = cnt;
             S = blocked_sum(r.total);
             l = blocked_levels(r.total);
@@ -366,8 +371,8 @@ __device__ __forceinline__ bool walk_step_bounded(const KParams &p, const StepKe
         pend = true;
         return false;
     }
-    // the row's search tree: levels l .. 1 (summary array), then the 8-record block
-    const unsigned char *base = reinterpret_cast<const unsigned char *>(p.sum + 8ull * S);
+    // the row's search tree: levels l .. 1, then the 8-record block
+    const unsigned char *base = summary_base<SPLIT>(edges.e, p.sum, beg, S);
     while (l >= 1 && budget > 0) {
         const Sector kv = ld_sector(base + 32ull * (off + b));
         const uint32_t c = rank8(kv.v[0], kv.v[1], kv.v[2], kv.v[3], kv.v[4], kv.v[5], kv.v[6], x);
@@ -379,9 +384,9 @@ __device__ __forceinline__ bool walk_step_bounded(const KParams &p, const StepKe
     if (budget > 0) {
         const uint32_t len = min(8u, d - 8 * b);
         const unsigned char *q = reinterpret_cast<const unsigned char *>(edges.e + beg) + 64ull * b;
-        const Sector r0 = ld_block_sector(q);
+        const Sector r0 = ld_block_sector<SPLIT>(q);
         Sector r1;
-        if (len > 4) r1 = ld_block_sector(q + 32);
+        if (len > 4) r1 = ld_block_sector<SPLIT>(q + 32);
         else {
 #pragma unroll
             for (int i = 0; i < 8; ++i) r1.v[i] = 0xffffffffu;
