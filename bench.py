@@ -168,9 +168,9 @@ RENUMBER = {"auto": None, "on": True, "off": False}  # --renumber -> ppr load_gr
 
 
 def kernel_source_hash():
-    """Hash of the walker's source files (the launch, the step, the layout, its numbering)."""
+    """Hash of the walker's source files (the launch, the step, the layout and its build, the numbering)."""
     h = hashlib.sha256()
-    for f in ("walk.cu", "walk_step.cuh", "ppr_internal.cuh", "renumber.cu"):
+    for f in ("walk.cu", "walk_step.cuh", "ppr_internal.cuh", "renumber.cu", "graph.cu"):
         h.update(open(os.path.join(ROOT, "paper_1903_11749_gb300", "csrc", f), "rb").read())
     return h.hexdigest()[:16]
 

@@ -202,7 +202,9 @@ __global__ void __launch_bounds__(256) k_layout(int64_t n, int64_t m, const int6
             dmax = max(dmax, d);
             dang += d == 0;
             ssz = d >= 2 ? summary_sectors(d) : 0u;
-            sz = blocked_row_records(d) + (interleave ? 4 * ssz : 0u);
+            // split layout: every row's blocks start on 64 bytes (a full block is
+            // one 64-byte DRAM fetch); otherwise on 32 bytes after the summary
+            sz = interleave ? blocked_row_records(d) + 4 * ssz : (d <= 1 ? 0u : 8u * ceil_shift(d, 3));
             if (d > kHugeRow) {  // a valid row_ptr has at most m / kHugeRow of them
                 const uint32_t k = atomicAdd(&st->n_huge, 1u);
                 if (k < huge_cap) huge[k] = make_uint2((uint32_t)u, d);
