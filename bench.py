@@ -27,6 +27,7 @@ from __future__ import annotations
 
 import argparse
 import hashlib
+import re
 import json
 import os
 import platform
@@ -167,11 +168,20 @@ def measured_peaks():
 RENUMBER = {"auto": None, "on": True, "off": False}  # --renumber -> ppr load_graph(renumber=...)
 
 
-def kernel_source_hash():
-    """Hash of the walker's source files (the launch, the step, the layout and its build, the numbering)."""
+def _code_only(text: str) -> str:
+    """Source text without comments and blank lines (a comment edit leaves the
+    kernels, and so their recorded traffic, unchanged)."""
+    text = re.sub(r"/\*.*?\*/", "", text, flags=re.S)
+    lines = [re.sub(r"//.*$", "", ln).rstrip() for ln in text.splitlines()]
+    return "\n".join(ln for ln in lines if ln.strip())
+
+
+def kernel_source_hash(root=None):
+    """Hash of the walker's source files (the launch, the step, the layout and
+    its build, the numbering), comments left out."""
     h = hashlib.sha256()
     for f in ("walk.cu", "walk_step.cuh", "ppr_internal.cuh", "renumber.cu", "graph.cu"):
-        h.update(open(os.path.join(ROOT, "paper_1903_11749_gb300", "csrc", f), "rb").read())
+        h.update(_code_only(open(os.path.join(root or ROOT, "paper_1903_11749_gb300", "csrc", f)).read()).encode())
     return h.hexdigest()[:16]
 
 

@@ -6,9 +6,9 @@
 //     word1 = W_u, the row's total weight (Sec. 2.1 routing denominator), or
 //             the target id when the row has exactly one edge (no search), or
 //             Q_v, the total fixed-point mass of a segment table (Algorithm 4);
-//             narrow blocked rows keep W_u in bits 0..31, the first sector
-//             of their summary in the summary array (bits 32..59) and their
-//             level count L (bits 60..63) above it
+//             narrow blocked rows keep W_u in bits 0..31, a summary field
+//             (bits 32..59, see blocked_sum) and their level count L (bits
+//             60..63) above it
 //   NodeRecN (32 B, one sector per node; narrow layout): a NodeRec and the
 //     first four keys of the row's top summary level when that level has at
 //     most five keys (the fifth is W_u), so the step that reads the record
@@ -19,15 +19,20 @@
 //   EdgeW (16 B): {uint64 P, int32 col, pad} -- wide layout (flat rows)
 //
 // Narrow rows are stored as static search trees ("blocked" rows).  A row with
-// d >= 2 edges has its edge records in blocks of 8 in the edge array,
-// starting on a 32-byte sector (the area rounded up to whole sectors, padding
-// keys 0xFFFFFFFF), and, when d > 8, its summary levels (top level first) in
-// the summary array, which holds nothing else: the summary sectors that every
-// draw at a node passes through sit densely in L2 lines and DRAM pages
-// instead of one per row between the blocks, which a draw reads once.  Level
-// 1 keeps the last prefix of every 8-record block, level l+1 the last key of
-// every 8-key sector of level l, up to a top level of at most 8 keys (one
-// sector).
+// d >= 2 edges has its edge records in blocks of 8 in the edge array (the
+// area rounded up to whole sectors, padding keys 0xFFFFFFFF) and, when d > 8,
+// summary levels, top level first.  Two placements (the walkers' SPLIT
+// template parameter):
+//   split (renumbered graphs far larger than L2): the summaries sit in a
+//     summary array that holds nothing else, so the summary sectors that
+//     every draw at a node passes through share L2 lines and DRAM pages
+//     instead of lying one per row between blocks that a draw reads once;
+//     every row's blocks start on 64 bytes, so a full block is one fetch;
+//   interleaved (otherwise): each row's area holds its summary, then its
+//     blocks, starting on a 32-byte sector.
+// Level 1 keeps the last prefix of every 8-record block, level l+1 the last
+// key of every 8-key sector of level l, up to a top level of at most 8 keys
+// (one sector).
 // A search reads one sector per level and one 8-record block: the same edge
 // as bisection of the flat prefix (the first P > x is unique), found with
 // ceil(log8 d) + 1 dependent loads instead of ceil(log2 d) + 1.  The alias
@@ -118,9 +123,9 @@ __host__ __device__ __forceinline__ uint32_t summary_sectors(uint32_t d)
     return S;
 }
 
-// 8-byte record slots a blocked row's blocks occupy in the edge array (a
-// one-edge row keeps its target in the node record and needs none); its
-// summary levels (summary_sectors) sit in the summary array.
+// 8-byte record slots a blocked row's blocks take (a one-edge row keeps its
+// target in the node record and needs none), not counting its summary
+// levels (summary_sectors) or the split layout's padding to 64 bytes.
 __host__ __device__ __forceinline__ uint32_t blocked_row_records(uint32_t d)
 {
     if (d <= 1) return 0;

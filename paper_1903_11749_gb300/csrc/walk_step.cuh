@@ -19,7 +19,7 @@ namespace ppr {
 struct KParams {
     const void *node;         // NodeRecN (narrow layout) or NodeRec (wide layout, alias tables)
     const void *edges;
-    const uint32_t *sum;      // narrow layout: the summary levels of the blocked rows
+    const uint32_t *sum;      // narrow split layout: the summary array of the blocked rows
     const SegEntry *seg;
     uint32_t k0, k1, T, R, tag;
     int32_t dangling;
@@ -47,7 +47,7 @@ struct KParams {
     uint64_t r_magic;         // ceil(2^40 / R): walk index -> source index by multiply-shift
     int64_t n_nodes;          // node records (for the L2 window and the checked build)
     uint64_t n_records;       // checked build: records of the edge layout walked (alias: slots)
-    uint64_t n_sum;           // checked build: summary sectors
+    uint64_t n_sum;           // checked build: sectors of the summary array
     uint64_t n_seg;           // checked build: segment entries allocated
     unsigned long long *err;  // checked build: flags of indices that left their array
 };
