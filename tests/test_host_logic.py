@@ -102,3 +102,17 @@ def test_recorded_traffic_needs_the_same_kernel_and_launch(tmp_path, monkeypatch
     assert abs(r["flat_csr_model"]["frac"] - 4000 * 32 / 1e-3 / 1e9 / 1000.0) < 1e-12
     r = bench.walker_roofline("old", shape, False, 1000, 2500, 4000, 1.0, 1000.0, "measured")
     assert r["traffic"] is None and r["frac"] == r["counted_sector_frac"] and "no current ncu" in r["basis"]
+
+def test_kernel_hash_ignores_comments_only(tmp_path):
+    """The traffic records stay valid across comment edits of the walker
+    sources and lapse on any code change."""
+    src = tmp_path / "paper_1903_11749_gb300" / "csrc"
+    src.mkdir(parents=True)
+    files = ("walk.cu", "walk_step.cuh", "ppr_internal.cuh", "renumber.cu", "graph.cu")
+    for f in files:
+        (src / f).write_text("// header\nint f_%s(int x) { return x + 1; }  // trailing\n/* block\n comment */\n" % f[0])
+    h0 = bench.kernel_source_hash(str(tmp_path))
+    (src / "walk.cu").write_text("// another header\n\nint f_w(int x) { return x + 1; }\n")
+    assert bench.kernel_source_hash(str(tmp_path)) == h0
+    (src / "walk.cu").write_text("int f_w(int x) { return x + 2; }\n")
+    assert bench.kernel_source_hash(str(tmp_path)) != h0
