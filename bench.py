@@ -47,10 +47,10 @@ WORKLOADS = {
                    desc="R-MAT scale 20, 16.8M edges (a=.57 b=.19 c=.19), Zipf(1.5) w in [1,1000], 5% dangling"),
     "er1k": dict(alpha=0.15, R=1000, seed=1, topk=32, segments=False,
                  desc="Erdos-Renyi n=1000 m=10000, w U[1,10], dense n x n counts"),
-    "rmat24": dict(alpha=0.15, R=50, seed=1, topk=64, segments=True, launch=dict(refill_lanes=24, step_loads=5),
+    "rmat24": dict(alpha=0.15, R=50, seed=1, topk=64, segments=True, launch=dict(refill_lanes=16, step_loads=6),
                    desc="R-MAT scale 24, 268M edges + hub > 1e6, Zipf(1.5) w in [1,1000], 5% dangling, "
                         "depth-3 segments for out-degree <= 8"),
-    "rmat24plain": dict(alpha=0.15, R=50, seed=1, topk=64, segments=False, launch=dict(refill_lanes=24, step_loads=5),
+    "rmat24plain": dict(alpha=0.15, R=50, seed=1, topk=64, segments=False, launch=dict(refill_lanes=16, step_loads=6),
                         desc="R-MAT scale 24 as rmat24, plain steps only"),
     "rmat20alias": dict(alpha=0.2, R=100, seed=1, topk=32, segments=False, sampler=1,
                         desc="R-MAT scale 20 as rmat20, integer alias sampler (Algorithm 1 tables built every step)"),

@@ -69,7 +69,7 @@ def test_rmat24_every_source_equals_threaded_oracle(oracle, mode):
     1.57 M edges): every source against the oracle in source ranges on host
     threads, with depth-3 segment tables (the oracle builds every table up
     front, so the threads only read them) or with alias tables, each in the
-    launch shape the benchmark times (segments: refill 24)."""
+    launch shape the benchmark times (segments: refill 16)."""
     from paper_1903_11749_gb300 import build as B
     B.build()
     from paper_1903_11749_gb300 import ppr
@@ -77,7 +77,7 @@ def test_rmat24_every_source_equals_threaded_oracle(oracle, mode):
     kw = dict(alpha=0.15, R=50, seed=1)
     seg, sampler = (True, 0) if mode == "segments" else (False, 1)
     G = ppr.Context(0).load_graph(g.n, g.row_ptr, g.col, g.w)
-    res = G.run(segments=seg, sampler=sampler, refill_lanes=24 if seg else 0, **kw)
+    res = G.run(segments=seg, sampler=sampler, refill_lanes=16 if seg else 0, **kw)
     rp, col, cnt = res.sparse_rows()
     steps_gpu = res.info().steps
     del res, G
