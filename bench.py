@@ -128,6 +128,16 @@ class Clocks:
                                          stderr=subprocess.DEVNULL)
         except (OSError, FileNotFoundError):
             self.proc = None
+            return
+        # nvidia-smi's start-up (NVML initialisation, some hundred ms of host
+        # work) would otherwise overlap a short timed region whose steps are
+        # bound by host launch latency: wait for its first sample (at most 3 s)
+        t0 = time.perf_counter()
+        while self.proc.poll() is None and time.perf_counter() - t0 < 3.0:
+            self.f.flush()
+            if os.path.getsize(self.path) > 0:
+                break
+            time.sleep(0.02)
 
     def stop(self):
         if not self.proc:
@@ -970,13 +980,19 @@ def main():
     walks_s = units[1] / T_max
 
     # plain one-thread-per-walk kernel on the same pass, for comparison
+    # (short steps: as many warm-up and timed steps as the persistent kernel,
+    # under a clock sampler of its own, so both see the same host conditions)
     plain = None
     if not args.no_plain:
-        G, r = step(kernel=ppr.KERNEL_PLAIN)
-        r.wait()
-        del r, G
+        short = bool(step_ms) and statistics.mean(step_ms) < 10
+        for _ in range(max(1, args.warmup if short else 1)):
+            G, r = step(kernel=ppr.KERNEL_PLAIN)
+            r.wait()
+            del r, G
         pm, pk = [], []
-        for _ in range(max(1, min(10 if step_ms and statistics.mean(step_ms) < 10 else 3, args.steps))):
+        pclocks = Clocks(local, None)
+        pclocks.start()
+        for _ in range(max(1, args.steps if short else min(3, args.steps))):
             flush.fill_(1)
             e0 = torch.cuda.Event(enable_timing=True)
             e1 = torch.cuda.Event(enable_timing=True)
@@ -988,9 +1004,11 @@ def main():
             pm.append(e0.elapsed_time(e1))
             pk.append(r.info().kernel_ms)
             del r, G
+        pclk = pclocks.stop()
         plain = {"value": steps_per_pass / (statistics.mean(pm) / 1e3), "unit": "walk steps/s",
-                 "kernel_ms": statistics.mean(pk),
-                 "ms_per_step": statistics.mean(pm), "kernel": "one thread per walk + separate aggregation"}
+                 "kernel_ms": statistics.mean(pk), "steps": len(pm),
+                 "ms_per_step": statistics.mean(pm), "kernel": "one thread per walk + separate aggregation",
+                 "clocks": pclk}
 
     # end to end through the C ABI with host buffers: pinned CSR in, rows + top-k out to pinned memory
     e2e = None

@@ -579,7 +579,8 @@ static int run_common(ppr_ctx *ctx, const ppr_graph *g, const ppr_run_args *a, c
     const Outputs o{r->d_nnz, r->d_cols, r->d_cnts, r->cap, r->d_topk_idx, r->d_topk_cnt, r->topk, r->d_steps};
     for (int64_t b = 0; b < r->S; b += batch) {
         const int64_t nb = std::min<int64_t>(r->S - b, batch);
-        rc = launch_walks(ctx, g, plan, o, r->src_begin + b, nb, d_list ? d_list + b : nullptr, b, ws, st, r);
+        rc = launch_walks(ctx, g, plan, o, r->src_begin + b, nb, d_list ? d_list + b : nullptr, b, ws, st, r,
+                          b > 0);
         if (rc) {
             cudaStreamSynchronize(st);
             return fail(rc);
@@ -719,7 +720,8 @@ int ppr_run_to_host(ppr_ctx *ctx, const ppr_graph *g, const ppr_run_args *a, int
             if (i >= 2 && (e = cudaStreamWaitEvent(st, q.copied, 0)) != cudaSuccess)
                 return finish(cuda_fail(e, "cudaStreamWaitEvent"));
             const Outputs o{q.nnz, q.cols, q.cnts, rcap, q.ti, q.tc, k, r->d_steps};
-            if ((rc = launch_walks(ctx, g, plan, o, a->src_begin + b0, nb, nullptr, 0, ws, st, r))) return finish(rc);
+            if ((rc = launch_walks(ctx, g, plan, o, a->src_begin + b0, nb, nullptr, 0, ws, st, r, i > 0)))
+                return finish(rc);
             exclusive_scan_u32(q.nnz, nb, q.off, q.tmp, st);
             k_compact_rows<<<std::max(1, cblocks), 256, 0, st>>>(nb, rcap, q.nnz, q.off, q.cols, q.cnts, q.ccol, q.ccnt);
             note_launch();

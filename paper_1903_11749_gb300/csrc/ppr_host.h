@@ -186,7 +186,11 @@ size_t launch_workspace_bytes(const ppr_graph *g, const RunPlan &p, int64_t S);
 // Enqueues walks and reduction for S sources: node s_begin + i, or
 // src_list[i] (device) when given; rows go to out_row0 + i.  ws holds
 // launch_workspace_bytes.  ev_owner: record walker-time events into it.
+// The persistent walker's work queue (o.counters[1]) must be zero when the
+// launch runs: callers zero the counters before their first launch and pass
+// reset_queue for every later launch on the same counters.
 int launch_walks(ppr_ctx *ctx, const ppr_graph *g, const RunPlan &p, const Outputs &o, int64_t s_begin, int64_t S,
-                 const uint32_t *src_list, int64_t out_row0, unsigned char *ws, cudaStream_t st, ppr_result *ev_owner);
+                 const uint32_t *src_list, int64_t out_row0, unsigned char *ws, cudaStream_t st, ppr_result *ev_owner,
+                 bool reset_queue = false);
 
 }  // namespace ppr

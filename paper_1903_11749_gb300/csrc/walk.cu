@@ -8,6 +8,7 @@
 // Both write one endpoint per walk to HBM; k_aggregate (aggregate.cuh) then
 // turns each source's R endpoints into its count row and top-k.
 #include <algorithm>
+#include <atomic>
 #include <type_traits>
 #include <mutex>
 
@@ -229,12 +230,19 @@ static int launch_typed(ppr_ctx *ctx, const KParams &kp, const RunPlan &plan, in
         if ((rc = walker_event(r, st))) return rc;
         return launch_aggregate(ctx, AggParams{kp.ends, kp.R, kp.P2, S, kp.out_row0, kp.out, kp.order}, st);
     }
-    int per_sm = 0;
     // walkers per CTA: 32 * warps_per_block (4 or 8 warps; default 8)
     const int wpb = plan.warps_per_block == 4 ? 4 : 8;
-    PPR_CUDA(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_walk_persistent<E, SEG, STATS, BOUNDED, SPLIT>,
-                                                           32 * wpb, 0));
-    if (per_sm < 1) per_sm = 1;
+    // resident blocks per SM: fixed for this kernel, device and block size,
+    // so queried once (a host call per run shows in short runs)
+    static std::atomic<int> occupancy[64][2];
+    std::atomic<int> *occ = ctx->device >= 0 && ctx->device < 64 ? &occupancy[ctx->device][wpb == 8] : nullptr;
+    int per_sm = occ ? occ->load(std::memory_order_relaxed) : 0;
+    if (per_sm < 1) {
+        PPR_CUDA(cudaOccupancyMaxActiveBlocksPerMultiprocessor(
+            &per_sm, k_walk_persistent<E, SEG, STATS, BOUNDED, SPLIT>, 32 * wpb, 0));
+        if (per_sm < 1) per_sm = 1;
+        if (occ) occ->store(per_sm, std::memory_order_relaxed);
+    }
     int64_t blocks = (int64_t)ctx->sms * per_sm;
     int64_t needed = ((int64_t)kp.nchunks + wpb - 1) / wpb;
     if (blocks > needed) blocks = std::max<int64_t>(needed, 1);
@@ -383,7 +391,8 @@ static int launch_narrow(ppr_ctx *ctx, const KParams &kp, const RunPlan &plan, i
 }
 
 int launch_walks(ppr_ctx *ctx, const ppr_graph *g, const RunPlan &plan, const Outputs &o, int64_t s_begin, int64_t S,
-                 const uint32_t *src_list, int64_t out_row0, unsigned char *ws, cudaStream_t st, ppr_result *ev_owner)
+                 const uint32_t *src_list, int64_t out_row0, unsigned char *ws, cudaStream_t st, ppr_result *ev_owner,
+                 bool reset_queue)
 {
     if (S <= 0) return PPR_OK;
     KParams kp{};
@@ -468,7 +477,7 @@ int launch_walks(ppr_ctx *ctx, const ppr_graph *g, const RunPlan &plan, const Ou
             kp.walks = walks;
             kp.nchunks = (uint32_t)((walks + cw - 1) / cw);
         }
-        PPR_CUDA(cudaMemsetAsync(kp.queue, 0, sizeof(unsigned long long), st));
+        if (reset_queue) PPR_CUDA(cudaMemsetAsync(kp.queue, 0, sizeof(unsigned long long), st));
     }
     if (plan.sampler == 1)
         return plan.stats ? launch_typed<AliasEdges, false, true>(ctx, kp, plan, S, st, ev_owner)
