@@ -26,6 +26,7 @@ of the same workload and prints the same line with "impl": "reference".
 from __future__ import annotations
 
 import argparse
+import gc
 import hashlib
 import re
 import json
@@ -105,6 +106,18 @@ def reduce_over_ranks(seconds: float, units, world: int, dist=None, device=None)
         dist.all_reduce(t, op=dist.ReduceOp.MAX)
         dist.all_reduce(u, op=dist.ReduceOp.SUM)
     return float(t.item()), [float(x) for x in u.tolist()]
+
+
+def gc_pause():
+    """Python's cyclic collector off over a timed region: a full collection of
+    this process's objects takes tens of milliseconds and would land inside
+    whichever step it interrupts (short steps are bound by host launches)."""
+    gc.collect()
+    gc.disable()
+
+
+def gc_resume():
+    gc.enable()
 
 
 class Clocks:
@@ -462,6 +475,7 @@ def run_batched(args):
     clocks.start()
     launches0 = ppr.kernel_launches()
     step_ms = []
+    gc_pause()
     for _ in range(args.steps):
         flush.fill_(1)
         e0 = torch.cuda.Event(enable_timing=True)
@@ -473,6 +487,7 @@ def run_batched(args):
         e1.synchronize()
         step_ms.append(e0.elapsed_time(e1))
     torch.cuda.synchronize(dev)
+    gc_resume()
     clk = clocks.stop()
     T_max, units = reduce_over_ranks(sum(step_ms) / 1e3, [draws * args.steps, walks * args.steps], world, dist, dev)
     # kernels per replay: chunk count, 3 scan kernels, chunk fill, walker, reduction
@@ -502,6 +517,7 @@ def run_batched(args):
         o_ti = torch.empty((N, k), dtype=torch.int32).pin_memory()
         o_tc = torch.empty((N, k), dtype=torch.int32).pin_memory()
         times = []
+        gc_pause()
         for it in range(3):
             torch.cuda.synchronize(dev)
             t0 = time.perf_counter()
@@ -512,6 +528,7 @@ def run_batched(args):
             if it > 0:
                 times.append(time.perf_counter() - t0)
             del r, Gh
+        gc_resume()
         e2e = {"value": draws / statistics.mean(times), "unit": "walk steps/s",
                "h2d_bytes_per_step": int(inst.row_ptr.nbytes + inst.col.nbytes + inst.w.nbytes),
                "d2h_bytes_per_step": int((N + 1) * 8 + nz * 8 + N * k * 8), "ms_per_step": 1e3 * statistics.mean(times)}
@@ -958,6 +975,7 @@ def main():
     clocks = Clocks(local, None)
     clocks.start()
     launches0 = ppr.kernel_launches()
+    gc_pause()
     for _ in range(args.steps):
         flush.fill_(1)  # L2 flush outside the timed events
         e0 = torch.cuda.Event(enable_timing=True)
@@ -972,6 +990,7 @@ def main():
         run_ms.append(r.info().run_ms)
         del r, G
     torch.cuda.synchronize(dev)
+    gc_resume()
     launches = ppr.kernel_launches() - launches0
     clk = clocks.stop()
     T = sum(step_ms) / 1e3
@@ -992,6 +1011,7 @@ def main():
         pm, pk = [], []
         pclocks = Clocks(local, None)
         pclocks.start()
+        gc_pause()
         for _ in range(max(1, args.steps if short else min(3, args.steps))):
             flush.fill_(1)
             e0 = torch.cuda.Event(enable_timing=True)
@@ -1004,6 +1024,7 @@ def main():
             pm.append(e0.elapsed_time(e1))
             pk.append(r.info().kernel_ms)
             del r, G
+        gc_resume()
         pclk = pclocks.stop()
         plain = {"value": steps_per_pass / (statistics.mean(pm) / 1e3), "unit": "walk steps/s",
                  "kernel_ms": statistics.mean(pk), "steps": len(pm),
@@ -1046,6 +1067,7 @@ def main():
             return t1 - t0, nnz
 
         times, serial_times, nnz = [], [], 0
+        gc_pause()
         for it in range(1 + min(5, args.steps)):
             dt, nnz = e2e_once(True)
             if it > 0:
@@ -1054,6 +1076,7 @@ def main():
             dt, _ = e2e_once(False)
             if it > 0:
                 serial_times.append(dt)
+        gc_resume()
         d2h = o_rp.numel() * 8 + nnz * 8 + (S * wl["topk"] * 8 if wl["topk"] else 0)
         # the median iteration: host-timed iterations catch occasional host stalls
         e2e = {"value": steps_per_pass / statistics.median(times), "unit": "walk steps/s", "h2d_bytes_per_step": h2d,

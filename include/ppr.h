@@ -320,9 +320,12 @@ int ppr_result_get_info(const ppr_result *r, ppr_result_info *info);
  * and the top-k straight into host memory, pipelined against the walks
  * (the batching of the paper's pipelines, Sec. 4.3, with the output stream
  * of each batch overlapped with the next batch's walks): the sources are
- * cut into `parts` batches (0 = the library's choice); while batch i+1 walks
- * on args->stream, batch i's rows are compacted and copied to the host on a
- * second stream of the library's own.  Returns when every row is in place.
+ * cut into `parts` batches (0 = the library's choice), the last of which is
+ * cut once more into three quarters and a quarter (when there are two or
+ * more), so that little copying is left after the last walk; while batch
+ * i+1 walks on args->stream, batch i's rows are compacted and copied to the
+ * host on a second stream of the library's own.  Returns when every row is
+ * in place.
  *   row_ptr  int64[S+1] (row s = entries [row_ptr[s], row_ptr[s+1]))
  *   col, cnt int32 / uint32 [cap]; cap >= nnz or PPR_ERANGE (nothing beyond
  *            cap is written; row_ptr is then incomplete)

@@ -653,6 +653,13 @@ int ppr_run_to_host(ppr_ctx *ctx, const ppr_graph *g, const ppr_run_args *a, int
         B = std::max<int64_t>(1, std::min<int64_t>(B, fit));
     }
     P = (S + B - 1) / B;
+    // batch starts: B sources each, and the last batch split into three
+    // quarters and one, so the copies left after the last walk are short
+    std::vector<int64_t> start;
+    for (int64_t b = 0; b < S; b += B) start.push_back(b);
+    if (P >= 2 && S - start.back() >= 4) start.push_back(S - (S - start.back()) / 4);
+    start.push_back(S);
+    P = (int64_t)start.size() - 1;
     const int64_t tiles = (B + kScanTile - 1) / kScanTile;
     struct Slot {
         uint32_t *nnz = nullptr;
@@ -716,7 +723,7 @@ int ppr_run_to_host(ppr_ctx *ctx, const ppr_graph *g, const ppr_run_args *a, int
         if (i < P) {  // batch i: walk, reduce, compact on the run's stream
             Range batch_range("batch");
             Slot &q = slot[i & 1];
-            const int64_t b0 = i * B, nb = std::min<int64_t>(B, S - b0);
+            const int64_t b0 = start[i], nb = start[i + 1] - b0;
             if (i >= 2 && (e = cudaStreamWaitEvent(st, q.copied, 0)) != cudaSuccess)
                 return finish(cuda_fail(e, "cudaStreamWaitEvent"));
             const Outputs o{q.nnz, q.cols, q.cnts, rcap, q.ti, q.tc, k, r->d_steps};
@@ -740,7 +747,7 @@ int ppr_run_to_host(ppr_ctx *ctx, const ppr_graph *g, const ppr_run_args *a, int
         if (i >= 1) {  // batch i - 1: its copies on the copy stream, overlapping batch i
             const int64_t j = i - 1;
             Slot &q = slot[j & 1];
-            const int64_t b0 = j * B, nb = std::min<int64_t>(B, S - b0);
+            const int64_t b0 = start[j], nb = start[j + 1] - b0;
             if ((e = cudaEventSynchronize(q.ready)) != cudaSuccess) return finish(cuda_fail(e, "batch"));
             const uint64_t tot = ctx->pinned[j & 1] - base;  // the batch's last absolute row start, less the base
             if ((uint64_t)cap < base + tot) {
