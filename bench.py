@@ -1050,10 +1050,14 @@ def main():
                       topk=wl["topk"], segments=wl["segments"], stream=stream, sampler=wl.get("sampler", 0), **tune)
         ti_arg = (o_ti, o_tc) if wl["topk"] else (None, None)
 
+        load_call_ms = []  # host time until ppr_load_graph returns (its copies and build run on)
+
         def e2e_once(pipelined):
             torch.cuda.synchronize(dev)
             t0 = time.perf_counter()
             G = ctx.load_graph(g.n, h_rp, h_col, h_w, stream=stream, m=g.m, renumber=renum)
+            if pipelined:
+                load_call_ms.append(1e3 * (time.perf_counter() - t0))
             if pipelined:  # rows and top-k copied to the host batch by batch, behind the walks
                 nnz, _ = G.run_to_host(o_rp, o_col, o_cnt, *ti_arg, **run_kw)
             else:  # run, then read everything back
@@ -1082,6 +1086,7 @@ def main():
         e2e = {"value": steps_per_pass / statistics.median(times), "unit": "walk steps/s", "h2d_bytes_per_step": h2d,
                "d2h_bytes_per_step": d2h, "ms_per_step": 1e3 * statistics.median(times),
                "ms_mean": 1e3 * statistics.mean(times), "ms_each": [1e3 * t for t in times],
+               "load_call_ms_each": load_call_ms[1:],
                "call": "ppr_load_graph (pinned host CSR) + ppr_run_to_host (pinned host rows and top-k)",
                "unpipelined": {"value": steps_per_pass / statistics.median(serial_times),
                                "ms_per_step": 1e3 * statistics.median(serial_times),
