@@ -116,3 +116,51 @@ def test_kernel_hash_ignores_comments_only(tmp_path):
     assert bench.kernel_source_hash(str(tmp_path)) == h0
     (src / "walk.cu").write_text("int f_w(int x) { return x + 2; }\n")
     assert bench.kernel_source_hash(str(tmp_path)) != h0
+
+
+def test_committed_traffic_records_belong_to_the_committed_walker():
+    """Every DRAM traffic record under profiles/ was taken on the walker
+    sources as they stand (the benchmark reports no DRAM fraction otherwise),
+    with a positive figure per draw and the launch shape of its workload."""
+    d = json.load(open(bench.os.path.join(bench.ROOT, "profiles", "walker_traffic.json")))
+    h = bench.kernel_source_hash()
+    for name, e in d.items():
+        if name.startswith("_"):
+            continue
+        assert e["kernel_hash"] == h, name
+        assert e["dram_bytes_per_draw"] > 0, name
+        assert e["launch"] == {k: v for k, v in bench.WORKLOADS[name].get("launch", {}).items() if v}, name
+
+
+def test_clock_samples_give_median_max_and_reasons(tmp_path):
+    """The sampler's CSV (nvidia-smi query fields) becomes the median SM clock
+    under load, the highest maximum clock and the throttle reasons seen."""
+    path = tmp_path / "clocks.csv"
+    rows = ["0, 2070, 2070, 900.1, 0x0, Not Active, Not Active, Not Active, Not Active",
+            "0, 1980, 2070, 1390.0, 0x4, Not Active, Not Active, Not Active, Active",
+            "0, 2070, 2070, 1100.0, 0x0, Not Active, Not Active, Not Active, Not Active",
+            "garbled line"]
+    path.write_text("\n".join(rows) + "\n")
+
+    class _Done:
+        def terminate(self):
+            pass
+
+        def wait(self, timeout=None):
+            return 0
+
+    c = bench.Clocks(0, str(path))
+    c.proc, c.f = _Done(), open(tmp_path / "unused", "w")
+    out = c.stop()
+    assert out == {"sm_mhz": 2070.0, "sm_max_mhz": 2070.0, "reasons": ["sw_power_cap"], "samples": 3}
+
+
+def test_collector_paused_over_timed_regions():
+    import gc
+    was = gc.isenabled()
+    bench.gc_pause()
+    assert not gc.isenabled()
+    bench.gc_resume()
+    assert gc.isenabled()
+    if not was:
+        gc.disable()
